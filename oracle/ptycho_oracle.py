@@ -1,0 +1,388 @@
+"""FP64 CPU oracle of the ptychographic reconstruction hot path.
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module.  The library
+itself (``paper_2202_03144_b300``) never calls it and has no CPU fallback.
+
+What it computes, and where it comes from
+-----------------------------------------
+The ptychopy paper (Yue et al., arXiv 2202.03144) names the method and its
+three reconstruction algorithms but prints no formulas:
+
+* the far-field forward model -- an exit wave (probe times object patch),
+  whose Fourier transform's squared modulus is the measured diffraction
+  pattern -- and the "multiple FFTs over thousands of diffraction patterns"
+  are stated in Sec. 2.3 (Data reconstruction back end module);
+* ePIE (Maiden & Rodenburg 2009), DM (Thibault et al. 2009, 2008) and LSQML
+  (Thibault & Menzel 2013; Odstrcil et al. 2018) are named in the Abstract,
+  Sec. 1 and Sec. 2.3; the multi-mode probe and the iteration after which
+  the probe is updated are GUI parameters in Sec. 2.2.
+
+The update rules below are therefore the standard published forms of those
+cited algorithms, written out from their mathematics; every constant that the
+paper does not fix (tau, reg, lambda, beta, the ePIE order) is a documented
+reading of this library, identical on the CUDA side.
+
+Conventions (shared with the C ABI):
+
+* O: object [Ny, Nx] complex; P: probe modes [K, M, M] complex;
+* positions: (y, x) of each patch's top-left corner, rounded half-to-even;
+* F: unnormalised 2-D DFT (numpy ``fft2``); F^-1 = numpy ``ifft2`` (1/M^2);
+* I: measured intensities [J, M, M], detector-centred (zero frequency at
+  pixel (M/2, M/2)); a negative value marks a masked pixel.
+
+Only library primitives used: ``numpy.fft.fft2/ifft2`` for the DFT and
+elementwise numpy.  No blocking, fusion or reordering beyond the algorithms'
+own steps.  Every function is pinned by the CPU tests in ``tests/``
+(brute-force DFT, Parseval, adjointness, projection idempotence, fixed
+points, reductions to an error-reduction step, least-squares optimality).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TAU = 1e-30          # modulus floor of the projection (FP64)
+MASK64 = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------------------
+# Fourier transform and geometry (Sec. 2.3: far-field diffraction, FFTs)
+# ---------------------------------------------------------------------------
+
+def fft2(x: np.ndarray) -> np.ndarray:
+    """Unnormalised forward 2-D DFT over the last two axes."""
+    return np.fft.fft2(x, axes=(-2, -1))
+
+
+def ifft2(x: np.ndarray) -> np.ndarray:
+    """Inverse 2-D DFT over the last two axes, normalised by 1/M^2."""
+    return np.fft.ifft2(x, axes=(-2, -1))
+
+
+def round_positions(positions: np.ndarray) -> np.ndarray:
+    """Integer top-left corners: round half to even."""
+    return np.rint(np.asarray(positions, dtype=np.float64)).astype(np.int64)
+
+
+def check_positions(pos: np.ndarray, M: int, ny: int, nx: int) -> None:
+    if pos.ndim != 2 or pos.shape[1] != 2:
+        raise ValueError("positions must be [J, 2]")
+    if (pos < 0).any() or (pos[:, 0] + M > ny).any() or (pos[:, 1] + M > nx).any():
+        raise ValueError("a patch falls outside the object")
+
+
+def gather(O: np.ndarray, pos: np.ndarray, M: int) -> np.ndarray:
+    """Object patches O_j = O[y_j:y_j+M, x_j:x_j+M], shape [J, M, M]."""
+    return np.stack([O[y:y + M, x:x + M] for y, x in pos])
+
+
+def scatter_add(shape: tuple, pos: np.ndarray, patches: np.ndarray) -> np.ndarray:
+    """Sum_j S_j[patches_j]: the adjoint of :func:`gather`, summed in j order."""
+    M = patches.shape[-1]
+    acc = np.zeros(shape, dtype=patches.dtype)
+    for j, (y, x) in enumerate(pos):
+        acc[y:y + M, x:x + M] += patches[j]
+    return acc
+
+
+def exit_waves(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    """psi_{j,k} = P_k * O_j, shape [J, K, M, M]."""
+    M = P.shape[-1]
+    return P[None, :, :, :] * gather(O, pos, M)[:, None, :, :]
+
+
+def far_field_intensity(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    """Detector-centred I_j = fftshift(sum_k |F(P_k O_j)|^2), shape [J, M, M]."""
+    Psi = fft2(exit_waves(O, P, pos))
+    I = np.sum(np.abs(Psi) ** 2, axis=1)
+    return np.fft.fftshift(I, axes=(-2, -1))
+
+
+def to_fft_order(I: np.ndarray) -> np.ndarray:
+    """Move the zero frequency of detector-centred frames back to pixel (0, 0)."""
+    return np.fft.ifftshift(I, axes=(-2, -1))
+
+
+# ---------------------------------------------------------------------------
+# Modulus projection and Fourier error
+# ---------------------------------------------------------------------------
+
+def project(Psi: np.ndarray, I_fft: np.ndarray, tau: float = TAU) -> np.ndarray:
+    """Replace the mode-summed Fourier modulus by sqrt(I).
+
+    Psi: [J, K, M, M] far fields; I_fft: [J, M, M] intensities in FFT order.
+    A = sqrt(sum_k |Psi_k|^2).  Where I < 0 (masked) Psi is returned
+    unchanged; where A <= tau the result is 0; elsewhere Psi_k sqrt(I) / A.
+    """
+    A = np.sqrt(np.sum(np.abs(Psi) ** 2, axis=1))
+    masked = I_fft < 0
+    sqrtI = np.sqrt(np.where(masked, 0.0, I_fft))
+    safe_A = np.where(A > tau, A, 1.0)
+    ratio = np.where(A > tau, sqrtI / safe_A, 0.0)
+    out = Psi * ratio[:, None, :, :]
+    return np.where(masked[:, None, :, :], Psi, out)
+
+
+def fourier_error(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) -> float:
+    """E = sum m (A - sqrt I)^2 / sum m I over all frames and unmasked pixels,
+    from a fresh forward pass at the current (O, P)."""
+    I_fft = to_fft_order(I)
+    A = np.sqrt(np.sum(np.abs(fft2(exit_waves(O, P, pos))) ** 2, axis=1))
+    m = I_fft >= 0
+    sqrtI = np.sqrt(np.where(m, I_fft, 0.0))
+    num = float(np.sum(np.where(m, (A - sqrtI) ** 2, 0.0)))
+    den = float(np.sum(np.where(m, I_fft, 0.0)))
+    return num / den if den > 0 else 0.0
+
+
+def fourier_residual(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) -> np.ndarray:
+    """chi_{j,k} = F^-1 Pi(F(P_k O_j)) - P_k O_j, shape [J, K, M, M]."""
+    phi = exit_waves(O, P, pos)
+    return ifft2(project(fft2(phi), to_fft_order(I))) - phi
+
+
+# ---------------------------------------------------------------------------
+# ePIE  (Maiden & Rodenburg 2009; multi-mode form of Thibault & Menzel 2013)
+# ---------------------------------------------------------------------------
+
+def splitmix64_stream(state: int):
+    """Counter-based 64-bit generator (Steele, Lea & Flood's SplitMix64)."""
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & MASK64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        yield z ^ (z >> 31)
+
+
+def epie_order(seed: int, t: int, J: int) -> np.ndarray:
+    """Visiting order of iteration t: identity for seed 0, else a
+    Fisher-Yates (Durstenfeld) shuffle drawn from SplitMix64(seed XOR t)."""
+    order = list(range(J))
+    if seed == 0:
+        return np.asarray(order, dtype=np.int64)
+    g = splitmix64_stream((seed ^ t) & MASK64)
+    for i in range(J - 1, 0, -1):
+        r = next(g) % (i + 1)
+        order[i], order[r] = order[r], order[i]
+    return np.asarray(order, dtype=np.int64)
+
+
+def epie_position_update(O, P, y, x, I_fft_j, alpha, beta, update_probe):
+    """One ePIE step at the patch with top-left (y, x); updates O and P in place.
+
+    psi_k = P_k O_j; Delta_k = F^-1 Pi(F psi)_k - psi_k;
+    O_j += alpha sum_k conj(P_k) Delta_k / max_u sum_k |P_k(u)|^2;
+    P_k += beta conj(O_j_old) Delta_k / max_u |O_j_old(u)|^2  (if update_probe),
+    both from the values held before this step.
+    """
+    M = P.shape[-1]
+    Oj = O[y:y + M, x:x + M].copy()
+    psi = P * Oj[None]
+    Delta = ifft2(project(fft2(psi)[None], I_fft_j[None])[0]) - psi
+    pmax = float(np.max(np.sum(np.abs(P) ** 2, axis=0)))
+    omax = float(np.max(np.abs(Oj) ** 2))
+    if pmax > 0:
+        O[y:y + M, x:x + M] = Oj + alpha * np.sum(np.conj(P) * Delta, axis=0) / pmax
+    if update_probe and omax > 0:
+        P[...] = P + beta * np.conj(Oj)[None] * Delta / omax
+
+
+def epie_iteration(O, P, pos, I, t, seed=0, alpha=1.0, beta=1.0, probe_start=0):
+    """One ePIE sweep (iteration index t) over all positions; returns new (O, P)."""
+    O = O.astype(np.complex128).copy()
+    P = P.astype(np.complex128).copy()
+    I_fft = to_fft_order(I)
+    for j in epie_order(seed, t, len(pos)):
+        y, x = pos[j]
+        epie_position_update(O, P, y, x, I_fft[j], alpha, beta, t >= probe_start)
+    return O, P
+
+
+# ---------------------------------------------------------------------------
+# Overlap quantities shared by DM and LSQML
+# ---------------------------------------------------------------------------
+
+def object_denominator(P: np.ndarray, pos: np.ndarray, shape: tuple) -> np.ndarray:
+    """den_O = sum_j S_j[sum_k |P_k|^2] (real, object-sized)."""
+    w = np.sum(np.abs(P) ** 2, axis=0)
+    return scatter_add(shape, pos, np.broadcast_to(w, (len(pos),) + w.shape).astype(np.float64))
+
+
+def object_numerator(P: np.ndarray, X: np.ndarray, pos: np.ndarray, shape: tuple,
+                     weights: np.ndarray | None = None) -> np.ndarray:
+    """sum_j w_j S_j[sum_k conj(P_k) X_{j,k}] (object-sized)."""
+    c = np.sum(np.conj(P)[None] * X, axis=1)
+    if weights is not None:
+        c = c * np.asarray(weights, dtype=np.float64)[:, None, None]
+    return scatter_add(shape, pos, c)
+
+
+def probe_numerator(O: np.ndarray, X: np.ndarray, pos: np.ndarray,
+                    weights: np.ndarray | None = None) -> np.ndarray:
+    """sum_j w_j conj(O_j) X_{j,k}, shape [K, M, M]."""
+    M = X.shape[-1]
+    Oc = np.conj(gather(O, pos, M))[:, None]
+    t = Oc * X
+    if weights is not None:
+        t = t * np.asarray(weights, dtype=np.float64)[:, None, None, None]
+    return np.sum(t, axis=0)
+
+
+def probe_denominator(O: np.ndarray, pos: np.ndarray, M: int) -> np.ndarray:
+    """den_P = sum_j |O_j|^2, shape [M, M]."""
+    return np.sum(np.abs(gather(O, pos, M)) ** 2, axis=0)
+
+
+# ---------------------------------------------------------------------------
+# DM  (difference map; Thibault et al. 2009 / 2008)
+# ---------------------------------------------------------------------------
+
+def dm_init(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    """Initial exit-wave state psi = P_k O_j."""
+    return exit_waves(O, P, pos)
+
+
+def dm_overlap_update(O, P, psi, pos, reg, update_probe):
+    """Overlap projection: object then probe least-squares update from psi.
+
+    O <- (sum_j S_j[sum_k conj(P_k) psi_jk] + d_O O) / (den_O + d_O),
+    then, with the new O, P_k <- (sum_j conj(O_j) psi_jk + d_P P_k) / (den_P + d_P),
+    d = reg * max(den).
+    """
+    M = P.shape[-1]
+    den_O = object_denominator(P, pos, O.shape)
+    num_O = object_numerator(P, psi, pos, O.shape)
+    d_O = reg * float(den_O.max())
+    O = (num_O + d_O * O) / (den_O + d_O)
+    if update_probe:
+        den_P = probe_denominator(O, pos, M)
+        num_P = probe_numerator(O, psi, pos)
+        d_P = reg * float(den_P.max())
+        P = (num_P + d_P * P) / (den_P[None] + d_P)
+    return O, P
+
+
+def dm_iteration(O, P, psi, pos, I, t, reg=1e-3, probe_start=0):
+    """One DM iteration (index t); returns new (O, P, psi).
+
+    1-2. overlap update of O, then of P (when t >= probe_start);
+    3.   phi = P_k O_j;  psi <- psi + F^-1 Pi(F(2 phi - psi)) - phi.
+    """
+    O, P = dm_overlap_update(O.astype(np.complex128), P.astype(np.complex128), psi, pos,
+                             reg, t >= probe_start)
+    phi = exit_waves(O, P, pos)
+    psi = psi + ifft2(project(fft2(2.0 * phi - psi), to_fft_order(I))) - phi
+    return O, P, psi
+
+
+# ---------------------------------------------------------------------------
+# LSQML  (Odstrcil et al. 2018, amplitude likelihood, whole batch)
+# ---------------------------------------------------------------------------
+
+def lsqml_directions(O, P, chi, pos, reg, update_probe):
+    """Steepest-descent directions and their normalising denominators.
+
+    dO = sum_j S_j[sum_k conj(P_k) chi_jk] / (den_O + d_O);
+    dP_k = sum_j conj(O_j) chi_jk / (den_P + d_P)   (zero if the probe is fixed).
+    Returns (dO, dP, den_O + d_O, den_P + d_P or None).
+    """
+    M = P.shape[-1]
+    den_O = object_denominator(P, pos, O.shape)
+    d_O = reg * float(den_O.max())
+    wO = den_O + d_O
+    dO = object_numerator(P, chi, pos, O.shape) / wO
+    if update_probe:
+        den_P = probe_denominator(O, pos, M)
+        d_P = reg * float(den_P.max())
+        wP = den_P + d_P
+        dP = probe_numerator(O, chi, pos) / wP[None]
+    else:
+        wP = None
+        dP = np.zeros_like(P)
+    return dO, dP, wO, wP
+
+
+def lsqml_solve_2x2(A11: float, A12: float, A22: float, r1: float, r2: float) -> tuple[float, float]:
+    """Solve ([[A11, A12], [A12, A22]] + lam I) alpha = r, lam = 1e-6 (A11 + A22) / 2;
+    alpha = 0 when the trace vanishes."""
+    tr = A11 + A22
+    if not tr > 0.0:
+        return 0.0, 0.0
+    lam = 1e-6 * tr / 2.0
+    a, b, d = A11 + lam, A12, A22 + lam
+    det = a * d - b * b
+    return (d * r1 - b * r2) / det, (a * r2 - b * r1) / det
+
+
+def lsqml_step_sizes(O, P, chi, pos, dO, dP):
+    """Per-position (alpha_O, alpha_P): least squares fit of chi_j by
+    alpha_O a_j + alpha_P b_j with a_jk = P_k dO_j and b_jk = O_j dP_k."""
+    M = P.shape[-1]
+    Oj = gather(O, pos, M)
+    dOj = gather(dO, pos, M)
+    aO = np.empty(len(pos))
+    aP = np.empty(len(pos))
+    for j in range(len(pos)):
+        a = P * dOj[j][None]
+        b = Oj[j][None] * dP
+        A11 = float(np.sum(np.abs(a) ** 2))
+        A12 = float(np.real(np.sum(np.conj(a) * b)))
+        A22 = float(np.sum(np.abs(b) ** 2))
+        r1 = float(np.real(np.sum(np.conj(a) * chi[j])))
+        r2 = float(np.real(np.sum(np.conj(b) * chi[j])))
+        aO[j], aP[j] = lsqml_solve_2x2(A11, A12, A22, r1, r2)
+    return aO, aP
+
+
+def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_steps=False):
+    """One LSQML iteration (index t); returns new (O, P) [and (alpha_O, alpha_P)].
+
+    1. chi_jk = F^-1 Pi(F(P_k O_j)) - P_k O_j;
+    2. directions dO, dP (see :func:`lsqml_directions`);
+    3. per-position step sizes (see :func:`lsqml_step_sizes`);
+    4. O <- O + beta sum_j S_j[alpha_O,j sum_k conj(P_k) chi_jk] / (den_O + d_O),
+       P_k <- P_k + beta sum_j alpha_P,j conj(O_j) chi_jk / (den_P + d_P),
+       both from the values held at the start of the iteration.
+    """
+    O = O.astype(np.complex128)
+    P = P.astype(np.complex128)
+    upd = t >= probe_start
+    chi = fourier_residual(O, P, pos, I)
+    dO, dP, wO, wP = lsqml_directions(O, P, chi, pos, reg, upd)
+    aO, aP = lsqml_step_sizes(O, P, chi, pos, dO, dP)
+    O_new = O + beta * object_numerator(P, chi, pos, O.shape, weights=aO) / wO
+    if upd:
+        P_new = P + beta * probe_numerator(O, chi, pos, weights=aP) / wP[None]
+    else:
+        P_new = P.copy()
+    if return_steps:
+        return O_new, P_new, (aO, aP)
+    return O_new, P_new
+
+
+# ---------------------------------------------------------------------------
+# Driver used by tests and the CPU baseline
+# ---------------------------------------------------------------------------
+
+def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, reg=1e-3,
+                epie_alpha=1.0, epie_beta=1.0, lsqml_beta=0.9, probe_start=0):
+    """Run n_iter iterations of 'epie', 'dm' or 'lsqml' starting at index t0.
+
+    Returns (O, P, psi) -- psi is the DM state (None for the others)."""
+    pos = round_positions(positions)
+    O = np.asarray(O, dtype=np.complex128)
+    P = np.asarray(P, dtype=np.complex128)
+    check_positions(pos, P.shape[-1], *O.shape)
+    for t in range(t0, t0 + n_iter):
+        if alg == "epie":
+            O, P = epie_iteration(O, P, pos, I, t, seed, epie_alpha, epie_beta, probe_start)
+        elif alg == "dm":
+            if psi is None:
+                psi = dm_init(O, P, pos)
+            O, P, psi = dm_iteration(O, P, psi, pos, I, t, reg, probe_start)
+        elif alg == "lsqml":
+            O, P = lsqml_iteration(O, P, pos, I, t, reg, lsqml_beta, probe_start)
+        else:
+            raise ValueError(alg)
+    return O, P, psi

@@ -1,0 +1,393 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each ``pin_*`` takes the oracle module as an argument and raises
+AssertionError if the oracle disagrees with a definition, an identity, a
+closed form or brute force.  ``test_oracle_pins.py`` runs them on the real
+oracle; ``test_oracle_mutations.py`` plants plausible mistakes in a copy of
+the oracle and checks that some pin catches each one.
+"""
+from __future__ import annotations
+
+import cmath
+import math
+import os
+
+import numpy as np
+from scipy import optimize
+
+from util import small_scan
+
+RNG = np.random.default_rng(12345)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _crandn(*shape, rng=None):
+    rng = rng or RNG
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _dft2_bruteforce(x: np.ndarray) -> np.ndarray:
+    """X[ky,kx] = sum_{y,x} x[y,x] exp(-2 pi i (ky y + kx x)/M), by explicit sums."""
+    M = x.shape[0]
+    N = x.shape[1]
+    X = np.zeros((M, N), dtype=complex)
+    for ky in range(M):
+        for kx in range(N):
+            s = 0j
+            for yy in range(M):
+                for xx in range(N):
+                    s += x[yy, xx] * cmath.exp(-2j * math.pi * (ky * yy / M + kx * xx / N))
+            X[ky, kx] = s
+    return X
+
+
+# --------------------------------------------------------------------- FFT
+
+def pin_fft_bruteforce(orc):
+    for M in (2, 3, 4, 6, 8, 12):
+        x = _crandn(M, M)
+        X = orc.fft2(x)
+        ref = _dft2_bruteforce(x)
+        assert np.allclose(X, ref, atol=1e-12 * M * M, rtol=0), f"fft2 != DFT at M={M}"
+        assert np.allclose(orc.ifft2(ref), x, atol=1e-12, rtol=0), f"ifft2 not the inverse at M={M}"
+
+
+def pin_parseval(orc):
+    for M in (4, 16, 64):
+        x = _crandn(3, M, M)
+        X = orc.fft2(x)
+        assert abs(np.sum(np.abs(X) ** 2) - M * M * np.sum(np.abs(x) ** 2)) < 1e-9 * M * M * np.sum(np.abs(x) ** 2)
+        assert np.allclose(orc.ifft2(orc.fft2(x)), x, atol=1e-12)
+
+
+# ----------------------------------------------------------- forward model
+
+def pin_forward_bruteforce(orc):
+    """I_j(q) = sum_k |DFT(P_k O_j)|^2 with the zero frequency at (M/2, M/2),
+    by explicit loops over a 4x4 probe, 8x8 object, 2 positions, 2 modes."""
+    M, K = 4, 2
+    P = _crandn(K, M, M)
+    O = _crandn(8, 8)
+    pos = np.array([[0, 1], [3, 4]])
+    I = orc.far_field_intensity(O, P, pos)
+    for j, (y, x) in enumerate(pos):
+        ref = np.zeros((M, M))
+        for k in range(K):
+            ex = np.array([[P[k, u, v] * O[y + u, x + v] for v in range(M)] for u in range(M)])
+            X = _dft2_bruteforce(ex)
+            for ky in range(M):
+                for kx in range(M):
+                    ref[(ky + M // 2) % M, (kx + M // 2) % M] += abs(X[ky, kx]) ** 2
+        assert np.allclose(I[j], ref, rtol=1e-12, atol=1e-12 * ref.max()), f"forward model frame {j}"
+
+
+def pin_mode_mixing_invariance(orc):
+    """Incoherent modes: a unitary mixing of the K modes leaves I unchanged."""
+    P, O, pos = small_scan(M=8, K=3, grid=2, step=3)
+    pos = orc.round_positions(pos)
+    Q, _ = np.linalg.qr(_crandn(3, 3))
+    Pm = np.einsum("kl,luv->kuv", Q, P)
+    I1 = orc.far_field_intensity(O, P, pos)
+    I2 = orc.far_field_intensity(O, Pm, pos)
+    assert np.allclose(I1, I2, rtol=1e-10, atol=1e-10 * I1.max())
+
+
+def pin_gather_scatter_adjoint(orc):
+    """<S x, y> = <x, G y> for random complex patches and object."""
+    M = 5
+    pos = np.array([[0, 0], [2, 3], [4, 1], [2, 3]])
+    shape = (9, 9)
+    x = _crandn(len(pos), M, M)
+    y = _crandn(*shape)
+    lhs = np.vdot(orc.scatter_add(shape, pos, x), y)
+    rhs = np.vdot(x, orc.gather(y, pos, M))
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+    cover = orc.scatter_add(shape, pos, np.ones((len(pos), M, M)))
+    ref = np.zeros(shape)
+    for (py, px) in pos:
+        for u in range(M):
+            for v in range(M):
+                ref[py + u, px + v] += 1
+    assert np.array_equal(cover, ref)
+
+
+def pin_rounding(orc):
+    p = orc.round_positions(np.array([[2.5, 3.5], [0.4999, 1.5000001], [-0.5, 7.0]]))
+    assert p.tolist() == [[2, 4], [0, 2], [0, 7]]
+
+
+# -------------------------------------------------------------- projection
+
+def pin_projection(orc):
+    J, K, M = 3, 2, 8
+    Psi = _crandn(J, K, M, M) * 3.0
+    I = np.abs(RNG.standard_normal((J, M, M))) * 10.0
+    I[0, 1, 2] = -1.0          # masked
+    Psi[1, :, 3, 3] = 0.0       # A = 0 -> projected to 0
+    Q = orc.project(Psi, I)
+    A2 = np.sum(np.abs(Q) ** 2, axis=1)
+    m = (I >= 0)
+    m[1, 3, 3] = False
+    assert np.allclose(np.sqrt(A2[m]), np.sqrt(I[m]), rtol=1e-12), "modulus != sqrt(I)"
+    # phases and mode ratios unchanged where the modulus is positive
+    nz = np.abs(Psi) > 0
+    assert np.allclose(np.angle(Q[nz & np.broadcast_to(m[:, None], Q.shape)]),
+                       np.angle(Psi[nz & np.broadcast_to(m[:, None], Q.shape)]), atol=1e-12)
+    assert np.allclose(Q[0, :, 1, 2], Psi[0, :, 1, 2]), "masked pixel changed"
+    assert np.all(Q[1, :, 3, 3] == 0)
+    assert np.allclose(orc.project(Q, I), Q, rtol=1e-12, atol=1e-12), "projection not idempotent"
+
+
+def pin_fourier_error(orc):
+    P, O, pos = small_scan(M=16, K=2)
+    pos = orc.round_positions(pos)
+    I = orc.far_field_intensity(O, P, pos)
+    assert orc.fourier_error(O, P, pos, I) < 1e-24
+    c = 1.7
+    E = orc.fourier_error(O, P, pos, c * c * I)
+    assert abs(E - (1 - c) ** 2 / c ** 2) < 1e-12, "scaled data: E != (1-c)^2/c^2"
+    Im = c * c * I.copy()
+    Im[:, ::2, :] = -1.0        # mask half the rows: the ratio is unchanged
+    assert abs(orc.fourier_error(O, P, pos, Im) - (1 - c) ** 2 / c ** 2) < 1e-12
+
+
+# ------------------------------------------------------------ fixed points
+
+def _truth_case(orc, K=2):
+    P, O, pos = small_scan(M=16, K=K)
+    pos = orc.round_positions(pos)
+    I = orc.far_field_intensity(O, P, pos)
+    return P, O, pos, I
+
+
+def pin_fixed_points(orc):
+    P, O, pos, I = _truth_case(orc)
+    O1, P1 = orc.epie_iteration(O, P, pos, I, t=0, seed=5)
+    assert np.allclose(O1, O, atol=1e-12) and np.allclose(P1, P, atol=1e-12), "ePIE moved off the truth"
+    psi = orc.dm_init(O, P, pos)
+    O2, P2, psi2 = orc.dm_iteration(O, P, psi, pos, I, t=0)
+    assert np.allclose(O2, O, atol=1e-12) and np.allclose(P2, P, atol=1e-12), "DM moved O/P off the truth"
+    assert np.allclose(psi2, psi, atol=1e-12), "DM moved psi off the truth"
+    O3, P3 = orc.lsqml_iteration(O, P, pos, I, t=0)
+    assert np.allclose(O3, O, atol=1e-12) and np.allclose(P3, P, atol=1e-12), "LSQML moved off the truth"
+
+
+def _er_step(patch, I_centred):
+    """Error-reduction step written with polar form: keep the phase, impose sqrt(I)."""
+    F = np.fft.fft2(patch)
+    amp = np.sqrt(np.fft.ifftshift(I_centred))
+    return np.fft.ifft2(amp * np.exp(1j * np.angle(F)))
+
+
+def pin_epie_er_special_case(orc):
+    """J=1, K=1, P = 1, alpha = 1, probe fixed: the patch becomes F^-1 Pi F(patch)."""
+    M = 8
+    O = _crandn(12, 12)
+    P = np.ones((1, M, M), dtype=complex)
+    pos = np.array([[2, 3]])
+    I = np.abs(_crandn(1, M, M)) ** 2
+    O1, P1 = orc.epie_iteration(O, P, pos, I, t=0, probe_start=10)
+    ref = O.copy()
+    ref[2:10, 3:11] = _er_step(O[2:10, 3:11], I[0])
+    assert np.allclose(O1, ref, atol=1e-12), "ePIE object step != error reduction"
+    assert np.array_equal(P1, P)
+    # symmetric case for the probe: O = 1 on the patch, probe updated
+    O = np.ones((12, 12), dtype=complex)
+    Pr = _crandn(1, M, M)
+    O2, P2 = orc.epie_iteration(O, Pr, pos, I, t=0, probe_start=0)
+    assert np.allclose(P2[0], _er_step(Pr[0], I[0]), atol=1e-12), "ePIE probe step != error reduction"
+
+
+def pin_epie_gradient(orc):
+    """The ePIE object/probe corrections are steepest-descent steps of
+    f = 1/2 sum_k ||z_k - P_k O_j||^2 (z fixed) with steps alpha/max|P|^2, beta/max|O_j|^2."""
+    M, K = 6, 2
+    O = _crandn(8, 8)
+    P = _crandn(K, M, M)
+    pos = np.array([[1, 2]])
+    I = np.abs(_crandn(1, M, M)) ** 2
+    alpha, beta = 0.7, 0.3
+    O1, P1 = orc.epie_iteration(O, P, pos, I, t=0, alpha=alpha, beta=beta)
+    Oj = O[1:7, 2:8]
+    # target exit waves: the mode-summed modulus replaced by sqrt(I), phases and mode ratios kept
+    F = np.fft.fft2(P * Oj)
+    A = np.sqrt(np.sum(np.abs(F) ** 2, axis=0))
+    z = np.fft.ifft2(F * np.fft.ifftshift(np.sqrt(I[0]))[None] / A[None])
+
+    def f(Ov, Pv):
+        return 0.5 * np.sum(np.abs(z - Pv * Ov[None]) ** 2)
+
+    h = 1e-6
+    gO = np.zeros_like(Oj)
+    for u in range(M):
+        for v in range(M):
+            e = np.zeros_like(Oj)
+            e[u, v] = h
+            gr = (f(Oj + e, P) - f(Oj - e, P)) / (2 * h)
+            gi = (f(Oj + 1j * e, P) - f(Oj - 1j * e, P)) / (2 * h)
+            gO[u, v] = gr + 1j * gi
+    pmax = np.max(np.sum(np.abs(P) ** 2, axis=0))
+    assert np.allclose(O1[1:7, 2:8] - Oj, -alpha / pmax * gO, atol=1e-6), "ePIE object step direction"
+    gP = np.zeros_like(P)
+    for k in range(K):
+        for u in range(M):
+            for v in range(M):
+                e = np.zeros_like(P)
+                e[k, u, v] = h
+                gr = (f(Oj, P + e) - f(Oj, P - e)) / (2 * h)
+                gi = (f(Oj, P + 1j * e) - f(Oj, P - 1j * e)) / (2 * h)
+                gP[k, u, v] = gr + 1j * gi
+    omax = np.max(np.abs(Oj) ** 2)
+    assert np.allclose(P1 - P, -beta / omax * gP, atol=1e-6), "ePIE probe step direction"
+
+
+def pin_epie_order(orc):
+    golden = [l for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if not l.startswith("#")]
+    g = orc.splitmix64_stream(0)
+    assert next(g) == int(golden[0], 16), "SplitMix64 seed-0 test vector"
+    assert orc.epie_order(0, 3, 7).tolist() == list(range(7))
+    for t in range(4):
+        o = orc.epie_order(99, t, 50)
+        assert sorted(o.tolist()) == list(range(50))
+    assert orc.epie_order(99, 0, 50).tolist() != orc.epie_order(99, 1, 50).tolist()
+
+
+# --------------------------------------------------------------------- DM
+
+def _ls_directional_derivative(g, X, rng):
+    """Max over a few random directions of |dg/ds| at s = 0 (central differences)."""
+    h = 1e-6
+    worst = 0.0
+    for _ in range(4):
+        eta = _crandn(*X.shape, rng=rng)
+        d = (g(X + h * eta) - g(X - h * eta)) / (2 * h)
+        worst = max(worst, abs(d))
+    return worst
+
+
+def pin_dm_overlap_least_squares(orc):
+    """O_new minimises sum ||psi - P O_j||^2 + d_O ||O - O_old||^2; then P_new minimises
+    sum ||psi - P O_new,j||^2 + d_P ||P - P_old||^2 (d = reg max den, den by brute force)."""
+    rng = np.random.default_rng(7)
+    P, O, pos = small_scan(M=8, K=2, grid=3, step=3)
+    pos = orc.round_positions(pos)
+    psi = _crandn(len(pos), 2, 8, 8, rng=rng)
+    reg = 0.05
+    On, Pn = orc.dm_overlap_update(O, P, psi, pos, reg, True)
+    M = 8
+    denO = np.zeros(O.shape)
+    for (y, x) in pos:
+        denO[y:y + M, x:x + M] += np.sum(np.abs(P) ** 2, axis=0)
+    dO = reg * denO.max()
+
+    def gO(Ov):
+        s = sum(np.sum(np.abs(psi[j] - P * Ov[y:y + M, x:x + M][None]) ** 2) for j, (y, x) in enumerate(pos))
+        return s + dO * np.sum(np.abs(Ov - O) ** 2)
+
+    base = _ls_directional_derivative(gO, O, rng)
+    assert _ls_directional_derivative(gO, On, rng) < 1e-6 * base, "DM object update not the LS minimiser"
+    denP = sum(np.abs(On[y:y + M, x:x + M]) ** 2 for (y, x) in pos)
+    dP = reg * denP.max()
+
+    def gP(Pv):
+        s = sum(np.sum(np.abs(psi[j] - Pv * On[y:y + M, x:x + M][None]) ** 2) for j, (y, x) in enumerate(pos))
+        return s + dP * np.sum(np.abs(Pv - P) ** 2)
+
+    base = _ls_directional_derivative(gP, P, rng)
+    assert _ls_directional_derivative(gP, Pn, rng) < 1e-6 * base, "DM probe update not the LS minimiser"
+
+
+def pin_dm_all_masked(orc):
+    """With every detector pixel masked the Fourier constraint is the identity,
+    so one DM iteration returns the overlap projection: psi_new = P_new O_new,j."""
+    rng = np.random.default_rng(3)
+    P, O, pos = small_scan(M=8, K=2, grid=3, step=3)
+    pos = orc.round_positions(pos)
+    psi = _crandn(len(pos), 2, 8, 8, rng=rng)
+    I = -np.ones((len(pos), 8, 8))
+    On, Pn, psin = orc.dm_iteration(O, P, psi, pos, I, t=0, reg=0.01)
+    assert np.allclose(psin, orc.exit_waves(On, Pn, pos), atol=1e-12), "DM with identity Fourier step"
+
+
+# ------------------------------------------------------------------ LSQML
+
+def pin_lsqml_step_sizes(orc):
+    """alpha_j minimises ||chi_j - aO a_j - aP b_j||^2 + lam (aO^2 + aP^2), found by BFGS."""
+    rng = np.random.default_rng(5)
+    P, O, pos = small_scan(M=8, K=2, grid=2, step=4)
+    pos = orc.round_positions(pos)
+    J = len(pos)
+    chi = _crandn(J, 2, 8, 8, rng=rng)
+    dO = _crandn(*O.shape, rng=rng)
+    dP = _crandn(2, 8, 8, rng=rng)
+    aO, aP = orc.lsqml_step_sizes(O, P, chi, pos, dO, dP)
+    for j, (y, x) in enumerate(pos):
+        a = P * dO[y:y + 8, x:x + 8][None]
+        b = O[y:y + 8, x:x + 8][None] * dP
+        lam = 1e-6 * (np.sum(np.abs(a) ** 2) + np.sum(np.abs(b) ** 2)) / 2
+
+        def q(v):
+            return np.sum(np.abs(chi[j] - v[0] * a - v[1] * b) ** 2) + lam * (v[0] ** 2 + v[1] ** 2)
+
+        res = optimize.minimize(q, np.zeros(2), method="BFGS", options=dict(gtol=1e-12))
+        assert np.allclose([aO[j], aP[j]], res.x, rtol=1e-5, atol=1e-7), f"step sizes of position {j}"
+
+
+def pin_lsqml_er_special_case(orc):
+    """J=1, K=1, P = 1, probe fixed, beta = 1: the patch moves to the error-reduction
+    step up to the lambda and reg terms (relative 1e-6)."""
+    M = 8
+    O = _crandn(12, 12)
+    P = np.ones((1, M, M), dtype=complex)
+    pos = np.array([[2, 3]])
+    I = np.abs(_crandn(1, M, M)) ** 2
+    O1, P1 = orc.lsqml_iteration(O, P, pos, I, t=0, beta=1.0, probe_start=5)
+    ref = O.copy()
+    ref[2:10, 3:11] = _er_step(O[2:10, 3:11], I[0])
+    assert np.allclose(O1, ref, rtol=0, atol=2e-6 * np.abs(ref).max()), "LSQML with P = 1 != error reduction"
+    assert np.array_equal(P1, P)
+
+
+def pin_lsqml_all_masked(orc):
+    P, O, pos = small_scan(M=8, K=2, grid=3, step=3)
+    pos = orc.round_positions(pos)
+    I = -np.ones((len(pos), 8, 8))
+    O1, P1 = orc.lsqml_iteration(O, P, pos, I, t=0)
+    assert np.allclose(O1, O, atol=1e-14) and np.allclose(P1, P, atol=1e-14)
+
+
+def pin_lsqml_directions(orc):
+    """dO and dP are steepest-descent directions of 1/2 sum ||chi - delta(P O_j)||^2 at zero
+    change, scaled by the denominators: dO * wO = -grad_O, dP * wP = -grad_P."""
+    rng = np.random.default_rng(9)
+    M = 6
+    P, O, pos = small_scan(M=M, K=2, grid=2, step=3)
+    pos = orc.round_positions(pos)
+    chi = _crandn(len(pos), 2, M, M, rng=rng)
+    dO, dP, wO, wP = orc.lsqml_directions(O, P, chi, pos, 1e-3, True)
+
+    def f(Ov, Pv):
+        return 0.5 * sum(np.sum(np.abs(chi[j] + P * O[y:y + M, x:x + M][None] - Pv * Ov[y:y + M, x:x + M][None]) ** 2)
+                         for j, (y, x) in enumerate(pos))
+
+    h = 1e-6
+    # object gradient on a few pixels
+    for (u, v) in [(pos[0][0] + 1, pos[0][1] + 2), (pos[-1][0] + 3, pos[-1][1] + 3)]:
+        e = np.zeros_like(O)
+        e[u, v] = h
+        g = ((f(O + e, P) - f(O - e, P)) + 1j * (f(O + 1j * e, P) - f(O - 1j * e, P))) / (2 * h)
+        assert abs(dO[u, v] * wO[u, v] + g) < 1e-6 * (1 + abs(g)), "LSQML object direction"
+    for (k, u, v) in [(0, 1, 1), (1, 4, 2)]:
+        e = np.zeros_like(P)
+        e[k, u, v] = h
+        g = ((f(O, P + e) - f(O, P - e)) + 1j * (f(O, P + 1j * e) - f(O, P - 1j * e))) / (2 * h)
+        assert abs(dP[k, u, v] * wP[u, v] + g) < 1e-6 * (1 + abs(g)), "LSQML probe direction"
+
+
+ALL_PINS = [
+    pin_fft_bruteforce, pin_parseval, pin_forward_bruteforce, pin_mode_mixing_invariance,
+    pin_gather_scatter_adjoint, pin_rounding, pin_projection, pin_fourier_error,
+    pin_fixed_points, pin_epie_er_special_case, pin_epie_gradient, pin_epie_order,
+    pin_dm_overlap_least_squares, pin_dm_all_masked, pin_lsqml_step_sizes,
+    pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
+]

@@ -1,0 +1,69 @@
+"""The pins have teeth: plant a plausible mistake in a copy of the oracle's
+source (a dropped term, a wrong sign, a missing conjugate, a transposed index)
+and check that at least one pin fails on it.  CPU only; the real oracle is
+never modified."""
+import importlib.util
+import inspect
+import types
+
+import pytest
+
+import pins
+from oracle import ptycho_oracle as orc
+
+SRC = inspect.getsource(orc)
+
+MUTATIONS = {
+    "no_sqrt_in_projection": ("sqrtI = np.sqrt(np.where(masked, 0.0, I_fft))",
+                              "sqrtI = np.where(masked, 0.0, I_fft)"),
+    "conj_probe_in_exit_wave": ("return P[None, :, :, :] * gather(O, pos, M)[:, None, :, :]",
+                                "return np.conj(P)[None, :, :, :] * gather(O, pos, M)[:, None, :, :]"),
+    "no_fftshift_in_forward": ("return np.fft.fftshift(I, axes=(-2, -1))", "return I"),
+    "ifft_as_forward": ("return np.fft.fft2(x, axes=(-2, -1))",
+                        "return np.fft.ifft2(x, axes=(-2, -1)) * (x.shape[-1] * x.shape[-2])"),
+    "scatter_transposed": ("acc[y:y + M, x:x + M] += patches[j]", "acc[x:x + M, y:y + M] += patches[j]"),
+    "object_numerator_no_conj": ("c = np.sum(np.conj(P)[None] * X, axis=1)", "c = np.sum(P[None] * X, axis=1)"),
+    "probe_numerator_no_conj": ("Oc = np.conj(gather(O, pos, M))[:, None]", "Oc = gather(O, pos, M)[:, None]"),
+    "dm_reflection_swapped": ("project(fft2(2.0 * phi - psi)", "project(fft2(2.0 * psi - phi)"),
+    "dm_wrong_sign_phi": ("psi = psi + ifft2(project(fft2(2.0 * phi - psi), to_fft_order(I))) - phi",
+                          "psi = psi + ifft2(project(fft2(2.0 * phi - psi), to_fft_order(I))) + phi"),
+    "dm_drop_prox_term": ("O = (num_O + d_O * O) / (den_O + d_O)", "O = num_O / (den_O + d_O)"),
+    "lsqml_solve_sign": ("return (d * r1 - b * r2) / det, (a * r2 - b * r1) / det",
+                         "return (d * r1 + b * r2) / det, (a * r2 - b * r1) / det"),
+    "lsqml_conj_object_in_b": ("b = Oj[j][None] * dP", "b = np.conj(Oj[j])[None] * dP"),
+    "lsqml_swapped_weights": ("object_numerator(P, chi, pos, O.shape, weights=aO)",
+                              "object_numerator(P, chi, pos, O.shape, weights=aP)"),
+    "lsqml_lambda_too_big": ("lam = 1e-6 * tr / 2.0", "lam = 1e-3 * tr / 2.0"),
+    "epie_no_conj_probe": ("alpha * np.sum(np.conj(P) * Delta, axis=0) / pmax",
+                           "alpha * np.sum(P * Delta, axis=0) / pmax"),
+    "epie_sum_not_max": ("pmax = float(np.max(np.sum(np.abs(P) ** 2, axis=0)))",
+                         "pmax = float(np.sum(np.abs(P) ** 2))"),
+    "epie_probe_from_new_object": ("P[...] = P + beta * np.conj(Oj)[None] * Delta / omax",
+                                   "P[...] = P + beta * np.conj(O[y:y + M, x:x + M])[None] * Delta / omax"),
+    "error_den_sqrt": ("den = float(np.sum(np.where(m, I_fft, 0.0)))",
+                       "den = float(np.sum(np.where(m, sqrtI, 0.0)))"),
+    "splitmix_constant": ("0xBF58476D1CE4E5B9", "0xBF58476D1CE4E5B8"),
+    "rounding_floor": ("return np.rint(np.asarray(positions, dtype=np.float64)).astype(np.int64)",
+                       "return np.floor(np.asarray(positions, dtype=np.float64)).astype(np.int64)"),
+}
+
+
+def _mutant(name: str) -> types.ModuleType:
+    old, new = MUTATIONS[name]
+    assert SRC.count(old) == 1, f"mutation {name}: pattern not found exactly once"
+    spec = importlib.util.spec_from_loader(f"oracle_mutant_{name}", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    exec(compile(SRC.replace(old, new), f"<mutant {name}>", "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_some_pin_catches(name):
+    mod = _mutant(name)
+    caught = []
+    for pin in pins.ALL_PINS:
+        try:
+            pin(mod)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught the planted mistake {name}"
