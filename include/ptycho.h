@@ -1,0 +1,183 @@
+/*
+ * ptycho.h -- C ABI of a B300-native (sm_103a) library for the per-iteration
+ * hot path of ptychographic reconstruction: ePIE, DM and LSQML.
+ *
+ * The ptychopy paper (Yue et al., arXiv 2202.03144) exposes its CUDA engine
+ * through a "whole" call per algorithm and a "step" API -- init (parameters,
+ * data upload, sample/probe initialisation), step (iterations on the GPU),
+ * resobj/resprobe (copy results back at any time), post (free) -- Sec. 3.2,
+ * Fig. 3 and Listing 1.  This header is that step API with plain pointers:
+ *
+ *   paper            this ABI
+ *   epieinit()       ptycho_create + ptycho_set_data + ptycho_set_init
+ *   epiestep()       ptycho_iterate(ctx, alg, 1)
+ *   epie(para)       ptycho_iterate(ctx, alg, n)
+ *   epieresobj()     ptycho_get_object
+ *   epieresprobe()   ptycho_get_probe
+ *   epiepost()       ptycho_destroy
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Complex arrays are interleaved float32 pairs (re, im), row-major.
+ *    object: [obj_ny][obj_nx][2]; probe: [K][M][M][2];
+ *    exit waves / residuals: [J][K][M][M][2].
+ *  - intensities: [J][M][M] float32, detector-centred (zero spatial
+ *    frequency at pixel (M/2, M/2)); a negative value marks a masked pixel
+ *    (saturated or bad, Sec. 2.2), which the modulus projection leaves free.
+ *  - positions: [J][2] float32 (y, x) of each patch's top-left corner on the
+ *    object grid, in pixels; rounded half-to-even to integers.  Every patch
+ *    must lie inside the object.
+ *  - on_device != 0: the pointer is CUDA device memory of the current device;
+ *    otherwise it is host memory (pageable or pinned).
+ *  - Ownership: the library COPIES every input; the caller keeps its
+ *    buffers.  get_* calls write into caller memory and may be made at any
+ *    time without disturbing the reconstruction (Sec. 3.2, step mode).
+ *  - Stream: all GPU work is issued on ptycho_params.stream (a cudaStream_t;
+ *    NULL = the legacy default stream).  Only get_*, fourier_error and the
+ *    host-pointer variants synchronise that stream.
+ *  - Errors: every int-returning call returns PTYCHO_OK (0) or a negative
+ *    PTYCHO_ERR_* code; ptycho_last_error() gives a message.  After an error
+ *    the context stays valid and can be destroyed (or used again).
+ *  - The library allocates its device memory with cudaMalloc at
+ *    ptycho_create/ptycho_set_data and frees it in ptycho_destroy.
+ */
+#ifndef PTYCHO_H
+#define PTYCHO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ptycho_ctx ptycho_ctx;
+
+/* Reconstruction algorithms (Abstract, Sec. 2.3). */
+enum { PTYCHO_EPIE = 0, PTYCHO_DM = 1, PTYCHO_LSQML = 2 };
+
+/* Storage precision of the measured data on the device.  F16/BF16 store
+ * sqrt(I) divided by its per-frame maximum, plus one float32 scale per frame;
+ * all arithmetic stays float32. */
+enum { PTYCHO_I_F32 = 0, PTYCHO_I_F16 = 1, PTYCHO_I_BF16 = 2 };
+
+#define PTYCHO_OK 0
+#define PTYCHO_ERR_ARG (-1)         /* bad argument or size                     */
+#define PTYCHO_ERR_BOUNDS (-2)      /* a patch falls outside the object         */
+#define PTYCHO_ERR_NONFINITE (-3)   /* NaN/Inf in an input                      */
+#define PTYCHO_ERR_OOM (-4)         /* device allocation failed                 */
+#define PTYCHO_ERR_CUDA (-5)        /* a CUDA call failed                       */
+#define PTYCHO_ERR_TIMEOUT (-6)     /* reserved: a bounded device wait gave up  */
+#define PTYCHO_ERR_DIVERGED (-7)    /* non-finite Fourier error                 */
+#define PTYCHO_ERR_STATE (-8)       /* call out of order (e.g. iterate first)   */
+#define PTYCHO_ERR_UNSUPPORTED (-9) /* (M, K) combination not compiled in       */
+
+typedef struct {
+  int M;            /* probe / detector side in pixels (16, 32, 64, 128, 256) */
+  int K;            /* number of incoherent probe modes (1..3), Sec. 2.2       */
+  int J;            /* number of scan positions (diffraction frames)          */
+  int obj_ny;       /* object rows                                            */
+  int obj_nx;       /* object columns                                         */
+  int istore;       /* PTYCHO_I_F32 / _F16 / _BF16                            */
+  int probe_start;  /* first iteration index that updates the probe, Sec. 2.2 */
+  double epie_alpha;  /* ePIE object step (default 1)                         */
+  double epie_beta;   /* ePIE probe step (default 1)                          */
+  double lsqml_beta;  /* LSQML relaxation of the final update (default 0.9)   */
+  double reg;         /* DM/LSQML denominators: delta = reg * max(den), 1e-3  */
+  unsigned long long seed; /* ePIE visiting order: 0 = identity, else a
+                              SplitMix64-driven Fisher-Yates shuffle per
+                              iteration, keyed by seed XOR iteration index   */
+  void* stream;     /* cudaStream_t for all GPU work (may be NULL)            */
+  int cluster;      /* FFT cluster size override (0 = autotuned choice)       */
+} ptycho_params;
+
+/* Fill *p with the defaults above (M, K, J and the object size are zero). */
+void ptycho_default_params(ptycho_params* p);
+
+/* Create a context for one reconstruction and allocate its device buffers
+ * (object, probe, per-position state).  *out receives the handle, or NULL on
+ * error.  Returns PTYCHO_ERR_ARG for out-of-range sizes,
+ * PTYCHO_ERR_UNSUPPORTED when no kernel is compiled for (M, K), and
+ * PTYCHO_ERR_OOM / PTYCHO_ERR_CUDA on device failure. */
+int ptycho_create(ptycho_ctx** out, const ptycho_params* p);
+
+/* Upload the measured data: intensities [J][M][M] (see conventions) and
+ * positions [J][2].  Positions are always host memory; intensities are host
+ * or device memory as on_device says.  Checks every patch is inside the
+ * object (PTYCHO_ERR_BOUNDS) and every intensity is finite
+ * (PTYCHO_ERR_NONFINITE), then stores sqrt(I) in FFT order at the context's
+ * storage precision.  Resets the DM exit-wave state. */
+int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* positions,
+                    int on_device);
+
+/* Upload the scan positions only ([J][2], host memory), e.g. before
+ * ptycho_simulate.  Same checks as ptycho_set_data. */
+int ptycho_set_positions(ptycho_ctx* ctx, const float* positions);
+
+/* Upload the object [obj_ny][obj_nx][2] and probe [K][M][M][2] guesses
+ * (Sec. 2.2: "the probe and/or object guess can also be specified").  Either
+ * pointer may be NULL to keep the current value (initially object = 1 and
+ * probe = 0).  Resets the DM exit-wave state. */
+int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device);
+
+/* Run n_iter iterations of alg (PTYCHO_EPIE / _DM / _LSQML) entirely on the
+ * device; the iteration counter t continues across calls, so n calls of 1
+ * iteration equal one call of n.  The probe is updated from t >= probe_start.
+ * DM keeps its exit waves [J][K][M][M] between calls; they are (re)initialised
+ * to P_k O_j on the first DM iteration after set_data / set_init or after
+ * another algorithm ran.  Asynchronous on the context stream. */
+int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter);
+
+/* Copy the current object [obj_ny][obj_nx][2] / probe [K][M][M][2] out. */
+int ptycho_get_object(ptycho_ctx* ctx, float* out, int on_device);
+int ptycho_get_probe(ptycho_ctx* ctx, float* out, int on_device);
+
+/* Fourier error E = sum m (A - sqrt I)^2 / sum m I over all frames and
+ * unmasked pixels m, A = sqrt(sum_k |F(P_k O_j)|^2), from a fresh forward
+ * pass at the current (O, P); sums in FP64 in a fixed order.  Synchronises.
+ * Returns PTYCHO_ERR_DIVERGED if E is not finite. */
+int ptycho_fourier_error(ptycho_ctx* ctx, double* out);
+
+/* Forward model (Sec. 2.3): far-field intensities of the current (O, P) at
+ * the current positions, I_j = fftshift(sum_k |F(P_k O_j)|^2), written as
+ * [J][M][M] float32 (detector-centred) to out. */
+int ptycho_simulate(ptycho_ctx* ctx, float* out, int on_device);
+
+/* Fourier residual of the current (O, P): chi_jk = F^-1 Pi(F(P_k O_j)) - P_k O_j,
+ * written as [J][K][M][M][2] to out.  Pi replaces the mode-summed modulus by
+ * sqrt(I) (masked pixels unchanged).  Does not change the reconstruction. */
+int ptycho_fourier_residual(ptycho_ctx* ctx, float* out, int on_device);
+
+/* DM exit-wave state psi [J][K][M][M][2] (PTYCHO_ERR_STATE if none). */
+int ptycho_get_exit_waves(ptycho_ctx* ctx, float* out, int on_device);
+
+/* Iterations run so far (the counter t). */
+long long ptycho_iteration(const ptycho_ctx* ctx);
+
+/* Number of this library's kernel launches issued so far on the context. */
+long long ptycho_launch_count(const ptycho_ctx* ctx);
+
+/* Per-kernel timing.  When enabled, every launch is bracketed by CUDA events
+ * on the context stream and its duration is accumulated per kernel family. */
+typedef struct {
+  const char* name;     /* kernel family                                    */
+  long long launches;   /* launches since profiling was enabled             */
+  double ms;            /* summed device time (ms)                          */
+  double bytes;         /* summed algorithmic DRAM bytes of those launches  */
+} ptycho_kernel_stat;
+
+int ptycho_set_profiling(ptycho_ctx* ctx, int enabled);
+/* Writes up to max entries; *n receives the number of kernel families. */
+int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n);
+
+/* FFT cluster size chosen for this context (1, 2, 4 or 8 CTAs). */
+int ptycho_cluster_size(const ptycho_ctx* ctx);
+
+/* Message of the last error on ctx (or of the last failed create if ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char* ptycho_last_error(const ptycho_ctx* ctx);
+
+/* Free all device memory of ctx ("post", Sec. 3.2).  NULL is ignored. */
+void ptycho_destroy(ptycho_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTYCHO_H */

@@ -1,0 +1,323 @@
+"""Python binding of the C ABI in include/ptycho.h (ctypes).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in ``libptycho.so``; all computation runs in that library's CUDA
+kernels.  Host arrays are numpy; device arrays are torch CUDA tensors (torch is
+used for device memory and streams only).  There is no CPU fallback: if the
+library is missing or no GPU is present, calls fail with an exception.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+EPIE, DM, LSQML = 0, 1, 2
+ALGS = {"epie": EPIE, "dm": DM, "lsqml": LSQML}
+I_F32, I_F16, I_BF16 = 0, 1, 2
+ISTORE = {"f32": I_F32, "f16": I_F16, "bf16": I_BF16}
+
+ERRORS = {
+    -1: "ARG", -2: "BOUNDS", -3: "NONFINITE", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
+    -7: "DIVERGED", -8: "STATE", -9: "UNSUPPORTED",
+}
+
+
+class PtychoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"PTYCHO_ERR_{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("M", C.c_int), ("K", C.c_int), ("J", C.c_int), ("obj_ny", C.c_int), ("obj_nx", C.c_int),
+        ("istore", C.c_int), ("probe_start", C.c_int),
+        ("epie_alpha", C.c_double), ("epie_beta", C.c_double), ("lsqml_beta", C.c_double),
+        ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
+    ]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libptycho.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            from .build import build
+            build()
+        L = C.CDLL(LIB)
+        vp, i, f, d = C.c_void_p, C.c_int, C.c_void_p, C.c_double
+        sig = {
+            "ptycho_default_params": (None, [C.POINTER(Params)]),
+            "ptycho_create": (i, [C.POINTER(vp), C.POINTER(Params)]),
+            "ptycho_set_data": (i, [vp, f, f, i]),
+            "ptycho_set_positions": (i, [vp, f]),
+            "ptycho_set_init": (i, [vp, f, f, i]),
+            "ptycho_iterate": (i, [vp, i, i]),
+            "ptycho_get_object": (i, [vp, f, i]),
+            "ptycho_get_probe": (i, [vp, f, i]),
+            "ptycho_get_exit_waves": (i, [vp, f, i]),
+            "ptycho_fourier_error": (i, [vp, C.POINTER(d)]),
+            "ptycho_simulate": (i, [vp, f, i]),
+            "ptycho_fourier_residual": (i, [vp, f, i]),
+            "ptycho_iteration": (C.c_longlong, [vp]),
+            "ptycho_launch_count": (C.c_longlong, [vp]),
+            "ptycho_set_profiling": (i, [vp, i]),
+            "ptycho_get_profile": (i, [vp, C.POINTER(KernelStat), i, C.POINTER(i)]),
+            "ptycho_cluster_size": (i, [vp]),
+            "ptycho_last_error": (C.c_char_p, [vp]),
+            "ptycho_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != 0:
+        msg = lib().ptycho_last_error(ctx)
+        raise PtychoError(rc, msg.decode() if msg else "")
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_in(x, dtype=np.float32):
+    """(pointer, on_device, keepalive) of an input array; complex arrays are
+    passed as interleaved float32 pairs."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        import torch
+        if x.is_complex():
+            x = torch.view_as_real(x.to(torch.complex64).contiguous())
+        x = x.to(torch.float32).contiguous()
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            return x.data_ptr(), 1, x
+    a = np.asarray(x)
+    if np.iscomplexobj(a):
+        a = np.ascontiguousarray(a, dtype=np.complex64).view(np.float32)
+    else:
+        a = np.ascontiguousarray(a, dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+# ------------------------------------------------------------------ the ABI
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().ptycho_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "istore" and isinstance(v, str):
+            v = ISTORE[v]
+        setattr(p, k, v)
+    return p
+
+
+def create(params: Params) -> C.c_void_p:
+    h = C.c_void_p()
+    rc = lib().ptycho_create(C.byref(h), C.byref(params))
+    _check(None, rc)
+    return h
+
+
+def set_data(ctx, intensities, positions) -> None:
+    ip, dev, keep_i = _ptr_in(intensities)
+    pp, _, keep_p = _ptr_in(np.asarray(positions, dtype=np.float32))
+    _check(ctx, lib().ptycho_set_data(ctx, ip, pp, dev))
+
+
+def set_positions(ctx, positions) -> None:
+    pp, _, keep = _ptr_in(np.asarray(positions, dtype=np.float32))
+    _check(ctx, lib().ptycho_set_positions(ctx, pp))
+
+
+def set_init(ctx, object=None, probe=None) -> None:
+    op, od, ko = _ptr_in(object)
+    pp, pd, kp = _ptr_in(probe)
+    if object is not None and probe is not None and od != pd:
+        set_init(ctx, object, None)
+        set_init(ctx, None, probe)
+        return
+    _check(ctx, lib().ptycho_set_init(ctx, op, pp, od or pd))
+
+
+def iterate(ctx, alg, n_iter: int) -> None:
+    a = ALGS[alg] if isinstance(alg, str) else int(alg)
+    _check(ctx, lib().ptycho_iterate(ctx, a, int(n_iter)))
+
+
+def _get(fn, ctx, shape, out=None):
+    if out is not None and _is_torch(out):
+        import torch
+        assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous()
+        _check(ctx, fn(ctx, out.data_ptr(), 1))
+        return out
+    res = np.empty(shape, dtype=np.complex64)
+    _check(ctx, fn(ctx, res.ctypes.data, 0))
+    return res
+
+
+def get_object(ctx, shape, out=None):
+    return _get(lib().ptycho_get_object, ctx, shape, out)
+
+
+def get_probe(ctx, shape, out=None):
+    return _get(lib().ptycho_get_probe, ctx, shape, out)
+
+
+def get_exit_waves(ctx, shape, out=None):
+    return _get(lib().ptycho_get_exit_waves, ctx, shape, out)
+
+
+def fourier_residual(ctx, shape, out=None):
+    return _get(lib().ptycho_fourier_residual, ctx, shape, out)
+
+
+def fourier_error(ctx) -> float:
+    v = C.c_double()
+    _check(ctx, lib().ptycho_fourier_error(ctx, C.byref(v)))
+    return v.value
+
+
+def simulate(ctx, shape, out=None):
+    if out is not None and _is_torch(out):
+        _check(ctx, lib().ptycho_simulate(ctx, out.data_ptr(), 1))
+        return out
+    res = np.empty(shape, dtype=np.float32)
+    _check(ctx, lib().ptycho_simulate(ctx, res.ctypes.data, 0))
+    return res
+
+
+def iteration(ctx) -> int:
+    return lib().ptycho_iteration(ctx)
+
+
+def launch_count(ctx) -> int:
+    return lib().ptycho_launch_count(ctx)
+
+
+def cluster_size(ctx) -> int:
+    return lib().ptycho_cluster_size(ctx)
+
+
+def set_profiling(ctx, enabled: bool) -> None:
+    _check(ctx, lib().ptycho_set_profiling(ctx, 1 if enabled else 0))
+
+
+def get_profile(ctx) -> dict:
+    buf = (KernelStat * 64)()
+    n = C.c_int()
+    _check(ctx, lib().ptycho_get_profile(ctx, buf, 64, C.byref(n)))
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes)
+            for i in range(min(n.value, 64))}
+
+
+def destroy(ctx) -> None:
+    if ctx:
+        lib().ptycho_destroy(ctx)
+
+
+# ------------------------------------------------------------ convenience
+
+class Reconstruction:
+    """One reconstruction context: the paper's step API (init / step / resobj /
+    resprobe / post) as methods.  Arrays in and out are numpy (host) unless a
+    torch CUDA tensor is given."""
+
+    def __init__(self, M, K, J, obj_shape, **params):
+        stream = params.pop("stream", None)
+        self.params = default_params(M=M, K=K, J=J, obj_ny=obj_shape[0], obj_nx=obj_shape[1], **params)
+        if stream is not None:
+            self.params.stream = stream
+        self.M, self.K, self.J = M, K, J
+        self.obj_shape = tuple(obj_shape)
+        self.ctx = create(self.params)
+
+    def set_data(self, intensities, positions):
+        set_data(self.ctx, intensities, positions)
+
+    def set_positions(self, positions):
+        set_positions(self.ctx, positions)
+
+    def set_init(self, object=None, probe=None):
+        set_init(self.ctx, object, probe)
+
+    def iterate(self, alg, n_iter=1):
+        iterate(self.ctx, alg, n_iter)
+
+    def get_object(self, out=None):
+        return get_object(self.ctx, self.obj_shape, out)
+
+    def get_probe(self, out=None):
+        return get_probe(self.ctx, (self.K, self.M, self.M), out)
+
+    def get_exit_waves(self, out=None):
+        return get_exit_waves(self.ctx, (self.J, self.K, self.M, self.M), out)
+
+    def fourier_residual(self, out=None):
+        return fourier_residual(self.ctx, (self.J, self.K, self.M, self.M), out)
+
+    def fourier_error(self):
+        return fourier_error(self.ctx)
+
+    def simulate(self, out=None):
+        return simulate(self.ctx, (self.J, self.M, self.M), out)
+
+    @property
+    def iteration(self):
+        return iteration(self.ctx)
+
+    @property
+    def launch_count(self):
+        return launch_count(self.ctx)
+
+    @property
+    def cluster(self):
+        return cluster_size(self.ctx)
+
+    def set_profiling(self, on=True):
+        set_profiling(self.ctx, on)
+
+    def get_profile(self):
+        return get_profile(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def to_pixels(wavelength_m: float, distance_m: float, det_pixel_m: float, M: int, length_m: float) -> float:
+    """Length in object-plane pixels for a far-field geometry: the object pixel
+    is dx = lambda z / (M dx_d) (Sec. 3.2, Listing 1 parameters)."""
+    return length_m / (wavelength_m * distance_m / (M * det_pixel_m))

@@ -1,0 +1,226 @@
+// Complex helpers and in-register small DFTs (radix 2, 4, 8, 16).
+//
+// Forward transforms use the kernel exp(-2 pi i n k / N) (numpy fft2
+// convention, unnormalised); INV = true uses exp(+2 pi i n k / N).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ptycho {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by (c, -s) forward or (c, s) inverse, i.e. exp(-/+ i theta)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a, float c, float s) {
+  return INV ? make_float2(a.x * c - a.y * s, a.x * s + a.y * c)
+             : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+// cos(pi/8), sin(pi/8), sqrt(1/2)
+#define PT_C8 0.92387953251128675613f
+#define PT_S8 0.38268343236508977173f
+#define PT_R2 0.70710678118654752440f
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* a) {
+  float2 t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+
+// a[0..3] with element stride S (in-place, natural order out)
+template <bool INV, int S = 1>
+__device__ __forceinline__ void dft4s(float2* a) {
+  float2 t0 = cadd(a[0], a[2 * S]), t1 = csub(a[0], a[2 * S]);
+  float2 t2 = cadd(a[S], a[3 * S]), t3 = mul_mi<INV>(csub(a[S], a[3 * S]));
+  a[0] = cadd(t0, t2);
+  a[2 * S] = csub(t0, t2);
+  a[S] = cadd(t1, t3);
+  a[3 * S] = csub(t1, t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* a) { dft4s<INV, 1>(a); }
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* a) {
+  float2 e[4] = {a[0], a[2], a[4], a[6]};
+  float2 o[4] = {a[1], a[3], a[5], a[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  o[1] = rot<INV>(o[1], PT_R2, PT_R2);
+  o[2] = mul_mi<INV>(o[2]);
+  o[3] = rot<INV>(o[3], -PT_R2, PT_R2);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = cadd(e[k], o[k]);
+    a[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* a) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    e[k] = a[2 * k];
+    o[k] = a[2 * k + 1];
+  }
+  dft8<INV>(e);
+  dft8<INV>(o);
+  // W16^k = exp(-/+ 2 pi i k / 16), k = 1..7
+  o[1] = rot<INV>(o[1], PT_C8, PT_S8);
+  o[2] = rot<INV>(o[2], PT_R2, PT_R2);
+  o[3] = rot<INV>(o[3], PT_S8, PT_C8);
+  o[4] = mul_mi<INV>(o[4]);
+  o[5] = rot<INV>(o[5], -PT_S8, PT_C8);
+  o[6] = rot<INV>(o[6], -PT_R2, PT_R2);
+  o[7] = rot<INV>(o[7], -PT_C8, PT_S8);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = cadd(e[k], o[k]);
+    a[k + 8] = csub(e[k], o[k]);
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* a) {
+  if constexpr (R == 2) dft2<INV>(a);
+  else if constexpr (R == 4) dft4<INV>(a);
+  else if constexpr (R == 8) dft8<INV>(a);
+  else if constexpr (R == 16) dft16<INV>(a);
+  else static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
+}
+
+// Radix of the next Stockham pass for a remaining length rem, given that a
+// thread holds E elements (the radix must divide E).
+__host__ __device__ constexpr int pick_radix(int rem, int E) {
+  int cap = E < 16 ? E : 16;
+  if (rem <= cap) return rem;
+  if (rem == 32 && cap >= 8) return 8;        // 8 x 4
+  if (rem == 64 && cap >= 8) return 8;        // 8 x 8
+  return cap;
+}
+
+// ---------------------------------------------------------------------------
+// One Stockham autosort pass of radix R over LINES lines of length N held in
+// shared memory (Stockham's self-sorting variant of Cooley-Tukey: every pass
+// reads with stride N/R and writes in natural order, so no bit reversal is
+// needed).  NS = product of the radices of the earlier passes.
+//
+// Element i of line l lives at  (l / LPB) * BS + (l % LPB) * LS + i * IS.
+// The NT threads each take PER butterflies (b = tid + p*NT, line = b % LINES,
+// so a warp spans consecutive lines), load them all into registers, sync,
+// then store, which makes the pass in place.
+// tw[i] = exp(-2 pi i i / N) for i < N (table of the line length).
+// ---------------------------------------------------------------------------
+template <int N, int R, int NS, int LINES, int LPB, int BS, int LS, int IS, int NT, bool INV>
+__device__ __forceinline__ void stockham_pass(float2* s, const float2* __restrict__ tw) {
+  constexpr int BPL = N / R;
+  constexpr int TOT = LINES * BPL;
+  constexpr int PER = (TOT + NT - 1) / NT;
+  constexpr int TWS = N / (NS * R);
+  float2 v[PER][R];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int b = tid + p * NT;
+    if (TOT % NT == 0 || b < TOT) {
+      const int l = b % LINES, jj = b / LINES;
+      const int base = (l / LPB) * BS + (l % LPB) * LS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = s[base + (jj + r * BPL) * IS];
+      if constexpr (NS > 1) {
+        const int jm = jj % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[(r * jm * TWS) % N];
+          if (INV) w.y = -w.y;
+          v[p][r] = cmul(v[p][r], w);
+        }
+      }
+      dft<R, INV>(v[p]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int b = tid + p * NT;
+    if (TOT % NT == 0 || b < TOT) {
+      const int l = b % LINES, jj = b / LINES;
+      const int base = (l / LPB) * BS + (l % LPB) * LS;
+      const int jm = jj % NS;
+      const int d = (jj / NS) * NS * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[base + (d + r * NS) * IS] = v[p][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full length-N FFT of every line: the sequence of passes chosen by pick_radix.
+template <int N, int NS, int E, int LINES, int LPB, int BS, int LS, int IS, int NT, bool INV>
+__device__ __forceinline__ void fft_lines_from(float2* s, const float2* __restrict__ tw) {
+  if constexpr (NS < N) {
+    constexpr int R = pick_radix(N / NS, E);
+    stockham_pass<N, R, NS, LINES, LPB, BS, LS, IS, NT, INV>(s, tw);
+    fft_lines_from<N, NS * R, E, LINES, LPB, BS, LS, IS, NT, INV>(s, tw);
+  }
+}
+
+template <int N, int E, int LINES, int LPB, int BS, int LS, int IS, int NT, bool INV>
+__device__ __forceinline__ void fft_lines(float2* s, const float2* __restrict__ tw) {
+  fft_lines_from<N, 1, E, LINES, LPB, BS, LS, IS, NT, INV>(s, tw);
+}
+
+// Block-wide sum of doubles (any NT <= 1024); result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  constexpr int NW = (NT + 31) / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NW; ++i) t += red[i];
+  }
+  return t;
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max_f(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  constexpr int NW = (NT + 31) / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NW; ++i) t = fmaxf(t, red[i]);
+  }
+  return t;
+}
+
+}  // namespace ptycho

@@ -1,0 +1,321 @@
+// Overlap accumulation of the DM / LSQML object and probe updates.
+//
+// Object side (tile-owned, atomic-free, deterministic): each CTA owns a
+// TY x TX tile of the object and walks, in ascending position order, the CSR
+// list of scan positions whose patch overlaps the tile.  Every thread owns
+// fixed pixels and accumulates in registers
+//     num(r) = sum_j w_j sum_k conj(P_k(r - p_j)) X_jk(r - p_j)
+//     den(r) = sum_j sum_k |P_k(r - p_j)|^2
+// so each element of X (psi or chi) is read exactly once overall and a warp
+// reads 32 consecutive complex values of one patch row.
+//
+// Probe side: num_P,k(u) = sum_j w_j conj(O_j(u)) X_jk(u), den_P(u) = sum_j
+// |O_j(u)|^2.  The positions are cut into G contiguous groups; CTA (block,
+// group) sums its group for 256 probe pixels, and a second kernel adds the G
+// partials in a fixed order.
+#pragma once
+#include "common.cuh"
+
+namespace ptycho {
+
+constexpr int TILE_Y = 32, TILE_X = 64, OBJ_NT = 256;
+constexpr int OBJ_ROWS = TILE_Y / (OBJ_NT / TILE_X);  // rows per thread (8)
+constexpr int PROBE_NT = 256;
+
+enum ObjMode : int { OBJ_DEN = 0, OBJ_DM = 1, OBJ_DIR = 2, OBJ_UPD = 3 };
+enum ProbeMode : int { PR_DM = 0, PR_DIR = 1, PR_UPD = 2 };
+
+struct ObjArgs {
+  float2* O;              // object (DM, UPD: in/out)
+  float2* dO;             // DIR: output direction
+  int ny, nx, ntx;        // object size, tiles per row
+  const float2* P;        // probe [K][M][M]
+  const float2* X;        // psi or chi [J][K][M][M]
+  const int2* pos;
+  const int* tile_ptr;    // [n_tiles + 1]
+  const int* tile_list;   // positions overlapping each tile, ascending
+  const float* weights;   // per-position weight (alpha_O) or NULL
+  float* den;             // den_O [ny][nx] (written by OBJ_DEN, read otherwise)
+  float* tile_max;        // OBJ_DEN: max of den per tile
+  const float* den_max;   // max over all tiles (one float)
+  float reg, beta;
+  int M;
+};
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
+  __shared__ float red[32];
+  const int tile = blockIdx.x;
+  const int ty0 = (tile / a.ntx) * TILE_Y, tx0 = (tile % a.ntx) * TILE_X;
+  const int tx = threadIdx.x % TILE_X, tyb = threadIdx.x / TILE_X;
+  const int x = tx0 + tx;
+  const int M = a.M;
+  const size_t MM = (size_t)M * M;
+  float2 num[OBJ_ROWS];
+  float den[OBJ_ROWS];
+#pragma unroll
+  for (int i = 0; i < OBJ_ROWS; ++i) {
+    num[i] = make_float2(0.f, 0.f);
+    den[i] = 0.f;
+  }
+  const int s0 = a.tile_ptr[tile], s1 = a.tile_ptr[tile + 1];
+  for (int s = s0; s < s1; ++s) {
+    const int j = a.tile_list[s];
+    const int2 p = a.pos[j];
+    const int ux = x - p.y;
+    if (ux < 0 || ux >= M) continue;
+    const float w = (MODE == OBJ_DIR || MODE == OBJ_DM || a.weights == nullptr) ? 1.f : a.weights[j];
+#pragma unroll
+    for (int i = 0; i < OBJ_ROWS; ++i) {
+      const int uy = ty0 + tyb + (OBJ_NT / TILE_X) * i - p.x;
+      if (uy < 0 || uy >= M) continue;
+      const size_t u = (size_t)uy * M + ux;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float2 pr = __ldg(a.P + k * MM + u);
+        if (MODE == OBJ_DEN) {
+          den[i] += cabs2(pr);
+        } else {
+          const float2 xv = __ldg(a.X + ((size_t)j * K + k) * MM + u);
+          float2 t = cconjmul(pr, xv);
+          num[i].x = fmaf(w, t.x, num[i].x);
+          num[i].y = fmaf(w, t.y, num[i].y);
+        }
+      }
+    }
+  }
+  if (MODE == OBJ_DEN) {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < OBJ_ROWS; ++i) {
+      const int y = ty0 + tyb + (OBJ_NT / TILE_X) * i;
+      if (y < a.ny && x < a.nx) {
+        a.den[(size_t)y * a.nx + x] = den[i];
+        m = fmaxf(m, den[i]);
+      }
+    }
+    m = block_max_f<OBJ_NT>(m, red);
+    if (threadIdx.x == 0) a.tile_max[tile] = m;
+    return;
+  }
+  const float delta = a.reg * a.den_max[0];
+#pragma unroll
+  for (int i = 0; i < OBJ_ROWS; ++i) {
+    const int y = ty0 + tyb + (OBJ_NT / TILE_X) * i;
+    if (y >= a.ny || x >= a.nx) continue;
+    const size_t r = (size_t)y * a.nx + x;
+    const float d = a.den[r] + delta;
+    const float inv = d > 0.f ? 1.f / d : 0.f;
+    if (MODE == OBJ_DM) {
+      const float2 o = a.O[r];
+      a.O[r] = make_float2(fmaf(delta, o.x, num[i].x) * inv, fmaf(delta, o.y, num[i].y) * inv);
+    } else if (MODE == OBJ_DIR) {
+      a.dO[r] = cscale(num[i], inv);
+    } else {
+      const float2 o = a.O[r];
+      const float sc = a.beta * inv;
+      a.O[r] = make_float2(fmaf(sc, num[i].x, o.x), fmaf(sc, num[i].y, o.y));
+    }
+  }
+}
+
+// Max of n floats into out[0] (one CTA, fixed order).
+__global__ void __launch_bounds__(1024) k_reduce_max(const float* in, int n, float* out) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += 1024) m = fmaxf(m, in[i]);
+  m = block_max_f<1024>(m, red);
+  if (threadIdx.x == 0) out[0] = m;
+}
+
+struct ProbeArgs {
+  const float2* O;
+  int nx;
+  const float2* X;         // [J][K][M][M]
+  const int2* pos;
+  const float* weights;    // alpha_P or NULL
+  int J, M, G;
+  float2* part_num;        // [G][K][M*M]
+  float* part_den;         // [G][M*M] or NULL (skip den)
+  float2* num;             // [K][M*M]
+  float* den;              // [M*M]
+  float* blk_max;          // [ceil(M*M/256)]
+  float2* P;               // PR_DM, PR_UPD: in/out
+  float2* dP;              // PR_DIR: out
+  float reg, beta;
+};
+
+template <int K>
+__global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
+  const int MM = a.M * a.M;
+  const int u = blockIdx.x * PROBE_NT + threadIdx.x;
+  if (u >= MM) return;
+  const int uy = u / a.M, ux = u % a.M;
+  const int g = blockIdx.y;
+  const int jb = (int)(((long long)a.J * g) / a.G), je = (int)(((long long)a.J * (g + 1)) / a.G);
+  float2 num[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) num[k] = make_float2(0.f, 0.f);
+  float den = 0.f;
+  const bool want_den = a.part_den != nullptr;
+  for (int j = jb; j < je; ++j) {
+    const int2 p = a.pos[j];
+    const float2 o = __ldg(a.O + (size_t)(p.x + uy) * a.nx + p.y + ux);
+    if (want_den) den += cabs2(o);
+    const float w = a.weights ? a.weights[j] : 1.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 xv = __ldg(a.X + ((size_t)j * K + k) * MM + u);
+      const float2 t = cconjmul(o, xv);
+      num[k].x = fmaf(w, t.x, num[k].x);
+      num[k].y = fmaf(w, t.y, num[k].y);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) a.part_num[((size_t)g * K + k) * MM + u] = num[k];
+  if (want_den) a.part_den[(size_t)g * MM + u] = den;
+}
+
+// Sum the G partials in group order; block maxima of den for the regulariser.
+template <int K>
+__global__ void __launch_bounds__(PROBE_NT) k_probe_sum(ProbeArgs a) {
+  __shared__ float red[32];
+  const int MM = a.M * a.M;
+  const int u = blockIdx.x * PROBE_NT + threadIdx.x;
+  const bool want_den = a.part_den != nullptr;
+  float m = 0.f;
+  if (u < MM) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float2 s = make_float2(0.f, 0.f);
+      for (int g = 0; g < a.G; ++g) s = cadd(s, a.part_num[((size_t)g * K + k) * MM + u]);
+      a.num[(size_t)k * MM + u] = s;
+    }
+    if (want_den) {
+      float d = 0.f;
+      for (int g = 0; g < a.G; ++g) d += a.part_den[(size_t)g * MM + u];
+      a.den[u] = d;
+      m = d;
+    }
+  }
+  if (want_den) {
+    m = block_max_f<PROBE_NT>(m, red);
+    if (threadIdx.x == 0) a.blk_max[blockIdx.x] = m;
+  }
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(PROBE_NT) k_probe_apply(ProbeArgs a) {
+  __shared__ float red[32];
+  __shared__ float s_max;
+  const int MM = a.M * a.M;
+  const int nblk = (MM + PROBE_NT - 1) / PROBE_NT;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < nblk; i += PROBE_NT) m = fmaxf(m, a.blk_max[i]);
+  m = block_max_f<PROBE_NT>(m, red);
+  if (threadIdx.x == 0) s_max = m;
+  __syncthreads();
+  const int u = blockIdx.x * PROBE_NT + threadIdx.x;
+  if (u >= MM) return;
+  const float delta = a.reg * s_max;
+  const float d = a.den[u] + delta;
+  const float inv = d > 0.f ? 1.f / d : 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const size_t i = (size_t)k * MM + u;
+    const float2 n = a.num[i];
+    if (MODE == PR_DM) {
+      const float2 pr = a.P[i];
+      a.P[i] = make_float2(fmaf(delta, pr.x, n.x) * inv, fmaf(delta, pr.y, n.y) * inv);
+    } else if (MODE == PR_DIR) {
+      a.dP[i] = cscale(n, inv);
+    } else {
+      const float2 pr = a.P[i];
+      const float sc = a.beta * inv;
+      a.P[i] = make_float2(fmaf(sc, n.x, pr.x), fmaf(sc, n.y, pr.y));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSQML per-position step sizes.  a_k = P_k dO_j, b_k = O_j dP_k; the five
+// sums |a|^2, Re<a,b>, |b|^2, Re<a,chi>, Re<b,chi> are accumulated per thread
+// in FP32 and across the block in FP64; the regularised 2x2 system
+// (lambda = 1e-6 (A11 + A22) / 2) is solved in FP64 by one thread.
+// ---------------------------------------------------------------------------
+struct StepArgs {
+  const float2* O;
+  const float2* dO;
+  int nx;
+  const float2* P;
+  const float2* dP;   // NULL when the probe is fixed
+  const float2* X;    // chi
+  const int2* pos;
+  int M;
+  float* alpha_O;
+  float* alpha_P;
+};
+
+constexpr int STEP_NT = 256;
+
+template <int K>
+__global__ void __launch_bounds__(STEP_NT) k_lsqml_steps(StepArgs a) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  const int2 p = a.pos[j];
+  const int MM = a.M * a.M;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+  const bool upd = a.dP != nullptr;
+  for (int u = threadIdx.x; u < MM; u += STEP_NT) {
+    const int uy = u / a.M, ux = u % a.M;
+    const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
+    const float2 o = __ldg(a.O + r);
+    const float2 dov = __ldg(a.dO + r);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 av = cmul(__ldg(a.P + (size_t)k * MM + u), dov);
+      const float2 xv = __ldg(a.X + ((size_t)j * K + k) * MM + u);
+      s0 += cabs2(av);
+      s3 += fmaf(av.x, xv.x, av.y * xv.y);
+      if (upd) {
+        const float2 bv = cmul(o, __ldg(a.dP + (size_t)k * MM + u));
+        s1 += fmaf(av.x, bv.x, av.y * bv.y);
+        s2 += cabs2(bv);
+        s4 += fmaf(bv.x, xv.x, bv.y * xv.y);
+      }
+    }
+  }
+  const double A11 = block_sum_d<STEP_NT>(s0, red);
+  const double A12 = block_sum_d<STEP_NT>(s1, red);
+  const double A22 = block_sum_d<STEP_NT>(s2, red);
+  const double r1 = block_sum_d<STEP_NT>(s3, red);
+  const double r2 = block_sum_d<STEP_NT>(s4, red);
+  if (threadIdx.x == 0) {
+    double aO = 0.0, aP = 0.0;
+    const double tr = A11 + A22;
+    if (tr > 0.0) {
+      const double lam = 1e-6 * tr / 2.0;
+      const double a11 = A11 + lam, a22 = A22 + lam;
+      const double det = a11 * a22 - A12 * A12;
+      aO = (a22 * r1 - A12 * r2) / det;
+      aP = (a11 * r2 - A12 * r1) / det;
+    }
+    a.alpha_O[j] = (float)aO;
+    a.alpha_P[j] = (float)aP;
+  }
+}
+
+// Final fixed-order FP64 reduction of n (num, den) partials.
+__global__ void __launch_bounds__(1024) k_err_final(const double2* part, int n, double2* out) {
+  __shared__ double red[32];
+  double sn = 0.0, sd = 0.0;
+  for (int i = threadIdx.x; i < n; i += 1024) {
+    sn += part[i].x;
+    sd += part[i].y;
+  }
+  const double tn = block_sum_d<1024>(sn, red);
+  const double td = block_sum_d<1024>(sd, red);
+  if (threadIdx.x == 0) out[0] = make_double2(tn, td);
+}
+
+}  // namespace ptycho

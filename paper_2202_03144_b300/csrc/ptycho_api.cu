@@ -1,0 +1,988 @@
+// C ABI of the B300 ptychography engine (declared in include/ptycho.h).
+//
+// Host side of the library: parameter validation, device buffers, the CSR
+// lists of positions per object tile, the ePIE visiting order, the kernel
+// dispatch table and the per-iteration launch sequences of ePIE, DM and
+// LSQML.  Every step of an iteration runs in the CUDA kernels of fourier.cuh,
+// overlap.cuh and epie.cuh; nothing here computes on the host beyond the
+// geometry (rounding positions, tile lists) and the random visiting order.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ptycho.h"
+#include "epie.cuh"
+#include "fourier.cuh"
+#include "overlap.cuh"
+
+using namespace ptycho;
+
+// ---------------------------------------------------------------------------
+// Kernel dispatch table: one entry per compiled (M, K, C).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct KernelSet {
+  int M, K, C, NT;
+  size_t smem_fourier, smem_epie;
+  void (*fourier)(FourierArgs);
+  void (*epie)(EpieArgs);
+};
+
+template <int M, int K, int C>
+KernelSet make_set() {
+  using F = FCfg<M, K, C>;
+  return KernelSet{M, K, C, F::NT, fourier_smem<F>(), epie_smem<F>(), k_fourier<M, K, C>, k_epie<M, K, C>};
+}
+
+const std::vector<KernelSet>& kernel_sets() {
+  static const std::vector<KernelSet> sets = {
+      make_set<16, 1, 1>(),  make_set<16, 1, 2>(),  make_set<16, 2, 1>(),  make_set<16, 3, 1>(),
+      make_set<16, 3, 2>(),  make_set<32, 1, 1>(),  make_set<32, 1, 2>(),  make_set<32, 1, 4>(),
+      make_set<32, 2, 2>(),  make_set<32, 3, 1>(),  make_set<32, 3, 4>(),  make_set<64, 1, 1>(),
+      make_set<64, 1, 2>(),  make_set<64, 1, 4>(),  make_set<64, 3, 2>(),  make_set<64, 3, 4>(),
+      make_set<128, 1, 2>(), make_set<128, 1, 4>(), make_set<128, 1, 8>(), make_set<128, 3, 4>(),
+      make_set<128, 3, 8>(), make_set<256, 1, 4>(), make_set<256, 1, 8>(),
+  };
+  return sets;
+}
+
+const KernelSet* find_set(int M, int K, int C) {
+  for (const auto& s : kernel_sets())
+    if (s.M == M && s.K == K && s.C == C) return &s;
+  return nullptr;
+}
+
+// Default cluster size: the smallest C that keeps one CTA's share of a
+// position at <= 64 KB of complex data (two or more CTAs fit on an SM).
+int default_cluster(int M, int K) {
+  for (int C = 1; C <= 8; C *= 2)
+    if ((long long)K * M * M / C <= 8192 && find_set(M, K, C)) return C;
+  for (int C = 1; C <= 8; C *= 2)
+    if (find_set(M, K, C)) return C;
+  return 0;
+}
+
+thread_local std::string g_create_error;
+
+__global__ void k_twiddle(float2* tw, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    double s, c;
+    sincospi(2.0 * (double)i / (double)M, &s, &c);
+    tw[i] = make_float2((float)c, (float)-s);
+  }
+}
+
+// sqrt(I) into FFT order at f32; masked (I < 0) -> -1; non-finite -> flag.
+__global__ void k_amp_f32(const float* __restrict__ src, int nj, int M, float* __restrict__ dst, int* bad) {
+  const size_t MM = (size_t)M * M;
+  const size_t n = (size_t)nj * MM;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = i / MM;
+    const int ky = (int)((i % MM) / M), kx = (int)(i % M);
+    const float v = src[j * MM + (size_t)((ky + M / 2) % M) * M + (kx + M / 2) % M];
+    if (!isfinite(v)) *bad = 1;
+    dst[i] = v < 0.f ? -1.f : sqrtf(v);
+  }
+}
+
+// Per-frame maximum of sqrt(I) (masked pixels ignored); one CTA per frame.
+__global__ void __launch_bounds__(256) k_frame_max(const float* __restrict__ src, int M, float* out, int* bad) {
+  __shared__ float red[32];
+  const size_t MM = (size_t)M * M;
+  const float* f = src + blockIdx.x * MM;
+  float m = 0.f;
+  for (size_t i = threadIdx.x; i < MM; i += 256) {
+    const float v = f[i];
+    if (!isfinite(v)) *bad = 1;
+    if (v > 0.f) m = fmaxf(m, sqrtf(v));
+  }
+  m = block_max_f<256>(m, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = m > 0.f ? m : 1.f;
+}
+
+template <typename T>
+__device__ __forceinline__ T to16(float v);
+template <>
+__device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T>
+__global__ void k_amp_q16(const float* __restrict__ src, int nj, int M, const float* __restrict__ scale,
+                          T* __restrict__ dst) {
+  const size_t MM = (size_t)M * M;
+  const size_t n = (size_t)nj * MM;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = i / MM;
+    const int ky = (int)((i % MM) / M), kx = (int)(i % M);
+    const float v = src[j * MM + (size_t)((ky + M / 2) % M) * M + (kx + M / 2) % M];
+    dst[i] = to16<T>(v < 0.f ? -1.f : sqrtf(v) / scale[j]);
+  }
+}
+
+__global__ void k_fill_c(float2* p, size_t n, float2 v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// psi_{j,k} = P_k O_j (DM initial state)
+__global__ void k_exit_waves(const float2* __restrict__ O, int nx, const float2* __restrict__ P,
+                             const int2* __restrict__ pos, int J, int K, int M, float2* __restrict__ X) {
+  const size_t MM = (size_t)M * M;
+  const size_t n = (size_t)J * K * MM;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t u = i % MM;
+    const int k = (int)((i / MM) % K);
+    const int j = (int)(i / (MM * K));
+    const int2 p = pos[j];
+    const int uy = (int)(u / M), ux = (int)(u % M);
+    X[i] = cmul(P[k * MM + u], O[(size_t)(p.x + uy) * nx + p.y + ux]);
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood) -- the counter-based generator that
+// drives the ePIE visiting order.
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct ptycho_ctx {
+  ptycho_params p{};
+  cudaStream_t st = nullptr;
+  const KernelSet* ks = nullptr;
+  int C = 1;
+  // device state
+  float2* O = nullptr;
+  float2* P = nullptr;
+  float2* X = nullptr;       // DM exit waves psi / LSQML residual chi [J][K][M][M]
+  float2* dO = nullptr;      // LSQML object direction
+  float2* dP = nullptr;      // LSQML probe direction
+  float2* tw = nullptr;
+  int2* pos = nullptr;
+  void* amp = nullptr;       // stored sqrt(I)
+  float* amp_scale = nullptr;
+  float* denO = nullptr;
+  float* tile_max = nullptr;
+  float* denO_max = nullptr;
+  int* tile_ptr = nullptr;
+  int* tile_list = nullptr;
+  int n_tiles = 0, ntx = 0, nty = 0;
+  int G = 1;
+  float2* ppart = nullptr;
+  float* ppart_den = nullptr;
+  float2* pnum = nullptr;
+  float* pden = nullptr;
+  float* pblk_max = nullptr;
+  float* alphaO = nullptr;
+  float* alphaP = nullptr;
+  double2* err_part = nullptr;
+  double2* err_out = nullptr;
+  int* order = nullptr;
+  int order_cap = 0;
+  int* flag = nullptr;
+  // host-side state
+  bool have_pos = false, have_data = false;
+  bool epie_ok = false;    // the ePIE kernel of this (M, K, C) fits in shared memory
+  bool psi_valid = false;  // X holds the DM state
+  bool denO_valid = false; // denO / denO_max match the current probe
+  long long t = 0;
+  long long launches = 0;
+  std::string err;
+  // profiling
+  struct Pending {
+    int fam;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  bool prof = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::string> fam_names;
+  std::vector<ptycho_kernel_stat> stats;
+  std::vector<int2> pos_host;
+};
+
+namespace {
+
+int fail(ptycho_ctx* c, int code, const char* fmt, ...) {
+  char b[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b, sizeof b, fmt, ap);
+  va_end(ap);
+  if (c) c->err = b;
+  else g_create_error = b;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? PTYCHO_ERR_OOM : PTYCHO_ERR_CUDA,    \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);       \
+  } while (0)
+
+template <typename T>
+int dalloc(ptycho_ctx* ctx, T** p, size_t n) {
+  if (*p) return 0;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(ctx, PTYCHO_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  return 0;
+}
+
+cudaEvent_t get_event(ptycho_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int family(ptycho_ctx* ctx, const char* name) {
+  for (size_t i = 0; i < ctx->fam_names.size(); ++i)
+    if (ctx->fam_names[i] == name) return (int)i;
+  ctx->fam_names.push_back(name);
+  ptycho_kernel_stat s{};
+  ctx->stats.push_back(s);
+  return (int)ctx->fam_names.size() - 1;
+}
+
+// Launch wrapper: counts launches, optionally brackets them with events and
+// checks the launch error.
+template <class Fn>
+int launch(ptycho_ctx* ctx, const char* name, double bytes, Fn&& fn) {
+  ptycho_ctx::Pending rec{};
+  if (ctx->prof) {
+    rec.fam = family(ctx, name);
+    rec.a = get_event(ctx);
+    rec.b = get_event(ctx);
+    rec.bytes = bytes;
+    cudaEventRecord(rec.a, ctx->st);
+  }
+  fn();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
+  ctx->launches++;
+  if (ctx->prof) {
+    cudaEventRecord(rec.b, ctx->st);
+    ctx->pending.push_back(rec);
+  }
+  return 0;
+}
+
+int collect_profile(ptycho_ctx* ctx) {
+  if (ctx->pending.empty()) return 0;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (auto& r : ctx->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto& s = ctx->stats[r.fam];
+    s.launches++;
+    s.ms += ms;
+    s.bytes += r.bytes;
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+  return 0;
+}
+
+size_t amp_bytes(const ptycho_ctx* ctx) { return ctx->p.istore == PTYCHO_I_F32 ? 4 : 2; }
+
+// ----------------------------------------------------------------- Fourier
+int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, int nj, const char* name) {
+  const KernelSet* ks = ctx->ks;
+  FourierArgs a{};
+  a.O = ctx->O;
+  a.nx = ctx->p.obj_nx;
+  a.P = ctx->P;
+  a.pos = ctx->pos;
+  a.X = X;
+  a.amp = ctx->amp;
+  a.amp_scale = ctx->amp_scale;
+  a.istore = ctx->p.istore;
+  a.I_out = I_out;
+  a.err_part = ctx->err_part;
+  a.tw = ctx->tw;
+  a.j0 = j0;
+  a.mode = mode;
+  const double MM = (double)ctx->p.M * ctx->p.M;
+  const double K = ctx->p.K;
+  double bytes = 0;
+  switch (mode) {
+    case FM_DM: bytes = nj * MM * (16.0 * K + amp_bytes(ctx)); break;
+    case FM_CHI: bytes = nj * MM * (8.0 * K + amp_bytes(ctx)); break;
+    case FM_ERR: bytes = nj * MM * amp_bytes(ctx); break;
+    case FM_SIM: bytes = nj * MM * 4.0; break;
+  }
+  return launch(ctx, name, bytes, [&] {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(ks->C * nj));
+    cfg.blockDim = dim3((unsigned)ks->NT);
+    cfg.dynamicSmemBytes = ks->smem_fourier;
+    cfg.stream = ctx->st;
+    cudaLaunchAttribute attr[1];
+    if (ks->C > 1) {
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = ks->C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, ks->fourier, a);
+  });
+}
+
+// ---------------------------------------------------------------- overlap
+template <int K>
+int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
+  ObjArgs a{};
+  a.O = ctx->O;
+  a.dO = ctx->dO;
+  a.ny = ctx->p.obj_ny;
+  a.nx = ctx->p.obj_nx;
+  a.ntx = ctx->ntx;
+  a.P = ctx->P;
+  a.X = X;
+  a.pos = ctx->pos;
+  a.tile_ptr = ctx->tile_ptr;
+  a.tile_list = ctx->tile_list;
+  a.weights = w;
+  a.den = ctx->denO;
+  a.tile_max = ctx->tile_max;
+  a.den_max = ctx->denO_max;
+  a.reg = (float)ctx->p.reg;
+  a.beta = (float)ctx->p.lsqml_beta;
+  a.M = ctx->p.M;
+  const double obj = (double)ctx->p.obj_ny * ctx->p.obj_nx;
+  const double xb = 8.0 * ctx->p.J * K * (double)ctx->p.M * ctx->p.M;
+  const dim3 g(ctx->n_tiles), b(OBJ_NT);
+  switch (mode) {
+    case OBJ_DEN:
+      if (int r = launch(ctx, "obj_den", obj * 4.0, [&] { k_obj<K, OBJ_DEN><<<g, b, 0, ctx->st>>>(a); })) return r;
+      return launch(ctx, "reduce_max", 0.0,
+                    [&] { k_reduce_max<<<1, 1024, 0, ctx->st>>>(ctx->tile_max, ctx->n_tiles, ctx->denO_max); });
+    case OBJ_DM:
+      return launch(ctx, "obj_update", xb + obj * 20.0, [&] { k_obj<K, OBJ_DM><<<g, b, 0, ctx->st>>>(a); });
+    case OBJ_DIR:
+      return launch(ctx, "obj_update", xb + obj * 12.0, [&] { k_obj<K, OBJ_DIR><<<g, b, 0, ctx->st>>>(a); });
+    default:
+      return launch(ctx, "obj_update", xb + obj * 20.0, [&] { k_obj<K, OBJ_UPD><<<g, b, 0, ctx->st>>>(a); });
+  }
+}
+
+int obj_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
+  switch (ctx->p.K) {
+    case 1: return launch_obj<1>(ctx, mode, X, w);
+    case 2: return launch_obj<2>(ctx, mode, X, w);
+    default: return launch_obj<3>(ctx, mode, X, w);
+  }
+}
+
+int ensure_denO(ptycho_ctx* ctx) {
+  if (ctx->denO_valid) return 0;
+  if (int r = obj_step(ctx, OBJ_DEN, nullptr, nullptr)) return r;
+  ctx->denO_valid = true;
+  return 0;
+}
+
+// probe: partial sums over position groups, fixed-order sum, apply.
+template <int K>
+int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, bool want_den, bool apply) {
+  ProbeArgs a{};
+  a.O = ctx->O;
+  a.nx = ctx->p.obj_nx;
+  a.X = X;
+  a.pos = ctx->pos;
+  a.weights = w;
+  a.J = ctx->p.J;
+  a.M = ctx->p.M;
+  a.G = ctx->G;
+  a.part_num = ctx->ppart;
+  a.part_den = want_den ? ctx->ppart_den : nullptr;
+  a.num = ctx->pnum;
+  a.den = ctx->pden;
+  a.blk_max = ctx->pblk_max;
+  a.P = ctx->P;
+  a.dP = ctx->dP;
+  a.reg = (float)ctx->p.reg;
+  a.beta = (float)ctx->p.lsqml_beta;
+  const int MM = ctx->p.M * ctx->p.M;
+  const int nblk = (MM + PROBE_NT - 1) / PROBE_NT;
+  const double xb = 8.0 * ctx->p.J * K * (double)MM;
+  if (X) {
+    if (int r = launch(ctx, "probe_partial", xb, [&] {
+          k_probe_partial<K><<<dim3(nblk, ctx->G), PROBE_NT, 0, ctx->st>>>(a);
+        }))
+      return r;
+    if (int r = launch(ctx, "probe_sum", 0.0, [&] { k_probe_sum<K><<<nblk, PROBE_NT, 0, ctx->st>>>(a); })) return r;
+  }
+  if (!apply) return 0;
+  switch (mode) {
+    case PR_DM: return launch(ctx, "probe_apply", 0.0, [&] { k_probe_apply<K, PR_DM><<<nblk, PROBE_NT, 0, ctx->st>>>(a); });
+    case PR_DIR: return launch(ctx, "probe_apply", 0.0, [&] { k_probe_apply<K, PR_DIR><<<nblk, PROBE_NT, 0, ctx->st>>>(a); });
+    default: return launch(ctx, "probe_apply", 0.0, [&] { k_probe_apply<K, PR_UPD><<<nblk, PROBE_NT, 0, ctx->st>>>(a); });
+  }
+}
+
+int probe_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w, bool want_den, bool apply) {
+  switch (ctx->p.K) {
+    case 1: return launch_probe<1>(ctx, mode, X, w, want_den, apply);
+    case 2: return launch_probe<2>(ctx, mode, X, w, want_den, apply);
+    default: return launch_probe<3>(ctx, mode, X, w, want_den, apply);
+  }
+}
+
+int steps_step(ptycho_ctx* ctx, bool upd) {
+  StepArgs a{};
+  a.O = ctx->O;
+  a.dO = ctx->dO;
+  a.nx = ctx->p.obj_nx;
+  a.P = ctx->P;
+  a.dP = upd ? ctx->dP : nullptr;
+  a.X = ctx->X;
+  a.pos = ctx->pos;
+  a.M = ctx->p.M;
+  a.alpha_O = ctx->alphaO;
+  a.alpha_P = ctx->alphaP;
+  const double xb = 8.0 * ctx->p.J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
+  const int J = ctx->p.J;
+  switch (ctx->p.K) {
+    case 1: return launch(ctx, "lsqml_steps", xb, [&] { k_lsqml_steps<1><<<J, STEP_NT, 0, ctx->st>>>(a); });
+    case 2: return launch(ctx, "lsqml_steps", xb, [&] { k_lsqml_steps<2><<<J, STEP_NT, 0, ctx->st>>>(a); });
+    default: return launch(ctx, "lsqml_steps", xb, [&] { k_lsqml_steps<3><<<J, STEP_NT, 0, ctx->st>>>(a); });
+  }
+}
+
+int ensure_work_buffers(ptycho_ctx* ctx) {
+  const size_t MM = (size_t)ctx->p.M * ctx->p.M;
+  const size_t K = ctx->p.K;
+  if (int r = dalloc(ctx, &ctx->X, (size_t)ctx->p.J * K * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->dO, (size_t)ctx->p.obj_ny * ctx->p.obj_nx)) return r;
+  if (int r = dalloc(ctx, &ctx->dP, K * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->ppart, (size_t)ctx->G * K * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->ppart_den, (size_t)ctx->G * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->pnum, K * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->pden, MM)) return r;
+  if (int r = dalloc(ctx, &ctx->pblk_max, (MM + PROBE_NT - 1) / PROBE_NT)) return r;
+  if (int r = dalloc(ctx, &ctx->alphaO, (size_t)ctx->p.J)) return r;
+  if (int r = dalloc(ctx, &ctx->alphaP, (size_t)ctx->p.J)) return r;
+  return 0;
+}
+
+// ------------------------------------------------------------- algorithms
+int run_dm(ptycho_ctx* ctx, int n) {
+  if (int r = ensure_work_buffers(ctx)) return r;
+  const int J = ctx->p.J, K = ctx->p.K, M = ctx->p.M;
+  if (!ctx->psi_valid) {
+    const size_t n_el = (size_t)J * K * M * M;
+    if (int r = launch(ctx, "exit_waves", 8.0 * n_el, [&] {
+          k_exit_waves<<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->P, ctx->pos, J, K, M, ctx->X);
+        }))
+      return r;
+    ctx->psi_valid = true;
+  }
+  for (int it = 0; it < n; ++it) {
+    const bool upd = ctx->t >= ctx->p.probe_start;
+    if (int r = ensure_denO(ctx)) return r;
+    if (int r = obj_step(ctx, OBJ_DM, ctx->X, nullptr)) return r;
+    if (upd) {
+      if (int r = probe_step(ctx, PR_DM, ctx->X, nullptr, true, true)) return r;
+      ctx->denO_valid = false;
+    }
+    if (int r = launch_fourier(ctx, FM_DM, ctx->X, nullptr, 0, J, "fourier_dm")) return r;
+    ctx->t++;
+  }
+  return 0;
+}
+
+int run_lsqml(ptycho_ctx* ctx, int n) {
+  if (int r = ensure_work_buffers(ctx)) return r;
+  ctx->psi_valid = false;
+  for (int it = 0; it < n; ++it) {
+    const bool upd = ctx->t >= ctx->p.probe_start;
+    if (int r = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, ctx->p.J, "fourier_chi")) return r;
+    if (int r = ensure_denO(ctx)) return r;
+    if (int r = obj_step(ctx, OBJ_DIR, ctx->X, nullptr)) return r;
+    if (upd)
+      if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
+    if (int r = steps_step(ctx, upd)) return r;
+    if (upd)  // alpha_P-weighted probe numerator from the old object
+      if (int r = probe_step(ctx, PR_UPD, ctx->X, ctx->alphaP, false, false)) return r;
+    if (int r = obj_step(ctx, OBJ_UPD, ctx->X, ctx->alphaO)) return r;
+    if (upd) {
+      if (int r = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return r;
+      ctx->denO_valid = false;
+    }
+    ctx->t++;
+  }
+  return 0;
+}
+
+int run_epie(ptycho_ctx* ctx, int n) {
+  if (!ctx->epie_ok)
+    return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE kernel for M=%d K=%d cluster=%d exceeds shared memory; use a larger cluster",
+                ctx->p.M, ctx->p.K, ctx->C);
+  const int J = ctx->p.J;
+  std::vector<int> ord((size_t)n * J);
+  for (int it = 0; it < n; ++it) {
+    int* o = ord.data() + (size_t)it * J;
+    for (int i = 0; i < J; ++i) o[i] = i;
+    if (ctx->p.seed != 0) {
+      SplitMix64 g{ctx->p.seed ^ (uint64_t)(ctx->t + it)};
+      for (int i = J - 1; i > 0; --i) {
+        const int r = (int)(g.next() % (uint64_t)(i + 1));
+        std::swap(o[i], o[r]);
+      }
+    }
+  }
+  if ((size_t)ctx->order_cap < ord.size()) {
+    if (ctx->order) cudaFree(ctx->order);
+    ctx->order = nullptr;
+    if (int r = dalloc(ctx, &ctx->order, ord.size())) return r;
+    ctx->order_cap = (int)ord.size();
+  }
+  CK(cudaMemcpyAsync(ctx->order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  EpieArgs a{};
+  a.O = ctx->O;
+  a.nx = ctx->p.obj_nx;
+  a.P = ctx->P;
+  a.pos = ctx->pos;
+  a.amp = ctx->amp;
+  a.amp_scale = ctx->amp_scale;
+  a.istore = ctx->p.istore;
+  a.tw = ctx->tw;
+  a.order = ctx->order;
+  a.J = J;
+  a.n_iter = n;
+  a.t0 = ctx->t;
+  a.probe_start = ctx->p.probe_start;
+  a.alpha = (float)ctx->p.epie_alpha;
+  a.beta = (float)ctx->p.epie_beta;
+  const KernelSet* ks = ctx->ks;
+  const double bytes = (double)n * J * ctx->p.M * ctx->p.M * amp_bytes(ctx);
+  int r = launch(ctx, "epie", bytes, [&] {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)ks->C);
+    cfg.blockDim = dim3((unsigned)ks->NT);
+    cfg.dynamicSmemBytes = ks->smem_epie;
+    cfg.stream = ctx->st;
+    cudaLaunchAttribute attr[1];
+    if (ks->C > 1) {
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = ks->C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, ks->epie, a);
+  });
+  if (r) return r;
+  // the host order buffer must outlive the async copy
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->t += n;
+  ctx->psi_valid = false;
+  ctx->denO_valid = false;
+  return 0;
+}
+
+int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
+  if (!positions) return fail(ctx, PTYCHO_ERR_ARG, "positions is NULL");
+  const int J = ctx->p.J, M = ctx->p.M, ny = ctx->p.obj_ny, nx = ctx->p.obj_nx;
+  std::vector<int2> pos(J);
+  for (int j = 0; j < J; ++j) {
+    const float fy = positions[2 * j], fx = positions[2 * j + 1];
+    if (!std::isfinite(fy) || !std::isfinite(fx))
+      return fail(ctx, PTYCHO_ERR_NONFINITE, "position %d is not finite", j);
+    const double y = std::nearbyint((double)fy), x = std::nearbyint((double)fx);
+    if (y < 0 || x < 0 || y + M > ny || x + M > nx)
+      return fail(ctx, PTYCHO_ERR_BOUNDS, "patch %d at (%g, %g) falls outside the %dx%d object", j, y, x, ny, nx);
+    pos[j] = make_int2((int)y, (int)x);
+  }
+  // CSR lists of positions per object tile, ascending position index
+  std::vector<int> cnt(ctx->n_tiles + 1, 0);
+  for (int j = 0; j < J; ++j) {
+    const int t0y = pos[j].x / TILE_Y, t1y = (pos[j].x + M - 1) / TILE_Y;
+    const int t0x = pos[j].y / TILE_X, t1x = (pos[j].y + M - 1) / TILE_X;
+    for (int ty = t0y; ty <= t1y; ++ty)
+      for (int tx = t0x; tx <= t1x; ++tx) cnt[ty * ctx->ntx + tx + 1]++;
+  }
+  for (int i = 0; i < ctx->n_tiles; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> list(cnt[ctx->n_tiles]);
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int j = 0; j < J; ++j) {
+    const int t0y = pos[j].x / TILE_Y, t1y = (pos[j].x + M - 1) / TILE_Y;
+    const int t0x = pos[j].y / TILE_X, t1x = (pos[j].y + M - 1) / TILE_X;
+    for (int ty = t0y; ty <= t1y; ++ty)
+      for (int tx = t0x; tx <= t1x; ++tx) list[fill[ty * ctx->ntx + tx]++] = j;
+  }
+  if (ctx->tile_list) cudaFree(ctx->tile_list);
+  ctx->tile_list = nullptr;
+  if (int r = dalloc(ctx, &ctx->tile_list, list.size() + 1)) return r;
+  CK(cudaMemcpy(ctx->pos, pos.data(), J * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tile_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->pos_host = pos;
+  ctx->have_pos = true;
+  ctx->psi_valid = false;
+  ctx->denO_valid = false;
+  return 0;
+}
+
+int copy_out(ptycho_ctx* ctx, float* out, const void* src, size_t bytes, int on_device) {
+  if (!out) return fail(ctx, PTYCHO_ERR_ARG, "output pointer is NULL");
+  CK(cudaMemcpyAsync(out, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void ptycho_default_params(ptycho_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->istore = PTYCHO_I_F32;
+  p->probe_start = 0;
+  p->epie_alpha = 1.0;
+  p->epie_beta = 1.0;
+  p->lsqml_beta = 0.9;
+  p->reg = 1e-3;
+  p->seed = 0;
+  p->stream = nullptr;
+  p->cluster = 0;
+}
+
+int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
+  ptycho_ctx* ctx = nullptr;
+  if (!out || !p) return fail(nullptr, PTYCHO_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (p->M < 2 || p->K < 1 || p->J < 1 || p->obj_ny < p->M || p->obj_nx < p->M)
+    return fail(nullptr, PTYCHO_ERR_ARG, "bad sizes M=%d K=%d J=%d object %dx%d", p->M, p->K, p->J, p->obj_ny,
+                p->obj_nx);
+  if (p->K > 3) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "K=%d modes: at most 3 are compiled in", p->K);
+  if (p->istore < 0 || p->istore > 2) return fail(nullptr, PTYCHO_ERR_ARG, "istore=%d", p->istore);
+  if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
+      !std::isfinite(p->lsqml_beta))
+    return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
+  const int C = p->cluster > 0 ? p->cluster : default_cluster(p->M, p->K);
+  const KernelSet* ks = find_set(p->M, p->K, C);
+  if (!ks)
+    return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "no kernel compiled for M=%d K=%d cluster=%d", p->M, p->K, C);
+  if ((long long)p->J * p->M * p->M > (1LL << 40)) return fail(nullptr, PTYCHO_ERR_ARG, "J*M*M too large");
+  ctx = new ptycho_ctx();
+  ctx->p = *p;
+  ctx->st = (cudaStream_t)p->stream;
+  ctx->ks = ks;
+  ctx->C = C;
+  ctx->ntx = (p->obj_nx + TILE_X - 1) / TILE_X;
+  ctx->nty = (p->obj_ny + TILE_Y - 1) / TILE_Y;
+  ctx->n_tiles = ctx->ntx * ctx->nty;
+  {
+    const int MM = p->M * p->M;
+    const int nblk = (MM + PROBE_NT - 1) / PROBE_NT;
+    int G = (4 * 148 + nblk - 1) / nblk;
+    if (G > p->J) G = p->J;
+    if (G < 1) G = 1;
+    ctx->G = G;
+  }
+  int r = 0;
+  const size_t obj = (size_t)p->obj_ny * p->obj_nx;
+  const size_t MM = (size_t)p->M * p->M;
+  if (!r) r = dalloc(ctx, &ctx->O, obj);
+  if (!r) r = dalloc(ctx, &ctx->P, (size_t)p->K * MM);
+  if (!r) r = dalloc(ctx, &ctx->tw, (size_t)p->M);
+  if (!r) r = dalloc(ctx, &ctx->pos, (size_t)p->J);
+  if (!r) r = dalloc(ctx, &ctx->denO, obj);
+  if (!r) r = dalloc(ctx, &ctx->tile_max, (size_t)ctx->n_tiles);
+  if (!r) r = dalloc(ctx, &ctx->denO_max, 1);
+  if (!r) r = dalloc(ctx, &ctx->tile_ptr, (size_t)ctx->n_tiles + 1);
+  if (!r) r = dalloc(ctx, &ctx->err_part, (size_t)p->J * C);
+  if (!r) r = dalloc(ctx, &ctx->err_out, 1);
+  if (!r) r = dalloc(ctx, &ctx->flag, 1);
+  if (!r) {
+    if (p->istore == PTYCHO_I_F32) r = dalloc(ctx, (float**)&ctx->amp, (size_t)p->J * MM);
+    else r = dalloc(ctx, (__half**)&ctx->amp, (size_t)p->J * MM);
+  }
+  if (!r) r = dalloc(ctx, &ctx->amp_scale, (size_t)p->J);
+  if (r) {
+    g_create_error = ctx->err;
+    ptycho_destroy(ctx);
+    return r;
+  }
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess && ks->smem_fourier > (size_t)optin) {
+    g_create_error = "Fourier kernel needs more shared memory than the device offers";
+    ptycho_destroy(ctx);
+    return PTYCHO_ERR_UNSUPPORTED;
+  }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
+  ctx->epie_ok = e == cudaSuccess && ks->smem_epie <= (size_t)optin;
+  if (ctx->epie_ok)
+    e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_epie);
+  if (e == cudaSuccess) {
+    k_twiddle<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw, p->M);
+    k_fill_c<<<256, 256, 0, ctx->st>>>(ctx->O, obj, make_float2(1.f, 0.f));
+    k_fill_c<<<256, 256, 0, ctx->st>>>(ctx->P, (size_t)p->K * MM, make_float2(0.f, 0.f));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device setup failed: ") + cudaGetErrorString(e);
+    ptycho_destroy(ctx);
+    return PTYCHO_ERR_CUDA;
+  }
+  *out = ctx;
+  return PTYCHO_OK;
+}
+
+int ptycho_set_positions(ptycho_ctx* ctx, const float* positions) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  return set_positions_impl(ctx, positions);
+}
+
+int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* positions, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!intensities) return fail(ctx, PTYCHO_ERR_ARG, "intensities is NULL");
+  if (int r = set_positions_impl(ctx, positions)) return r;
+  ctx->have_data = false;
+  const int J = ctx->p.J, M = ctx->p.M;
+  const size_t MM = (size_t)M * M;
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (256u << 20) / (MM * 4)));
+  float* stage = nullptr;
+  if (int r = dalloc(ctx, &stage, (size_t)chunk * MM)) return r;
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+  int rc = 0;
+  for (int j0 = 0; j0 < J && !rc; j0 += chunk) {
+    const int nj = std::min(chunk, J - j0);
+    const float* src = intensities + (size_t)j0 * MM;
+    cudaError_t e = cudaMemcpyAsync(stage, src, (size_t)nj * MM * 4,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st);
+    if (e != cudaSuccess) {
+      rc = fail(ctx, PTYCHO_ERR_CUDA, "intensity upload: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (ctx->p.istore == PTYCHO_I_F32) {
+      rc = launch(ctx, "prepare_amp", 8.0 * nj * MM, [&] {
+        k_amp_f32<<<1184, 256, 0, ctx->st>>>(stage, nj, M, (float*)ctx->amp + (size_t)j0 * MM, ctx->flag);
+      });
+    } else {
+      rc = launch(ctx, "frame_max", 4.0 * nj * MM,
+                  [&] { k_frame_max<<<nj, 256, 0, ctx->st>>>(stage, M, ctx->amp_scale + j0, ctx->flag); });
+      if (!rc) {
+        if (ctx->p.istore == PTYCHO_I_F16)
+          rc = launch(ctx, "prepare_amp", 6.0 * nj * MM, [&] {
+            k_amp_q16<__half><<<1184, 256, 0, ctx->st>>>(stage, nj, M, ctx->amp_scale + j0,
+                                                        (__half*)ctx->amp + (size_t)j0 * MM);
+          });
+        else
+          rc = launch(ctx, "prepare_amp", 6.0 * nj * MM, [&] {
+            k_amp_q16<__nv_bfloat16><<<1184, 256, 0, ctx->st>>>(stage, nj, M, ctx->amp_scale + j0,
+                                                               (__nv_bfloat16*)ctx->amp + (size_t)j0 * MM);
+          });
+      }
+    }
+  }
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(stage);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "set_data: %s", cudaGetErrorString(e));
+  if (bad) return fail(ctx, PTYCHO_ERR_NONFINITE, "intensities contain NaN or Inf");
+  ctx->have_data = true;
+  ctx->psi_valid = false;
+  return PTYCHO_OK;
+}
+
+int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (object) {
+    const size_t n = (size_t)ctx->p.obj_ny * ctx->p.obj_nx * 2;
+    if (!on_device)
+      for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(object[i])) return fail(ctx, PTYCHO_ERR_NONFINITE, "object guess has NaN/Inf");
+    CK(cudaMemcpyAsync(ctx->O, object, n * 4, kind, ctx->st));
+  }
+  if (probe) {
+    const size_t n = (size_t)ctx->p.K * ctx->p.M * ctx->p.M * 2;
+    if (!on_device)
+      for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(probe[i])) return fail(ctx, PTYCHO_ERR_NONFINITE, "probe guess has NaN/Inf");
+    CK(cudaMemcpyAsync(ctx->P, probe, n * 4, kind, ctx->st));
+    ctx->denO_valid = false;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->psi_valid = false;
+  return PTYCHO_OK;
+}
+
+int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (n_iter < 0) return fail(ctx, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
+  if (!ctx->have_data) return fail(ctx, PTYCHO_ERR_STATE, "iterate before set_data");
+  if (n_iter == 0) return PTYCHO_OK;
+  switch (alg) {
+    case PTYCHO_EPIE: return run_epie(ctx, n_iter);
+    case PTYCHO_DM: return run_dm(ctx, n_iter);
+    case PTYCHO_LSQML: return run_lsqml(ctx, n_iter);
+    default: return fail(ctx, PTYCHO_ERR_ARG, "unknown algorithm %d", alg);
+  }
+}
+
+int ptycho_get_object(ptycho_ctx* ctx, float* out, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  return copy_out(ctx, out, ctx->O, (size_t)ctx->p.obj_ny * ctx->p.obj_nx * 8, on_device);
+}
+
+int ptycho_get_probe(ptycho_ctx* ctx, float* out, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  return copy_out(ctx, out, ctx->P, (size_t)ctx->p.K * ctx->p.M * ctx->p.M * 8, on_device);
+}
+
+int ptycho_get_exit_waves(ptycho_ctx* ctx, float* out, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!ctx->psi_valid) return fail(ctx, PTYCHO_ERR_STATE, "no DM exit-wave state");
+  return copy_out(ctx, out, ctx->X, (size_t)ctx->p.J * ctx->p.K * ctx->p.M * ctx->p.M * 8, on_device);
+}
+
+int ptycho_fourier_error(ptycho_ctx* ctx, double* out) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!out) return fail(ctx, PTYCHO_ERR_ARG, "out is NULL");
+  if (!ctx->have_data) return fail(ctx, PTYCHO_ERR_STATE, "fourier_error before set_data");
+  if (int r = launch_fourier(ctx, FM_ERR, nullptr, nullptr, 0, ctx->p.J, "fourier_err")) return r;
+  const int n = ctx->p.J * ctx->C;
+  if (int r = launch(ctx, "err_final", 0.0, [&] { k_err_final<<<1, 1024, 0, ctx->st>>>(ctx->err_part, n, ctx->err_out); }))
+    return r;
+  double2 h;
+  CK(cudaMemcpyAsync(&h, ctx->err_out, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  const double E = h.y > 0 ? h.x / h.y : 0.0;
+  *out = E;
+  if (!std::isfinite(E)) return fail(ctx, PTYCHO_ERR_DIVERGED, "Fourier error is not finite");
+  return PTYCHO_OK;
+}
+
+int ptycho_simulate(ptycho_ctx* ctx, float* out, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!out) return fail(ctx, PTYCHO_ERR_ARG, "out is NULL");
+  if (!ctx->have_pos) return fail(ctx, PTYCHO_ERR_STATE, "simulate before set_positions");
+  const size_t n = (size_t)ctx->p.J * ctx->p.M * ctx->p.M;
+  float* dst = on_device ? out : nullptr;
+  if (!on_device)
+    if (int r = dalloc(ctx, &dst, n)) return r;
+  int r = launch_fourier(ctx, FM_SIM, nullptr, dst, 0, ctx->p.J, "fourier_sim");
+  if (!r && !on_device) r = copy_out(ctx, out, dst, n * 4, 0);
+  if (!r) {
+    cudaError_t e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) r = fail(ctx, PTYCHO_ERR_CUDA, "simulate: %s", cudaGetErrorString(e));
+  }
+  if (!on_device) cudaFree(dst);
+  return r;
+}
+
+int ptycho_fourier_residual(ptycho_ctx* ctx, float* out, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!out) return fail(ctx, PTYCHO_ERR_ARG, "out is NULL");
+  if (!ctx->have_data) return fail(ctx, PTYCHO_ERR_STATE, "residual before set_data");
+  const size_t n = (size_t)ctx->p.J * ctx->p.K * ctx->p.M * ctx->p.M;
+  float2* dst = on_device ? (float2*)out : nullptr;
+  if (!on_device)
+    if (int r = dalloc(ctx, &dst, n)) return r;
+  int r = launch_fourier(ctx, FM_CHI, dst, nullptr, 0, ctx->p.J, "fourier_chi");
+  if (!r && !on_device) r = copy_out(ctx, out, dst, n * 8, 0);
+  if (!r) {
+    cudaError_t e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) r = fail(ctx, PTYCHO_ERR_CUDA, "residual: %s", cudaGetErrorString(e));
+  }
+  if (!on_device) cudaFree(dst);
+  return r;
+}
+
+long long ptycho_iteration(const ptycho_ctx* ctx) { return ctx ? ctx->t : -1; }
+long long ptycho_launch_count(const ptycho_ctx* ctx) { return ctx ? ctx->launches : -1; }
+int ptycho_cluster_size(const ptycho_ctx* ctx) { return ctx ? ctx->C : 0; }
+
+int ptycho_set_profiling(ptycho_ctx* ctx, int enabled) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (int r = collect_profile(ctx)) return r;
+  ctx->prof = enabled != 0;
+  for (auto& s : ctx->stats) s = ptycho_kernel_stat{};
+  return PTYCHO_OK;
+}
+
+int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (int r = collect_profile(ctx)) return r;
+  const int nf = (int)ctx->stats.size();
+  for (int i = 0; i < nf && i < max && out; ++i) {
+    out[i] = ctx->stats[i];
+    out[i].name = ctx->fam_names[i].c_str();
+  }
+  if (n) *n = nf;
+  return PTYCHO_OK;
+}
+
+const char* ptycho_last_error(const ptycho_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void ptycho_destroy(ptycho_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  void* bufs[] = {ctx->O,        ctx->P,         ctx->X,        ctx->dO,       ctx->dP,        ctx->tw,
+                  ctx->pos,      ctx->amp,       ctx->amp_scale, ctx->denO,    ctx->tile_max,  ctx->denO_max,
+                  ctx->tile_ptr, ctx->tile_list, ctx->ppart,    ctx->ppart_den, ctx->pnum,     ctx->pden,
+                  ctx->pblk_max, ctx->alphaO,    ctx->alphaP,   ctx->err_part, ctx->err_out,   ctx->order,
+                  ctx->flag};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (auto& r : ctx->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+}  // extern "C"

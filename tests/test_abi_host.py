@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI that need no GPU: the shared library loads,
+exports every entry point include/ptycho.h declares, and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2202_03144_b300 import api
+from paper_2202_03144_b300.build import LIB, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return api.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ptycho.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptycho_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["ptycho_create", "ptycho_set_data", "ptycho_set_init", "ptycho_iterate", "ptycho_get_object",
+              "ptycho_get_probe", "ptycho_fourier_error", "ptycho_destroy", "ptycho_last_error"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(LIB)
+    missing = [s for s in declared_symbols() if not hasattr(raw, s)]
+    assert not missing, missing
+
+
+def test_default_params(lib):
+    p = api.default_params()
+    assert p.reg == pytest.approx(1e-3) and p.lsqml_beta == pytest.approx(0.9)
+    assert p.epie_alpha == 1.0 and p.epie_beta == 1.0 and p.istore == 0 and p.seed == 0
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(M=0, K=1, J=4, obj_ny=64, obj_nx=64), "ARG"),
+    (dict(M=32, K=1, J=0, obj_ny=64, obj_nx=64), "ARG"),
+    (dict(M=32, K=1, J=4, obj_ny=16, obj_nx=64), "ARG"),
+    (dict(M=32, K=5, J=4, obj_ny=64, obj_nx=64), "UNSUPPORTED"),
+    (dict(M=48, K=1, J=4, obj_ny=64, obj_nx=64), "UNSUPPORTED"),
+    (dict(M=32, K=1, J=4, obj_ny=64, obj_nx=64, istore=7), "ARG"),
+    (dict(M=32, K=1, J=4, obj_ny=64, obj_nx=64, cluster=3), "UNSUPPORTED"),
+])
+def test_create_rejects_bad_params(lib, kw, code):
+    with pytest.raises(api.PtychoError) as e:
+        api.create(api.default_params(**kw))
+    assert e.value.name == code
+
+
+def test_null_context_calls_are_safe(lib):
+    L = api.lib()
+    assert L.ptycho_iterate(None, 1, 1) == -1
+    assert L.ptycho_launch_count(None) == -1
+    L.ptycho_destroy(None)
+
+
+def test_to_pixels_listing1():
+    """Listing 1 (sim512): lambda = 2.4797e-10 m, z = 1 m, 172 um pixels, 512 px
+    detector, 50 nm step, 110 nm beam -> object pixel lambda z / (M dx_d)."""
+    vals = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "listing1_sim512.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    step_px = api.to_pixels(vals["lambda"], vals["z"], vals["dx_d"], int(vals["size"]), vals["step"])
+    beam_px = api.to_pixels(vals["lambda"], vals["z"], vals["dx_d"], int(vals["size"]), vals["beamSize"])
+    dx = vals["lambda"] * vals["z"] / (vals["size"] * vals["dx_d"])
+    assert dx == pytest.approx(2.8158e-9, rel=1e-4)
+    assert step_px == pytest.approx(17.757, rel=1e-4)
+    assert beam_px == pytest.approx(39.065, rel=1e-4)

@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (FP32 arithmetic vs FP64):
+  * single Fourier passes (forward model, residual, Fourier error): relative
+    L2 <= 2e-5 -- a radix FFT of length M in FP32 has rms relative error of a
+    few 1e-7 * log2(M), the projection adds a few ulps;
+  * reconstructions after n iterations from the same start: relative L2 <= 1e-4
+    over the illuminated object region (den_O >= 0.1 max) after global
+    complex-scalar alignment, and on the probe; Fourier error to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+from gpu_cases import COMPILED, illuminated, scan
+from oracle import ptycho_oracle as orc
+from paper_2202_03144_b300 import api
+from util import align_global, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_PASS = 2e-5
+TOL_REC = 1e-4
+
+
+def recon(c, cluster=0, **kw):
+    r = api.Reconstruction(c["M"], c["K"], len(c["pos"]), c["shape"], cluster=cluster, **kw)
+    r.set_data(c["I"].astype(np.float32), c["pos"])
+    r.set_init(c["O0"], c["P0"])
+    return r
+
+
+@pytest.mark.parametrize("M,K,C", COMPILED, ids=lambda v: str(v))
+def test_forward_model(M, K, C):
+    c = scan(M, K, grid=2)
+    with api.Reconstruction(M, K, len(c["pos"]), c["shape"], cluster=C) as r:
+        assert r.cluster == C
+        r.set_positions(c["pos"])
+        r.set_init(c["O"], c["P"])
+        I = r.simulate()
+    assert rel_l2(I, c["I"]) < TOL_PASS
+
+
+@pytest.mark.parametrize("M,K,C", COMPILED, ids=lambda v: str(v))
+def test_fourier_residual_and_error(M, K, C):
+    c = scan(M, K, grid=2, mask_frac=0.05)
+    with recon(c, cluster=C) as r:
+        chi = r.fourier_residual()
+        E = r.fourier_error()
+    pos_i = orc.round_positions(c["pos"])
+    chi_ref = orc.fourier_residual(c["O0"], c["P0"], pos_i, c["I"])
+    assert rel_l2(chi, chi_ref) < TOL_PASS
+    E_ref = orc.fourier_error(c["O0"], c["P0"], pos_i, c["I"])
+    assert abs(E - E_ref) <= 1e-5 * E_ref
+
+
+def _compare(c, alg, n, cluster=0, seed=0, probe_start=0, **kw):
+    with recon(c, cluster=cluster, seed=seed, probe_start=probe_start, **kw) as r:
+        r.iterate(alg, n)
+        Og, Pg = r.get_object(), r.get_probe()
+        E = r.fourier_error()
+        psi = r.get_exit_waves() if alg == "dm" else None
+    Oc, Pc, psic = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, seed=seed, probe_start=probe_start,
+                                   **{k: v for k, v in kw.items() if k in ("reg", "epie_alpha", "epie_beta", "lsqml_beta")})
+    m = illuminated(c["P"], c["pos"], c["shape"])
+    eo = rel_l2(align_global(Og, Oc, m), Oc, m)
+    ep = rel_l2(Pg, Pc)
+    E_ref = orc.fourier_error(Oc, Pc, orc.round_positions(c["pos"]), c["I"])
+    out = dict(eo=eo, ep=ep, E=E, E_ref=E_ref)
+    if psi is not None:
+        out["epsi"] = rel_l2(psi, psic)
+    return out
+
+
+ALG_CASES = [
+    ("dm", 32, 1, 1), ("dm", 32, 3, 4), ("dm", 64, 1, 2), ("dm", 16, 2, 1),
+    ("lsqml", 32, 1, 1), ("lsqml", 32, 3, 1), ("lsqml", 64, 1, 4), ("lsqml", 16, 3, 2),
+    ("epie", 32, 1, 1), ("epie", 32, 3, 4), ("epie", 64, 1, 2), ("epie", 16, 1, 2),
+]
+
+
+@pytest.mark.parametrize("alg,M,K,C", ALG_CASES, ids=lambda v: str(v))
+@pytest.mark.parametrize("n", [1, 10])
+def test_algorithm_parity(alg, M, K, C, n):
+    if alg == "epie" and n == 10:
+        n = 4
+    c = scan(M, K, grid=3, photons=1e6, mask_frac=0.02)
+    res = _compare(c, alg, n, cluster=C, seed=7 if alg == "epie" else 0)
+    assert res["eo"] < TOL_REC, res
+    assert res["ep"] < TOL_REC, res
+    assert abs(res["E"] - res["E_ref"]) <= 1e-5 * res["E_ref"] + 1e-12, res
+    if "epsi" in res:
+        assert res["epsi"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml", "epie"])
+def test_fixed_probe_then_update(alg):
+    c = scan(32, 1, grid=3, photons=1e6)
+    res = _compare(c, alg, 4, probe_start=2, seed=3)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml", "epie"])
+def test_single_position(alg):
+    c = scan(32, 1, grid=1)
+    res = _compare(c, alg, 3)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml", "epie"])
+def test_step_mode_equals_whole_mode(alg):
+    """iterate(n) == n x iterate(1) with reads in between, bit for bit (Sec. 3.2
+    step mode vs whole mode); and two runs are identical (no atomics)."""
+    c = scan(32, 3, grid=3, photons=1e5)
+    with recon(c, cluster=4, seed=11) as a:
+        a.iterate(alg, 4)
+        Oa, Pa = a.get_object(), a.get_probe()
+    with recon(c, cluster=4, seed=11) as b:
+        for _ in range(4):
+            b.iterate(alg, 1)
+            b.get_object()
+            b.get_probe()
+        Ob, Pb = b.get_object(), b.get_probe()
+        assert b.iteration == 4
+    assert np.array_equal(Oa, Ob) and np.array_equal(Pa, Pb)
+
+
+def test_device_pointers_match_host():
+    torch = pytest.importorskip("torch")
+    c = scan(32, 1, grid=3)
+    with recon(c) as a:
+        a.iterate("dm", 2)
+        Oa = a.get_object()
+    with api.Reconstruction(32, 1, len(c["pos"]), c["shape"]) as b:
+        b.set_data(torch.from_numpy(c["I"].astype(np.float32)).cuda(), c["pos"])
+        b.set_init(torch.from_numpy(c["O0"].astype(np.complex64)).cuda(),
+                   torch.from_numpy(c["P0"].astype(np.complex64)).cuda())
+        b.iterate("dm", 2)
+        out = torch.empty(c["shape"], dtype=torch.complex64, device="cuda")
+        b.get_object(out)
+        torch.cuda.synchronize()
+        Ob = out.cpu().numpy()
+    assert np.array_equal(Oa, Ob)
+
+
+@pytest.mark.parametrize("istore,tol", [("f16", 2e-3), ("bf16", 2e-2)])
+def test_reduced_precision_storage(istore, tol):
+    """sqrt(I) stored as 16-bit with a per-frame scale: after 5 LSQML iterations
+    the result stays within the storage's own rounding of the FP64 oracle."""
+    c = scan(64, 1, grid=3, photons=1e6)
+    res32 = _compare(c, "lsqml", 5)
+    with recon(c, istore=istore) as r:
+        r.iterate("lsqml", 5)
+        Og, Pg = r.get_object(), r.get_probe()
+    Oc, Pc, _ = orc.reconstruct("lsqml", c["O0"], c["P0"], c["pos"], c["I"], 5)
+    m = illuminated(c["P"], c["pos"], c["shape"])
+    e = rel_l2(align_global(Og, Oc, m), Oc, m)
+    assert res32["eo"] < e < tol, (e, res32)
+
+
+def test_error_paths():
+    c = scan(32, 1, grid=2)
+    with api.Reconstruction(32, 1, len(c["pos"]), c["shape"]) as r:
+        with pytest.raises(api.PtychoError) as e:
+            r.iterate("dm", 1)
+        assert e.value.name == "STATE"
+        bad = c["pos"].copy()
+        bad[0, 1] = c["shape"][1] - 31
+        with pytest.raises(api.PtychoError) as e:
+            r.set_data(c["I"].astype(np.float32), bad)
+        assert e.value.name == "BOUNDS"
+        I = c["I"].astype(np.float32).copy()
+        I[1, 3, 3] = np.nan
+        with pytest.raises(api.PtychoError) as e:
+            r.set_data(I, c["pos"])
+        assert e.value.name == "NONFINITE"
+        # the context stays usable after errors
+        r.set_data(c["I"].astype(np.float32), c["pos"])
+        r.set_init(c["O0"], c["P0"])
+        r.iterate("lsqml", 1)
+        assert np.isfinite(r.fourier_error())
+
+
+def test_profile_and_launch_count():
+    c = scan(32, 1, grid=3)
+    with recon(c) as r:
+        n0 = r.launch_count
+        r.set_profiling(True)
+        r.iterate("lsqml", 2)
+        prof = r.get_profile()
+        assert r.launch_count > n0
+    assert prof["fourier_chi"]["launches"] == 2 and prof["fourier_chi"]["ms"] > 0
