@@ -1,0 +1,324 @@
+"""Throughput of the ptychographic reconstruction hot path on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): LSQML on a 256 x 256 detector, 10,000 scan positions
+(100 x 100 raster, step 24 px, +-2 px seeded jitter), 2640 x 2640 object,
+one probe mode, FP32 intensities with Poisson noise at 1e5 photons/frame.
+A step is one iteration over all positions (the whole hot path: Fourier
+step, object and probe overlap sums, LSQML step sizes, updates).  DM on the
+same scan and the 16-bit intensity stores are reported beside it.
+
+value   : patterns*iterations/s with all inputs resident in HBM;
+e2e     : the same metric for a whole job through the C ABI from pinned host
+          buffers (set_data + set_init + n iterations + get_object/get_probe);
+roofline: the dominant kernel's algorithmic HBM bytes per launch over its
+          CUDA-event duration, against the measured copy bandwidth;
+cpu_baseline: the FP64 oracle on a bounded sub-scan of the same workload.
+
+Under torchrun (N > 1) every rank reconstructs its own scan of the same shape
+(independent replicas, weak scaling; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "patterns·iter/s (DM/LSQML, 256² det, 10k pos) and time-to-ε vs plain FP32, 1 B300"
+UNIT = "patterns*iter/s"
+WORKLOAD = dict(M=256, K=1, grid=100, step=24, jitter=2, obj=2640, photons=1e5)
+
+
+def workload_desc(w=WORKLOAD):
+    return (f"LSQML, {w['M']}x{w['M']} detector, {w['grid'] ** 2} positions ({w['grid']}x{w['grid']} raster, "
+            f"step {w['step']} px, +-{w['jitter']} px jitter), {w['obj']}x{w['obj']} object, K={w['K']}, "
+            f"Poisson {w['photons']:.0e} photons/frame")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def make_scan(seed, w=WORKLOAD):
+    from paper_2202_03144_b300 import synth
+    M, K = w["M"], w["K"]
+    P = synth.make_probe(M, K, R=80.0, sigma=16.0, c=0.00125)
+    pos = synth.raster_positions(w["grid"], w["grid"], w["step"], w["jitter"], w["jitter"], seed=2000 + seed)
+    O = synth.make_object(w["obj"], w["obj"], seed=1000 + seed)
+    P0 = synth.make_probe(M, K, R=88.0, sigma=16.0, c=0.00125)
+    return P, O, pos, P0
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.p = None
+        if shutil.which("nvidia-smi"):
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(P, O, pos, P0, I_sample_fn, w=WORKLOAD, sub=24):
+    """FP64 oracle, one LSQML iteration on a sub x sub block of the raster."""
+    from oracle import ptycho_oracle as orc
+    g = w["grid"]
+    idx = np.array([r * g + c for r in range(sub) for c in range(sub)])
+    pos_s = pos[idx]
+    y0 = int(np.rint(pos_s[:, 0]).min())
+    x0 = int(np.rint(pos_s[:, 1]).min())
+    pos_s = pos_s - [y0, x0]
+    ny = int(np.rint(pos_s[:, 0]).max()) + w["M"]
+    nx = int(np.rint(pos_s[:, 1]).max()) + w["M"]
+    O_s = O[y0:y0 + ny, x0:x0 + nx]
+    I_s = I_sample_fn(P, O_s, pos_s)
+    O0 = np.ones((ny, nx), complex)
+    t = time.perf_counter()
+    orc.reconstruct("lsqml", O0, P0, pos_s, I_s, 1)
+    dt = time.perf_counter() - t
+    return {"value": len(idx) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 LSQML iteration of the FP64 numpy oracle on a {sub}x{sub}-position block "
+                      f"({len(idx)} positions, same M, probe and step) in {dt:.1f} s, single-threaded FFT"}
+
+
+def oracle_intensities(P, O, pos, photons, seed):
+    from oracle import ptycho_oracle as orc
+    from paper_2202_03144_b300 import synth
+    I = orc.far_field_intensity(O, P, orc.round_positions(pos))
+    I = I * photons / I.sum(axis=(1, 2)).mean()
+    return synth.poisson(I, seed)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, as it stands, on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    P, O, pos, P0 = make_scan(0)
+    sub = 12
+    times = []
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(P, O, pos, P0, lambda P_, O_, p_: oracle_intensities(P_, O_, p_, WORKLOAD["photons"], 5),
+                          sub=sub)
+        if s >= args.warmup:
+            times.append(cb)
+    vals = [c["value"] for c in times]
+    v = statistics.median(vals)
+    ms = sub * sub / v * 1e3
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(), "sample": f"{sub}x{sub}-position block per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": times[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-iters", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small", action="store_true", help="a 20x20-position scan (profiling runs)")
+    args = ap.parse_args()
+    if args.small:
+        WORKLOAD["grid"] = 20
+        WORKLOAD["obj"] = 736
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2202_03144_b300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = WORKLOAD
+    M, K, J = w["M"], w["K"], w["grid"] ** 2
+    P, O, pos, P0 = make_scan(rank)
+    stream = torch.cuda.Stream()
+    # --- synthetic data on the device: forward model of the truth + shot noise
+    with torch.cuda.stream(stream):
+        sim = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream)
+        sim.set_positions(pos)
+        sim.set_init(O, P)
+        I = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        sim.simulate(I)
+        stream.synchronize()
+        sim.close()
+        scale = w["photons"] / float(I.sum(dim=(1, 2)).mean())
+        gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
+        I = torch.poisson(I * scale, generator=gen)
+        P0s = P0 * np.sqrt(scale)
+    stream.synchronize()
+
+    def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False):
+        with torch.cuda.stream(stream):
+            r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore)
+            r.set_data(I, pos)
+            r.set_init(np.ones((w["obj"], w["obj"]), np.complex64), P0s)
+            r.iterate(alg, warm)
+            stream.synchronize()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            clk = Clocks(local) if not profile else None
+            n0 = r.launch_count
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if profile:
+                r.set_profiling(True)
+            e0.record(stream)
+            r.iterate(alg, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            launches = r.launch_count - n0
+            clocks = clk.stop() if clk else None
+            prof = r.get_profile() if profile else None
+            err = r.fourier_error()
+            r.close()
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t)
+        return dict(ms=ms, launches=launches, clocks=clocks, prof=prof, err=err)
+
+    main_run = timed("lsqml")
+    dm_run = timed("dm")
+    f16_run = timed("lsqml", istore="f16")
+    bf16_run = timed("lsqml", istore="bf16")
+    prof_run = timed("lsqml", steps=3, warm=1, profile=True)
+
+    def rate(run):
+        return J * world * args.steps / (run["ms"] / 1e3)
+
+    value = rate(main_run)
+    # --- roofline of the dominant kernel (live CUDA-event durations)
+    prof = prof_run["prof"]
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    hbm, peak_kind = peaks()
+    achieved = top[1]["bytes"] / (top[1]["ms"] / 1e3) / 1e9
+    total_ms = sum(v["ms"] for v in prof.values())
+    roof = {"bound": "hbm", "kernel": top[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": peak_kind,
+            "bytes_per_launch": top[1]["bytes"] / top[1]["launches"],
+            "ms_per_launch": top[1]["ms"] / top[1]["launches"], "traffic": None,
+            "share_of_step": top[1]["ms"] / total_ms,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                            "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] else None}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+    # --- end to end through the ABI from pinned host buffers
+    I_host = I.cpu().pin_memory()
+    O0 = np.ones((w["obj"], w["obj"]), np.complex64)
+    P0h = P0s.astype(np.complex64)
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream)
+        for s in range(2 + args.steps // 5 + 1):
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            r.set_data(I_host, pos)
+            r.set_init(O0, P0h)
+            r.iterate("lsqml", args.e2e_iters)
+            Oo = r.get_object()
+            Po = r.get_probe()
+            dt = time.perf_counter() - t0
+            if s >= 2:
+                e2e_times.append(dt)
+        r.close()
+    e2e_dt = statistics.median(e2e_times)
+    h2d = I_host.numel() * 4 + pos.size * 4 + O0.nbytes + P0h.nbytes
+    d2h = Oo.nbytes + Po.nbytes
+    e2e = {"value": J * world * args.e2e_iters / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h),
+           "step": f"one job: set_data + set_init from pinned host memory, {args.e2e_iters} LSQML iterations, "
+                   f"get_object + get_probe to host"}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cb = None
+    if not args.no_cpu:
+        cb = cpu_baseline(P, O, pos, P0, lambda P_, O_, p_: oracle_intensities(P_, O_, p_, w["photons"], 5))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(), "algorithm": "lsqml", "M": M, "K": K, "J": J,
+                   "object": [w["obj"], w["obj"]], "intensity_store": "f32",
+                   "l2": "inputs larger than L2: 5.2 GB of residuals and 2.6 GB of amplitudes per iteration",
+                   "replicas": world},
+        "by_variant": {
+            "lsqml_f32": {"value": value, "fourier_error": main_run["err"]},
+            "dm_f32": {"value": rate(dm_run), "fourier_error": dm_run["err"]},
+            "lsqml_f16": {"value": rate(f16_run), "fourier_error": f16_run["err"]},
+            "lsqml_bf16": {"value": rate(bf16_run), "fourier_error": bf16_run["err"]},
+        },
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": e2e,
+        "gpu_launches": main_run["launches"],
+        "clocks": main_run["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
