@@ -21,6 +21,7 @@
 #include "../../include/ptycho.h"
 #include "epie.cuh"
 #include "fourier.cuh"
+#include "fourier2.cuh"
 #include "overlap.cuh"
 
 using namespace ptycho;
@@ -31,16 +32,18 @@ using namespace ptycho;
 namespace {
 
 struct KernelSet {
-  int M, K, C, NT;
+  int M, K, C;
+  int NT2, NT_epie;
   size_t smem_fourier, smem_epie;
-  void (*fourier)(FourierArgs);
+  void (*fourier)(Fourier2Args);
   void (*epie)(EpieArgs);
 };
 
 template <int M, int K, int C>
 KernelSet make_set() {
   using F = FCfg<M, K, C>;
-  return KernelSet{M, K, C, F::NT, fourier_smem<F>(), epie_smem<F>(), k_fourier<M, K, C>, k_epie<M, K, C>};
+  using G = F2<M, K, C>;
+  return KernelSet{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>};
 }
 
 const std::vector<KernelSet>& kernel_sets() {
@@ -78,6 +81,18 @@ __global__ void k_twiddle(float2* tw, int M) {
   if (i < M) {
     double s, c;
     sincospi(2.0 * (double)i / (double)M, &s, &c);
+    tw[i] = make_float2((float)c, (float)-s);
+  }
+}
+
+// tw2[k1 * R2 + n2] = exp(-2 pi i n2 k1 / M), the inter-stage twiddles of
+// the two-stage (R1 x R2) transforms of k_fourier2.
+__global__ void k_twiddle2(float2* tw, int M, int R2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    const int k1 = i / R2, n2 = i % R2;
+    double s, c;
+    sincospi(2.0 * (double)(n2 * k1) / (double)M, &s, &c);
     tw[i] = make_float2((float)c, (float)-s);
   }
 }
@@ -179,6 +194,8 @@ struct ptycho_ctx {
   float2* dO = nullptr;      // LSQML object direction
   float2* dP = nullptr;      // LSQML probe direction
   float2* tw = nullptr;
+  float2* tw2 = nullptr;
+  int* err_flag = nullptr;   // set by a device wait that gave up
   int2* pos = nullptr;
   void* amp = nullptr;       // stored sqrt(I)
   float* amp_scale = nullptr;
@@ -321,7 +338,7 @@ size_t amp_bytes(const ptycho_ctx* ctx) { return ctx->p.istore == PTYCHO_I_F32 ?
 // ----------------------------------------------------------------- Fourier
 int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, int nj, const char* name) {
   const KernelSet* ks = ctx->ks;
-  FourierArgs a{};
+  Fourier2Args a{};
   a.O = ctx->O;
   a.nx = ctx->p.obj_nx;
   a.P = ctx->P;
@@ -332,7 +349,8 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   a.istore = ctx->p.istore;
   a.I_out = I_out;
   a.err_part = ctx->err_part;
-  a.tw = ctx->tw;
+  a.tw2 = ctx->tw2;
+  a.err_flag = ctx->err_flag;
   a.j0 = j0;
   a.mode = mode;
   const double MM = (double)ctx->p.M * ctx->p.M;
@@ -347,7 +365,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   return launch(ctx, name, bytes, [&] {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(ks->C * nj));
-    cfg.blockDim = dim3((unsigned)ks->NT);
+    cfg.blockDim = dim3((unsigned)ks->NT2);
     cfg.dynamicSmemBytes = ks->smem_fourier;
     cfg.stream = ctx->st;
     cudaLaunchAttribute attr[1];
@@ -361,6 +379,17 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
     }
     cudaLaunchKernelEx(&cfg, ks->fourier, a);
   });
+}
+
+int check_device_flag(ptycho_ctx* ctx) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (h) {
+    cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->st);
+    return fail(ctx, PTYCHO_ERR_TIMEOUT, "a bounded device wait gave up (bulk copy did not complete)");
+  }
+  return 0;
 }
 
 // ---------------------------------------------------------------- overlap
@@ -594,7 +623,7 @@ int run_epie(ptycho_ctx* ctx, int n) {
   int r = launch(ctx, "epie", bytes, [&] {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)ks->C);
-    cfg.blockDim = dim3((unsigned)ks->NT);
+    cfg.blockDim = dim3((unsigned)ks->NT_epie);
     cfg.dynamicSmemBytes = ks->smem_epie;
     cfg.stream = ctx->st;
     cudaLaunchAttribute attr[1];
@@ -727,6 +756,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (!r) r = dalloc(ctx, &ctx->O, obj);
   if (!r) r = dalloc(ctx, &ctx->P, (size_t)p->K * MM);
   if (!r) r = dalloc(ctx, &ctx->tw, (size_t)p->M);
+  if (!r) r = dalloc(ctx, &ctx->tw2, (size_t)p->M);
+  if (!r) r = dalloc(ctx, &ctx->err_flag, 1);
   if (!r) r = dalloc(ctx, &ctx->pos, (size_t)p->J);
   if (!r) r = dalloc(ctx, &ctx->denO, obj);
   if (!r) r = dalloc(ctx, &ctx->tile_max, (size_t)ctx->n_tiles);
@@ -760,6 +791,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_epie);
   if (e == cudaSuccess) {
     k_twiddle<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw, p->M);
+    k_twiddle2<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw2, p->M, p->M / radix1(p->M));
+    cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->st);
     k_fill_c<<<256, 256, 0, ctx->st>>>(ctx->O, obj, make_float2(1.f, 0.f));
     k_fill_c<<<256, 256, 0, ctx->st>>>(ctx->P, (size_t)p->K * MM, make_float2(0.f, 0.f));
     e = cudaGetLastError();
@@ -871,11 +904,13 @@ int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter) {
 
 int ptycho_get_object(ptycho_ctx* ctx, float* out, int on_device) {
   if (!ctx) return PTYCHO_ERR_ARG;
+  if (int r = check_device_flag(ctx)) return r;
   return copy_out(ctx, out, ctx->O, (size_t)ctx->p.obj_ny * ctx->p.obj_nx * 8, on_device);
 }
 
 int ptycho_get_probe(ptycho_ctx* ctx, float* out, int on_device) {
   if (!ctx) return PTYCHO_ERR_ARG;
+  if (int r = check_device_flag(ctx)) return r;
   return copy_out(ctx, out, ctx->P, (size_t)ctx->p.K * ctx->p.M * ctx->p.M * 8, on_device);
 }
 
@@ -896,6 +931,7 @@ int ptycho_fourier_error(ptycho_ctx* ctx, double* out) {
   double2 h;
   CK(cudaMemcpyAsync(&h, ctx->err_out, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (int r = check_device_flag(ctx)) return r;
   const double E = h.y > 0 ? h.x / h.y : 0.0;
   *out = E;
   if (!std::isfinite(E)) return fail(ctx, PTYCHO_ERR_DIVERGED, "Fourier error is not finite");
@@ -970,7 +1006,7 @@ void ptycho_destroy(ptycho_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
-  void* bufs[] = {ctx->O,        ctx->P,         ctx->X,        ctx->dO,       ctx->dP,        ctx->tw,
+  void* bufs[] = {ctx->tw2, ctx->err_flag, ctx->O,        ctx->P,         ctx->X,        ctx->dO,       ctx->dP,        ctx->tw,
                   ctx->pos,      ctx->amp,       ctx->amp_scale, ctx->denO,    ctx->tile_max,  ctx->denO_max,
                   ctx->tile_ptr, ctx->tile_list, ctx->ppart,    ctx->ppart_den, ctx->pnum,     ctx->pden,
                   ctx->pblk_max, ctx->alphaO,    ctx->alphaP,   ctx->err_part, ctx->err_out,   ctx->order,
