@@ -170,6 +170,43 @@ int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n
 /* FFT cluster size chosen for this context (1, 2, 4 or 8 CTAs). */
 int ptycho_cluster_size(const ptycho_ctx* ctx);
 
+/* Fourier error without any device allocation.
+ *
+ * The paper has no counterpart to this call.  It exists for callers that
+ * cannot call cudaMalloc: code embedded in a host application that owns all
+ * device memory through its own pool and forbids other allocations, or a
+ * live-feedback loop that cannot afford the implicit device-wide
+ * synchronisation an allocation may bring.  Such a caller keeps its data in
+ * its own device buffers and gets E without creating a context.
+ *
+ * E is computed exactly as ptycho_fourier_error computes it (same kernel,
+ * same cluster split, same fixed-order FP64 sums).  Inputs:
+ *   object      device, [obj_ny][obj_nx][2] float32 (re, im)
+ *   probe       device, [K][M][M][2] float32
+ *   positions   HOST, [J][2] float32 (y, x) top-left, rounded half-to-even;
+ *               every patch must lie inside the object (PTYCHO_ERR_BOUNDS)
+ *   amplitudes  device, [J][M][M] float32 = sqrt(I) in FFT order (zero
+ *               frequency at pixel (0, 0), i.e. NOT detector-centred);
+ *               a negative value marks a masked pixel
+ *   out         HOST, receives E
+ *   stream      cudaStream_t for the work (NULL = legacy default stream);
+ *               the call synchronises it before returning.
+ * Limits: J <= 16384 and M <= 256, beyond which the call fails with
+ * PTYCHO_ERR_ARG; (M, K) must be a compiled combination (else
+ * PTYCHO_ERR_UNSUPPORTED).  Errors are reported by ptycho_last_error(NULL).
+ *
+ * Scratch: one fixed array of about 2.2 MB in device memory, defined at file
+ * scope in the library, which every GPU that loads the library keeps until
+ * the process exits.  The first call on each device looks up that array's
+ * device address (once per device, with the device current); make that first
+ * call before any stream capture.  All calls share the array: two calls whose
+ * GPU work overlaps (different streams or threads) race on it and must be
+ * serialised by the caller.  The call itself allocates nothing (no
+ * cudaMalloc, no cudaFree, no allocating library routine). */
+int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int obj_nx, const float* probe, int M, int K,
+                                 const float* positions, int J, const float* amplitudes, double* out,
+                                 void* stream);
+
 /* Message of the last error on ctx (or of the last failed create if ctx is
  * NULL).  Valid until the next call on the same context. */
 const char* ptycho_last_error(const ptycho_ctx* ctx);

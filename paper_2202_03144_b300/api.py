@@ -77,6 +77,7 @@ def lib() -> C.CDLL:
             "ptycho_get_profile": (i, [vp, C.POINTER(KernelStat), i, C.POINTER(i)]),
             "ptycho_cluster_size": (i, [vp]),
             "ptycho_last_error": (C.c_char_p, [vp]),
+            "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
             "ptycho_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -204,6 +205,27 @@ def simulate(ctx, shape, out=None):
     res = np.empty(shape, dtype=np.float32)
     _check(ctx, lib().ptycho_simulate(ctx, res.ctypes.data, 0))
     return res
+
+
+def fourier_error_noalloc(object, probe, positions, amplitudes, stream=None) -> float:
+    """ptycho_fourier_error_noalloc: E from caller-owned device buffers with no
+    device allocation inside the call.  object [ny, nx] and probe [K, M, M] are
+    complex64 torch CUDA tensors, amplitudes a float32 torch CUDA tensor
+    [J, M, M] of sqrt(I) in FFT order (negative = masked), positions host
+    [J, 2] (y, x)."""
+    import torch
+    assert object.is_cuda and probe.is_cuda and amplitudes.is_cuda
+    o = torch.view_as_real(object.contiguous())
+    p = torch.view_as_real(probe.contiguous())
+    a = amplitudes.contiguous()
+    pos = np.ascontiguousarray(positions, dtype=np.float32)
+    K, M = int(probe.shape[0]), int(probe.shape[-1])
+    v = C.c_double()
+    rc = lib().ptycho_fourier_error_noalloc(o.data_ptr(), int(object.shape[0]), int(object.shape[1]), p.data_ptr(),
+                                            M, K, pos.ctypes.data, int(pos.shape[0]), a.data_ptr(), C.byref(v),
+                                            stream)
+    _check(None, rc)
+    return v.value
 
 
 def iteration(ctx) -> int:

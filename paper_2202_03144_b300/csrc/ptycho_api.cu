@@ -10,11 +10,13 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -697,6 +699,140 @@ int copy_out(ptycho_ctx* ctx, float* out, const void* src, size_t bytes, int on_
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Allocation-free Fourier error.  Its scratch is one file-scope device array
+// that every GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_J = 16384;   // positions per call
+constexpr int NOALLOC_MAX_M = 256;
+constexpr int NOALLOC_MAX_C = 8;
+// layout: [twiddles M_max float2][flag int, pad][err_out double2][positions int2 x J_max]
+//         [per-CTA error partials double2 x J_max * C_max]
+constexpr size_t NA_TW = 0;
+constexpr size_t NA_FLAG = NA_TW + NOALLOC_MAX_M * sizeof(float2);
+constexpr size_t NA_OUT = NA_FLAG + 256;
+constexpr size_t NA_POS = NA_OUT + 256;
+constexpr size_t NA_PART = NA_POS + (size_t)NOALLOC_MAX_J * sizeof(int2);
+constexpr size_t NA_BYTES = NA_PART + (size_t)NOALLOC_MAX_J * NOALLOC_MAX_C * sizeof(double2);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_dev[128] = {};   // device address of the scratch, per device
+
+// Once per device, with that device current: resolve the device address of
+// the scratch array (the host-side name is only a stand-in).
+int noalloc_setup(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 128) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "device index %d", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_dev[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(nullptr, PTYCHO_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+    g_noalloc_dev[dev] = (unsigned char*)ptr;
+  }
+  *out = g_noalloc_dev[dev];
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int obj_nx, const float* probe, int M,
+                                            int K, const float* positions, int J, const float* amplitudes,
+                                            double* out, void* stream) {
+  if (!object || !probe || !positions || !amplitudes || !out)
+    return fail(nullptr, PTYCHO_ERR_ARG, "NULL argument");
+  if (M < 2 || K < 1 || J < 1 || obj_ny < M || obj_nx < M)
+    return fail(nullptr, PTYCHO_ERR_ARG, "bad sizes M=%d K=%d J=%d object %dx%d", M, K, J, obj_ny, obj_nx);
+  if (J > NOALLOC_MAX_J || M > NOALLOC_MAX_M)
+    return fail(nullptr, PTYCHO_ERR_ARG,
+                "J=%d, M=%d exceed the fixed scratch of the allocation-free call (at most J=%d, M=%d)", J, M,
+                NOALLOC_MAX_J, NOALLOC_MAX_M);
+  const int C = default_cluster(M, K);
+  const KernelSet* ks = C ? find_set(M, K, C) : nullptr;
+  if (!ks) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "no kernel compiled for M=%d K=%d", M, K);
+  unsigned char* sc = nullptr;
+  if (int r = noalloc_setup(&sc)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  int2* pos = (int2*)(sc + NA_POS);
+  // positions: round half-to-even, check bounds, copy through a small stack
+  // buffer (a pageable-source copy returns once the source has been staged)
+  int2 chunk[512];
+  for (int j0 = 0; j0 < J; j0 += 512) {
+    const int n = std::min(512, J - j0);
+    for (int i = 0; i < n; ++i) {
+      const float fy = positions[2 * (j0 + i)], fx = positions[2 * (j0 + i) + 1];
+      if (!std::isfinite(fy) || !std::isfinite(fx))
+        return fail(nullptr, PTYCHO_ERR_NONFINITE, "position %d is not finite", j0 + i);
+      const double y = std::nearbyint((double)fy), x = std::nearbyint((double)fx);
+      if (y < 0 || x < 0 || y + M > obj_ny || x + M > obj_nx)
+        return fail(nullptr, PTYCHO_ERR_BOUNDS, "patch %d at (%g, %g) falls outside the %dx%d object", j0 + i, y, x,
+                    obj_ny, obj_nx);
+      chunk[i] = make_int2((int)y, (int)x);
+    }
+    cudaError_t e = cudaMemcpyAsync(pos + j0, chunk, n * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "position upload: %s", cudaGetErrorString(e));
+  }
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess && ks->smem_fourier > (size_t)optin)
+    return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "Fourier kernel needs more shared memory than the device offers");
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + NA_FLAG, 0, sizeof(int), st);  // the only state that must start at 0
+  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "setup: %s", cudaGetErrorString(e));
+  k_twiddle2<<<(M + 255) / 256, 256, 0, st>>>((float2*)(sc + NA_TW), M, M / radix1(M));
+  Fourier2Args a{};
+  a.O = (const float2*)object;
+  a.nx = obj_nx;
+  a.P = (const float2*)probe;
+  a.pos = pos;
+  a.amp = amplitudes;
+  a.istore = PTYCHO_I_F32;
+  a.err_part = (double2*)(sc + NA_PART);
+  a.tw2 = (const float2*)(sc + NA_TW);
+  a.err_flag = (int*)(sc + NA_FLAG);
+  a.mode = FM_ERR;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(ks->C * J));
+  cfg.blockDim = dim3((unsigned)ks->NT2);
+  cfg.dynamicSmemBytes = ks->smem_fourier;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (ks->C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ks->C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, ks->fourier, a);
+  k_err_final<<<1, 1024, 0, st>>>((const double2*)(sc + NA_PART), J * ks->C, (double2*)(sc + NA_OUT));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+  struct {
+    double2 v;
+    int flag;
+  } h{};
+  e = cudaMemcpyAsync(&h.v, sc + NA_OUT, sizeof(double2), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h.flag, sc + NA_FLAG, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "fourier_error_noalloc: %s", cudaGetErrorString(e));
+  if (h.flag) return fail(nullptr, PTYCHO_ERR_TIMEOUT, "a bounded device wait gave up (bulk copy did not complete)");
+  const double E = h.v.y > 0 ? h.v.x / h.v.y : 0.0;
+  *out = E;
+  if (!std::isfinite(E)) return fail(nullptr, PTYCHO_ERR_DIVERGED, "Fourier error is not finite");
+  return PTYCHO_OK;
+}
 
 // ---------------------------------------------------------------------------
 // ABI
