@@ -168,6 +168,7 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a 20x20-position scan (profiling runs)")
+    ap.add_argument("--cluster", type=int, default=0, help="FFT cluster size (0 = library default)")
     args = ap.parse_args()
     if args.small:
         WORKLOAD["grid"] = 20
@@ -208,7 +209,8 @@ def main():
 
     def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False):
         with torch.cuda.stream(stream):
-            r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore)
+            r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore,
+                                   cluster=args.cluster)
             r.set_data(I, pos)
             r.set_init(np.ones((w["obj"], w["obj"]), np.complex64), P0s)
             r.iterate(alg, warm)

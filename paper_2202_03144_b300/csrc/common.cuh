@@ -75,29 +75,32 @@ __device__ __forceinline__ void dft8(float2* a) {
   }
 }
 
+// 16-point DFT as 4 x 4 (n = 4 n1 + n2, k = k1 + 4 k2), in place with only
+// the temporaries of one radix-4 butterfly live at a time.
 template <bool INV>
 __device__ __forceinline__ void dft16(float2* a) {
-  float2 e[8], o[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    e[k] = a[2 * k];
-    o[k] = a[2 * k + 1];
-  }
-  dft8<INV>(e);
-  dft8<INV>(o);
-  // W16^k = exp(-/+ 2 pi i k / 16), k = 1..7
-  o[1] = rot<INV>(o[1], PT_C8, PT_S8);
-  o[2] = rot<INV>(o[2], PT_R2, PT_R2);
-  o[3] = rot<INV>(o[3], PT_S8, PT_C8);
-  o[4] = mul_mi<INV>(o[4]);
-  o[5] = rot<INV>(o[5], -PT_S8, PT_C8);
-  o[6] = rot<INV>(o[6], -PT_R2, PT_R2);
-  o[7] = rot<INV>(o[7], -PT_C8, PT_S8);
+  for (int n2 = 0; n2 < 4; ++n2) dft4s<INV, 4>(a + n2);  // a[n2 + 4 k1] = Y_n2[k1]
+  // twiddles W16^(n2 k1)
+  a[1 + 4 * 1] = rot<INV>(a[1 + 4 * 1], PT_C8, PT_S8);
+  a[1 + 4 * 2] = rot<INV>(a[1 + 4 * 2], PT_R2, PT_R2);
+  a[1 + 4 * 3] = rot<INV>(a[1 + 4 * 3], PT_S8, PT_C8);
+  a[2 + 4 * 1] = rot<INV>(a[2 + 4 * 1], PT_R2, PT_R2);
+  a[2 + 4 * 2] = mul_mi<INV>(a[2 + 4 * 2]);
+  a[2 + 4 * 3] = rot<INV>(a[2 + 4 * 3], -PT_R2, PT_R2);
+  a[3 + 4 * 1] = rot<INV>(a[3 + 4 * 1], PT_S8, PT_C8);
+  a[3 + 4 * 2] = rot<INV>(a[3 + 4 * 2], -PT_R2, PT_R2);
+  a[3 + 4 * 3] = rot<INV>(a[3 + 4 * 3], -PT_C8, -PT_S8);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    a[k] = cadd(e[k], o[k]);
-    a[k + 8] = csub(e[k], o[k]);
-  }
+  for (int k1 = 0; k1 < 4; ++k1) dft4s<INV, 1>(a + 4 * k1);  // a[4 k1 + k2] = X[k1 + 4 k2]
+  // natural order: a 4 x 4 transpose of the register array (renaming only)
+  float2 t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = a[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = t[i];
 }
 
 template <int R, bool INV>

@@ -66,7 +66,7 @@ struct F2 {
 // reduction scratch, mbarrier
 template <class F>
 __host__ __device__ constexpr size_t fourier2_smem() {
-  return (size_t)F::SBUF * 8 + (size_t)F::M * 8 + (size_t)F::H * F::M * 4 + F::NRED * 8 + 16;
+  return (size_t)F::SBUF * 8 + (size_t)F::M * 16 + (size_t)F::H * F::M * 4 + F::NRED * 8 + 16;
 }
 
 template <class F>
@@ -87,6 +87,16 @@ __device__ __forceinline__ void cluster_sync_rw() {
 // Write-after-read: every CTA has consumed (into registers) what it read.
 __device__ __forceinline__ void cluster_sync_war() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
+// Shared::cluster address of the same offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_f2(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
 // --- bulk async copy (TMA engine) of the amplitude tile -------------------
@@ -142,13 +152,14 @@ __device__ __forceinline__ float amp_at(const Fourier2Args& a, const void* amp_s
 }
 
 template <int M, int K, int C>
-__global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 : 1)) k_fourier2(Fourier2Args a) {
+__global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 256 ? 4 : (F2<M, K, C>::NT <= 512 ? 2 : 1))) k_fourier2(Fourier2Args a) {
   using F = F2<M, K, C>;
   constexpr int R1 = F::R1, R2 = F::R2, W = F::W, H = F::H, NT = F::NT, Q = F::Q;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* buf = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = buf + F::SBUF;
-  unsigned char* amp_s = reinterpret_cast<unsigned char*>(tw + M);
+  float2* tw = buf + F::SBUF;   // tw[k1 * R2 + n2] = W_M^(n2 k1)
+  float2* twT = tw + M;          // twT[n2 * R1 + k1], the same values transposed
+  unsigned char* amp_s = reinterpret_cast<unsigned char*>(twT + M);
   double* red = reinterpret_cast<double*>(amp_s + (size_t)H * M * 4);
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + F::NRED);
 
@@ -168,21 +179,35 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 :
       bulk_load(amp_s, src, (uint32_t)(H * M * esz), bar);
     }
   }
-  for (int i = tid; i < M; i += NT) tw[i] = a.tw2[i];
+  for (int i = tid; i < M; i += NT) {
+    const float2 t = a.tw2[i];
+    tw[i] = t;
+    twT[(i % R2) * R1 + i / R2] = t;
+  }
 
   float2 v[R1];
   // ---- prologue + column stage 1: thread = (k, colL, n2), rows n1*R2 + n2
   {
     const int colL = tid % W, n2 = (tid / W) % R2, k = tid / (W * R2);
     const int col = c * W + colL;
+    // probe values first, then the object in groups of four: bounds the number
+    // of loads in flight per thread (and so the registers they occupy)
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) {
-      const int row = n1 * R2 + n2;
-      const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-      const float2 pr = __ldg(a.P + ((size_t)k * M + row) * M + col);
-      float2 z = cmul(pr, o);
-      if (mode == FM_DM) z = csub(cscale(z, 2.f), a.X[(((size_t)j * K + k) * M + row) * M + col]);
-      v[n1] = z;
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(a.P + ((size_t)k * M + n1 * R2 + n2) * M + col);
+    const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
+#pragma unroll
+    for (int g0 = 0; g0 < R1; g0 += 4) {
+      float2 o[4];
+#pragma unroll
+      for (int i = 0; i < 4 && g0 + i < R1; ++i) o[i] = __ldg(orow + (size_t)(g0 + i) * R2 * a.nx);
+#pragma unroll
+      for (int i = 0; i < 4 && g0 + i < R1; ++i) v[g0 + i] = cmul(v[g0 + i], o[i]);
+      asm volatile("" ::: "memory");
+    }
+    if (mode == FM_DM) {
+      const float2* xrow = a.X + (((size_t)j * K + k) * M + n2) * M + col;
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[n1] = csub(cscale(v[n1], 2.f), xrow[(size_t)n1 * R2 * M]);
     }
     __syncthreads();  // twiddle table and mbarrier initialisation
     dft<R1, false>(v);
@@ -214,9 +239,11 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 :
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) {
         const int f = k1 + R1 * k2;
-        float2* dst = buf;
-        if constexpr (C > 1) dst = cooperative_groups::this_cluster().map_shared_rank(buf, f / H);
-        dst[rb<F>(k, f % H, col)] = w[q][k2];
+        if constexpr (C > 1) {
+          st_cluster_f2(mapa_u32(smem_u32(buf + rb<F>(k, f % H, col)), (uint32_t)(f / H)), w[q][k2]);
+        } else {
+          buf[rb<F>(k, f % H, col)] = w[q][k2];
+        }
       }
     }
     if constexpr (C > 1) cluster_sync_rw();
@@ -270,11 +297,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 :
                 ed += (double)am * (double)am;
               }
             } else {
-              float fct = 0.f;
-              if (am >= 0.f) {
-                const float A = sqrtf(A2);
-                fct = ((A > 1e-20f) ? am / A : 0.f) - 1.f;
-              }
+              // factor sqrt(I)/A - 1 (A^2 <= 1e-38: projected value 0); masked: 0
+              const float fct = (am >= 0.f) ? ((A2 > 1e-38f) ? am * rsqrtf(A2) : 0.f) - 1.f : 0.f;
               w[q][k2] = cscale(w[q][k2], fct * inv);
             }
           }
@@ -315,11 +339,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 :
           }
           continue;
         }
-        float fct = 0.f;
-        if (am >= 0.f) {
-          const float A = sqrtf(A2);
-          fct = ((A > 1e-20f) ? am / A : 0.f) - 1.f;
-        }
+        const float fct = (am >= 0.f) ? ((A2 > 1e-38f) ? am * rsqrtf(A2) : 0.f) - 1.f : 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) buf[rb<F>(k, rowL, pp)] = cscale(z[k], fct * inv);
       }
@@ -340,14 +360,15 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 :
       if (tid == 0) a.err_part[(size_t)j * C + c] = make_double2(sn, sd);
     }
     if (mode == FM_ERR || mode == FM_SIM) return;  // no DSMEM access after the transpose
-    // inverse row stage A: radix R2 over k2', conjugate twiddle
+    // inverse row stage A: radix R2 over k2', conjugate twiddle (threads of a
+    // warp differ in k1, so read the transposed table: no bank conflicts)
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int s = tid + q * NT;
       const int k1 = s % R1;
       dft<R2, true>(w[q]);
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) w[q][n2] = cmul(w[q][n2], cconj(tw[k1 * R2 + n2]));
+      for (int n2 = 1; n2 < R2; ++n2) w[q][n2] = cmul(w[q][n2], cconj(twT[n2 * R1 + k1]));
     }
     __syncthreads();
 #pragma unroll
@@ -372,9 +393,11 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 512 ? 2 :
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       const int x = n1 * R2 + n2;
-      float2* dst = buf;
-      if constexpr (C > 1) dst = cooperative_groups::this_cluster().map_shared_rank(buf, x / W);
-      dst[cb<F>(k, f, x % W)] = v[n1];
+      if constexpr (C > 1) {
+        st_cluster_f2(mapa_u32(smem_u32(buf + cb<F>(k, f, x % W)), (uint32_t)(x / W)), v[n1]);
+      } else {
+        buf[cb<F>(k, f, x % W)] = v[n1];
+      }
     }
     if constexpr (C > 1) cluster_sync_rw();
     else __syncthreads();

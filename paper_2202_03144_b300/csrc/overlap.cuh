@@ -21,6 +21,8 @@ namespace ptycho {
 constexpr int TILE_Y = 32, TILE_X = 64, OBJ_NT = 256;
 constexpr int OBJ_ROWS = TILE_Y / (OBJ_NT / TILE_X);  // rows per thread (8)
 constexpr int PROBE_NT = 256;
+constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
+constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
 
 enum ObjMode : int { OBJ_DEN = 0, OBJ_DM = 1, OBJ_DIR = 2, OBJ_UPD = 3 };
 enum ProbeMode : int { PR_DM = 0, PR_DIR = 1, PR_UPD = 2 };
@@ -59,29 +61,67 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
     den[i] = 0.f;
   }
   const int s0 = a.tile_ptr[tile], s1 = a.tile_ptr[tile + 1];
-  for (int s = s0; s < s1; ++s) {
-    const int j = a.tile_list[s];
-    const int2 p = a.pos[j];
-    const int ux = x - p.y;
-    if (ux < 0 || ux >= M) continue;
-    const float w = (MODE == OBJ_DIR || MODE == OBJ_DM || a.weights == nullptr) ? 1.f : a.weights[j];
+  // the tile's positions (index, corner, weight) staged in shared memory in
+  // chunks, so the inner loop has no chain of dependent global loads
+  __shared__ int sj[OBJ_CHUNK];
+  __shared__ int2 sp[OBJ_CHUNK];
+  __shared__ float sw[OBJ_CHUNK];
+  const bool weighted = !(MODE == OBJ_DIR || MODE == OBJ_DM || a.weights == nullptr);
+  for (int c0 = s0; c0 < s1; c0 += OBJ_CHUNK) {
+    const int nc = min(OBJ_CHUNK, s1 - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += OBJ_NT) {
+      const int j = a.tile_list[c0 + i];
+      sj[i] = j;
+      sp[i] = a.pos[j];
+      sw[i] = weighted ? a.weights[j] : 1.f;
+    }
+    __syncthreads();
+    // two positions per step so that twice the loads are in flight
+    for (int s = 0; s < nc; s += 2) {
+      int jj[2], ux[2], uy0[2];
+      float w[2];
+      bool on[2];
 #pragma unroll
-    for (int i = 0; i < OBJ_ROWS; ++i) {
-      const int uy = ty0 + tyb + (OBJ_NT / TILE_X) * i - p.x;
-      if (uy < 0 || uy >= M) continue;
-      const size_t u = (size_t)uy * M + ux;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float2 pr = __ldg(a.P + k * MM + u);
-        if (MODE == OBJ_DEN) {
-          den[i] += cabs2(pr);
-        } else {
-          const float2 xv = __ldg(a.X + ((size_t)j * K + k) * MM + u);
-          float2 t = cconjmul(pr, xv);
-          num[i].x = fmaf(w, t.x, num[i].x);
-          num[i].y = fmaf(w, t.y, num[i].y);
-        }
+      for (int h = 0; h < 2; ++h) {
+        const int i = min(s + h, nc - 1);
+        jj[h] = sj[i];
+        const int2 p = sp[i];
+        ux[h] = x - p.y;
+        uy0[h] = ty0 + tyb - p.x;
+        on[h] = (s + h < nc) && ux[h] >= 0 && ux[h] < M;
+        w[h] = sw[i];
       }
+      float2 xv[2][OBJ_ROWS][K];
+      float2 pv[2][OBJ_ROWS][K];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 0; i < OBJ_ROWS; ++i) {
+          const int uy = uy0[h] + (OBJ_NT / TILE_X) * i;
+          const bool in = on[h] && uy >= 0 && uy < M;
+          const size_t u = in ? (size_t)uy * M + ux[h] : 0;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            pv[h][i][k] = in ? __ldg(a.P + k * MM + u) : make_float2(0.f, 0.f);
+            if (MODE != OBJ_DEN)
+              xv[h][i][k] = in ? __ldcs(a.X + ((size_t)jj[h] * K + k) * MM + u) : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 0; i < OBJ_ROWS; ++i)
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            if (MODE == OBJ_DEN) {
+              den[i] += cabs2(pv[h][i][k]);
+            } else {
+              const float2 t = cconjmul(pv[h][i][k], xv[h][i][k]);
+              num[i].x = fmaf(w[h], t.x, num[i].x);
+              num[i].y = fmaf(w[h], t.y, num[i].y);
+            }
+          }
     }
   }
   if (MODE == OBJ_DEN) {
@@ -149,7 +189,6 @@ template <int K>
 __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   const int MM = a.M * a.M;
   const int u = blockIdx.x * PROBE_NT + threadIdx.x;
-  if (u >= MM) return;
   const int uy = u / a.M, ux = u % a.M;
   const int g = blockIdx.y;
   const int jb = (int)(((long long)a.J * g) / a.G), je = (int)(((long long)a.J * (g + 1)) / a.G);
@@ -158,19 +197,46 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   for (int k = 0; k < K; ++k) num[k] = make_float2(0.f, 0.f);
   float den = 0.f;
   const bool want_den = a.part_den != nullptr;
-  for (int j = jb; j < je; ++j) {
-    const int2 p = a.pos[j];
-    const float2 o = __ldg(a.O + (size_t)(p.x + uy) * a.nx + p.y + ux);
-    if (want_den) den += cabs2(o);
-    const float w = a.weights ? a.weights[j] : 1.f;
+  constexpr int UJ = 4;  // positions per step: UJ*(K+1) independent loads in flight
+  __shared__ int2 sp[PROBE_CHUNK];
+  __shared__ float sw[PROBE_CHUNK];
+  for (int c0 = jb; c0 < je; c0 += PROBE_CHUNK) {
+    const int nc = min(PROBE_CHUNK, je - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += PROBE_NT) {
+      sp[i] = a.pos[c0 + i];
+      sw[i] = a.weights ? a.weights[c0 + i] : 1.f;
+    }
+    __syncthreads();
+    if (u < MM) {
+      for (int s = 0; s < nc; s += UJ) {
+        float2 o[UJ], xv[UJ][K];
+        float w[UJ];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float2 xv = __ldg(a.X + ((size_t)j * K + k) * MM + u);
-      const float2 t = cconjmul(o, xv);
-      num[k].x = fmaf(w, t.x, num[k].x);
-      num[k].y = fmaf(w, t.y, num[k].y);
+        for (int h = 0; h < UJ; ++h) {
+          const bool in = s + h < nc;
+          const int i = in ? s + h : 0;
+          const int2 p = sp[i];
+          o[h] = in ? __ldg(a.O + (size_t)(p.x + uy) * a.nx + p.y + ux) : make_float2(0.f, 0.f);
+          w[h] = in ? sw[i] : 0.f;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            xv[h][k] = in ? __ldcs(a.X + ((size_t)(c0 + i) * K + k) * MM + u) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int h = 0; h < UJ; ++h) {
+          if (want_den) den += cabs2(o[h]);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const float2 t = cconjmul(o[h], xv[h][k]);
+            num[k].x = fmaf(w[h], t.x, num[k].x);
+            num[k].y = fmaf(w[h], t.y, num[k].y);
+          }
+        }
+      }
     }
   }
+  if (u >= MM) return;
 #pragma unroll
   for (int k = 0; k < K; ++k) a.part_num[((size_t)g * K + k) * MM + u] = num[k];
   if (want_den) a.part_den[(size_t)g * MM + u] = den;
@@ -266,22 +332,51 @@ __global__ void __launch_bounds__(STEP_NT) k_lsqml_steps(StepArgs a) {
   const int MM = a.M * a.M;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
   const bool upd = a.dP != nullptr;
-  for (int u = threadIdx.x; u < MM; u += STEP_NT) {
-    const int uy = u / a.M, ux = u % a.M;
-    const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
-    const float2 o = __ldg(a.O + r);
-    const float2 dov = __ldg(a.dO + r);
+  // two adjacent pixels per thread per step (16-byte loads), two steps unrolled
+  for (int u0 = 2 * threadIdx.x; u0 < MM; u0 += 4 * STEP_NT) {
+    float4 o[2], dov[2], xv[2][K], pr[2][K], dp[2][K];
+    bool in[2];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float2 av = cmul(__ldg(a.P + (size_t)k * MM + u), dov);
-      const float2 xv = __ldg(a.X + ((size_t)j * K + k) * MM + u);
-      s0 += cabs2(av);
-      s3 += fmaf(av.x, xv.x, av.y * xv.y);
-      if (upd) {
-        const float2 bv = cmul(o, __ldg(a.dP + (size_t)k * MM + u));
-        s1 += fmaf(av.x, bv.x, av.y * bv.y);
-        s2 += cabs2(bv);
-        s4 += fmaf(bv.x, xv.x, bv.y * xv.y);
+    for (int h = 0; h < 2; ++h) {
+      const int u = u0 + h * 2 * STEP_NT;
+      in[h] = u < MM;
+      const int uu = in[h] ? u : 0;
+      const int uy = uu / a.M, ux = uu % a.M;
+      const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
+      // O and dO rows are 8-byte aligned only: two 8-byte loads each
+      const float2 o0 = __ldg(a.O + r), o1 = __ldg(a.O + r + 1);
+      const float2 d0 = __ldg(a.dO + r), d1 = __ldg(a.dO + r + 1);
+      o[h] = make_float4(o0.x, o0.y, o1.x, o1.y);
+      dov[h] = make_float4(d0.x, d0.y, d1.x, d1.y);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        pr[h][k] = __ldg(reinterpret_cast<const float4*>(a.P + (size_t)k * MM + uu));
+        xv[h][k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)j * K + k) * MM + uu));
+        dp[h][k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + (size_t)k * MM + uu)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!in[h]) continue;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float2 oo = e ? make_float2(o[h].z, o[h].w) : make_float2(o[h].x, o[h].y);
+        const float2 dd = e ? make_float2(dov[h].z, dov[h].w) : make_float2(dov[h].x, dov[h].y);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float2 pk = e ? make_float2(pr[h][k].z, pr[h][k].w) : make_float2(pr[h][k].x, pr[h][k].y);
+          const float2 xk = e ? make_float2(xv[h][k].z, xv[h][k].w) : make_float2(xv[h][k].x, xv[h][k].y);
+          const float2 av = cmul(pk, dd);
+          s0 += cabs2(av);
+          s3 += fmaf(av.x, xk.x, av.y * xk.y);
+          if (upd) {
+            const float2 dk = e ? make_float2(dp[h][k].z, dp[h][k].w) : make_float2(dp[h][k].x, dp[h][k].y);
+            const float2 bv = cmul(oo, dk);
+            s1 += fmaf(av.x, bv.x, av.y * bv.y);
+            s2 += cabs2(bv);
+            s4 += fmaf(bv.x, xk.x, bv.y * xk.y);
+          }
+        }
       }
     }
   }

@@ -55,7 +55,7 @@ const std::vector<KernelSet>& kernel_sets() {
       make_set<32, 2, 2>(),  make_set<32, 3, 1>(),  make_set<32, 3, 4>(),  make_set<64, 1, 1>(),
       make_set<64, 1, 2>(),  make_set<64, 1, 4>(),  make_set<64, 3, 2>(),  make_set<64, 3, 4>(),
       make_set<128, 1, 2>(), make_set<128, 1, 4>(), make_set<128, 1, 8>(), make_set<128, 3, 4>(),
-      make_set<128, 3, 8>(), make_set<256, 1, 4>(), make_set<256, 1, 8>(),
+      make_set<128, 3, 8>(), make_set<256, 1, 4>(), make_set<256, 1, 8>(), make_set<256, 1, 16>(),
   };
   return sets;
 }
@@ -881,7 +881,7 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   {
     const int MM = p->M * p->M;
     const int nblk = (MM + PROBE_NT - 1) / PROBE_NT;
-    int G = (4 * 148 + nblk - 1) / nblk;
+    int G = (16 * 148 + nblk - 1) / nblk;  // ~16 CTAs per SM of position groups
     if (G > p->J) G = p->J;
     if (G < 1) G = 1;
     ctx->G = G;
@@ -922,6 +922,10 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
+  if (e == cudaSuccess && ks->C > 8) {
+    e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
   ctx->epie_ok = e == cudaSuccess && ks->smem_epie <= (size_t)optin;
   if (ctx->epie_ok)
     e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_epie);
