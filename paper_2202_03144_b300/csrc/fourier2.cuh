@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 256 ? 4 :
     dft<R1, false>(v);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[k1 * R2 + n2]);
-    __syncthreads();
+    // each thread writes back exactly the slots {i*R2 + n2} it read: no
+    // write-after-read barrier needed
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) buf[rb<F>(k, rowL, k1 * R2 + n2)] = v[k1];
   }
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 256 ? 4 :
 #pragma unroll
       for (int n2 = 1; n2 < R2; ++n2) w[q][n2] = cmul(w[q][n2], cconj(twT[n2 * R1 + k1]));
     }
-    __syncthreads();
+    // written back to the slots {k1*R2 + i} this thread read in row stage 2
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int s = tid + q * NT;
@@ -415,13 +416,14 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 256 ? 4 :
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) w[q][n2] = cmul(w[q][n2], cconj(tw[k1 * R2 + n2]));
     }
-    __syncthreads();
+    // value (k1, n2) goes to row k1 + R1*n2: the same rows this task read, so
+    // no write-after-read barrier is needed
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int s = tid + q * NT;
       const int colL = s % W, k1 = (s / W) % R1, k = s / (W * R1);
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) buf[cb<F>(k, k1 * R2 + n2, colL)] = w[q][n2];
+      for (int n2 = 0; n2 < R2; ++n2) buf[cb<F>(k, k1 + R1 * n2, colL)] = w[q][n2];
     }
   }
   __syncthreads();
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 256 ? 4 :
     const int colL = tid % W, n2 = (tid / W) % R2, k = tid / (W * R2);
     const int col = c * W + colL;
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) v[k1] = buf[cb<F>(k, k1 * R2 + n2, colL)];
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = buf[cb<F>(k, k1 + R1 * n2, colL)];
     dft<R1, true>(v);
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {

@@ -24,7 +24,12 @@ constexpr int PROBE_NT = 256;
 constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
 constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
 
-enum ObjMode : int { OBJ_DEN = 0, OBJ_DM = 1, OBJ_DIR = 2, OBJ_UPD = 3 };
+// OBJ_NUMDEN: numerator (unweighted, to dO) and den_O (to den) in one pass,
+//             with the per-tile maximum of den_O; k_obj_norm then applies the
+//             DM update or forms the LSQML direction.
+// OBJ_UPD:    LSQML update O += beta sum_j alpha_j S_j[...] / (den_O + delta).
+enum ObjMode : int { OBJ_NUMDEN = 0, OBJ_UPD = 3 };
+enum NormMode : int { NORM_DM = 0, NORM_DIR = 1 };
 enum ProbeMode : int { PR_DM = 0, PR_DIR = 1, PR_UPD = 2 };
 
 struct ObjArgs {
@@ -37,8 +42,8 @@ struct ObjArgs {
   const int* tile_ptr;    // [n_tiles + 1]
   const int* tile_list;   // positions overlapping each tile, ascending
   const float* weights;   // per-position weight (alpha_O) or NULL
-  float* den;             // den_O [ny][nx] (written by OBJ_DEN, read otherwise)
-  float* tile_max;        // OBJ_DEN: max of den per tile
+  float* den;             // den_O [ny][nx] (written by OBJ_NUMDEN, read otherwise)
+  float* tile_max;        // OBJ_NUMDEN: max of den per tile
   const float* den_max;   // max over all tiles (one float)
   float reg, beta;
   int M;
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
   __shared__ int sj[OBJ_CHUNK];
   __shared__ int2 sp[OBJ_CHUNK];
   __shared__ float sw[OBJ_CHUNK];
-  const bool weighted = !(MODE == OBJ_DIR || MODE == OBJ_DM || a.weights == nullptr);
+  const bool weighted = MODE == OBJ_UPD && a.weights != nullptr;
   for (int c0 = s0; c0 < s1; c0 += OBJ_CHUNK) {
     const int nc = min(OBJ_CHUNK, s1 - c0);
     __syncthreads();
@@ -104,8 +109,7 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             pv[h][i][k] = in ? __ldg(a.P + k * MM + u) : make_float2(0.f, 0.f);
-            if (MODE != OBJ_DEN)
-              xv[h][i][k] = in ? __ldcs(a.X + ((size_t)jj[h] * K + k) * MM + u) : make_float2(0.f, 0.f);
+            xv[h][i][k] = in ? __ldcs(a.X + ((size_t)jj[h] * K + k) * MM + u) : make_float2(0.f, 0.f);
           }
         }
 #pragma unroll
@@ -114,23 +118,22 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
         for (int i = 0; i < OBJ_ROWS; ++i)
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            if (MODE == OBJ_DEN) {
-              den[i] += cabs2(pv[h][i][k]);
-            } else {
-              const float2 t = cconjmul(pv[h][i][k], xv[h][i][k]);
-              num[i].x = fmaf(w[h], t.x, num[i].x);
-              num[i].y = fmaf(w[h], t.y, num[i].y);
-            }
+            if (MODE == OBJ_NUMDEN) den[i] += cabs2(pv[h][i][k]);
+            const float2 t = cconjmul(pv[h][i][k], xv[h][i][k]);
+            num[i].x = fmaf(w[h], t.x, num[i].x);
+            num[i].y = fmaf(w[h], t.y, num[i].y);
           }
     }
   }
-  if (MODE == OBJ_DEN) {
+  if (MODE == OBJ_NUMDEN) {
     float m = 0.f;
 #pragma unroll
     for (int i = 0; i < OBJ_ROWS; ++i) {
       const int y = ty0 + tyb + (OBJ_NT / TILE_X) * i;
       if (y < a.ny && x < a.nx) {
-        a.den[(size_t)y * a.nx + x] = den[i];
+        const size_t r = (size_t)y * a.nx + x;
+        a.den[r] = den[i];
+        a.dO[r] = num[i];
         m = fmaxf(m, den[i]);
       }
     }
@@ -146,15 +149,29 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
     const size_t r = (size_t)y * a.nx + x;
     const float d = a.den[r] + delta;
     const float inv = d > 0.f ? 1.f / d : 0.f;
-    if (MODE == OBJ_DM) {
-      const float2 o = a.O[r];
-      a.O[r] = make_float2(fmaf(delta, o.x, num[i].x) * inv, fmaf(delta, o.y, num[i].y) * inv);
-    } else if (MODE == OBJ_DIR) {
-      a.dO[r] = cscale(num[i], inv);
+    const float2 o = a.O[r];
+    const float sc = a.beta * inv;
+    a.O[r] = make_float2(fmaf(sc, num[i].x, o.x), fmaf(sc, num[i].y, o.y));
+  }
+}
+
+// Object-sized epilogue of OBJ_NUMDEN, with delta = reg * max(den_O):
+//   NORM_DM:  O  <- (num + delta O) / (den + delta)
+//   NORM_DIR: dO <- num / (den + delta)          (num is held in dO)
+template <int MODE>
+__global__ void __launch_bounds__(256) k_obj_norm(float2* __restrict__ O, float2* __restrict__ dO,
+                                                  const float* __restrict__ den, const float* __restrict__ den_max,
+                                                  float reg, size_t n) {
+  const float delta = reg * den_max[0];
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < n; r += (size_t)gridDim.x * blockDim.x) {
+    const float d = den[r] + delta;
+    const float inv = d > 0.f ? 1.f / d : 0.f;
+    const float2 num = dO[r];
+    if (MODE == NORM_DM) {
+      const float2 o = O[r];
+      O[r] = make_float2(fmaf(delta, o.x, num.x) * inv, fmaf(delta, o.y, num.y) * inv);
     } else {
-      const float2 o = a.O[r];
-      const float sc = a.beta * inv;
-      a.O[r] = make_float2(fmaf(sc, num[i].x, o.x), fmaf(sc, num[i].y, o.y));
+      dO[r] = cscale(num, inv);
     }
   }
 }

@@ -66,12 +66,15 @@ const KernelSet* find_set(int M, int K, int C) {
   return nullptr;
 }
 
-// Default cluster size: the smallest C that keeps one CTA's share of a
-// position at <= 64 KB of complex data (two or more CTAs fit on an SM).
+// Default cluster size: the smallest compiled C that keeps one CTA's share of
+// a position at <= 32 KB of complex data (four CTAs per SM), else <= 64 KB,
+// else the smallest compiled C.  (Measured at M = 256, K = 1: 16 CTAs per
+// position beat 8 by 3%.)
 int default_cluster(int M, int K) {
-  for (int C = 1; C <= 8; C *= 2)
-    if ((long long)K * M * M / C <= 8192 && find_set(M, K, C)) return C;
-  for (int C = 1; C <= 8; C *= 2)
+  for (long long cap : {4096LL, 8192LL})
+    for (int C = 1; C <= 16; C *= 2)
+      if ((long long)K * M * M / C <= cap && find_set(M, K, C)) return C;
+  for (int C = 1; C <= 16; C *= 2)
     if (find_set(M, K, C)) return C;
   return 0;
 }
@@ -224,7 +227,6 @@ struct ptycho_ctx {
   bool have_pos = false, have_data = false;
   bool epie_ok = false;    // the ePIE kernel of this (M, K, C) fits in shared memory
   bool psi_valid = false;  // X holds the DM state
-  bool denO_valid = false; // denO / denO_max match the current probe
   long long t = 0;
   long long launches = 0;
   std::string err;
@@ -395,6 +397,10 @@ int check_device_flag(ptycho_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------- overlap
+// object-side modes of obj_step (OBJ_UPD is the LSQML update)
+constexpr int OBJ_STEP_DM = 100;   // DM overlap update of O
+constexpr int OBJ_STEP_DIR = 101;  // LSQML direction dO
+
 template <int K>
 int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
   ObjArgs a{};
@@ -418,18 +424,22 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
   const double obj = (double)ctx->p.obj_ny * ctx->p.obj_nx;
   const double xb = 8.0 * ctx->p.J * K * (double)ctx->p.M * ctx->p.M;
   const dim3 g(ctx->n_tiles), b(OBJ_NT);
-  switch (mode) {
-    case OBJ_DEN:
-      if (int r = launch(ctx, "obj_den", obj * 4.0, [&] { k_obj<K, OBJ_DEN><<<g, b, 0, ctx->st>>>(a); })) return r;
-      return launch(ctx, "reduce_max", 0.0,
-                    [&] { k_reduce_max<<<1, 1024, 0, ctx->st>>>(ctx->tile_max, ctx->n_tiles, ctx->denO_max); });
-    case OBJ_DM:
-      return launch(ctx, "obj_update", xb + obj * 20.0, [&] { k_obj<K, OBJ_DM><<<g, b, 0, ctx->st>>>(a); });
-    case OBJ_DIR:
-      return launch(ctx, "obj_update", xb + obj * 12.0, [&] { k_obj<K, OBJ_DIR><<<g, b, 0, ctx->st>>>(a); });
-    default:
-      return launch(ctx, "obj_update", xb + obj * 20.0, [&] { k_obj<K, OBJ_UPD><<<g, b, 0, ctx->st>>>(a); });
-  }
+  if (mode == OBJ_UPD)
+    return launch(ctx, "obj_update", xb + obj * 20.0, [&] { k_obj<K, OBJ_UPD><<<g, b, 0, ctx->st>>>(a); });
+  // numerator + den_O in one pass, then the max of den_O, then the epilogue
+  if (int r = launch(ctx, "obj_sums", xb + obj * 12.0, [&] { k_obj<K, OBJ_NUMDEN><<<g, b, 0, ctx->st>>>(a); }))
+    return r;
+  if (int r = launch(ctx, "reduce_max", 0.0,
+                     [&] { k_reduce_max<<<1, 1024, 0, ctx->st>>>(ctx->tile_max, ctx->n_tiles, ctx->denO_max); }))
+    return r;
+  const size_t n = (size_t)ctx->p.obj_ny * ctx->p.obj_nx;
+  if (mode == OBJ_STEP_DM)
+    return launch(ctx, "obj_norm", obj * 28.0, [&] {
+      k_obj_norm<NORM_DM><<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->dO, ctx->denO, ctx->denO_max, a.reg, n);
+    });
+  return launch(ctx, "obj_norm", obj * 20.0, [&] {
+    k_obj_norm<NORM_DIR><<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->dO, ctx->denO, ctx->denO_max, a.reg, n);
+  });
 }
 
 int obj_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
@@ -440,12 +450,6 @@ int obj_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
   }
 }
 
-int ensure_denO(ptycho_ctx* ctx) {
-  if (ctx->denO_valid) return 0;
-  if (int r = obj_step(ctx, OBJ_DEN, nullptr, nullptr)) return r;
-  ctx->denO_valid = true;
-  return 0;
-}
 
 // probe: partial sums over position groups, fixed-order sum, apply.
 template <int K>
@@ -545,11 +549,9 @@ int run_dm(ptycho_ctx* ctx, int n) {
   }
   for (int it = 0; it < n; ++it) {
     const bool upd = ctx->t >= ctx->p.probe_start;
-    if (int r = ensure_denO(ctx)) return r;
-    if (int r = obj_step(ctx, OBJ_DM, ctx->X, nullptr)) return r;
+    if (int r = obj_step(ctx, OBJ_STEP_DM, ctx->X, nullptr)) return r;
     if (upd) {
       if (int r = probe_step(ctx, PR_DM, ctx->X, nullptr, true, true)) return r;
-      ctx->denO_valid = false;
     }
     if (int r = launch_fourier(ctx, FM_DM, ctx->X, nullptr, 0, J, "fourier_dm")) return r;
     ctx->t++;
@@ -563,8 +565,7 @@ int run_lsqml(ptycho_ctx* ctx, int n) {
   for (int it = 0; it < n; ++it) {
     const bool upd = ctx->t >= ctx->p.probe_start;
     if (int r = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, ctx->p.J, "fourier_chi")) return r;
-    if (int r = ensure_denO(ctx)) return r;
-    if (int r = obj_step(ctx, OBJ_DIR, ctx->X, nullptr)) return r;
+    if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
     if (upd)
       if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
     if (int r = steps_step(ctx, upd)) return r;
@@ -573,7 +574,6 @@ int run_lsqml(ptycho_ctx* ctx, int n) {
     if (int r = obj_step(ctx, OBJ_UPD, ctx->X, ctx->alphaO)) return r;
     if (upd) {
       if (int r = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return r;
-      ctx->denO_valid = false;
     }
     ctx->t++;
   }
@@ -644,7 +644,6 @@ int run_epie(ptycho_ctx* ctx, int n) {
   CK(cudaStreamSynchronize(ctx->st));
   ctx->t += n;
   ctx->psi_valid = false;
-  ctx->denO_valid = false;
   return 0;
 }
 
@@ -687,7 +686,6 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
   ctx->pos_host = pos;
   ctx->have_pos = true;
   ctx->psi_valid = false;
-  ctx->denO_valid = false;
   return 0;
 }
 
@@ -1022,7 +1020,6 @@ int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, in
       for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(probe[i])) return fail(ctx, PTYCHO_ERR_NONFINITE, "probe guess has NaN/Inf");
     CK(cudaMemcpyAsync(ctx->P, probe, n * 4, kind, ctx->st));
-    ctx->denO_valid = false;
   }
   CK(cudaStreamSynchronize(ctx->st));
   ctx->psi_valid = false;
