@@ -70,7 +70,8 @@ enum { PTYCHO_I_F32 = 0, PTYCHO_I_F16 = 1, PTYCHO_I_BF16 = 2 };
 #define PTYCHO_ERR_UNSUPPORTED (-9) /* (M, K) combination not compiled in       */
 
 typedef struct {
-  int M;            /* probe / detector side in pixels (16, 32, 64, 128, 256) */
+  int M;            /* probe / detector side in pixels (16, 32, 64, 96, 128,
+                       192, 256; 96 and 192 without ePIE)                    */
   int K;            /* number of incoherent probe modes (1..3), Sec. 2.2       */
   int J;            /* number of scan positions (diffraction frames)          */
   int obj_ny;       /* object rows                                            */
@@ -85,7 +86,9 @@ typedef struct {
                               SplitMix64-driven Fisher-Yates shuffle per
                               iteration, keyed by seed XOR iteration index   */
   void* stream;     /* cudaStream_t for all GPU work (may be NULL)            */
-  int cluster;      /* FFT cluster size override (0 = autotuned choice)       */
+  int cluster;      /* CTAs per scan position in the Fourier kernel: 0 = the
+                       built-in choice, -1 = autotuned (ptycho_autotune),
+                       > 0 = that size (must be compiled for (M, K))          */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */
@@ -170,6 +173,44 @@ int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n
 /* FFT cluster size chosen for this context (1, 2, 4 or 8 CTAs). */
 int ptycho_cluster_size(const ptycho_ctx* ctx);
 
+/* ---- Many reconstructions per launch --------------------------------------
+ * The paper's batch GPU mode queues many small scans, one job per GPU
+ * (Sec. 3.3).  On one B300 a batch groups N reconstructions of unequal size:
+ * one iteration of every member is captured into a single CUDA graph (each
+ * member's kernels on its own stream branch) and replayed once per iteration.
+ *
+ * ptycho_batch_create: params[n] describes each member (its stream field is
+ *   ignored: the batch creates one stream per member); stream is the batch
+ *   stream the graph runs on (NULL: the batch creates its own).
+ * ptycho_batch_member: the member's context, for ptycho_set_data,
+ *   ptycho_set_init, ptycho_get_*, ptycho_fourier_error (owned by the batch;
+ *   do not destroy it).
+ * ptycho_batch_iterate: n_iter iterations of DM or LSQML (ePIE:
+ *   PTYCHO_ERR_UNSUPPORTED) on every member; every member must have data.
+ *   The graph is captured again when the algorithm or a member's
+ *   probe-update state changes.  Asynchronous on the batch stream; member
+ *   streams are ordered after it.
+ * ptycho_batch_kernels_per_iteration: kernel nodes in the captured graph.
+ * Errors: PTYCHO_ERR_* codes; ptycho_batch_last_error(b) (b = NULL: last
+ * failed create). */
+typedef struct ptycho_batch ptycho_batch;
+int ptycho_batch_create(ptycho_batch** out, int n, const ptycho_params* params, void* stream);
+ptycho_ctx* ptycho_batch_member(ptycho_batch* b, int i);
+int ptycho_batch_size(const ptycho_batch* b);
+int ptycho_batch_iterate(ptycho_batch* b, int alg, int n_iter);
+long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b);
+int ptycho_batch_synchronize(ptycho_batch* b);
+const char* ptycho_batch_last_error(const ptycho_batch* b);
+void ptycho_batch_destroy(ptycho_batch* b);
+
+/* FFT shape autotuner: times the Fourier kernel (residual pass) of every
+ * compiled cluster size for (M, K) on synthetic data of about 512 MB, keeps
+ * the fastest in a process-wide table (later calls return it at once) and
+ * writes it to *best_cluster and its time per scan position to
+ * *ms_per_position (either may be NULL).  Allocates and frees temporary
+ * contexts; synchronises the device work it issues. */
+int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position);
+
 /* Fourier error without any device allocation.
  *
  * The paper has no counterpart to this call.  It exists for callers that
@@ -195,7 +236,7 @@ int ptycho_cluster_size(const ptycho_ctx* ctx);
  * PTYCHO_ERR_ARG; (M, K) must be a compiled combination (else
  * PTYCHO_ERR_UNSUPPORTED).  Errors are reported by ptycho_last_error(NULL).
  *
- * Scratch: one fixed array of about 2.2 MB in device memory, defined at file
+ * Scratch: one fixed array of about 4.3 MB in device memory, defined at file
  * scope in the library, which every GPU that loads the library keeps until
  * the process exits.  The first call on each device looks up that array's
  * device address (once per device, with the device current); make that first

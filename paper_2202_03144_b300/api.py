@@ -78,6 +78,15 @@ def lib() -> C.CDLL:
             "ptycho_cluster_size": (i, [vp]),
             "ptycho_last_error": (C.c_char_p, [vp]),
             "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
+            "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
+            "ptycho_batch_member": (vp, [vp, i]),
+            "ptycho_batch_size": (i, [vp]),
+            "ptycho_batch_iterate": (i, [vp, i, i]),
+            "ptycho_batch_kernels_per_iteration": (C.c_longlong, [vp]),
+            "ptycho_batch_synchronize": (i, [vp]),
+            "ptycho_batch_last_error": (C.c_char_p, [vp]),
+            "ptycho_batch_destroy": (None, [vp]),
+            "ptycho_autotune": (i, [i, i, C.POINTER(i), C.POINTER(d)]),
             "ptycho_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -325,6 +334,81 @@ class Reconstruction:
         if self.ctx:
             destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(M: int, K: int) -> tuple[int, float]:
+    """ptycho_autotune: (fastest cluster size, ms per scan position) for (M, K)."""
+    best = C.c_int()
+    ms = C.c_double()
+    _check(None, lib().ptycho_autotune(M, K, C.byref(best), C.byref(ms)))
+    return best.value, ms.value
+
+
+class _Member(Reconstruction):
+    """A batch member: a context owned by its batch (never destroyed here)."""
+
+    def __init__(self, handle, M, K, J, obj_shape):
+        self.ctx = C.c_void_p(handle)
+        self.M, self.K, self.J = M, K, J
+        self.obj_shape = tuple(obj_shape)
+
+    def close(self):
+        self.ctx = None
+
+
+class Batch:
+    """ptycho_batch_*: N reconstructions of unequal size, one CUDA graph per
+    iteration.  ``members`` is a list of dicts with keys M, K, J, obj_shape and
+    optional parameters (cluster, reg, lsqml_beta, probe_start, istore)."""
+
+    def __init__(self, members, stream=None):
+        n = len(members)
+        arr = (Params * n)()
+        for i, m in enumerate(members):
+            kw = {k: v for k, v in m.items() if k not in ("M", "K", "J", "obj_shape")}
+            arr[i] = default_params(M=m["M"], K=m["K"], J=m["J"], obj_ny=m["obj_shape"][0],
+                                    obj_nx=m["obj_shape"][1], **kw)
+        h = C.c_void_p()
+        rc = lib().ptycho_batch_create(C.byref(h), n, arr, stream)
+        if rc != 0:
+            raise PtychoError(rc, (lib().ptycho_batch_last_error(None) or b"").decode())
+        self.h = h
+        self.members = [_Member(lib().ptycho_batch_member(h, i), m["M"], m["K"], m["J"], m["obj_shape"])
+                        for i, m in enumerate(members)]
+
+    def _check(self, rc):
+        if rc != 0:
+            raise PtychoError(rc, (lib().ptycho_batch_last_error(self.h) or b"").decode())
+
+    def iterate(self, alg, n_iter=1):
+        a = ALGS[alg] if isinstance(alg, str) else int(alg)
+        self._check(lib().ptycho_batch_iterate(self.h, a, int(n_iter)))
+
+    def synchronize(self):
+        self._check(lib().ptycho_batch_synchronize(self.h))
+
+    @property
+    def kernels_per_iteration(self):
+        return lib().ptycho_batch_kernels_per_iteration(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.ctx = None
+            lib().ptycho_batch_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self

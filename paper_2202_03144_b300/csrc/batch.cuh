@@ -1,0 +1,285 @@
+// Many reconstructions per launch, and the FFT cluster-size autotuner.
+//
+// The ptychopy paper runs many small scans by queueing one job per GPU
+// (Sec. 3.3, batch GPU mode).  On one B300 a single small scan (J ~ 100..4000
+// positions) fills only part of the machine and each of its iterations costs
+// a dozen kernel launches.  A batch groups N reconstructions of unequal probe
+// size and position count: one iteration of every member is captured once
+// into a CUDA graph -- each member's kernels on its own branch, forked from
+// and joined back to the batch stream -- and that graph is replayed once per
+// iteration, so the members run concurrently and the host issues one launch
+// per iteration instead of N x (launches per iteration).
+//
+// This file is included by ptycho_api.cu (it uses the context internals).
+
+struct ptycho_batch {
+  std::vector<ptycho_ctx*> m;
+  std::vector<cudaStream_t> streams;  // one per member, created here
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_alg = -1;
+  std::vector<char> graph_upd;        // probe-update flag of each member baked into the graph
+  long long kernels_per_launch = 0;
+  long long graph_launches = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(ptycho_batch* b, int code, const char* fmt, ...) {
+  char t[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t, sizeof t, fmt, ap);
+  va_end(ap);
+  if (b) b->err = t;
+  else g_batch_error = t;
+  return code;
+}
+
+void batch_drop_graph(ptycho_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->graph_alg = -1;
+}
+
+// Capture one iteration of every member (probe-update flags `upd`) into a graph.
+int batch_capture(ptycho_batch* b, int alg, const std::vector<char>& upd) {
+  batch_drop_graph(b);
+  cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(b, PTYCHO_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  cudaEventRecord(b->fork, b->main);
+  long long before = 0, after = 0;
+  int rc = 0;
+  for (size_t i = 0; i < b->m.size() && !rc; ++i) {
+    ptycho_ctx* c = b->m[i];
+    cudaStreamWaitEvent(c->st, b->fork, 0);
+    before += c->launches;
+    rc = alg == PTYCHO_DM ? dm_step(c, upd[i] != 0) : lsqml_step(c, upd[i] != 0);
+    after += c->launches;
+    if (rc) {
+      b->err = "member " + std::to_string(i) + ": " + c->err;
+      break;
+    }
+    cudaEventRecord(b->join[i], c->st);
+    cudaStreamWaitEvent(b->main, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->main, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bfail(b, PTYCHO_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return bfail(b, PTYCHO_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  b->graph = g;
+  b->graph_alg = alg;
+  b->graph_upd = upd;
+  b->kernels_per_launch = after - before;
+  return 0;
+}
+
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, std::pair<int, double>> g_tune_cache;
+
+// k_fill_amp: a deterministic pseudo-random amplitude pattern (tuning data)
+__global__ void k_fill_amp(float* a, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ 0x9e3779b9u;
+    h ^= h >> 16;
+    a[i] = (float)(h & 0xffff) * (1.0f / 65536.0f);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position) {
+  if (M < 2 || K < 1) return fail(nullptr, PTYCHO_ERR_ARG, "bad sizes M=%d K=%d", M, K);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find({M, K});
+    if (it != g_tune_cache.end()) {
+      if (best_cluster) *best_cluster = it->second.first;
+      if (ms_per_position) *ms_per_position = it->second.second;
+      return PTYCHO_OK;
+    }
+  }
+  // enough positions to fill the GPU several times over (capped at ~512 MB)
+  long long J = (512LL << 20) / ((long long)K * M * M * 12);
+  if (J > 4096) J = 4096;
+  if (J < 64) J = 64;
+  const int ny = M + 64, nx = M + 64;
+  std::vector<float> pos(2 * J);
+  for (long long j = 0; j < J; ++j) {
+    pos[2 * j] = (float)((j * 37) % 65);
+    pos[2 * j + 1] = (float)((j * 53) % 65);
+  }
+  int best = 0;
+  double best_ms = 1e30;
+  for (int C = 1; C <= 16; C *= 2) {
+    if (!find_set(M, K, C)) continue;
+    ptycho_params p;
+    ptycho_default_params(&p);
+    p.M = M;
+    p.K = K;
+    p.J = (int)J;
+    p.obj_ny = ny;
+    p.obj_nx = nx;
+    p.cluster = C;
+    ptycho_ctx* ctx = nullptr;
+    if (ptycho_create(&ctx, &p) != PTYCHO_OK) continue;  // e.g. shared memory too small
+    int rc = set_positions_impl(ctx, pos.data());
+    if (!rc) {
+      k_fill_amp<<<1184, 256, 0, ctx->st>>>((float*)ctx->amp, (size_t)J * M * M);
+      ctx->have_data = true;
+      rc = ensure_work_buffers(ctx);
+    }
+    double ms_min = 1e30;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int rep = 0; rep < 4 && !rc; ++rep) {
+      cudaEventRecord(e0, ctx->st);
+      rc = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, (int)J, "fourier_chi");
+      cudaEventRecord(e1, ctx->st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = PTYCHO_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < ms_min) ms_min = ms;  // first launch is the warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ptycho_destroy(ctx);
+    if (!rc && ms_min < best_ms) {
+      best_ms = ms_min;
+      best = C;
+    }
+  }
+  if (!best) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "no runnable kernel for M=%d K=%d", M, K);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[{M, K}] = {best, best_ms / (double)J};
+  }
+  if (best_cluster) *best_cluster = best;
+  if (ms_per_position) *ms_per_position = best_ms / (double)J;
+  return PTYCHO_OK;
+}
+
+int ptycho_batch_create(ptycho_batch** out, int n, const ptycho_params* params, void* stream) {
+  if (!out || !params || n < 1) return bfail(nullptr, PTYCHO_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  ptycho_batch* b = new ptycho_batch();
+  b->main = (cudaStream_t)stream;
+  if (!b->main) {
+    cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
+    b->own_main = true;
+  }
+  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n; ++i) {
+    ptycho_params p = params[i];
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ptycho_batch_destroy(b);
+      return bfail(nullptr, PTYCHO_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    }
+    b->streams.push_back(s);
+    p.stream = s;
+    ptycho_ctx* c = nullptr;
+    const int rc = ptycho_create(&c, &p);
+    if (rc) {
+      std::string msg = g_create_error;
+      ptycho_batch_destroy(b);
+      return bfail(nullptr, rc, "member %d: %s", i, msg.c_str());
+    }
+    b->m.push_back(c);
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    b->join.push_back(ev);
+  }
+  *out = b;
+  return PTYCHO_OK;
+}
+
+ptycho_ctx* ptycho_batch_member(ptycho_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->m.size()) return nullptr;
+  return b->m[i];
+}
+
+int ptycho_batch_size(const ptycho_batch* b) { return b ? (int)b->m.size() : 0; }
+
+int ptycho_batch_iterate(ptycho_batch* b, int alg, int n_iter) {
+  if (!b) return PTYCHO_ERR_ARG;
+  if (alg != PTYCHO_DM && alg != PTYCHO_LSQML)
+    return bfail(b, PTYCHO_ERR_UNSUPPORTED, "batches run DM or LSQML (ePIE is sequential per scan)");
+  if (n_iter < 0) return bfail(b, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    ptycho_ctx* c = b->m[i];
+    if (!c->have_data) return bfail(b, PTYCHO_ERR_STATE, "member %zu has no data", i);
+    const int rc = alg == PTYCHO_DM ? dm_prepare(c) : lsqml_prepare(c);
+    if (rc) return bfail(b, rc, "member %zu: %s", i, c->err.c_str());
+  }
+  // the members' own streams must have finished their eager work (uploads,
+  // DM initial exit waves) before the graph runs on the batch stream
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    cudaEventRecord(b->join[i], b->m[i]->st);
+    cudaStreamWaitEvent(b->main, b->join[i], 0);
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    std::vector<char> upd(b->m.size());
+    for (size_t i = 0; i < b->m.size(); ++i) upd[i] = b->m[i]->t >= b->m[i]->p.probe_start;
+    if (!b->exec || b->graph_alg != alg || b->graph_upd != upd)
+      if (int rc = batch_capture(b, alg, upd)) return rc;
+    cudaError_t e = cudaGraphLaunch(b->exec, b->main);
+    if (e != cudaSuccess) return bfail(b, PTYCHO_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    b->graph_launches++;
+    for (ptycho_ctx* c : b->m) {
+      c->t++;
+      if (alg == PTYCHO_DM) c->psi_valid = true;
+    }
+  }
+  // later per-member calls (get_*, fourier_error) on the members' streams
+  // must see the graph's results
+  cudaEventRecord(b->fork, b->main);
+  for (ptycho_ctx* c : b->m) cudaStreamWaitEvent(c->st, b->fork, 0);
+  return PTYCHO_OK;
+}
+
+long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b) { return b ? b->kernels_per_launch : -1; }
+
+int ptycho_batch_synchronize(ptycho_batch* b) {
+  if (!b) return PTYCHO_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(b->main);
+  if (e != cudaSuccess) return bfail(b, PTYCHO_ERR_CUDA, "synchronize: %s", cudaGetErrorString(e));
+  return PTYCHO_OK;
+}
+
+const char* ptycho_batch_last_error(const ptycho_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+void ptycho_batch_destroy(ptycho_batch* b) {
+  if (!b) return;
+  if (b->main) cudaStreamSynchronize(b->main);
+  batch_drop_graph(b);
+  for (ptycho_ctx* c : b->m) ptycho_destroy(c);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->own_main) cudaStreamDestroy(b->main);
+  delete b;
+}
+
+}  // extern "C"

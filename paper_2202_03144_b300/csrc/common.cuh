@@ -103,13 +103,73 @@ __device__ __forceinline__ void dft16(float2* a) {
   for (int i = 0; i < 16; ++i) a[i] = t[i];
 }
 
+
+// 3-point DFT: X1,2 = a0 - (a1 + a2)/2 -/+ i (sqrt 3 / 2)(a1 - a2) (forward).
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* a) {
+  const float2 t1 = cadd(a[1], a[2]);
+  const float2 m = make_float2(fmaf(-0.5f, t1.x, a[0].x), fmaf(-0.5f, t1.y, a[0].y));
+  const float2 d = cscale(csub(a[1], a[2]), 0.86602540378443864676f);
+  a[0] = cadd(a[0], t1);
+  a[1] = cadd(m, mul_mi<INV>(d));
+  a[2] = csub(m, mul_mi<INV>(d));
+}
+
+// (cos, sin) of 2 pi e / 24 for e = 1..14
+__device__ __constant__ const float2 kTw24[14] = {
+  {0.96592582628906831221f, 0.25881904510252073948f},  // e = 1
+  {0.86602540378443870761f, 0.49999999999999994449f},  // e = 2
+  {0.70710678118654757274f, 0.70710678118654746172f},  // e = 3
+  {0.50000000000000011102f, 0.86602540378443859659f},  // e = 4
+  {0.25881904510252073948f, 0.96592582628906831221f},  // e = 5
+  {0.00000000000000006123f, 1.00000000000000000000f},  // e = 6
+  {-0.25881904510252062845f, 0.96592582628906831221f},  // e = 7
+  {-0.49999999999999977796f, 0.86602540378443870761f},  // e = 8
+  {-0.70710678118654746172f, 0.70710678118654757274f},  // e = 9
+  {-0.86602540378443870761f, 0.49999999999999994449f},  // e = 10
+  {-0.96592582628906820119f, 0.25881904510252101703f},  // e = 11
+  {-1.00000000000000000000f, 0.00000000000000012246f},  // e = 12
+  {-0.96592582628906831221f, -0.25881904510252079499f},  // e = 13
+  {-0.86602540378443881863f, -0.49999999999999972244f},  // e = 14
+};
+
+// 24-point DFT as 8 x 3 (n = 3 n1 + n2, k = k1 + 8 k2).
+template <bool INV>
+__device__ __forceinline__ void dft24(float2* a) {
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    float2 t[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) t[n1] = a[3 * n1 + n2];
+    dft8<INV>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+      float2 v = t[k1];
+      const int e = n2 * k1;
+      if (e > 0) v = rot<INV>(v, kTw24[e - 1].x, kTw24[e - 1].y);
+      a[3 * k1 + n2] = v;  // Y[n2][k1]
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) dft3<INV>(a + 3 * k1);  // a[3 k1 + k2] = X[k1 + 8 k2]
+  float2 t[24];
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) t[k1 + 8 * k2] = a[3 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 24; ++i) a[i] = t[i];
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* a) {
   if constexpr (R == 2) dft2<INV>(a);
   else if constexpr (R == 4) dft4<INV>(a);
   else if constexpr (R == 8) dft8<INV>(a);
   else if constexpr (R == 16) dft16<INV>(a);
-  else static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
+  else if constexpr (R == 3) dft3<INV>(a);
+  else if constexpr (R == 24) dft24<INV>(a);
+  else static_assert(R == 2 || R == 4 || R == 8 || R == 16 || R == 3 || R == 24, "radix");
 }
 
 // Radix of the next Stockham pass for a remaining length rem, given that a

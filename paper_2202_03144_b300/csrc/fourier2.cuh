@@ -44,7 +44,11 @@
 
 namespace ptycho {
 
-__host__ __device__ constexpr int radix1(int M) { return M >= 128 ? 16 : (M >= 32 ? 8 : 4); }
+// First-stage radix: 16 for 128 and 256, 8 for 32 and 64, 4 for 16; 24 (= 8 x 3)
+// for the mixed-radix sizes 96 (24 x 4) and 192 (24 x 8).
+__host__ __device__ constexpr int radix1(int M) {
+  return (M % 3 == 0) ? 24 : (M >= 128 ? 16 : (M >= 32 ? 8 : 4));
+}
 
 template <int M_, int K_, int C_>
 struct F2 {
@@ -57,7 +61,7 @@ struct F2 {
   static constexpr int PB = M + (R2 >= 16 ? 0 : (R2 == 8 ? 8 : 4));  // row pitch
   static constexpr int SBUF = (K * H * PB > L) ? K * H * PB : L;
   static constexpr int NRED = 64;
-  static_assert(R1 * R2 == M && R1 % R2 == 0 && R1 <= 16, "radix split");
+  static_assert(R1 * R2 == M && R1 % R2 == 0 && R1 <= 24, "radix split");
   static_assert(M % C == 0 && W >= 1, "cluster split");
   static_assert(NT % 32 == 0 && NT <= 1024, "threads");
 };
@@ -152,7 +156,7 @@ __device__ __forceinline__ float amp_at(const Fourier2Args& a, const void* amp_s
 }
 
 template <int M, int K, int C>
-__global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::NT <= 256 ? 4 : (F2<M, K, C>::NT <= 512 ? 2 : 1))) k_fourier2(Fourier2Args a) {
+__global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (F2<M, K, C>::NT <= 256 ? 4 : (F2<M, K, C>::NT <= 512 ? 2 : 1)))) k_fourier2(Fourier2Args a) {
   using F = F2<M, K, C>;
   constexpr int R1 = F::R1, R2 = F::R2, W = F::W, H = F::H, NT = F::NT, Q = F::Q;
   extern __shared__ __align__(128) unsigned char smem_raw[];

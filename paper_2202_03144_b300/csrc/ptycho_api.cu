@@ -48,6 +48,13 @@ KernelSet make_set() {
   return KernelSet{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>};
 }
 
+// mixed-radix sizes: DM / LSQML / error / forward model only (no ePIE kernel)
+template <int M, int K, int C>
+KernelSet make_set_noepie() {
+  using G = F2<M, K, C>;
+  return KernelSet{M, K, C, G::NT, 0, fourier2_smem<G>(), 0, k_fourier2<M, K, C>, nullptr};
+}
+
 const std::vector<KernelSet>& kernel_sets() {
   static const std::vector<KernelSet> sets = {
       make_set<16, 1, 1>(),  make_set<16, 1, 2>(),  make_set<16, 2, 1>(),  make_set<16, 3, 1>(),
@@ -56,6 +63,8 @@ const std::vector<KernelSet>& kernel_sets() {
       make_set<64, 1, 2>(),  make_set<64, 1, 4>(),  make_set<64, 3, 2>(),  make_set<64, 3, 4>(),
       make_set<128, 1, 2>(), make_set<128, 1, 4>(), make_set<128, 1, 8>(), make_set<128, 3, 4>(),
       make_set<128, 3, 8>(), make_set<256, 1, 4>(), make_set<256, 1, 8>(), make_set<256, 1, 16>(),
+      make_set_noepie<96, 1, 1>(), make_set_noepie<96, 1, 2>(), make_set_noepie<96, 1, 4>(),
+      make_set_noepie<192, 1, 2>(), make_set_noepie<192, 1, 4>(), make_set_noepie<192, 1, 8>(),
   };
   return sets;
 }
@@ -536,7 +545,8 @@ int ensure_work_buffers(ptycho_ctx* ctx) {
 }
 
 // ------------------------------------------------------------- algorithms
-int run_dm(ptycho_ctx* ctx, int n) {
+// DM: buffers and the initial exit waves psi = P_k O_j (outside any graph).
+int dm_prepare(ptycho_ctx* ctx) {
   if (int r = ensure_work_buffers(ctx)) return r;
   const int J = ctx->p.J, K = ctx->p.K, M = ctx->p.M;
   if (!ctx->psi_valid) {
@@ -547,34 +557,51 @@ int run_dm(ptycho_ctx* ctx, int n) {
       return r;
     ctx->psi_valid = true;
   }
+  return 0;
+}
+
+// One DM iteration with the probe update on or off (all device work).
+int dm_step(ptycho_ctx* ctx, bool upd) {
+  if (int r = obj_step(ctx, OBJ_STEP_DM, ctx->X, nullptr)) return r;
+  if (upd)
+    if (int r = probe_step(ctx, PR_DM, ctx->X, nullptr, true, true)) return r;
+  return launch_fourier(ctx, FM_DM, ctx->X, nullptr, 0, ctx->p.J, "fourier_dm");
+}
+
+int lsqml_prepare(ptycho_ctx* ctx) {
+  if (int r = ensure_work_buffers(ctx)) return r;
+  ctx->psi_valid = false;
+  return 0;
+}
+
+// One LSQML iteration with the probe update on or off (all device work).
+int lsqml_step(ptycho_ctx* ctx, bool upd) {
+  if (int r = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, ctx->p.J, "fourier_chi")) return r;
+  if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
+  if (upd)
+    if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
+  if (int r = steps_step(ctx, upd)) return r;
+  if (upd)  // alpha_P-weighted probe numerator from the old object
+    if (int r = probe_step(ctx, PR_UPD, ctx->X, ctx->alphaP, false, false)) return r;
+  if (int r = obj_step(ctx, OBJ_UPD, ctx->X, ctx->alphaO)) return r;
+  if (upd)
+    if (int r = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return r;
+  return 0;
+}
+
+int run_dm(ptycho_ctx* ctx, int n) {
+  if (int r = dm_prepare(ctx)) return r;
   for (int it = 0; it < n; ++it) {
-    const bool upd = ctx->t >= ctx->p.probe_start;
-    if (int r = obj_step(ctx, OBJ_STEP_DM, ctx->X, nullptr)) return r;
-    if (upd) {
-      if (int r = probe_step(ctx, PR_DM, ctx->X, nullptr, true, true)) return r;
-    }
-    if (int r = launch_fourier(ctx, FM_DM, ctx->X, nullptr, 0, J, "fourier_dm")) return r;
+    if (int r = dm_step(ctx, ctx->t >= ctx->p.probe_start)) return r;
     ctx->t++;
   }
   return 0;
 }
 
 int run_lsqml(ptycho_ctx* ctx, int n) {
-  if (int r = ensure_work_buffers(ctx)) return r;
-  ctx->psi_valid = false;
+  if (int r = lsqml_prepare(ctx)) return r;
   for (int it = 0; it < n; ++it) {
-    const bool upd = ctx->t >= ctx->p.probe_start;
-    if (int r = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, ctx->p.J, "fourier_chi")) return r;
-    if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
-    if (upd)
-      if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
-    if (int r = steps_step(ctx, upd)) return r;
-    if (upd)  // alpha_P-weighted probe numerator from the old object
-      if (int r = probe_step(ctx, PR_UPD, ctx->X, ctx->alphaP, false, false)) return r;
-    if (int r = obj_step(ctx, OBJ_UPD, ctx->X, ctx->alphaO)) return r;
-    if (upd) {
-      if (int r = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return r;
-    }
+    if (int r = lsqml_step(ctx, ctx->t >= ctx->p.probe_start)) return r;
     ctx->t++;
   }
   return 0;
@@ -706,7 +733,7 @@ namespace {
 
 constexpr int NOALLOC_MAX_J = 16384;   // positions per call
 constexpr int NOALLOC_MAX_M = 256;
-constexpr int NOALLOC_MAX_C = 8;
+constexpr int NOALLOC_MAX_C = 16;  // largest compiled cluster size
 // layout: [twiddles M_max float2][flag int, pad][err_out double2][positions int2 x J_max]
 //         [per-CTA error partials double2 x J_max * C_max]
 constexpr size_t NA_TW = 0;
@@ -756,6 +783,7 @@ extern "C" int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int
   const int C = default_cluster(M, K);
   const KernelSet* ks = C ? find_set(M, K, C) : nullptr;
   if (!ks) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "no kernel compiled for M=%d K=%d", M, K);
+  if (C > NOALLOC_MAX_C) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "cluster size %d exceeds the scratch layout", C);
   unsigned char* sc = nullptr;
   if (int r = noalloc_setup(&sc)) return r;
   cudaStream_t st = (cudaStream_t)stream;
@@ -863,7 +891,11 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
-  const int C = p->cluster > 0 ? p->cluster : default_cluster(p->M, p->K);
+  int C = p->cluster > 0 ? p->cluster : default_cluster(p->M, p->K);
+  if (p->cluster < 0) {  // autotuned: the fastest compiled cluster size for (M, K)
+    int best = 0;
+    if (ptycho_autotune(p->M, p->K, &best, nullptr) == PTYCHO_OK) C = best;
+  }
   const KernelSet* ks = find_set(p->M, p->K, C);
   if (!ks)
     return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "no kernel compiled for M=%d K=%d cluster=%d", p->M, p->K, C);
@@ -922,9 +954,10 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
   if (e == cudaSuccess && ks->C > 8) {
     e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess && ks->epie)
+      e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
-  ctx->epie_ok = e == cudaSuccess && ks->smem_epie <= (size_t)optin;
+  ctx->epie_ok = e == cudaSuccess && ks->epie != nullptr && ks->smem_epie <= (size_t)optin;
   if (ctx->epie_ok)
     e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_epie);
   if (e == cudaSuccess) {
@@ -1159,3 +1192,5 @@ void ptycho_destroy(ptycho_ctx* ctx) {
 }
 
 }  // extern "C"
+
+#include "batch.cuh"

@@ -13,7 +13,8 @@ COMPILED = [
     (32, 1, 1), (32, 1, 2), (32, 1, 4), (32, 2, 2), (32, 3, 1), (32, 3, 4),
     (64, 1, 1), (64, 1, 2), (64, 1, 4), (64, 3, 2), (64, 3, 4),
     (128, 1, 2), (128, 1, 4), (128, 1, 8), (128, 3, 4), (128, 3, 8),
-    (256, 1, 4), (256, 1, 8),
+    (256, 1, 4), (256, 1, 8), (256, 1, 16),
+    (96, 1, 1), (96, 1, 2), (96, 1, 4), (192, 1, 2), (192, 1, 4), (192, 1, 8),
 ]
 
 

@@ -1,0 +1,66 @@
+"""Batched reconstructions (one CUDA graph per iteration) and the autotuner.
+
+Every member of a batch must end exactly where the same reconstruction run
+alone ends (same kernels, same order inside each member: bit-identical), and
+within the parity tolerance of the FP64 oracle."""
+import numpy as np
+import pytest
+
+from gpu_cases import illuminated, scan
+from oracle import ptycho_oracle as orc
+from paper_2202_03144_b300 import api
+from util import align_global, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(16, 1, 3), (32, 1, 4), (64, 1, 3), (96, 1, 2), (32, 3, 3), (192, 1, 2)]
+
+
+def _cases():
+    return [scan(M, K, grid=g, photons=1e5, seed=10 + i) for i, (M, K, g) in enumerate(SHAPES)]
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+def test_batch_matches_single_and_oracle(alg):
+    cases = _cases()
+    n = 3
+    members = [dict(M=c["M"], K=c["K"], J=len(c["pos"]), obj_shape=c["shape"], probe_start=1) for c in cases]
+    with api.Batch(members) as b:
+        for m, c in zip(b.members, cases):
+            m.set_data(c["I"].astype(np.float32), c["pos"])
+            m.set_init(c["O0"], c["P0"])
+        b.iterate(alg, n)
+        assert b.kernels_per_iteration > len(cases)
+        got = [(m.get_object(), m.get_probe(), m.iteration) for m in b.members]
+    for (Og, Pg, t), c in zip(got, cases):
+        assert t == n
+        with api.Reconstruction(c["M"], c["K"], len(c["pos"]), c["shape"], probe_start=1) as r:
+            r.set_data(c["I"].astype(np.float32), c["pos"])
+            r.set_init(c["O0"], c["P0"])
+            r.iterate(alg, n)
+            Os, Ps = r.get_object(), r.get_probe()
+        assert np.array_equal(Og, Os) and np.array_equal(Pg, Ps), c["M"]
+        Oc, Pc, _ = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, probe_start=1)
+        m = illuminated(c["P"], c["pos"], c["shape"])
+        assert rel_l2(align_global(Og, Oc, m), Oc, m) < 1e-4 and rel_l2(Pg, Pc) < 1e-4, c["M"]
+
+
+def test_batch_rejects_epie_and_missing_data():
+    c = scan(32, 1, grid=2)
+    with api.Batch([dict(M=32, K=1, J=len(c["pos"]), obj_shape=c["shape"])]) as b:
+        with pytest.raises(api.PtychoError) as e:
+            b.iterate("lsqml", 1)
+        assert e.value.name == "STATE"
+        b.members[0].set_data(c["I"].astype(np.float32), c["pos"])
+        with pytest.raises(api.PtychoError) as e:
+            b.iterate("epie", 1)
+        assert e.value.name == "UNSUPPORTED"
+
+
+def test_autotune_picks_a_compiled_cluster():
+    best, ms = api.autotune(64, 1)
+    assert best in (1, 2, 4) and ms > 0
+    assert api.autotune(64, 1) == (best, ms)  # cached
+    c = scan(64, 1, grid=2)
+    with api.Reconstruction(64, 1, len(c["pos"]), c["shape"], cluster=-1) as r:
+        assert r.cluster == best

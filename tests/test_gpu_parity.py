@@ -75,6 +75,7 @@ ALG_CASES = [
     ("dm", 32, 1, 1), ("dm", 32, 3, 4), ("dm", 64, 1, 2), ("dm", 16, 2, 1),
     ("lsqml", 32, 1, 1), ("lsqml", 32, 3, 1), ("lsqml", 64, 1, 4), ("lsqml", 16, 3, 2),
     ("epie", 32, 1, 1), ("epie", 32, 3, 4), ("epie", 64, 1, 2), ("epie", 16, 1, 2),
+    ("dm", 96, 1, 2), ("lsqml", 96, 1, 1), ("lsqml", 192, 1, 4),
 ]
 
 

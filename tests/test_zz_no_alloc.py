@@ -43,8 +43,9 @@ def _noalloc_E(c):
 def test_noalloc_matches_regular_on_two_calls_in_a_row():
     pytest.importorskip("torch")
     cases = [scan(64, 1, grid=3, photons=1e5, mask_frac=0.03, seed=1),
-             scan(32, 3, grid=2, photons=1e6, seed=2)]
-    for c in cases:  # two consecutive calls, different sizes, shared scratch
+             scan(32, 3, grid=2, photons=1e6, seed=2),
+             scan(256, 1, grid=2, photons=1e6, seed=3)]   # 16-CTA clusters
+    for c in cases:  # consecutive calls, different sizes, shared scratch
         E_ref = _regular_E(c)
         E = _noalloc_E(c)
         assert abs(E - E_ref) <= TOL_E * E_ref, (E, E_ref)
