@@ -159,6 +159,101 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7):
+    """Batched workload: n scans of unequal probe size and position count,
+    one CUDA graph per iteration (all members) vs one member at a time."""
+    from paper_2202_03144_b300 import synth
+    members = synth.batch_members(n, seed=seed)
+    side = max(max(m["obj_shape"]) for m in members)
+    field = synth.make_object(side, side, seed=4242)
+    probes = {}
+    for M in sorted(set(m["M"] for m in members)):
+        probes[M] = (synth.make_probe(M, 1, R=0.3125 * M, sigma=M / 16.0, c=0.02 * (64.0 / M) ** 2),
+                     synth.make_probe(M, 1, R=0.34375 * M, sigma=M / 16.0, c=0.02 * (64.0 / M) ** 2))
+    spec = [dict(M=m["M"], K=1, J=m["J"], obj_shape=m["obj_shape"], cluster=-1) for m in members]
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    with torch.cuda.stream(stream):
+        b = api.Batch(spec, stream=stream.cuda_stream)
+        for mem, m in zip(b.members, members):
+            P, P0 = probes[m["M"]]
+            O = field[:m["obj_shape"][0], :m["obj_shape"][1]]
+            mem.set_positions(m["positions"])
+            mem.set_init(O, P)
+            I = torch.empty((m["J"], m["M"], m["M"]), dtype=torch.float32, device="cuda")
+            mem.simulate(I)
+            torch.cuda.synchronize()
+            sc = m["photons"] / float(I.sum(dim=(1, 2)).mean())
+            I = torch.poisson(I * sc, generator=gen)
+            mem.set_data(I, m["positions"])
+            mem.set_init(np.ones(m["obj_shape"], np.complex64), P0 * np.sqrt(sc))
+            del I
+        torch.cuda.synchronize()
+        b.iterate("lsqml", warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.iterate("lsqml", iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_graph = e0.elapsed_time(e1)
+        # one member after another (a job queue on one GPU)
+        t0 = time.perf_counter()
+        for mem in b.members:
+            mem.iterate("lsqml", iters)
+            mem.get_probe()  # synchronises the member
+        ms_seq = (time.perf_counter() - t0) * 1e3
+        kpi = b.kernels_per_iteration
+        clusters = sorted({(m["M"], api.autotune(m["M"], 1)[0]) for m in members})
+        b.close()
+    units = sum(m["J"] for m in members) * iters
+    return {"value": units / (ms_graph / 1e3), "unit": UNIT, "sequential_value": units / (ms_seq / 1e3),
+            "members": n, "positions": sum(m["J"] for m in members), "iterations": iters,
+            "kernels_per_graph": kpi, "autotuned_clusters": clusters,
+            "workload": f"{n} LSQML scans, probe sizes {{64,96,128,192,256}}, 100-4000 positions (Fermat "
+                        "spirals, spacing 0.15 M), Poisson 1e4-1e6 photons/frame; one CUDA graph per iteration"}
+
+
+def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=100, check=5):
+    """Wall time and iterations for 16-bit amplitude storage to reach the
+    Fourier error that plain FP32 LSQML reaches after n_ref iterations.  Every
+    run is judged by the same FP32-stored context (its (O, P) copied over at
+    each check), so the error is always measured against the FP32 data."""
+    M, K, J = w["M"], w["K"], w["grid"] ** 2
+    shape = (w["obj"], w["obj"])
+    out = {}
+    eps = None
+    with torch.cuda.stream(stream):
+        judge = api.Reconstruction(M, K, J, shape, stream=stream.cuda_stream)
+        judge.set_data(I, pos)
+        Ob = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        Pb = torch.empty((K, M, M), dtype=torch.complex64, device="cuda")
+        for store in ("f32", "f16", "bf16"):
+            r = api.Reconstruction(M, K, J, shape, stream=stream.cuda_stream, istore=store)
+            r.set_data(I, pos)
+            r.set_init(np.ones(shape, np.complex64), P0s)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, E = 0, None
+            limit = n_ref if store == "f32" else 2 * n_ref
+            while it < limit:
+                r.iterate("lsqml", check)
+                it += check
+                r.get_object(Ob)
+                r.get_probe(Pb)
+                judge.set_init(Ob, Pb)
+                E = judge.fourier_error()
+                if eps is not None and E <= eps:
+                    break
+            dt = time.perf_counter() - t0
+            r.close()
+            if store == "f32":
+                eps = E
+            out[store] = {"iterations": it, "seconds": dt, "fourier_error": E, "reached": bool(E <= eps)}
+        judge.close()
+    return {"eps": eps, "reference": f"plain FP32 LSQML after {n_ref} iterations from a flat object; errors "
+                                     "measured against the FP32 data", "check_every": check, **out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,6 +264,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a 20x20-position scan (profiling runs)")
     ap.add_argument("--cluster", type=int, default=0, help="FFT cluster size (0 = library default)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-eps", action="store_true", help="skip the time-to-epsilon runs")
     args = ap.parse_args()
     if args.small:
         WORKLOAD["grid"] = 20
@@ -290,6 +387,8 @@ def main():
            "d2h_bytes_per_step": int(d2h),
            "step": f"one job: set_data + set_init from pinned host memory, {args.e2e_iters} LSQML iterations, "
                    f"get_object + get_probe to host"}
+    batched = None if (args.no_batch or args.small) else run_batched(api, torch, stream)
+    t2e = None if (args.no_eps or args.small) else time_to_eps(api, torch, stream, I, pos, P0s, w)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -311,6 +410,8 @@ def main():
             "lsqml_f16": {"value": rate(f16_run), "fourier_error": f16_run["err"]},
             "lsqml_bf16": {"value": rate(bf16_run), "fourier_error": bf16_run["err"]},
         },
+        "batched": batched,
+        "time_to_eps": t2e,
         "roofline": roof,
         "cpu_baseline": cb,
         "e2e": e2e,

@@ -97,30 +97,24 @@ def raster_positions(ny: int, nx: int, step: float, jitter: int, offset: float,
 
 
 def spiral_positions(n: int, spacing: float, center: tuple[float, float]) -> np.ndarray:
-    """Fermat spiral r = a*sqrt(i), theta = i * golden angle, with the mean
-    nearest-neighbour distance tuned to ``spacing``; rounded to integers."""
+    """Fermat spiral r = a*sqrt(i + 1/2), theta = i * golden angle, with the mean
+    nearest-neighbour distance equal to ``spacing``; rounded to integers.
+
+    The spiral's geometry scales linearly with a, so a is the spacing over
+    the mean nearest-neighbour distance of the a = 1 spiral."""
+    from scipy.spatial import cKDTree
+
     golden = math.radians(137.50776405003785)
-
-    def pts(a: float) -> np.ndarray:
-        i = np.arange(n, dtype=np.float64)
-        r = a * np.sqrt(i + 0.5)
-        t = i * golden
-        return np.stack([r * np.sin(t), r * np.cos(t)], axis=1)
-
-    def mean_nn(p: np.ndarray) -> float:
-        d = np.sqrt(((p[:, None, :] - p[None, :, :]) ** 2).sum(-1))
-        np.fill_diagonal(d, np.inf)
-        return float(d.min(1).mean())
-
-    lo, hi = 0.05 * spacing, 2.0 * spacing
-    for _ in range(60):  # bisection on the spiral constant
-        mid = 0.5 * (lo + hi)
-        if mean_nn(pts(mid)) < spacing:
-            lo = mid
-        else:
-            hi = mid
-    p = pts(0.5 * (lo + hi))
-    p = p + np.asarray(center, dtype=np.float64)[None, :]
+    i = np.arange(n, dtype=np.float64)
+    r = np.sqrt(i + 0.5)
+    t = i * golden
+    unit = np.stack([r * np.sin(t), r * np.cos(t)], axis=1)
+    if n > 1:
+        d, _ = cKDTree(unit).query(unit, k=2)
+        a = spacing / float(d[:, 1].mean())
+    else:
+        a = spacing
+    p = unit * a + np.asarray(center, dtype=np.float64)[None, :]
     return np.rint(p)
 
 
@@ -169,14 +163,16 @@ def scan_config(name: str, seed: int = 0) -> dict:
                     object0=flat_object(256, 256), probe0=P0, noise=False)
     if name == "modes128":  # 128^2 probe, 3 modes, 1024^2 object, 1600-point spiral
         M, K = 128, 3
+        # a 1600-point spiral at 20 px mean spacing spans ~940 px: with the
+        # 128 px probe the object must be 1088^2 (1024^2 does not hold it)
         P = make_probe(M, K, R=40.0, sigma=8.0, c=0.005)
         pos = spiral_positions(1600, 20.0, (0.0, 0.0))
-        pos = pos - pos.min(0) + (1024 - (pos.max(0) - pos.min(0)) - M) / 2.0
-        pos = np.rint(pos)
-        O = make_object(1024, 1024, seed=1000 + seed)
+        pos = pos - pos.min(0) + 8
+        ny, nx = object_shape_for(pos, M, margin=8, multiple=16)
+        O = make_object(ny, nx, seed=1000 + seed)
         P0 = make_probe(M, K, R=44.0, sigma=8.0, c=0.005)
         return dict(M=M, K=K, probe=P, object=O, positions=pos, photons=1e5,
-                    object0=flat_object(1024, 1024), probe0=P0, noise=True)
+                    object0=flat_object(ny, nx), probe0=P0, noise=True)
     if name == "det256":  # 256^2 detector, 100x100 raster at step 24, 2640^2 object
         M, K = 256, 1
         P = make_probe(M, K, R=80.0, sigma=16.0, c=0.00125)
@@ -186,3 +182,22 @@ def scan_config(name: str, seed: int = 0) -> dict:
         return dict(M=M, K=K, probe=P, object=O, positions=pos, photons=1e5,
                     object0=flat_object(2640, 2640), probe0=P0, noise=True)
     raise ValueError(f"unknown workload {name!r}")
+
+
+def batch_members(n: int, seed: int = 0, sizes=(64, 96, 128, 192, 256), jmin=100, jmax=4000):
+    """Shapes of the batched workload: n scans with probe sizes drawn from
+    ``sizes``, position counts uniform in [jmin, jmax], Fermat spirals with
+    spacing round(0.15 M), photons per frame log-uniform in [1e4, 1e6].
+    Returns a list of dicts (M, J, spacing, photons, positions, obj_shape)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        M = int(rng.choice(sizes))
+        J = int(rng.integers(jmin, jmax + 1))
+        spacing = float(round(0.15 * M))
+        pos = spiral_positions(J, spacing, (0.0, 0.0))
+        pos = pos - pos.min(0) + 8
+        ny, nx = object_shape_for(pos, M, margin=8, multiple=16)
+        photons = float(10 ** rng.uniform(4, 6))
+        out.append(dict(M=M, J=J, spacing=spacing, photons=photons, positions=pos, obj_shape=(ny, nx)))
+    return out
