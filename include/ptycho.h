@@ -211,6 +211,53 @@ void ptycho_batch_destroy(ptycho_batch* b);
  * contexts; synchronises the device work it issues. */
 int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position);
 
+/* ---- Learned warm start ----------------------------------------------------
+ * A convolutional encoder-decoder (6 levels, 128^2 -> 4^2 -> 64^2, ~1.96M
+ * parameters, BF16 weights and activations, FP32 sums) maps one diffraction
+ * frame, x = log(1 + I) / 10 of a 128 x 128 detector-centred pattern, to the
+ * amplitude and phase of the central 64 x 64 object patch under the probe.
+ * Its predictions, stitched together, replace the flat initial object of a
+ * DM or LSQML reconstruction, which stays the judge.  Not in the paper (whose
+ * "probe and/or object guess can also be specified", Sec. 2.2, is the hook it
+ * uses).  Training, inference and every gradient run in this library's CUDA
+ * kernels.
+ *
+ * Parameter vector (FP32, host order used by get/set): for each of the 12
+ * layers, weights [co][ci][3][3] then biases [co].
+ * ptycho_net_create: He-normal weights from SplitMix64(seed), zero biases;
+ *   max_batch bounds B in the calls below; flags = 0 (BF16 activations, the
+ *   method) or PTYCHO_NET_F32_ACTIVATIONS (same kernels with FP32 activation
+ *   storage, for checking the kernels against an unrounded reference);
+ *   stream as for contexts.
+ * ptycho_net_predict: intensities device [B][128][128] (detector-centred);
+ *   out device [B][2][64][64] (amplitude, phase).
+ * ptycho_net_gradients: loss L = sum (out - target)^2 / (B * 2 * 64 * 64)
+ *   against targets device [B][2][64][64]; grads (host, may be NULL)
+ *   receives dL/dparams; *loss (may be NULL) receives L.  Synchronises.
+ * ptycho_net_train_step: one AdamW step (beta 0.9 / 0.999, eps 1e-8, weight
+ *   decay 1e-4 on weights) at learning rate lr; *loss as above (NULL: no sync).
+ * ptycho_object_patches: amplitude and phase of the central 64 x 64 patch of
+ *   the context's current object at every position, device [J][2][64][64]
+ *   (training targets from a known object).
+ * ptycho_warm_start: predicts the patch of every position of ctx (M must be
+ *   128) from its stored data and writes their per-pixel mean into ctx's
+ *   object where at least one patch covers it.  Synchronises. */
+typedef struct ptycho_net ptycho_net;
+#define PTYCHO_NET_F32_ACTIVATIONS 1
+int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, int flags, void* stream);
+long long ptycho_net_num_params(const ptycho_net* n);
+int ptycho_net_get_params(ptycho_net* n, float* out);
+int ptycho_net_set_params(ptycho_net* n, const float* in);
+int ptycho_net_predict(ptycho_net* n, const float* intensities, int B, float* out);
+int ptycho_net_gradients(ptycho_net* n, const float* intensities, const float* targets, int B, float* grads,
+                         double* loss);
+int ptycho_net_train_step(ptycho_net* n, const float* intensities, const float* targets, int B, float lr,
+                          double* loss);
+const char* ptycho_net_last_error(const ptycho_net* n);
+void ptycho_net_destroy(ptycho_net* n);
+int ptycho_object_patches(ptycho_ctx* ctx, float* out);
+int ptycho_warm_start(ptycho_ctx* ctx, ptycho_net* n);
+
 /* Fourier error without any device allocation.
  *
  * The paper has no counterpart to this call.  It exists for callers that

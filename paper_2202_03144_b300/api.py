@@ -87,6 +87,17 @@ def lib() -> C.CDLL:
             "ptycho_batch_last_error": (C.c_char_p, [vp]),
             "ptycho_batch_destroy": (None, [vp]),
             "ptycho_autotune": (i, [i, i, C.POINTER(i), C.POINTER(d)]),
+            "ptycho_net_create": (i, [C.POINTER(vp), C.c_ulonglong, i, i, vp]),
+            "ptycho_net_num_params": (C.c_longlong, [vp]),
+            "ptycho_net_get_params": (i, [vp, f]),
+            "ptycho_net_set_params": (i, [vp, f]),
+            "ptycho_net_predict": (i, [vp, f, i, f]),
+            "ptycho_net_gradients": (i, [vp, f, f, i, f, C.POINTER(d)]),
+            "ptycho_net_train_step": (i, [vp, f, f, i, C.c_float, C.POINTER(d)]),
+            "ptycho_net_last_error": (C.c_char_p, [vp]),
+            "ptycho_net_destroy": (None, [vp]),
+            "ptycho_object_patches": (i, [vp, f]),
+            "ptycho_warm_start": (i, [vp, vp]),
             "ptycho_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -421,6 +432,83 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Net:
+    """ptycho_net_*: the warm-start encoder-decoder.  Frames and targets are
+    float32 torch CUDA tensors ([B,128,128] detector-centred intensities,
+    [B,2,64,64] amplitude/phase); parameters are host float32 arrays."""
+
+    def __init__(self, seed=0, max_batch=64, stream=None, f32_activations=False):
+        h = C.c_void_p()
+        rc = lib().ptycho_net_create(C.byref(h), seed, max_batch, 1 if f32_activations else 0, stream)
+        if rc != 0:
+            raise PtychoError(rc, (lib().ptycho_net_last_error(None) or b"").decode())
+        self.h = h
+        self.max_batch = max_batch
+
+    def _check(self, rc):
+        if rc != 0:
+            raise PtychoError(rc, (lib().ptycho_net_last_error(self.h) or b"").decode())
+
+    @property
+    def num_params(self):
+        return lib().ptycho_net_num_params(self.h)
+
+    def get_params(self):
+        out = np.empty(self.num_params, np.float32)
+        self._check(lib().ptycho_net_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        self._check(lib().ptycho_net_set_params(self.h, p.ctypes.data))
+
+    def predict(self, frames, out):
+        self._check(lib().ptycho_net_predict(self.h, frames.data_ptr(), int(frames.shape[0]), out.data_ptr()))
+        return out
+
+    def gradients(self, frames, targets):
+        g = np.empty(self.num_params, np.float32)
+        L = C.c_double()
+        self._check(lib().ptycho_net_gradients(self.h, frames.data_ptr(), targets.data_ptr(), int(frames.shape[0]),
+                                               g.ctypes.data, C.byref(L)))
+        return L.value, g
+
+    def train_step(self, frames, targets, lr, want_loss=False):
+        L = C.c_double()
+        self._check(lib().ptycho_net_train_step(self.h, frames.data_ptr(), targets.data_ptr(), int(frames.shape[0]),
+                                                C.c_float(lr), C.byref(L) if want_loss else None))
+        return L.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ptycho_net_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def object_patches(rec, out):
+    """ptycho_object_patches: central 64x64 amplitude/phase of rec's object at
+    every position, into a float32 torch CUDA tensor [J,2,64,64]."""
+    _check(rec.ctx, lib().ptycho_object_patches(rec.ctx, out.data_ptr()))
+    return out
+
+
+def warm_start(rec, net):
+    """ptycho_warm_start: stitch the network's predicted patches into rec's object."""
+    _check(rec.ctx, lib().ptycho_warm_start(rec.ctx, net.h))
 
 
 def to_pixels(wavelength_m: float, distance_m: float, det_pixel_m: float, M: int, length_m: float) -> float:

@@ -1,0 +1,436 @@
+// Learned warm start: a convolutional encoder-decoder that maps one
+// diffraction frame, log(1 + I) of a 128 x 128 detector-centred pattern, to
+// the amplitude and phase of the central 64 x 64 object patch under the
+// probe.  Predicted patches are stitched into the initial object of a DM or
+// LSQML reconstruction (the iterations remain the judge).
+//
+// Layers (3 x 3 kernels, padding 1; "s2" = stride 2, "up" = nearest x2
+// upsampling of the input folded into the convolution's index map):
+//   128^2:  1 ->  16            relu
+//    64^2: 16 ->  32  s2        relu
+//    32^2: 32 ->  64  s2        relu
+//    16^2: 64 -> 128  s2        relu
+//     8^2: 128 -> 256 s2        relu
+//     4^2: 256 -> 256 s2, 256 -> 256   relu
+//     8^2: 256 -> 128 up        relu
+//    16^2: 128 -> 64  up        relu
+//    32^2: 64 ->  32  up        relu
+//    64^2: 32 ->  16  up        relu, then 16 -> 2 (amplitude, phase)
+// 1,964,690 parameters (1,963,440 weights, 1,250 biases).  Weights and activations are stored in BF16, all
+// sums are FP32 (the last layer's output and every gradient are FP32).  Each
+// reduction (weight and bias gradients, loss) runs in a fixed order, so a
+// training step is deterministic.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ptycho {
+
+constexpr int NET_IN = 128, NET_OUT = 64, NET_LAYERS = 12;
+
+struct NetLayer {
+  int ci, co, hin, win, hout, wout, stride, up, relu;
+};
+
+__host__ __device__ constexpr NetLayer net_layer(int l) {
+  return l == 0    ? NetLayer{1, 16, 128, 128, 128, 128, 1, 0, 1}
+         : l == 1  ? NetLayer{16, 32, 128, 128, 64, 64, 2, 0, 1}
+         : l == 2  ? NetLayer{32, 64, 64, 64, 32, 32, 2, 0, 1}
+         : l == 3  ? NetLayer{64, 128, 32, 32, 16, 16, 2, 0, 1}
+         : l == 4  ? NetLayer{128, 256, 16, 16, 8, 8, 2, 0, 1}
+         : l == 5  ? NetLayer{256, 256, 8, 8, 4, 4, 2, 0, 1}
+         : l == 6  ? NetLayer{256, 256, 4, 4, 4, 4, 1, 0, 1}
+         : l == 7  ? NetLayer{256, 128, 4, 4, 8, 8, 1, 1, 1}
+         : l == 8  ? NetLayer{128, 64, 8, 8, 16, 16, 1, 1, 1}
+         : l == 9  ? NetLayer{64, 32, 16, 16, 32, 32, 1, 1, 1}
+         : l == 10 ? NetLayer{32, 16, 32, 32, 64, 64, 1, 1, 1}
+                   : NetLayer{16, 2, 64, 64, 64, 64, 1, 0, 0};
+}
+
+// Input coordinate of output coordinate o and tap d (0..2) of a layer, or -1
+// outside the (virtual, upsampled) input.
+__device__ __forceinline__ int net_src(int o, int d, int stride, int up, int hin) {
+  const int v = stride * o + d - 1;
+  const int hv = up ? 2 * hin : hin;
+  if (v < 0 || v >= hv) return -1;
+  return up ? (v >> 1) : v;
+}
+
+// activation storage: BF16 (the method) or FP32 (verification mode)
+__device__ __forceinline__ float ldact(const __nv_bfloat16* p, size_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ float ldact(const float* p, size_t i) { return p[i]; }
+__device__ __forceinline__ void stact(__nv_bfloat16* p, size_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void stact(float* p, size_t i, float v) { p[i] = v; }
+
+struct ConvArgs {
+  const void* in;            // [B][ci][hin][win] activations (TA)
+  const __nv_bfloat16* w;    // [co][ci][9]
+  const float* b;            // [co]
+  void* out;                 // [B][co][hout][wout], bf16 (or f32 for the last layer)
+  const float* dout;         // backward: delta of this layer [B][co][hout][wout]
+  float* din;                // backward data: delta of the previous layer
+  const void* mask;          // backward data: previous layer's output (relu mask, TA) or NULL
+  float* wpart;              // backward weights: partials [chunks][co][ci][9]
+  int B, ci, co, hin, win, hout, wout, stride, up, relu;
+};
+
+constexpr int CV_NT = 256, CV_CO = 16, CV_CI = 16;
+
+// Forward: thread = one output pixel, CV_CO output channels.
+template <typename TA, bool OUT_F32>
+__global__ void __launch_bounds__(CV_NT) k_conv_fwd(ConvArgs a) {
+  const TA* in = reinterpret_cast<const TA*>(a.in);
+  __shared__ __align__(16) float ws[CV_CI][9][CV_CO];
+  const int tid = threadIdx.x;
+  const long long npix = (long long)a.B * a.hout * a.wout;
+  const long long p = (long long)blockIdx.x * CV_NT + tid;
+  const bool valid = p < npix;
+  const int n = valid ? (int)(p / (a.hout * a.wout)) : 0;
+  const int y = valid ? (int)((p / a.wout) % a.hout) : 0;
+  const int x = valid ? (int)(p % a.wout) : 0;
+  const int co0 = blockIdx.y * CV_CO;
+  float acc[CV_CO];
+#pragma unroll
+  for (int c = 0; c < CV_CO; ++c) acc[c] = (co0 + c < a.co) ? a.b[co0 + c] : 0.f;
+  int sy[3], sx[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sy[d] = net_src(y, d, a.stride, a.up, a.hin);
+    sx[d] = net_src(x, d, a.stride, a.up, a.win);
+  }
+  for (int ci0 = 0; ci0 < a.ci; ci0 += CV_CI) {
+    __syncthreads();
+    for (int i = tid; i < CV_CI * 9 * CV_CO; i += CV_NT) {
+      const int ci = i / (9 * CV_CO), t = (i / CV_CO) % 9, c = i % CV_CO;
+      ws[ci][t][c] = (ci0 + ci < a.ci && co0 + c < a.co)
+                         ? __bfloat162float(a.w[((size_t)(co0 + c) * a.ci + ci0 + ci) * 9 + t])
+                         : 0.f;
+    }
+    __syncthreads();
+    if (valid) {
+      const int nci = min(CV_CI, a.ci - ci0);
+      for (int ci = 0; ci < nci; ++ci) {
+        const TA* src = in + ((size_t)n * a.ci + ci0 + ci) * a.hin * a.win;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          if (sy[dy] < 0) continue;
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            if (sx[dx] < 0) continue;
+            const float v = ldact(src, (size_t)sy[dy] * a.win + sx[dx]);
+            const float4* wv = reinterpret_cast<const float4*>(&ws[ci][dy * 3 + dx][0]);
+#pragma unroll
+            for (int q = 0; q < CV_CO / 4; ++q) {
+              const float4 w4 = wv[q];
+              acc[4 * q + 0] = fmaf(w4.x, v, acc[4 * q + 0]);
+              acc[4 * q + 1] = fmaf(w4.y, v, acc[4 * q + 1]);
+              acc[4 * q + 2] = fmaf(w4.z, v, acc[4 * q + 2]);
+              acc[4 * q + 3] = fmaf(w4.w, v, acc[4 * q + 3]);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (!valid) return;
+#pragma unroll
+  for (int c = 0; c < CV_CO; ++c) {
+    if (co0 + c >= a.co) continue;
+    float r = acc[c];
+    if (a.relu) r = fmaxf(r, 0.f);
+    const size_t o = (((size_t)n * a.co + co0 + c) * a.hout + y) * a.wout + x;
+    if (OUT_F32) reinterpret_cast<float*>(a.out)[o] = r;
+    else stact(reinterpret_cast<TA*>(a.out), o, r);
+  }
+}
+
+// Backward data: thread = one input pixel, CV_CI input channels:
+//   din[n][ci][iy][ix] = sum_co sum_taps w[co][ci][t] dout[n][co][y][x]
+// over the output pixels (y, x) whose tap t reads (iy, ix); multiplied by the
+// previous layer's relu derivative (mask > 0) when a mask is given.
+template <typename TA>
+__global__ void __launch_bounds__(CV_NT) k_conv_bwd_data(ConvArgs a) {
+  __shared__ __align__(16) float ws[CV_CO][9][CV_CI];
+  const int tid = threadIdx.x;
+  const long long npix = (long long)a.B * a.hin * a.win;
+  const long long p = (long long)blockIdx.x * CV_NT + tid;
+  const bool valid = p < npix;
+  const int n = valid ? (int)(p / (a.hin * a.win)) : 0;
+  const int iy = valid ? (int)((p / a.win) % a.hin) : 0;
+  const int ix = valid ? (int)(p % a.win) : 0;
+  const int ci0 = blockIdx.y * CV_CI;
+  float acc[CV_CI];
+#pragma unroll
+  for (int c = 0; c < CV_CI; ++c) acc[c] = 0.f;
+  // output rows / columns reading this input row / column, per tap (<= 2 each
+  // with upsampling: the two virtual rows 2 iy and 2 iy + 1)
+  int oy[3][2], ox[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      oy[d][h] = -1;
+      ox[d][h] = -1;
+      if (h == 1 && !a.up) continue;
+      const int vy = a.up ? 2 * iy + h : iy, vx = a.up ? 2 * ix + h : ix;
+      const int ty = vy + 1 - d, tx = vx + 1 - d;
+      if (ty >= 0 && ty % a.stride == 0 && ty / a.stride < a.hout) oy[d][h] = ty / a.stride;
+      if (tx >= 0 && tx % a.stride == 0 && tx / a.stride < a.wout) ox[d][h] = tx / a.stride;
+    }
+  }
+  for (int co0 = 0; co0 < a.co; co0 += CV_CO) {
+    __syncthreads();
+    for (int i = tid; i < CV_CO * 9 * CV_CI; i += CV_NT) {
+      const int c = i / (9 * CV_CI), t = (i / CV_CI) % 9, ci = i % CV_CI;
+      ws[c][t][ci] = (co0 + c < a.co && ci0 + ci < a.ci)
+                         ? __bfloat162float(a.w[((size_t)(co0 + c) * a.ci + ci0 + ci) * 9 + t])
+                         : 0.f;
+    }
+    __syncthreads();
+    if (valid) {
+      const int nco = min(CV_CO, a.co - co0);
+      for (int c = 0; c < nco; ++c) {
+        const float* g = a.dout + ((size_t)n * a.co + co0 + c) * a.hout * a.wout;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int hy = 0; hy < 2; ++hy) {
+            if (oy[dy][hy] < 0) continue;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+              for (int hx = 0; hx < 2; ++hx) {
+                if (ox[dx][hx] < 0) continue;
+                const float gv = g[oy[dy][hy] * a.wout + ox[dx][hx]];
+                const float4* wv = reinterpret_cast<const float4*>(&ws[c][dy * 3 + dx][0]);
+#pragma unroll
+                for (int q = 0; q < CV_CI / 4; ++q) {
+                  const float4 w4 = wv[q];
+                  acc[4 * q + 0] = fmaf(w4.x, gv, acc[4 * q + 0]);
+                  acc[4 * q + 1] = fmaf(w4.y, gv, acc[4 * q + 1]);
+                  acc[4 * q + 2] = fmaf(w4.z, gv, acc[4 * q + 2]);
+                  acc[4 * q + 3] = fmaf(w4.w, gv, acc[4 * q + 3]);
+                }
+              }
+          }
+      }
+    }
+  }
+  if (!valid) return;
+#pragma unroll
+  for (int c = 0; c < CV_CI; ++c) {
+    if (ci0 + c >= a.ci) continue;
+    const size_t o = (((size_t)n * a.ci + ci0 + c) * a.hin + iy) * a.win + ix;
+    float r = acc[c];
+    if (a.mask && !(ldact(reinterpret_cast<const TA*>(a.mask), o) > 0.f)) r = 0.f;
+    a.din[o] = r;
+  }
+}
+
+// Backward weights, stage 1: CTA = (co, 4 input channels, chunk of output
+// pixels); per-thread FP32 sums, fixed-order block reduction, one partial per
+// chunk.
+constexpr int BW_CI = 4, BW_CHUNK = 4096;
+template <typename TA>
+__global__ void __launch_bounds__(CV_NT) k_conv_bwd_w(ConvArgs a) {
+  const TA* in = reinterpret_cast<const TA*>(a.in);
+  __shared__ float red[CV_NT / 32][BW_CI * 9];
+  const int tid = threadIdx.x;
+  const int nciq = (a.ci + BW_CI - 1) / BW_CI;
+  const int co = blockIdx.x / nciq, ci0 = (blockIdx.x % nciq) * BW_CI;
+  const long long npix = (long long)a.B * a.hout * a.wout;
+  const long long p0 = (long long)blockIdx.y * BW_CHUNK;
+  const long long p1 = min(npix, p0 + BW_CHUNK);
+  float acc[BW_CI][9];
+#pragma unroll
+  for (int c = 0; c < BW_CI; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[c][t] = 0.f;
+  for (long long p = p0 + tid; p < p1; p += CV_NT) {
+    const int n = (int)(p / (a.hout * a.wout));
+    const int y = (int)((p / a.wout) % a.hout), x = (int)(p % a.wout);
+    const float g = a.dout[(((size_t)n * a.co + co) * a.hout + y) * a.wout + x];
+    int sy[3], sx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      sy[d] = net_src(y, d, a.stride, a.up, a.hin);
+      sx[d] = net_src(x, d, a.stride, a.up, a.win);
+    }
+#pragma unroll
+    for (int c = 0; c < BW_CI; ++c) {
+      if (ci0 + c >= a.ci) continue;
+      const TA* src = in + ((size_t)n * a.ci + ci0 + c) * a.hin * a.win;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          if (sy[dy] < 0 || sx[dx] < 0) continue;
+          acc[c][dy * 3 + dx] = fmaf(g, ldact(src, (size_t)sy[dy] * a.win + sx[dx]), acc[c][dy * 3 + dx]);
+        }
+    }
+  }
+  // warp tree, then warps in order
+  const int lane = tid & 31, wp = tid >> 5;
+#pragma unroll
+  for (int c = 0; c < BW_CI; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      float v = acc[c][t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wp][c * 9 + t] = v;
+    }
+  __syncthreads();
+  if (tid < BW_CI * 9) {
+    float s = 0.f;
+    for (int w = 0; w < CV_NT / 32; ++w) s += red[w][tid];
+    const int c = tid / 9, t = tid % 9;
+    if (ci0 + c < a.ci) a.wpart[(((size_t)blockIdx.y * a.co + co) * a.ci + ci0 + c) * 9 + t] = s;
+  }
+}
+
+// Backward weights, stage 2: sum the chunk partials in order.
+__global__ void k_sum_chunks(const float* __restrict__ part, int nchunk, size_t n, float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * n + i];
+    out[i] = s;
+  }
+}
+
+// Bias gradient: one CTA per output channel, fixed-order block sum.
+__global__ void __launch_bounds__(CV_NT) k_bias_grad(const float* __restrict__ dout, int B, int co, int hw,
+                                                      float* __restrict__ db) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (long long i = threadIdx.x; i < (long long)B * hw; i += CV_NT) {
+    const int n = (int)(i / hw), r = (int)(i % hw);
+    s += dout[((size_t)n * co + c) * hw + r];
+  }
+  const double t = block_sum_d<CV_NT>((double)s, red);
+  if (threadIdx.x == 0) db[c] = (float)t;
+}
+
+// Loss L = sum (out - target)^2 / (B * 2 * 64 * 64) and its gradient.
+__global__ void __launch_bounds__(CV_NT) k_net_loss(const float* __restrict__ out, const float* __restrict__ tgt,
+                                                     size_t n, float scale, float* __restrict__ dout,
+                                                     double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)CV_NT + threadIdx.x; i < n; i += (size_t)gridDim.x * CV_NT) {
+    const float d = out[i] - tgt[i];
+    dout[i] = 2.f * d * scale;
+    s += (double)d * d;
+  }
+  const double t = block_sum_d<CV_NT>(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t * scale;
+}
+
+// AdamW on the FP32 master parameters; refreshes the BF16 weight copy.
+struct AdamArgs {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  __nv_bfloat16* wb;     // BF16 copy (weights only; NULL entries skipped via is_w)
+  const unsigned char* is_w;
+  const int* wb_index;   // position of the parameter in the BF16 copy
+  size_t n;
+  float lr, b1, b2, eps, wd, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+
+__global__ void k_adam(AdamArgs a) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.n; i += (size_t)gridDim.x * blockDim.x) {
+    const float g = a.g[i];
+    const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+    const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+    a.m[i] = m;
+    a.v[i] = v;
+    float p = a.p[i];
+    p -= a.lr * ((m / a.c1) / (sqrtf(v / a.c2) + a.eps) + (a.is_w[i] ? a.wd * p : 0.f));
+    a.p[i] = p;
+    if (a.is_w[i]) a.wb[a.wb_index[i]] = __float2bfloat16_rn(p);
+  }
+}
+
+// Network input: x = log(1 + max(I, 0)) / 10 (BF16, or FP32 in verification
+// mode), from detector-centred
+// FP32 intensities (src_fft == 0) or from stored FFT-order amplitudes sqrt(I)
+// (src_fft == 1; masked pixels count as 0).
+template <typename TA>
+__global__ void k_net_input(const void* __restrict__ src, int src_fft, int istore, const float* __restrict__ scale,
+                            int j0, int B, int M, TA* __restrict__ x) {
+  const size_t MM = (size_t)M * M;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)B * MM;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / MM;
+    const int y = (int)((i % MM) / M), xx = (int)(i % M);
+    float I;
+    if (!src_fft) {
+      I = reinterpret_cast<const float*>(src)[i];
+    } else {
+      const size_t k = (j0 + b) * MM + (size_t)((y + M / 2) % M) * M + (xx + M / 2) % M;
+      float a;
+      if (istore == 0) a = reinterpret_cast<const float*>(src)[k];
+      else if (istore == 1) a = __half2float(reinterpret_cast<const __half*>(src)[k]) * scale[j0 + b];
+      else a = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(src)[k]) * scale[j0 + b];
+      I = a > 0.f ? a * a : 0.f;
+    }
+    stact(x, i, log1pf(fmaxf(I, 0.f)) * 0.1f);
+  }
+}
+
+// Training targets: amplitude and phase of the central 64 x 64 object patch
+// of each position, [J][2][64][64].
+__global__ void k_patch_targets(const float2* __restrict__ O, int nx, const int2* __restrict__ pos, int J, int M,
+                                float* __restrict__ out) {
+  const int c0 = (M - NET_OUT) / 2;
+  const size_t per = (size_t)NET_OUT * NET_OUT;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)J * per;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i / per);
+    const int y = (int)((i % per) / NET_OUT), x = (int)(i % NET_OUT);
+    const int2 p = pos[j];
+    const float2 o = O[(size_t)(p.x + c0 + y) * nx + p.y + c0 + x];
+    out[(size_t)j * 2 * per + (size_t)y * NET_OUT + x] = sqrtf(cabs2(o));
+    out[(size_t)j * 2 * per + per + (size_t)y * NET_OUT + x] = atan2f(o.y, o.x);
+  }
+}
+
+// Stitch predicted central patches into the object: each pixel covered by at
+// least one patch becomes the mean of amp * exp(i phase) over the patches that
+// cover it; other pixels keep their value.  Tile-owned over the positions'
+// CSR lists (deterministic).
+__global__ void __launch_bounds__(256) k_stitch(float2* __restrict__ O, int ny, int nx, int ntx,
+                                                 const int* __restrict__ tile_ptr, const int* __restrict__ tile_list,
+                                                 const int2* __restrict__ pos, int M, const float* __restrict__ pred,
+                                                 int tile_y, int tile_x) {
+  const int tile = blockIdx.x;
+  const int ty0 = (tile / ntx) * tile_y, tx0 = (tile % ntx) * tile_x;
+  const int c0 = (M - NET_OUT) / 2;
+  const size_t per = (size_t)NET_OUT * NET_OUT;
+  for (int e = threadIdx.x; e < tile_y * tile_x; e += 256) {
+    const int y = ty0 + e / tile_x, x = tx0 + e % tile_x;
+    if (y >= ny || x >= nx) continue;
+    float2 s = make_float2(0.f, 0.f);
+    int cnt = 0;
+    for (int q = tile_ptr[tile]; q < tile_ptr[tile + 1]; ++q) {
+      const int j = tile_list[q];
+      const int2 p = pos[j];
+      const int uy = y - p.x - c0, ux = x - p.y - c0;
+      if (uy < 0 || uy >= NET_OUT || ux < 0 || ux >= NET_OUT) continue;
+      const float amp = pred[(size_t)j * 2 * per + (size_t)uy * NET_OUT + ux];
+      const float ph = pred[(size_t)j * 2 * per + per + (size_t)uy * NET_OUT + ux];
+      float sn, cs;
+      sincosf(ph, &sn, &cs);
+      s.x += amp * cs;
+      s.y += amp * sn;
+      ++cnt;
+    }
+    if (cnt) O[(size_t)y * nx + x] = cscale(s, 1.f / cnt);
+  }
+}
+
+}  // namespace ptycho

@@ -1,0 +1,411 @@
+// Host side of the learned warm start (declared in include/ptycho.h):
+// parameters, buffers, the forward / backward launch sequence, AdamW, and the
+// stitching of predicted patches into a reconstruction's initial object.
+// Included by ptycho_api.cu (uses the context internals).
+
+struct ptycho_net {
+  cudaStream_t st = nullptr;
+  int max_batch = 0;
+  long long n_params = 0, n_w = 0;
+  long long w_off[NET_LAYERS], b_off[NET_LAYERS], wb_off[NET_LAYERS];
+  float* params = nullptr;   // FP32 master
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  __nv_bfloat16* wb = nullptr;  // BF16 weights
+  unsigned char* is_w = nullptr;
+  int* wb_index = nullptr;
+  bool f32 = false;             // FP32 activations (verification mode)
+  void* x = nullptr;            // input [B][1][128][128]
+  void* act[NET_LAYERS] = {};   // layers 0..10 (BF16, or FP32 in verification mode)
+  float* out = nullptr;         // layer 11 output [B][2][64][64] (FP32)
+  float* delta[2] = {nullptr, nullptr};
+  float* wpart = nullptr;
+  double* lpart = nullptr;
+  long long adam_t = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_net_error;
+
+int nfail(ptycho_net* n, int code, const char* fmt, ...) {
+  char t[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t, sizeof t, fmt, ap);
+  va_end(ap);
+  if (n) n->err = t;
+  else g_net_error = t;
+  return code;
+}
+
+template <typename T>
+int nalloc(ptycho_net* n, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return nfail(n, PTYCHO_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  return 0;
+}
+
+size_t act_size(int l, int B) {
+  const NetLayer L = net_layer(l);
+  return (size_t)B * L.co * L.hout * L.wout;
+}
+
+int net_check(ptycho_net* n, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return 0;
+}
+
+ConvArgs conv_args(ptycho_net* n, int l, int B) {
+  const NetLayer L = net_layer(l);
+  ConvArgs a{};
+  a.in = l == 0 ? n->x : n->act[l - 1];
+  a.w = n->wb + n->wb_off[l];
+  a.b = n->params + n->b_off[l];
+  a.B = B;
+  a.ci = L.ci;
+  a.co = L.co;
+  a.hin = L.hin;
+  a.win = L.win;
+  a.hout = L.hout;
+  a.wout = L.wout;
+  a.stride = L.stride;
+  a.up = L.up;
+  a.relu = L.relu;
+  return a;
+}
+
+template <typename TA>
+int net_forward_t(ptycho_net* n, int B) {
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    ConvArgs a = conv_args(n, l, B);
+    const dim3 g((unsigned)(((long long)B * L.hout * L.wout + CV_NT - 1) / CV_NT), (unsigned)((L.co + CV_CO - 1) / CV_CO));
+    if (l == NET_LAYERS - 1) {
+      a.out = n->out;
+      k_conv_fwd<TA, true><<<g, CV_NT, 0, n->st>>>(a);
+    } else {
+      a.out = n->act[l];
+      k_conv_fwd<TA, false><<<g, CV_NT, 0, n->st>>>(a);
+    }
+  }
+  return net_check(n, "forward");
+}
+
+int net_forward(ptycho_net* n, int B) {
+  return n->f32 ? net_forward_t<float>(n, B) : net_forward_t<__nv_bfloat16>(n, B);
+}
+
+// Loss against targets and all parameter gradients (into n->grads).
+int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
+  const size_t nout = (size_t)B * 2 * NET_OUT * NET_OUT;
+  const int lb = 256;
+  k_net_loss<<<lb, CV_NT, 0, n->st>>>(n->out, targets, nout, 1.f / (float)nout, n->delta[0], n->lpart);
+  int cur = 0;
+  for (int l = NET_LAYERS - 1; l >= 0; --l) {
+    const NetLayer L = net_layer(l);
+    ConvArgs a = conv_args(n, l, B);
+    a.dout = n->delta[cur];
+    a.wpart = n->wpart;
+    const long long npo = (long long)B * L.hout * L.wout;
+    const int nchunk = (int)((npo + BW_CHUNK - 1) / BW_CHUNK);
+    const int nciq = (L.ci + BW_CI - 1) / BW_CI;
+    if (n->f32) k_conv_bwd_w<float><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
+    else k_conv_bwd_w<__nv_bfloat16><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
+    const size_t nw = (size_t)L.co * L.ci * 9;
+    k_sum_chunks<<<(unsigned)std::min<size_t>((nw + 255) / 256, 1184), 256, 0, n->st>>>(n->wpart, nchunk, nw,
+                                                                                          n->grads + n->w_off[l]);
+    k_bias_grad<<<L.co, CV_NT, 0, n->st>>>(n->delta[cur], B, L.co, L.hout * L.wout, n->grads + n->b_off[l]);
+    if (l > 0) {
+      a.din = n->delta[cur ^ 1];
+      a.mask = net_layer(l - 1).relu ? n->act[l - 1] : nullptr;
+      const dim3 g((unsigned)(((long long)B * L.hin * L.win + CV_NT - 1) / CV_NT), (unsigned)((L.ci + CV_CI - 1) / CV_CI));
+      if (n->f32) k_conv_bwd_data<float><<<g, CV_NT, 0, n->st>>>(a);
+      else k_conv_bwd_data<__nv_bfloat16><<<g, CV_NT, 0, n->st>>>(a);
+      cur ^= 1;
+    }
+  }
+  if (int r = net_check(n, "backward")) return r;
+  if (loss) {
+    double part[lb];
+    cudaError_t e = cudaMemcpyAsync(part, n->lpart, sizeof part, cudaMemcpyDeviceToHost, n->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->st);
+    if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "loss: %s", cudaGetErrorString(e));
+    double s = 0.0;
+    for (int i = 0; i < lb; ++i) s += part[i];
+    *loss = s;
+  }
+  return 0;
+}
+
+int net_input_src(ptycho_net* n, const void* src, int src_fft, int istore, const float* scale, int j0, int B) {
+  if (n->f32)
+    k_net_input<float><<<1184, 256, 0, n->st>>>(src, src_fft, istore, scale, j0, B, NET_IN, (float*)n->x);
+  else
+    k_net_input<__nv_bfloat16><<<1184, 256, 0, n->st>>>(src, src_fft, istore, scale, j0, B, NET_IN,
+                                                        (__nv_bfloat16*)n->x);
+  return net_check(n, "input");
+}
+
+int net_input(ptycho_net* n, const float* intensities, int B) {
+  return net_input_src(n, intensities, 0, 0, nullptr, 0, B);
+}
+
+// SplitMix64-driven Box-Muller normals for the initial weights.
+double net_normal(uint64_t& s) {
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const double u1 = ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+int net_upload_params(ptycho_net* n, const float* host) {
+  std::vector<__nv_bfloat16> wb(n->n_w);
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    const long long nw = (long long)L.co * L.ci * 9;
+    for (long long i = 0; i < nw; ++i) wb[n->wb_off[l] + i] = __float2bfloat16_rn(host[n->w_off[l] + i]);
+  }
+  cudaError_t e = cudaMemcpy(n->params, host, n->n_params * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(n->wb, wb.data(), n->n_w * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "parameter upload: %s", cudaGetErrorString(e));
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, int flags, void* stream) {
+  if (!out || max_batch < 1 || max_batch > 4096 || (flags & ~PTYCHO_NET_F32_ACTIVATIONS))
+    return nfail(nullptr, PTYCHO_ERR_ARG, "bad arguments");
+  *out = nullptr;
+  ptycho_net* n = new ptycho_net();
+  n->f32 = (flags & PTYCHO_NET_F32_ACTIVATIONS) != 0;
+  n->st = (cudaStream_t)stream;
+  n->max_batch = max_batch;
+  long long off = 0, woff = 0;
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    n->w_off[l] = off;
+    off += (long long)L.co * L.ci * 9;
+    n->b_off[l] = off;
+    off += L.co;
+    n->wb_off[l] = woff;
+    woff += (long long)L.co * L.ci * 9;
+  }
+  n->n_params = off;
+  n->n_w = woff;
+  size_t maxd = 0, maxpart = 0;
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    maxd = std::max(maxd, (size_t)max_batch * L.co * L.hout * L.wout);
+    maxd = std::max(maxd, (size_t)max_batch * L.ci * L.hin * L.win);
+    const long long npo = (long long)max_batch * L.hout * L.wout;
+    maxpart = std::max(maxpart, (size_t)((npo + BW_CHUNK - 1) / BW_CHUNK) * L.co * L.ci * 9);
+  }
+  int r = 0;
+  if (!r) r = nalloc(n, &n->params, n->n_params);
+  if (!r) r = nalloc(n, &n->grads, n->n_params);
+  if (!r) r = nalloc(n, &n->m, n->n_params);
+  if (!r) r = nalloc(n, &n->v, n->n_params);
+  if (!r) r = nalloc(n, &n->wb, n->n_w);
+  if (!r) r = nalloc(n, &n->is_w, n->n_params);
+  if (!r) r = nalloc(n, &n->wb_index, n->n_params);
+  const size_t asz = n->f32 ? 4 : 2;
+  if (!r) r = nalloc(n, (unsigned char**)&n->x, (size_t)max_batch * NET_IN * NET_IN * asz);
+  for (int l = 0; l + 1 < NET_LAYERS && !r; ++l) r = nalloc(n, (unsigned char**)&n->act[l], act_size(l, max_batch) * asz);
+  if (!r) r = nalloc(n, &n->out, act_size(NET_LAYERS - 1, max_batch));
+  if (!r) r = nalloc(n, &n->delta[0], maxd);
+  if (!r) r = nalloc(n, &n->delta[1], maxd);
+  if (!r) r = nalloc(n, &n->wpart, maxpart);
+  if (!r) r = nalloc(n, &n->lpart, 256);
+  if (r) {
+    g_net_error = n->err;
+    ptycho_net_destroy(n);
+    return r;
+  }
+  // He-normal weights (std = sqrt(2 / (9 ci))), zero biases, from SplitMix64(seed)
+  std::vector<float> p(n->n_params, 0.f);
+  std::vector<unsigned char> isw(n->n_params, 0);
+  std::vector<int> idx(n->n_params, 0);
+  uint64_t s = seed;
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    const double sd = std::sqrt(2.0 / (9.0 * L.ci));
+    const long long nw = (long long)L.co * L.ci * 9;
+    for (long long i = 0; i < nw; ++i) {
+      p[n->w_off[l] + i] = (float)(sd * net_normal(s));
+      isw[n->w_off[l] + i] = 1;
+      idx[n->w_off[l] + i] = (int)(n->wb_off[l] + i);
+    }
+  }
+  cudaError_t e = cudaMemcpy(n->is_w, isw.data(), isw.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(n->wb_index, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(n->m, 0, n->n_params * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->v, 0, n->n_params * sizeof(float));
+  int rc = e == cudaSuccess ? net_upload_params(n, p.data()) : PTYCHO_ERR_CUDA;
+  if (rc) {
+    g_net_error = n->err.empty() ? std::string(cudaGetErrorString(e)) : n->err;
+    ptycho_net_destroy(n);
+    return rc;
+  }
+  *out = n;
+  return PTYCHO_OK;
+}
+
+long long ptycho_net_num_params(const ptycho_net* n) { return n ? n->n_params : -1; }
+
+int ptycho_net_get_params(ptycho_net* n, float* out) {
+  if (!n || !out) return PTYCHO_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(out, n->params, n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->st);
+  if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "get_params: %s", cudaGetErrorString(e));
+  return PTYCHO_OK;
+}
+
+int ptycho_net_set_params(ptycho_net* n, const float* in) {
+  if (!n || !in) return PTYCHO_ERR_ARG;
+  for (long long i = 0; i < n->n_params; ++i)
+    if (!std::isfinite(in[i])) return nfail(n, PTYCHO_ERR_NONFINITE, "parameter %lld is not finite", i);
+  if (cudaStreamSynchronize(n->st) != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "sync");
+  n->adam_t = 0;
+  cudaMemset(n->m, 0, n->n_params * sizeof(float));
+  cudaMemset(n->v, 0, n->n_params * sizeof(float));
+  return net_upload_params(n, in);
+}
+
+int ptycho_net_predict(ptycho_net* n, const float* intensities, int B, float* out) {
+  if (!n || !intensities || !out) return PTYCHO_ERR_ARG;
+  if (B < 1 || B > n->max_batch) return nfail(n, PTYCHO_ERR_ARG, "batch %d outside [1, %d]", B, n->max_batch);
+  if (int r = net_input(n, intensities, B)) return r;
+  if (int r = net_forward(n, B)) return r;
+  cudaError_t e = cudaMemcpyAsync(out, n->out, act_size(NET_LAYERS - 1, B) * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  n->st);
+  if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "predict: %s", cudaGetErrorString(e));
+  return PTYCHO_OK;
+}
+
+int ptycho_net_gradients(ptycho_net* n, const float* intensities, const float* targets, int B, float* grads,
+                         double* loss) {
+  if (!n || !intensities || !targets) return PTYCHO_ERR_ARG;
+  if (B < 1 || B > n->max_batch) return nfail(n, PTYCHO_ERR_ARG, "batch %d outside [1, %d]", B, n->max_batch);
+  if (int r = net_input(n, intensities, B)) return r;
+  if (int r = net_forward(n, B)) return r;
+  if (int r = net_backward(n, targets, B, loss)) return r;
+  if (grads) {
+    cudaError_t e = cudaMemcpyAsync(grads, n->grads, n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->st);
+    if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "gradients: %s", cudaGetErrorString(e));
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_net_train_step(ptycho_net* n, const float* intensities, const float* targets, int B, float lr,
+                          double* loss) {
+  if (!n || !intensities || !targets) return PTYCHO_ERR_ARG;
+  if (B < 1 || B > n->max_batch) return nfail(n, PTYCHO_ERR_ARG, "batch %d outside [1, %d]", B, n->max_batch);
+  if (!(lr > 0.f) || !std::isfinite(lr)) return nfail(n, PTYCHO_ERR_ARG, "learning rate %g", lr);
+  if (int r = net_input(n, intensities, B)) return r;
+  if (int r = net_forward(n, B)) return r;
+  if (int r = net_backward(n, targets, B, loss)) return r;
+  n->adam_t++;
+  AdamArgs a{};
+  a.p = n->params;
+  a.g = n->grads;
+  a.m = n->m;
+  a.v = n->v;
+  a.wb = n->wb;
+  a.is_w = n->is_w;
+  a.wb_index = n->wb_index;
+  a.n = (size_t)n->n_params;
+  a.lr = lr;
+  a.b1 = 0.9f;
+  a.b2 = 0.999f;
+  a.eps = 1e-8f;
+  a.wd = 1e-4f;
+  a.c1 = (float)(1.0 - std::pow(0.9, (double)n->adam_t));
+  a.c2 = (float)(1.0 - std::pow(0.999, (double)n->adam_t));
+  k_adam<<<1184, 256, 0, n->st>>>(a);
+  return net_check(n, "adam");
+}
+
+const char* ptycho_net_last_error(const ptycho_net* n) { return n ? n->err.c_str() : g_net_error.c_str(); }
+
+void ptycho_net_destroy(ptycho_net* n) {
+  if (!n) return;
+  if (n->st) cudaStreamSynchronize(n->st);
+  else cudaDeviceSynchronize();
+  void* bufs[] = {n->params, n->grads, n->m,   n->v,        n->wb,       n->is_w,     n->wb_index,
+                  n->x,      n->out,   n->wpart, n->lpart, n->delta[0], n->delta[1]};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int l = 0; l < NET_LAYERS; ++l)
+    if (n->act[l]) cudaFree(n->act[l]);
+  delete n;
+}
+
+int ptycho_object_patches(ptycho_ctx* ctx, float* out) {
+  if (!ctx || !out) return PTYCHO_ERR_ARG;
+  if (!ctx->have_pos) return fail(ctx, PTYCHO_ERR_STATE, "object_patches before set_positions");
+  if (ctx->p.M < NET_OUT) return fail(ctx, PTYCHO_ERR_ARG, "M=%d is smaller than the %d-pixel patch", ctx->p.M, NET_OUT);
+  return launch(ctx, "patch_targets", 0.0, [&] {
+    k_patch_targets<<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->pos, ctx->p.J, ctx->p.M, out);
+  });
+}
+
+int ptycho_warm_start(ptycho_ctx* ctx, ptycho_net* n) {
+  if (!ctx || !n) return PTYCHO_ERR_ARG;
+  if (!ctx->have_data) return fail(ctx, PTYCHO_ERR_STATE, "warm_start before set_data");
+  if (ctx->p.M != NET_IN) return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "the network takes %d-pixel frames", NET_IN);
+  // predictions for all positions, batch by batch (ordered on the context stream)
+  const int J = ctx->p.J;
+  float* pred = nullptr;
+  if (int r = dalloc(ctx, &pred, (size_t)J * 2 * NET_OUT * NET_OUT)) return r;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, ctx->st);
+  cudaStreamWaitEvent(n->st, ev, 0);
+  int rc = 0;
+  for (int j0 = 0; j0 < J && !rc; j0 += n->max_batch) {
+    const int B = std::min(n->max_batch, J - j0);
+    rc = net_input_src(n, ctx->amp, 1, ctx->p.istore, ctx->amp_scale, j0, B);
+    if (!rc) rc = net_forward(n, B);
+    if (!rc && cudaMemcpyAsync(pred + (size_t)j0 * 2 * NET_OUT * NET_OUT, n->out,
+                               act_size(NET_LAYERS - 1, B) * sizeof(float), cudaMemcpyDeviceToDevice,
+                               n->st) != cudaSuccess)
+      rc = PTYCHO_ERR_CUDA;
+  }
+  cudaEventRecord(ev, n->st);
+  cudaStreamWaitEvent(ctx->st, ev, 0);
+  cudaEventDestroy(ev);
+  if (rc) {
+    cudaFree(pred);
+    return fail(ctx, rc, "warm start prediction: %s", n->err.c_str());
+  }
+  rc = launch(ctx, "stitch", 0.0, [&] {
+    k_stitch<<<ctx->n_tiles, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_ny, ctx->p.obj_nx, ctx->ntx, ctx->tile_ptr,
+                                               ctx->tile_list, ctx->pos, ctx->p.M, pred, TILE_Y, TILE_X);
+  });
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  cudaFree(pred);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "warm start: %s", cudaGetErrorString(e));
+  ctx->psi_valid = false;
+  return PTYCHO_OK;
+}
+
+}  // extern "C"

@@ -24,6 +24,7 @@
 #include "epie.cuh"
 #include "fourier.cuh"
 #include "fourier2.cuh"
+#include "net.cuh"
 #include "overlap.cuh"
 
 using namespace ptycho;
@@ -1194,3 +1195,4 @@ void ptycho_destroy(ptycho_ctx* ctx) {
 }  // extern "C"
 
 #include "batch.cuh"
+#include "net_api.cuh"
