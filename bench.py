@@ -213,7 +213,7 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7):
                         "spirals, spacing 0.15 M), Poisson 1e4-1e6 photons/frame; one CUDA graph per iteration"}
 
 
-def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=100, check=5):
+def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
     """Wall time and iterations for 16-bit amplitude storage to reach the
     Fourier error that plain FP32 LSQML reaches after n_ref iterations.  Every
     run is judged by the same FP32-stored context (its (O, P) copied over at
@@ -254,6 +254,70 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=100, check=5):
                                      "measured against the FP32 data", "check_every": check, **out}
 
 
+def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, check=5):
+    """Learned warm start on a 1600-position, 3-mode 128^2 scan: network
+    training (one-off, reported apart), then iterations and wall time to the
+    Fourier error the plain FP32 LSQML reaches from a flat object after n_ref
+    iterations, for: flat start; warm start; warm start with FP16 storage."""
+    from paper_2202_03144_b300 import synth, warmstart
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    frames, targets, _ = warmstart.make_training_set(n_frames, seed=3, per_object=25000)
+    t_data = time.perf_counter() - t0
+    net = api.Net(seed=11, max_batch=64)
+    losses, t_train = warmstart.train(net, frames, targets, epochs=epochs, batch=64, lr=1e-3, log_every=500)
+    del frames, targets
+    d = synth.scan_config("modes128", seed=5)
+    M, K, pos = d["M"], d["K"], d["positions"]
+    shape = d["object"].shape
+    with torch.cuda.stream(stream):
+        sim = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream)
+        sim.set_positions(pos)
+        sim.set_init(d["object"], d["probe"])
+        I = torch.empty((len(pos), M, M), dtype=torch.float32, device="cuda")
+        sim.simulate(I)
+        torch.cuda.synchronize()
+        sim.close()
+        sc = d["photons"] / float(I.sum(dim=(1, 2)).mean())
+        I = torch.poisson(I * sc, generator=torch.Generator(device="cuda").manual_seed(17))
+    P0 = d["probe0"] * np.sqrt(float(I.sum(dim=(1, 2)).mean()) / (M * M) / np.sum(np.abs(d["probe0"]) ** 2))
+    scan = dict(M=M, K=K, positions=pos, object0=d["object0"], probe0=P0)
+    res = warmstart.compare(net, scan, I, alg="lsqml", n_ref=n_ref, check=check, stream=stream.cuda_stream)
+    # warm start + 16-bit amplitude storage, judged on the FP32 data
+    with torch.cuda.stream(stream):
+        judge = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream)
+        judge.set_data(I, pos)
+        r = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream, istore="f16")
+        r.set_data(I, pos)
+        r.set_init(scan["object0"], scan["probe0"])
+        Ob = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        Pb = torch.empty((K, M, M), dtype=torch.complex64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.warm_start(r, net)
+        it, E = 0, None
+        while it < 2 * n_ref:
+            r.iterate("lsqml", check)
+            it += check
+            r.get_object(Ob)
+            r.get_probe(Pb)
+            judge.set_init(Ob, Pb)
+            E = judge.fourier_error()
+            if E <= res["eps"]:
+                break
+        res["warm_f16"] = {"iterations": it, "seconds": time.perf_counter() - t0, "final_error": E,
+                           "reached": bool(E <= res["eps"])}
+        r.close()
+        judge.close()
+    net.close()
+    res["training"] = {"frames": n_frames, "epochs": epochs, "seconds": t_train, "data_seconds": t_data,
+                       "frames_per_s": n_frames * epochs / t_train, "loss_first": losses[0][1],
+                       "loss_last": losses[-1][1], "parameters": 1964690}
+    res["workload"] = ("LSQML on 1600 Fermat-spiral positions (20 px mean spacing), 3-mode 128^2 probe, 1088^2 "
+                       "object, Poisson 1e5; net trained on frames simulated from other seeded objects")
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,6 +330,8 @@ def main():
     ap.add_argument("--cluster", type=int, default=0, help="FFT cluster size (0 = library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-eps", action="store_true", help="skip the time-to-epsilon runs")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--warm-frames", type=int, default=200_000)
     args = ap.parse_args()
     if args.small:
         WORKLOAD["grid"] = 20
@@ -389,6 +455,8 @@ def main():
                    f"get_object + get_probe to host"}
     batched = None if (args.no_batch or args.small) else run_batched(api, torch, stream)
     t2e = None if (args.no_eps or args.small) else time_to_eps(api, torch, stream, I, pos, P0s, w)
+    del I
+    warm = None if (args.no_warm or args.small) else run_warm_start(api, torch, stream, n_frames=args.warm_frames)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -412,6 +480,7 @@ def main():
         },
         "batched": batched,
         "time_to_eps": t2e,
+        "warm_start": warm,
         "roofline": roof,
         "cpu_baseline": cb,
         "e2e": e2e,
