@@ -1,0 +1,104 @@
+"""Parity at the full size of the headline workload, in the launch
+configuration bench.py times (256^2 detector, 10,000 positions on a 100 x 100
+raster at step 24 px, 2640^2 object, 16-CTA clusters).
+
+The FP64 oracle cannot run 10,000 frames in a test, so:
+* sampled outputs it computes one by one: the Fourier residual and the
+  forward model of 8 positions spread over the scan (corners, edges, middle);
+* properties that hold at any size: whole mode == step mode bit for bit, and
+  noise-free data is a fixed point of one LSQML and one DM iteration.
+The residual of a position depends only on its own frame: the sampled
+positions get noisy frames of the true object from the oracle's forward model,
+all others seeded synthetic frames.  The residual is taken at a start whose
+far field covers the data's band: where data asks for amplitude and the
+model's far field is at rounding-noise level (a flat object under a smooth
+probe), the projected phase is noise-determined in FP32 and FP64 alike."""
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from paper_2202_03144_b300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+M, K, G, STEP = 256, 1, 100, 24
+SAMPLE = [0, 99, 9900, 9999, 4950, 5049, 1234, 8765]
+
+
+@pytest.fixture(scope="module")
+def workload():
+    P = synth.make_probe(M, K, R=80.0, sigma=16.0, c=0.00125)
+    pos = synth.raster_positions(G, G, STEP, 2, 2, seed=2000)
+    O = synth.make_object(2640, 2640, seed=1000)
+    P0 = synth.make_probe(M, K, R=88.0, sigma=16.0, c=0.00125)
+    rng = np.random.default_rng(77)
+    I = rng.gamma(0.5, 40.0, size=(G * G, M, M)).astype(np.float32)
+    Is = orc.far_field_intensity(O, P, orc.round_positions(pos[SAMPLE]))
+    I[SAMPLE] = synth.poisson(Is * 1e5 / Is.sum(axis=(1, 2)).mean(), seed=78).astype(np.float32)
+    I[:, :3, :3] = -1.0  # a few masked pixels in every frame
+    return P, O, pos, P0, I
+
+
+def test_fullsize_residual_and_forward_sampled(workload):
+    torch = pytest.importorskip("torch")
+    P, O, pos, P0, I = workload
+    J = len(pos)
+    # a start whose far field covers the data's band (another random object,
+    # the probe with 10% noise), so the projection is well conditioned
+    O0 = synth.make_object(2640, 2640, seed=1001)
+    P0 = synth.noisy_probe(P, 0.1, seed=79)
+    with api.Reconstruction(M, K, J, O.shape) as r:
+        assert r.cluster == 16
+        r.set_data(I, pos)
+        r.set_init(O0, P0)
+        chi = torch.empty((J, K, M, M), dtype=torch.complex64, device="cuda")
+        r.fourier_residual(chi)
+        torch.cuda.synchronize()
+        got = chi[SAMPLE].cpu().numpy()
+        del chi
+        r.set_init(O, P)
+        Isim = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        r.simulate(Isim)
+        torch.cuda.synchronize()
+        Ig = Isim[SAMPLE].cpu().numpy()
+    pi = orc.round_positions(pos[SAMPLE])
+    ref = orc.fourier_residual(O0, P0, pi, I[SAMPLE].astype(np.float64))
+    for s in range(len(SAMPLE)):
+        e = np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s])
+        assert e < 2e-5, (SAMPLE[s], e)
+    Iref = orc.far_field_intensity(O, P, pi)
+    for s in range(len(SAMPLE)):
+        e = np.linalg.norm(Ig[s] - Iref[s]) / np.linalg.norm(Iref[s])
+        assert e < 2e-5, (SAMPLE[s], e)
+
+
+def test_fullsize_step_mode_equals_whole_mode(workload):
+    P, O, pos, P0, I = workload
+    outs = []
+    for steps in ([2], [1, 1]):
+        with api.Reconstruction(M, K, len(pos), O.shape) as r:
+            r.set_data(I, pos)
+            r.set_init(np.ones_like(O), P0)
+            for n in steps:
+                r.iterate("lsqml", n)
+            outs.append((r.get_object(), r.get_probe()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("alg", ["lsqml", "dm"])
+def test_fullsize_truth_is_a_fixed_point(workload, alg):
+    torch = pytest.importorskip("torch")
+    P, O, pos, P0, _ = workload
+    J = len(pos)
+    with api.Reconstruction(M, K, J, O.shape) as r:
+        r.set_positions(pos)
+        r.set_init(O, P)
+        Isim = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        r.simulate(Isim)
+        torch.cuda.synchronize()
+        r.set_data(Isim, pos)
+        r.set_init(O, P)
+        r.iterate(alg, 1)
+        O1, P1 = r.get_object(), r.get_probe()
+    assert np.linalg.norm(O1 - O) / np.linalg.norm(O) < 1e-5
+    assert np.linalg.norm(P1 - P) / np.linalg.norm(P) < 1e-5
