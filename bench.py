@@ -254,6 +254,41 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
                                      "measured against the FP32 data", "check_every": check, **out}
 
 
+def run_epie(api, torch, stream, iters=3, warm=1):
+    """ePIE (sequential by definition) on the 3-mode 128^2 spiral scan:
+    positions*iterations/s of the persistent single-cluster kernel."""
+    from paper_2202_03144_b300 import synth
+    d = synth.scan_config("modes128", seed=5)
+    M, K, pos = d["M"], d["K"], d["positions"]
+    shape = d["object"].shape
+    with torch.cuda.stream(stream):
+        r = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream, seed=1)
+        r.set_positions(pos)
+        r.set_init(d["object"], d["probe"])
+        I = torch.empty((len(pos), M, M), dtype=torch.float32, device="cuda")
+        r.simulate(I)
+        torch.cuda.synchronize()
+        sc = d["photons"] / float(I.sum(dim=(1, 2)).mean())
+        I = torch.poisson(I * sc, generator=torch.Generator(device="cuda").manual_seed(21))
+        P0 = d["probe0"] * np.sqrt(float(I.sum(dim=(1, 2)).mean()) / (M * M) / np.sum(np.abs(d["probe0"]) ** 2))
+        r.set_data(I, pos)
+        r.set_init(d["object0"], P0)
+        r.iterate("epie", warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.iterate("epie", iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        cl = r.cluster
+        E = r.fourier_error()
+        r.close()
+    return {"value": len(pos) * iters / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms / iters,
+            "cluster": cl, "fourier_error": E,
+            "workload": "ePIE, 1600-position Fermat spiral, 3-mode 128^2 probe, 1088^2 object, Poisson 1e5"}
+
+
 def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, check=5):
     """Learned warm start on a 1600-position, 3-mode 128^2 scan: network
     training (one-off, reported apart), then iterations and wall time to the
@@ -264,7 +299,7 @@ def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, che
     t0 = time.perf_counter()
     frames, targets, _ = warmstart.make_training_set(n_frames, seed=3, per_object=25000)
     t_data = time.perf_counter() - t0
-    net = api.Net(seed=11, max_batch=64)
+    net = api.Net(seed=11, max_batch=256)  # training uses batches of 64; inference up to 256
     losses, t_train = warmstart.train(net, frames, targets, epochs=epochs, batch=64, lr=1e-3, log_every=500)
     del frames, targets
     d = synth.scan_config("modes128", seed=5)
@@ -456,6 +491,7 @@ def main():
     batched = None if (args.no_batch or args.small) else run_batched(api, torch, stream)
     t2e = None if (args.no_eps or args.small) else time_to_eps(api, torch, stream, I, pos, P0s, w)
     del I
+    epie = None if args.small else run_epie(api, torch, stream)
     warm = None if (args.no_warm or args.small) else run_warm_start(api, torch, stream, n_frames=args.warm_frames)
     if rank != 0:
         if dist:
@@ -481,6 +517,7 @@ def main():
         "batched": batched,
         "time_to_eps": t2e,
         "warm_start": warm,
+        "epie": epie,
         "roofline": roof,
         "cpu_baseline": cb,
         "e2e": e2e,

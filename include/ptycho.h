@@ -226,8 +226,10 @@ int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position);
  * layers, weights [co][ci][3][3] then biases [co].
  * ptycho_net_create: He-normal weights from SplitMix64(seed), zero biases;
  *   max_batch bounds B in the calls below; flags = 0 (BF16 activations, the
- *   method) or PTYCHO_NET_F32_ACTIVATIONS (same kernels with FP32 activation
- *   storage, for checking the kernels against an unrounded reference);
+ *   method; forward convolutions as implicit GEMMs on the tcgen05 tensor
+ *   cores, backward on CUDA cores), PTYCHO_NET_F32_ACTIVATIONS (CUDA-core
+ *   kernels with FP32 activation storage, for checking the kernels against an
+ *   unrounded reference) or PTYCHO_NET_CUDA_CORES (BF16, CUDA-core forward);
  *   stream as for contexts.
  * ptycho_net_predict: intensities device [B][128][128] (detector-centred);
  *   out device [B][2][64][64] (amplitude, phase).
@@ -243,7 +245,9 @@ int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position);
  *   128) from its stored data and writes their per-pixel mean into ctx's
  *   object where at least one patch covers it.  Synchronises. */
 typedef struct ptycho_net ptycho_net;
-#define PTYCHO_NET_F32_ACTIVATIONS 1
+#define PTYCHO_NET_F32_ACTIVATIONS 1 /* FP32 activation storage (verification)      */
+#define PTYCHO_NET_CUDA_CORES 2      /* forward convolutions on CUDA cores instead of
+                                        the tensor cores (comparison)               */
 int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, int flags, void* stream);
 long long ptycho_net_num_params(const ptycho_net* n);
 int ptycho_net_get_params(ptycho_net* n, float* out);

@@ -439,9 +439,10 @@ class Net:
     float32 torch CUDA tensors ([B,128,128] detector-centred intensities,
     [B,2,64,64] amplitude/phase); parameters are host float32 arrays."""
 
-    def __init__(self, seed=0, max_batch=64, stream=None, f32_activations=False):
+    def __init__(self, seed=0, max_batch=64, stream=None, f32_activations=False, cuda_cores=False):
         h = C.c_void_p()
-        rc = lib().ptycho_net_create(C.byref(h), seed, max_batch, 1 if f32_activations else 0, stream)
+        flags = (1 if f32_activations else 0) | (2 if cuda_cores else 0)
+        rc = lib().ptycho_net_create(C.byref(h), seed, max_batch, flags, stream)
         if rc != 0:
             raise PtychoError(rc, (lib().ptycho_net_last_error(None) or b"").decode())
         self.h = h

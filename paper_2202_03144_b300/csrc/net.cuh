@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace ptycho {
 
@@ -142,6 +143,185 @@ __global__ void __launch_bounds__(CV_NT) k_conv_fwd(ConvArgs a) {
     const size_t o = (((size_t)n * a.co + co0 + c) * a.hout + y) * a.wout + x;
     if (OUT_F32) reinterpret_cast<float*>(a.out)[o] = r;
     else stact(reinterpret_cast<TA*>(a.out), o, r);
+  }
+}
+
+// Forward on the tensor cores (implicit GEMM): D[pixel][co] =
+// sum_k A[pixel][k] B[co][k] with k = ci * 9 + tap, A gathered from the
+// BF16 activations (im2col, zero outside the input), B = the BF16 weights.
+// CTA = 128 output pixels x all output channels (NP = co rounded up to 16)
+// x one slice of the K chunks (split-K for the deep layers, whose few pixels
+// would otherwise leave most SMs idle).  Two shared-memory stages: the 128
+// threads gather chunk c+1 into one stage while the tensor cores run the four
+// K=16 MMAs of chunk c from the other; each stage's mbarrier phase tells when
+// its MMAs are done.  The FP32 accumulator lives in tensor memory.
+// Epilogue: tensor memory -> registers -> bias, ReLU, BF16 store (ksplit = 1)
+// or an FP32 partial tile (ksplit > 1, summed in order by k_conv_tc_reduce).
+constexpr int TC_KC = 64;
+template <int NP>
+__host__ __device__ constexpr int tc_ncols() { return NP < 32 ? 32 : NP; }
+template <int NP>
+__host__ __device__ constexpr size_t conv_tc_smem() {
+  return 2 * ((size_t)128 * TC_KC * 2 + (size_t)NP * TC_KC * 2) + 64;
+}
+
+template <bool OUT_F32, int NP>
+__global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvArgs a, int ksplit, float* part, int* err_flag) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr size_t ABYTES = 128 * TC_KC * 2, BBYTES = (size_t)NP * TC_KC * 2;
+  unsigned char* stage[2] = {smem_raw, smem_raw + ABYTES + BBYTES};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (ABYTES + BBYTES));  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  constexpr uint32_t LBO = 128, SBO = (TC_KC / 8) * 128;
+  constexpr uint32_t NCOLS = tc_ncols<NP>();
+  const __nv_bfloat16* in = reinterpret_cast<const __nv_bfloat16*>(a.in);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long npix = (long long)a.B * a.hout * a.wout;
+  const long long p = (long long)blockIdx.x * 128 + tid;
+  const bool valid = p < npix;
+  const int n = valid ? (int)(p / (a.hout * a.wout)) : 0;
+  const int y = valid ? (int)((p / a.wout) % a.hout) : 0;
+  const int x = valid ? (int)(p % a.wout) : 0;
+  int off[9];  // input offset of each tap within a channel plane, -1 outside
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int yy = net_src(y, t / 3, a.stride, a.up, a.hin), xx = net_src(x, t % 3, a.stride, a.up, a.win);
+    off[t] = (valid && yy >= 0 && xx >= 0) ? yy * a.win + xx : -1;
+  }
+  if (tid == 0) {
+    tc::mbar_init1(&bar[0]);
+    tc::mbar_init1(&bar[1]);
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, NCOLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  const int K = a.ci * 9;
+  const int nchunk = (K + TC_KC - 1) / TC_KC;
+  const int c_begin = (int)(((long long)nchunk * blockIdx.y) / ksplit);
+  const int c_end = (int)(((long long)nchunk * (blockIdx.y + 1)) / ksplit);
+  const size_t plane = (size_t)a.hin * a.win;
+  const __nv_bfloat16* src = in + (size_t)n * a.ci * plane;
+  const bool wvec = (K % 8) == 0;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+  uint32_t ph[2] = {0u, 0u};
+  bool pending[2] = {false, false};  // a commit on this stage not yet waited for
+  bool ok = true;
+  for (int c = c_begin; c < c_end; ++c) {
+    const int s = (c - c_begin) & 1;
+    if (pending[s]) {  // the MMAs that read this stage two chunks ago must be done
+      if (!tc::mbar_wait(&bar[s], ph[s])) ok = false;
+      ph[s] ^= 1u;
+      pending[s] = false;
+      tc::fence_after();
+    }
+    unsigned char* As = stage[s];
+    unsigned char* Bs = stage[s] + ABYTES;
+    const int k0 = c * TC_KC;
+    // A: this thread's pixel (row tid), 64 values of k = ci * 9 + tap
+    int ci = k0 / 9, t = k0 - 9 * (k0 / 9);
+#pragma unroll
+    for (int g = 0; g < TC_KC / 8; ++g) {
+      __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        // select off[t] without indexing the register array
+        const int o = t < 3 ? (t == 0 ? off[0] : t == 1 ? off[1] : off[2])
+                            : t < 6 ? (t == 3 ? off[3] : t == 4 ? off[4] : off[5])
+                                    : (t == 6 ? off[6] : t == 7 ? off[7] : off[8]);
+        const bool in_k = ci < a.ci;
+        v8[e] = (in_k && o >= 0) ? src[ci * plane + o] : __float2bfloat16_rn(0.f);
+        if (++t == 9) {
+          t = 0;
+          ++ci;
+        }
+      }
+      *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = *reinterpret_cast<const uint4*>(v8);
+    }
+    // B: weight rows (output channels) tid, tid + 128
+    for (int r = tid; r < NP; r += 128) {
+#pragma unroll
+      for (int g = 0; g < TC_KC / 8; ++g) {
+        const int kb = k0 + g * 8;
+        uint4 q;
+        if (wvec && r < a.co && kb + 8 <= K) {
+          q = __ldg(reinterpret_cast<const uint4*>(a.w + (size_t)r * K + kb));
+        } else {
+          __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            v8[e] = (r < a.co && kb + e < K) ? a.w[(size_t)r * K + kb + e] : __float2bfloat16_rn(0.f);
+          q = *reinterpret_cast<const uint4*>(v8);
+        }
+        *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = q;
+      }
+    }
+    // generic-proxy writes -> visible to the tensor cores' async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 16; ++kk) {
+        const uint64_t ad = tc::smem_desc(As + kk * 2 * LBO, LBO, SBO);
+        const uint64_t bd = tc::smem_desc(Bs + kk * 2 * LBO, LBO, SBO);
+        tc::mma_bf16(tbase, ad, bd, idesc, (c > c_begin || kk > 0) ? 1u : 0u);
+      }
+      tc::commit(&bar[s]);
+    }
+    pending[s] = true;
+  }
+  // drain the stages still in flight
+  const int nloc = c_end - c_begin;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    if (pending[s] && !tc::mbar_wait(&bar[s], ph[s])) ok = false;
+  tc::fence_after();
+  if (!ok && tid == 0) atomicExch(err_flag, 1);
+  // epilogue: this warp's 32 lanes = pixels blockIdx.x*128 + 32*warp + lane
+#pragma unroll 1
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int co = c0 + j;
+        if (co >= a.co) continue;
+        if (ksplit > 1) {
+          part[((size_t)blockIdx.y * a.co + co) * npix + p] = nloc > 0 ? v[j] : 0.f;
+          continue;
+        }
+        float r = v[j] + a.b[co];
+        if (a.relu) r = fmaxf(r, 0.f);
+        const size_t o = (((size_t)n * a.co + co) * a.hout + y) * a.wout + x;
+        if (OUT_F32) reinterpret_cast<float*>(a.out)[o] = r;
+        else reinterpret_cast<__nv_bfloat16*>(a.out)[o] = __float2bfloat16_rn(r);
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tbase, NCOLS);
+}
+
+// Split-K epilogue: out = act(bias + sum of the ksplit partial tiles, in order).
+template <bool OUT_F32>
+__global__ void k_conv_tc_reduce(ConvArgs a, int ksplit, const float* __restrict__ part) {
+  const long long npix = (long long)a.B * a.hout * a.wout;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix * a.co;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int co = (int)(i / npix);
+    const long long p = i % npix;
+    float r = a.b[co];
+    for (int s = 0; s < ksplit; ++s) r += part[((size_t)s * a.co + co) * npix + p];
+    if (a.relu) r = fmaxf(r, 0.f);
+    const int n = (int)(p / (a.hout * a.wout));
+    const int yx = (int)(p % (a.hout * a.wout));
+    const size_t o = ((size_t)n * a.co + co) * a.hout * a.wout + yx;
+    if (OUT_F32) reinterpret_cast<float*>(a.out)[o] = r;
+    else reinterpret_cast<__nv_bfloat16*>(a.out)[o] = __float2bfloat16_rn(r);
   }
 }
 

@@ -16,6 +16,10 @@ struct ptycho_net {
   unsigned char* is_w = nullptr;
   int* wb_index = nullptr;
   bool f32 = false;             // FP32 activations (verification mode)
+  bool tc = true;               // forward convolutions on the tensor cores (BF16 mode)
+  int* err_flag = nullptr;      // set by a bounded device wait that gave up
+  float* tc_part = nullptr;     // split-K partial tiles of the tensor-core forward
+  size_t tc_part_n = 0;
   void* x = nullptr;            // input [B][1][128][128]
   void* act[NET_LAYERS] = {};   // layers 0..10 (BF16, or FP32 in verification mode)
   float* out = nullptr;         // layer 11 output [B][2][64][64] (FP32)
@@ -99,8 +103,65 @@ int net_forward_t(ptycho_net* n, int B) {
   return net_check(n, "forward");
 }
 
+// split-K factor: enough CTAs for ~2 per SM, at most one K chunk each
+int tc_ksplit(const NetLayer& L, int B) {
+  const long long tiles = ((long long)B * L.hout * L.wout + 127) / 128;
+  const int nchunk = (L.ci * 9 + TC_KC - 1) / TC_KC;
+  long long ks = (2 * 148 + tiles - 1) / tiles;
+  if (ks > nchunk) ks = nchunk;
+  if (ks < 1) ks = 1;
+  return (int)ks;
+}
+
+// largest split-K scratch over every batch size up to max_batch (a smaller
+// batch can split K further)
+size_t tc_part_size(int max_batch) {
+  size_t m = 0;
+  for (int B = 1; B <= max_batch; ++B)
+    for (int l = 0; l < NET_LAYERS; ++l) {
+      const NetLayer L = net_layer(l);
+      const int ks = tc_ksplit(L, B);
+      if (ks > 1) m = std::max(m, (size_t)ks * L.co * B * L.hout * L.wout);
+    }
+  return m;
+}
+
+template <int NP>
+void launch_conv_tc(ptycho_net* n, const ConvArgs& a, const NetLayer& L, bool out_f32) {
+  const long long npix = (long long)a.B * a.hout * a.wout;
+  const int ks = tc_ksplit(L, a.B);
+  const dim3 g((unsigned)((npix + 127) / 128), (unsigned)ks);
+  if (out_f32) k_conv_fwd_tc<true, NP><<<g, 128, conv_tc_smem<NP>(), n->st>>>(a, ks, n->tc_part, n->err_flag);
+  else k_conv_fwd_tc<false, NP><<<g, 128, conv_tc_smem<NP>(), n->st>>>(a, ks, n->tc_part, n->err_flag);
+  if (ks > 1) {
+    const long long tot = npix * a.co;
+    const unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 4 * 1184);
+    if (out_f32) k_conv_tc_reduce<true><<<rb, 256, 0, n->st>>>(a, ks, n->tc_part);
+    else k_conv_tc_reduce<false><<<rb, 256, 0, n->st>>>(a, ks, n->tc_part);
+  }
+}
+
+int net_forward_tc(ptycho_net* n, int B) {
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    ConvArgs a = conv_args(n, l, B);
+    const bool last = l == NET_LAYERS - 1;
+    a.out = last ? (void*)n->out : n->act[l];
+    const int np = L.co <= 16 ? 16 : L.co;
+    switch (np) {
+      case 16: launch_conv_tc<16>(n, a, L, last); break;
+      case 32: launch_conv_tc<32>(n, a, L, last); break;
+      case 64: launch_conv_tc<64>(n, a, L, last); break;
+      case 128: launch_conv_tc<128>(n, a, L, last); break;
+      default: launch_conv_tc<256>(n, a, L, last); break;
+    }
+  }
+  return net_check(n, "forward (tensor cores)");
+}
+
 int net_forward(ptycho_net* n, int B) {
-  return n->f32 ? net_forward_t<float>(n, B) : net_forward_t<__nv_bfloat16>(n, B);
+  if (n->f32) return net_forward_t<float>(n, B);
+  return n->tc ? net_forward_tc(n, B) : net_forward_t<__nv_bfloat16>(n, B);
 }
 
 // Loss against targets and all parameter gradients (into n->grads).
@@ -190,11 +251,13 @@ int net_upload_params(ptycho_net* n, const float* host) {
 extern "C" {
 
 int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, int flags, void* stream) {
-  if (!out || max_batch < 1 || max_batch > 4096 || (flags & ~PTYCHO_NET_F32_ACTIVATIONS))
+  if (!out || max_batch < 1 || max_batch > 4096 ||
+      (flags & ~(PTYCHO_NET_F32_ACTIVATIONS | PTYCHO_NET_CUDA_CORES)))
     return nfail(nullptr, PTYCHO_ERR_ARG, "bad arguments");
   *out = nullptr;
   ptycho_net* n = new ptycho_net();
   n->f32 = (flags & PTYCHO_NET_F32_ACTIVATIONS) != 0;
+  n->tc = !n->f32 && !(flags & PTYCHO_NET_CUDA_CORES);
   n->st = (cudaStream_t)stream;
   n->max_batch = max_batch;
   long long off = 0, woff = 0;
@@ -233,6 +296,27 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
   if (!r) r = nalloc(n, &n->delta[1], maxd);
   if (!r) r = nalloc(n, &n->wpart, maxpart);
   if (!r) r = nalloc(n, &n->lpart, 256);
+  if (!r) r = nalloc(n, &n->err_flag, 1);
+  if (!r && cudaMemset(n->err_flag, 0, sizeof(int)) != cudaSuccess) r = nfail(n, PTYCHO_ERR_CUDA, "memset");
+  if (!r && n->tc) {
+    n->tc_part_n = tc_part_size(max_batch);
+    if (n->tc_part_n) r = nalloc(n, &n->tc_part, n->tc_part_n);
+    cudaError_t e2 = cudaSuccess;
+    auto setsm = [&](const void* f, size_t b) {
+      if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    };
+    setsm((const void*)k_conv_fwd_tc<false, 16>, conv_tc_smem<16>());
+    setsm((const void*)k_conv_fwd_tc<true, 16>, conv_tc_smem<16>());
+    setsm((const void*)k_conv_fwd_tc<false, 32>, conv_tc_smem<32>());
+    setsm((const void*)k_conv_fwd_tc<true, 32>, conv_tc_smem<32>());
+    setsm((const void*)k_conv_fwd_tc<false, 64>, conv_tc_smem<64>());
+    setsm((const void*)k_conv_fwd_tc<true, 64>, conv_tc_smem<64>());
+    setsm((const void*)k_conv_fwd_tc<false, 128>, conv_tc_smem<128>());
+    setsm((const void*)k_conv_fwd_tc<true, 128>, conv_tc_smem<128>());
+    setsm((const void*)k_conv_fwd_tc<false, 256>, conv_tc_smem<256>());
+    setsm((const void*)k_conv_fwd_tc<true, 256>, conv_tc_smem<256>());
+    if (!r && e2 != cudaSuccess) r = nfail(n, PTYCHO_ERR_CUDA, "tensor-core kernel setup: %s", cudaGetErrorString(e2));
+  }
   if (r) {
     g_net_error = n->err;
     ptycho_net_destroy(n);
@@ -349,7 +433,7 @@ void ptycho_net_destroy(ptycho_net* n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
   else cudaDeviceSynchronize();
-  void* bufs[] = {n->params, n->grads, n->m,   n->v,        n->wb,       n->is_w,     n->wb_index,
+  void* bufs[] = {n->tc_part, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->is_w,     n->wb_index,
                   n->x,      n->out,   n->wpart, n->lpart, n->delta[0], n->delta[1]};
   for (void* b : bufs)
     if (b) cudaFree(b);

@@ -93,3 +93,23 @@ def test_set_params_roundtrip_and_errors():
         with pytest.raises(api.PtychoError) as e:
             net.set_params(bad)
         assert e.value.name == "NONFINITE"
+
+
+def test_tensor_core_forward_matches_cuda_cores():
+    """Forward convolutions as tcgen05 implicit GEMMs (the default) against the
+    CUDA-core kernels on identical BF16 weights and frames; only the FP32
+    summation order differs (then BF16-rounded per layer): 1e-2."""
+    torch = pytest.importorskip("torch")
+    I, _ = _batch(8, 4)
+    It = torch.from_numpy(I).cuda()
+    outs = []
+    for cc in (False, True):
+        with api.Net(seed=9, max_batch=8, cuda_cores=cc) as net:
+            o = torch.empty((8, 2, 64, 64), dtype=torch.float32, device="cuda")
+            net.predict(It, o)
+            net.predict(It, o)  # second call: reused tensor memory and barriers
+            torch.cuda.synchronize()
+            outs.append(o.cpu().numpy())
+    e = np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1])
+    print("tensor-core vs CUDA-core forward:", e)
+    assert e < 1e-2
