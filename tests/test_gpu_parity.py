@@ -190,3 +190,27 @@ def test_profile_and_launch_count():
         prof = r.get_profile()
         assert r.launch_count > n0
     assert prof["fourier_chi"]["launches"] == 2 and prof["fourier_chi"]["ms"] > 0
+
+
+def test_precision_report_16bit_storage():
+    """Error of each result against the FP64 oracle after 20 LSQML iterations
+    (64^2 probe, 36 positions, Poisson 1e6) for FP32, FP16 and BF16 amplitude
+    storage.  FP32 stays within the parity tolerance; FP16 and BF16 within
+    their storage rounding (2^-11 and 2^-8 relative on sqrt(I))."""
+    c = scan(64, 1, grid=6, step=12, photons=1e6)
+    n = 20
+    Oc, Pc, _ = orc.reconstruct("lsqml", c["O0"], c["P0"], c["pos"], c["I"], n)
+    E_ref = orc.fourier_error(Oc, Pc, orc.round_positions(c["pos"]), c["I"])
+    m = illuminated(c["P"], c["pos"], c["shape"])
+    report = {}
+    for store in ("f32", "f16", "bf16"):
+        with recon(c, istore=store) as r:
+            r.iterate("lsqml", n)
+            Og, Pg = r.get_object(), r.get_probe()
+        E = orc.fourier_error(Og, Pg, orc.round_positions(c["pos"]), c["I"])
+        report[store] = dict(object=rel_l2(align_global(Og, Oc, m), Oc, m), probe=rel_l2(Pg, Pc),
+                             fourier_error=abs(E - E_ref) / E_ref)
+    print("precision report (relative to the FP64 oracle):", report)
+    assert max(report["f32"].values()) < 1e-4
+    assert max(report["f16"].values()) < 5e-3
+    assert max(report["bf16"].values()) < 5e-2
