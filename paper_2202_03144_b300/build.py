@@ -36,7 +36,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, *FLAGS, "-o", LIB + ".tmp", os.path.join(CSRC, "ptycho_api.cu")]
+    extra = os.environ.get("PTYCHO_NVCC_EXTRA", "").split()  # e.g. tuning macros
+    cmd = [nvcc, *ARCH, *FLAGS, *extra, "-o", LIB + ".tmp", os.path.join(CSRC, "ptycho_api.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

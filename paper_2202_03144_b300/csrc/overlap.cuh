@@ -21,6 +21,25 @@ namespace ptycho {
 constexpr int TILE_Y = 32, TILE_X = 64, OBJ_NT = 256;
 constexpr int OBJ_ROWS = TILE_Y / (OBJ_NT / TILE_X);  // rows per thread (8)
 constexpr int PROBE_NT = 256;
+// Object kernel: one position per step and 3 CTAs per SM (78 registers)
+// measured fastest at the 256^2 / 10k workload (4.5-4.7 TB/s, against 4.1 for
+// two positions per step at 2 CTAs per SM).
+#ifndef PT_OBJ_UNROLL
+#define PT_OBJ_UNROLL 1   // positions per step of the object kernel
+#endif
+#ifndef PT_OBJ_MINB
+#define PT_OBJ_MINB 3     // occupancy hint (CTAs per SM) of the object kernel
+#endif
+// Step-size kernel: one pixel pair per thread per step at 4 CTAs per SM
+// measured fastest (3.9 TB/s against 3.6 for two pairs at the default
+// occupancy); it also reads ~40 B/pixel from L2 (O, dO, P, dP) per 8 B of chi.
+#ifndef PT_STEP_MINB
+#define PT_STEP_MINB 4    // occupancy hint of the LSQML step-size kernel
+#endif
+#ifndef PT_STEP_UNROLL
+#define PT_STEP_UNROLL 1  // pixel pairs per thread per step of the step-size kernel
+#endif
+constexpr int OBJ_U = PT_OBJ_UNROLL;
 constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
 constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
 
@@ -50,7 +69,7 @@ struct ObjArgs {
 };
 
 template <int K, int MODE>
-__global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
+__global__ void __launch_bounds__(OBJ_NT, PT_OBJ_MINB) k_obj(ObjArgs a) {
   __shared__ float red[32];
   const int tile = blockIdx.x;
   const int ty0 = (tile / a.ntx) * TILE_Y, tx0 = (tile % a.ntx) * TILE_X;
@@ -82,13 +101,13 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
       sw[i] = weighted ? a.weights[j] : 1.f;
     }
     __syncthreads();
-    // two positions per step so that twice the loads are in flight
-    for (int s = 0; s < nc; s += 2) {
-      int jj[2], ux[2], uy0[2];
-      float w[2];
-      bool on[2];
+    // OBJ_U positions per step so that more loads are in flight
+    for (int s = 0; s < nc; s += OBJ_U) {
+      int jj[OBJ_U], ux[OBJ_U], uy0[OBJ_U];
+      float w[OBJ_U];
+      bool on[OBJ_U];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < OBJ_U; ++h) {
         const int i = min(s + h, nc - 1);
         jj[h] = sj[i];
         const int2 p = sp[i];
@@ -97,10 +116,10 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
         on[h] = (s + h < nc) && ux[h] >= 0 && ux[h] < M;
         w[h] = sw[i];
       }
-      float2 xv[2][OBJ_ROWS][K];
-      float2 pv[2][OBJ_ROWS][K];
+      float2 xv[OBJ_U][OBJ_ROWS][K];
+      float2 pv[OBJ_U][OBJ_ROWS][K];
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < OBJ_U; ++h)
 #pragma unroll
         for (int i = 0; i < OBJ_ROWS; ++i) {
           const int uy = uy0[h] + (OBJ_NT / TILE_X) * i;
@@ -113,7 +132,7 @@ __global__ void __launch_bounds__(OBJ_NT) k_obj(ObjArgs a) {
           }
         }
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < OBJ_U; ++h)
 #pragma unroll
         for (int i = 0; i < OBJ_ROWS; ++i)
 #pragma unroll
@@ -342,19 +361,20 @@ struct StepArgs {
 constexpr int STEP_NT = 256;
 
 template <int K>
-__global__ void __launch_bounds__(STEP_NT) k_lsqml_steps(StepArgs a) {
+__global__ void __launch_bounds__(STEP_NT, PT_STEP_MINB) k_lsqml_steps(StepArgs a) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   const int2 p = a.pos[j];
   const int MM = a.M * a.M;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
   const bool upd = a.dP != nullptr;
-  // two adjacent pixels per thread per step (16-byte loads), two steps unrolled
-  for (int u0 = 2 * threadIdx.x; u0 < MM; u0 += 4 * STEP_NT) {
-    float4 o[2], dov[2], xv[2][K], pr[2][K], dp[2][K];
-    bool in[2];
+  // two adjacent pixels per thread (16-byte loads), PT_STEP_UNROLL steps in flight
+  constexpr int SU = PT_STEP_UNROLL;
+  for (int u0 = 2 * threadIdx.x; u0 < MM; u0 += 2 * SU * STEP_NT) {
+    float4 o[SU], dov[SU], xv[SU][K], pr[SU][K], dp[SU][K];
+    bool in[SU];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < SU; ++h) {
       const int u = u0 + h * 2 * STEP_NT;
       in[h] = u < MM;
       const int uu = in[h] ? u : 0;
@@ -373,7 +393,7 @@ __global__ void __launch_bounds__(STEP_NT) k_lsqml_steps(StepArgs a) {
       }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < SU; ++h) {
       if (!in[h]) continue;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
