@@ -159,9 +159,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7):
+def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7, group_bytes=None):
     """Batched workload: n scans of unequal probe size and position count,
-    one CUDA graph per iteration (all members) vs one member at a time."""
+    one CUDA graph per iteration (members in L2-sized groups) vs every member
+    at once and vs one member at a time."""
     from paper_2202_03144_b300 import synth
     members = synth.batch_members(n, seed=seed)
     side = max(max(m["obj_shape"]) for m in members)
@@ -173,7 +174,7 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7):
     spec = [dict(M=m["M"], K=1, J=m["J"], obj_shape=m["obj_shape"], cluster=-1) for m in members]
     gen = torch.Generator(device="cuda").manual_seed(99)
     with torch.cuda.stream(stream):
-        b = api.Batch(spec, stream=stream.cuda_stream)
+        b = api.Batch(spec, stream=stream.cuda_stream, group_bytes=group_bytes)
         for mem, m in zip(b.members, members):
             P, P0 = probes[m["M"]]
             O = field[:m["obj_shape"][0], :m["obj_shape"][1]]
@@ -196,6 +197,15 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_graph = e0.elapsed_time(e1)
+        n_groups = max(b.groups()) + 1
+        # every member at once (one group)
+        b.set_group_bytes(0)
+        b.iterate("lsqml", 1)
+        e0.record(stream)
+        b.iterate("lsqml", iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_all = e0.elapsed_time(e1)
         # one member after another (a job queue on one GPU)
         t0 = time.perf_counter()
         for mem in b.members:
@@ -206,11 +216,14 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7):
         clusters = sorted({(m["M"], api.autotune(m["M"], 1)[0]) for m in members})
         b.close()
     units = sum(m["J"] for m in members) * iters
-    return {"value": units / (ms_graph / 1e3), "unit": UNIT, "sequential_value": units / (ms_seq / 1e3),
+    gb_mib = (512 << 20 if group_bytes is None else group_bytes) / 2**20
+    return {"value": units / (ms_graph / 1e3), "unit": UNIT, "groups": n_groups,
+            "all_at_once_value": units / (ms_all / 1e3), "sequential_value": units / (ms_seq / 1e3),
             "members": n, "positions": sum(m["J"] for m in members), "iterations": iters,
             "kernels_per_graph": kpi, "autotuned_clusters": clusters,
             "workload": f"{n} LSQML scans, probe sizes {{64,96,128,192,256}}, 100-4000 positions (Fermat "
-                        "spirals, spacing 0.15 M), Poisson 1e4-1e6 photons/frame; one CUDA graph per iteration"}
+                        "spirals, spacing 0.15 M), Poisson 1e4-1e6 photons/frame; one CUDA graph per iteration, "
+                        f"members run in groups of at most {gb_mib:g} MiB working set"}
 
 
 def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):

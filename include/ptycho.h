@@ -170,7 +170,7 @@ int ptycho_set_profiling(ptycho_ctx* ctx, int enabled);
 /* Writes up to max entries; *n receives the number of kernel families. */
 int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n);
 
-/* FFT cluster size chosen for this context (1, 2, 4 or 8 CTAs). */
+/* FFT cluster size chosen for this context (1, 2, 4, 8 or 16 CTAs). */
 int ptycho_cluster_size(const ptycho_ctx* ctx);
 
 /* ---- Many reconstructions per launch --------------------------------------
@@ -178,6 +178,12 @@ int ptycho_cluster_size(const ptycho_ctx* ctx);
  * (Sec. 3.3).  On one B300 a batch groups N reconstructions of unequal size:
  * one iteration of every member is captured into a single CUDA graph (each
  * member's kernels on its own stream branch) and replayed once per iteration.
+ * Members run in groups, one group after another, so that large members do
+ * not contend with each other for L2 and SMs while small ones still share
+ * the GPU: a member whose per-iteration working set (J*K*M^2*8 bytes of
+ * residuals, the stored amplitudes, 24 bytes per object pixel) reaches the
+ * group budget runs alone; the others are packed, largest first, into
+ * groups whose working sets sum to at most the budget (default 512 MiB).
  *
  * ptycho_batch_create: params[n] describes each member (its stream field is
  *   ignored: the batch creates one stream per member); stream is the batch
@@ -191,6 +197,12 @@ int ptycho_cluster_size(const ptycho_ctx* ctx);
  *   probe-update state changes.  Asynchronous on the batch stream; member
  *   streams are ordered after it.
  * ptycho_batch_kernels_per_iteration: kernel nodes in the captured graph.
+ * ptycho_batch_set_group_bytes: the group budget in bytes (<= 0: all members
+ *   in one group); the graph is captured again at the next iterate.
+ * ptycho_batch_groups: number of groups of the current plan; if group_of is
+ *   not NULL it receives each member's group index (n ints).  The schedule
+ *   changes only the order of independent work: results are bit-identical
+ *   for every budget.
  * Errors: PTYCHO_ERR_* codes; ptycho_batch_last_error(b) (b = NULL: last
  * failed create). */
 typedef struct ptycho_batch ptycho_batch;
@@ -199,6 +211,8 @@ ptycho_ctx* ptycho_batch_member(ptycho_batch* b, int i);
 int ptycho_batch_size(const ptycho_batch* b);
 int ptycho_batch_iterate(ptycho_batch* b, int alg, int n_iter);
 long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b);
+int ptycho_batch_set_group_bytes(ptycho_batch* b, long long bytes);
+int ptycho_batch_groups(ptycho_batch* b, int* group_of);
 int ptycho_batch_synchronize(ptycho_batch* b);
 const char* ptycho_batch_last_error(const ptycho_batch* b);
 void ptycho_batch_destroy(ptycho_batch* b);

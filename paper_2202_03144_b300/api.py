@@ -83,6 +83,8 @@ def lib() -> C.CDLL:
             "ptycho_batch_size": (i, [vp]),
             "ptycho_batch_iterate": (i, [vp, i, i]),
             "ptycho_batch_kernels_per_iteration": (C.c_longlong, [vp]),
+            "ptycho_batch_set_group_bytes": (i, [vp, C.c_longlong]),
+            "ptycho_batch_groups": (i, [vp, C.POINTER(C.c_int)]),
             "ptycho_batch_synchronize": (i, [vp]),
             "ptycho_batch_last_error": (C.c_char_p, [vp]),
             "ptycho_batch_destroy": (None, [vp]),
@@ -384,7 +386,7 @@ class Batch:
     iteration.  ``members`` is a list of dicts with keys M, K, J, obj_shape and
     optional parameters (cluster, reg, lsqml_beta, probe_start, istore)."""
 
-    def __init__(self, members, stream=None):
+    def __init__(self, members, stream=None, group_bytes=None):
         n = len(members)
         arr = (Params * n)()
         for i, m in enumerate(members):
@@ -398,6 +400,22 @@ class Batch:
         self.h = h
         self.members = [_Member(lib().ptycho_batch_member(h, i), m["M"], m["K"], m["J"], m["obj_shape"])
                         for i, m in enumerate(members)]
+        if group_bytes is not None:
+            self.set_group_bytes(group_bytes)
+
+    def set_group_bytes(self, nbytes):
+        """Working-set budget of a group of concurrently running members
+        (<= 0: all members at once)."""
+        self._check(lib().ptycho_batch_set_group_bytes(self.h, int(nbytes)))
+
+    def groups(self):
+        """Group index of every member under the current budget."""
+        n = len(self.members)
+        out = (C.c_int * n)()
+        ng = lib().ptycho_batch_groups(self.h, out)
+        if ng < 0:
+            raise PtychoError(-1, "bad batch")
+        return list(out)
 
     def _check(self, rc):
         if rc != 0:

@@ -10,6 +10,18 @@
 // iteration, so the members run concurrently and the host issues one launch
 // per iteration instead of N x (launches per iteration).
 //
+// Running every member at once makes their working sets (residuals,
+// amplitudes, objects) compete for the 126 MB L2 -- the residuals of a scan
+// are re-read four times per iteration -- and was measured slower than
+// running them one after another.  So the graph runs the members in groups,
+// one group after another: a member whose per-iteration working set reaches
+// the group budget forms a group of its own (it fills the GPU by itself), the
+// others are packed greedily, largest first, into groups whose working sets
+// sum to at most the budget and run concurrently (small scans alone leave
+// most SMs idle).  A budget <= 0 puts every member in one group.  The default
+// budget, 512 MiB, was the fastest of 0 .. 4 GiB on the 64-scan mixed
+// workload of the benchmark.
+//
 // This file is included by ptycho_api.cu (it uses the context internals).
 
 struct ptycho_batch {
@@ -19,6 +31,9 @@ struct ptycho_batch {
   bool own_main = false;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
+  std::vector<cudaEvent_t> gfork;     // one fork event per group
+  long long group_bytes = 512LL << 20;
+  std::vector<std::vector<int>> groups;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_alg = -1;
@@ -51,26 +66,67 @@ void batch_drop_graph(ptycho_batch* b) {
   b->graph_alg = -1;
 }
 
-// Capture one iteration of every member (probe-update flags `upd`) into a graph.
+// Bytes one iteration of a member streams: the exit-wave / residual array,
+// the stored amplitudes and the object-sized arrays.
+long long member_bytes(const ptycho_ctx* c) {
+  const long long MM = (long long)c->p.M * c->p.M;
+  return (long long)c->p.J * MM * (8LL * c->p.K + (c->p.istore == 0 ? 4 : 2)) +
+         (long long)c->p.obj_ny * c->p.obj_nx * 24;
+}
+
+// Partition the members into groups (see the top of this file).
+void batch_plan(ptycho_batch* b) {
+  const int n = (int)b->m.size();
+  b->groups.clear();
+  if (b->group_bytes <= 0) {
+    b->groups.emplace_back();
+    for (int i = 0; i < n; ++i) b->groups.back().push_back(i);
+  } else {
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return member_bytes(b->m[x]) > member_bytes(b->m[y]); });
+    long long cur = 0;
+    for (int i : order) {
+      const long long w = member_bytes(b->m[i]);
+      if (b->groups.empty() || w >= b->group_bytes || cur + w > b->group_bytes) {
+        b->groups.emplace_back();
+        cur = 0;
+      }
+      b->groups.back().push_back(i);
+      cur += w;
+    }
+  }
+  while (b->gfork.size() < b->groups.size()) {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    b->gfork.push_back(ev);
+  }
+}
+
+// Capture one iteration of every member (probe-update flags `upd`) into a
+// graph: group after group, the members of a group on parallel branches.
 int batch_capture(ptycho_batch* b, int alg, const std::vector<char>& upd) {
   batch_drop_graph(b);
+  batch_plan(b);
   cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bfail(b, PTYCHO_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-  cudaEventRecord(b->fork, b->main);
   long long before = 0, after = 0;
   int rc = 0;
-  for (size_t i = 0; i < b->m.size() && !rc; ++i) {
-    ptycho_ctx* c = b->m[i];
-    cudaStreamWaitEvent(c->st, b->fork, 0);
-    before += c->launches;
-    rc = alg == PTYCHO_DM ? dm_step(c, upd[i] != 0) : lsqml_step(c, upd[i] != 0);
-    after += c->launches;
-    if (rc) {
-      b->err = "member " + std::to_string(i) + ": " + c->err;
-      break;
+  for (size_t g = 0; g < b->groups.size() && !rc; ++g) {
+    cudaEventRecord(b->gfork[g], b->main);  // after the previous group's joins
+    for (int i : b->groups[g]) {
+      ptycho_ctx* c = b->m[i];
+      cudaStreamWaitEvent(c->st, b->gfork[g], 0);
+      before += c->launches;
+      rc = alg == PTYCHO_DM ? dm_step(c, upd[i] != 0) : lsqml_step(c, upd[i] != 0);
+      after += c->launches;
+      if (rc) b->err = "member " + std::to_string(i) + ": " + c->err;
+      // joined even on failure, so that the capture ends cleanly
+      cudaEventRecord(b->join[i], c->st);
+      cudaStreamWaitEvent(b->main, b->join[i], 0);
+      if (rc) break;
     }
-    cudaEventRecord(b->join[i], c->st);
-    cudaStreamWaitEvent(b->main, b->join[i], 0);
   }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(b->main, &g);
@@ -261,6 +317,24 @@ int ptycho_batch_iterate(ptycho_batch* b, int alg, int n_iter) {
 
 long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b) { return b ? b->kernels_per_launch : -1; }
 
+int ptycho_batch_set_group_bytes(ptycho_batch* b, long long bytes) {
+  if (!b) return PTYCHO_ERR_ARG;
+  if (bytes != b->group_bytes) {
+    b->group_bytes = bytes;
+    batch_drop_graph(b);  // captured again at the next iterate
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_batch_groups(ptycho_batch* b, int* group_of) {
+  if (!b) return -1;
+  batch_plan(b);
+  if (group_of)
+    for (size_t g = 0; g < b->groups.size(); ++g)
+      for (int i : b->groups[g]) group_of[i] = (int)g;
+  return (int)b->groups.size();
+}
+
 int ptycho_batch_synchronize(ptycho_batch* b) {
   if (!b) return PTYCHO_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(b->main);
@@ -277,6 +351,7 @@ void ptycho_batch_destroy(ptycho_batch* b) {
   for (ptycho_ctx* c : b->m) ptycho_destroy(c);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->gfork) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->own_main) cudaStreamDestroy(b->main);
   delete b;

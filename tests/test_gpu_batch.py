@@ -64,3 +64,43 @@ def test_autotune_picks_a_compiled_cluster():
     c = scan(64, 1, grid=2)
     with api.Reconstruction(64, 1, len(c["pos"]), c["shape"], cluster=-1) as r:
         assert r.cluster == best
+
+
+def _bytes(c):
+    M, K, J = c["M"], c["K"], len(c["pos"])
+    return J * M * M * (8 * K + 4) + c["shape"][0] * c["shape"][1] * 24
+
+
+@pytest.mark.parametrize("budget", [0, 1, 200_000, 1 << 30])
+def test_batch_group_schedule_is_bit_identical(budget):
+    """The group budget only reorders independent work: every schedule gives
+    the results of the default one bit for bit; the plan follows the packing
+    rule (a member at or above the budget alone, the rest packed largest
+    first without exceeding it)."""
+    cases = _cases()
+    members = [dict(M=c["M"], K=c["K"], J=len(c["pos"]), obj_shape=c["shape"]) for c in cases]
+    outs = []
+    for gb in (None, budget):
+        with api.Batch(members, group_bytes=gb) as b:
+            for m, c in zip(b.members, cases):
+                m.set_data(c["I"].astype(np.float32), c["pos"])
+                m.set_init(c["O0"], c["P0"])
+            b.iterate("lsqml", 2)
+            outs.append([(m.get_object(), m.get_probe()) for m in b.members])
+            groups = b.groups()
+    for (O1, P1), (O2, P2) in zip(*outs):
+        assert np.array_equal(O1, O2) and np.array_equal(P1, P2)
+    w = [_bytes(c) for c in cases]
+    ng = max(groups) + 1
+    assert sorted(set(groups)) == list(range(ng))
+    if budget <= 0:
+        assert ng == 1
+    for g in range(ng):
+        idx = [i for i in range(len(cases)) if groups[i] == g]
+        if budget > 0 and len(idx) > 1:
+            assert sum(w[i] for i in idx) <= budget
+            assert all(w[i] < budget for i in idx)
+    if budget == 1:
+        assert ng == len(cases)
+    if budget == 1 << 30:
+        assert ng == 1
