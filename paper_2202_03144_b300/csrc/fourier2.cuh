@@ -149,13 +149,19 @@ struct Fourier2Args {
   int mode;
 };
 
+// IST >= 0: storage format fixed at compile time (0 f32, 1 f16, 2 bf16);
+// -1: read from the arguments.
+template <int IST>
 __device__ __forceinline__ float amp_at(const Fourier2Args& a, const void* amp_s, int idx, float scale) {
-  if (a.istore == 0) return reinterpret_cast<const float*>(amp_s)[idx];
-  if (a.istore == 1) return __half2float(reinterpret_cast<const __half*>(amp_s)[idx]) * scale;
+  const int ist = IST >= 0 ? IST : a.istore;
+  if (ist == 0) return reinterpret_cast<const float*>(amp_s)[idx];
+  if (ist == 1) return __half2float(reinterpret_cast<const __half*>(amp_s)[idx]) * scale;
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(amp_s)[idx]) * scale;
 }
 
-template <int M, int K, int C>
+// MODE_T / IST_T >= 0 compile one mode / amplitude format (the hot LSQML and
+// DM passes); -1 takes them from the arguments.
+template <int M, int K, int C, int MODE_T = -1, int IST_T = -1>
 __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (F2<M, K, C>::NT <= 256 ? 4 : (F2<M, K, C>::NT <= 512 ? 2 : 1)))) k_fourier2(Fourier2Args a) {
   using F = F2<M, K, C>;
   constexpr int R1 = F::R1, R2 = F::R2, W = F::W, H = F::H, NT = F::NT, Q = F::Q;
@@ -170,7 +176,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
   const int tid = threadIdx.x;
   const int c = (C > 1) ? (int)(blockIdx.x % C) : 0;
   const int j = a.j0 + (int)(blockIdx.x / C);
-  const int mode = a.mode;
+  const int mode = MODE_T >= 0 ? MODE_T : a.mode;
+  const int istore = IST_T >= 0 ? IST_T : a.istore;
   const int2 p = a.pos[j];
   const bool need_amp = mode != FM_SIM;
 
@@ -178,7 +185,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
   if (tid == 0) {
     mbar_init(bar, 1);
     if (need_amp) {
-      const size_t esz = a.istore == 0 ? 4 : 2;
+      const size_t esz = istore == 0 ? 4 : 2;
       const unsigned char* src = reinterpret_cast<const unsigned char*>(a.amp) + ((size_t)j * M + c * H) * M * esz;
       bulk_load(amp_s, src, (uint32_t)(H * M * esz), bar);
     }
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
   __syncthreads();
   // ---- row stage 2 (+ projection + first inverse stage)
   float scale = 1.f;
-  if (need_amp && a.istore != 0) scale = __ldg(a.amp_scale + j);
+  if (need_amp && istore != 0) scale = __ldg(a.amp_scale + j);
   if (need_amp) {
     // every thread waits on the barrier (the copy's writes become visible)
     if (!mbar_wait0(bar)) atomicExch(a.err_flag, 1);
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
           if (mode == FM_SIM) {
             a.I_out[((size_t)j * M + ((ky + M / 2) % M)) * M + ((kx + M / 2) % M)] = A2;
           } else {
-            const float am = amp_at(a, amp_s, rowL * M + kx, scale);
+            const float am = amp_at<IST_T>(a, amp_s, rowL * M + kx, scale);
             if (mode == FM_ERR) {
               if (am >= 0.f) {
                 const double d = (double)sqrtf(A2) - (double)am;
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
           a.I_out[((size_t)j * M + ((ky + M / 2) % M)) * M + ((kx + M / 2) % M)] = A2;
           continue;
         }
-        const float am = amp_at(a, amp_s, rowL * M + kx, scale);
+        const float am = amp_at<IST_T>(a, amp_s, rowL * M + kx, scale);
         if (mode == FM_ERR) {
           if (am >= 0.f) {
             const double d = (double)sqrtf(A2) - (double)am;

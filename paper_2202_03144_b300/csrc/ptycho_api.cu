@@ -24,6 +24,7 @@
 #include "epie.cuh"
 #include "fourier.cuh"
 #include "fourier2.cuh"
+#include "kernel_sets.cuh"
 #include "net.cuh"
 #include "overlap.cuh"
 
@@ -34,39 +35,33 @@ using namespace ptycho;
 // ---------------------------------------------------------------------------
 namespace {
 
-struct KernelSet {
-  int M, K, C;
-  int NT2, NT_epie;
-  size_t smem_fourier, smem_epie;
-  void (*fourier)(Fourier2Args);
-  void (*epie)(EpieArgs);
-};
-
-template <int M, int K, int C>
-KernelSet make_set() {
-  using F = FCfg<M, K, C>;
-  using G = F2<M, K, C>;
-  return KernelSet{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>};
+// The Fourier kernel variants of a set, for attribute setup.
+std::vector<FourierFn> fourier_variants(const KernelSet* ks) {
+  std::vector<FourierFn> v{ks->fourier};
+  for (const auto& row : ks->spec)
+    for (FourierFn f : row)
+      if (f) v.push_back(f);
+  return v;
 }
 
-// mixed-radix sizes: DM / LSQML / error / forward model only (no ePIE kernel)
-template <int M, int K, int C>
-KernelSet make_set_noepie() {
-  using G = F2<M, K, C>;
-  return KernelSet{M, K, C, G::NT, 0, fourier2_smem<G>(), 0, k_fourier2<M, K, C>, nullptr};
+// Dynamic shared memory (and, above 8 CTAs, the non-portable cluster size)
+// for every Fourier kernel variant of a set.
+cudaError_t set_fourier_attributes(const KernelSet* ks) {
+  cudaError_t e = cudaSuccess;
+  for (auto f : fourier_variants(ks)) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
+    if (e == cudaSuccess && ks->C > 8) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  return e;
 }
 
 const std::vector<KernelSet>& kernel_sets() {
-  static const std::vector<KernelSet> sets = {
-      make_set<16, 1, 1>(),  make_set<16, 1, 2>(),  make_set<16, 2, 1>(),  make_set<16, 3, 1>(),
-      make_set<16, 3, 2>(),  make_set<32, 1, 1>(),  make_set<32, 1, 2>(),  make_set<32, 1, 4>(),
-      make_set<32, 2, 2>(),  make_set<32, 3, 1>(),  make_set<32, 3, 4>(),  make_set<64, 1, 1>(),
-      make_set<64, 1, 2>(),  make_set<64, 1, 4>(),  make_set<64, 3, 2>(),  make_set<64, 3, 4>(),
-      make_set<128, 1, 2>(), make_set<128, 1, 4>(), make_set<128, 1, 8>(), make_set<128, 3, 4>(),
-      make_set<128, 3, 8>(), make_set<256, 1, 4>(), make_set<256, 1, 8>(), make_set<256, 1, 16>(),
-      make_set_noepie<96, 1, 1>(), make_set_noepie<96, 1, 2>(), make_set_noepie<96, 1, 4>(),
-      make_set_noepie<192, 1, 2>(), make_set_noepie<192, 1, 4>(), make_set_noepie<192, 1, 8>(),
-  };
+  static const std::vector<KernelSet> sets = [] {
+    std::vector<KernelSet> v;
+    for (auto part : {kernel_sets_16_32, kernel_sets_64, kernel_sets_128, kernel_sets_256, kernel_sets_mixed})
+      for (const KernelSet& k : part()) v.push_back(k);
+    return v;
+  }();
   return sets;
 }
 
@@ -391,7 +386,10 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
       cfg.attrs = attr;
       cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, ks->fourier, a);
+    FourierFn fn = ks->fourier;
+    if ((mode == FM_DM || mode == FM_CHI) && a.istore >= 0 && a.istore < 3 && ks->spec[mode][a.istore])
+      fn = ks->spec[mode][a.istore];
+    cudaLaunchKernelEx(&cfg, fn, a);
   });
 }
 
@@ -812,8 +810,7 @@ extern "C" int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e == cudaSuccess && ks->smem_fourier > (size_t)optin)
     return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "Fourier kernel needs more shared memory than the device offers");
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
+  if (e == cudaSuccess) e = set_fourier_attributes(ks);
   if (e == cudaSuccess) e = cudaMemsetAsync(sc + NA_FLAG, 0, sizeof(int), st);  // the only state that must start at 0
   if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "setup: %s", cudaGetErrorString(e));
   k_twiddle2<<<(M + 255) / 256, 256, 0, st>>>((float2*)(sc + NA_TW), M, M / radix1(M));
@@ -951,13 +948,9 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     ptycho_destroy(ctx);
     return PTYCHO_ERR_UNSUPPORTED;
   }
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
-  if (e == cudaSuccess && ks->C > 8) {
-    e = cudaFuncSetAttribute(ks->fourier, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess && ks->epie)
-      e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  }
+  if (e == cudaSuccess) e = set_fourier_attributes(ks);
+  if (e == cudaSuccess && ks->C > 8 && ks->epie)
+    e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   ctx->epie_ok = e == cudaSuccess && ks->epie != nullptr && ks->smem_epie <= (size_t)optin;
   if (ctx->epie_ok)
     e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_epie);
