@@ -65,6 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed ({res.returncode}):\n{res.stderr[-4000:]}")
     os.replace(LIB + ".tmp", LIB)
+    for o in objs:  # every build is a full one: keep only the library
+        os.remove(o)
     return LIB
 
 

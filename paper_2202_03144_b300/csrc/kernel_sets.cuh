@@ -14,6 +14,14 @@
 
 #include "epie.cuh"
 #include "fourier2.cuh"
+#include "fourier3.cuh"
+
+// 1: the mode-specialised kernels of cluster shapes (C > 1) use the
+// asynchronous-transpose form k_fourier3 where its two buffers fit in shared
+// memory; 0: k_fourier2 throughout.
+#ifndef PT_F3
+#define PT_F3 1
+#endif
 
 namespace ptycho {
 
@@ -26,23 +34,35 @@ struct KernelSet {
   FourierFn fourier;       // any mode, any amplitude format
   void (*epie)(EpieArgs);  // null: no ePIE kernel for this shape
   FourierFn spec[2][3];    // [FM_DM, FM_CHI][f32, f16, bf16]
+  size_t smem_spec;        // dynamic shared memory of the spec kernels
 };
 
 template <int M, int K, int C>
 void fill_spec(KernelSet& s) {
-  s.spec[FM_DM][0] = k_fourier2<M, K, C, FM_DM, 0>;
-  s.spec[FM_DM][1] = k_fourier2<M, K, C, FM_DM, 1>;
-  s.spec[FM_DM][2] = k_fourier2<M, K, C, FM_DM, 2>;
-  s.spec[FM_CHI][0] = k_fourier2<M, K, C, FM_CHI, 0>;
-  s.spec[FM_CHI][1] = k_fourier2<M, K, C, FM_CHI, 1>;
-  s.spec[FM_CHI][2] = k_fourier2<M, K, C, FM_CHI, 2>;
+  if constexpr (C > 1 && PT_F3 && fourier3_smem<F2<M, K, C>>() <= 227 * 1024) {
+    s.spec[FM_DM][0] = k_fourier3<M, K, C, FM_DM, 0>;
+    s.spec[FM_DM][1] = k_fourier3<M, K, C, FM_DM, 1>;
+    s.spec[FM_DM][2] = k_fourier3<M, K, C, FM_DM, 2>;
+    s.spec[FM_CHI][0] = k_fourier3<M, K, C, FM_CHI, 0>;
+    s.spec[FM_CHI][1] = k_fourier3<M, K, C, FM_CHI, 1>;
+    s.spec[FM_CHI][2] = k_fourier3<M, K, C, FM_CHI, 2>;
+    s.smem_spec = fourier3_smem<F2<M, K, C>>();
+  } else {
+    s.spec[FM_DM][0] = k_fourier2<M, K, C, FM_DM, 0>;
+    s.spec[FM_DM][1] = k_fourier2<M, K, C, FM_DM, 1>;
+    s.spec[FM_DM][2] = k_fourier2<M, K, C, FM_DM, 2>;
+    s.spec[FM_CHI][0] = k_fourier2<M, K, C, FM_CHI, 0>;
+    s.spec[FM_CHI][1] = k_fourier2<M, K, C, FM_CHI, 1>;
+    s.spec[FM_CHI][2] = k_fourier2<M, K, C, FM_CHI, 2>;
+    s.smem_spec = fourier2_smem<F2<M, K, C>>();
+  }
 }
 
 template <int M, int K, int C>
 KernelSet make_set() {
   using F = FCfg<M, K, C>;
   using G = F2<M, K, C>;
-  KernelSet s{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>, {}};
+  KernelSet s{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>, {}, 0};
   fill_spec<M, K, C>(s);
   return s;
 }
@@ -51,7 +71,7 @@ KernelSet make_set() {
 template <int M, int K, int C>
 KernelSet make_set_noepie() {
   using G = F2<M, K, C>;
-  KernelSet s{M, K, C, G::NT, 0, fourier2_smem<G>(), 0, k_fourier2<M, K, C>, nullptr, {}};
+  KernelSet s{M, K, C, G::NT, 0, fourier2_smem<G>(), 0, k_fourier2<M, K, C>, nullptr, {}, 0};
   fill_spec<M, K, C>(s);
   return s;
 }

@@ -35,12 +35,12 @@ using namespace ptycho;
 // ---------------------------------------------------------------------------
 namespace {
 
-// The Fourier kernel variants of a set, for attribute setup.
-std::vector<FourierFn> fourier_variants(const KernelSet* ks) {
-  std::vector<FourierFn> v{ks->fourier};
+// The Fourier kernel variants of a set with their dynamic shared memory.
+std::vector<std::pair<FourierFn, size_t>> fourier_variants(const KernelSet* ks) {
+  std::vector<std::pair<FourierFn, size_t>> v{{ks->fourier, ks->smem_fourier}};
   for (const auto& row : ks->spec)
     for (FourierFn f : row)
-      if (f) v.push_back(f);
+      if (f) v.push_back({f, ks->smem_spec});
   return v;
 }
 
@@ -48,8 +48,8 @@ std::vector<FourierFn> fourier_variants(const KernelSet* ks) {
 // for every Fourier kernel variant of a set.
 cudaError_t set_fourier_attributes(const KernelSet* ks) {
   cudaError_t e = cudaSuccess;
-  for (auto f : fourier_variants(ks)) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_fourier);
+  for (auto [f, smem] : fourier_variants(ks)) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && ks->C > 8) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
   return e;
@@ -387,8 +387,10 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
       cfg.numAttrs = 1;
     }
     FourierFn fn = ks->fourier;
-    if ((mode == FM_DM || mode == FM_CHI) && a.istore >= 0 && a.istore < 3 && ks->spec[mode][a.istore])
+    if ((mode == FM_DM || mode == FM_CHI) && a.istore >= 0 && a.istore < 3 && ks->spec[mode][a.istore]) {
       fn = ks->spec[mode][a.istore];
+      cfg.dynamicSmemBytes = ks->smem_spec;
+    }
     cudaLaunchKernelEx(&cfg, fn, a);
   });
 }
