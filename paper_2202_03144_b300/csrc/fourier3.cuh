@@ -23,7 +23,8 @@
 // and waited for before the CTA exits.
 //
 // The amplitudes sqrt(I) are prefetched into L2 at kernel start (one bulk
-// prefetch per CTA) and read straight into registers in row stage 2; the
+// prefetch per CTA) and read into registers while the first transpose
+// completes; the
 // shared memory saved (two 32 KB buffers instead of one plus a 16 KB
 // amplitude tile and the barriers) keeps three 256-thread CTAs per SM at
 // M = 256, C = 16.
@@ -76,8 +77,24 @@ __device__ __forceinline__ float amp_global(const Fourier2Args& a, size_t idx, f
   return __bfloat162float(__ushort_as_bfloat16(u)) * scale;
 }
 
+// object loads in flight per thread in the prologue (4 and 8 measured equal)
+#ifndef PT_F3_OG
+#define PT_F3_OG 4
+#endif
+constexpr int F3_OG = PT_F3_OG;
+
+// CTAs per SM for the launch bounds: by threads (and the radix-24 register
+// demand) and by shared memory
+template <class F>
+constexpr int f3_min_blocks() {
+  const int by_threads = F::R1 > 16 ? 1 : (F::NT <= 256 ? 3 : (F::NT <= 512 ? 2 : 1));
+  const int by_smem = (int)((228 * 1024) / (fourier3_smem<F>() + 1024));
+  const int b = by_threads < by_smem ? by_threads : by_smem;
+  return b < 1 ? 1 : b;
+}
+
 template <int M, int K, int C, int MODE_T = -1, int IST_T = -1>
-__global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (F2<M, K, C>::NT <= 256 ? 3 : (F2<M, K, C>::NT <= 512 ? 2 : 1)))) k_fourier3(Fourier2Args a) {
+__global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>()) k_fourier3(Fourier2Args a) {
   using F = F2<M, K, C>;
   static_assert(C > 1, "cluster kernel");
   constexpr int R1 = F::R1, R2 = F::R2, W = F::W, H = F::H, NT = F::NT, Q = F::Q;
@@ -126,12 +143,12 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
     for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(a.P + ((size_t)k * M + n1 * R2 + n2) * M + col);
     const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
 #pragma unroll
-    for (int g0 = 0; g0 < R1; g0 += 4) {
-      float2 o[4];
+    for (int g0 = 0; g0 < R1; g0 += F3_OG) {
+      float2 o[F3_OG];
 #pragma unroll
-      for (int i = 0; i < 4 && g0 + i < R1; ++i) o[i] = __ldg(orow + (size_t)(g0 + i) * R2 * a.nx);
+      for (int i = 0; i < F3_OG && g0 + i < R1; ++i) o[i] = __ldg(orow + (size_t)(g0 + i) * R2 * a.nx);
 #pragma unroll
-      for (int i = 0; i < 4 && g0 + i < R1; ++i) v[g0 + i] = cmul(v[g0 + i], o[i]);
+      for (int i = 0; i < F3_OG && g0 + i < R1; ++i) v[g0 + i] = cmul(v[g0 + i], o[i]);
       asm volatile("" ::: "memory");
     }
     if (mode == FM_DM) {
@@ -174,6 +191,27 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
       }
     }
   }
+  // this thread's amplitudes for row stage 2 (K = 1: the projection runs in
+  // registers)
+  float scale = 1.f;
+  if (need_amp && istore != 0) scale = __ldg(a.amp_scale + j);
+  float am[Q][R2];
+  auto load_amp = [&]() {
+    if (K == 1 && need_amp) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int s = tid + q * NT;
+        const int k1 = s % R1, rowL = (s / R1) % H;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+          am[q][k2] = amp_global<IST_T>(a, amp_row0 + (size_t)rowL * M + k1 + R1 * k2, scale);
+      }
+    }
+  };
+  // LSQML residual pass: before the wait (256^2: 6.51 -> 6.24 ms); DM pass,
+  // whose prologue holds more registers: after row stage 1 (2% faster there)
+  constexpr bool amp_early = MODE_T != FM_DM;
+  if (amp_early) load_amp();
   if (!mbar_wait0_or_abort(barY, a.err_flag)) atomicExch(a.err_flag, 1);
   // ---- row stage 1: task (k, rowL, n2'), columns n1'*R2 + n2'
   {
@@ -186,10 +224,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) Y[rb<F>(k, rowL, k1 * R2 + n2)] = v[k1];
   }
+  if (!amp_early) load_amp();
   __syncthreads();
   // ---- row stage 2 (+ projection + first inverse stage)
-  float scale = 1.f;
-  if (need_amp && istore != 0) scale = __ldg(a.amp_scale + j);
   constexpr float inv = 1.0f / (float)(M * M);
   double en = 0.0, ed = 0.0;
   {
@@ -198,11 +235,6 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
     for (int q = 0; q < Q; ++q) {
       const int s = tid + q * NT;
       const int k1 = s % R1, rowL = (s / R1) % H, k = s / (R1 * H);
-      float am[R2];
-      if (K == 1 && need_amp) {
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) am[k2] = amp_global<IST_T>(a, amp_row0 + (size_t)rowL * M + k1 + R1 * k2, scale);
-      }
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) w[q][n2] = Y[rb<F>(k, rowL, k1 * R2 + n2)];
       dft<R2, false>(w[q]);
@@ -215,13 +247,13 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
           if (mode == FM_SIM) {
             a.I_out[((size_t)j * M + ((ky + M / 2) % M)) * M + ((kx + M / 2) % M)] = A2;
           } else if (mode == FM_ERR) {
-            if (am[k2] >= 0.f) {
-              const double d = (double)sqrtf(A2) - (double)am[k2];
+            if (am[q][k2] >= 0.f) {
+              const double d = (double)sqrtf(A2) - (double)am[q][k2];
               en += d * d;
-              ed += (double)am[k2] * (double)am[k2];
+              ed += (double)am[q][k2] * (double)am[q][k2];
             }
           } else {
-            const float fct = (am[k2] >= 0.f) ? ((A2 > 1e-38f) ? am[k2] * rsqrtf(A2) : 0.f) - 1.f : 0.f;
+            const float fct = (am[q][k2] >= 0.f) ? ((A2 > 1e-38f) ? am[q][k2] * rsqrtf(A2) : 0.f) - 1.f : 0.f;
             w[q][k2] = cscale(w[q][k2], fct * inv);
           }
         }
