@@ -375,6 +375,7 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a 20x20-position scan (profiling runs)")
+    ap.add_argument("--grid", type=int, default=0, help="raster side (positions = grid^2; profiling runs)")
     ap.add_argument("--cluster", type=int, default=0, help="FFT cluster size (0 = library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-eps", action="store_true", help="skip the time-to-epsilon runs")
@@ -384,6 +385,10 @@ def main():
     if args.small:
         WORKLOAD["grid"] = 20
         WORKLOAD["obj"] = 736
+    if args.grid:
+        # corners reach 24 (grid - 1) + 4; plus the 256^2 window, rounded up to 16
+        WORKLOAD["grid"] = args.grid
+        WORKLOAD["obj"] = -(-(24 * args.grid + 236) // 16) * 16
     if args.impl == "reference":
         return run_reference(args)
 
@@ -492,9 +497,12 @@ def main():
                 "ms_per_launch": ms_launch, "traffic": None, "share_of_step": top[1]["ms"] / total_ms,
                 "kernels": kernels}
     # --- end to end through the ABI from pinned host buffers
+    # inputs and outputs in pinned host memory, allocated once per job queue
     I_host = I.cpu().pin_memory()
-    O0 = np.ones((w["obj"], w["obj"]), np.complex64)
-    P0h = P0s.astype(np.complex64)
+    O0 = torch.ones((w["obj"], w["obj"]), dtype=torch.complex64).pin_memory()
+    P0h = torch.from_numpy(P0s.astype(np.complex64)).pin_memory()
+    O_out = torch.empty_like(O0).pin_memory()
+    P_out = torch.empty_like(P0h).pin_memory()
     e2e_times = []
     with torch.cuda.stream(stream):
         r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream)
@@ -505,24 +513,25 @@ def main():
             r.set_data(I_host, pos)
             r.set_init(O0, P0h)
             r.iterate("lsqml", args.e2e_iters)
-            Oo = r.get_object()
-            Po = r.get_probe()
+            Oo = r.get_object(O_out)
+            Po = r.get_probe(P_out)
             dt = time.perf_counter() - t0
             if s >= 2:
                 e2e_times.append(dt)
         r.close()
     e2e_dt = statistics.median(e2e_times)
-    h2d = I_host.numel() * 4 + pos.size * 4 + O0.nbytes + P0h.nbytes
-    d2h = Oo.nbytes + Po.nbytes
+    h2d = I_host.numel() * 4 + pos.size * 4 + O0.numel() * 8 + P0h.numel() * 8
+    d2h = Oo.numel() * 8 + Po.numel() * 8
     e2e = {"value": J * world * args.e2e_iters / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h),
            "step": f"one job: set_data + set_init from pinned host memory, {args.e2e_iters} LSQML iterations, "
-                   f"get_object + get_probe to host"}
-    batched = None if (args.no_batch or args.small) else run_batched(api, torch, stream)
-    t2e = None if (args.no_eps or args.small) else time_to_eps(api, torch, stream, I, pos, P0s, w)
+                   f"get_object + get_probe into pinned host memory"}
+    profiling_run = args.small or args.grid > 0
+    batched = None if (args.no_batch or profiling_run) else run_batched(api, torch, stream)
+    t2e = None if (args.no_eps or profiling_run) else time_to_eps(api, torch, stream, I, pos, P0s, w)
     del I
-    epie = None if args.small else run_epie(api, torch, stream)
-    warm = None if (args.no_warm or args.small) else run_warm_start(api, torch, stream, n_frames=args.warm_frames)
+    epie = None if profiling_run else run_epie(api, torch, stream)
+    warm = None if (args.no_warm or profiling_run) else run_warm_start(api, torch, stream, n_frames=args.warm_frames)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -536,7 +545,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_desc(), "algorithm": "lsqml", "M": M, "K": K, "J": J,
                    "object": [w["obj"], w["obj"]], "intensity_store": "f32",
-                   "l2": "inputs larger than L2: 5.2 GB of residuals and 2.6 GB of amplitudes per iteration",
+                   "l2": f"inputs larger than L2: {J * K * M * M * 8 / 1e9:.2g} GB of residuals and "
+                         f"{J * M * M * 4 / 1e9:.2g} GB of amplitudes per iteration",
                    "replicas": world},
         "by_variant": {
             "lsqml_f32": {"value": value, "fourier_error": main_run["err"]},

@@ -188,12 +188,21 @@ def iterate(ctx, alg, n_iter: int) -> None:
 
 
 def _get(fn, ctx, shape, out=None):
+    """Copy a result into ``out`` (a complex64 torch tensor on the GPU or the
+    host -- pinned host memory copies fastest -- or a numpy array), or into a
+    new numpy array."""
     if out is not None and _is_torch(out):
         import torch
-        assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous()
-        _check(ctx, fn(ctx, out.data_ptr(), 1))
+        if out.dtype != torch.complex64 or not out.is_contiguous() or out.numel() != int(np.prod(shape)):
+            raise ValueError("out must be a contiguous complex64 tensor of %s elements" % (int(np.prod(shape)),))
+        _check(ctx, fn(ctx, out.data_ptr(), 1 if out.is_cuda else 0))
         return out
-    res = np.empty(shape, dtype=np.complex64)
+    if out is not None:
+        if out.dtype != np.complex64 or not out.flags.c_contiguous or out.size != int(np.prod(shape)):
+            raise ValueError("out must be a C-contiguous complex64 array of %s elements" % (int(np.prod(shape)),))
+        res = out
+    else:
+        res = np.empty(shape, dtype=np.complex64)
     _check(ctx, fn(ctx, res.ctypes.data, 0))
     return res
 

@@ -36,9 +36,6 @@ constexpr int PROBE_NT = 256;
 #ifndef PT_STEP_MINB
 #define PT_STEP_MINB 4    // occupancy hint of the LSQML step-size kernel
 #endif
-#ifndef PT_STEP_UNROLL
-#define PT_STEP_UNROLL 1  // pixel pairs per thread per step of the step-size kernel
-#endif
 constexpr int OBJ_U = PT_OBJ_UNROLL;
 constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
 constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
@@ -368,53 +365,50 @@ __global__ void __launch_bounds__(STEP_NT, PT_STEP_MINB) k_lsqml_steps(StepArgs 
   const int MM = a.M * a.M;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
   const bool upd = a.dP != nullptr;
-  // two adjacent pixels per thread (16-byte loads), PT_STEP_UNROLL steps in flight
-  constexpr int SU = PT_STEP_UNROLL;
-  for (int u0 = 2 * threadIdx.x; u0 < MM; u0 += 2 * SU * STEP_NT) {
-    float4 o[SU], dov[SU], xv[SU][K], pr[SU][K], dp[SU][K];
-    bool in[SU];
+  // two adjacent pixels per thread (16-byte loads of chi, P, dP; M is even so
+  // both lie in one row); the pixel's row and column advance incrementally
+  const int M = a.M;
+  constexpr int STEP = 2 * STEP_NT;
+  const int dy = STEP / M, dx = STEP % M;
+  int u = 2 * threadIdx.x;
+  int uy = u / M, ux = u % M;
+  for (; u < MM; u += STEP) {
+    const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
+    // O and dO rows are 8-byte aligned only: two 8-byte loads each
+    const float2 o0 = __ldg(a.O + r), o1 = __ldg(a.O + r + 1);
+    const float2 d0 = __ldg(a.dO + r), d1 = __ldg(a.dO + r + 1);
+    float4 xv[K], pr[K], dp[K];
 #pragma unroll
-    for (int h = 0; h < SU; ++h) {
-      const int u = u0 + h * 2 * STEP_NT;
-      in[h] = u < MM;
-      const int uu = in[h] ? u : 0;
-      const int uy = uu / a.M, ux = uu % a.M;
-      const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
-      // O and dO rows are 8-byte aligned only: two 8-byte loads each
-      const float2 o0 = __ldg(a.O + r), o1 = __ldg(a.O + r + 1);
-      const float2 d0 = __ldg(a.dO + r), d1 = __ldg(a.dO + r + 1);
-      o[h] = make_float4(o0.x, o0.y, o1.x, o1.y);
-      dov[h] = make_float4(d0.x, d0.y, d1.x, d1.y);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        pr[h][k] = __ldg(reinterpret_cast<const float4*>(a.P + (size_t)k * MM + uu));
-        xv[h][k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)j * K + k) * MM + uu));
-        dp[h][k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + (size_t)k * MM + uu)) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+    for (int k = 0; k < K; ++k) {
+      pr[k] = __ldg(reinterpret_cast<const float4*>(a.P + (size_t)k * MM + u));
+      xv[k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)j * K + k) * MM + u));
+      dp[k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + (size_t)k * MM + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int h = 0; h < SU; ++h) {
-      if (!in[h]) continue;
+    for (int e = 0; e < 2; ++e) {
+      const float2 oo = e ? o1 : o0;
+      const float2 dd = e ? d1 : d0;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float2 oo = e ? make_float2(o[h].z, o[h].w) : make_float2(o[h].x, o[h].y);
-        const float2 dd = e ? make_float2(dov[h].z, dov[h].w) : make_float2(dov[h].x, dov[h].y);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float2 pk = e ? make_float2(pr[h][k].z, pr[h][k].w) : make_float2(pr[h][k].x, pr[h][k].y);
-          const float2 xk = e ? make_float2(xv[h][k].z, xv[h][k].w) : make_float2(xv[h][k].x, xv[h][k].y);
-          const float2 av = cmul(pk, dd);
-          s0 += cabs2(av);
-          s3 += fmaf(av.x, xk.x, av.y * xk.y);
-          if (upd) {
-            const float2 dk = e ? make_float2(dp[h][k].z, dp[h][k].w) : make_float2(dp[h][k].x, dp[h][k].y);
-            const float2 bv = cmul(oo, dk);
-            s1 += fmaf(av.x, bv.x, av.y * bv.y);
-            s2 += cabs2(bv);
-            s4 += fmaf(bv.x, xk.x, bv.y * xk.y);
-          }
+      for (int k = 0; k < K; ++k) {
+        const float2 pk = e ? make_float2(pr[k].z, pr[k].w) : make_float2(pr[k].x, pr[k].y);
+        const float2 xk = e ? make_float2(xv[k].z, xv[k].w) : make_float2(xv[k].x, xv[k].y);
+        const float2 av = cmul(pk, dd);
+        s0 += cabs2(av);
+        s3 += fmaf(av.x, xk.x, av.y * xk.y);
+        if (upd) {
+          const float2 dk = e ? make_float2(dp[k].z, dp[k].w) : make_float2(dp[k].x, dp[k].y);
+          const float2 bv = cmul(oo, dk);
+          s1 += fmaf(av.x, bv.x, av.y * bv.y);
+          s2 += cabs2(bv);
+          s4 += fmaf(bv.x, xk.x, bv.y * xk.y);
         }
       }
+    }
+    ux += dx;
+    uy += dy;
+    if (ux >= M) {
+      ux -= M;
+      ++uy;
     }
   }
   const double A11 = block_sum_d<STEP_NT>(s0, red);

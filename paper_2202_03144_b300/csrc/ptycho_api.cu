@@ -107,17 +107,37 @@ __global__ void k_twiddle2(float2* tw, int M, int R2) {
   }
 }
 
-// sqrt(I) into FFT order at f32; masked (I < 0) -> -1; non-finite -> flag.
+// Detector-centred frames -> FFT order (the half-size roll of ifftshift) and
+// sqrt(I), masked pixels (I < 0) -> -1, non-finite -> flag.  One block per
+// (row, frame); V = 4 pixels per thread from 16-byte aligned sources (M is a
+// multiple of 8, so a group of four never wraps around the roll), else 1.
+template <int V>
 __global__ void k_amp_f32(const float* __restrict__ src, int nj, int M, float* __restrict__ dst, int* bad) {
-  const size_t MM = (size_t)M * M;
-  const size_t n = (size_t)nj * MM;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = i / MM;
-    const int ky = (int)((i % MM) / M), kx = (int)(i % M);
-    const float v = src[j * MM + (size_t)((ky + M / 2) % M) * M + (kx + M / 2) % M];
-    if (!isfinite(v)) *bad = 1;
-    dst[i] = v < 0.f ? -1.f : sqrtf(v);
+  const int ky = blockIdx.x, h = M / 2;
+  const int sy = ky + h < M ? ky + h : ky + h - M;
+  int b = 0;
+  for (int j = blockIdx.y; j < nj; j += gridDim.y) {
+    const float* srow = src + ((size_t)j * M + sy) * M;
+    float* drow = dst + ((size_t)j * M + ky) * M;
+    for (int kx = V * threadIdx.x; kx < M; kx += V * blockDim.x) {
+      const int sx = kx + h < M ? kx + h : kx + h - M;
+      float v[V];
+      if constexpr (V == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(srow + sx);
+        v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+      } else {
+        v[0] = srow[sx];
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        b |= !isfinite(v[e]);
+        v[e] = v[e] < 0.f ? -1.f : sqrtf(v[e]);
+      }
+      if constexpr (V == 4) *reinterpret_cast<float4*>(drow + kx) = make_float4(v[0], v[1], v[2], v[3]);
+      else drow[kx] = v[0];
+    }
   }
+  if (b) *bad = 1;
 }
 
 // Per-frame maximum of sqrt(I) (masked pixels ignored); one CTA per frame.
@@ -142,17 +162,37 @@ __device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn
 template <>
 __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-template <typename T>
+// 16-bit storage: sqrt(I) / s_j rounded to the format; same layout as k_amp_f32.
+template <typename T, int V>
 __global__ void k_amp_q16(const float* __restrict__ src, int nj, int M, const float* __restrict__ scale,
                           T* __restrict__ dst) {
-  const size_t MM = (size_t)M * M;
-  const size_t n = (size_t)nj * MM;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = i / MM;
-    const int ky = (int)((i % MM) / M), kx = (int)(i % M);
-    const float v = src[j * MM + (size_t)((ky + M / 2) % M) * M + (kx + M / 2) % M];
-    dst[i] = to16<T>(v < 0.f ? -1.f : sqrtf(v) / scale[j]);
+  const int ky = blockIdx.x, h = M / 2;
+  const int sy = ky + h < M ? ky + h : ky + h - M;
+  for (int j = blockIdx.y; j < nj; j += gridDim.y) {
+    const float* srow = src + ((size_t)j * M + sy) * M;
+    T* drow = dst + ((size_t)j * M + ky) * M;
+    const float sc = scale[j];
+    for (int kx = V * threadIdx.x; kx < M; kx += V * blockDim.x) {
+      const int sx = kx + h < M ? kx + h : kx + h - M;
+      float v[V];
+      if constexpr (V == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(srow + sx);
+        v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+      } else {
+        v[0] = srow[sx];
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) drow[kx + e] = to16<T>(v[e] < 0.f ? -1.f : sqrtf(v[e]) / sc);
+    }
   }
+}
+
+// Raise *bad if any of n floats is NaN or Inf.
+__global__ void k_check_finite(const float* __restrict__ p, size_t n, int* bad) {
+  int b = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b |= !isfinite(p[i]);
+  if (__syncthreads_or(b) && threadIdx.x == 0) *bad = 1;
 }
 
 __global__ void k_fill_c(float2* p, size_t n, float2 v) {
@@ -228,6 +268,12 @@ struct ptycho_ctx {
   int* order = nullptr;
   int order_cap = 0;
   int* flag = nullptr;
+  // upload staging (host inputs): two halves of stage_bytes / 2, filled on
+  // st_copy while the kernels of the other half run on st
+  float* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaStream_t st_copy = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   // host-side state
   bool have_pos = false, have_data = false;
   bool epie_ok = false;    // the ePIE kernel of this (M, K, C) fits in shared memory
@@ -278,6 +324,29 @@ int dalloc(ptycho_ctx* ctx, T** p, size_t n) {
     *p = nullptr;
     cudaGetLastError();
     return fail(ctx, PTYCHO_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  return 0;
+}
+
+// Staging buffer of at least `bytes`, the copy stream and its events.
+int ensure_stage(ptycho_ctx* ctx, size_t bytes) {
+  if (ctx->stage_bytes < bytes) {
+    if (ctx->stage) {
+      CK(cudaStreamSynchronize(ctx->st));
+      if (ctx->st_copy) CK(cudaStreamSynchronize(ctx->st_copy));
+      cudaFree(ctx->stage);
+      ctx->stage = nullptr;
+      ctx->stage_bytes = 0;
+    }
+    if (int r = dalloc(ctx, &ctx->stage, bytes / 4 + 1)) return r;
+    ctx->stage_bytes = bytes;
+  }
+  if (!ctx->st_copy) {
+    CK(cudaStreamCreateWithFlags(&ctx->st_copy, cudaStreamNonBlocking));
+    for (int h = 0; h < 2; ++h) {
+      CK(cudaEventCreateWithFlags(&ctx->ev_copied[h], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_used[h], cudaEventDisableTiming));
+    }
   }
   return 0;
 }
@@ -979,6 +1048,36 @@ int ptycho_set_positions(ptycho_ctx* ctx, const float* positions) {
   return set_positions_impl(ctx, positions);
 }
 
+// sqrt(I) in FFT order (and the 16-bit scales) for frames [j0, j0 + nj) read
+// from src (frame j0 at src[0]).
+static int prepare_amp(ptycho_ctx* ctx, const float* src, int j0, int nj) {
+  const int M = ctx->p.M;
+  const size_t MM = (size_t)M * M;
+  const bool vec = ((uintptr_t)src & 15) == 0;
+  const dim3 grid((unsigned)M, (unsigned)std::min(nj, 65535));
+  const unsigned nt = (unsigned)std::min(256, std::max(32, M / 4));
+  if (ctx->p.istore == PTYCHO_I_F32)
+    return launch(ctx, "prepare_amp", 8.0 * nj * MM, [&] {
+      float* dst = (float*)ctx->amp + (size_t)j0 * MM;
+      if (vec) k_amp_f32<4><<<grid, nt, 0, ctx->st>>>(src, nj, M, dst, ctx->flag);
+      else k_amp_f32<1><<<grid, nt, 0, ctx->st>>>(src, nj, M, dst, ctx->flag);
+    });
+  if (int rc = launch(ctx, "frame_max", 4.0 * nj * MM,
+                      [&] { k_frame_max<<<nj, 256, 0, ctx->st>>>(src, M, ctx->amp_scale + j0, ctx->flag); }))
+    return rc;
+  if (ctx->p.istore == PTYCHO_I_F16)
+    return launch(ctx, "prepare_amp", 6.0 * nj * MM, [&] {
+      __half* dst = (__half*)ctx->amp + (size_t)j0 * MM;
+      if (vec) k_amp_q16<__half, 4><<<grid, nt, 0, ctx->st>>>(src, nj, M, ctx->amp_scale + j0, dst);
+      else k_amp_q16<__half, 1><<<grid, nt, 0, ctx->st>>>(src, nj, M, ctx->amp_scale + j0, dst);
+    });
+  return launch(ctx, "prepare_amp", 6.0 * nj * MM, [&] {
+    __nv_bfloat16* dst = (__nv_bfloat16*)ctx->amp + (size_t)j0 * MM;
+    if (vec) k_amp_q16<__nv_bfloat16, 4><<<grid, nt, 0, ctx->st>>>(src, nj, M, ctx->amp_scale + j0, dst);
+    else k_amp_q16<__nv_bfloat16, 1><<<grid, nt, 0, ctx->st>>>(src, nj, M, ctx->amp_scale + j0, dst);
+  });
+}
+
 int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* positions, int on_device) {
   if (!ctx) return PTYCHO_ERR_ARG;
   if (!intensities) return fail(ctx, PTYCHO_ERR_ARG, "intensities is NULL");
@@ -986,45 +1085,38 @@ int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* posi
   ctx->have_data = false;
   const int J = ctx->p.J, M = ctx->p.M;
   const size_t MM = (size_t)M * M;
-  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (256u << 20) / (MM * 4)));
-  float* stage = nullptr;
-  if (int r = dalloc(ctx, &stage, (size_t)chunk * MM)) return r;
   CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
   int rc = 0;
-  for (int j0 = 0; j0 < J && !rc; j0 += chunk) {
-    const int nj = std::min(chunk, J - j0);
-    const float* src = intensities + (size_t)j0 * MM;
-    cudaError_t e = cudaMemcpyAsync(stage, src, (size_t)nj * MM * 4,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st);
-    if (e != cudaSuccess) {
-      rc = fail(ctx, PTYCHO_ERR_CUDA, "intensity upload: %s", cudaGetErrorString(e));
-      break;
-    }
-    if (ctx->p.istore == PTYCHO_I_F32) {
-      rc = launch(ctx, "prepare_amp", 8.0 * nj * MM, [&] {
-        k_amp_f32<<<1184, 256, 0, ctx->st>>>(stage, nj, M, (float*)ctx->amp + (size_t)j0 * MM, ctx->flag);
-      });
-    } else {
-      rc = launch(ctx, "frame_max", 4.0 * nj * MM,
-                  [&] { k_frame_max<<<nj, 256, 0, ctx->st>>>(stage, M, ctx->amp_scale + j0, ctx->flag); });
-      if (!rc) {
-        if (ctx->p.istore == PTYCHO_I_F16)
-          rc = launch(ctx, "prepare_amp", 6.0 * nj * MM, [&] {
-            k_amp_q16<__half><<<1184, 256, 0, ctx->st>>>(stage, nj, M, ctx->amp_scale + j0,
-                                                        (__half*)ctx->amp + (size_t)j0 * MM);
-          });
-        else
-          rc = launch(ctx, "prepare_amp", 6.0 * nj * MM, [&] {
-            k_amp_q16<__nv_bfloat16><<<1184, 256, 0, ctx->st>>>(stage, nj, M, ctx->amp_scale + j0,
-                                                               (__nv_bfloat16*)ctx->amp + (size_t)j0 * MM);
-          });
+  if (on_device) {
+    rc = prepare_amp(ctx, intensities, 0, J);  // read in place
+  } else {
+    // host frames in chunks of <= 128 MB, double-buffered: the upload of one
+    // chunk overlaps the preparation of the previous one
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / (MM * 4)));
+    if (int r = ensure_stage(ctx, 2 * (size_t)chunk * MM * 4)) return r;
+    cudaEvent_t ready = get_event(ctx);
+    CK(cudaEventRecord(ready, ctx->st));  // earlier users of the stage are done
+    CK(cudaStreamWaitEvent(ctx->st_copy, ready, 0));
+    ctx->ev_pool.push_back(ready);
+    for (int j0 = 0, c = 0; j0 < J && !rc; j0 += chunk, ++c) {
+      const int nj = std::min(chunk, J - j0), h = c & 1;
+      float* half = ctx->stage + (size_t)h * chunk * MM;
+      if (c >= 2) CK(cudaStreamWaitEvent(ctx->st_copy, ctx->ev_used[h], 0));
+      cudaError_t e = cudaMemcpyAsync(half, intensities + (size_t)j0 * MM, (size_t)nj * MM * 4, cudaMemcpyHostToDevice,
+                                      ctx->st_copy);
+      if (e != cudaSuccess) {
+        rc = fail(ctx, PTYCHO_ERR_CUDA, "intensity upload: %s", cudaGetErrorString(e));
+        break;
       }
+      CK(cudaEventRecord(ctx->ev_copied[h], ctx->st_copy));
+      CK(cudaStreamWaitEvent(ctx->st, ctx->ev_copied[h], 0));
+      rc = prepare_amp(ctx, half, j0, nj);
+      CK(cudaEventRecord(ctx->ev_used[h], ctx->st));
     }
   }
   int bad = 0;
   cudaError_t e = cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
-  cudaFree(stage);
   if (rc) return rc;
   if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "set_data: %s", cudaGetErrorString(e));
   if (bad) return fail(ctx, PTYCHO_ERR_NONFINITE, "intensities contain NaN or Inf");
@@ -1035,21 +1127,29 @@ int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* posi
 
 int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device) {
   if (!ctx) return PTYCHO_ERR_ARG;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (object) {
-    const size_t n = (size_t)ctx->p.obj_ny * ctx->p.obj_nx * 2;
-    if (!on_device)
-      for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(object[i])) return fail(ctx, PTYCHO_ERR_NONFINITE, "object guess has NaN/Inf");
-    CK(cudaMemcpyAsync(ctx->O, object, n * 4, kind, ctx->st));
+  const size_t no = object ? (size_t)ctx->p.obj_ny * ctx->p.obj_nx * 2 : 0;
+  const size_t np = probe ? (size_t)ctx->p.K * ctx->p.M * ctx->p.M * 2 : 0;
+  if (!no && !np) return PTYCHO_OK;
+  // the guesses are checked for NaN / Inf on the device before they replace
+  // the current state (host inputs go through the staging buffer)
+  const float* so = object;
+  const float* sp = probe;
+  if (!on_device) {
+    if (int r = ensure_stage(ctx, (no + np) * 4)) return r;
+    if (no) CK(cudaMemcpyAsync(ctx->stage, object, no * 4, cudaMemcpyHostToDevice, ctx->st));
+    if (np) CK(cudaMemcpyAsync(ctx->stage + no, probe, np * 4, cudaMemcpyHostToDevice, ctx->st));
+    so = ctx->stage;
+    sp = ctx->stage + no;
   }
-  if (probe) {
-    const size_t n = (size_t)ctx->p.K * ctx->p.M * ctx->p.M * 2;
-    if (!on_device)
-      for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(probe[i])) return fail(ctx, PTYCHO_ERR_NONFINITE, "probe guess has NaN/Inf");
-    CK(cudaMemcpyAsync(ctx->P, probe, n * 4, kind, ctx->st));
-  }
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+  if (no) k_check_finite<<<592, 256, 0, ctx->st>>>(so, no, ctx->flag);
+  if (np) k_check_finite<<<592, 256, 0, ctx->st>>>(sp, np, ctx->flag);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (bad) return fail(ctx, PTYCHO_ERR_NONFINITE, "%s guess has NaN/Inf", no && np ? "object or probe" : (no ? "object" : "probe"));
+  if (no) CK(cudaMemcpyAsync(ctx->O, so, no * 4, cudaMemcpyDeviceToDevice, ctx->st));
+  if (np) CK(cudaMemcpyAsync(ctx->P, sp, np * 4, cudaMemcpyDeviceToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   ctx->psi_valid = false;
   return PTYCHO_OK;
@@ -1179,6 +1279,15 @@ void ptycho_destroy(ptycho_ctx* ctx) {
                   ctx->flag};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->st_copy) {
+    cudaStreamSynchronize(ctx->st_copy);
+    cudaStreamDestroy(ctx->st_copy);
+  }
+  for (int h = 0; h < 2; ++h) {
+    if (ctx->ev_copied[h]) cudaEventDestroy(ctx->ev_copied[h]);
+    if (ctx->ev_used[h]) cudaEventDestroy(ctx->ev_used[h]);
+  }
   for (auto& r : ctx->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

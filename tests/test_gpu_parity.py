@@ -214,3 +214,75 @@ def test_precision_report_16bit_storage():
     assert max(report["f32"].values()) < 1e-4
     assert max(report["f16"].values()) < 5e-3
     assert max(report["bf16"].values()) < 5e-2
+
+
+@pytest.mark.parametrize("istore", ["f32", "f16", "bf16"])
+def test_set_data_paths_agree(istore):
+    """Host frames (staged, double-buffered upload), device frames read in
+    place with 16-byte loads, and device frames at an address that is only
+    4-byte aligned (scalar path) give the same stored amplitudes: identical
+    residuals and Fourier errors."""
+    torch = pytest.importorskip("torch")
+    c = scan(64, 1, grid=4, photons=1e5)
+    I = c["I"].astype(np.float32)
+    J, M = I.shape[0], I.shape[1]
+    flat = torch.empty(I.size + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(I.ravel()).cuda()
+    sources = {"host": I, "device": torch.from_numpy(I).cuda(), "device_unaligned": flat[1:].view(J, M, M)}
+    assert sources["device_unaligned"].data_ptr() % 16 == 4
+    res = {}
+    for name, src in sources.items():
+        with api.Reconstruction(M, 1, J, c["shape"], istore=istore) as r:
+            r.set_data(src, c["pos"])
+            r.set_init(c["O0"], c["P0"])
+            chi = torch.empty((J, 1, M, M), dtype=torch.complex64, device="cuda")
+            r.fourier_residual(chi)
+            res[name] = (r.fourier_error(), chi.cpu().numpy())
+    for name in ("device", "device_unaligned"):
+        assert res[name][0] == res["host"][0]
+        assert np.array_equal(res[name][1], res["host"][1])
+
+
+def test_set_init_rejects_nonfinite_and_keeps_state():
+    c = scan(32, 1, grid=2)
+    with recon(c) as r:
+        O_before, P_before = r.get_object(), r.get_probe()
+        O_bad = c["O0"].copy()
+        O_bad[3, 4] = np.inf
+        with pytest.raises(api.PtychoError) as e:
+            r.set_init(O_bad, c["P0"])
+        assert e.value.name == "NONFINITE"
+        P_bad = c["P0"].copy()
+        P_bad[0, 1, 1] = np.nan
+        with pytest.raises(api.PtychoError) as e:
+            r.set_init(None, P_bad)
+        assert e.value.name == "NONFINITE"
+        assert np.array_equal(r.get_object(), O_before) and np.array_equal(r.get_probe(), P_before)
+        r.iterate("lsqml", 1)
+        assert np.isfinite(r.fourier_error())
+
+
+def test_get_into_caller_buffers():
+    """get_object / get_probe into a numpy array, a pinned host tensor and a
+    device tensor all return the same values; wrong shapes or dtypes are
+    rejected before any copy."""
+    torch = pytest.importorskip("torch")
+    c = scan(32, 1, grid=2)
+    with recon(c) as r:
+        r.iterate("lsqml", 1)
+        O = r.get_object()
+        out_np = np.empty_like(O)
+        assert r.get_object(out_np) is out_np and np.array_equal(out_np, O)
+        out_pin = torch.empty(O.shape, dtype=torch.complex64).pin_memory()
+        r.get_object(out_pin)
+        assert np.array_equal(out_pin.numpy(), O)
+        out_dev = torch.empty(O.shape, dtype=torch.complex64, device="cuda")
+        r.get_object(out_dev)
+        assert np.array_equal(out_dev.cpu().numpy(), O)
+        P = r.get_probe()
+        P_pin = torch.empty(P.shape, dtype=torch.complex64).pin_memory()
+        assert np.array_equal(r.get_probe(P_pin).numpy(), P)
+        with pytest.raises(ValueError):
+            r.get_object(np.empty(O.shape, np.complex128))
+        with pytest.raises(ValueError):
+            r.get_probe(torch.empty((1, 2, 2), dtype=torch.complex64))
