@@ -19,14 +19,15 @@
 namespace ptycho {
 
 constexpr int TILE_Y = 32, TILE_X = 64, OBJ_NT = 256;
-constexpr int OBJ_ROWS = TILE_Y / (OBJ_NT / TILE_X);  // rows per thread (8)
+// A thread owns OBJ_COLS adjacent columns of OBJ_ROWS rows of its tile: the
+// index arithmetic and bounds tests of a (position, row) step are shared by
+// four pixels, and the loads are 16 bytes wide when the patch column offset
+// is even (the pixel pairs are then aligned and never straddle the patch edge).
+constexpr int OBJ_COLS = 4;
+constexpr int OBJ_TX = TILE_X / OBJ_COLS;              // threads across the tile (16)
+constexpr int OBJ_RSTEP = OBJ_NT / OBJ_TX;             // row stride between a thread's rows (16)
+constexpr int OBJ_ROWS = TILE_Y / OBJ_RSTEP;           // rows per thread (2)
 constexpr int PROBE_NT = 256;
-// Object kernel: one position per step and 3 CTAs per SM (78 registers)
-// measured fastest at the 256^2 / 10k workload (4.5-4.7 TB/s, against 4.1 for
-// two positions per step at 2 CTAs per SM).
-#ifndef PT_OBJ_UNROLL
-#define PT_OBJ_UNROLL 1   // positions per step of the object kernel
-#endif
 #ifndef PT_OBJ_MINB
 #define PT_OBJ_MINB 3     // occupancy hint (CTAs per SM) of the object kernel
 #endif
@@ -36,7 +37,6 @@ constexpr int PROBE_NT = 256;
 #ifndef PT_STEP_MINB
 #define PT_STEP_MINB 4    // occupancy hint of the LSQML step-size kernel
 #endif
-constexpr int OBJ_U = PT_OBJ_UNROLL;
 constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
 constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
 
@@ -70,17 +70,19 @@ __global__ void __launch_bounds__(OBJ_NT, PT_OBJ_MINB) k_obj(ObjArgs a) {
   __shared__ float red[32];
   const int tile = blockIdx.x;
   const int ty0 = (tile / a.ntx) * TILE_Y, tx0 = (tile % a.ntx) * TILE_X;
-  const int tx = threadIdx.x % TILE_X, tyb = threadIdx.x / TILE_X;
-  const int x = tx0 + tx;
+  const int cx = threadIdx.x % OBJ_TX, ry = threadIdx.x / OBJ_TX;
+  const int x = tx0 + OBJ_COLS * cx;  // first of this thread's columns (even)
   const int M = a.M;
   const size_t MM = (size_t)M * M;
-  float2 num[OBJ_ROWS];
-  float den[OBJ_ROWS];
+  float2 num[OBJ_ROWS][OBJ_COLS];
+  float den[OBJ_ROWS][OBJ_COLS];
 #pragma unroll
-  for (int i = 0; i < OBJ_ROWS; ++i) {
-    num[i] = make_float2(0.f, 0.f);
-    den[i] = 0.f;
-  }
+  for (int i = 0; i < OBJ_ROWS; ++i)
+#pragma unroll
+    for (int e = 0; e < OBJ_COLS; ++e) {
+      num[i][e] = make_float2(0.f, 0.f);
+      den[i][e] = 0.f;
+    }
   const int s0 = a.tile_ptr[tile], s1 = a.tile_ptr[tile + 1];
   // the tile's positions (index, corner, weight) staged in shared memory in
   // chunks, so the inner loop has no chain of dependent global loads
@@ -98,77 +100,90 @@ __global__ void __launch_bounds__(OBJ_NT, PT_OBJ_MINB) k_obj(ObjArgs a) {
       sw[i] = weighted ? a.weights[j] : 1.f;
     }
     __syncthreads();
-    // OBJ_U positions per step so that more loads are in flight
-    for (int s = 0; s < nc; s += OBJ_U) {
-      int jj[OBJ_U], ux[OBJ_U], uy0[OBJ_U];
-      float w[OBJ_U];
-      bool on[OBJ_U];
+    for (int s = 0; s < nc; ++s) {
+      const int j = sj[s];
+      const int2 p = sp[s];
+      const float w = sw[s];
+      const int ux = x - p.y;                 // patch column of this thread's first pixel
+      const bool pairs = ((ux & 1) == 0);     // uniform over the CTA (x is even)
+      // one mode at a time (the per-pixel order of the sums is unchanged)
 #pragma unroll
-      for (int h = 0; h < OBJ_U; ++h) {
-        const int i = min(s + h, nc - 1);
-        jj[h] = sj[i];
-        const int2 p = sp[i];
-        ux[h] = x - p.y;
-        uy0[h] = ty0 + tyb - p.x;
-        on[h] = (s + h < nc) && ux[h] >= 0 && ux[h] < M;
-        w[h] = sw[i];
-      }
-      float2 xv[OBJ_U][OBJ_ROWS][K];
-      float2 pv[OBJ_U][OBJ_ROWS][K];
-#pragma unroll
-      for (int h = 0; h < OBJ_U; ++h)
+      for (int k = 0; k < K; ++k) {
+        float2 pv[OBJ_ROWS][OBJ_COLS], xv[OBJ_ROWS][OBJ_COLS];
 #pragma unroll
         for (int i = 0; i < OBJ_ROWS; ++i) {
-          const int uy = uy0[h] + (OBJ_NT / TILE_X) * i;
-          const bool in = on[h] && uy >= 0 && uy < M;
-          const size_t u = in ? (size_t)uy * M + ux[h] : 0;
+          const int uy = ty0 + ry + OBJ_RSTEP * i - p.x;
+          const bool row_in = uy >= 0 && uy < M;
+          const size_t u0 = (size_t)(row_in ? uy : 0) * M;
+          const float2* prow = a.P + k * MM + u0;
+          const float2* xrow = a.X + ((size_t)j * K + k) * MM + u0;
+          if (pairs) {
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            pv[h][i][k] = in ? __ldg(a.P + k * MM + u) : make_float2(0.f, 0.f);
-            xv[h][i][k] = in ? __ldcs(a.X + ((size_t)jj[h] * K + k) * MM + u) : make_float2(0.f, 0.f);
+            for (int e = 0; e < OBJ_COLS; e += 2) {
+              const bool in = row_in && ux + e >= 0 && ux + e < M;  // both pixels of the pair
+              float4 pq = make_float4(0.f, 0.f, 0.f, 0.f), xq = pq;
+              if (in) {
+                pq = __ldg(reinterpret_cast<const float4*>(prow + ux + e));
+                xq = __ldcs(reinterpret_cast<const float4*>(xrow + ux + e));
+              }
+              pv[i][e] = make_float2(pq.x, pq.y);
+              pv[i][e + 1] = make_float2(pq.z, pq.w);
+              xv[i][e] = make_float2(xq.x, xq.y);
+              xv[i][e + 1] = make_float2(xq.z, xq.w);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < OBJ_COLS; ++e) {
+              const bool in = row_in && ux + e >= 0 && ux + e < M;
+              pv[i][e] = in ? __ldg(prow + ux + e) : make_float2(0.f, 0.f);
+              xv[i][e] = in ? __ldcs(xrow + ux + e) : make_float2(0.f, 0.f);
+            }
           }
         }
 #pragma unroll
-      for (int h = 0; h < OBJ_U; ++h)
-#pragma unroll
         for (int i = 0; i < OBJ_ROWS; ++i)
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            if (MODE == OBJ_NUMDEN) den[i] += cabs2(pv[h][i][k]);
-            const float2 t = cconjmul(pv[h][i][k], xv[h][i][k]);
-            num[i].x = fmaf(w[h], t.x, num[i].x);
-            num[i].y = fmaf(w[h], t.y, num[i].y);
+          for (int e = 0; e < OBJ_COLS; ++e) {
+            if (MODE == OBJ_NUMDEN) den[i][e] += cabs2(pv[i][e]);
+            const float2 t = cconjmul(pv[i][e], xv[i][e]);
+            num[i][e].x = fmaf(w, t.x, num[i][e].x);
+            num[i][e].y = fmaf(w, t.y, num[i][e].y);
           }
+      }
     }
   }
   if (MODE == OBJ_NUMDEN) {
     float m = 0.f;
 #pragma unroll
-    for (int i = 0; i < OBJ_ROWS; ++i) {
-      const int y = ty0 + tyb + (OBJ_NT / TILE_X) * i;
-      if (y < a.ny && x < a.nx) {
-        const size_t r = (size_t)y * a.nx + x;
-        a.den[r] = den[i];
-        a.dO[r] = num[i];
-        m = fmaxf(m, den[i]);
+    for (int i = 0; i < OBJ_ROWS; ++i)
+#pragma unroll
+      for (int e = 0; e < OBJ_COLS; ++e) {
+        const int y = ty0 + ry + OBJ_RSTEP * i;
+        if (y < a.ny && x + e < a.nx) {
+          const size_t r = (size_t)y * a.nx + x + e;
+          a.den[r] = den[i][e];
+          a.dO[r] = num[i][e];
+          m = fmaxf(m, den[i][e]);
+        }
       }
-    }
     m = block_max_f<OBJ_NT>(m, red);
     if (threadIdx.x == 0) a.tile_max[tile] = m;
     return;
   }
   const float delta = a.reg * a.den_max[0];
 #pragma unroll
-  for (int i = 0; i < OBJ_ROWS; ++i) {
-    const int y = ty0 + tyb + (OBJ_NT / TILE_X) * i;
-    if (y >= a.ny || x >= a.nx) continue;
-    const size_t r = (size_t)y * a.nx + x;
-    const float d = a.den[r] + delta;
-    const float inv = d > 0.f ? 1.f / d : 0.f;
-    const float2 o = a.O[r];
-    const float sc = a.beta * inv;
-    a.O[r] = make_float2(fmaf(sc, num[i].x, o.x), fmaf(sc, num[i].y, o.y));
-  }
+  for (int i = 0; i < OBJ_ROWS; ++i)
+#pragma unroll
+    for (int e = 0; e < OBJ_COLS; ++e) {
+      const int y = ty0 + ry + OBJ_RSTEP * i;
+      if (y >= a.ny || x + e >= a.nx) continue;
+      const size_t r = (size_t)y * a.nx + x + e;
+      const float d = a.den[r] + delta;
+      const float inv = d > 0.f ? 1.f / d : 0.f;
+      const float2 o = a.O[r];
+      const float sc = a.beta * inv;
+      a.O[r] = make_float2(fmaf(sc, num[i][e].x, o.x), fmaf(sc, num[i][e].y, o.y));
+    }
 }
 
 // Object-sized epilogue of OBJ_NUMDEN, with delta = reg * max(den_O):
