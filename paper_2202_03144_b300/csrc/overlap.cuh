@@ -29,7 +29,7 @@ constexpr int OBJ_RSTEP = OBJ_NT / OBJ_TX;             // row stride between a t
 constexpr int OBJ_ROWS = TILE_Y / OBJ_RSTEP;           // rows per thread (2)
 constexpr int PROBE_NT = 256;
 #ifndef PT_OBJ_MINB
-#define PT_OBJ_MINB 3     // occupancy hint (CTAs per SM) of the object kernel
+#define PT_OBJ_MINB 4     // occupancy hint (CTAs per SM) of the object kernel (4: 1.06 ms vs 1.12 at 3)
 #endif
 // Step-size kernel: one pixel pair per thread per step at 4 CTAs per SM
 // measured fastest (3.9 TB/s against 3.6 for two pairs at the default
@@ -66,7 +66,7 @@ struct ObjArgs {
 };
 
 template <int K, int MODE>
-__global__ void __launch_bounds__(OBJ_NT, PT_OBJ_MINB) k_obj(ObjArgs a) {
+__global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArgs a) {  // K > 1: 3 (no spills)
   __shared__ float red[32];
   const int tile = blockIdx.x;
   const int ty0 = (tile / a.ntx) * TILE_Y, tx0 = (tile % a.ntx) * TILE_X;
@@ -387,11 +387,21 @@ __global__ void __launch_bounds__(STEP_NT, PT_STEP_MINB) k_lsqml_steps(StepArgs 
   const int dy = STEP / M, dx = STEP % M;
   int u = 2 * threadIdx.x;
   int uy = u / M, ux = u % M;
+  // the object pixel pair is 16-byte aligned when the patch's first object
+  // column and the row length are even (uniform over the block)
+  const bool pairs = ((p.y | a.nx) & 1) == 0;
   for (; u < MM; u += STEP) {
     const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
-    // O and dO rows are 8-byte aligned only: two 8-byte loads each
-    const float2 o0 = __ldg(a.O + r), o1 = __ldg(a.O + r + 1);
-    const float2 d0 = __ldg(a.dO + r), d1 = __ldg(a.dO + r + 1);
+    float2 o0, o1, d0, d1;
+    if (pairs) {
+      const float4 oq = __ldg(reinterpret_cast<const float4*>(a.O + r));
+      const float4 dq = __ldg(reinterpret_cast<const float4*>(a.dO + r));
+      o0 = make_float2(oq.x, oq.y), o1 = make_float2(oq.z, oq.w);
+      d0 = make_float2(dq.x, dq.y), d1 = make_float2(dq.z, dq.w);
+    } else {
+      o0 = __ldg(a.O + r), o1 = __ldg(a.O + r + 1);
+      d0 = __ldg(a.dO + r), d1 = __ldg(a.dO + r + 1);
+    }
     float4 xv[K], pr[K], dp[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
