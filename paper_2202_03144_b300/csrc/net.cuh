@@ -162,31 +162,41 @@ template <int NP>
 __host__ __device__ constexpr int tc_ncols() { return NP < 32 ? 32 : NP; }
 template <int NP>
 __host__ __device__ constexpr size_t conv_tc_smem() {
-  return 2 * ((size_t)128 * TC_KC * 2 + (size_t)NP * TC_KC * 2) + 64;
+  // two (A, B) stages, the per-pixel tap offsets [9][128], mbarriers
+  return 2 * ((size_t)128 * TC_KC * 2 + (size_t)NP * TC_KC * 2) + 9 * 128 * 4 + 64;
 }
 
-template <bool OUT_F32, int NP>
+// NHWC = true (inference): activations channel-last [B][h][w][c] and the
+// weights tap-major [co][tap][ci], i.e. k = tap * ci + c.  With ci a power of
+// two >= 8, each group of 8 consecutive k is 8 channels of one tap of one
+// input pixel: one 16-byte load instead of eight gathered elements; the
+// output tile is written as 16-byte channel vectors (the last layer stays
+// FP32 [B][co][h][w]).
+template <bool OUT_F32, int NP, bool NHWC = false>
 __global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvArgs a, int ksplit, float* part, int* err_flag) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr size_t ABYTES = 128 * TC_KC * 2, BBYTES = (size_t)NP * TC_KC * 2;
   unsigned char* stage[2] = {smem_raw, smem_raw + ABYTES + BBYTES};
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (ABYTES + BBYTES));  // [2]
+  int* offs = reinterpret_cast<int*>(smem_raw + 2 * (ABYTES + BBYTES));  // [9][128]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(offs + 9 * 128);            // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   constexpr uint32_t LBO = 128, SBO = (TC_KC / 8) * 128;
   constexpr uint32_t NCOLS = tc_ncols<NP>();
   const __nv_bfloat16* in = reinterpret_cast<const __nv_bfloat16*>(a.in);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const long long npix = (long long)a.B * a.hout * a.wout;
-  const long long p = (long long)blockIdx.x * 128 + tid;
+  const int npix = a.B * a.hout * a.wout;  // < 2^31 for every supported batch
+  const int p = blockIdx.x * 128 + tid;
   const bool valid = p < npix;
-  const int n = valid ? (int)(p / (a.hout * a.wout)) : 0;
-  const int y = valid ? (int)((p / a.wout) % a.hout) : 0;
-  const int x = valid ? (int)(p % a.wout) : 0;
-  int off[9];  // input offset of each tap within a channel plane, -1 outside
+  const int hw = a.hout * a.wout;
+  const int n = valid ? p / hw : 0;
+  const int yx = valid ? p - n * hw : 0;
+  const int y = yx / a.wout, x = yx - y * a.wout;
+  // input offset of each tap within a channel plane (-1 outside), kept in
+  // shared memory so that the gather indexes it by the tap of each k
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int yy = net_src(y, t / 3, a.stride, a.up, a.hin), xx = net_src(x, t % 3, a.stride, a.up, a.win);
-    off[t] = (valid && yy >= 0 && xx >= 0) ? yy * a.win + xx : -1;
+    offs[t * 128 + tid] = (valid && yy >= 0 && xx >= 0) ? yy * a.win + xx : -1;
   }
   if (tid == 0) {
     tc::mbar_init1(&bar[0]);
@@ -219,25 +229,53 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvArgs a, int ksplit, flo
     unsigned char* As = stage[s];
     unsigned char* Bs = stage[s] + ABYTES;
     const int k0 = c * TC_KC;
-    // A: this thread's pixel (row tid), 64 values of k = ci * 9 + tap
-    int ci = k0 / 9, t = k0 - 9 * (k0 / 9);
+    if (NHWC && a.ci >= 8) {
+      // A: 8 groups of 8 channels of one tap, 16-byte loads all in flight
+      const int lg = 31 - __clz(a.ci);
+      const __nv_bfloat16* img = in + (size_t)n * plane * a.ci;
+      uint4 q[TC_KC / 8];
 #pragma unroll
-    for (int g = 0; g < TC_KC / 8; ++g) {
-      __align__(16) __nv_bfloat16 v8[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        // select off[t] without indexing the register array
-        const int o = t < 3 ? (t == 0 ? off[0] : t == 1 ? off[1] : off[2])
-                            : t < 6 ? (t == 3 ? off[3] : t == 4 ? off[4] : off[5])
-                                    : (t == 6 ? off[6] : t == 7 ? off[7] : off[8]);
-        const bool in_k = ci < a.ci;
-        v8[e] = (in_k && o >= 0) ? src[ci * plane + o] : __float2bfloat16_rn(0.f);
-        if (++t == 9) {
-          t = 0;
-          ++ci;
-        }
+      for (int g = 0; g < TC_KC / 8; ++g) {
+        const int k = k0 + 8 * g;
+        const int o = k < K ? offs[(k >> lg) * 128 + tid] : -1;
+        q[g] = o >= 0 ? __ldg(reinterpret_cast<const uint4*>(img + (size_t)o * a.ci + (k & (a.ci - 1))))
+                      : make_uint4(0u, 0u, 0u, 0u);
       }
-      *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = *reinterpret_cast<const uint4*>(v8);
+#pragma unroll
+      for (int g = 0; g < TC_KC / 8; ++g)
+        *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = q[g];
+    } else {
+    // A: this thread's pixel (row tid), 64 values of k = ci * 9 + tap, in
+    // two halves of 32 independent loads (one memory latency per half, not
+    // one per group of 8); halves past the end of K are zeros (NHWC with
+    // ci = 1 is the same layout)
+    int ci = k0 / 9, t = k0 - 9 * (k0 / 9);
+    const unsigned short* src16 = reinterpret_cast<const unsigned short*>(src);
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      uint32_t w[16];
+      if (k0 + 32 * hh < K) {
+        unsigned short raw[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int o = ci < a.ci ? offs[t * 128 + tid] : -1;
+          raw[e] = o >= 0 ? __ldg(src16 + ci * plane + o) : (unsigned short)0;
+          if (++t == 9) {
+            t = 0;
+            ++ci;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) w[e] = (uint32_t)raw[2 * e] | ((uint32_t)raw[2 * e + 1] << 16);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) w[e] = 0u;
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+        *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + (4 * hh + g) * LBO + (tid & 7) * 16) =
+            make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+    }
     }
     // B: weight rows (output channels) tid, tid + 128
     for (int r = tid; r < NP; r += 128) {
@@ -284,7 +322,20 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvArgs a, int ksplit, flo
   for (int c0 = 0; c0 < NP; c0 += 16) {
     float v[16];
     tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (valid) {
+    if (NHWC && !OUT_F32 && ksplit == 1 && valid) {
+      // 16 channels of this pixel: two 16-byte stores (co is a multiple of 16)
+      uint32_t pk[8];
+#pragma unroll
+      for (int j = 0; j < 16; j += 2) {
+        float r0 = v[j] + a.b[c0 + j], r1 = v[j + 1] + a.b[c0 + j + 1];
+        if (a.relu) r0 = fmaxf(r0, 0.f), r1 = fmaxf(r1, 0.f);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0, r1);
+        pk[j / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + (size_t)p * a.co + c0);
+      dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    } else if (valid) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int co = c0 + j;
@@ -306,8 +357,9 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvArgs a, int ksplit, flo
   if (warp == 0) tc::tmem_free(tbase, NCOLS);
 }
 
-// Split-K epilogue: out = act(bias + sum of the ksplit partial tiles, in order).
-template <bool OUT_F32>
+// Split-K epilogue: out = act(bias + sum of the ksplit partial tiles, in
+// order), into [B][co][h][w] or (NHWC, BF16) [B][h][w][co].
+template <bool OUT_F32, bool NHWC = false>
 __global__ void k_conv_tc_reduce(ConvArgs a, int ksplit, const float* __restrict__ part) {
   const long long npix = (long long)a.B * a.hout * a.wout;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix * a.co;
@@ -319,9 +371,91 @@ __global__ void k_conv_tc_reduce(ConvArgs a, int ksplit, const float* __restrict
     if (a.relu) r = fmaxf(r, 0.f);
     const int n = (int)(p / (a.hout * a.wout));
     const int yx = (int)(p % (a.hout * a.wout));
-    const size_t o = ((size_t)n * a.co + co) * a.hout * a.wout + yx;
+    const size_t o = (NHWC && !OUT_F32) ? (size_t)p * a.co + co : ((size_t)n * a.co + co) * a.hout * a.wout + yx;
     if (OUT_F32) reinterpret_cast<float*>(a.out)[o] = r;
     else reinterpret_cast<__nv_bfloat16*>(a.out)[o] = __float2bfloat16_rn(r);
+  }
+}
+
+// First layer of the inference forward (1 -> 16 channels, 3 x 3, stride 1)
+// on the CUDA cores: 144 FMAs per pixel do not pay for a tensor-core tile.
+// Thread = one output pixel; output channel-last BF16 (two 16-byte stores).
+__global__ void __launch_bounds__(256) k_conv_first_nhwc(ConvArgs a) {
+  __shared__ float ws[16][9];
+  __shared__ float bs[16];
+  for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i / 9][i % 9] = __bfloat162float(a.w[i]);
+  if (threadIdx.x < 16) bs[threadIdx.x] = a.b[threadIdx.x];
+  __syncthreads();
+  const __nv_bfloat16* in = reinterpret_cast<const __nv_bfloat16*>(a.in);
+  const int hw = a.hout * a.wout, npix = a.B * hw;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const int n = p / hw, yx = p - n * hw, y = yx / a.wout, x = yx - y * a.wout;
+    float v[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int yy = net_src(y, t / 3, a.stride, a.up, a.hin), xx = net_src(x, t % 3, a.stride, a.up, a.win);
+      v[t] = (yy >= 0 && xx >= 0) ? __bfloat162float(in[((size_t)n * a.hin + yy) * a.win + xx]) : 0.f;
+    }
+    uint32_t pk[8];
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) {
+      float r0 = 0.f, r1 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        r0 = fmaf(ws[c][t], v[t], r0);
+        r1 = fmaf(ws[c + 1][t], v[t], r1);
+      }
+      r0 = fmaxf(r0 + bs[c], 0.f);
+      r1 = fmaxf(r1 + bs[c + 1], 0.f);
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0, r1);
+      pk[c / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + (size_t)p * 16);
+    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  }
+}
+
+// Last layer of the inference forward (16 -> 2 channels, 3 x 3, no ReLU) on
+// the CUDA cores, from channel-last BF16 input (tap-major weights) to the
+// FP32 [B][2][h][w] output.  Thread = one output pixel.
+__global__ void __launch_bounds__(256) k_conv_last_nhwc(ConvArgs a) {
+  __shared__ float ws[2][9][16];
+  for (int i = threadIdx.x; i < 2 * 9 * 16; i += blockDim.x) ws[i / 144][(i / 16) % 9][i % 16] = __bfloat162float(a.w[i]);
+  __syncthreads();
+  const __nv_bfloat16* in = reinterpret_cast<const __nv_bfloat16*>(a.in);
+  const int hw = a.hout * a.wout, npix = a.B * hw;
+  float* out = reinterpret_cast<float*>(a.out);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const int n = p / hw, yx = p - n * hw, y = yx / a.wout, x = yx - y * a.wout;
+    float r0 = 0.f, r1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int yy = net_src(y, t / 3, a.stride, a.up, a.hin), xx = net_src(x, t % 3, a.stride, a.up, a.win);
+      if (yy < 0 || xx < 0) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(in + (((size_t)n * a.hin + yy) * a.win + xx) * 16);
+      const uint4 q[2] = {__ldg(src), __ldg(src + 1)};
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(q);
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) {
+        const float2 f = __bfloat1622float2(h[c / 2]);
+        r0 = fmaf(ws[0][t][c], f.x, r0);
+        r0 = fmaf(ws[0][t][c + 1], f.y, r0);
+        r1 = fmaf(ws[1][t][c], f.x, r1);
+        r1 = fmaf(ws[1][t][c + 1], f.y, r1);
+      }
+    }
+    out[(size_t)(n * 2) * hw + yx] = r0 + a.b[0];
+    out[(size_t)(n * 2 + 1) * hw + yx] = r1 + a.b[1];
+  }
+}
+
+// Tap-major copy of one layer's BF16 weights: wt[co][tap][ci] = w[co][ci][tap].
+__global__ void k_perm_weights(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt, int co, int ci) {
+  const int n = co * ci * 9;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int o = i / (9 * ci), r = i - o * 9 * ci, t = r / ci, c = r - t * ci;
+    wt[i] = w[((size_t)o * ci + c) * 9 + t];
   }
 }
 

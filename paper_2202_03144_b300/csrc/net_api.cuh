@@ -12,7 +12,9 @@ struct ptycho_net {
   float* grads = nullptr;
   float* m = nullptr;
   float* v = nullptr;
-  __nv_bfloat16* wb = nullptr;  // BF16 weights
+  __nv_bfloat16* wb = nullptr;  // BF16 weights [co][ci][9]
+  __nv_bfloat16* wt = nullptr;  // the same, tap-major [co][9][ci] (inference path)
+  bool wt_valid = false;        // wt matches wb
   unsigned char* is_w = nullptr;
   int* wb_index = nullptr;
   bool f32 = false;             // FP32 activations (verification mode)
@@ -126,19 +128,61 @@ size_t tc_part_size(int max_batch) {
   return m;
 }
 
-template <int NP>
+template <int NP, bool NHWC = false>
 void launch_conv_tc(ptycho_net* n, const ConvArgs& a, const NetLayer& L, bool out_f32) {
   const long long npix = (long long)a.B * a.hout * a.wout;
   const int ks = tc_ksplit(L, a.B);
   const dim3 g((unsigned)((npix + 127) / 128), (unsigned)ks);
-  if (out_f32) k_conv_fwd_tc<true, NP><<<g, 128, conv_tc_smem<NP>(), n->st>>>(a, ks, n->tc_part, n->err_flag);
-  else k_conv_fwd_tc<false, NP><<<g, 128, conv_tc_smem<NP>(), n->st>>>(a, ks, n->tc_part, n->err_flag);
+  if (out_f32) k_conv_fwd_tc<true, NP, NHWC><<<g, 128, conv_tc_smem<NP>(), n->st>>>(a, ks, n->tc_part, n->err_flag);
+  else k_conv_fwd_tc<false, NP, NHWC><<<g, 128, conv_tc_smem<NP>(), n->st>>>(a, ks, n->tc_part, n->err_flag);
   if (ks > 1) {
     const long long tot = npix * a.co;
     const unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 4 * 1184);
-    if (out_f32) k_conv_tc_reduce<true><<<rb, 256, 0, n->st>>>(a, ks, n->tc_part);
-    else k_conv_tc_reduce<false><<<rb, 256, 0, n->st>>>(a, ks, n->tc_part);
+    if (out_f32) k_conv_tc_reduce<true, NHWC><<<rb, 256, 0, n->st>>>(a, ks, n->tc_part);
+    else k_conv_tc_reduce<false, NHWC><<<rb, 256, 0, n->st>>>(a, ks, n->tc_part);
   }
+}
+
+// Inference forward (predict, warm start): the tensor-core convolutions on
+// channel-last activations with tap-major weights (see k_conv_fwd_tc).  The
+// sums run in another order than the training forward, so the two agree to
+// FP32 rounding, then BF16 rounding per layer.
+static_assert(net_layer(0).ci == 1 && net_layer(0).co == 16 && net_layer(0).relu, "first-layer kernel shape");
+static_assert(net_layer(NET_LAYERS - 1).ci == 16 && net_layer(NET_LAYERS - 1).co == 2 &&
+                  !net_layer(NET_LAYERS - 1).relu && !net_layer(NET_LAYERS - 1).up,
+              "last-layer kernel shape");
+
+int net_infer(ptycho_net* n, int B) {
+  if (!n->wt_valid) {
+    for (int l = 0; l < NET_LAYERS; ++l) {
+      const NetLayer L = net_layer(l);
+      k_perm_weights<<<256, 256, 0, n->st>>>(n->wb + n->wb_off[l], n->wt + n->wb_off[l], L.co, L.ci);
+    }
+    n->wt_valid = true;
+  }
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    ConvArgs a = conv_args(n, l, B);
+    a.w = n->wt + n->wb_off[l];
+    const bool last = l == NET_LAYERS - 1;
+    a.out = last ? (void*)n->out : n->act[l];
+    if (l == 0 || last) {  // 1 -> 16 and 16 -> 2 channels: CUDA cores
+      const int npix = B * L.hout * L.wout;
+      const unsigned g = (unsigned)std::min(4 * 148 * 8, (npix + 255) / 256);
+      if (l == 0) k_conv_first_nhwc<<<g, 256, 0, n->st>>>(a);
+      else k_conv_last_nhwc<<<g, 256, 0, n->st>>>(a);
+      continue;
+    }
+    const int np = L.co <= 16 ? 16 : L.co;
+    switch (np) {
+      case 16: launch_conv_tc<16, true>(n, a, L, last); break;
+      case 32: launch_conv_tc<32, true>(n, a, L, last); break;
+      case 64: launch_conv_tc<64, true>(n, a, L, last); break;
+      case 128: launch_conv_tc<128, true>(n, a, L, last); break;
+      default: launch_conv_tc<256, true>(n, a, L, last); break;
+    }
+  }
+  return net_check(n, "inference forward (tensor cores)");
 }
 
 int net_forward_tc(ptycho_net* n, int B) {
@@ -163,6 +207,9 @@ int net_forward(ptycho_net* n, int B) {
   if (n->f32) return net_forward_t<float>(n, B);
   return n->tc ? net_forward_tc(n, B) : net_forward_t<__nv_bfloat16>(n, B);
 }
+
+// Forward pass for predictions only (no backward pass follows).
+int net_predict_forward(ptycho_net* n, int B) { return n->tc ? net_infer(n, B) : net_forward(n, B); }
 
 // Loss against targets and all parameter gradients (into n->grads).
 int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
@@ -243,6 +290,7 @@ int net_upload_params(ptycho_net* n, const float* host) {
   cudaError_t e = cudaMemcpy(n->params, host, n->n_params * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(n->wb, wb.data(), n->n_w * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "parameter upload: %s", cudaGetErrorString(e));
+  n->wt_valid = false;
   return 0;
 }
 
@@ -286,6 +334,7 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
   if (!r) r = nalloc(n, &n->m, n->n_params);
   if (!r) r = nalloc(n, &n->v, n->n_params);
   if (!r) r = nalloc(n, &n->wb, n->n_w);
+  if (!r && n->tc) r = nalloc(n, &n->wt, n->n_w);
   if (!r) r = nalloc(n, &n->is_w, n->n_params);
   if (!r) r = nalloc(n, &n->wb_index, n->n_params);
   const size_t asz = n->f32 ? 4 : 2;
@@ -315,6 +364,16 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     setsm((const void*)k_conv_fwd_tc<true, 128>, conv_tc_smem<128>());
     setsm((const void*)k_conv_fwd_tc<false, 256>, conv_tc_smem<256>());
     setsm((const void*)k_conv_fwd_tc<true, 256>, conv_tc_smem<256>());
+    setsm((const void*)k_conv_fwd_tc<false, 16, true>, conv_tc_smem<16>());
+    setsm((const void*)k_conv_fwd_tc<true, 16, true>, conv_tc_smem<16>());
+    setsm((const void*)k_conv_fwd_tc<false, 32, true>, conv_tc_smem<32>());
+    setsm((const void*)k_conv_fwd_tc<true, 32, true>, conv_tc_smem<32>());
+    setsm((const void*)k_conv_fwd_tc<false, 64, true>, conv_tc_smem<64>());
+    setsm((const void*)k_conv_fwd_tc<true, 64, true>, conv_tc_smem<64>());
+    setsm((const void*)k_conv_fwd_tc<false, 128, true>, conv_tc_smem<128>());
+    setsm((const void*)k_conv_fwd_tc<true, 128, true>, conv_tc_smem<128>());
+    setsm((const void*)k_conv_fwd_tc<false, 256, true>, conv_tc_smem<256>());
+    setsm((const void*)k_conv_fwd_tc<true, 256, true>, conv_tc_smem<256>());
     if (!r && e2 != cudaSuccess) r = nfail(n, PTYCHO_ERR_CUDA, "tensor-core kernel setup: %s", cudaGetErrorString(e2));
   }
   if (r) {
@@ -376,7 +435,7 @@ int ptycho_net_predict(ptycho_net* n, const float* intensities, int B, float* ou
   if (!n || !intensities || !out) return PTYCHO_ERR_ARG;
   if (B < 1 || B > n->max_batch) return nfail(n, PTYCHO_ERR_ARG, "batch %d outside [1, %d]", B, n->max_batch);
   if (int r = net_input(n, intensities, B)) return r;
-  if (int r = net_forward(n, B)) return r;
+  if (int r = net_predict_forward(n, B)) return r;
   cudaError_t e = cudaMemcpyAsync(out, n->out, act_size(NET_LAYERS - 1, B) * sizeof(float), cudaMemcpyDeviceToDevice,
                                   n->st);
   if (e != cudaSuccess) return nfail(n, PTYCHO_ERR_CUDA, "predict: %s", cudaGetErrorString(e));
@@ -424,6 +483,7 @@ int ptycho_net_train_step(ptycho_net* n, const float* intensities, const float* 
   a.c1 = (float)(1.0 - std::pow(0.9, (double)n->adam_t));
   a.c2 = (float)(1.0 - std::pow(0.999, (double)n->adam_t));
   k_adam<<<1184, 256, 0, n->st>>>(a);
+  n->wt_valid = false;
   return net_check(n, "adam");
 }
 
@@ -433,7 +493,7 @@ void ptycho_net_destroy(ptycho_net* n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
   else cudaDeviceSynchronize();
-  void* bufs[] = {n->tc_part, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->is_w,     n->wb_index,
+  void* bufs[] = {n->tc_part, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->wt,       n->is_w,     n->wb_index,
                   n->x,      n->out,   n->wpart, n->lpart, n->delta[0], n->delta[1]};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -467,7 +527,7 @@ int ptycho_warm_start(ptycho_ctx* ctx, ptycho_net* n) {
   for (int j0 = 0; j0 < J && !rc; j0 += n->max_batch) {
     const int B = std::min(n->max_batch, J - j0);
     rc = net_input_src(n, ctx->amp, 1, ctx->p.istore, ctx->amp_scale, j0, B);
-    if (!rc) rc = net_forward(n, B);
+    if (!rc) rc = net_predict_forward(n, B);
     if (!rc && cudaMemcpyAsync(pred + (size_t)j0 * 2 * NET_OUT * NET_OUT, n->out,
                                act_size(NET_LAYERS - 1, B) * sizeof(float), cudaMemcpyDeviceToDevice,
                                n->st) != cudaSuccess)

@@ -113,3 +113,34 @@ def test_tensor_core_forward_matches_cuda_cores():
     e = np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1])
     print("tensor-core vs CUDA-core forward:", e)
     assert e < 1e-2
+
+
+def test_inference_forward_follows_parameter_updates():
+    """The inference forward (channel-last tensor-core convolutions with a
+    cached tap-major copy of the weights) tracks every parameter change:
+    after a training step and after set_params its predictions match a
+    CUDA-core network holding the same parameters (1e-2, summation order)."""
+    torch = pytest.importorskip("torch")
+    I, t = _batch(4, 6)
+    It, tt = torch.from_numpy(I).cuda(), torch.from_numpy(t).cuda()
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+    with api.Net(seed=21, max_batch=4) as net, api.Net(seed=0, max_batch=4, cuda_cores=True) as ref:
+        o = torch.empty((4, 2, 64, 64), dtype=torch.float32, device="cuda")
+        r = torch.empty_like(o)
+        net.predict(It, o)  # builds the cached weights
+        net.train_step(It, tt, 1e-2)
+        ref.set_params(net.get_params())
+        net.predict(It, o)
+        ref.predict(It, r)
+        torch.cuda.synchronize()
+        assert rel(o, r) < 1e-2
+        p2 = (net.get_params() * 0.7).astype(np.float32)
+        net.set_params(p2)
+        ref.set_params(p2)
+        net.predict(It, o)
+        ref.predict(It, r)
+        torch.cuda.synchronize()
+        assert rel(o, r) < 1e-2
