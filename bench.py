@@ -476,9 +476,17 @@ def main():
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                    "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    # DRAM traffic of the residual pass from an ncu capture of the same kernel
+    # on a 2500-position cut (profiles/fourier_chi_det256_2500pos.md): bytes
+    # per position, scaled to this launch's positions (amplitudes in,
+    # residuals out: traffic grows in proportion).  Only for the kernel and
+    # shape that capture measured.
+    traffic = None
+    if top[0] == "fourier_chi" and (M, K) == (256, 1) and not args.cluster:
+        traffic = 770.7e3 * J
     if top[0].startswith("fourier"):
         # The fused Fourier kernel is bound by FP32 arithmetic issue, not by
-        # DRAM (ncu: 11.5% DRAM, 48% issue-active): report it against the FP32
+        # DRAM (ncu: 16% DRAM, 50% issue-active): report it against the FP32
         # peak from the unit counts and clock (148 SMs x 128 FP32 lanes x 2
         # FLOP x 2.032 GHz), counting the forward + inverse 2-D FFT of each
         # (position, mode) at 5 N log2 N FLOP (N = M^2).
@@ -487,7 +495,8 @@ def main():
         ach = fft_flop / (ms_launch / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": top[0], "achieved": ach, "peak": peak_fp32, "unit": "TFLOP/s",
                 "frac": ach / peak_fp32, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
-                "flop_per_launch": fft_flop, "ms_per_launch": ms_launch, "traffic": None,
+                "flop_per_launch": fft_flop, "ms_per_launch": ms_launch, "traffic": traffic,
+                "traffic_source": "ncu capture of the 2500-position cut, scaled per position" if traffic else None,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
                         "peak_kind": peak_kind, "bytes_per_launch": bytes_launch},
                 "share_of_step": top[1]["ms"] / total_ms, "kernels": kernels}
