@@ -135,10 +135,45 @@ def fourier_error(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) 
     return num / den if den > 0 else 0.0
 
 
-def fourier_residual(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) -> np.ndarray:
-    """chi_{j,k} = F^-1 Pi(F(P_k O_j)) - P_k O_j, shape [J, K, M, M]."""
+def poisson_correction(Psi: np.ndarray, I_fft: np.ndarray, tau: float = TAU) -> np.ndarray:
+    """Detector-plane correction of the Poisson likelihood (Odstrcil et al.
+    2018, the maximum-likelihood exit-wave update for photon-counting noise).
+
+    With A^2 = sum_k |Psi_k|^2 the negative log-likelihood of the counts is
+    L = sum_q (A^2 - I log A^2); its steepest-descent direction in Psi_k is
+    (I / A^2 - 1) Psi_k.  Masked pixels (I < 0) contribute nothing (0); where
+    A <= tau the direction is -Psi_k (the modulus there is taken as zero, as in
+    :func:`project`)."""
+    A2 = np.sum(np.abs(Psi) ** 2, axis=1)
+    masked = I_fft < 0
+    big = A2 > tau * tau
+    f = np.where(big, np.where(masked, 0.0, I_fft) / np.where(big, A2, 1.0) - 1.0, -1.0)
+    f = np.where(masked, 0.0, f)
+    return Psi * f[:, None, :, :]
+
+
+def poisson_nll(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) -> float:
+    """sum over unmasked pixels of A^2 - I log A^2 at the current (O, P)."""
+    I_fft = to_fft_order(I)
+    A2 = np.sum(np.abs(fft2(exit_waves(O, P, pos))) ** 2, axis=1)
+    m = I_fft >= 0
+    return float(np.sum(np.where(m, A2 - np.where(m, I_fft, 0.0) * np.log(np.where(m, A2, 1.0)), 0.0)))
+
+
+def fourier_residual(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray,
+                     likelihood: str = "amplitude") -> np.ndarray:
+    """Exit-wave residual chi_{j,k}, shape [J, K, M, M].
+
+    amplitude (Gaussian noise on sqrt I): chi = F^-1 Pi(F(P_k O_j)) - P_k O_j;
+    poisson: chi = F^-1 [(I / A^2 - 1) F(P_k O_j)] (:func:`poisson_correction`),
+    i.e. -1/M^2 times the Wirtinger gradient of the Poisson negative
+    log-likelihood with respect to the conjugate exit wave."""
     phi = exit_waves(O, P, pos)
-    return ifft2(project(fft2(phi), to_fft_order(I))) - phi
+    if likelihood == "amplitude":
+        return ifft2(project(fft2(phi), to_fft_order(I))) - phi
+    if likelihood == "poisson":
+        return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))
+    raise ValueError(likelihood)
 
 
 # ---------------------------------------------------------------------------
@@ -335,10 +370,13 @@ def lsqml_step_sizes(O, P, chi, pos, dO, dP):
     return aO, aP
 
 
-def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_steps=False):
+def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_steps=False,
+                    likelihood="amplitude"):
     """One LSQML iteration (index t); returns new (O, P) [and (alpha_O, alpha_P)].
 
-    1. chi_jk = F^-1 Pi(F(P_k O_j)) - P_k O_j;
+    1. chi_jk = F^-1 Pi(F(P_k O_j)) - P_k O_j (amplitude likelihood) or the
+       Poisson correction F^-1[(I / A^2 - 1) F(P_k O_j)] (see
+       :func:`fourier_residual`);
     2. directions dO, dP (see :func:`lsqml_directions`);
     3. per-position step sizes (see :func:`lsqml_step_sizes`);
     4. O <- O + beta sum_j S_j[alpha_O,j sum_k conj(P_k) chi_jk] / (den_O + d_O),
@@ -348,7 +386,7 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
     O = O.astype(np.complex128)
     P = P.astype(np.complex128)
     upd = t >= probe_start
-    chi = fourier_residual(O, P, pos, I)
+    chi = fourier_residual(O, P, pos, I, likelihood)
     dO, dP, wO, wP = lsqml_directions(O, P, chi, pos, reg, upd)
     aO, aP = lsqml_step_sizes(O, P, chi, pos, dO, dP)
     O_new = O + beta * object_numerator(P, chi, pos, O.shape, weights=aO) / wO
@@ -366,7 +404,7 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
 # ---------------------------------------------------------------------------
 
 def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, reg=1e-3,
-                epie_alpha=1.0, epie_beta=1.0, lsqml_beta=0.9, probe_start=0):
+                epie_alpha=1.0, epie_beta=1.0, lsqml_beta=0.9, probe_start=0, likelihood="amplitude"):
     """Run n_iter iterations of 'epie', 'dm' or 'lsqml' starting at index t0.
 
     Returns (O, P, psi) -- psi is the DM state (None for the others)."""
@@ -382,7 +420,7 @@ def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, re
                 psi = dm_init(O, P, pos)
             O, P, psi = dm_iteration(O, P, psi, pos, I, t, reg, probe_start)
         elif alg == "lsqml":
-            O, P = lsqml_iteration(O, P, pos, I, t, reg, lsqml_beta, probe_start)
+            O, P = lsqml_iteration(O, P, pos, I, t, reg, lsqml_beta, probe_start, likelihood=likelihood)
         else:
             raise ValueError(alg)
     return O, P, psi

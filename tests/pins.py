@@ -384,10 +384,72 @@ def pin_lsqml_directions(orc):
         assert abs(dP[k, u, v] * wP[u, v] + g) < 1e-6 * (1 + abs(g)), "LSQML probe direction"
 
 
+def pin_poisson_correction_gradient(orc):
+    """The Poisson correction, taken back to the exit wave, is -1/M^2 times the
+    Wirtinger gradient of the Poisson negative log-likelihood
+    L(psi) = sum_unmasked (A^2 - I log A^2), A^2 = sum_k |F psi_k|^2
+    (central differences on the real and imaginary parts of psi)."""
+    rng = np.random.default_rng(12)
+    M, K = 4, 2
+    psi = _crandn(1, K, M, M, rng=rng)
+    I = rng.uniform(0.5, 20.0, (1, M, M))
+    I[0, 1, 2] = -1.0  # a masked pixel
+    I[0, 3, 0] = -1.0
+
+    def L(ps):
+        A2 = np.sum(np.abs(np.fft.fft2(ps)) ** 2, axis=1)
+        m = I >= 0
+        return float(np.sum(np.where(m, A2 - np.where(m, I, 0) * np.log(A2), 0.0)))
+
+    chi = np.fft.ifft2(orc.poisson_correction(np.fft.fft2(psi), I))
+    h = 1e-6
+    for (k, u, v) in [(0, 0, 0), (0, 2, 3), (1, 1, 1), (1, 3, 2)]:
+        e = np.zeros_like(psi)
+        e[0, k, u, v] = h
+        g = ((L(psi + e) - L(psi - e)) + 1j * (L(psi + 1j * e) - L(psi - 1j * e))) / (2 * h) / 2
+        assert abs(chi[0, k, u, v] + g / M ** 2) < 1e-6 * (1 + abs(g)), "Poisson correction gradient"
+    # fully masked frame: no correction; vanishing modulus: -Psi
+    Psi = np.fft.fft2(psi)
+    assert np.allclose(orc.poisson_correction(Psi, -np.ones_like(I)), 0.0)
+    Z = Psi.copy()
+    Z[0, :, 0, 0] = 0.0
+    assert np.allclose(orc.poisson_correction(Z, I)[0, :, 0, 0], 0.0)
+    Z[0, :, 0, 0] = 1e-40
+    assert np.allclose(orc.poisson_correction(Z, I)[0, :, 0, 0], -Z[0, :, 0, 0], atol=0)
+
+
+def pin_lsqml_poisson_object_gradient(orc):
+    """With the Poisson residual, the LSQML object direction times its
+    denominator is -1/M^2 times the Wirtinger gradient of the Poisson
+    negative log-likelihood with respect to the object (central differences
+    of :func:`poisson_nll`), which ties the residual, the gather and the
+    scatter together; and noise-free data is a fixed point."""
+    M = 6
+    P, O, pos = small_scan(M=M, K=2, grid=2, step=3)
+    pos = orc.round_positions(pos)
+    rng = np.random.default_rng(4)
+    I = orc.far_field_intensity(O * (1 + 0.1 * _crandn(*O.shape, rng=rng)), P, pos)
+    I = orc.to_fft_order(orc.to_fft_order(I))  # detector-centred, unchanged
+    I[0, 2, 2] = -1.0
+    chi = orc.fourier_residual(O, P, pos, I, likelihood="poisson")
+    dO, _, wO, _ = orc.lsqml_directions(O, P, chi, pos, 1e-3, False)
+    h = 1e-6
+    for (u, v) in [(pos[0][0] + 1, pos[0][1] + 2), (pos[-1][0] + 3, pos[-1][1] + 4)]:
+        e = np.zeros_like(O)
+        e[u, v] = h
+        f = lambda Ov: orc.poisson_nll(Ov, P, pos, I)
+        g = ((f(O + e) - f(O - e)) + 1j * (f(O + 1j * e) - f(O - 1j * e))) / (2 * h) / 2
+        assert abs(dO[u, v] * wO[u, v] + g / M ** 2) < 1e-6 * (1 + abs(g)), "Poisson LSQML object direction"
+    P0, O0, pos0, I0 = _truth_case(orc)
+    O1, P1 = orc.lsqml_iteration(O0, P0, pos0, I0, t=0, likelihood="poisson")
+    assert np.allclose(O1, O0, atol=1e-12) and np.allclose(P1, P0, atol=1e-12), "Poisson LSQML moved off the truth"
+
+
 ALL_PINS = [
     pin_fft_bruteforce, pin_parseval, pin_forward_bruteforce, pin_mode_mixing_invariance,
     pin_gather_scatter_adjoint, pin_rounding, pin_projection, pin_fourier_error,
     pin_fixed_points, pin_epie_er_special_case, pin_epie_gradient, pin_epie_order,
     pin_dm_overlap_least_squares, pin_dm_all_masked, pin_lsqml_step_sizes,
     pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
+    pin_poisson_correction_gradient, pin_lsqml_poisson_object_gradient,
 ]
