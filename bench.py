@@ -423,10 +423,10 @@ def main():
         P0s = P0 * np.sqrt(scale)
     stream.synchronize()
 
-    def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False):
+    def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False, likelihood="amplitude"):
         with torch.cuda.stream(stream):
             r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore,
-                                   cluster=args.cluster)
+                                   cluster=args.cluster, likelihood=likelihood)
             r.set_data(I, pos)
             r.set_init(np.ones((w["obj"], w["obj"]), np.complex64), P0s)
             r.iterate(alg, warm)
@@ -459,6 +459,7 @@ def main():
     dm_run = timed("dm")
     f16_run = timed("lsqml", istore="f16")
     bf16_run = timed("lsqml", istore="bf16")
+    poisson_run = timed("lsqml", likelihood="poisson")
     prof_run = timed("lsqml", steps=3, warm=1, profile=True)
 
     def rate(run):
@@ -561,6 +562,7 @@ def main():
             "lsqml_f32": {"value": value, "fourier_error": main_run["err"]},
             "dm_f32": {"value": rate(dm_run), "fourier_error": dm_run["err"]},
             "lsqml_f16": {"value": rate(f16_run), "fourier_error": f16_run["err"]},
+            "lsqml_poisson_f32": {"value": rate(poisson_run), "fourier_error": poisson_run["err"]},
             "lsqml_bf16": {"value": rate(bf16_run), "fourier_error": bf16_run["err"]},
         },
         "batched": batched,

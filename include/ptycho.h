@@ -58,6 +58,9 @@ enum { PTYCHO_EPIE = 0, PTYCHO_DM = 1, PTYCHO_LSQML = 2 };
  * all arithmetic stays float32. */
 enum { PTYCHO_I_F32 = 0, PTYCHO_I_F16 = 1, PTYCHO_I_BF16 = 2 };
 
+/* LSQML likelihood (ptycho_params.likelihood). */
+enum { PTYCHO_LIK_AMPLITUDE = 0, PTYCHO_LIK_POISSON = 1 };
+
 #define PTYCHO_OK 0
 #define PTYCHO_ERR_ARG (-1)         /* bad argument or size                     */
 #define PTYCHO_ERR_BOUNDS (-2)      /* a patch falls outside the object         */
@@ -89,6 +92,15 @@ typedef struct {
   int cluster;      /* CTAs per scan position in the Fourier kernel: 0 = the
                        built-in choice, -1 = autotuned (ptycho_autotune),
                        > 0 = that size (must be compiled for (M, K))          */
+  int likelihood;   /* LSQML noise model (Odstrcil et al. 2018, cited for
+                       LSQML in Sec. 1): PTYCHO_LIK_AMPLITUDE (default,
+                       Gaussian noise on sqrt I: chi = F^-1 Pi F(phi) - phi)
+                       or PTYCHO_LIK_POISSON (photon counts:
+                       chi = F^-1 [(I - A^2)/(I + A^2) F(phi)], A^2 = sum_k
+                       |F(phi_k)|^2: one per-pixel Newton step of the Poisson
+                       negative log-likelihood along its gradient; masked
+                       pixels 0).  DM and ePIE ignore it;
+                       ptycho_fourier_residual follows it.                   */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */
@@ -119,6 +131,11 @@ int ptycho_set_positions(ptycho_ctx* ctx, const float* positions);
  * pointer may be NULL to keep the current value (initially object = 1 and
  * probe = 0).  Resets the DM exit-wave state. */
 int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device);
+
+/* Switch the LSQML likelihood of an existing context (PTYCHO_LIK_*), e.g.
+ * Poisson refinement after amplitude-model iterations.  Takes effect at the
+ * next LSQML iteration; errors: PTYCHO_ERR_ARG. */
+int ptycho_set_likelihood(ptycho_ctx* ctx, int likelihood);
 
 /* Run n_iter iterations of alg (PTYCHO_EPIE / _DM / _LSQML) entirely on the
  * device; the iteration counter t continues across calls, so n calls of 1

@@ -135,20 +135,26 @@ def fourier_error(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) 
     return num / den if den > 0 else 0.0
 
 
-def poisson_correction(Psi: np.ndarray, I_fft: np.ndarray, tau: float = TAU) -> np.ndarray:
-    """Detector-plane correction of the Poisson likelihood (Odstrcil et al.
-    2018, the maximum-likelihood exit-wave update for photon-counting noise).
+def poisson_correction(Psi: np.ndarray, I_fft: np.ndarray) -> np.ndarray:
+    """Detector-plane correction of the Poisson likelihood (maximum-likelihood
+    exit-wave update for photon counts; Odstrcil et al. 2018).
 
-    With A^2 = sum_k |Psi_k|^2 the negative log-likelihood of the counts is
-    L = sum_q (A^2 - I log A^2); its steepest-descent direction in Psi_k is
-    (I / A^2 - 1) Psi_k.  Masked pixels (I < 0) contribute nothing (0); where
-    A <= tau the direction is -Psi_k (the modulus there is taken as zero, as in
-    :func:`project`)."""
+    With A^2 = sum_k |Psi_k|^2 the pixel's negative log-likelihood is
+    A^2 - I log A^2; its steepest-descent direction in Psi_k is
+    g = (I / A^2 - 1) Psi_k, unbounded where the model is far weaker than the
+    counts.  One Newton step along g from the current value, per pixel, scales
+    it by A^2 / (A^2 + I), giving
+
+        (I - A^2) / (I + A^2) * Psi_k,
+
+    a factor in [-1, 1] that equals the amplitude projection's
+    sqrt(I)/A - 1 to first order near a fit.  Masked pixels (I < 0) and
+    pixels with I + A^2 = 0 get no correction."""
     A2 = np.sum(np.abs(Psi) ** 2, axis=1)
     masked = I_fft < 0
-    big = A2 > tau * tau
-    f = np.where(big, np.where(masked, 0.0, I_fft) / np.where(big, A2, 1.0) - 1.0, -1.0)
-    f = np.where(masked, 0.0, f)
+    Iu = np.where(masked, 0.0, I_fft)
+    den = Iu + A2
+    f = np.where(masked | (den <= 0), 0.0, (Iu - A2) / np.where(den > 0, den, 1.0))
     return Psi * f[:, None, :, :]
 
 
@@ -165,9 +171,9 @@ def fourier_residual(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarra
     """Exit-wave residual chi_{j,k}, shape [J, K, M, M].
 
     amplitude (Gaussian noise on sqrt I): chi = F^-1 Pi(F(P_k O_j)) - P_k O_j;
-    poisson: chi = F^-1 [(I / A^2 - 1) F(P_k O_j)] (:func:`poisson_correction`),
-    i.e. -1/M^2 times the Wirtinger gradient of the Poisson negative
-    log-likelihood with respect to the conjugate exit wave."""
+    poisson: chi = F^-1 [(I - A^2) / (I + A^2) F(P_k O_j)], the per-pixel
+    Newton step of the Poisson negative log-likelihood along its gradient
+    (:func:`poisson_correction`)."""
     phi = exit_waves(O, P, pos)
     if likelihood == "amplitude":
         return ifft2(project(fft2(phi), to_fft_order(I))) - phi
@@ -375,7 +381,7 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
     """One LSQML iteration (index t); returns new (O, P) [and (alpha_O, alpha_P)].
 
     1. chi_jk = F^-1 Pi(F(P_k O_j)) - P_k O_j (amplitude likelihood) or the
-       Poisson correction F^-1[(I / A^2 - 1) F(P_k O_j)] (see
+       Poisson correction F^-1[(I - A^2)/(I + A^2) F(P_k O_j)] (see
        :func:`fourier_residual`);
     2. directions dO, dP (see :func:`lsqml_directions`);
     3. per-position step sizes (see :func:`lsqml_step_sizes`);

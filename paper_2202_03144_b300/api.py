@@ -19,6 +19,7 @@ EPIE, DM, LSQML = 0, 1, 2
 ALGS = {"epie": EPIE, "dm": DM, "lsqml": LSQML}
 I_F32, I_F16, I_BF16 = 0, 1, 2
 ISTORE = {"f32": I_F32, "f16": I_F16, "bf16": I_BF16}
+LIKELIHOOD = {"amplitude": 0, "poisson": 1}  # PTYCHO_LIK_AMPLITUDE, PTYCHO_LIK_POISSON
 
 ERRORS = {
     -1: "ARG", -2: "BOUNDS", -3: "NONFINITE", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
@@ -39,6 +40,7 @@ class Params(C.Structure):
         ("istore", C.c_int), ("probe_start", C.c_int),
         ("epie_alpha", C.c_double), ("epie_beta", C.c_double), ("lsqml_beta", C.c_double),
         ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
+        ("likelihood", C.c_int),
     ]
 
 
@@ -78,6 +80,7 @@ def lib() -> C.CDLL:
             "ptycho_cluster_size": (i, [vp]),
             "ptycho_last_error": (C.c_char_p, [vp]),
             "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
+            "ptycho_set_likelihood": (i, [vp, i]),
             "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
             "ptycho_batch_member": (vp, [vp, i]),
             "ptycho_batch_size": (i, [vp]),
@@ -150,6 +153,8 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         if k == "istore" and isinstance(v, str):
             v = ISTORE[v]
+        if k == "likelihood" and isinstance(v, str):
+            v = LIKELIHOOD[v]
         setattr(p, k, v)
     return p
 
@@ -315,6 +320,11 @@ class Reconstruction:
 
     def iterate(self, alg, n_iter=1):
         iterate(self.ctx, alg, n_iter)
+
+    def set_likelihood(self, likelihood):
+        """LSQML noise model from the next iteration on: "amplitude" or "poisson"."""
+        v = LIKELIHOOD[likelihood] if isinstance(likelihood, str) else int(likelihood)
+        _check(self.ctx, lib().ptycho_set_likelihood(self.ctx, v))
 
     def get_object(self, out=None):
         return get_object(self.ctx, self.obj_shape, out)

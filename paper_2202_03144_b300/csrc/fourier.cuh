@@ -32,7 +32,9 @@
 namespace ptycho {
 namespace cg = cooperative_groups;
 
-enum FourierMode : int { FM_DM = 0, FM_CHI = 1, FM_ERR = 2, FM_SIM = 3 };
+// DM pass, LSQML residual (amplitude likelihood), Fourier error, forward
+// model, LSQML residual with the Poisson-likelihood correction.
+enum FourierMode : int { FM_DM = 0, FM_CHI = 1, FM_ERR = 2, FM_SIM = 3, FM_CHIP = 4 };
 
 __host__ __device__ constexpr int choose_E(int L) {
   // elements per thread: a power of two <= 16 giving a whole number of warps

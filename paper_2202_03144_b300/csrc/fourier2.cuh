@@ -149,6 +149,24 @@ struct Fourier2Args {
   int mode;
 };
 
+// Detector-plane factor f with D = f Psi (before the 1/M^2 of the inverse
+// transform), from the stored amplitude am = sqrt(I) (< 0: masked) and
+// A^2 = sum_k |Psi_k|^2:
+//   amplitude likelihood  f = sqrt(I)/A - 1  (projection minus identity;
+//                         A^2 <= 1e-38 counts as zero modulus: f = -1)
+//   Poisson likelihood    f = (I - A^2) / (I + A^2)  (FM_CHIP: one Newton
+//                         step of the pixel's negative log-likelihood along
+//                         its gradient; 0 where I + A^2 = 0)
+// masked pixels f = 0.
+__device__ __forceinline__ float proj_factor(int mode, float am, float A2) {
+  if (am < 0.f) return 0.f;
+  if (mode == FM_CHIP) {
+    const float I = am * am, d = I + A2;
+    return d > 0.f ? __fdividef(I - A2, d) : 0.f;
+  }
+  return (A2 > 1e-38f ? am * rsqrtf(A2) : 0.f) - 1.f;
+}
+
 // IST >= 0: storage format fixed at compile time (0 f32, 1 f16, 2 bf16);
 // -1: read from the arguments.
 template <int IST>
@@ -309,8 +327,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
                 ed += (double)am * (double)am;
               }
             } else {
-              // factor sqrt(I)/A - 1 (A^2 <= 1e-38: projected value 0); masked: 0
-              const float fct = (am >= 0.f) ? ((A2 > 1e-38f) ? am * rsqrtf(A2) : 0.f) - 1.f : 0.f;
+              const float fct = proj_factor(mode, am, A2);
               w[q][k2] = cscale(w[q][k2], fct * inv);
             }
           }
@@ -351,12 +368,12 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
           }
           continue;
         }
-        const float fct = (am >= 0.f) ? ((A2 > 1e-38f) ? am * rsqrtf(A2) : 0.f) - 1.f : 0.f;
+        const float fct = proj_factor(mode, am, A2);
 #pragma unroll
         for (int k = 0; k < K; ++k) buf[rb<F>(k, rowL, pp)] = cscale(z[k], fct * inv);
       }
       __syncthreads();
-      if (mode == FM_DM || mode == FM_CHI) {
+      if (mode == FM_DM || mode == FM_CHI || mode == FM_CHIP) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int s = tid + q * NT;
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
     for (int n1 = 0; n1 < R1; ++n1) {
       const int row = n1 * R2 + n2;
       const size_t xi = (((size_t)j * K + k) * M + row) * M + col;
-      if (mode == FM_CHI) {
+      if (mode == FM_CHI || mode == FM_CHIP) {
         a.X[xi] = v[n1];
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);

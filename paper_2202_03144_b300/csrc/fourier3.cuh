@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
               ed += (double)am[q][k2] * (double)am[q][k2];
             }
           } else {
-            const float fct = (am[q][k2] >= 0.f) ? ((A2 > 1e-38f) ? am[q][k2] * rsqrtf(A2) : 0.f) - 1.f : 0.f;
+            const float fct = proj_factor(mode, am[q][k2], A2);
             w[q][k2] = cscale(w[q][k2], fct * inv);
           }
         }
@@ -292,12 +292,12 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
           }
           continue;
         }
-        const float fct = (am >= 0.f) ? ((A2 > 1e-38f) ? am * rsqrtf(A2) : 0.f) - 1.f : 0.f;
+        const float fct = proj_factor(mode, am, A2);
 #pragma unroll
         for (int k = 0; k < K; ++k) Y[rb<F>(k, rowL, pp)] = cscale(z[k], fct * inv);
       }
       __syncthreads();
-      if (mode == FM_DM || mode == FM_CHI) {
+      if (mode == FM_DM || mode == FM_CHI || mode == FM_CHIP) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int s = tid + q * NT;
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     for (int n1 = 0; n1 < R1; ++n1) {
       const int row = n1 * R2 + n2;
       const size_t xi = (((size_t)j * K + k) * M + row) * M + col;
-      if (mode == FM_CHI) {
+      if (mode == FM_CHI || mode == FM_CHIP) {
         a.X[xi] = v[n1];
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);

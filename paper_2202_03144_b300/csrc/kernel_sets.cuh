@@ -33,29 +33,37 @@ struct KernelSet {
   size_t smem_fourier, smem_epie;
   FourierFn fourier;       // any mode, any amplitude format
   void (*epie)(EpieArgs);  // null: no ePIE kernel for this shape
-  FourierFn spec[2][3];    // [FM_DM, FM_CHI][f32, f16, bf16]
+  FourierFn spec[3][3];    // [spec_row(mode)][f32, f16, bf16]
   size_t smem_spec;        // dynamic shared memory of the spec kernels
 };
 
-template <int M, int K, int C>
-void fill_spec(KernelSet& s) {
+// Row of KernelSet::spec for a Fourier mode: DM, LSQML residual (amplitude),
+// LSQML residual (Poisson); -1 for the modes only the generic kernel runs.
+__host__ __device__ constexpr int spec_row(int mode) {
+  return mode == FM_DM ? 0 : mode == FM_CHI ? 1 : mode == FM_CHIP ? 2 : -1;
+}
+
+template <int M, int K, int C, int MODE>
+void fill_spec_row(KernelSet& s) {
+  constexpr int r = spec_row(MODE);
   if constexpr (C > 1 && PT_F3 && fourier3_smem<F2<M, K, C>>() <= 227 * 1024) {
-    s.spec[FM_DM][0] = k_fourier3<M, K, C, FM_DM, 0>;
-    s.spec[FM_DM][1] = k_fourier3<M, K, C, FM_DM, 1>;
-    s.spec[FM_DM][2] = k_fourier3<M, K, C, FM_DM, 2>;
-    s.spec[FM_CHI][0] = k_fourier3<M, K, C, FM_CHI, 0>;
-    s.spec[FM_CHI][1] = k_fourier3<M, K, C, FM_CHI, 1>;
-    s.spec[FM_CHI][2] = k_fourier3<M, K, C, FM_CHI, 2>;
+    s.spec[r][0] = k_fourier3<M, K, C, MODE, 0>;
+    s.spec[r][1] = k_fourier3<M, K, C, MODE, 1>;
+    s.spec[r][2] = k_fourier3<M, K, C, MODE, 2>;
     s.smem_spec = fourier3_smem<F2<M, K, C>>();
   } else {
-    s.spec[FM_DM][0] = k_fourier2<M, K, C, FM_DM, 0>;
-    s.spec[FM_DM][1] = k_fourier2<M, K, C, FM_DM, 1>;
-    s.spec[FM_DM][2] = k_fourier2<M, K, C, FM_DM, 2>;
-    s.spec[FM_CHI][0] = k_fourier2<M, K, C, FM_CHI, 0>;
-    s.spec[FM_CHI][1] = k_fourier2<M, K, C, FM_CHI, 1>;
-    s.spec[FM_CHI][2] = k_fourier2<M, K, C, FM_CHI, 2>;
+    s.spec[r][0] = k_fourier2<M, K, C, MODE, 0>;
+    s.spec[r][1] = k_fourier2<M, K, C, MODE, 1>;
+    s.spec[r][2] = k_fourier2<M, K, C, MODE, 2>;
     s.smem_spec = fourier2_smem<F2<M, K, C>>();
   }
+}
+
+template <int M, int K, int C>
+void fill_spec(KernelSet& s) {
+  fill_spec_row<M, K, C, FM_DM>(s);
+  fill_spec_row<M, K, C, FM_CHI>(s);
+  fill_spec_row<M, K, C, FM_CHIP>(s);
 }
 
 template <int M, int K, int C>

@@ -436,7 +436,8 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   double bytes = 0;
   switch (mode) {
     case FM_DM: bytes = nj * MM * (16.0 * K + amp_bytes(ctx)); break;
-    case FM_CHI: bytes = nj * MM * (8.0 * K + amp_bytes(ctx)); break;
+    case FM_CHI:
+    case FM_CHIP: bytes = nj * MM * (8.0 * K + amp_bytes(ctx)); break;
     case FM_ERR: bytes = nj * MM * amp_bytes(ctx); break;
     case FM_SIM: bytes = nj * MM * 4.0; break;
   }
@@ -456,8 +457,9 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
       cfg.numAttrs = 1;
     }
     FourierFn fn = ks->fourier;
-    if ((mode == FM_DM || mode == FM_CHI) && a.istore >= 0 && a.istore < 3 && ks->spec[mode][a.istore]) {
-      fn = ks->spec[mode][a.istore];
+    const int row = spec_row(mode);
+    if (row >= 0 && a.istore >= 0 && a.istore < 3 && ks->spec[row][a.istore]) {
+      fn = ks->spec[row][a.istore];
       cfg.dynamicSmemBytes = ks->smem_spec;
     }
     cudaLaunchKernelEx(&cfg, fn, a);
@@ -645,8 +647,14 @@ int lsqml_prepare(ptycho_ctx* ctx) {
 }
 
 // One LSQML iteration with the probe update on or off (all device work).
+// LSQML residual into dst under the context's likelihood.
+int launch_chi(ptycho_ctx* ctx, float2* dst) {
+  const int mode = ctx->p.likelihood == PTYCHO_LIK_POISSON ? FM_CHIP : FM_CHI;
+  return launch_fourier(ctx, mode, dst, nullptr, 0, ctx->p.J, "fourier_chi");
+}
+
 int lsqml_step(ptycho_ctx* ctx, bool upd) {
-  if (int r = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, ctx->p.J, "fourier_chi")) return r;
+  if (int r = launch_chi(ctx, ctx->X)) return r;
   if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
   if (upd)
     if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
@@ -946,6 +954,7 @@ void ptycho_default_params(ptycho_params* p) {
   p->seed = 0;
   p->stream = nullptr;
   p->cluster = 0;
+  p->likelihood = PTYCHO_LIK_AMPLITUDE;
 }
 
 int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
@@ -957,6 +966,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
                 p->obj_nx);
   if (p->K > 3) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "K=%d modes: at most 3 are compiled in", p->K);
   if (p->istore < 0 || p->istore > 2) return fail(nullptr, PTYCHO_ERR_ARG, "istore=%d", p->istore);
+  if (p->likelihood != PTYCHO_LIK_AMPLITUDE && p->likelihood != PTYCHO_LIK_POISSON)
+    return fail(nullptr, PTYCHO_ERR_ARG, "likelihood=%d", p->likelihood);
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
@@ -1155,6 +1166,14 @@ int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, in
   return PTYCHO_OK;
 }
 
+int ptycho_set_likelihood(ptycho_ctx* ctx, int likelihood) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (likelihood != PTYCHO_LIK_AMPLITUDE && likelihood != PTYCHO_LIK_POISSON)
+    return fail(ctx, PTYCHO_ERR_ARG, "likelihood=%d", likelihood);
+  ctx->p.likelihood = likelihood;
+  return PTYCHO_OK;
+}
+
 int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter) {
   if (!ctx) return PTYCHO_ERR_ARG;
   if (n_iter < 0) return fail(ctx, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
@@ -1230,7 +1249,7 @@ int ptycho_fourier_residual(ptycho_ctx* ctx, float* out, int on_device) {
   float2* dst = on_device ? (float2*)out : nullptr;
   if (!on_device)
     if (int r = dalloc(ctx, &dst, n)) return r;
-  int r = launch_fourier(ctx, FM_CHI, dst, nullptr, 0, ctx->p.J, "fourier_chi");
+  int r = launch_chi(ctx, dst);
   if (!r && !on_device) r = copy_out(ctx, out, dst, n * 8, 0);
   if (!r) {
     cudaError_t e = cudaStreamSynchronize(ctx->st);

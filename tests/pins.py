@@ -384,62 +384,51 @@ def pin_lsqml_directions(orc):
         assert abs(dP[k, u, v] * wP[u, v] + g) < 1e-6 * (1 + abs(g)), "LSQML probe direction"
 
 
-def pin_poisson_correction_gradient(orc):
-    """The Poisson correction, taken back to the exit wave, is -1/M^2 times the
-    Wirtinger gradient of the Poisson negative log-likelihood
-    L(psi) = sum_unmasked (A^2 - I log A^2), A^2 = sum_k |F psi_k|^2
-    (central differences on the real and imaginary parts of psi)."""
+def pin_poisson_newton_step(orc):
+    """Per pixel, the Poisson correction is one Newton step of the pixel's
+    negative log-likelihood l(s) = a(s) - I log a(s), a(s) = (1 + s)^2 A^2,
+    along its steepest-descent direction: with s* = -l'(0) / l''(0) from
+    central differences of l, correction = s* Psi_k (sum over modes in A^2);
+    and s* has the sign of -dl/ds (a descent step).  Masked pixels: none."""
     rng = np.random.default_rng(12)
     M, K = 4, 2
-    psi = _crandn(1, K, M, M, rng=rng)
-    I = rng.uniform(0.5, 20.0, (1, M, M))
-    I[0, 1, 2] = -1.0  # a masked pixel
-    I[0, 3, 0] = -1.0
-
-    def L(ps):
-        A2 = np.sum(np.abs(np.fft.fft2(ps)) ** 2, axis=1)
-        m = I >= 0
-        return float(np.sum(np.where(m, A2 - np.where(m, I, 0) * np.log(A2), 0.0)))
-
-    chi = np.fft.ifft2(orc.poisson_correction(np.fft.fft2(psi), I))
-    h = 1e-6
-    for (k, u, v) in [(0, 0, 0), (0, 2, 3), (1, 1, 1), (1, 3, 2)]:
-        e = np.zeros_like(psi)
-        e[0, k, u, v] = h
-        g = ((L(psi + e) - L(psi - e)) + 1j * (L(psi + 1j * e) - L(psi - 1j * e))) / (2 * h) / 2
-        assert abs(chi[0, k, u, v] + g / M ** 2) < 1e-6 * (1 + abs(g)), "Poisson correction gradient"
-    # fully masked frame: no correction; vanishing modulus: -Psi
-    Psi = np.fft.fft2(psi)
+    Psi = _crandn(2, K, M, M, rng=rng)
+    I = rng.poisson(3.0 * np.sum(np.abs(Psi) ** 2, axis=1) * rng.uniform(0.2, 5.0, (2, M, M))).astype(float)
+    I[0, 1, 2] = -1.0  # masked
+    I[1, 0, 0] = 0.0   # zero counts
+    corr = orc.poisson_correction(Psi, I)
+    h = 1e-4
+    for (j, u, v) in [(0, 0, 0), (0, 1, 2), (0, 3, 1), (1, 0, 0), (1, 2, 3)]:
+        A2 = float(np.sum(np.abs(Psi[j, :, u, v]) ** 2))
+        if I[j, u, v] < 0:
+            assert np.allclose(corr[j, :, u, v], 0.0)
+            continue
+        l = lambda s_: (1 + s_) ** 2 * A2 - I[j, u, v] * np.log((1 + s_) ** 2 * A2)
+        d1 = (l(h) - l(-h)) / (2 * h)
+        d2 = (l(h) - 2 * l(0.0) + l(-h)) / h ** 2
+        s_star = -d1 / d2
+        assert np.allclose(corr[j, :, u, v], s_star * Psi[j, :, u, v], rtol=1e-6, atol=1e-9), "Poisson Newton step"
+        assert s_star * d1 <= 0.0
     assert np.allclose(orc.poisson_correction(Psi, -np.ones_like(I)), 0.0)
-    Z = Psi.copy()
-    Z[0, :, 0, 0] = 0.0
-    assert np.allclose(orc.poisson_correction(Z, I)[0, :, 0, 0], 0.0)
-    Z[0, :, 0, 0] = 1e-40
-    assert np.allclose(orc.poisson_correction(Z, I)[0, :, 0, 0], -Z[0, :, 0, 0], atol=0)
 
 
-def pin_lsqml_poisson_object_gradient(orc):
-    """With the Poisson residual, the LSQML object direction times its
-    denominator is -1/M^2 times the Wirtinger gradient of the Poisson
-    negative log-likelihood with respect to the object (central differences
-    of :func:`poisson_nll`), which ties the residual, the gather and the
-    scatter together; and noise-free data is a fixed point."""
+def pin_lsqml_poisson(orc):
+    """Poisson LSQML: the object direction is a descent direction of the
+    Poisson negative log-likelihood (directional derivative from central
+    differences of :func:`poisson_nll` is negative), and noise-free data is a
+    fixed point."""
     M = 6
     P, O, pos = small_scan(M=M, K=2, grid=2, step=3)
     pos = orc.round_positions(pos)
     rng = np.random.default_rng(4)
     I = orc.far_field_intensity(O * (1 + 0.1 * _crandn(*O.shape, rng=rng)), P, pos)
-    I = orc.to_fft_order(orc.to_fft_order(I))  # detector-centred, unchanged
     I[0, 2, 2] = -1.0
     chi = orc.fourier_residual(O, P, pos, I, likelihood="poisson")
-    dO, _, wO, _ = orc.lsqml_directions(O, P, chi, pos, 1e-3, False)
-    h = 1e-6
-    for (u, v) in [(pos[0][0] + 1, pos[0][1] + 2), (pos[-1][0] + 3, pos[-1][1] + 4)]:
-        e = np.zeros_like(O)
-        e[u, v] = h
-        f = lambda Ov: orc.poisson_nll(Ov, P, pos, I)
-        g = ((f(O + e) - f(O - e)) + 1j * (f(O + 1j * e) - f(O - 1j * e))) / (2 * h) / 2
-        assert abs(dO[u, v] * wO[u, v] + g / M ** 2) < 1e-6 * (1 + abs(g)), "Poisson LSQML object direction"
+    dO, _, _, _ = orc.lsqml_directions(O, P, chi, pos, 1e-3, False)
+    h = 1e-7
+    f = lambda Ov: orc.poisson_nll(Ov, P, pos, I)
+    slope = (f(O + h * dO) - f(O - h * dO)) / (2 * h)
+    assert slope < 0.0, "Poisson LSQML object direction is not a descent direction"
     P0, O0, pos0, I0 = _truth_case(orc)
     O1, P1 = orc.lsqml_iteration(O0, P0, pos0, I0, t=0, likelihood="poisson")
     assert np.allclose(O1, O0, atol=1e-12) and np.allclose(P1, P0, atol=1e-12), "Poisson LSQML moved off the truth"
@@ -451,5 +440,5 @@ ALL_PINS = [
     pin_fixed_points, pin_epie_er_special_case, pin_epie_gradient, pin_epie_order,
     pin_dm_overlap_least_squares, pin_dm_all_masked, pin_lsqml_step_sizes,
     pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
-    pin_poisson_correction_gradient, pin_lsqml_poisson_object_gradient,
+    pin_poisson_newton_step, pin_lsqml_poisson,
 ]

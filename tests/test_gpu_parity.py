@@ -60,7 +60,8 @@ def _compare(c, alg, n, cluster=0, seed=0, probe_start=0, **kw):
         E = r.fourier_error()
         psi = r.get_exit_waves() if alg == "dm" else None
     Oc, Pc, psic = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, seed=seed, probe_start=probe_start,
-                                   **{k: v for k, v in kw.items() if k in ("reg", "epie_alpha", "epie_beta", "lsqml_beta")})
+                                   **{k: v for k, v in kw.items()
+                                      if k in ("reg", "epie_alpha", "epie_beta", "lsqml_beta", "likelihood")})
     m = illuminated(c["P"], c["pos"], c["shape"])
     eo = rel_l2(align_global(Og, Oc, m), Oc, m)
     ep = rel_l2(Pg, Pc)
@@ -286,3 +287,84 @@ def test_get_into_caller_buffers():
             r.get_object(np.empty(O.shape, np.complex128))
         with pytest.raises(ValueError):
             r.get_probe(torch.empty((1, 2, 2), dtype=torch.complex64))
+
+
+# Poisson-likelihood LSQML: every compiled kernel form (single CTA, the
+# asynchronous-transpose cluster kernel, K > 1 through shared memory, mixed radix)
+POISSON_CASES = [(32, 1, 1), (64, 1, 4), (32, 3, 4), (128, 3, 8), (96, 1, 2)]
+
+
+@pytest.mark.parametrize("M,K,C", POISSON_CASES, ids=lambda v: str(v))
+def test_poisson_residual_matches_oracle(M, K, C):
+    c = scan(M, K, grid=2, photons=1e5, mask_frac=0.05)
+    with recon(c, cluster=C, likelihood="poisson") as r:
+        chi = r.fourier_residual()
+    chi_ref = orc.fourier_residual(c["O0"], c["P0"], orc.round_positions(c["pos"]), c["I"], likelihood="poisson")
+    assert rel_l2(chi, chi_ref) < TOL_PASS
+
+
+def _poisson_sensitivity(c, n):
+    """Relative change of the oracle's own result (object, probe) after n
+    Poisson LSQML iterations when its starting object is perturbed by 1e-7
+    relative noise: how much FP32-sized rounding the method itself amplifies."""
+    rng = np.random.default_rng(2024)
+    O0p = c["O0"] * (1 + 1e-7 * rng.standard_normal(c["O0"].shape))
+    Oa, Pa, _ = orc.reconstruct("lsqml", c["O0"], c["P0"], c["pos"], c["I"], n, likelihood="poisson")
+    Ob, Pb, _ = orc.reconstruct("lsqml", O0p, c["P0"], c["pos"], c["I"], n, likelihood="poisson")
+    m = illuminated(c["P"], c["pos"], c["shape"])
+    pos_i = orc.round_positions(c["pos"])
+    Ea, Eb = orc.fourier_error(Oa, Pa, pos_i, c["I"]), orc.fourier_error(Ob, Pb, pos_i, c["I"])
+    return rel_l2(Ob, Oa, m), rel_l2(Pb, Pa), abs(Eb - Ea) / Ea
+
+
+@pytest.mark.parametrize("M,K,C", POISSON_CASES, ids=lambda v: str(v))
+@pytest.mark.parametrize("n", [1, 6])
+def test_lsqml_poisson_parity(M, K, C, n):
+    """The Poisson factor I / A^2 amplifies rounding where the model's far
+    field is much weaker than the counts (early iterations from a flat
+    start): the bound is 1e-4 or 20x the oracle's own response to a 1e-7
+    perturbation of its start, whichever is larger."""
+    c = scan(M, K, grid=3, photons=1e5, mask_frac=0.02)
+    res = _compare(c, "lsqml", n, cluster=C, likelihood="poisson")
+    so, sp, se = _poisson_sensitivity(c, n)
+    assert res["eo"] < max(TOL_REC, 20 * so) and res["ep"] < max(TOL_REC, 20 * sp), (res, so, sp)
+    # E = ||A - sqrt I||^2 / ||sqrt I||^2 moves by at most 2 ||dA|| / ||A - sqrt I|| relative, i.e. about
+    # 2 (eo + ep) / sqrt(E) for the model changes measured above
+    tol_e = max(1e-5, 20 * se, 4 * max(res["eo"], res["ep"]) / np.sqrt(res["E_ref"]))
+    assert abs(res["E"] - res["E_ref"]) <= tol_e * res["E_ref"] + 1e-12, (res, se)
+
+
+@pytest.mark.parametrize("istore", ["f16", "bf16"])
+def test_lsqml_poisson_16bit_storage(istore):
+    """The Poisson residual squares the stored amplitude: 16-bit storage stays
+    within twice its amplitude rounding of the FP32 result."""
+    c = scan(64, 1, grid=3, photons=1e6)
+    outs = {}
+    for store in ("f32", istore):
+        with recon(c, istore=store, likelihood="poisson") as r:
+            r.iterate("lsqml", 4)
+            outs[store] = r.get_object()
+    m = illuminated(c["P"], c["pos"], c["shape"])
+    tol = {"f16": 2e-3, "bf16": 2e-2}[istore]
+    assert rel_l2(outs[istore], outs["f32"], m) < tol
+
+
+def test_lsqml_poisson_step_equals_whole_and_reduces_nll():
+    c = scan(64, 1, grid=4, photons=1e4)
+    with recon(c, likelihood="poisson") as a:
+        a.iterate("lsqml", 5)
+        Oa, Pa = a.get_object(), a.get_probe()
+    with recon(c, likelihood="poisson") as b:
+        for _ in range(5):
+            b.iterate("lsqml", 1)
+        Ob, Pb = b.get_object(), b.get_probe()
+    assert np.array_equal(Oa, Ob) and np.array_equal(Pa, Pb)
+    pos_i = orc.round_positions(c["pos"])
+    assert orc.poisson_nll(Oa, Pa, pos_i, c["I"]) < orc.poisson_nll(c["O0"], c["P0"], pos_i, c["I"])
+
+
+def test_bad_likelihood_rejected():
+    c = scan(32, 1, grid=2)
+    with pytest.raises(api.PtychoError) as e:
+        api.Reconstruction(32, 1, len(c["pos"]), c["shape"], likelihood=7)
+    assert e.value.name == "ARG"

@@ -45,11 +45,12 @@ MUTATIONS = {
     "splitmix_constant": ("0xBF58476D1CE4E5B9", "0xBF58476D1CE4E5B8"),
     "rounding_floor": ("return np.rint(np.asarray(positions, dtype=np.float64)).astype(np.int64)",
                        "return np.floor(np.asarray(positions, dtype=np.float64)).astype(np.int64)"),
-    "poisson_sqrt_counts": ("np.where(masked, 0.0, I_fft) / np.where(big, A2, 1.0) - 1.0",
-                            "np.sqrt(np.where(masked, 0.0, I_fft)) / np.where(big, A2, 1.0) - 1.0"),
-    "poisson_no_mode_sum": ("A2 = np.sum(np.abs(Psi) ** 2, axis=1)\n    masked = I_fft < 0\n    big",
-                            "A2 = np.abs(Psi[:, 0]) ** 2\n    masked = I_fft < 0\n    big"),
-    "poisson_masked_pulls": ("f = np.where(masked, 0.0, f)", "f = np.where(masked, -1.0, f)"),
+    "poisson_sqrt_counts": ("Iu = np.where(masked, 0.0, I_fft)\n    den", "Iu = np.sqrt(np.where(masked, 0.0, I_fft))\n    den"),
+    "poisson_no_mode_sum": ("A2 = np.sum(np.abs(Psi) ** 2, axis=1)\n    masked = I_fft < 0\n    Iu",
+                            "A2 = np.abs(Psi[:, 0]) ** 2\n    masked = I_fft < 0\n    Iu"),
+    "poisson_raw_gradient": ("(Iu - A2) / np.where(den > 0, den, 1.0))",
+                             "(Iu - A2) / np.where(A2 > 0, A2, 1.0))"),
+    "poisson_masked_pulls": ("f = np.where(masked | (den <= 0), 0.0,", "f = np.where(den <= 0, 0.0,"),
     "poisson_residual_minus_phi": ("return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))",
                                    "return ifft2(poisson_correction(fft2(phi), to_fft_order(I))) - phi"),
 }
