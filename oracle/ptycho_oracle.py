@@ -406,12 +406,52 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
 
 
 # ---------------------------------------------------------------------------
+# Probe-mode orthogonalisation (Thibault & Menzel 2013, cited in Sec. 1)
+# ---------------------------------------------------------------------------
+
+def mode_basis(P: np.ndarray) -> np.ndarray:
+    """Unitary V [K, K] whose columns are the eigenvectors of the modes' Gram
+    matrix G[l, k] = <P_l, P_k> = sum_u conj(P_l(u)) P_k(u), ordered by
+    decreasing eigenvalue (mode power); each column's phase is fixed so that
+    its entry of largest modulus (the first one on a tie) is real positive."""
+    K = P.shape[0]
+    flat = P.reshape(K, -1)
+    G = np.conj(flat) @ flat.T
+    lam, V = np.linalg.eigh(G)
+    V = V[:, np.argsort(-lam, kind="stable")]
+    for m in range(K):
+        i = int(np.argmax(np.abs(V[:, m])))
+        V[:, m] *= np.conj(V[i, m]) / abs(V[i, m])
+    return V
+
+
+def mix_modes(X: np.ndarray, V: np.ndarray, axis: int = 0) -> np.ndarray:
+    """X'_m = sum_l V[l, m] X_l along the mode axis."""
+    return np.moveaxis(np.tensordot(V, np.moveaxis(X, axis, 0), axes=([0], [0])), 0, axis)
+
+
+def orthogonalize_modes(P: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Orthogonal probe modes P'_m = sum_l V[l, m] P_l (see :func:`mode_basis`):
+    <P'_m, P'_n> = 0 for m != n, powers ||P'_m||^2 the eigenvalues of G in
+    decreasing order, and sum_m |P'_m(u)|^2 = sum_l |P_l(u)|^2 at every pixel
+    (a unitary mixing leaves every diffraction pattern unchanged).  Returns
+    (P', V)."""
+    V = mode_basis(P)
+    return mix_modes(P, V), V
+
+
+# ---------------------------------------------------------------------------
 # Driver used by tests and the CPU baseline
 # ---------------------------------------------------------------------------
 
 def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, reg=1e-3,
-                epie_alpha=1.0, epie_beta=1.0, lsqml_beta=0.9, probe_start=0, likelihood="amplitude"):
+                epie_alpha=1.0, epie_beta=1.0, lsqml_beta=0.9, probe_start=0, likelihood="amplitude",
+                probe_ortho=False):
     """Run n_iter iterations of 'epie', 'dm' or 'lsqml' starting at index t0.
+
+    probe_ortho: after every iteration that updated the probe, orthogonalise
+    its modes (:func:`orthogonalize_modes`); DM's exit waves are mixed with
+    the same unitary so that psi_jk stays P_k O_j-shaped.
 
     Returns (O, P, psi) -- psi is the DM state (None for the others)."""
     pos = round_positions(positions)
@@ -429,4 +469,8 @@ def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, re
             O, P = lsqml_iteration(O, P, pos, I, t, reg, lsqml_beta, probe_start, likelihood=likelihood)
         else:
             raise ValueError(alg)
+        if probe_ortho and t >= probe_start and P.shape[0] > 1:
+            P, V = orthogonalize_modes(P)
+            if alg == "dm":
+                psi = mix_modes(psi, V, axis=1)
     return O, P, psi

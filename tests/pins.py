@@ -434,11 +434,63 @@ def pin_lsqml_poisson(orc):
     assert np.allclose(O1, O0, atol=1e-12) and np.allclose(P1, P0, atol=1e-12), "Poisson LSQML moved off the truth"
 
 
+def pin_mode_orthogonalisation(orc):
+    """Orthogonalised modes: mutually orthogonal, powers decreasing, the
+    largest power equal to the maximum of ||sum_l c_l P_l||^2 over unit
+    vectors c (checked against random unit vectors, never exceeded and
+    attained by the first mode), the sum of powers unchanged, every
+    diffraction pattern unchanged, idempotent, and the phase convention
+    (largest entry of each column of V real positive) met."""
+    rng = np.random.default_rng(17)
+    M, K = 8, 3
+    P = _crandn(K, M, M, rng=rng) * np.array([3.0, 1.5, 1.0])[:, None, None]
+    Q, V = orc.orthogonalize_modes(P)
+    flat = Q.reshape(K, -1)
+    G = np.conj(flat) @ flat.T
+    pw = np.real(np.diag(G))
+    assert np.max(np.abs(G - np.diag(np.diag(G)))) < 1e-10 * pw.max(), "modes not orthogonal"
+    assert np.all(np.diff(pw) < 0), "powers not decreasing"
+    assert abs(pw.sum() - np.sum(np.abs(P) ** 2)) < 1e-10 * pw.sum()
+    c = _crandn(4000, K, rng=rng)
+    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    comb = np.einsum("nk,kxy->nxy", c, P)
+    best = np.max(np.sum(np.abs(comb) ** 2, axis=(1, 2)))
+    assert best <= pw[0] * (1 + 1e-12) and best > 0.9 * pw[0]
+    assert np.allclose(np.sum(np.abs(Q) ** 2, axis=0), np.sum(np.abs(P) ** 2, axis=0), atol=1e-10)
+    O = 1.0 + 0.3 * _crandn(12, 12, rng=rng)
+    pos = np.array([[0, 0], [2, 3], [4, 1]])
+    assert np.allclose(orc.far_field_intensity(O, Q, pos), orc.far_field_intensity(O, P, pos), rtol=1e-10)
+    Q2, V2 = orc.orthogonalize_modes(Q)
+    assert np.allclose(Q2, Q, atol=1e-10) and np.allclose(V2, np.eye(K), atol=1e-10), "not idempotent"
+    for m in range(K):
+        i = int(np.argmax(np.abs(V[:, m])))
+        assert abs(V[i, m].imag) < 1e-12 and V[i, m].real > 0
+
+
+def pin_dm_mode_orthogonalisation_keeps_truth(orc):
+    """DM with orthogonalisation on noise-free data whose true modes are a
+    non-orthogonal mixture: the object stays at the truth and every
+    diffraction pattern and the per-pixel mode power stay fixed (the exit
+    waves are mixed with the probe)."""
+    rng = np.random.default_rng(23)
+    P, O, pos = small_scan(M=16, K=2, grid=3, step=6)
+    pos = orc.round_positions(pos)
+    U, _ = np.linalg.qr(_crandn(2, 2, rng=rng))
+    Pm = orc.mix_modes(P, U) * np.array([1.0, 1.0])[:, None, None]
+    Pm[1] += 0.3 * Pm[0]  # no longer orthogonal
+    I = orc.far_field_intensity(O, Pm, pos)
+    O1, P1, psi1 = orc.reconstruct("dm", O, Pm, pos, I, 3, probe_ortho=True)
+    assert np.allclose(O1, O, atol=1e-9), "DM with orthogonalisation moved the object"
+    assert np.allclose(orc.far_field_intensity(O1, P1, pos), I, rtol=1e-8)
+    assert np.allclose(np.sum(np.abs(P1) ** 2, axis=0), np.sum(np.abs(Pm) ** 2, axis=0), atol=1e-9)
+
+
 ALL_PINS = [
     pin_fft_bruteforce, pin_parseval, pin_forward_bruteforce, pin_mode_mixing_invariance,
     pin_gather_scatter_adjoint, pin_rounding, pin_projection, pin_fourier_error,
     pin_fixed_points, pin_epie_er_special_case, pin_epie_gradient, pin_epie_order,
     pin_dm_overlap_least_squares, pin_dm_all_masked, pin_lsqml_step_sizes,
     pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
-    pin_poisson_newton_step, pin_lsqml_poisson,
+    pin_poisson_newton_step, pin_lsqml_poisson, pin_mode_orthogonalisation,
+    pin_dm_mode_orthogonalisation_keeps_truth,
 ]

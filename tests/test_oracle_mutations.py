@@ -51,6 +51,11 @@ MUTATIONS = {
     "poisson_raw_gradient": ("(Iu - A2) / np.where(den > 0, den, 1.0))",
                              "(Iu - A2) / np.where(A2 > 0, A2, 1.0))"),
     "poisson_masked_pulls": ("f = np.where(masked | (den <= 0), 0.0,", "f = np.where(den <= 0, 0.0,"),
+    "modes_ascending": ("V = V[:, np.argsort(-lam, kind=\"stable\")]", "V = V[:, np.argsort(lam, kind=\"stable\")]"),
+    "modes_gram_no_conj": ("G = np.conj(flat) @ flat.T", "G = flat @ flat.T"),
+    "modes_mix_transposed": ("return np.moveaxis(np.tensordot(V, np.moveaxis(X, axis, 0), axes=([0], [0])), 0, axis)",
+                             "return np.moveaxis(np.tensordot(V, np.moveaxis(X, axis, 0), axes=([1], [0])), 0, axis)"),
+    "modes_dm_psi_not_mixed": ("                psi = mix_modes(psi, V, axis=1)", "                pass"),
     "poisson_residual_minus_phi": ("return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))",
                                    "return ifft2(poisson_correction(fft2(phi), to_fft_order(I))) - phi"),
 }
