@@ -101,6 +101,13 @@ typedef struct {
                        negative log-likelihood along its gradient; masked
                        pixels 0).  DM and ePIE ignore it;
                        ptycho_fourier_residual follows it.                   */
+  int probe_ortho;  /* 1: after every iteration that updates the probe,
+                       orthogonalise its modes (Thibault & Menzel 2013, cited
+                       in Sec. 1): rotate them into the eigenbasis of their
+                       Gram matrix <P_l, P_k>, decreasing power, each
+                       eigenvector's largest entry real positive; DM's exit
+                       waves are mixed with the same unitary.  0 (default):
+                       modes are left as the updates make them.              */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */
@@ -131,6 +138,11 @@ int ptycho_set_positions(ptycho_ctx* ctx, const float* positions);
  * pointer may be NULL to keep the current value (initially object = 1 and
  * probe = 0).  Resets the DM exit-wave state. */
 int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device);
+
+/* Orthogonalise the probe modes now (see ptycho_params.probe_ortho; the DM
+ * exit-wave state, if any, is mixed too).  Asynchronous on the context's
+ * stream; K = 1: no change. */
+int ptycho_orthogonalize_probe(ptycho_ctx* ctx);
 
 /* Switch the LSQML likelihood of an existing context (PTYCHO_LIK_*), e.g.
  * Poisson refinement after amplitude-model iterations.  Takes effect at the

@@ -40,7 +40,7 @@ class Params(C.Structure):
         ("istore", C.c_int), ("probe_start", C.c_int),
         ("epie_alpha", C.c_double), ("epie_beta", C.c_double), ("lsqml_beta", C.c_double),
         ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
-        ("likelihood", C.c_int),
+        ("likelihood", C.c_int), ("probe_ortho", C.c_int),
     ]
 
 
@@ -81,6 +81,7 @@ def lib() -> C.CDLL:
             "ptycho_last_error": (C.c_char_p, [vp]),
             "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
             "ptycho_set_likelihood": (i, [vp, i]),
+            "ptycho_orthogonalize_probe": (i, [vp]),
             "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
             "ptycho_batch_member": (vp, [vp, i]),
             "ptycho_batch_size": (i, [vp]),
@@ -155,6 +156,8 @@ def default_params(**kw) -> Params:
             v = ISTORE[v]
         if k == "likelihood" and isinstance(v, str):
             v = LIKELIHOOD[v]
+        if k == "probe_ortho":
+            v = int(bool(v))
         setattr(p, k, v)
     return p
 
@@ -320,6 +323,10 @@ class Reconstruction:
 
     def iterate(self, alg, n_iter=1):
         iterate(self.ctx, alg, n_iter)
+
+    def orthogonalize_probe(self):
+        """Rotate the probe modes into orthogonal modes of decreasing power now."""
+        _check(self.ctx, lib().ptycho_orthogonalize_probe(self.ctx))
 
     def set_likelihood(self, likelihood):
         """LSQML noise model from the next iteration on: "amplitude" or "poisson"."""

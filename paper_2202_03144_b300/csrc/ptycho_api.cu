@@ -25,6 +25,7 @@
 #include "fourier.cuh"
 #include "fourier2.cuh"
 #include "kernel_sets.cuh"
+#include "modes.cuh"
 #include "net.cuh"
 #include "overlap.cuh"
 
@@ -263,6 +264,8 @@ struct ptycho_ctx {
   float* pblk_max = nullptr;
   float* alphaO = nullptr;
   float* alphaP = nullptr;
+  double2* gram = nullptr;   // probe-mode Gram matrix [K][K]
+  double2* modeV = nullptr;  // its eigenvectors [K][K] (orthogonalisation)
   double2* err_part = nullptr;
   double2* err_out = nullptr;
   int* order = nullptr;
@@ -633,11 +636,29 @@ int dm_prepare(ptycho_ctx* ctx) {
 }
 
 // One DM iteration with the probe update on or off (all device work).
+// Orthogonalise the probe modes (K > 1): Gram matrix, eigenvectors, mixing
+// of the probe and, for DM, of the exit waves with the same unitary.
+int ortho_step(ptycho_ctx* ctx, bool mix_psi) {
+  const int K = ctx->p.K;
+  if (K < 2) return 0;
+  const int MM = ctx->p.M * ctx->p.M;
+  if (int r = dalloc(ctx, &ctx->gram, (size_t)K * K)) return r;
+  if (int r = dalloc(ctx, &ctx->modeV, (size_t)K * K)) return r;
+  return launch(ctx, "probe_ortho", 8.0 * K * MM * (mix_psi ? 2.0 * ctx->p.J + 3.0 : 3.0), [&] {
+    k_mode_gram<<<K * K, 256, 0, ctx->st>>>(ctx->P, K, MM, ctx->gram);
+    k_mode_eig<<<1, 32, 0, ctx->st>>>(ctx->gram, K, ctx->modeV);
+    k_mode_mix<<<(MM + 255) / 256, 256, 0, ctx->st>>>(ctx->P, 1, K, MM, ctx->modeV);
+    if (mix_psi) k_mode_mix<<<1184, 256, 0, ctx->st>>>(ctx->X, (size_t)ctx->p.J, K, MM, ctx->modeV);
+  });
+}
+
 int dm_step(ptycho_ctx* ctx, bool upd) {
   if (int r = obj_step(ctx, OBJ_STEP_DM, ctx->X, nullptr)) return r;
   if (upd)
     if (int r = probe_step(ctx, PR_DM, ctx->X, nullptr, true, true)) return r;
-  return launch_fourier(ctx, FM_DM, ctx->X, nullptr, 0, ctx->p.J, "fourier_dm");
+  if (int r = launch_fourier(ctx, FM_DM, ctx->X, nullptr, 0, ctx->p.J, "fourier_dm")) return r;
+  if (upd && ctx->p.probe_ortho) return ortho_step(ctx, true);
+  return 0;
 }
 
 int lsqml_prepare(ptycho_ctx* ctx) {
@@ -664,6 +685,7 @@ int lsqml_step(ptycho_ctx* ctx, bool upd) {
   if (int r = obj_step(ctx, OBJ_UPD, ctx->X, ctx->alphaO)) return r;
   if (upd)
     if (int r = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return r;
+  if (upd && ctx->p.probe_ortho) return ortho_step(ctx, false);
   return 0;
 }
 
@@ -726,24 +748,41 @@ int run_epie(ptycho_ctx* ctx, int n) {
   a.alpha = (float)ctx->p.epie_alpha;
   a.beta = (float)ctx->p.epie_beta;
   const KernelSet* ks = ctx->ks;
-  const double bytes = (double)n * J * ctx->p.M * ctx->p.M * amp_bytes(ctx);
-  int r = launch(ctx, "epie", bytes, [&] {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)ks->C);
-    cfg.blockDim = dim3((unsigned)ks->NT_epie);
-    cfg.dynamicSmemBytes = ks->smem_epie;
-    cfg.stream = ctx->st;
-    cudaLaunchAttribute attr[1];
-    if (ks->C > 1) {
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = ks->C;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
+  auto sweep = [&](const EpieArgs& ea, int iters) {
+    const double bytes = (double)iters * J * ctx->p.M * ctx->p.M * amp_bytes(ctx);
+    return launch(ctx, "epie", bytes, [&] {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3((unsigned)ks->C);
+      cfg.blockDim = dim3((unsigned)ks->NT_epie);
+      cfg.dynamicSmemBytes = ks->smem_epie;
+      cfg.stream = ctx->st;
+      cudaLaunchAttribute attr[1];
+      if (ks->C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = ks->C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+      }
+      cudaLaunchKernelEx(&cfg, ks->epie, ea);
+    });
+  };
+  int r = 0;
+  if (ctx->p.probe_ortho && ctx->p.K > 1) {
+    // one sweep per launch, the modes orthogonalised after each sweep that
+    // updated the probe
+    for (int it = 0; it < n && !r; ++it) {
+      EpieArgs e1 = a;
+      e1.order = ctx->order + (size_t)it * J;
+      e1.n_iter = 1;
+      e1.t0 = ctx->t + it;
+      r = sweep(e1, 1);
+      if (!r && ctx->t + it >= ctx->p.probe_start) r = ortho_step(ctx, false);
     }
-    cudaLaunchKernelEx(&cfg, ks->epie, a);
-  });
+  } else {
+    r = sweep(a, n);
+  }
   if (r) return r;
   // the host order buffer must outlive the async copy
   CK(cudaStreamSynchronize(ctx->st));
@@ -955,6 +994,7 @@ void ptycho_default_params(ptycho_params* p) {
   p->stream = nullptr;
   p->cluster = 0;
   p->likelihood = PTYCHO_LIK_AMPLITUDE;
+  p->probe_ortho = 0;
 }
 
 int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
@@ -968,6 +1008,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (p->istore < 0 || p->istore > 2) return fail(nullptr, PTYCHO_ERR_ARG, "istore=%d", p->istore);
   if (p->likelihood != PTYCHO_LIK_AMPLITUDE && p->likelihood != PTYCHO_LIK_POISSON)
     return fail(nullptr, PTYCHO_ERR_ARG, "likelihood=%d", p->likelihood);
+  if (p->probe_ortho != 0 && p->probe_ortho != 1) return fail(nullptr, PTYCHO_ERR_ARG, "probe_ortho=%d", p->probe_ortho);
+  if (p->K > MODE_KMAX) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "K=%d probe modes (at most %d)", p->K, MODE_KMAX);
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
@@ -1166,6 +1208,11 @@ int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, in
   return PTYCHO_OK;
 }
 
+int ptycho_orthogonalize_probe(ptycho_ctx* ctx) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  return ortho_step(ctx, ctx->psi_valid);
+}
+
 int ptycho_set_likelihood(ptycho_ctx* ctx, int likelihood) {
   if (!ctx) return PTYCHO_ERR_ARG;
   if (likelihood != PTYCHO_LIK_AMPLITUDE && likelihood != PTYCHO_LIK_POISSON)
@@ -1295,7 +1342,7 @@ void ptycho_destroy(ptycho_ctx* ctx) {
                   ctx->pos,      ctx->amp,       ctx->amp_scale, ctx->denO,    ctx->tile_max,  ctx->denO_max,
                   ctx->tile_ptr, ctx->tile_list, ctx->ppart,    ctx->ppart_den, ctx->pnum,     ctx->pden,
                   ctx->pblk_max, ctx->alphaO,    ctx->alphaP,   ctx->err_part, ctx->err_out,   ctx->order,
-                  ctx->flag};
+                  ctx->flag,     ctx->gram,      ctx->modeV};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (ctx->stage) cudaFree(ctx->stage);

@@ -61,7 +61,8 @@ def _compare(c, alg, n, cluster=0, seed=0, probe_start=0, **kw):
         psi = r.get_exit_waves() if alg == "dm" else None
     Oc, Pc, psic = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, seed=seed, probe_start=probe_start,
                                    **{k: v for k, v in kw.items()
-                                      if k in ("reg", "epie_alpha", "epie_beta", "lsqml_beta", "likelihood")})
+                                      if k in ("reg", "epie_alpha", "epie_beta", "lsqml_beta", "likelihood",
+                                               "probe_ortho")})
     m = illuminated(c["P"], c["pos"], c["shape"])
     eo = rel_l2(align_global(Og, Oc, m), Oc, m)
     ep = rel_l2(Pg, Pc)
@@ -368,3 +369,40 @@ def test_bad_likelihood_rejected():
     with pytest.raises(api.PtychoError) as e:
         api.Reconstruction(32, 1, len(c["pos"]), c["shape"], likelihood=7)
     assert e.value.name == "ARG"
+
+
+def _nonorthogonal_modes(P, seed=3):
+    rng = np.random.default_rng(seed)
+    K = P.shape[0]
+    U, _ = np.linalg.qr(rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K)))
+    Pm = orc.mix_modes(P, U)
+    Pm[1] = Pm[1] + 0.4 * Pm[0]
+    return Pm
+
+
+@pytest.mark.parametrize("M,K,C", [(32, 3, 4), (128, 3, 8), (32, 2, 2)], ids=lambda v: str(v))
+def test_orthogonalize_probe_matches_oracle(M, K, C):
+    c = scan(M, K, grid=2)
+    Pm = _nonorthogonal_modes(c["P"])
+    with api.Reconstruction(M, K, len(c["pos"]), c["shape"], cluster=C) as r:
+        r.set_init(c["O"], Pm)
+        r.orthogonalize_probe()
+        Pg = r.get_probe()
+    Pref, _ = orc.orthogonalize_modes(Pm)
+    assert rel_l2(Pg, Pref) < TOL_PASS
+    G = np.conj(Pg.reshape(K, -1)) @ Pg.reshape(K, -1).T
+    assert np.max(np.abs(G - np.diag(np.diag(G)))) < 1e-5 * np.abs(G).max()
+
+
+@pytest.mark.parametrize("alg,M,K,C", [("dm", 32, 3, 4), ("lsqml", 32, 3, 4), ("epie", 32, 3, 4),
+                                       ("lsqml", 128, 3, 8), ("dm", 32, 2, 2)], ids=lambda v: str(v))
+def test_algorithm_parity_with_probe_orthogonalisation(alg, M, K, C):
+    """Every iteration that updates the probe ends with the modes rotated into
+    their orthogonal basis (DM: the exit waves too), as in the oracle."""
+    c = scan(M, K, grid=3, photons=1e6, mask_frac=0.02)
+    c["P0"] = _nonorthogonal_modes(c["P0"])
+    res = _compare(c, alg, 4, cluster=C, seed=5 if alg == "epie" else 0, probe_ortho=True, probe_start=1)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
+    assert abs(res["E"] - res["E_ref"]) <= 1e-5 * res["E_ref"] + 1e-12, res
+    if "epsi" in res:
+        assert res["epsi"] < TOL_REC, res
