@@ -183,6 +183,17 @@ int ptycho_get_exit_waves(ptycho_ctx* ctx, float* out, int on_device);
 /* Iterations run so far (the counter t). */
 long long ptycho_iteration(const ptycho_ctx* ctx);
 
+/* Checkpoint / resume (SURVEY-listed DM state checkpointing): a run is
+ * resumed bit for bit from (object, probe, iteration index) -- plus, for DM,
+ * the exit waves of ptycho_get_exit_waves.
+ * ptycho_set_iteration: the index t of the next iteration (>= 0; sets the
+ *   probe_start test and the ePIE visiting order).
+ * ptycho_set_exit_waves: the DM state psi [J][K][M][M][2] (host or device,
+ *   copied; NaN/Inf rejected with the state unchanged); later DM iterations
+ *   continue from it instead of P_k O_j.  Errors: PTYCHO_ERR_* codes. */
+int ptycho_set_iteration(ptycho_ctx* ctx, long long t);
+int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* psi, int on_device);
+
 /* Number of this library's kernel launches issued so far on the context. */
 long long ptycho_launch_count(const ptycho_ctx* ctx);
 

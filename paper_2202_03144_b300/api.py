@@ -82,6 +82,8 @@ def lib() -> C.CDLL:
             "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
             "ptycho_set_likelihood": (i, [vp, i]),
             "ptycho_orthogonalize_probe": (i, [vp]),
+            "ptycho_set_iteration": (i, [vp, C.c_longlong]),
+            "ptycho_set_exit_waves": (i, [vp, vp, i]),
             "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
             "ptycho_batch_member": (vp, [vp, i]),
             "ptycho_batch_size": (i, [vp]),
@@ -323,6 +325,25 @@ class Reconstruction:
 
     def iterate(self, alg, n_iter=1):
         iterate(self.ctx, alg, n_iter)
+
+    def checkpoint(self):
+        """Everything a run needs to resume bit for bit: object, probe,
+        iteration index and (DM) the exit waves (host arrays)."""
+        state = {"object": self.get_object(), "probe": self.get_probe(), "iteration": self.iteration}
+        try:
+            state["exit_waves"] = self.get_exit_waves()
+        except PtychoError as e:
+            if e.name != "STATE":
+                raise
+        return state
+
+    def restore(self, state):
+        """Resume from :meth:`checkpoint` (data must already be set)."""
+        self.set_init(state["object"], state["probe"])
+        _check(self.ctx, lib().ptycho_set_iteration(self.ctx, int(state["iteration"])))
+        if "exit_waves" in state:
+            p, dev, keep = _ptr_in(state["exit_waves"])
+            _check(self.ctx, lib().ptycho_set_exit_waves(self.ctx, p, dev))
 
     def orthogonalize_probe(self):
         """Rotate the probe modes into orthogonal modes of decreasing power now."""

@@ -1307,6 +1307,38 @@ int ptycho_fourier_residual(ptycho_ctx* ctx, float* out, int on_device) {
 }
 
 long long ptycho_iteration(const ptycho_ctx* ctx) { return ctx ? ctx->t : -1; }
+
+int ptycho_set_iteration(ptycho_ctx* ctx, long long t) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (t < 0) return fail(ctx, PTYCHO_ERR_ARG, "iteration index %lld", t);
+  ctx->t = t;
+  return PTYCHO_OK;
+}
+
+int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* psi, int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!psi) return fail(ctx, PTYCHO_ERR_ARG, "psi is NULL");
+  if (int r = ensure_work_buffers(ctx)) return r;
+  const size_t n = (size_t)ctx->p.J * ctx->p.K * ctx->p.M * ctx->p.M * 2;  // floats
+  // checked for NaN / Inf before it replaces the state (host data through the
+  // staging buffer)
+  const float* src = psi;
+  if (!on_device) {
+    if (int r = ensure_stage(ctx, n * 4)) return r;
+    CK(cudaMemcpyAsync(ctx->stage, psi, n * 4, cudaMemcpyHostToDevice, ctx->st));
+    src = ctx->stage;
+  }
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+  k_check_finite<<<1184, 256, 0, ctx->st>>>(src, n, ctx->flag);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (bad) return fail(ctx, PTYCHO_ERR_NONFINITE, "exit waves contain NaN/Inf");
+  CK(cudaMemcpyAsync(ctx->X, src, n * 4, cudaMemcpyDeviceToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->psi_valid = true;
+  return PTYCHO_OK;
+}
 long long ptycho_launch_count(const ptycho_ctx* ctx) { return ctx ? ctx->launches : -1; }
 int ptycho_cluster_size(const ptycho_ctx* ctx) { return ctx ? ctx->C : 0; }
 

@@ -406,3 +406,39 @@ def test_algorithm_parity_with_probe_orthogonalisation(alg, M, K, C):
     assert abs(res["E"] - res["E_ref"]) <= 1e-5 * res["E_ref"] + 1e-12, res
     if "epsi" in res:
         assert res["epsi"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml", "epie"])
+def test_checkpoint_resume_is_bit_identical(alg):
+    """Four iterations in one context equal two, a checkpoint (object, probe,
+    iteration index, DM exit waves), and two more in a fresh context."""
+    c = scan(32, 3, grid=3, photons=1e5)
+    kw = dict(cluster=4, seed=11, probe_start=1)
+    with recon(c, **kw) as a:
+        a.iterate(alg, 4)
+        Oa, Pa = a.get_object(), a.get_probe()
+    with recon(c, **kw) as b:
+        b.iterate(alg, 2)
+        state = b.checkpoint()
+    assert state["iteration"] == 2 and (("exit_waves" in state) == (alg == "dm"))
+    with recon(c, **kw) as d:
+        d.restore(state)
+        assert d.iteration == 2
+        d.iterate(alg, 2)
+        Od, Pd = d.get_object(), d.get_probe()
+    assert np.array_equal(Oa, Od) and np.array_equal(Pa, Pd)
+
+
+def test_set_exit_waves_rejects_nonfinite():
+    c = scan(32, 1, grid=2)
+    with recon(c) as r:
+        r.iterate("dm", 1)
+        psi = r.get_exit_waves()
+        bad = psi.copy()
+        bad[0, 0, 1, 1] = np.nan
+        with pytest.raises(api.PtychoError) as e:
+            api._check(r.ctx, api.lib().ptycho_set_exit_waves(r.ctx, bad.ctypes.data, 0))
+        assert e.value.name == "NONFINITE"
+        assert np.array_equal(r.get_exit_waves(), psi)
+        with pytest.raises(api.PtychoError):
+            api._check(r.ctx, api.lib().ptycho_set_iteration(r.ctx, -1))
