@@ -406,6 +406,43 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
 
 
 # ---------------------------------------------------------------------------
+# Detector preprocessing (Sec. 2.2: centre, crop size, saturation bit depth,
+# noise threshold and rotation of the diffraction patterns)
+# ---------------------------------------------------------------------------
+
+def preprocess_frames(raw: np.ndarray, center: tuple, M: int, saturation_bits: int = 0,
+                      threshold: float = 0.0, rot90: int = 0) -> np.ndarray:
+    """Detector-centred M x M intensities from raw frames [J, H, W].
+
+    Output pixel (y, x) has offset d = (y - M/2, x - M/2) from the zero
+    frequency.  It reads the raw pixel center + R^-k d, where R turns an
+    offset a quarter turn counter-clockwise, (a, b) -> (-b, a), k = rot90, and
+    offsets wrap into [-M/2, M/2) (the DFT grid is periodic).  center is
+    rounded half-to-even.  A raw pixel outside the frame, negative, or (with
+    saturation_bits > 0) at or above 2^bits - 1 is masked (-1); a value below
+    threshold (> 0) becomes 0 (noise removal)."""
+    raw = np.asarray(raw, dtype=np.float64)
+    J, H, W = raw.shape
+    cy, cx = (int(v) for v in np.rint(np.asarray(center, dtype=np.float64)))
+    h = M // 2
+    dy, dx = np.meshgrid(np.arange(M) - h, np.arange(M) - h, indexing="ij")
+    sy, sx = dy, dx
+    for _ in range(rot90 % 4):  # apply R^-1: (a, b) -> (b, -a)
+        sy, sx = sx, -sy
+    sy = np.mod(sy + h, M) - h
+    sx = np.mod(sx + h, M) - h
+    ry, rx = cy + sy, cx + sx
+    inside = (ry >= 0) & (ry < H) & (rx >= 0) & (rx < W)
+    v = raw[:, np.clip(ry, 0, H - 1), np.clip(rx, 0, W - 1)]
+    masked = ~inside[None] | (v < 0)
+    if saturation_bits > 0:
+        masked |= v >= float(2 ** saturation_bits - 1)
+    if threshold > 0:
+        v = np.where(v < threshold, 0.0, v)
+    return np.where(masked, -1.0, v)
+
+
+# ---------------------------------------------------------------------------
 # Probe-mode orthogonalisation (Thibault & Menzel 2013, cited in Sec. 1)
 # ---------------------------------------------------------------------------
 

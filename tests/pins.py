@@ -485,6 +485,39 @@ def pin_dm_mode_orthogonalisation_keeps_truth(orc):
     assert np.allclose(np.sum(np.abs(P1) ** 2, axis=0), np.sum(np.abs(Pm) ** 2, axis=0), atol=1e-9)
 
 
+def pin_preprocess(orc):
+    """Detector preprocessing: a plain crop around the centre (identity for a
+    centred M x M frame), a quarter turn moves the pixel right of the zero
+    frequency to the one above it, two turns are the point reflection about
+    the zero frequency on the periodic grid, four are the identity; pixels
+    outside the raw frame, negative ones and saturated ones (>= 2^bits - 1)
+    are masked; values below the threshold become 0."""
+    rng = np.random.default_rng(5)
+    M, h = 8, 4
+    raw = rng.uniform(1.0, 100.0, (2, M, M))
+    assert np.array_equal(orc.preprocess_frames(raw, (h, h), M), raw)
+    assert np.array_equal(orc.preprocess_frames(raw, (h, h), M, rot90=4), raw)
+    y, x = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
+    assert np.array_equal(orc.preprocess_frames(raw, (h, h), M, rot90=2), raw[:, (2 * h - y) % M, (2 * h - x) % M])
+    spot = np.zeros((1, M, M))
+    spot[0, h, h + 1] = 7.0
+    q = orc.preprocess_frames(spot, (h, h), M, rot90=1)
+    assert q[0, h - 1, h] == 7.0 and np.count_nonzero(q) == 1, "quarter turn direction"
+    big = rng.uniform(1.0, 100.0, (1, 20, 24))
+    c = orc.preprocess_frames(big, (9.0, 13.0), M)
+    assert np.array_equal(c, big[:, 9 - h:9 + h, 13 - h:13 + h])
+    edge = orc.preprocess_frames(big, (2.0, 22.0), M)
+    assert np.all(edge[0, :2, :] == -1.0) and np.all(edge[0, :, -2:] == -1.0) and np.all(edge[0, 2:, :-2] > 0)
+    sat = raw.copy()
+    sat[0, 1, 1] = 4095.0
+    sat[0, 2, 2] = 4094.0
+    sat[1, 3, 3] = -5.0
+    p_ = orc.preprocess_frames(sat, (h, h), M, saturation_bits=12, threshold=10.0)
+    assert p_[0, 1, 1] == -1.0 and p_[0, 2, 2] == 4094.0 and p_[1, 3, 3] == -1.0
+    low = (sat >= 0) & (sat < 10.0)
+    assert np.all(p_[low] == 0.0) and np.all(p_[(sat >= 10.0) & (sat < 4095)] == sat[(sat >= 10.0) & (sat < 4095)])
+
+
 ALL_PINS = [
     pin_fft_bruteforce, pin_parseval, pin_forward_bruteforce, pin_mode_mixing_invariance,
     pin_gather_scatter_adjoint, pin_rounding, pin_projection, pin_fourier_error,
@@ -492,5 +525,5 @@ ALL_PINS = [
     pin_dm_overlap_least_squares, pin_dm_all_masked, pin_lsqml_step_sizes,
     pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
     pin_poisson_newton_step, pin_lsqml_poisson, pin_mode_orthogonalisation,
-    pin_dm_mode_orthogonalisation_keeps_truth,
+    pin_dm_mode_orthogonalisation_keeps_truth, pin_preprocess,
 ]

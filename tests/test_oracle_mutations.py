@@ -56,6 +56,12 @@ MUTATIONS = {
     "modes_mix_transposed": ("return np.moveaxis(np.tensordot(V, np.moveaxis(X, axis, 0), axes=([0], [0])), 0, axis)",
                              "return np.moveaxis(np.tensordot(V, np.moveaxis(X, axis, 0), axes=([1], [0])), 0, axis)"),
     "modes_dm_psi_not_mixed": ("                psi = mix_modes(psi, V, axis=1)", "                pass"),
+    "preprocess_clockwise": ("        sy, sx = sx, -sy", "        sy, sx = -sx, sy"),
+    "preprocess_no_wrap": ("    sy = np.mod(sy + h, M) - h", "    sy = sy"),
+    "preprocess_saturation_strict": ("masked |= v >= float(2 ** saturation_bits - 1)",
+                                     "masked |= v > float(2 ** saturation_bits - 1)"),
+    "preprocess_center_floor": ("cy, cx = (int(v) for v in np.rint(np.asarray(center, dtype=np.float64)))",
+                                "cy, cx = (int(v) + 1 for v in np.rint(np.asarray(center, dtype=np.float64)))"),
     "poisson_residual_minus_phi": ("return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))",
                                    "return ifft2(poisson_correction(fft2(phi), to_fft_order(I))) - phi"),
 }
