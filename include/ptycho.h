@@ -129,6 +129,31 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p);
 int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* positions,
                     int on_device);
 
+/* ---- Raw detector frames (Sec. 2.2 preprocessing parameters) ------------
+ * ptycho_set_data_raw replaces ptycho_set_data for frames straight from the
+ * detector: raw[J][raw_h][raw_w] of dtype, host or device (on_device),
+ * copied.  Each frame becomes the detector-centred M x M intensity whose
+ * pixel (y, x), at offset d = (y - M/2, x - M/2) from the zero frequency,
+ * reads the raw pixel (round(center_y), round(center_x)) + R^-rot90 d, with R
+ * a quarter turn counter-clockwise, (a, b) -> (-b, a), and offsets wrapped
+ * into [-M/2, M/2) (the DFT grid is periodic).  A raw pixel outside the
+ * frame, negative, or at / above 2^saturation_bits - 1 (saturation_bits > 0,
+ * at most 24) is masked; values below threshold (> 0) become 0 (noise
+ * removal).  Then as ptycho_set_data (same storage, checks and errors;
+ * PTYCHO_ERR_ARG for bad parameters). */
+enum { PTYCHO_RAW_U16 = 0, PTYCHO_RAW_U32 = 1, PTYCHO_RAW_F32 = 2 };
+typedef struct {
+  int raw_h, raw_w;        /* raw frame size in pixels                       */
+  int dtype;               /* PTYCHO_RAW_U16 / _U32 / _F32                    */
+  float center_y;          /* raw pixel of zero frequency (rounded half-even) */
+  float center_x;
+  int saturation_bits;     /* 0: no saturation test; 1..24: pixel bit depth  */
+  float threshold;         /* <= 0: off                                      */
+  int rot90;               /* 0..3 quarter turns counter-clockwise            */
+} ptycho_preprocess;
+int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preprocess* pp, const float* positions,
+                        int on_device);
+
 /* Upload the scan positions only ([J][2], host memory), e.g. before
  * ptycho_simulate.  Same checks as ptycho_set_data. */
 int ptycho_set_positions(ptycho_ctx* ctx, const float* positions);

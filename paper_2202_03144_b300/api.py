@@ -44,6 +44,16 @@ class Params(C.Structure):
     ]
 
 
+RAW_DTYPES = {"uint16": 0, "uint32": 1, "float32": 2}  # PTYCHO_RAW_U16 / _U32 / _F32
+
+
+class Preprocess(C.Structure):
+    _fields_ = [
+        ("raw_h", C.c_int), ("raw_w", C.c_int), ("dtype", C.c_int), ("center_y", C.c_float),
+        ("center_x", C.c_float), ("saturation_bits", C.c_int), ("threshold", C.c_float), ("rot90", C.c_int),
+    ]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double)]
 
@@ -83,6 +93,7 @@ def lib() -> C.CDLL:
             "ptycho_set_likelihood": (i, [vp, i]),
             "ptycho_orthogonalize_probe": (i, [vp]),
             "ptycho_set_iteration": (i, [vp, C.c_longlong]),
+            "ptycho_set_data_raw": (i, [vp, vp, C.POINTER(Preprocess), vp, i]),
             "ptycho_set_exit_waves": (i, [vp, vp, i]),
             "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
             "ptycho_batch_member": (vp, [vp, i]),
@@ -319,6 +330,32 @@ class Reconstruction:
 
     def set_positions(self, positions):
         set_positions(self.ctx, positions)
+
+    def set_data_raw(self, raw, positions, center, saturation_bits=0, threshold=0.0, rot90=0):
+        """Raw detector frames [J, H, W] (uint16, uint32 or float32; numpy or
+        torch, host or GPU): cropped around center (y, x), saturated pixels
+        masked, values below threshold zeroed, rotated by rot90 quarter turns
+        (counter-clockwise) about the zero frequency; see ptycho_set_data_raw."""
+        if _is_torch(raw):
+            name = str(raw.dtype).replace("torch.", "")
+            if name not in RAW_DTYPES:
+                raise ValueError("raw frames must be uint16, uint32 or float32")
+            raw = raw.contiguous()
+            ptr, dev, keep = raw.data_ptr(), int(raw.is_cuda), raw
+            if not raw.is_cuda:
+                keep = raw.numpy()
+                ptr = keep.ctypes.data
+        else:
+            keep = np.ascontiguousarray(raw)
+            name = str(keep.dtype)
+            if name not in RAW_DTYPES:
+                raise ValueError("raw frames must be uint16, uint32 or float32")
+            ptr, dev = keep.ctypes.data, 0
+        J, H, W = raw.shape
+        pp = Preprocess(H, W, RAW_DTYPES[name], float(center[0]), float(center[1]), int(saturation_bits),
+                        float(threshold), int(rot90))
+        pp_ptr, _, keep_p = _ptr_in(np.asarray(positions, dtype=np.float32))
+        _check(self.ctx, lib().ptycho_set_data_raw(self.ctx, ptr, C.byref(pp), pp_ptr, dev))
 
     def set_init(self, object=None, probe=None):
         set_init(self.ctx, object, probe)

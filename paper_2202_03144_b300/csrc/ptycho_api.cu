@@ -188,6 +188,49 @@ __global__ void k_amp_q16(const float* __restrict__ src, int nj, int M, const fl
   }
 }
 
+// Detector preprocessing of nj raw frames [H][W] into detector-centred
+// M x M intensities: output offset d = (y - M/2, x - M/2) reads raw pixel
+// (cy, cx) + R^-rot d (R: quarter turn counter-clockwise, (a, b) -> (-b, a)),
+// offsets wrapped into [-M/2, M/2); outside the frame, negative or >= sat:
+// masked (-1); below thr (> 0): 0; NaN/Inf raise *bad.  One block per
+// (output row, frame).
+struct PreArgs {
+  const void* raw;
+  int nj, H, W, cy, cx, M, rot;
+  float sat, thr;
+  float* out;
+  int* bad;
+};
+
+template <typename T>
+__global__ void k_preprocess(PreArgs a) {
+  const int y = blockIdx.x, h = a.M / 2;
+  const T* raw = reinterpret_cast<const T*>(a.raw);
+  int b = 0;
+  for (int f = blockIdx.y; f < a.nj; f += gridDim.y) {
+    for (int x = threadIdx.x; x < a.M; x += blockDim.x) {
+      int sy = y - h, sx = x - h;
+      for (int k = 0; k < a.rot; ++k) {  // R^-1: (a, b) -> (b, -a)
+        const int t = sy;
+        sy = sx;
+        sx = -t;
+      }
+      sy = ((sy + h) % a.M + a.M) % a.M - h;
+      sx = ((sx + h) % a.M + a.M) % a.M - h;
+      const int ry = a.cy + sy, rx = a.cx + sx;
+      float v = -1.f;
+      if (ry >= 0 && ry < a.H && rx >= 0 && rx < a.W) {
+        v = (float)raw[((size_t)f * a.H + ry) * a.W + rx];
+        b |= !isfinite(v);
+        if (v < 0.f || v >= a.sat) v = -1.f;
+        else if (a.thr > 0.f && v < a.thr) v = 0.f;
+      }
+      a.out[((size_t)f * a.M + y) * a.M + x] = v;
+    }
+  }
+  if (b) *a.bad = 1;
+}
+
 // Raise *bad if any of n floats is NaN or Inf.
 __global__ void k_check_finite(const float* __restrict__ p, size_t n, int* bad) {
   int b = 0;
@@ -275,6 +318,8 @@ struct ptycho_ctx {
   // st_copy while the kernels of the other half run on st
   float* stage = nullptr;
   size_t stage_bytes = 0;
+  float* pre = nullptr;      // preprocessed detector-centred frames of one chunk
+  int pre_frames = 0;
   cudaStream_t st_copy = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   // host-side state
@@ -1131,6 +1176,54 @@ static int prepare_amp(ptycho_ctx* ctx, const float* src, int j0, int nj) {
   });
 }
 
+}  // extern "C"
+
+namespace {
+
+// Frames from host memory in chunks of <= 128 MB, double-buffered on the copy
+// stream: the upload of one chunk overlaps the processing of the previous
+// one; process(dev, j0, nj) reads the chunk's frames at dev on ctx->st.
+template <class Fn>
+int upload_chunks(ptycho_ctx* ctx, const unsigned char* host, size_t frame_bytes, int J, Fn&& process) {
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / frame_bytes));
+  if (int r = ensure_stage(ctx, 2 * (size_t)chunk * frame_bytes)) return r;
+  cudaEvent_t ready = get_event(ctx);
+  CK(cudaEventRecord(ready, ctx->st));  // earlier users of the stage are done
+  CK(cudaStreamWaitEvent(ctx->st_copy, ready, 0));
+  ctx->ev_pool.push_back(ready);
+  int rc = 0;
+  for (int j0 = 0, c = 0; j0 < J && !rc; j0 += chunk, ++c) {
+    const int nj = std::min(chunk, J - j0), h = c & 1;
+    unsigned char* half = reinterpret_cast<unsigned char*>(ctx->stage) + (size_t)h * chunk * frame_bytes;
+    if (c >= 2) CK(cudaStreamWaitEvent(ctx->st_copy, ctx->ev_used[h], 0));
+    cudaError_t e = cudaMemcpyAsync(half, host + (size_t)j0 * frame_bytes, (size_t)nj * frame_bytes,
+                                    cudaMemcpyHostToDevice, ctx->st_copy);
+    if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "frame upload: %s", cudaGetErrorString(e));
+    CK(cudaEventRecord(ctx->ev_copied[h], ctx->st_copy));
+    CK(cudaStreamWaitEvent(ctx->st, ctx->ev_copied[h], 0));
+    rc = process(half, j0, nj);
+    CK(cudaEventRecord(ctx->ev_used[h], ctx->st));
+  }
+  return rc;
+}
+
+// Read the NaN/Inf flag of the uploads and mark the data present.
+int finish_set_data(ptycho_ctx* ctx, int rc, const char* what) {
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  if (bad) return fail(ctx, PTYCHO_ERR_NONFINITE, "%s: frames contain NaN or Inf", what);
+  ctx->have_data = true;
+  ctx->psi_valid = false;
+  return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* positions, int on_device) {
   if (!ctx) return PTYCHO_ERR_ARG;
   if (!intensities) return fail(ctx, PTYCHO_ERR_ARG, "intensities is NULL");
@@ -1139,43 +1232,73 @@ int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* posi
   const int J = ctx->p.J, M = ctx->p.M;
   const size_t MM = (size_t)M * M;
   CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
-  int rc = 0;
+  int rc;
   if (on_device) {
     rc = prepare_amp(ctx, intensities, 0, J);  // read in place
   } else {
-    // host frames in chunks of <= 128 MB, double-buffered: the upload of one
-    // chunk overlaps the preparation of the previous one
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / (MM * 4)));
-    if (int r = ensure_stage(ctx, 2 * (size_t)chunk * MM * 4)) return r;
-    cudaEvent_t ready = get_event(ctx);
-    CK(cudaEventRecord(ready, ctx->st));  // earlier users of the stage are done
-    CK(cudaStreamWaitEvent(ctx->st_copy, ready, 0));
-    ctx->ev_pool.push_back(ready);
-    for (int j0 = 0, c = 0; j0 < J && !rc; j0 += chunk, ++c) {
-      const int nj = std::min(chunk, J - j0), h = c & 1;
-      float* half = ctx->stage + (size_t)h * chunk * MM;
-      if (c >= 2) CK(cudaStreamWaitEvent(ctx->st_copy, ctx->ev_used[h], 0));
-      cudaError_t e = cudaMemcpyAsync(half, intensities + (size_t)j0 * MM, (size_t)nj * MM * 4, cudaMemcpyHostToDevice,
-                                      ctx->st_copy);
-      if (e != cudaSuccess) {
-        rc = fail(ctx, PTYCHO_ERR_CUDA, "intensity upload: %s", cudaGetErrorString(e));
-        break;
-      }
-      CK(cudaEventRecord(ctx->ev_copied[h], ctx->st_copy));
-      CK(cudaStreamWaitEvent(ctx->st, ctx->ev_copied[h], 0));
-      rc = prepare_amp(ctx, half, j0, nj);
-      CK(cudaEventRecord(ctx->ev_used[h], ctx->st));
-    }
+    rc = upload_chunks(ctx, reinterpret_cast<const unsigned char*>(intensities), MM * 4, J,
+                       [&](const void* dev, int j0, int nj) { return prepare_amp(ctx, (const float*)dev, j0, nj); });
   }
-  int bad = 0;
-  cudaError_t e = cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
-  if (rc) return rc;
-  if (e != cudaSuccess) return fail(ctx, PTYCHO_ERR_CUDA, "set_data: %s", cudaGetErrorString(e));
-  if (bad) return fail(ctx, PTYCHO_ERR_NONFINITE, "intensities contain NaN or Inf");
-  ctx->have_data = true;
-  ctx->psi_valid = false;
-  return PTYCHO_OK;
+  return finish_set_data(ctx, rc, "set_data");
+}
+
+int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preprocess* pp, const float* positions,
+                        int on_device) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!raw || !pp) return fail(ctx, PTYCHO_ERR_ARG, "raw frames or preprocessing parameters are NULL");
+  if (pp->raw_h < 1 || pp->raw_w < 1 || pp->dtype < PTYCHO_RAW_U16 || pp->dtype > PTYCHO_RAW_F32 ||
+      pp->saturation_bits < 0 || pp->saturation_bits > 24 || pp->rot90 < 0 || pp->rot90 > 3 ||
+      !std::isfinite(pp->center_y) || !std::isfinite(pp->center_x) || !std::isfinite(pp->threshold))
+    return fail(ctx, PTYCHO_ERR_ARG, "bad preprocessing parameters");
+  if (int r = set_positions_impl(ctx, positions)) return r;
+  ctx->have_data = false;
+  const int J = ctx->p.J, M = ctx->p.M;
+  const size_t MM = (size_t)M * M;
+  const size_t esz = pp->dtype == PTYCHO_RAW_U16 ? 2 : 4;
+  const size_t frame_bytes = (size_t)pp->raw_h * pp->raw_w * esz;
+  PreArgs q{};
+  q.H = pp->raw_h;
+  q.W = pp->raw_w;
+  q.cy = (int)std::nearbyint((double)pp->center_y);
+  q.cx = (int)std::nearbyint((double)pp->center_x);
+  q.M = M;
+  q.sat = pp->saturation_bits > 0 ? (float)((1u << pp->saturation_bits) - 1u) : INFINITY;
+  q.thr = pp->threshold;
+  q.rot = pp->rot90;
+  q.bad = ctx->flag;
+  // detector-centred intensities of one chunk, then the amplitude preparation
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / std::max(frame_bytes, MM * 4)));
+  if (ctx->pre_frames < chunk) {  // none yet, or one for a smaller chunk
+    if (ctx->pre) {
+      CK(cudaStreamSynchronize(ctx->st));
+      cudaFree(ctx->pre);
+      ctx->pre = nullptr;
+    }
+    if (int r = dalloc(ctx, &ctx->pre, (size_t)chunk * MM)) return r;
+    ctx->pre_frames = chunk;
+  }
+  auto process = [&](const void* dev, int j0, int nj) {
+    q.raw = dev;
+    q.nj = nj;
+    q.out = ctx->pre;
+    if (int r = launch(ctx, "preprocess", (double)nj * (frame_bytes + MM * 4), [&] {
+          const dim3 g((unsigned)M, (unsigned)std::min(nj, 65535));
+          if (pp->dtype == PTYCHO_RAW_U16) k_preprocess<unsigned short><<<g, 128, 0, ctx->st>>>(q);
+          else if (pp->dtype == PTYCHO_RAW_U32) k_preprocess<unsigned int><<<g, 128, 0, ctx->st>>>(q);
+          else k_preprocess<float><<<g, 128, 0, ctx->st>>>(q);
+        }))
+      return r;
+    return prepare_amp(ctx, ctx->pre, j0, nj);
+  };
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+  int rc = 0;
+  if (on_device) {
+    for (int j0 = 0; j0 < J && !rc; j0 += chunk)
+      rc = process(reinterpret_cast<const unsigned char*>(raw) + (size_t)j0 * frame_bytes, j0, std::min(chunk, J - j0));
+  } else {
+    rc = upload_chunks(ctx, reinterpret_cast<const unsigned char*>(raw), frame_bytes, J, process);
+  }
+  return finish_set_data(ctx, rc, "set_data_raw");
 }
 
 int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device) {
@@ -1378,6 +1501,7 @@ void ptycho_destroy(ptycho_ctx* ctx) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->pre) cudaFree(ctx->pre);
   if (ctx->st_copy) {
     cudaStreamSynchronize(ctx->st_copy);
     cudaStreamDestroy(ctx->st_copy);

@@ -442,3 +442,52 @@ def test_set_exit_waves_rejects_nonfinite():
         assert np.array_equal(r.get_exit_waves(), psi)
         with pytest.raises(api.PtychoError):
             api._check(r.ctx, api.lib().ptycho_set_iteration(r.ctx, -1))
+
+
+@pytest.mark.parametrize("dtype,rot,device", [("uint16", 0, False), ("uint16", 1, True), ("uint32", 3, False),
+                                              ("float32", 2, True)])
+def test_set_data_raw_matches_oracle_preprocessing(dtype, rot, device):
+    """Raw frames larger than M around an off-centre zero frequency, with
+    saturated pixels and sub-threshold noise: the stored data equal those of
+    ptycho_set_data on the oracle's preprocessed frames (identical residuals
+    and Fourier errors)."""
+    torch = pytest.importorskip("torch")
+    c = scan(64, 1, grid=3, photons=1e5)
+    J, M = len(c["pos"]), 64
+    rng = np.random.default_rng(41)
+    H, W, cy, cx = 80, 90, 37.0, 44.0
+    raw = rng.poisson(2.0, (J, H, W)).astype(np.float64)
+    # the scan's frames (detector-centred) placed so that the oracle's crop undoes the placement
+    Ic = orc.preprocess_frames(np.pad(c["I"], ((0, 0), (0, H - M), (0, W - M))), (M / 2, M / 2), M)
+    assert np.array_equal(Ic, c["I"])
+    y0, x0 = int(cy) - M // 2, int(cx) - M // 2
+    frames = np.rint(c["I"]) if dtype != "float32" else c["I"]
+    raw[:, y0:y0 + M, x0:x0 + M] = np.maximum(frames, 0)
+    raw[:, y0 + 5, x0 + 7] = 4095.0  # saturated at 12 bits
+    raw = raw.astype(dtype)
+    kw = dict(saturation_bits=12, threshold=3.0, rot90=rot)
+    Iref = orc.preprocess_frames(raw, (cy, cx), M, **kw).astype(np.float32)
+    assert (Iref == -1).sum() >= J and (Iref == 0).sum() > 0
+    res = []
+    for use_raw in (True, False):
+        with api.Reconstruction(M, 1, J, c["shape"]) as r:
+            if use_raw:
+                src = torch.from_numpy(raw).cuda() if device else raw
+                r.set_data_raw(src, c["pos"], (cy, cx), **kw)
+            else:
+                r.set_data(Iref, c["pos"])
+            r.set_init(c["O0"], c["P0"])
+            res.append((r.fourier_residual(), r.fourier_error()))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
+def test_set_data_raw_rejects_bad_parameters():
+    c = scan(32, 1, grid=2)
+    raw = np.zeros((len(c["pos"]), 40, 40), np.uint16)
+    with api.Reconstruction(32, 1, len(c["pos"]), c["shape"]) as r:
+        for kw in (dict(rot90=4), dict(saturation_bits=25), dict(saturation_bits=-1)):
+            with pytest.raises(api.PtychoError) as e:
+                r.set_data_raw(raw, c["pos"], (20, 20), **kw)
+            assert e.value.name == "ARG"
+        with pytest.raises(ValueError):
+            r.set_data_raw(raw.astype(np.int8), c["pos"], (20, 20))
