@@ -35,6 +35,7 @@ struct KernelSet {
   void (*epie)(EpieArgs);  // null: no ePIE kernel for this shape
   FourierFn spec[3][3];    // [spec_row(mode)][f32, f16, bf16]
   size_t smem_spec;        // dynamic shared memory of the spec kernels
+  bool default_ok = true;  // a candidate for the default cluster size of DM/LSQML
 };
 
 // Row of KernelSet::spec for a Fourier mode: DM, LSQML residual (amplitude),
@@ -70,7 +71,7 @@ template <int M, int K, int C>
 KernelSet make_set() {
   using F = FCfg<M, K, C>;
   using G = F2<M, K, C>;
-  KernelSet s{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>, {}, 0};
+  KernelSet s{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>, {}, 0, true};
   fill_spec<M, K, C>(s);
   return s;
 }
@@ -79,7 +80,7 @@ KernelSet make_set() {
 template <int M, int K, int C>
 KernelSet make_set_noepie() {
   using G = F2<M, K, C>;
-  KernelSet s{M, K, C, G::NT, 0, fourier2_smem<G>(), 0, k_fourier2<M, K, C>, nullptr, {}, 0};
+  KernelSet s{M, K, C, G::NT, 0, fourier2_smem<G>(), 0, k_fourier2<M, K, C>, nullptr, {}, 0, true};
   fill_spec<M, K, C>(s);
   return s;
 }

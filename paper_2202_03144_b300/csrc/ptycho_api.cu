@@ -77,12 +77,28 @@ const KernelSet* find_set(int M, int K, int C) {
 // else the smallest compiled C.  (Measured at M = 256, K = 1: 16 CTAs per
 // position beat 8 by 3%.)
 int default_cluster(int M, int K) {
+  auto ok = [&](int C) {
+    const KernelSet* s = find_set(M, K, C);
+    return s && s->default_ok;
+  };
   for (long long cap : {4096LL, 8192LL})
     for (int C = 1; C <= 16; C *= 2)
-      if ((long long)K * M * M / C <= cap && find_set(M, K, C)) return C;
+      if ((long long)K * M * M / C <= cap && ok(C)) return C;
   for (int C = 1; C <= 16; C *= 2)
-    if (find_set(M, K, C)) return C;
+    if (ok(C)) return C;
   return 0;
+}
+
+// Kernel set of the ePIE sweep: the context's own when the caller chose the
+// cluster size, else the compiled (M, K) set with the most CTAs whose ePIE
+// kernel fits in shared memory (the sweep is latency-bound: more SMs per
+// position, less time per position).
+const KernelSet* epie_set(const ptycho_params* p, const KernelSet* own, int optin) {
+  if (p->cluster > 0) return own;
+  const KernelSet* best = nullptr;
+  for (const auto& s : kernel_sets())
+    if (s.M == p->M && s.K == p->K && s.epie && s.smem_epie <= (size_t)optin && (!best || s.C > best->C)) best = &s;
+  return best ? best : own;
 }
 
 thread_local std::string g_create_error;
@@ -280,6 +296,7 @@ struct ptycho_ctx {
   ptycho_params p{};
   cudaStream_t st = nullptr;
   const KernelSet* ks = nullptr;
+  const KernelSet* eks = nullptr;  // kernel set of the ePIE sweep
   int C = 1;
   // device state
   float2* O = nullptr;
@@ -755,7 +772,7 @@ int run_lsqml(ptycho_ctx* ctx, int n) {
 int run_epie(ptycho_ctx* ctx, int n) {
   if (!ctx->epie_ok)
     return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE kernel for M=%d K=%d cluster=%d exceeds shared memory; use a larger cluster",
-                ctx->p.M, ctx->p.K, ctx->C);
+                ctx->p.M, ctx->p.K, ctx->eks ? ctx->eks->C : ctx->C);
   const int J = ctx->p.J;
   std::vector<int> ord((size_t)n * J);
   for (int it = 0; it < n; ++it) {
@@ -792,7 +809,7 @@ int run_epie(ptycho_ctx* ctx, int n) {
   a.probe_start = ctx->p.probe_start;
   a.alpha = (float)ctx->p.epie_alpha;
   a.beta = (float)ctx->p.epie_beta;
-  const KernelSet* ks = ctx->ks;
+  const KernelSet* ks = ctx->eks;
   auto sweep = [&](const EpieArgs& ea, int iters) {
     const double bytes = (double)iters * J * ctx->p.M * ctx->p.M * amp_bytes(ctx);
     return launch(ctx, "epie", bytes, [&] {
@@ -1118,11 +1135,13 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     return PTYCHO_ERR_UNSUPPORTED;
   }
   if (e == cudaSuccess) e = set_fourier_attributes(ks);
-  if (e == cudaSuccess && ks->C > 8 && ks->epie)
-    e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  ctx->epie_ok = e == cudaSuccess && ks->epie != nullptr && ks->smem_epie <= (size_t)optin;
+  if (e == cudaSuccess) ctx->eks = epie_set(p, ks, optin);
+  const KernelSet* eks = ctx->eks;
+  if (e == cudaSuccess && eks->C > 8 && eks->epie)
+    e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  ctx->epie_ok = e == cudaSuccess && eks->epie != nullptr && eks->smem_epie <= (size_t)optin;
   if (ctx->epie_ok)
-    e = cudaFuncSetAttribute(ks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->smem_epie);
+    e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eks->smem_epie);
   if (e == cudaSuccess) {
     k_twiddle<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw, p->M);
     k_twiddle2<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw2, p->M, p->M / radix1(p->M));

@@ -78,6 +78,7 @@ ALG_CASES = [
     ("lsqml", 32, 1, 1), ("lsqml", 32, 3, 1), ("lsqml", 64, 1, 4), ("lsqml", 16, 3, 2),
     ("epie", 32, 1, 1), ("epie", 32, 3, 4), ("epie", 64, 1, 2), ("epie", 16, 1, 2),
     ("dm", 96, 1, 2), ("lsqml", 96, 1, 1), ("lsqml", 192, 1, 4),
+    ("epie", 128, 3, 0),  # default: ePIE on its widest compiled cluster (16 CTAs)
 ]
 
 
