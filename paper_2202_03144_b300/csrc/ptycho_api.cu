@@ -1199,12 +1199,12 @@ static int prepare_amp(ptycho_ctx* ctx, const float* src, int j0, int nj) {
 
 namespace {
 
-// Frames from host memory in chunks of <= 128 MB, double-buffered on the copy
-// stream: the upload of one chunk overlaps the processing of the previous
-// one; process(dev, j0, nj) reads the chunk's frames at dev on ctx->st.
+// Frames from host memory in chunks of `chunk` frames, double-buffered on the
+// copy stream: the upload of one chunk overlaps the processing of the
+// previous one; process(dev, j0, nj) reads the chunk's nj <= chunk frames at
+// dev on ctx->st.
 template <class Fn>
-int upload_chunks(ptycho_ctx* ctx, const unsigned char* host, size_t frame_bytes, int J, Fn&& process) {
-  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / frame_bytes));
+int upload_chunks(ptycho_ctx* ctx, const unsigned char* host, size_t frame_bytes, int J, int chunk, Fn&& process) {
   if (int r = ensure_stage(ctx, 2 * (size_t)chunk * frame_bytes)) return r;
   cudaEvent_t ready = get_event(ctx);
   CK(cudaEventRecord(ready, ctx->st));  // earlier users of the stage are done
@@ -1255,7 +1255,8 @@ int ptycho_set_data(ptycho_ctx* ctx, const float* intensities, const float* posi
   if (on_device) {
     rc = prepare_amp(ctx, intensities, 0, J);  // read in place
   } else {
-    rc = upload_chunks(ctx, reinterpret_cast<const unsigned char*>(intensities), MM * 4, J,
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / (MM * 4)));  // <= 128 MB
+    rc = upload_chunks(ctx, reinterpret_cast<const unsigned char*>(intensities), MM * 4, J, chunk,
                        [&](const void* dev, int j0, int nj) { return prepare_amp(ctx, (const float*)dev, j0, nj); });
   }
   return finish_set_data(ctx, rc, "set_data");
@@ -1285,7 +1286,9 @@ int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preproces
   q.thr = pp->threshold;
   q.rot = pp->rot90;
   q.bad = ctx->flag;
-  // detector-centred intensities of one chunk, then the amplitude preparation
+  // detector-centred intensities of one chunk (<= 128 MB of raw frames and of
+  // their preprocessed form), then the amplitude preparation; the same chunk
+  // bounds the uploads, so a chunk never exceeds the preprocessing buffer
   const int chunk = (int)std::max<size_t>(1, std::min<size_t>(J, (128u << 20) / std::max(frame_bytes, MM * 4)));
   if (ctx->pre_frames < chunk) {  // none yet, or one for a smaller chunk
     if (ctx->pre) {
@@ -1297,6 +1300,7 @@ int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preproces
     ctx->pre_frames = chunk;
   }
   auto process = [&](const void* dev, int j0, int nj) {
+    if (nj > ctx->pre_frames) return fail(ctx, PTYCHO_ERR_ARG, "internal: chunk of %d frames exceeds %d", nj, ctx->pre_frames);
     q.raw = dev;
     q.nj = nj;
     q.out = ctx->pre;
@@ -1315,7 +1319,7 @@ int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preproces
     for (int j0 = 0; j0 < J && !rc; j0 += chunk)
       rc = process(reinterpret_cast<const unsigned char*>(raw) + (size_t)j0 * frame_bytes, j0, std::min(chunk, J - j0));
   } else {
-    rc = upload_chunks(ctx, reinterpret_cast<const unsigned char*>(raw), frame_bytes, J, process);
+    rc = upload_chunks(ctx, reinterpret_cast<const unsigned char*>(raw), frame_bytes, J, chunk, process);
   }
   return finish_set_data(ctx, rc, "set_data_raw");
 }

@@ -13,7 +13,7 @@ import pytest
 
 from gpu_cases import COMPILED, illuminated, scan
 from oracle import ptycho_oracle as orc
-from paper_2202_03144_b300 import api
+from paper_2202_03144_b300 import api, synth
 from util import align_global, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -492,3 +492,34 @@ def test_set_data_raw_rejects_bad_parameters():
             assert e.value.name == "ARG"
         with pytest.raises(ValueError):
             r.set_data_raw(raw.astype(np.int8), c["pos"], (20, 20))
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_set_data_raw_spans_several_chunks(device):
+    """600 raw 16-bit frames of a 256^2 detector (the uploads and the
+    preprocessing run in chunks of 512 frames): identical stored data to
+    ptycho_set_data on the oracle's preprocessed frames, frames on both
+    sides of the chunk boundary included."""
+    torch = pytest.importorskip("torch")
+    M, J, H, W, cy, cx = 256, 600, 270, 262, 131.0, 129.0
+    rng = np.random.default_rng(77)
+    raw = rng.poisson(5.0, (J, H, W)).astype(np.uint16)
+    raw[:, 10, 10] = 65535
+    pos = np.stack([rng.integers(0, 60, J), rng.integers(0, 60, J)], axis=1).astype(np.float64)
+    shape = (320, 320)
+    kw = dict(saturation_bits=16, threshold=2.0, rot90=1)
+    Iref = orc.preprocess_frames(raw, (cy, cx), M, **kw).astype(np.float32)
+    out = []
+    for use_raw in (True, False):
+        with api.Reconstruction(M, 1, J, shape) as r:
+            if use_raw:
+                r.set_data_raw(torch.from_numpy(raw).cuda() if device else raw, pos, (cy, cx), **kw)
+            else:
+                r.set_data(Iref, pos)
+            r.set_init(np.ones(shape, np.complex64), synth.make_probe(M, 1, R=60.0, sigma=10.0, c=0.002))
+            chi = torch.empty((J, 1, M, M), dtype=torch.complex64, device="cuda")
+            r.fourier_residual(chi)
+            torch.cuda.synchronize()
+            out.append((r.fourier_error(), chi[[0, 511, 512, 599]].cpu().numpy()))
+            del chi
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
