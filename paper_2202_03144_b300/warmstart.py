@@ -132,3 +132,45 @@ def compare(net, scan: dict, I, alg: str = "lsqml", n_ref: int = 50, check: int 
     res["warm"] = {"initial_error": E0_warm, "iterations": it, "seconds": t_inf + t_it,
                    "inference_and_stitch_seconds": t_inf, "final_error": E, "reached": bool(E <= eps)}
     return res
+
+
+def time_inference(n_warm: int = 4, n_predict: int = 3, seed: int = 11):
+    """Wall time of the warm start (network inference + stitching) on the
+    1600-position 3-mode 128^2 spiral scan, with an untrained network (the
+    time does not depend on the weights), and of predictions of 256 frames.
+    Returns (warm-start seconds per call, predict seconds per 256 frames)."""
+    import torch
+    d = synth.scan_config("modes128", seed=5)
+    M, K, pos = d["M"], d["K"], d["positions"]
+    shape = d["object"].shape
+    with api.Reconstruction(M, K, len(pos), shape) as sim:
+        sim.set_positions(pos)
+        sim.set_init(d["object"], d["probe"])
+        I = torch.empty((len(pos), M, M), dtype=torch.float32, device="cuda")
+        sim.simulate(I)
+        torch.cuda.synchronize()
+    with api.Net(seed=seed, max_batch=256) as net, api.Reconstruction(M, K, len(pos), shape) as r:
+        r.set_data(I, pos)
+        r.set_init(d["object0"], d["probe0"])
+        ws = []
+        for _ in range(n_warm):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            api.warm_start(r, net)
+            torch.cuda.synchronize()
+            ws.append(time.perf_counter() - t0)
+        out = torch.empty((256, 2, 64, 64), dtype=torch.float32, device="cuda")
+        fr = I[:256].contiguous()
+        pr = []
+        for _ in range(n_predict):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            net.predict(fr, out)
+            torch.cuda.synchronize()
+            pr.append(time.perf_counter() - t0)
+    return min(ws), min(pr)
+
+
+if __name__ == "__main__":
+    w, p = time_inference()
+    print(f"warm start (1600 frames): {w * 1e3:.2f} ms; predict (256 frames): {p * 1e3:.3f} ms")
