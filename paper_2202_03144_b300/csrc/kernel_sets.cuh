@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "epie.cuh"
+#include "epie2.cuh"
 #include "fourier2.cuh"
 #include "fourier3.cuh"
 
@@ -36,6 +37,8 @@ struct KernelSet {
   FourierFn spec[3][3];    // [spec_row(mode)][f32, f16, bf16]
   size_t smem_spec;        // dynamic shared memory of the spec kernels
   bool default_ok = true;  // a candidate for the default cluster size of DM/LSQML
+  void (*epie2)(Epie2Args) = nullptr;  // register-resident ePIE sweep (C > 1), or null
+  size_t smem_epie2 = 0;
 };
 
 // Row of KernelSet::spec for a Fourier mode: DM, LSQML residual (amplitude),
@@ -73,6 +76,10 @@ KernelSet make_set() {
   using G = F2<M, K, C>;
   KernelSet s{M, K, C, G::NT, F::NT, fourier2_smem<G>(), epie_smem<F>(), k_fourier2<M, K, C>, k_epie<M, K, C>, {}, 0, true};
   fill_spec<M, K, C>(s);
+  if constexpr (C > 1 && epie2_smem<G>() <= 227 * 1024) {
+    s.epie2 = k_epie2<M, K, C>;
+    s.smem_epie2 = epie2_smem<G>();
+  }
   return s;
 }
 

@@ -96,8 +96,10 @@ int default_cluster(int M, int K) {
 const KernelSet* epie_set(const ptycho_params* p, const KernelSet* own, int optin) {
   if (p->cluster > 0) return own;
   const KernelSet* best = nullptr;
-  for (const auto& s : kernel_sets())
-    if (s.M == p->M && s.K == p->K && s.epie && s.smem_epie <= (size_t)optin && (!best || s.C > best->C)) best = &s;
+  for (const auto& s : kernel_sets()) {
+    const bool fits = (s.epie2 && s.smem_epie2 <= (size_t)optin) || (s.epie && s.smem_epie <= (size_t)optin);
+    if (s.M == p->M && s.K == p->K && fits && (!best || s.C > best->C)) best = &s;
+  }
   return best ? best : own;
 }
 
@@ -342,6 +344,7 @@ struct ptycho_ctx {
   // host-side state
   bool have_pos = false, have_data = false;
   bool epie_ok = false;    // the ePIE kernel of this (M, K, C) fits in shared memory
+  bool epie2 = false;      // ... and it is the register-resident form (k_epie2)
   bool psi_valid = false;  // X holds the DM state
   long long t = 0;
   long long launches = 0;
@@ -815,8 +818,8 @@ int run_epie(ptycho_ctx* ctx, int n) {
     return launch(ctx, "epie", bytes, [&] {
       cudaLaunchConfig_t cfg{};
       cfg.gridDim = dim3((unsigned)ks->C);
-      cfg.blockDim = dim3((unsigned)ks->NT_epie);
-      cfg.dynamicSmemBytes = ks->smem_epie;
+      cfg.blockDim = dim3((unsigned)(ctx->epie2 ? ks->NT2 : ks->NT_epie));
+      cfg.dynamicSmemBytes = ctx->epie2 ? ks->smem_epie2 : ks->smem_epie;
       cfg.stream = ctx->st;
       cudaLaunchAttribute attr[1];
       if (ks->C > 1) {
@@ -827,7 +830,28 @@ int run_epie(ptycho_ctx* ctx, int n) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
       }
-      cudaLaunchKernelEx(&cfg, ks->epie, ea);
+      if (ctx->epie2) {
+        Epie2Args e2{};
+        e2.O = ea.O;
+        e2.nx = ea.nx;
+        e2.P = ea.P;
+        e2.pos = ea.pos;
+        e2.amp = ea.amp;
+        e2.amp_scale = ea.amp_scale;
+        e2.istore = ea.istore;
+        e2.tw2 = ctx->tw2;
+        e2.order = ea.order;
+        e2.J = ea.J;
+        e2.n_iter = ea.n_iter;
+        e2.t0 = ea.t0;
+        e2.probe_start = ea.probe_start;
+        e2.alpha = ea.alpha;
+        e2.beta = ea.beta;
+        e2.err_flag = ctx->err_flag;
+        cudaLaunchKernelEx(&cfg, ks->epie2, e2);
+      } else {
+        cudaLaunchKernelEx(&cfg, ks->epie, ea);
+      }
     });
   };
   int r = 0;
@@ -1137,11 +1161,21 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (e == cudaSuccess) e = set_fourier_attributes(ks);
   if (e == cudaSuccess) ctx->eks = epie_set(p, ks, optin);
   const KernelSet* eks = ctx->eks;
-  if (e == cudaSuccess && eks->C > 8 && eks->epie)
-    e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  ctx->epie_ok = e == cudaSuccess && eks->epie != nullptr && eks->smem_epie <= (size_t)optin;
-  if (ctx->epie_ok)
-    e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eks->smem_epie);
+  // the register-resident sweep where it is compiled and fits, else the
+  // shared-memory-pass one
+  ctx->epie2 = e == cudaSuccess && eks->epie2 != nullptr && eks->smem_epie2 <= (size_t)optin;
+  if (ctx->epie2) {
+    if (eks->C > 8) e = cudaFuncSetAttribute(eks->epie2, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(eks->epie2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eks->smem_epie2);
+    ctx->epie_ok = e == cudaSuccess;
+  } else {
+    if (e == cudaSuccess && eks->C > 8 && eks->epie)
+      e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    ctx->epie_ok = e == cudaSuccess && eks->epie != nullptr && eks->smem_epie <= (size_t)optin;
+    if (ctx->epie_ok)
+      e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eks->smem_epie);
+  }
   if (e == cudaSuccess) {
     k_twiddle<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw, p->M);
     k_twiddle2<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw2, p->M, p->M / radix1(p->M));
