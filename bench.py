@@ -269,7 +269,8 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
 
 def run_epie(api, torch, stream, iters=3, warm=1):
     """ePIE (sequential by definition) on the 3-mode 128^2 spiral scan:
-    positions*iterations/s of the persistent single-cluster kernel."""
+    positions*iterations/s of the persistent single-cluster sweep (on the
+    widest compiled cluster: its latency per position bounds the sweep)."""
     from paper_2202_03144_b300 import synth
     d = synth.scan_config("modes128", seed=5)
     M, K, pos = d["M"], d["K"], d["positions"]
@@ -294,7 +295,7 @@ def run_epie(api, torch, stream, iters=3, warm=1):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        cl = r.cluster
+        cl = r.epie_cluster
         E = r.fourier_error()
         r.close()
     return {"value": len(pos) * iters / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms / iters,

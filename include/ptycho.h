@@ -235,8 +235,13 @@ int ptycho_set_profiling(ptycho_ctx* ctx, int enabled);
 /* Writes up to max entries; *n receives the number of kernel families. */
 int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n);
 
-/* FFT cluster size chosen for this context (1, 2, 4, 8 or 16 CTAs). */
+/* CTAs per scan position of the Fourier kernels of this context (1, 2, 4, 8
+ * or 16). */
 int ptycho_cluster_size(const ptycho_ctx* ctx);
+
+/* CTAs of the persistent ePIE sweep (the widest compiled cluster for (M, K)
+ * unless ptycho_params.cluster fixed it); 0 if no ePIE kernel fits. */
+int ptycho_epie_cluster_size(const ptycho_ctx* ctx);
 
 /* ---- Many reconstructions per launch --------------------------------------
  * The paper's batch GPU mode queues many small scans, one job per GPU

@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
             "ptycho_set_likelihood": (i, [vp, i]),
             "ptycho_orthogonalize_probe": (i, [vp]),
             "ptycho_set_iteration": (i, [vp, C.c_longlong]),
+            "ptycho_epie_cluster_size": (i, [vp]),
             "ptycho_set_data_raw": (i, [vp, vp, C.POINTER(Preprocess), vp, i]),
             "ptycho_set_exit_waves": (i, [vp, vp, i]),
             "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
@@ -408,6 +409,11 @@ class Reconstruction:
 
     def simulate(self, out=None):
         return simulate(self.ctx, (self.J, self.M, self.M), out)
+
+    @property
+    def epie_cluster(self):
+        """CTAs of the ePIE sweep."""
+        return lib().ptycho_epie_cluster_size(self.ctx)
 
     @property
     def iteration(self):

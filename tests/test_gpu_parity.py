@@ -523,3 +523,11 @@ def test_set_data_raw_spans_several_chunks(device):
             out.append((r.fourier_error(), chi[[0, 511, 512, 599]].cpu().numpy()))
             del chi
     assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+
+
+def test_epie_runs_on_the_widest_cluster_by_default():
+    c = scan(128, 3, grid=2)
+    with api.Reconstruction(128, 3, len(c["pos"]), c["shape"]) as r:
+        assert r.cluster == 8 and r.epie_cluster == 16
+    with api.Reconstruction(128, 3, len(c["pos"]), c["shape"], cluster=4) as r:
+        assert r.cluster == 4 and r.epie_cluster == 4
