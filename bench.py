@@ -134,9 +134,31 @@ def oracle_intensities(P, O, pos, photons, seed):
     return synth.poisson(I, seed)
 
 
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(dist, value, device="cuda"):
+    """The largest of every rank's value (the job ends when the slowest rank
+    does); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle, as it stands, on bounded samples of the workload."""
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return
     P, O, pos, P0 = make_scan(0)
@@ -396,9 +418,7 @@ def main():
     import torch
     from paper_2202_03144_b300 import api
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -450,10 +470,7 @@ def main():
             prof = r.get_profile() if profile else None
             err = r.fourier_error()
             r.close()
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t)
+        ms = max_over_ranks(dist, ms)
         return dict(ms=ms, launches=launches, clocks=clocks, prof=prof, err=err)
 
     main_run = timed("lsqml")
@@ -464,7 +481,7 @@ def main():
     prof_run = timed("lsqml", steps=3, warm=1, profile=True)
 
     def rate(run):
-        return J * world * args.steps / (run["ms"] / 1e3)
+        return aggregate_rate(J * args.steps, world, run["ms"] / 1e3)
 
     value = rate(main_run)
     # --- roofline of the dominant kernel (live CUDA-event durations)
@@ -530,7 +547,7 @@ def main():
             if s >= 2:
                 e2e_times.append(dt)
         r.close()
-    e2e_dt = statistics.median(e2e_times)
+    e2e_dt = max_over_ranks(dist, statistics.median(e2e_times))
     # the same job from raw 16-bit detector counts (ptycho_set_data_raw: the
     # frames are already detector-centred M x M, so the crop is the identity;
     # counts at 65535 would be masked as saturated)
@@ -540,6 +557,8 @@ def main():
     with torch.cuda.stream(stream):
         r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream)
         for s in range(2 + args.steps // 5 + 1):
+            if dist:
+                dist.barrier()
             t0 = time.perf_counter()
             r.set_data_raw(I_u16, pos, (M // 2, M // 2), saturation_bits=16)
             r.set_init(O0, P0h)
@@ -550,14 +569,14 @@ def main():
             if s >= 2:
                 raw_times.append(dt)
         r.close()
-    raw_dt = statistics.median(raw_times)
+    raw_dt = max_over_ranks(dist, statistics.median(raw_times))
     h2d = I_host.numel() * 4 + pos.size * 4 + O0.numel() * 8 + P0h.numel() * 8
     d2h = Oo.numel() * 8 + Po.numel() * 8
-    e2e = {"value": J * world * args.e2e_iters / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": aggregate_rate(J * args.e2e_iters, world, e2e_dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h),
            "step": f"one job: set_data + set_init from pinned host memory, {args.e2e_iters} LSQML iterations, "
                    f"get_object + get_probe into pinned host memory",
-           "raw_u16": {"value": J * world * args.e2e_iters / raw_dt, "unit": UNIT,
+           "raw_u16": {"value": aggregate_rate(J * args.e2e_iters, world, raw_dt), "unit": UNIT,
                        "h2d_bytes_per_step": int(I_u16.numel() * 2 + pos.size * 4 + O0.numel() * 8 + P0h.numel() * 8),
                        "saturated_pixels": n_sat,
                        "step": "the same job with the frames as 16-bit detector counts (set_data_raw)"}}
