@@ -102,3 +102,49 @@ def test_fullsize_truth_is_a_fixed_point(workload, alg):
         O1, P1 = r.get_object(), r.get_probe()
     assert np.linalg.norm(O1 - O) / np.linalg.norm(O) < 1e-5
     assert np.linalg.norm(P1 - P) / np.linalg.norm(P) < 1e-5
+
+
+def test_beyond_2_to_31_elements():
+    """33,124 positions of a 256^2 detector: the residual array holds
+    2.17e9 complex values (> 2^31), so every index past frame 32,768 needs
+    64-bit arithmetic.  Forward model and residuals of frames on both sides
+    of that boundary against the oracle, and one LSQML and one DM iteration
+    that stay finite."""
+    torch = pytest.importorskip("torch")
+    G = 182
+    J = G * G
+    assert J * M * M > 2 ** 31
+    P = synth.make_probe(M, K, R=80.0, sigma=16.0, c=0.00125)
+    pos = synth.raster_positions(G, G, STEP, 2, 2, seed=2001)
+    side = -(-(24 * G + 236) // 16) * 16
+    O = synth.make_object(side, side, seed=1002)
+    sample = [0, 32767, 32768, J - 1]
+    with api.Reconstruction(M, K, J, O.shape) as r:
+        r.set_positions(pos)
+        r.set_init(O, P)
+        I = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        r.simulate(I)
+        torch.cuda.synchronize()
+        Is = I[sample].cpu().numpy()
+        pi = orc.round_positions(pos[sample])
+        Iref = orc.far_field_intensity(O, P, pi)
+        for s in range(len(sample)):
+            assert np.linalg.norm(Is[s] - Iref[s]) / np.linalg.norm(Iref[s]) < 2e-5, sample[s]
+        r.set_data(I, pos)
+        O0 = synth.make_object(side, side, seed=1003)
+        P0 = synth.noisy_probe(P, 0.1, seed=80)
+        r.set_init(O0, P0)
+        del I
+        chi = torch.empty((J, K, M, M), dtype=torch.complex64, device="cuda")
+        r.fourier_residual(chi)
+        torch.cuda.synchronize()
+        got = chi[sample].cpu().numpy()
+        del chi
+        ref = orc.fourier_residual(O0, P0, pi, Is.astype(np.float64))
+        for s in range(len(sample)):
+            assert np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s]) < 2e-5, sample[s]
+        r.iterate("lsqml", 1)
+        assert np.isfinite(r.fourier_error())
+        r.iterate("dm", 1)
+        assert np.isfinite(r.fourier_error())
+        assert np.all(np.isfinite(r.get_object())) and np.all(np.isfinite(r.get_probe()))
