@@ -681,6 +681,10 @@ int ensure_work_buffers(ptycho_ctx* ctx) {
   if (int r = dalloc(ctx, &ctx->pblk_max, (MM + PROBE_NT - 1) / PROBE_NT)) return r;
   if (int r = dalloc(ctx, &ctx->alphaO, (size_t)ctx->p.J)) return r;
   if (int r = dalloc(ctx, &ctx->alphaP, (size_t)ctx->p.J)) return r;
+  if (K > 1) {  // probe-mode orthogonalisation (allocated here: iterations may be graph-captured)
+    if (int r = dalloc(ctx, &ctx->gram, K * K)) return r;
+    if (int r = dalloc(ctx, &ctx->modeV, K * K)) return r;
+  }
   return 0;
 }
 
