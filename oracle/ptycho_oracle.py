@@ -64,6 +64,39 @@ def round_positions(positions: np.ndarray) -> np.ndarray:
     return np.rint(np.asarray(positions, dtype=np.float64)).astype(np.int64)
 
 
+def subpixel_positions(positions: np.ndarray, S: int) -> tuple[np.ndarray, np.ndarray]:
+    """Positions quantised to 1/S pixel (S even), split into integer corners
+    and sub-pixel shifts: q = rint(S y) (half to even), corner
+    p = floor((q + S/2) / S), shift delta = q / S - p in [-1/2, 1/2).
+    Returns (p [J, 2] integers, delta [J, 2] floats)."""
+    if S < 2 or S % 2:
+        raise ValueError("S must be an even integer >= 2")
+    q = np.rint(S * np.asarray(positions, dtype=np.float64)).astype(np.int64)
+    p = np.floor_divide(q + S // 2, S)
+    return p, (q - S * p) / S
+
+
+def shift_probe(P: np.ndarray, dy: float, dx: float) -> np.ndarray:
+    """T_delta P: the probe (last two axes, M x M) translated by (dy, dx)
+    pixels by the Fourier shift theorem, so (T P)(u) = P(u - delta) for a
+    band-limited periodic P:
+        F(T P)(f) = F(P)(f) exp(-2 pi i (f_y dy + f_x dx)),
+    f = k / M for k < M/2 and (k - M) / M otherwise (numpy ``fftfreq``).
+    T is unitary and T_delta^H = T_-delta."""
+    M = P.shape[-1]
+    f = np.fft.fftfreq(M)
+    ph = np.exp(-2j * np.pi * (f[:, None] * dy + f[None, :] * dx))
+    return ifft2(fft2(P) * ph)
+
+
+def position_probes(P: np.ndarray, delta: np.ndarray | None) -> np.ndarray:
+    """The probe each position sees: P[None] for integer positions (delta
+    None), else P_j = T_delta_j P, shape [J, K, M, M]."""
+    if delta is None:
+        return P[None]
+    return np.stack([shift_probe(P, dy, dx) for dy, dx in delta])
+
+
 def check_positions(pos: np.ndarray, M: int, ny: int, nx: int) -> None:
     if pos.ndim != 2 or pos.shape[1] != 2:
         raise ValueError("positions must be [J, 2]")
@@ -85,15 +118,15 @@ def scatter_add(shape: tuple, pos: np.ndarray, patches: np.ndarray) -> np.ndarra
     return acc
 
 
-def exit_waves(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
-    """psi_{j,k} = P_k * O_j, shape [J, K, M, M]."""
+def exit_waves(O: np.ndarray, P: np.ndarray, pos: np.ndarray, delta=None) -> np.ndarray:
+    """psi_{j,k} = P_k * O_j (sub-pixel: (T_delta_j P_k) * O_j), shape [J, K, M, M]."""
     M = P.shape[-1]
-    return P[None, :, :, :] * gather(O, pos, M)[:, None, :, :]
+    return position_probes(P, delta) * gather(O, pos, M)[:, None, :, :]
 
 
-def far_field_intensity(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
+def far_field_intensity(O: np.ndarray, P: np.ndarray, pos: np.ndarray, delta=None) -> np.ndarray:
     """Detector-centred I_j = fftshift(sum_k |F(P_k O_j)|^2), shape [J, M, M]."""
-    Psi = fft2(exit_waves(O, P, pos))
+    Psi = fft2(exit_waves(O, P, pos, delta))
     I = np.sum(np.abs(Psi) ** 2, axis=1)
     return np.fft.fftshift(I, axes=(-2, -1))
 
@@ -123,11 +156,11 @@ def project(Psi: np.ndarray, I_fft: np.ndarray, tau: float = TAU) -> np.ndarray:
     return np.where(masked[:, None, :, :], Psi, out)
 
 
-def fourier_error(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) -> float:
+def fourier_error(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray, delta=None) -> float:
     """E = sum m (A - sqrt I)^2 / sum m I over all frames and unmasked pixels,
     from a fresh forward pass at the current (O, P)."""
     I_fft = to_fft_order(I)
-    A = np.sqrt(np.sum(np.abs(fft2(exit_waves(O, P, pos))) ** 2, axis=1))
+    A = np.sqrt(np.sum(np.abs(fft2(exit_waves(O, P, pos, delta))) ** 2, axis=1))
     m = I_fft >= 0
     sqrtI = np.sqrt(np.where(m, I_fft, 0.0))
     num = float(np.sum(np.where(m, (A - sqrtI) ** 2, 0.0)))
@@ -158,23 +191,23 @@ def poisson_correction(Psi: np.ndarray, I_fft: np.ndarray) -> np.ndarray:
     return Psi * f[:, None, :, :]
 
 
-def poisson_nll(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray) -> float:
+def poisson_nll(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray, delta=None) -> float:
     """sum over unmasked pixels of A^2 - I log A^2 at the current (O, P)."""
     I_fft = to_fft_order(I)
-    A2 = np.sum(np.abs(fft2(exit_waves(O, P, pos))) ** 2, axis=1)
+    A2 = np.sum(np.abs(fft2(exit_waves(O, P, pos, delta))) ** 2, axis=1)
     m = I_fft >= 0
     return float(np.sum(np.where(m, A2 - np.where(m, I_fft, 0.0) * np.log(np.where(m, A2, 1.0)), 0.0)))
 
 
 def fourier_residual(O: np.ndarray, P: np.ndarray, pos: np.ndarray, I: np.ndarray,
-                     likelihood: str = "amplitude") -> np.ndarray:
+                     likelihood: str = "amplitude", delta=None) -> np.ndarray:
     """Exit-wave residual chi_{j,k}, shape [J, K, M, M].
 
     amplitude (Gaussian noise on sqrt I): chi = F^-1 Pi(F(P_k O_j)) - P_k O_j;
     poisson: chi = F^-1 [(I - A^2) / (I + A^2) F(P_k O_j)], the per-pixel
     Newton step of the Poisson negative log-likelihood along its gradient
     (:func:`poisson_correction`)."""
-    phi = exit_waves(O, P, pos)
+    phi = exit_waves(O, P, pos, delta)
     if likelihood == "amplitude":
         return ifft2(project(fft2(phi), to_fft_order(I))) - phi
     if likelihood == "poisson":
@@ -244,34 +277,42 @@ def epie_iteration(O, P, pos, I, t, seed=0, alpha=1.0, beta=1.0, probe_start=0):
 # Overlap quantities shared by DM and LSQML
 # ---------------------------------------------------------------------------
 
-def object_denominator(P: np.ndarray, pos: np.ndarray, shape: tuple) -> np.ndarray:
-    """den_O = sum_j S_j[sum_k |P_k|^2] (real, object-sized)."""
-    w = np.sum(np.abs(P) ** 2, axis=0)
-    return scatter_add(shape, pos, np.broadcast_to(w, (len(pos),) + w.shape).astype(np.float64))
+def object_denominator(P: np.ndarray, pos: np.ndarray, shape: tuple, delta=None) -> np.ndarray:
+    """den_O = sum_j S_j[sum_k |P_jk|^2] (real, object-sized); P_j is the probe
+    position j sees (:func:`position_probes`)."""
+    w = np.sum(np.abs(position_probes(P, delta)) ** 2, axis=1)
+    return scatter_add(shape, pos, np.broadcast_to(w, (len(pos),) + w.shape[1:]).astype(np.float64))
 
 
 def object_numerator(P: np.ndarray, X: np.ndarray, pos: np.ndarray, shape: tuple,
-                     weights: np.ndarray | None = None) -> np.ndarray:
-    """sum_j w_j S_j[sum_k conj(P_k) X_{j,k}] (object-sized)."""
-    c = np.sum(np.conj(P)[None] * X, axis=1)
+                     weights: np.ndarray | None = None, delta=None) -> np.ndarray:
+    """sum_j w_j S_j[sum_k conj(P_jk) X_{j,k}] (object-sized)."""
+    c = np.sum(np.conj(position_probes(P, delta)) * X, axis=1)
     if weights is not None:
         c = c * np.asarray(weights, dtype=np.float64)[:, None, None]
     return scatter_add(shape, pos, c)
 
 
 def probe_numerator(O: np.ndarray, X: np.ndarray, pos: np.ndarray,
-                    weights: np.ndarray | None = None) -> np.ndarray:
-    """sum_j w_j conj(O_j) X_{j,k}, shape [K, M, M]."""
+                    weights: np.ndarray | None = None, delta=None) -> np.ndarray:
+    """sum_j w_j conj(O_j) X_{j,k}, shape [K, M, M].  Sub-pixel positions:
+    sum_j w_j T_-delta_j[conj(O_j) X_{j,k}], the adjoint of P -> T_delta_j P
+    applied to each term (summed in j order)."""
     M = X.shape[-1]
     Oc = np.conj(gather(O, pos, M))[:, None]
     t = Oc * X
     if weights is not None:
         t = t * np.asarray(weights, dtype=np.float64)[:, None, None, None]
+    if delta is not None:
+        t = np.stack([shift_probe(t[j], -dy, -dx) for j, (dy, dx) in enumerate(delta)])
     return np.sum(t, axis=0)
 
 
 def probe_denominator(O: np.ndarray, pos: np.ndarray, M: int) -> np.ndarray:
-    """den_P = sum_j |O_j|^2, shape [M, M]."""
+    """den_P = sum_j |O_j|^2, shape [M, M].  With sub-pixel positions the same
+    unshifted sum serves as the (diagonal) preconditioner of the probe: the
+    exact normal operator sum_j T_j^H |O_j|^2 T_j is not diagonal, and
+    |O_j|^2 varies little over a fraction of a pixel."""
     return np.sum(np.abs(gather(O, pos, M)) ** 2, axis=0)
 
 
@@ -279,40 +320,42 @@ def probe_denominator(O: np.ndarray, pos: np.ndarray, M: int) -> np.ndarray:
 # DM  (difference map; Thibault et al. 2009 / 2008)
 # ---------------------------------------------------------------------------
 
-def dm_init(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
+def dm_init(O: np.ndarray, P: np.ndarray, pos: np.ndarray, delta=None) -> np.ndarray:
     """Initial exit-wave state psi = P_k O_j."""
-    return exit_waves(O, P, pos)
+    return exit_waves(O, P, pos, delta)
 
 
-def dm_overlap_update(O, P, psi, pos, reg, update_probe):
+def dm_overlap_update(O, P, psi, pos, reg, update_probe, delta=None):
     """Overlap projection: object then probe least-squares update from psi.
 
     O <- (sum_j S_j[sum_k conj(P_k) psi_jk] + d_O O) / (den_O + d_O),
     then, with the new O, P_k <- (sum_j conj(O_j) psi_jk + d_P P_k) / (den_P + d_P),
-    d = reg * max(den).
+    d = reg * max(den).  Sub-pixel positions: P_k -> P_jk in the object
+    update (exact), and the probe update takes the shifted numerator over the
+    unshifted den_P (see :func:`probe_denominator`).
     """
     M = P.shape[-1]
-    den_O = object_denominator(P, pos, O.shape)
-    num_O = object_numerator(P, psi, pos, O.shape)
+    den_O = object_denominator(P, pos, O.shape, delta)
+    num_O = object_numerator(P, psi, pos, O.shape, delta=delta)
     d_O = reg * float(den_O.max())
     O = (num_O + d_O * O) / (den_O + d_O)
     if update_probe:
         den_P = probe_denominator(O, pos, M)
-        num_P = probe_numerator(O, psi, pos)
+        num_P = probe_numerator(O, psi, pos, delta=delta)
         d_P = reg * float(den_P.max())
         P = (num_P + d_P * P) / (den_P[None] + d_P)
     return O, P
 
 
-def dm_iteration(O, P, psi, pos, I, t, reg=1e-3, probe_start=0):
+def dm_iteration(O, P, psi, pos, I, t, reg=1e-3, probe_start=0, delta=None):
     """One DM iteration (index t); returns new (O, P, psi).
 
     1-2. overlap update of O, then of P (when t >= probe_start);
     3.   phi = P_k O_j;  psi <- psi + F^-1 Pi(F(2 phi - psi)) - phi.
     """
     O, P = dm_overlap_update(O.astype(np.complex128), P.astype(np.complex128), psi, pos,
-                             reg, t >= probe_start)
-    phi = exit_waves(O, P, pos)
+                             reg, t >= probe_start, delta)
+    phi = exit_waves(O, P, pos, delta)
     psi = psi + ifft2(project(fft2(2.0 * phi - psi), to_fft_order(I))) - phi
     return O, P, psi
 
@@ -321,7 +364,7 @@ def dm_iteration(O, P, psi, pos, I, t, reg=1e-3, probe_start=0):
 # LSQML  (Odstrcil et al. 2018, amplitude likelihood, whole batch)
 # ---------------------------------------------------------------------------
 
-def lsqml_directions(O, P, chi, pos, reg, update_probe):
+def lsqml_directions(O, P, chi, pos, reg, update_probe, delta=None):
     """Steepest-descent directions and their normalising denominators.
 
     dO = sum_j S_j[sum_k conj(P_k) chi_jk] / (den_O + d_O);
@@ -329,15 +372,15 @@ def lsqml_directions(O, P, chi, pos, reg, update_probe):
     Returns (dO, dP, den_O + d_O, den_P + d_P or None).
     """
     M = P.shape[-1]
-    den_O = object_denominator(P, pos, O.shape)
+    den_O = object_denominator(P, pos, O.shape, delta)
     d_O = reg * float(den_O.max())
     wO = den_O + d_O
-    dO = object_numerator(P, chi, pos, O.shape) / wO
+    dO = object_numerator(P, chi, pos, O.shape, delta=delta) / wO
     if update_probe:
         den_P = probe_denominator(O, pos, M)
         d_P = reg * float(den_P.max())
         wP = den_P + d_P
-        dP = probe_numerator(O, chi, pos) / wP[None]
+        dP = probe_numerator(O, chi, pos, delta=delta) / wP[None]
     else:
         wP = None
         dP = np.zeros_like(P)
@@ -356,17 +399,21 @@ def lsqml_solve_2x2(A11: float, A12: float, A22: float, r1: float, r2: float) ->
     return (d * r1 - b * r2) / det, (a * r2 - b * r1) / det
 
 
-def lsqml_step_sizes(O, P, chi, pos, dO, dP):
+def lsqml_step_sizes(O, P, chi, pos, dO, dP, delta=None):
     """Per-position (alpha_O, alpha_P): least squares fit of chi_j by
-    alpha_O a_j + alpha_P b_j with a_jk = P_k dO_j and b_jk = O_j dP_k."""
+    alpha_O a_j + alpha_P b_j with a_jk = P_jk dO_j and b_jk = O_j dP_jk
+    (P_j, dP_j: the probe and its direction as position j sees them)."""
     M = P.shape[-1]
     Oj = gather(O, pos, M)
     dOj = gather(dO, pos, M)
+    Pj = position_probes(P, delta)     # [1 or J, K, M, M]
+    dPj = position_probes(dP, delta)
     aO = np.empty(len(pos))
     aP = np.empty(len(pos))
     for j in range(len(pos)):
-        a = P * dOj[j][None]
-        b = Oj[j][None] * dP
+        i = 0 if delta is None else j
+        a = Pj[i] * dOj[j][None]
+        b = Oj[j][None] * dPj[i]
         A11 = float(np.sum(np.abs(a) ** 2))
         A12 = float(np.real(np.sum(np.conj(a) * b)))
         A22 = float(np.sum(np.abs(b) ** 2))
@@ -377,7 +424,7 @@ def lsqml_step_sizes(O, P, chi, pos, dO, dP):
 
 
 def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_steps=False,
-                    likelihood="amplitude"):
+                    likelihood="amplitude", delta=None):
     """One LSQML iteration (index t); returns new (O, P) [and (alpha_O, alpha_P)].
 
     1. chi_jk = F^-1 Pi(F(P_k O_j)) - P_k O_j (amplitude likelihood) or the
@@ -388,16 +435,18 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
     4. O <- O + beta sum_j S_j[alpha_O,j sum_k conj(P_k) chi_jk] / (den_O + d_O),
        P_k <- P_k + beta sum_j alpha_P,j conj(O_j) chi_jk / (den_P + d_P),
        both from the values held at the start of the iteration.
+    Sub-pixel positions (delta): every P_k O_j is (T_delta_j P_k) O_j and the
+    probe sums take the adjoint shift (:func:`probe_numerator`).
     """
     O = O.astype(np.complex128)
     P = P.astype(np.complex128)
     upd = t >= probe_start
-    chi = fourier_residual(O, P, pos, I, likelihood)
-    dO, dP, wO, wP = lsqml_directions(O, P, chi, pos, reg, upd)
-    aO, aP = lsqml_step_sizes(O, P, chi, pos, dO, dP)
-    O_new = O + beta * object_numerator(P, chi, pos, O.shape, weights=aO) / wO
+    chi = fourier_residual(O, P, pos, I, likelihood, delta)
+    dO, dP, wO, wP = lsqml_directions(O, P, chi, pos, reg, upd, delta)
+    aO, aP = lsqml_step_sizes(O, P, chi, pos, dO, dP, delta)
+    O_new = O + beta * object_numerator(P, chi, pos, O.shape, weights=aO, delta=delta) / wO
     if upd:
-        P_new = P + beta * probe_numerator(O, chi, pos, weights=aP) / wP[None]
+        P_new = P + beta * probe_numerator(O, chi, pos, weights=aP, delta=delta) / wP[None]
     else:
         P_new = P.copy()
     if return_steps:
@@ -483,15 +532,26 @@ def orthogonalize_modes(P: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 
 def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, reg=1e-3,
                 epie_alpha=1.0, epie_beta=1.0, lsqml_beta=0.9, probe_start=0, likelihood="amplitude",
-                probe_ortho=False):
+                probe_ortho=False, subpixel=0):
     """Run n_iter iterations of 'epie', 'dm' or 'lsqml' starting at index t0.
 
     probe_ortho: after every iteration that updated the probe, orthogonalise
     its modes (:func:`orthogonalize_modes`); DM's exit waves are mixed with
     the same unitary so that psi_jk stays P_k O_j-shaped.
 
+    subpixel: S > 0 quantises the positions to 1/S pixel and shifts the probe
+    by each position's sub-pixel part (:func:`subpixel_positions`); DM and
+    LSQML only (ePIE visits one position at a time and keeps integer
+    positions).
+
     Returns (O, P, psi) -- psi is the DM state (None for the others)."""
-    pos = round_positions(positions)
+    delta = None
+    if subpixel:
+        if alg == "epie":
+            raise ValueError("sub-pixel positions are not supported by ePIE")
+        pos, delta = subpixel_positions(positions, subpixel)
+    else:
+        pos = round_positions(positions)
     O = np.asarray(O, dtype=np.complex128)
     P = np.asarray(P, dtype=np.complex128)
     check_positions(pos, P.shape[-1], *O.shape)
@@ -500,10 +560,11 @@ def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, re
             O, P = epie_iteration(O, P, pos, I, t, seed, epie_alpha, epie_beta, probe_start)
         elif alg == "dm":
             if psi is None:
-                psi = dm_init(O, P, pos)
-            O, P, psi = dm_iteration(O, P, psi, pos, I, t, reg, probe_start)
+                psi = dm_init(O, P, pos, delta)
+            O, P, psi = dm_iteration(O, P, psi, pos, I, t, reg, probe_start, delta)
         elif alg == "lsqml":
-            O, P = lsqml_iteration(O, P, pos, I, t, reg, lsqml_beta, probe_start, likelihood=likelihood)
+            O, P = lsqml_iteration(O, P, pos, I, t, reg, lsqml_beta, probe_start, likelihood=likelihood,
+                                   delta=delta)
         else:
             raise ValueError(alg)
         if probe_ortho and t >= probe_start and P.shape[0] > 1:

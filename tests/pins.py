@@ -518,6 +518,191 @@ def pin_preprocess(orc):
     assert np.all(p_[low] == 0.0) and np.all(p_[(sat >= 10.0) & (sat < 4095)] == sat[(sat >= 10.0) & (sat < 4095)])
 
 
+
+# ------------------------------------------------------- sub-pixel positions
+
+def pin_subpixel_positions(orc):
+    """Quantisation to 1/S pixel and the split into corner + shift in
+    [-1/2, 1/2), on hand-worked values (S = 8 unless stated)."""
+    raw = np.array([[10.3, -0.3], [10.5, 3.0625], [10.45, 3.1875], [7.0, 6.9375]])
+    p, d = orc.subpixel_positions(raw, 8)
+    # 10.3 -> q 82 -> (10, +1/4); -0.3 -> q -2 -> (0, -1/4); 10.5 -> q 84 -> (11, -1/2);
+    # 3.0625 -> 24.5 -> q 24 (half to even) -> (3, 0); 10.45 -> 83.6 -> q 84 -> (11, -1/2);
+    # 3.1875 -> 25.5 -> q 26 -> (3, +1/4); 7 -> (7, 0); 6.9375 -> 55.5 -> q 56 -> (7, 0)
+    assert p.tolist() == [[10, 0], [11, 3], [11, 3], [7, 7]]
+    assert d.tolist() == [[0.25, -0.25], [-0.5, 0.0], [-0.5, 0.25], [0.0, 0.0]]
+    p2, d2 = orc.subpixel_positions(np.array([[1.25, 1.75]]), 2)   # q = 2 (half to even), 4
+    assert p2.tolist() == [[1, 2]] and d2.tolist() == [[0.0, 0.0]]
+    rng = np.random.default_rng(21)
+    for S in (2, 4, 16):
+        r = rng.uniform(0, 50, (40, 2))
+        p, d = orc.subpixel_positions(r, S)
+        assert ((d >= -0.5) & (d < 0.5)).all()
+        assert np.all(np.abs(p + d - r) <= 0.5 / S + 1e-12)
+
+
+def _bandlimited(rng, M, nmax, n_terms=5):
+    """Coefficients and frequencies of a sum of complex exponentials
+    exp(2 pi i (ny y + nx x) / M) with |ny|, |nx| <= nmax."""
+    freqs = rng.integers(-nmax, nmax + 1, (n_terms, 2))
+    coef = _crandn(n_terms, rng=rng)
+    return coef, freqs
+
+
+def _eval_bandlimited(coef, freqs, M, y, x):
+    return sum(c * np.exp(2j * np.pi * (fy * y + fx * x) / M) for c, (fy, fx) in zip(coef, freqs))
+
+
+def pin_fourier_shift(orc):
+    """T_delta: integer shifts are circular shifts (np.roll), a band-limited
+    periodic function is translated exactly ((T f)(u) = f(u - delta), by
+    direct evaluation), T_a T_b = T_(a+b), and T_-delta is the adjoint."""
+    rng = np.random.default_rng(22)
+    M = 12
+    X = _crandn(2, M, M, rng=rng)
+    for dy, dx in [(1, 0), (0, 1), (-2, 3)]:
+        assert np.allclose(orc.shift_probe(X, dy, dx), np.roll(X, (dy, dx), axis=(-2, -1)), atol=1e-12)
+    coef, freqs = _bandlimited(rng, M, M // 2 - 1)
+    yy, xx = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
+    f = _eval_bandlimited(coef, freqs, M, yy, xx)
+    for dy, dx in [(0.25, -0.5), (-0.375, 0.125), (0.4, 0.3)]:
+        ref = _eval_bandlimited(coef, freqs, M, yy - dy, xx - dx)
+        assert np.allclose(orc.shift_probe(f, dy, dx), ref, atol=1e-11 * np.abs(ref).max()), "band-limited translation"
+    a = orc.shift_probe(orc.shift_probe(X, 0.25, -0.125), -0.5, 0.375)
+    assert np.allclose(a, orc.shift_probe(X, -0.25, 0.25), atol=1e-12)
+    Y = _crandn(2, M, M, rng=rng)
+    lhs = np.vdot(orc.shift_probe(X, 0.3, -0.2), Y)
+    rhs = np.vdot(X, orc.shift_probe(Y, -0.3, 0.2))
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+def pin_subpixel_forward(orc):
+    """A probe and an M-periodic object, both band-limited so that their
+    product has no frequency at or beyond M/2: the pattern of the probe at the
+    sub-pixel position y equals, by translation invariance of |F|, the pattern
+    of the unshifted probe over the object evaluated at y + u (direct
+    evaluation of the object's exponentials at non-integer points), with a
+    brute-force DFT."""
+    rng = np.random.default_rng(23)
+    M, K, S = 8, 2, 8
+    pc = [_bandlimited(rng, M, 1, 4) for _ in range(K)]
+    oc, of = _bandlimited(rng, M, 1, 5)
+    yy, xx = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
+    P = np.stack([_eval_bandlimited(c, f, M, yy, xx) for c, f in pc])
+    ny = nx = 20
+    gy, gx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    O = _eval_bandlimited(oc, of, M, gy, gx)
+    raw = np.array([[2.25, 3.625], [5.5, 1.875], [9.0, 10.125]])   # on the 1/8 grid
+    pos, delta = orc.subpixel_positions(raw, S)
+    I = orc.far_field_intensity(O, P, pos, delta)
+    for j, (y, x) in enumerate(raw):
+        ref = np.zeros((M, M))
+        Oj = _eval_bandlimited(oc, of, M, y + yy, x + xx)
+        for k in range(K):
+            X = _dft2_bruteforce(P[k] * Oj)
+            ref += np.abs(np.fft.fftshift(X)) ** 2
+        assert np.allclose(I[j], ref, rtol=1e-10, atol=1e-10 * ref.max()), f"sub-pixel pattern {j}"
+
+
+def _subpixel_case(orc, M=8, K=2, S=8, seed=24):
+    rng = np.random.default_rng(seed)
+    P, O, pos = small_scan(M=M, K=K, grid=2, step=3)
+    raw = pos + rng.uniform(-0.5, 0.5, pos.shape)
+    raw = np.clip(raw, 0.0, None)
+    p, d = orc.subpixel_positions(raw, S)
+    assert (p >= 0).all() and (p + M <= np.array(O.shape)).all()
+    return P, O, raw, p, d, rng
+
+
+def pin_subpixel_gradients(orc):
+    """Sub-pixel LSQML directions are the scaled steepest-descent directions of
+    1/2 sum_j ||chi_j - delta((T_j P) O_j)||^2 (central differences), den_O is
+    sum_j S_j[sum_k |T_j P_k|^2] by explicit loops, and the DM object update
+    minimises sum ||psi - (T_j P) O_j||^2 + d_O ||O - O_old||^2."""
+    P, O, raw, pos, delta, rng = _subpixel_case(orc)
+    M = P.shape[-1]
+    J = len(pos)
+    Pj = [orc.shift_probe(P, dy, dx) for dy, dx in delta]
+    chi = _crandn(J, 2, M, M, rng=rng)
+    dO, dP, wO, wP = orc.lsqml_directions(O, P, chi, pos, 1e-3, True, delta)
+    den = np.zeros(O.shape)
+    for j, (y, x) in enumerate(pos):
+        den[y:y + M, x:x + M] += np.sum(np.abs(Pj[j]) ** 2, axis=0)
+    assert np.allclose(wO, den + 1e-3 * den.max(), rtol=1e-12), "sub-pixel den_O"
+
+    def f(Ov, Pv):
+        return 0.5 * sum(np.sum(np.abs(chi[j] + Pj[j] * O[y:y + M, x:x + M][None]
+                                       - orc.shift_probe(Pv, *delta[j]) * Ov[y:y + M, x:x + M][None]) ** 2)
+                         for j, (y, x) in enumerate(pos))
+
+    h = 1e-6
+    for (u, v) in [(pos[0][0] + 1, pos[0][1] + 2), (pos[-1][0] + 3, pos[-1][1] + 3)]:
+        e = np.zeros_like(O)
+        e[u, v] = h
+        g = ((f(O + e, P) - f(O - e, P)) + 1j * (f(O + 1j * e, P) - f(O - 1j * e, P))) / (2 * h)
+        assert abs(dO[u, v] * wO[u, v] + g) < 1e-6 * (1 + abs(g)), "sub-pixel object direction"
+    for (k, u, v) in [(0, 1, 1), (1, 4, 2), (0, 7, 6)]:
+        e = np.zeros_like(P)
+        e[k, u, v] = h
+        g = ((f(O, P + e) - f(O, P - e)) + 1j * (f(O, P + 1j * e) - f(O, P - 1j * e))) / (2 * h)
+        assert abs(dP[k, u, v] * wP[u, v] + g) < 1e-6 * (1 + abs(g)), "sub-pixel probe direction"
+    psi = _crandn(J, 2, M, M, rng=rng)
+    reg = 0.05
+    On, _ = orc.dm_overlap_update(O, P, psi, pos, reg, False, delta)
+    dreg = reg * den.max()
+
+    def gO(Ov):
+        s = sum(np.sum(np.abs(psi[j] - Pj[j] * Ov[y:y + M, x:x + M][None]) ** 2) for j, (y, x) in enumerate(pos))
+        return s + dreg * np.sum(np.abs(Ov - O) ** 2)
+
+    base = _ls_directional_derivative(gO, O, rng)
+    assert _ls_directional_derivative(gO, On, rng) < 1e-6 * base, "sub-pixel DM object update not the LS minimiser"
+
+
+def pin_subpixel_step_sizes(orc):
+    """Sub-pixel step sizes minimise ||chi_j - aO a_j - aP b_j||^2 + lam |alpha|^2
+    with a_j = (T_j P) dO_j and b_j = O_j (T_j dP) (BFGS)."""
+    P, O, raw, pos, delta, rng = _subpixel_case(orc, seed=25)
+    M = P.shape[-1]
+    J = len(pos)
+    chi = _crandn(J, 2, M, M, rng=rng)
+    dO = _crandn(*O.shape, rng=rng)
+    dP = _crandn(2, M, M, rng=rng)
+    aO, aP = orc.lsqml_step_sizes(O, P, chi, pos, dO, dP, delta)
+    for j, (y, x) in enumerate(pos):
+        a = orc.shift_probe(P, *delta[j]) * dO[y:y + M, x:x + M][None]
+        b = O[y:y + M, x:x + M][None] * orc.shift_probe(dP, *delta[j])
+        lam = 1e-6 * (np.sum(np.abs(a) ** 2) + np.sum(np.abs(b) ** 2)) / 2
+
+        def q(v):
+            return np.sum(np.abs(chi[j] - v[0] * a - v[1] * b) ** 2) + lam * (v[0] ** 2 + v[1] ** 2)
+
+        res = optimize.minimize(q, np.zeros(2), method="BFGS", options=dict(gtol=1e-12))
+        assert np.allclose([aO[j], aP[j]], res.x, rtol=1e-5, atol=1e-7), f"sub-pixel step sizes of position {j}"
+
+
+def pin_subpixel_fixed_point_and_reduction(orc):
+    """Noise-free data simulated at sub-pixel positions is a fixed point of
+    sub-pixel LSQML, and of DM while the probe is fixed (the object update is
+    then exact least squares and psi = (T_j P) O_j is unchanged); positions
+    that fall on integers give exactly the integer path (the shift by zero is
+    the identity)."""
+    P, O, raw, pos, delta, rng = _subpixel_case(orc, M=16, seed=26)
+    I = orc.far_field_intensity(O, P, pos, delta)
+    O1, P1, _ = orc.reconstruct("lsqml", O, P, raw, I, 1, subpixel=8)
+    assert np.allclose(O1, O, atol=1e-12) and np.allclose(P1, P, atol=1e-12), "sub-pixel LSQML moved off the truth"
+    psi = orc.dm_init(O, P, pos, delta)
+    O2, P2, psi2 = orc.reconstruct("dm", O, P, raw, I, 1, psi=psi, probe_start=5, subpixel=8)
+    assert np.allclose(O2, O, atol=1e-12) and np.allclose(psi2, psi, atol=1e-12), "sub-pixel DM moved off the truth"
+    ip = pos.astype(float)
+    I2 = orc.far_field_intensity(O, P, pos)
+    O0 = np.ones_like(O)
+    for alg in ("dm", "lsqml"):
+        a = orc.reconstruct(alg, O0, P * 1.1, ip, I2, 2, subpixel=8)
+        b = orc.reconstruct(alg, O0, P * 1.1, ip, I2, 2)
+        assert np.allclose(a[0], b[0], atol=1e-12) and np.allclose(a[1], b[1], atol=1e-12), f"{alg}: zero shift"
+
+
 ALL_PINS = [
     pin_fft_bruteforce, pin_parseval, pin_forward_bruteforce, pin_mode_mixing_invariance,
     pin_gather_scatter_adjoint, pin_rounding, pin_projection, pin_fourier_error,
@@ -525,5 +710,7 @@ ALL_PINS = [
     pin_dm_overlap_least_squares, pin_dm_all_masked, pin_lsqml_step_sizes,
     pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
     pin_poisson_newton_step, pin_lsqml_poisson, pin_mode_orthogonalisation,
-    pin_dm_mode_orthogonalisation_keeps_truth, pin_preprocess,
+    pin_dm_mode_orthogonalisation_keeps_truth, pin_preprocess, pin_subpixel_positions,
+    pin_fourier_shift, pin_subpixel_forward, pin_subpixel_gradients, pin_subpixel_step_sizes,
+    pin_subpixel_fixed_point_and_reduction,
 ]

@@ -16,13 +16,14 @@ SRC = inspect.getsource(orc)
 MUTATIONS = {
     "no_sqrt_in_projection": ("sqrtI = np.sqrt(np.where(masked, 0.0, I_fft))",
                               "sqrtI = np.where(masked, 0.0, I_fft)"),
-    "conj_probe_in_exit_wave": ("return P[None, :, :, :] * gather(O, pos, M)[:, None, :, :]",
-                                "return np.conj(P)[None, :, :, :] * gather(O, pos, M)[:, None, :, :]"),
+    "conj_probe_in_exit_wave": ("return position_probes(P, delta) * gather(O, pos, M)[:, None, :, :]",
+                                "return np.conj(position_probes(P, delta)) * gather(O, pos, M)[:, None, :, :]"),
     "no_fftshift_in_forward": ("return np.fft.fftshift(I, axes=(-2, -1))", "return I"),
     "ifft_as_forward": ("return np.fft.fft2(x, axes=(-2, -1))",
                         "return np.fft.ifft2(x, axes=(-2, -1)) * (x.shape[-1] * x.shape[-2])"),
     "scatter_transposed": ("acc[y:y + M, x:x + M] += patches[j]", "acc[x:x + M, y:y + M] += patches[j]"),
-    "object_numerator_no_conj": ("c = np.sum(np.conj(P)[None] * X, axis=1)", "c = np.sum(P[None] * X, axis=1)"),
+    "object_numerator_no_conj": ("c = np.sum(np.conj(position_probes(P, delta)) * X, axis=1)",
+                                 "c = np.sum(position_probes(P, delta) * X, axis=1)"),
     "probe_numerator_no_conj": ("Oc = np.conj(gather(O, pos, M))[:, None]", "Oc = gather(O, pos, M)[:, None]"),
     "dm_reflection_swapped": ("project(fft2(2.0 * phi - psi)", "project(fft2(2.0 * psi - phi)"),
     "dm_wrong_sign_phi": ("psi = psi + ifft2(project(fft2(2.0 * phi - psi), to_fft_order(I))) - phi",
@@ -30,9 +31,9 @@ MUTATIONS = {
     "dm_drop_prox_term": ("O = (num_O + d_O * O) / (den_O + d_O)", "O = num_O / (den_O + d_O)"),
     "lsqml_solve_sign": ("return (d * r1 - b * r2) / det, (a * r2 - b * r1) / det",
                          "return (d * r1 + b * r2) / det, (a * r2 - b * r1) / det"),
-    "lsqml_conj_object_in_b": ("b = Oj[j][None] * dP", "b = np.conj(Oj[j])[None] * dP"),
-    "lsqml_swapped_weights": ("object_numerator(P, chi, pos, O.shape, weights=aO)",
-                              "object_numerator(P, chi, pos, O.shape, weights=aP)"),
+    "lsqml_conj_object_in_b": ("b = Oj[j][None] * dPj[i]", "b = np.conj(Oj[j])[None] * dPj[i]"),
+    "lsqml_swapped_weights": ("object_numerator(P, chi, pos, O.shape, weights=aO,",
+                              "object_numerator(P, chi, pos, O.shape, weights=aP,"),
     "lsqml_lambda_too_big": ("lam = 1e-6 * tr / 2.0", "lam = 1e-3 * tr / 2.0"),
     "epie_no_conj_probe": ("alpha * np.sum(np.conj(P) * Delta, axis=0) / pmax",
                            "alpha * np.sum(P * Delta, axis=0) / pmax"),
@@ -62,6 +63,18 @@ MUTATIONS = {
                                      "masked |= v > float(2 ** saturation_bits - 1)"),
     "preprocess_center_floor": ("cy, cx = (int(v) for v in np.rint(np.asarray(center, dtype=np.float64)))",
                                 "cy, cx = (int(v) + 1 for v in np.rint(np.asarray(center, dtype=np.float64)))"),
+    "shift_sign": ("ph = np.exp(-2j * np.pi", "ph = np.exp(2j * np.pi"),
+    "shift_half_frequencies": ("f = np.fft.fftfreq(M)", "f = np.fft.fftfreq(M) / 2"),
+    "shift_adjoint_same_sign": ("shift_probe(t[j], -dy, -dx)", "shift_probe(t[j], dy, dx)"),
+    "subpixel_corner_floor": ("p = np.floor_divide(q + S // 2, S)", "p = np.floor_divide(q, S)"),
+    "subpixel_truncate": ("q = np.rint(S * np.asarray(positions, dtype=np.float64)).astype(np.int64)",
+                          "q = np.trunc(S * np.asarray(positions, dtype=np.float64)).astype(np.int64)"),
+    "subpixel_den_unshifted": ("w = np.sum(np.abs(position_probes(P, delta)) ** 2, axis=1)",
+                               "w = np.sum(np.abs(position_probes(P, None)) ** 2, axis=1)"),
+    "subpixel_steps_unshifted_dP": ("b = Oj[j][None] * dPj[i]", "b = Oj[j][None] * dP"),
+    "subpixel_steps_unshifted_P": ("a = Pj[i] * dOj[j][None]", "a = P * dOj[j][None]"),
+    "subpixel_dm_phi_unshifted": ("phi = exit_waves(O, P, pos, delta)\n    psi = psi",
+                                  "phi = exit_waves(O, P, pos)\n    psi = psi"),
     "poisson_residual_minus_phi": ("return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))",
                                    "return ifft2(poisson_correction(fft2(phi), to_fft_order(I))) - phi"),
 }
