@@ -310,15 +310,68 @@ def probe_numerator(O: np.ndarray, X: np.ndarray, pos: np.ndarray,
 
 def probe_denominator(O: np.ndarray, pos: np.ndarray, M: int) -> np.ndarray:
     """den_P = sum_j |O_j|^2, shape [M, M].  With sub-pixel positions the same
-    unshifted sum serves as the (diagonal) preconditioner of the probe: the
-    exact normal operator sum_j T_j^H |O_j|^2 T_j is not diagonal, and
-    |O_j|^2 varies little over a fraction of a pixel."""
+    unshifted sum serves as the diagonal scaling of the LSQML probe direction
+    and as the preconditioner of the DM probe solve: the exact normal operator
+    sum_j T_j^H |O_j|^2 T_j is not diagonal, and |O_j|^2 varies little over a
+    fraction of a pixel."""
     return np.sum(np.abs(gather(O, pos, M)) ** 2, axis=0)
 
 
 # ---------------------------------------------------------------------------
 # DM  (difference map; Thibault et al. 2009 / 2008)
 # ---------------------------------------------------------------------------
+
+DM_PROBE_CG = 4     # conjugate-gradient iterations of the sub-pixel DM probe solve
+
+
+def probe_normal_operator(O: np.ndarray, pos: np.ndarray, delta: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """B X = sum_j T_-delta_j[|O_j|^2 T_delta_j X]: the normal operator of
+    P -> {(T_delta_j P) O_j}, applied to probe-shaped X [K, M, M] (summed in j
+    order)."""
+    M = X.shape[-1]
+    D = np.abs(gather(O, pos, M)) ** 2
+    out = np.zeros_like(X, dtype=np.complex128)
+    for j, (dy, dx) in enumerate(delta):
+        out += shift_probe(D[j][None] * shift_probe(X, dy, dx), -dy, -dx)
+    return out
+
+
+def dm_probe_solve(O, P, psi, pos, reg, delta, n_cg=DM_PROBE_CG):
+    """Sub-pixel DM probe update: the least-squares problem
+        min_P sum_j ||psi_j - (T_delta_j P) O_j||^2 + d_P ||P - P_old||^2
+    has the normal equations (B + d_P) P = sum_j T_-delta_j[conj(O_j) psi_j]
+    + d_P P_old (B: :func:`probe_normal_operator`), no longer diagonal.  They
+    are solved by n_cg iterations of preconditioned conjugate gradients from
+    P_old, with the diagonal preconditioner den_P + d_P (den_P =
+    sum_j |O_j|^2, d_P = reg max den_P) and Re<.,.> over all modes and pixels:
+        r = rhs - (B + d) X,  z = r / (den + d),  p = z;
+        repeat: q = (B + d) p, a = <r,z>/<p,q>, X += a p, r -= a q,
+                z = r / (den + d), b = <r,z>_new/<r,z>_old, p = z + b p.
+    A zero <p,q> or <r,z> ends the updates (a = 0, b = 0).  Without the exact
+    solve the overlap step is not a projection and the difference map drifts
+    off (the diagonal form with the shifted numerator diverges)."""
+    M = P.shape[-1]
+    den = probe_denominator(O, pos, M)
+    d = reg * float(den.max())
+    w = (den + d)[None]
+    X = P.copy()
+    r = probe_numerator(O, psi, pos, delta=delta) - probe_normal_operator(O, pos, delta, X)
+    z = r / w
+    p = z.copy()
+    rz = float(np.real(np.vdot(r, z)))
+    for _ in range(n_cg):
+        q = probe_normal_operator(O, pos, delta, p) + d * p
+        pq = float(np.real(np.vdot(p, q)))
+        a = rz / pq if pq > 0 else 0.0
+        X = X + a * p
+        r = r - a * q
+        z = r / w
+        rz_new = float(np.real(np.vdot(r, z)))
+        b = rz_new / rz if rz > 0 else 0.0
+        p = z + b * p
+        rz = rz_new
+    return X
+
 
 def dm_init(O: np.ndarray, P: np.ndarray, pos: np.ndarray, delta=None) -> np.ndarray:
     """Initial exit-wave state psi = P_k O_j."""
@@ -331,17 +384,19 @@ def dm_overlap_update(O, P, psi, pos, reg, update_probe, delta=None):
     O <- (sum_j S_j[sum_k conj(P_k) psi_jk] + d_O O) / (den_O + d_O),
     then, with the new O, P_k <- (sum_j conj(O_j) psi_jk + d_P P_k) / (den_P + d_P),
     d = reg * max(den).  Sub-pixel positions: P_k -> P_jk in the object
-    update (exact), and the probe update takes the shifted numerator over the
-    unshifted den_P (see :func:`probe_denominator`).
+    update (exact), and the probe update solves its (non-diagonal) normal
+    equations by conjugate gradients (:func:`dm_probe_solve`).
     """
     M = P.shape[-1]
     den_O = object_denominator(P, pos, O.shape, delta)
     num_O = object_numerator(P, psi, pos, O.shape, delta=delta)
     d_O = reg * float(den_O.max())
     O = (num_O + d_O * O) / (den_O + d_O)
-    if update_probe:
+    if update_probe and delta is not None:
+        P = dm_probe_solve(O, P, psi, pos, reg, delta)
+    elif update_probe:
         den_P = probe_denominator(O, pos, M)
-        num_P = probe_numerator(O, psi, pos, delta=delta)
+        num_P = probe_numerator(O, psi, pos)
         d_P = reg * float(den_P.max())
         P = (num_P + d_P * P) / (den_P[None] + d_P)
     return O, P

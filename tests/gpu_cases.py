@@ -46,3 +46,26 @@ def scan(M, K, grid=3, step=None, jitter=1, seed=0, photons=None, mask_frac=0.0,
 def illuminated(P, pos, shape, frac=0.1):
     den = orc.object_denominator(P, orc.round_positions(pos), shape)
     return den >= frac * den.max()
+
+
+def subpixel_scan(M, K, S, grid=3, step=None, seed=0, photons=None, mask_frac=0.0):
+    """A scan at fractional positions (raster + uniform offsets in [0, 1)),
+    float32 like the values the ABI receives, with the oracle's sub-pixel
+    forward model at 1/S-pixel quantisation."""
+    step = step or max(2, M // 4)
+    rng = np.random.default_rng(seed + 30)
+    P = synth.make_probe(M, K, R=M / 4.0, sigma=M / 16.0, c=0.6 / M)
+    base = synth.raster_positions(grid, grid, step, 1, 1, seed=seed + 1)
+    pos = (np.rint(base) + rng.uniform(0.0, 1.0, base.shape)).astype(np.float32).astype(np.float64)
+    corner, delta = orc.subpixel_positions(pos, S)
+    ny = int(corner[:, 0].max()) + M
+    nx = int(corner[:, 1].max()) + M
+    O = synth.make_object(ny, nx, seed=seed + 2, smooth=max(1.0, M / 16))
+    I = orc.far_field_intensity(O, P, corner, delta)
+    if photons:
+        I = synth.poisson(I * photons / I.sum(axis=(1, 2)).mean(), seed=seed + 3)
+    if mask_frac > 0:
+        I = np.where(rng.random(I.shape) < mask_frac, -1.0, I)
+    O0 = synth.flat_object(ny, nx)
+    P0 = synth.noisy_probe(P, 0.1, seed=seed + 5)
+    return dict(M=M, K=K, S=S, P=P, O=O, pos=pos, corner=corner, delta=delta, I=I, O0=O0, P0=P0, shape=(ny, nx))

@@ -659,6 +659,58 @@ def pin_subpixel_gradients(orc):
     assert _ls_directional_derivative(gO, On, rng) < 1e-6 * base, "sub-pixel DM object update not the LS minimiser"
 
 
+def pin_subpixel_dm_probe_solve(orc):
+    """The sub-pixel DM probe update: run to convergence (60 conjugate-gradient
+    iterations) it minimises sum ||psi_j - (T_j P) O_j||^2 + d_P ||P - P_old||^2
+    (central differences along random directions, the shift from explicit
+    loops over positions); the normal operator is Hermitian positive; the
+    default iteration count already leaves a smaller normal-equation residual
+    than the diagonal (unshifted-denominator) update."""
+    P, O, raw, pos, delta, rng = _subpixel_case(orc, seed=27)
+    M = P.shape[-1]
+    J = len(pos)
+    psi = _crandn(J, 2, M, M, rng=rng)
+    reg = 0.05
+    den = sum(np.abs(O[y:y + M, x:x + M]) ** 2 for (y, x) in pos)
+    d = reg * den.max()
+
+    def g(Pv):
+        s = sum(np.sum(np.abs(psi[j] - orc.shift_probe(Pv, *delta[j]) * O[y:y + M, x:x + M][None]) ** 2)
+                for j, (y, x) in enumerate(pos))
+        return s + d * np.sum(np.abs(Pv - P) ** 2)
+
+    Pn = orc.dm_probe_solve(O, P, psi, pos, reg, delta, n_cg=60)
+    base = _ls_directional_derivative(g, P, rng)
+    assert _ls_directional_derivative(g, Pn, rng) < 1e-6 * base, "sub-pixel DM probe solve not the LS minimiser"
+    X, Y = _crandn(2, M, M, rng=rng), _crandn(2, M, M, rng=rng)
+    BX, BY = orc.probe_normal_operator(O, pos, delta, X), orc.probe_normal_operator(O, pos, delta, Y)
+    assert abs(np.vdot(Y, BX) - np.vdot(BY, X)) < 1e-12 * abs(np.vdot(Y, BX)) and np.vdot(X, BX).real > 0
+
+    def residual(Pv):
+        rhs = sum(orc.shift_probe(np.conj(O[y:y + M, x:x + M])[None] * psi[j], -delta[j][0], -delta[j][1])
+                  for j, (y, x) in enumerate(pos)) + d * P
+        return np.linalg.norm(orc.probe_normal_operator(O, pos, delta, Pv) + d * Pv - rhs)
+
+    num = sum(orc.shift_probe(np.conj(O[y:y + M, x:x + M])[None] * psi[j], -delta[j][0], -delta[j][1])
+              for j, (y, x) in enumerate(pos))
+    diag = (num + d * P) / (den + d)[None]
+    assert residual(orc.dm_probe_solve(O, P, psi, pos, reg, delta)) < residual(diag)
+    # n conjugate-gradient steps = the A-norm-optimal point of the real Krylov
+    # space P + span{z0, (W^-1 A) z0, ...} (Hestenes & Stiefel), found here by
+    # a Galerkin solve over an explicit basis; A = B + d, W = den + d
+    A = lambda V: orc.probe_normal_operator(O, pos, delta, V) + d * V
+    r0 = num + d * P - A(P)
+    basis = [r0 / (den + d)[None]]
+    for n in (1, 2, 3):
+        V = basis[:n]
+        G = np.array([[np.real(np.vdot(a, A(b))) for b in V] for a in V])
+        y = np.linalg.solve(G, np.array([np.real(np.vdot(a, r0)) for a in V]))
+        ref = P + sum(c * v for c, v in zip(y, V))
+        got = orc.dm_probe_solve(O, P, psi, pos, reg, delta, n_cg=n)
+        assert np.linalg.norm(got - ref) < 1e-8 * np.linalg.norm(ref), f"CG step {n} is not Krylov-optimal"
+        basis.append(A(basis[-1]) / (den + d)[None])
+
+
 def pin_subpixel_step_sizes(orc):
     """Sub-pixel step sizes minimise ||chi_j - aO a_j - aP b_j||^2 + lam |alpha|^2
     with a_j = (T_j P) dO_j and b_j = O_j (T_j dP) (BFGS)."""
@@ -694,6 +746,9 @@ def pin_subpixel_fixed_point_and_reduction(orc):
     psi = orc.dm_init(O, P, pos, delta)
     O2, P2, psi2 = orc.reconstruct("dm", O, P, raw, I, 1, psi=psi, probe_start=5, subpixel=8)
     assert np.allclose(O2, O, atol=1e-12) and np.allclose(psi2, psi, atol=1e-12), "sub-pixel DM moved off the truth"
+    O3, P3, psi3 = orc.reconstruct("dm", O, P, raw, I, 1, psi=psi, subpixel=8)
+    assert np.allclose(O3, O, atol=1e-12) and np.allclose(P3, P, atol=1e-12) and np.allclose(psi3, psi, atol=1e-12), \
+        "sub-pixel DM (probe updated) moved off the truth"
     ip = pos.astype(float)
     I2 = orc.far_field_intensity(O, P, pos)
     O0 = np.ones_like(O)
@@ -711,6 +766,7 @@ ALL_PINS = [
     pin_lsqml_er_special_case, pin_lsqml_all_masked, pin_lsqml_directions,
     pin_poisson_newton_step, pin_lsqml_poisson, pin_mode_orthogonalisation,
     pin_dm_mode_orthogonalisation_keeps_truth, pin_preprocess, pin_subpixel_positions,
-    pin_fourier_shift, pin_subpixel_forward, pin_subpixel_gradients, pin_subpixel_step_sizes,
+    pin_fourier_shift, pin_subpixel_forward, pin_subpixel_gradients, pin_subpixel_dm_probe_solve,
+    pin_subpixel_step_sizes,
     pin_subpixel_fixed_point_and_reduction,
 ]

@@ -1,0 +1,186 @@
+"""GPU parity of sub-pixel positions (probe translated by the Fourier shift
+theorem, positions quantised to 1/S pixel) against the FP64 oracle.
+
+Same tolerances as the integer path: the shifted-probe table adds four
+length-M FP32 transforms per probe value (relative error a few 1e-7), well
+inside 2e-5 for single passes and 1e-4 for reconstructions."""
+import numpy as np
+import pytest
+
+from gpu_cases import subpixel_scan
+from oracle import ptycho_oracle as orc
+from paper_2202_03144_b300 import api
+from util import align_global, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_PASS = 2e-5
+TOL_REC = 1e-4
+
+
+def _recon(c, cluster=0, **kw):
+    r = api.Reconstruction(c["M"], c["K"], len(c["pos"]), c["shape"], cluster=cluster, subpixel=c["S"], **kw)
+    r.set_data(c["I"].astype(np.float32), c["pos"])
+    r.set_init(c["O0"], c["P0"])
+    return r
+
+
+def _illuminated(c, frac=0.1):
+    den = orc.object_denominator(c["P"], c["corner"], c["shape"], c["delta"])
+    return den >= frac * den.max()
+
+
+PASS_CASES = [(16, 1, 1, 2), (32, 3, 4, 8), (64, 1, 2, 16), (96, 1, 2, 8), (128, 3, 8, 4), (192, 1, 4, 8),
+              (256, 1, 16, 8)]
+
+
+@pytest.mark.parametrize("M,K,C,S", PASS_CASES, ids=lambda v: str(v))
+def test_subpixel_forward_model(M, K, C, S):
+    c = subpixel_scan(M, K, S, grid=2)
+    with api.Reconstruction(M, K, len(c["pos"]), c["shape"], cluster=C, subpixel=S) as r:
+        r.set_positions(c["pos"])
+        r.set_init(c["O"], c["P"])
+        I = r.simulate()
+    assert rel_l2(I, c["I"]) < TOL_PASS
+
+
+@pytest.mark.parametrize("M,K,C,S", PASS_CASES, ids=lambda v: str(v))
+def test_subpixel_residual_and_error(M, K, C, S):
+    c = subpixel_scan(M, K, S, grid=2, mask_frac=0.05)
+    with _recon(c, cluster=C) as r:
+        chi = r.fourier_residual()
+        E = r.fourier_error()
+    chi_ref = orc.fourier_residual(c["O0"], c["P0"], c["corner"], c["I"], delta=c["delta"])
+    assert rel_l2(chi, chi_ref) < TOL_PASS
+    E_ref = orc.fourier_error(c["O0"], c["P0"], c["corner"], c["I"], delta=c["delta"])
+    assert abs(E - E_ref) <= 1e-5 * E_ref
+
+
+def _compare(c, alg, n, cluster=0, probe_start=0, **kw):
+    with _recon(c, cluster=cluster, probe_start=probe_start, **kw) as r:
+        r.iterate(alg, n)
+        Og, Pg = r.get_object(), r.get_probe()
+        E = r.fourier_error()
+        psi = r.get_exit_waves() if alg == "dm" else None
+    Oc, Pc, psic = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, probe_start=probe_start,
+                                   subpixel=c["S"], **{k: v for k, v in kw.items() if k in ("likelihood", "probe_ortho")})
+    m = _illuminated(c)
+    out = dict(eo=rel_l2(align_global(Og, Oc, m), Oc, m), ep=rel_l2(Pg, Pc), E=E,
+               E_ref=orc.fourier_error(Oc, Pc, c["corner"], c["I"], delta=c["delta"]))
+    if psi is not None:
+        out["epsi"] = rel_l2(psi, psic)
+    return out
+
+
+ALG_CASES = [
+    ("dm", 32, 1, 1, 8), ("dm", 32, 3, 4, 4), ("dm", 16, 2, 1, 2), ("dm", 96, 1, 2, 16),
+    ("lsqml", 32, 1, 1, 8), ("lsqml", 32, 3, 4, 16), ("lsqml", 64, 1, 2, 4), ("lsqml", 16, 3, 2, 2),
+    ("lsqml", 192, 1, 4, 8), ("lsqml", 256, 1, 8, 8), ("dm", 128, 3, 8, 8),
+]
+
+
+@pytest.mark.parametrize("alg,M,K,C,S", ALG_CASES, ids=lambda v: str(v))
+@pytest.mark.parametrize("n", [1, 8])
+def test_subpixel_algorithm_parity(alg, M, K, C, S, n):
+    if M >= 128 and n > 1:
+        n = 3
+    c = subpixel_scan(M, K, S, grid=3, photons=1e6, mask_frac=0.02)
+    res = _compare(c, alg, n, cluster=C)
+    assert res["eo"] < TOL_REC, res
+    assert res["ep"] < TOL_REC, res
+    # E is evaluated at each side's own (O, P): besides the 1e-5 of one pass it
+    # carries their difference, |dE|/E <= 2 |dA|/|A - sqrt I| ~ 2 rel(A)/sqrt(E)
+    # with rel(A) <= eo + ep
+    tol_E = 1e-5 + 4.0 * max(res["eo"], res["ep"]) / np.sqrt(res["E_ref"])
+    assert abs(res["E"] - res["E_ref"]) <= tol_E * res["E_ref"] + 1e-12, res
+    if "epsi" in res:
+        assert res["epsi"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+def test_subpixel_fixed_probe_then_update(alg):
+    c = subpixel_scan(32, 2, 8, grid=3, photons=1e6)
+    res = _compare(c, alg, 4, probe_start=2)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
+
+
+def test_subpixel_poisson_and_orthogonalisation():
+    c = subpixel_scan(32, 3, 8, grid=3, photons=1e5)
+    res = _compare(c, "lsqml", 4, likelihood="poisson", probe_ortho=True)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
+    res = _compare(c, "dm", 4, probe_ortho=True)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC and res["epsi"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("istore", ["f16", "bf16"])
+def test_subpixel_16bit_storage(istore):
+    """16-bit amplitude storage with sub-pixel positions against the FP64
+    oracle: within the storage rounding (2^-11 and 2^-8 relative on sqrt I)."""
+    c = subpixel_scan(64, 1, 8, grid=3, photons=1e6)
+    n = 3
+    Oc, Pc, _ = orc.reconstruct("lsqml", c["O0"], c["P0"], c["pos"], c["I"], n, subpixel=8)
+    with _recon(c, cluster=2, istore=istore) as r:
+        r.iterate("lsqml", n)
+        Og, Pg = r.get_object(), r.get_probe()
+    m = _illuminated(c)
+    tol = 5e-3 if istore == "f16" else 5e-2
+    assert rel_l2(align_global(Og, Oc, m), Oc, m) < tol and rel_l2(Pg, Pc) < tol
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+def test_subpixel_step_mode_equals_whole_mode(alg):
+    c = subpixel_scan(32, 3, 8, grid=3, photons=1e5)
+    with _recon(c, cluster=4) as a:
+        a.iterate(alg, 4)
+        Oa, Pa = a.get_object(), a.get_probe()
+    with _recon(c, cluster=4) as b:
+        for _ in range(4):
+            b.iterate(alg, 1)
+            b.get_object()
+        Ob, Pb = b.get_object(), b.get_probe()
+    assert np.array_equal(Oa, Ob) and np.array_equal(Pa, Pb)
+
+
+def test_subpixel_integral_positions_match_integer_path():
+    """Positions on whole pixels: every shift is zero and the sub-pixel path
+    equals the integer one up to the rounding of the zero shift's transforms."""
+    c = subpixel_scan(32, 1, 8, grid=3, photons=1e6)
+    pos = np.rint(c["pos"])
+    corner, delta = orc.subpixel_positions(pos, 8)
+    assert not delta.any()
+    I = orc.far_field_intensity(c["O"], c["P"], corner).astype(np.float32)
+    out = []
+    for S in (0, 8):
+        with api.Reconstruction(32, 1, len(pos), c["shape"], subpixel=S) as r:
+            r.set_data(I, pos)
+            r.set_init(c["O0"], c["P0"])
+            r.iterate("lsqml", 5)
+            out.append((r.get_object(), r.get_probe()))
+    assert rel_l2(out[1][0], out[0][0]) < 1e-5 and rel_l2(out[1][1], out[0][1]) < 1e-5
+
+
+def test_subpixel_epie_unsupported_and_bad_params():
+    c = subpixel_scan(32, 1, 8, grid=2)
+    with _recon(c) as r:
+        with pytest.raises(api.PtychoError) as e:
+            r.iterate("epie", 1)
+        assert e.value.name == "UNSUPPORTED"
+        r.iterate("lsqml", 1)   # the context stays usable
+    for S in (1, 3, 6, 32, -2):
+        with pytest.raises(api.PtychoError) as e:
+            api.Reconstruction(32, 1, 4, (64, 64), subpixel=S)
+        assert e.value.name == "ARG"
+
+
+def test_subpixel_bounds():
+    """The corner of a position within 1/(2S) of the object's edge rounds up
+    and the patch falls outside: PTYCHO_ERR_BOUNDS, as for integer positions."""
+    M = 32
+    with api.Reconstruction(M, 1, 2, (64, 64), subpixel=8) as r:
+        r.set_positions(np.array([[0.0, 0.0], [32.0, 31.9]], np.float32))  # 31.9 -> corner 32: fits
+        with pytest.raises(api.PtychoError) as e:
+            r.set_positions(np.array([[0.0, 0.0], [32.5, 0.0]], np.float32))  # corner 33
+        assert e.value.name == "BOUNDS"
+        with pytest.raises(api.PtychoError) as e:
+            r.set_positions(np.array([[-0.6, 0.0], [0.0, 0.0]], np.float32))  # corner -1
+        assert e.value.name == "BOUNDS"

@@ -75,6 +75,11 @@ MUTATIONS = {
     "subpixel_steps_unshifted_P": ("a = Pj[i] * dOj[j][None]", "a = P * dOj[j][None]"),
     "subpixel_dm_phi_unshifted": ("phi = exit_waves(O, P, pos, delta)\n    psi = psi",
                                   "phi = exit_waves(O, P, pos)\n    psi = psi"),
+    "subpixel_cg_unshifted_operator": ("out += shift_probe(D[j][None] * shift_probe(X, dy, dx), -dy, -dx)",
+                                       "out += D[j][None] * X"),
+    "subpixel_cg_step_sign": ("        X = X + a * p\n", "        X = X - a * p\n"),
+    "subpixel_cg_no_conjugation": ("        p = z + b * p\n", "        p = z\n"),
+    "subpixel_dm_diagonal_probe": ("    if update_probe and delta is not None:", "    if False:"),
     "poisson_residual_minus_phi": ("return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))",
                                    "return ifft2(poisson_correction(fft2(phi), to_fft_order(I))) - phi"),
 }
