@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "patterns·iter/s (DM/LSQML, 256² det, 10k pos) and time-to-ε vs plain FP32, 1 B300"
 UNIT = "patterns*iter/s"
 WORKLOAD = dict(M=256, K=1, grid=100, step=24, jitter=2, obj=2640, photons=1e5)
+SUBPIXEL = 8   # 1/8-pixel position quantisation of the sub-pixel variants
 
 
 def workload_desc(w=WORKLOAD):
@@ -416,7 +417,7 @@ def main():
         return run_reference(args)
 
     import torch
-    from paper_2202_03144_b300 import api
+    from paper_2202_03144_b300 import api, synth
 
     world, rank, local = rank_env()
     torch.cuda.set_device(local)
@@ -442,13 +443,27 @@ def main():
         gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
         I = torch.poisson(I * scale, generator=gen)
         P0s = P0 * np.sqrt(scale)
+        # the same scan at fractional positions (1/8-pixel shifts of the probe)
+        pos_sub = synth.fractional_positions(pos, seed=2002 + rank)
+        sim = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, subpixel=SUBPIXEL)
+        sim.set_positions(pos_sub)
+        sim.set_init(O, P)
+        I_sub = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        sim.simulate(I_sub)
+        stream.synchronize()
+        sim.close()
+        I_sub = torch.poisson(I_sub * scale, generator=gen)
     stream.synchronize()
 
-    def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False, likelihood="amplitude"):
+    def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False, likelihood="amplitude",
+              subpixel=0):
         with torch.cuda.stream(stream):
             r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore,
-                                   cluster=args.cluster, likelihood=likelihood)
-            r.set_data(I, pos)
+                                   cluster=args.cluster, likelihood=likelihood, subpixel=subpixel)
+            if subpixel:
+                r.set_data(I_sub, pos_sub)
+            else:
+                r.set_data(I, pos)
             r.set_init(np.ones((w["obj"], w["obj"]), np.complex64), P0s)
             r.iterate(alg, warm)
             stream.synchronize()
@@ -478,6 +493,8 @@ def main():
     f16_run = timed("lsqml", istore="f16")
     bf16_run = timed("lsqml", istore="bf16")
     poisson_run = timed("lsqml", likelihood="poisson")
+    sub_run = timed("lsqml", subpixel=SUBPIXEL)
+    sub_dm_run = timed("dm", subpixel=SUBPIXEL)
     prof_run = timed("lsqml", steps=3, warm=1, profile=True)
 
     def rate(run):
@@ -608,6 +625,9 @@ def main():
             "lsqml_f16": {"value": rate(f16_run), "fourier_error": f16_run["err"]},
             "lsqml_poisson_f32": {"value": rate(poisson_run), "fourier_error": poisson_run["err"]},
             "lsqml_bf16": {"value": rate(bf16_run), "fourier_error": bf16_run["err"]},
+            f"lsqml_subpixel{SUBPIXEL}_f32": {"value": rate(sub_run), "fourier_error": sub_run["err"],
+                                              "positions": "whole-pixel raster + uniform [0, 1) offsets"},
+            f"dm_subpixel{SUBPIXEL}_f32": {"value": rate(sub_dm_run), "fourier_error": sub_dm_run["err"]},
         },
         "batched": batched,
         "time_to_eps": t2e,

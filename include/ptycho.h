@@ -108,6 +108,25 @@ typedef struct {
                        eigenvector's largest entry real positive; DM's exit
                        waves are mixed with the same unitary.  0 (default):
                        modes are left as the updates make them.              */
+  int subpixel;     /* 0 (default): positions rounded half-to-even to whole
+                       pixels.  S = 2, 4, 8 or 16: positions quantised to 1/S
+                       pixel, q = rint(S y); corner p = floor((q + S/2) / S);
+                       the probe seen at the position is the probe translated
+                       by delta = q/S - p in [-1/2, 1/2) with the Fourier shift
+                       theorem, F(T P)(f) = F(P)(f) exp(-2 pi i f . delta),
+                       f = k/M, k >= M/2 taken as k - M.  (The script
+                       example of Sec. 3.2 scans in 50 nm steps at a
+                       2.8 nm pixel: 17.76 pixels.)  The
+                       probe sums take the adjoint shift.  LSQML scales its
+                       probe direction by the unshifted den_P = sum |O_j|^2;
+                       DM's probe update solves its normal equations
+                       sum_j T_j^H |O_j|^2 T_j P + d P = rhs by 4
+                       preconditioned conjugate-gradient iterations from the
+                       current probe (the diagonal form makes the difference
+                       map diverge).  DM and LSQML (and the Fourier error /
+                       simulation / residual calls); ePIE returns
+                       PTYCHO_ERR_UNSUPPORTED.  Device memory: three tables
+                       of S^2 K M^2 complex values and S^2 M^2 floats.       */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */
@@ -208,7 +227,8 @@ int ptycho_get_exit_waves(ptycho_ctx* ctx, float* out, int on_device);
 /* Iterations run so far (the counter t). */
 long long ptycho_iteration(const ptycho_ctx* ctx);
 
-/* Checkpoint / resume (SURVEY-listed DM state checkpointing): a run is
+/* Checkpoint / resume (for runs longer than one session; the DM state
+ * included): a run is
  * resumed bit for bit from (object, probe, iteration index) -- plus, for DM,
  * the exit waves of ptycho_get_exit_waves.
  * ptycho_set_iteration: the index t of the next iteration (>= 0; sets the
@@ -218,6 +238,26 @@ long long ptycho_iteration(const ptycho_ctx* ctx);
  *   continue from it instead of P_k O_j.  Errors: PTYCHO_ERR_* codes. */
 int ptycho_set_iteration(ptycho_ctx* ctx, long long t);
 int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* psi, int on_device);
+
+/* Position refinement (sub-pixel contexts; the position-correction step of
+ * the LSQML method of Odstrcil et al. 2018, cited in Sec. 1).  One call takes
+ * a fresh Fourier residual chi at the current (O, P) and positions (under the
+ * context's likelihood), and for every position the shift s = (s_y, s_x)
+ * minimising ||chi_j - s_y a_y - s_x a_x||^2 + lam |s|^2 over modes and
+ * pixels, a_y = P_jk dO_j/dy, a_x = P_jk dO_j/dx (P_j the shifted probe the
+ * position sees, dO central differences of the object with indices past the
+ * edge clamped; lam = 1e-6 (A11 + A22) / 2, FP64 solve).  Each position moves
+ * by step * clamp(s, -max_shift, max_shift) pixels (float32) and is
+ * re-quantised.  The residual pass overwrites the DM exit-wave state: a DM
+ * iteration after this call restarts from psi = P_j O_j.
+ * Errors: PTYCHO_ERR_UNSUPPORTED (subpixel = 0), PTYCHO_ERR_STATE (no data),
+ * PTYCHO_ERR_ARG (non-finite step, negative max_shift), PTYCHO_ERR_BOUNDS (a
+ * moved patch would leave the object: no position changes). */
+int ptycho_refine_positions(ptycho_ctx* ctx, double step, double max_shift);
+
+/* The current positions [J][2] (y, x) in float32 pixels: as last set, or as
+ * moved by ptycho_refine_positions.  Host memory. */
+int ptycho_get_positions(ptycho_ctx* ctx, float* out);
 
 /* Number of this library's kernel launches issued so far on the context. */
 long long ptycho_launch_count(const ptycho_ctx* ctx);

@@ -510,6 +510,60 @@ def lsqml_iteration(O, P, pos, I, t, reg=1e-3, beta=0.9, probe_start=0, return_s
 
 
 # ---------------------------------------------------------------------------
+# Position refinement (sub-pixel positions; the position-correction step of
+# Odstrcil et al. 2018, cited for LSQML in Sec. 1)
+# ---------------------------------------------------------------------------
+
+def object_gradient(O: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Central differences (d/dy, d/dx) of the object,
+    (O(y + 1, x) - O(y - 1, x)) / 2 and likewise in x, an index past the edge
+    taken as the edge pixel."""
+    Op = np.pad(O, 1, mode="edge")
+    return (Op[2:, 1:-1] - Op[:-2, 1:-1]) / 2.0, (Op[1:-1, 2:] - Op[1:-1, :-2]) / 2.0
+
+
+def position_correction(O, P, pos, delta, chi):
+    """Per-position shift (dy, dx) that best explains the exit-wave residual.
+    The exit wave of the probe at r is P(u) O(r + u) in its own window; moving
+    r by s changes it by s_y a_y + s_x a_x to first order with
+    a_y = P_jk d_yO_j (the illuminated object's gradient, central differences:
+    :func:`object_gradient`; P_j the probe position j sees).  (In the window
+    of the integer corner the same move also translates the whole exit wave,
+    which changes no far-field modulus and so cannot be fitted.)  s minimises
+    ||chi_j - s_y a_y - s_x a_x||^2 over all modes and pixels; the 2x2 normal
+    equations are solved as the LSQML step sizes are (:func:`lsqml_solve_2x2`,
+    FP64).  Returns [J, 2]."""
+    M = P.shape[-1]
+    gy, gx = object_gradient(O)
+    Gy, Gx = gather(gy, pos, M), gather(gx, pos, M)
+    Pj = position_probes(P, delta)
+    out = np.empty((len(pos), 2))
+    for j in range(len(pos)):
+        Pk = Pj[0 if delta is None else j]
+        ay = Pk * Gy[j][None]
+        ax = Pk * Gx[j][None]
+        A11 = float(np.sum(np.abs(ay) ** 2))
+        A12 = float(np.real(np.sum(np.conj(ay) * ax)))
+        A22 = float(np.sum(np.abs(ax) ** 2))
+        r1 = float(np.real(np.sum(np.conj(ay) * chi[j])))
+        r2 = float(np.real(np.sum(np.conj(ax) * chi[j])))
+        out[j] = lsqml_solve_2x2(A11, A12, A22, r1, r2)
+    return out
+
+
+def refine_positions(O, P, positions, I, S, step=1.0, max_shift=0.5, likelihood="amplitude"):
+    """One position-refinement step at the current (O, P): the residual chi of
+    a fresh Fourier pass (:func:`fourier_residual`) at the positions quantised
+    to 1/S pixel, the correction of :func:`position_correction`, each
+    component clipped to [-max_shift, max_shift] pixels and scaled by step.
+    Returns the new (unquantised) positions."""
+    pos, delta = subpixel_positions(positions, S)
+    chi = fourier_residual(O, P, pos, I, likelihood, delta)
+    d = position_correction(O, P, pos, delta, chi)
+    return np.asarray(positions, dtype=np.float64) + step * np.clip(d, -max_shift, max_shift)
+
+
+# ---------------------------------------------------------------------------
 # Detector preprocessing (Sec. 2.2: centre, crop size, saturation bit depth,
 # noise threshold and rotation of the diffraction patterns)
 # ---------------------------------------------------------------------------

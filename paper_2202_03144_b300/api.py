@@ -40,7 +40,7 @@ class Params(C.Structure):
         ("istore", C.c_int), ("probe_start", C.c_int),
         ("epie_alpha", C.c_double), ("epie_beta", C.c_double), ("lsqml_beta", C.c_double),
         ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
-        ("likelihood", C.c_int), ("probe_ortho", C.c_int),
+        ("likelihood", C.c_int), ("probe_ortho", C.c_int), ("subpixel", C.c_int),
     ]
 
 
@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
             "ptycho_epie_cluster_size": (i, [vp]),
             "ptycho_set_data_raw": (i, [vp, vp, C.POINTER(Preprocess), vp, i]),
             "ptycho_set_exit_waves": (i, [vp, vp, i]),
+            "ptycho_refine_positions": (i, [vp, d, d]),
+            "ptycho_get_positions": (i, [vp, f]),
             "ptycho_batch_create": (i, [C.POINTER(vp), i, C.POINTER(Params), vp]),
             "ptycho_batch_member": (vp, [vp, i]),
             "ptycho_batch_size": (i, [vp]),
@@ -406,6 +408,18 @@ class Reconstruction:
 
     def fourier_error(self):
         return fourier_error(self.ctx)
+
+    def refine_positions(self, step=1.0, max_shift=0.5):
+        """One position-correction step (sub-pixel contexts): every position
+        moves by step * clamp(s, +-max_shift) px, s the shift that best
+        explains the current Fourier residual (see ptycho_refine_positions)."""
+        _check(self.ctx, lib().ptycho_refine_positions(self.ctx, float(step), float(max_shift)))
+
+    def get_positions(self):
+        """Current positions [J, 2] (y, x), float32."""
+        out = np.empty((self.J, 2), np.float32)
+        _check(self.ctx, lib().ptycho_get_positions(self.ctx, out.ctypes.data))
+        return out
 
     def simulate(self, out=None):
         return simulate(self.ctx, (self.J, self.M, self.M), out)

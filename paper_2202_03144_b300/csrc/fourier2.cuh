@@ -135,7 +135,8 @@ __device__ __forceinline__ bool mbar_wait0(uint64_t* bar) {
 struct Fourier2Args {
   const float2* O;
   int nx;
-  const float2* P;
+  const float2* P;        // probe [K][M][M], or the shifted table [bins][K][M][M]
+  const unsigned short* pbin;  // sub-pixel bin of each position, or NULL
   const int2* pos;
   float2* X;
   const void* amp;
@@ -194,6 +195,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
   const int tid = threadIdx.x;
   const int c = (C > 1) ? (int)(blockIdx.x % C) : 0;
   const int j = a.j0 + (int)(blockIdx.x / C);
+  // probe of this position (sub-pixel: its bin of the shifted-probe table)
+  const float2* Pj = a.pbin ? a.P + (size_t)__ldg(a.pbin + j) * (K * M * M) : a.P;
   const int mode = MODE_T >= 0 ? MODE_T : a.mode;
   const int istore = IST_T >= 0 ? IST_T : a.istore;
   const int2 p = a.pos[j];
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
     // probe values first, then the object in groups of four: bounds the number
     // of loads in flight per thread (and so the registers they occupy)
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(a.P + ((size_t)k * M + n1 * R2 + n2) * M + col);
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
     const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
 #pragma unroll
     for (int g0 = 0; g0 < R1; g0 += 4) {
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
         a.X[xi] = v[n1];
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-        const float2 pr = __ldg(a.P + ((size_t)k * M + row) * M + col);
+        const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);
         a.X[xi] = cadd(cmul(pr, o), v[n1]);
       }
     }

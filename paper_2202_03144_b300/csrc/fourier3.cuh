@@ -110,6 +110,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
   const int tid = threadIdx.x;
   const int c = (int)(blockIdx.x % C);
   const int j = a.j0 + (int)(blockIdx.x / C);
+  // probe of this position (sub-pixel: its bin of the shifted-probe table)
+  const float2* Pj = a.pbin ? a.P + (size_t)__ldg(a.pbin + j) * (K * M * M) : a.P;
   const int mode = MODE_T >= 0 ? MODE_T : a.mode;
   const int istore = IST_T >= 0 ? IST_T : a.istore;
   const int2 p = a.pos[j];
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     const int colL = tid % W, n2 = (tid / W) % R2, k = tid / (W * R2);
     const int col = c * W + colL;
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(a.P + ((size_t)k * M + n1 * R2 + n2) * M + col);
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
     const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
 #pragma unroll
     for (int g0 = 0; g0 < R1; g0 += F3_OG) {
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
         a.X[xi] = v[n1];
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-        const float2 pr = __ldg(a.P + ((size_t)k * M + row) * M + col);
+        const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);
         a.X[xi] = cadd(cmul(pr, o), v[n1]);
       }
     }

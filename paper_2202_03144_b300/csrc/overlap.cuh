@@ -13,6 +13,11 @@
 // |O_j(u)|^2.  The positions are cut into G contiguous groups; CTA (block,
 // group) sums its group for 256 probe pixels, and a second kernel adds the G
 // partials in a fixed order.
+//
+// Sub-pixel positions: P is a table of shifted probes, [bins][K][M][M], and
+// position j reads bin pbin[j]; on the probe side the positions are taken in
+// bin order and the groups never straddle a bin, so the fixed-order sum
+// yields one numerator per bin (the caller then applies the adjoint shifts).
 #pragma once
 #include "common.cuh"
 
@@ -52,7 +57,8 @@ struct ObjArgs {
   float2* O;              // object (DM, UPD: in/out)
   float2* dO;             // DIR: output direction
   int ny, nx, ntx;        // object size, tiles per row
-  const float2* P;        // probe [K][M][M]
+  const float2* P;        // probe [K][M][M], or the shifted table [bins][K][M][M]
+  const unsigned short* pbin;  // sub-pixel bin of each position, or NULL
   const float2* X;        // psi or chi [J][K][M][M]
   const int2* pos;
   const int* tile_ptr;    // [n_tiles + 1]
@@ -65,7 +71,8 @@ struct ObjArgs {
   int M;
 };
 
-template <int K, int MODE>
+// SUB: sub-pixel positions (P is the shifted table, indexed by pbin).
+template <int K, int MODE, bool SUB>
 __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArgs a) {  // K > 1: 3 (no spills)
   __shared__ float red[32];
   const int tile = blockIdx.x;
@@ -89,6 +96,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
   __shared__ int sj[OBJ_CHUNK];
   __shared__ int2 sp[OBJ_CHUNK];
   __shared__ float sw[OBJ_CHUNK];
+  __shared__ int sb[SUB ? OBJ_CHUNK : 1];
   const bool weighted = MODE == OBJ_UPD && a.weights != nullptr;
   for (int c0 = s0; c0 < s1; c0 += OBJ_CHUNK) {
     const int nc = min(OBJ_CHUNK, s1 - c0);
@@ -98,12 +106,14 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
       sj[i] = j;
       sp[i] = a.pos[j];
       sw[i] = weighted ? a.weights[j] : 1.f;
+      if (SUB) sb[i] = a.pbin[j];
     }
     __syncthreads();
     for (int s = 0; s < nc; ++s) {
       const int j = sj[s];
       const int2 p = sp[s];
       const float w = sw[s];
+      const float2* Pj = SUB ? a.P + (size_t)sb[s] * K * MM : a.P;
       const int ux = x - p.y;                 // patch column of this thread's first pixel
       const bool pairs = ((ux & 1) == 0);     // uniform over the CTA (x is even)
       // one mode at a time (the per-pixel order of the sums is unchanged)
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
           const int uy = ty0 + ry + OBJ_RSTEP * i - p.x;
           const bool row_in = uy >= 0 && uy < M;
           const size_t u0 = (size_t)(row_in ? uy : 0) * M;
-          const float2* prow = a.P + k * MM + u0;
+          const float2* prow = Pj + k * MM + u0;
           const float2* xrow = a.X + ((size_t)j * K + k) * MM + u0;
           if (pairs) {
 #pragma unroll
@@ -222,24 +232,31 @@ struct ProbeArgs {
   const float2* X;         // [J][K][M][M]
   const int2* pos;
   const float* weights;    // alpha_P or NULL
+  const int* order;        // positions in group order (sub-pixel: by bin), or NULL = 0..J-1
+  const int* goff;         // [G + 1] group offsets into the order, or NULL = even split of J
+  const int* bgrp;         // [bins + 1] first group of each bin (sub-pixel), or NULL
+  int nbins;
   int J, M, G;
   float2* part_num;        // [G][K][M*M]
   float* part_den;         // [G][M*M] or NULL (skip den)
-  float2* num;             // [K][M*M]
+  float2* num;             // [K][M*M] (sub-pixel: [bins][K][M*M])
   float* den;              // [M*M]
+  float* bin_den;          // sub-pixel: per-bin den [bins][M*M], or NULL
   float* blk_max;          // [ceil(M*M/256)]
   float2* P;               // PR_DM, PR_UPD: in/out
   float2* dP;              // PR_DIR: out
   float reg, beta;
 };
 
-template <int K>
+// SUB: positions taken through the bin order and its group offsets.
+template <int K, bool SUB>
 __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   const int MM = a.M * a.M;
   const int u = blockIdx.x * PROBE_NT + threadIdx.x;
   const int uy = u / a.M, ux = u % a.M;
   const int g = blockIdx.y;
-  const int jb = (int)(((long long)a.J * g) / a.G), je = (int)(((long long)a.J * (g + 1)) / a.G);
+  const int jb = SUB ? a.goff[g] : (int)(((long long)a.J * g) / a.G);
+  const int je = SUB ? a.goff[g + 1] : (int)(((long long)a.J * (g + 1)) / a.G);
   float2 num[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) num[k] = make_float2(0.f, 0.f);
@@ -248,12 +265,15 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   constexpr int UJ = 4;  // positions per step: UJ*(K+1) independent loads in flight
   __shared__ int2 sp[PROBE_CHUNK];
   __shared__ float sw[PROBE_CHUNK];
+  __shared__ int sj[SUB ? PROBE_CHUNK : 1];
   for (int c0 = jb; c0 < je; c0 += PROBE_CHUNK) {
     const int nc = min(PROBE_CHUNK, je - c0);
     __syncthreads();
     for (int i = threadIdx.x; i < nc; i += PROBE_NT) {
-      sp[i] = a.pos[c0 + i];
-      sw[i] = a.weights ? a.weights[c0 + i] : 1.f;
+      const int j = SUB ? a.order[c0 + i] : c0 + i;
+      if (SUB) sj[i] = j;
+      sp[i] = a.pos[j];
+      sw[i] = a.weights ? a.weights[j] : 1.f;
     }
     __syncthreads();
     if (u < MM) {
@@ -269,7 +289,7 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
           w[h] = in ? sw[i] : 0.f;
 #pragma unroll
           for (int k = 0; k < K; ++k)
-            xv[h][k] = in ? __ldcs(a.X + ((size_t)(c0 + i) * K + k) * MM + u) : make_float2(0.f, 0.f);
+            xv[h][k] = in ? __ldcs(a.X + ((size_t)(SUB ? sj[i] : c0 + i) * K + k) * MM + u) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int h = 0; h < UJ; ++h) {
@@ -290,7 +310,8 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   if (want_den) a.part_den[(size_t)g * MM + u] = den;
 }
 
-// Sum the G partials in group order; block maxima of den for the regulariser.
+// Sum the G partials in group order (sub-pixel: per bin, into num[bin]);
+// block maxima of den for the regulariser.
 template <int K>
 __global__ void __launch_bounds__(PROBE_NT) k_probe_sum(ProbeArgs a) {
   __shared__ float red[32];
@@ -299,17 +320,27 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_sum(ProbeArgs a) {
   const bool want_den = a.part_den != nullptr;
   float m = 0.f;
   if (u < MM) {
+    const int nb = a.bgrp ? a.nbins : 1;
+    for (int b = 0; b < nb; ++b) {
+      const int g0 = a.bgrp ? a.bgrp[b] : 0, g1 = a.bgrp ? a.bgrp[b + 1] : a.G;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float2 s = make_float2(0.f, 0.f);
-      for (int g = 0; g < a.G; ++g) s = cadd(s, a.part_num[((size_t)g * K + k) * MM + u]);
-      a.num[(size_t)k * MM + u] = s;
+      for (int k = 0; k < K; ++k) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int g = g0; g < g1; ++g) s = cadd(s, a.part_num[((size_t)g * K + k) * MM + u]);
+        a.num[((size_t)b * K + k) * MM + u] = s;
+      }
     }
     if (want_den) {
       float d = 0.f;
       for (int g = 0; g < a.G; ++g) d += a.part_den[(size_t)g * MM + u];
       a.den[u] = d;
       m = d;
+      if (a.bgrp && a.bin_den)
+        for (int b = 0; b < a.nbins; ++b) {
+          float db = 0.f;
+          for (int g = a.bgrp[b]; g < a.bgrp[b + 1]; ++g) db += a.part_den[(size_t)g * MM + u];
+          a.bin_den[(size_t)b * MM + u] = db;
+        }
     }
   }
   if (want_den) {
@@ -361,8 +392,9 @@ struct StepArgs {
   const float2* O;
   const float2* dO;
   int nx;
-  const float2* P;
-  const float2* dP;   // NULL when the probe is fixed
+  const float2* P;    // probe, or the shifted table [bins][K][M][M]
+  const float2* dP;   // NULL when the probe is fixed (sub-pixel: shifted table)
+  const unsigned short* pbin;  // sub-pixel bin of each position, or NULL
   const float2* X;    // chi
   const int2* pos;
   int M;
@@ -372,14 +404,17 @@ struct StepArgs {
 
 constexpr int STEP_NT = 256;
 
-template <int K>
-__global__ void __launch_bounds__(STEP_NT, PT_STEP_MINB) k_lsqml_steps(StepArgs a) {
+// SUB: sub-pixel positions (P and dP are shifted tables indexed by pbin); the
+// extra offset costs registers, so K = 3 then runs at three CTAs per SM.
+template <int K, bool SUB>
+__global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k_lsqml_steps(StepArgs a) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   const int2 p = a.pos[j];
   const int MM = a.M * a.M;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
   const bool upd = a.dP != nullptr;
+  const size_t boff = SUB ? (size_t)a.pbin[j] * K * MM : 0;  // sub-pixel: this position's table bin
   // two adjacent pixels per thread (16-byte loads of chi, P, dP; M is even so
   // both lie in one row); the pixel's row and column advance incrementally
   const int M = a.M;
@@ -405,9 +440,9 @@ __global__ void __launch_bounds__(STEP_NT, PT_STEP_MINB) k_lsqml_steps(StepArgs 
     float4 xv[K], pr[K], dp[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      pr[k] = __ldg(reinterpret_cast<const float4*>(a.P + (size_t)k * MM + u));
+      pr[k] = __ldg(reinterpret_cast<const float4*>(a.P + boff + (size_t)k * MM + u));
       xv[k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)j * K + k) * MM + u));
-      dp[k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + (size_t)k * MM + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      dp[k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + boff + (size_t)k * MM + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -453,6 +488,69 @@ __global__ void __launch_bounds__(STEP_NT, PT_STEP_MINB) k_lsqml_steps(StepArgs 
     }
     a.alpha_O[j] = (float)aO;
     a.alpha_P[j] = (float)aP;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Position correction (sub-pixel positions): per position the shift s that
+// best explains the residual, a_y = P_jk dO/dy, a_x = P_jk dO/dx (central
+// differences of the object, an index past the edge clamped to it), sums in
+// FP32 per thread and FP64 across the block, the regularised 2x2 system
+// solved in FP64 as for the LSQML step sizes.  out[j] = (s_y, s_x).
+// ---------------------------------------------------------------------------
+struct PosCorrArgs {
+  const float2* O;
+  int ny, nx;
+  const float2* P;             // shifted-probe table [bins][K][M][M]
+  const unsigned short* pbin;
+  const float2* X;             // chi
+  const int2* pos;
+  int M;
+  float2* out;
+};
+
+template <int K>
+__global__ void __launch_bounds__(STEP_NT) k_pos_corr(PosCorrArgs a) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  const int2 p = a.pos[j];
+  const int M = a.M, MM = M * M;
+  const float2* Pj = a.P + (size_t)a.pbin[j] * K * MM;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+  for (int u = threadIdx.x; u < MM; u += STEP_NT) {
+    const int y = p.x + u / M, x = p.y + u % M;
+    const int yp = min(y + 1, a.ny - 1), ym = max(y - 1, 0);
+    const int xp = min(x + 1, a.nx - 1), xm = max(x - 1, 0);
+    const float2 gy = cscale(csub(__ldg(a.O + (size_t)yp * a.nx + x), __ldg(a.O + (size_t)ym * a.nx + x)), 0.5f);
+    const float2 gx = cscale(csub(__ldg(a.O + (size_t)y * a.nx + xp), __ldg(a.O + (size_t)y * a.nx + xm)), 0.5f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 pk = __ldg(Pj + (size_t)k * MM + u);
+      const float2 xk = __ldcs(a.X + ((size_t)j * K + k) * MM + u);
+      const float2 ay = cmul(pk, gy), ax = cmul(pk, gx);
+      s0 += cabs2(ay);
+      s1 += fmaf(ay.x, ax.x, ay.y * ax.y);
+      s2 += cabs2(ax);
+      s3 += fmaf(ay.x, xk.x, ay.y * xk.y);
+      s4 += fmaf(ax.x, xk.x, ax.y * xk.y);
+    }
+  }
+  const double A11 = block_sum_d<STEP_NT>(s0, red);
+  const double A12 = block_sum_d<STEP_NT>(s1, red);
+  const double A22 = block_sum_d<STEP_NT>(s2, red);
+  const double r1 = block_sum_d<STEP_NT>(s3, red);
+  const double r2 = block_sum_d<STEP_NT>(s4, red);
+  if (threadIdx.x == 0) {
+    double sy = 0.0, sx = 0.0;
+    const double tr = A11 + A22;
+    if (tr > 0.0) {
+      const double lam = 1e-6 * tr / 2.0;
+      const double a11 = A11 + lam, a22 = A22 + lam;
+      const double det = a11 * a22 - A12 * A12;
+      sy = (a22 * r1 - A12 * r2) / det;
+      sx = (a11 * r2 - A12 * r1) / det;
+    }
+    a.out[j] = make_float2((float)sy, (float)sx);
   }
 }
 

@@ -28,6 +28,8 @@
 #include "modes.cuh"
 #include "net.cuh"
 #include "overlap.cuh"
+#include "shift.cuh"
+#include "probe_cg.cuh"
 
 using namespace ptycho;
 
@@ -263,7 +265,8 @@ __global__ void k_fill_c(float2* p, size_t n, float2 v) {
 
 // psi_{j,k} = P_k O_j (DM initial state)
 __global__ void k_exit_waves(const float2* __restrict__ O, int nx, const float2* __restrict__ P,
-                             const int2* __restrict__ pos, int J, int K, int M, float2* __restrict__ X) {
+                             const unsigned short* __restrict__ pbin, const int2* __restrict__ pos, int J, int K,
+                             int M, float2* __restrict__ X) {
   const size_t MM = (size_t)M * M;
   const size_t n = (size_t)J * K * MM;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -272,7 +275,8 @@ __global__ void k_exit_waves(const float2* __restrict__ O, int nx, const float2*
     const int j = (int)(i / (MM * K));
     const int2 p = pos[j];
     const int uy = (int)(u / M), ux = (int)(u % M);
-    X[i] = cmul(P[k * MM + u], O[(size_t)(p.x + uy) * nx + p.y + ux]);
+    const size_t b = pbin ? pbin[j] : 0;
+    X[i] = cmul(P[(b * K + k) * MM + u], O[(size_t)(p.x + uy) * nx + p.y + ux]);
   }
 }
 
@@ -318,7 +322,28 @@ struct ptycho_ctx {
   int* tile_ptr = nullptr;
   int* tile_list = nullptr;
   int n_tiles = 0, ntx = 0, nty = 0;
-  int G = 1;
+  int G = 1;                 // position groups of the probe sums
+  int G_cap = 1;             // capacity of the group partials
+  // sub-pixel positions (S = params.subpixel > 0): per-position bin of the
+  // shifted-probe table, the tables of P and dP, per-bin probe sums, the
+  // line-shift scratch, and the probe-sum groups in bin order
+  int S = 0;
+  int G_sub = 0;             // groups in bin order (sub-pixel)
+  unsigned short* pbin = nullptr;
+  float2* Pt = nullptr;
+  float2* dPt = nullptr;
+  float2* pbins = nullptr;
+  float2* stmp = nullptr;
+  int* porder = nullptr;
+  int* goff = nullptr;
+  int* bgrp = nullptr;
+  float* pbins_den = nullptr;  // per-bin den_P (the DM probe solve)
+  float2* cg_r = nullptr;      // DM probe solve: residual, direction, operator output
+  float2* cg_p = nullptr;
+  float2* cg_q = nullptr;
+  double* cg_part = nullptr;   // [3][blocks] inner-product partials
+  float2* pos_corr = nullptr;  // position refinement: per-position shift
+  std::vector<float> pos_f;    // positions as last set (or refined), [J][2]
   float2* ppart = nullptr;
   float* ppart_den = nullptr;
   float2* pnum = nullptr;
@@ -482,12 +507,21 @@ int collect_profile(ptycho_ctx* ctx) {
 size_t amp_bytes(const ptycho_ctx* ctx) { return ctx->p.istore == PTYCHO_I_F32 ? 4 : 2; }
 
 // ----------------------------------------------------------------- Fourier
+int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst);
+int refresh_probe_table(ptycho_ctx* ctx);
+const float2* probe_view(const ptycho_ctx* ctx);
+const unsigned short* bin_view(const ptycho_ctx* ctx);
+
+// Every Fourier pass reads the probe as it is now: with sub-pixel positions
+// the shifted table is rebuilt first.
 int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, int nj, const char* name) {
+  if (int r = refresh_probe_table(ctx)) return r;
   const KernelSet* ks = ctx->ks;
   Fourier2Args a{};
   a.O = ctx->O;
   a.nx = ctx->p.obj_nx;
-  a.P = ctx->P;
+  a.P = probe_view(ctx);
+  a.pbin = bin_view(ctx);
   a.pos = ctx->pos;
   a.X = X;
   a.amp = ctx->amp;
@@ -545,6 +579,47 @@ int check_device_flag(ptycho_ctx* ctx) {
   return 0;
 }
 
+// ------------------------------------------------------ sub-pixel shifts
+template <int M>
+int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) {
+  constexpr int LN = 8;
+  const int K = ctx->p.K, S = ctx->S;
+  const double tab = 8.0 * S * S * K * (double)M * M;
+  if (build) {
+    if (int r = launch(ctx, "shift_build", tab, [&] {
+          k_shift_build_rows<M, LN><<<dim3(K * M / LN, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw);
+          k_shift_build_cols<M, LN><<<dim3(M / LN, K, S * S), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw);
+        }))
+      return r;
+    return 0;
+  }
+  return launch(ctx, "shift_sum", tab, [&] {
+    k_shift_sum_cols<M, LN><<<dim3(M / LN, K, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->bgrp, ctx->tw);
+    k_shift_sum_rows<M, LN><<<dim3(K * M / LN), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw);
+  });
+}
+
+// build: dst[bin][k] = T_delta(bin) src[k];  sum: dst[k] = sum_bin T_-delta(bin) src[bin][k]
+int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) {
+  switch (ctx->p.M) {
+    case 16: return launch_shift_m<16>(ctx, build, src, dst);
+    case 32: return launch_shift_m<32>(ctx, build, src, dst);
+    case 64: return launch_shift_m<64>(ctx, build, src, dst);
+    case 96: return launch_shift_m<96>(ctx, build, src, dst);
+    case 128: return launch_shift_m<128>(ctx, build, src, dst);
+    case 192: return launch_shift_m<192>(ctx, build, src, dst);
+    case 256: return launch_shift_m<256>(ctx, build, src, dst);
+    default: return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "sub-pixel shifts are not compiled for M=%d", ctx->p.M);
+  }
+}
+
+// The shifted-probe table of the current probe (sub-pixel positions only).
+int refresh_probe_table(ptycho_ctx* ctx) {
+  return ctx->S ? launch_shift(ctx, true, ctx->P, ctx->Pt) : 0;
+}
+const float2* probe_view(const ptycho_ctx* ctx) { return ctx->S ? ctx->Pt : ctx->P; }
+const unsigned short* bin_view(const ptycho_ctx* ctx) { return ctx->S ? ctx->pbin : nullptr; }
+
 // ---------------------------------------------------------------- overlap
 // object-side modes of obj_step (OBJ_UPD is the LSQML update)
 constexpr int OBJ_STEP_DM = 100;   // DM overlap update of O
@@ -558,7 +633,8 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
   a.ny = ctx->p.obj_ny;
   a.nx = ctx->p.obj_nx;
   a.ntx = ctx->ntx;
-  a.P = ctx->P;
+  a.P = probe_view(ctx);
+  a.pbin = bin_view(ctx);
   a.X = X;
   a.pos = ctx->pos;
   a.tile_ptr = ctx->tile_ptr;
@@ -573,10 +649,17 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
   const double obj = (double)ctx->p.obj_ny * ctx->p.obj_nx;
   const double xb = 8.0 * ctx->p.J * K * (double)ctx->p.M * ctx->p.M;
   const dim3 g(ctx->n_tiles), b(OBJ_NT);
+  const bool sub = ctx->S != 0;
   if (mode == OBJ_UPD)
-    return launch(ctx, "obj_update", xb + obj * 20.0, [&] { k_obj<K, OBJ_UPD><<<g, b, 0, ctx->st>>>(a); });
+    return launch(ctx, "obj_update", xb + obj * 20.0, [&] {
+      if (sub) k_obj<K, OBJ_UPD, true><<<g, b, 0, ctx->st>>>(a);
+      else k_obj<K, OBJ_UPD, false><<<g, b, 0, ctx->st>>>(a);
+    });
   // numerator + den_O in one pass, then the max of den_O, then the epilogue
-  if (int r = launch(ctx, "obj_sums", xb + obj * 12.0, [&] { k_obj<K, OBJ_NUMDEN><<<g, b, 0, ctx->st>>>(a); }))
+  if (int r = launch(ctx, "obj_sums", xb + obj * 12.0, [&] {
+        if (sub) k_obj<K, OBJ_NUMDEN, true><<<g, b, 0, ctx->st>>>(a);
+        else k_obj<K, OBJ_NUMDEN, false><<<g, b, 0, ctx->st>>>(a);
+      }))
     return r;
   if (int r = launch(ctx, "reduce_max", 0.0,
                      [&] { k_reduce_max<<<1, 1024, 0, ctx->st>>>(ctx->tile_max, ctx->n_tiles, ctx->denO_max); }))
@@ -600,6 +683,55 @@ int obj_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
 }
 
 
+// Sub-pixel DM probe update: DM_PROBE_CG iterations of preconditioned
+// conjugate gradients on the probe's normal equations (probe_cg.cuh), from
+// the current probe; pnum, pden, pbins_den and pblk_max come from the probe
+// sums of this iteration.
+constexpr int DM_PROBE_CG = 4;
+
+// q = B v = sum_b T_-delta(b)[Dbar_b T_delta(b) v]
+int probe_normal_op(ptycho_ctx* ctx, const float2* v, float2* q) {
+  if (int r = launch_shift(ctx, true, v, ctx->dPt)) return r;
+  const int nb = ctx->S * ctx->S, K = ctx->p.K, MM = ctx->p.M * ctx->p.M;
+  if (int r = launch(ctx, "bin_scale", 0.0, [&] {
+        k_bin_scale<<<1184, 256, 0, ctx->st>>>(ctx->dPt, ctx->pbins_den, nb, K, MM);
+      }))
+    return r;
+  return launch_shift(ctx, false, ctx->dPt, q);
+}
+
+int dm_probe_cg(ptycho_ctx* ctx) {
+  const int K = ctx->p.K, MM = ctx->p.M * ctx->p.M;
+  CgArgs a{};
+  a.X = ctx->P;
+  a.r = ctx->cg_r;
+  a.p = ctx->cg_p;
+  a.q = ctx->cg_q;
+  a.num = ctx->pnum;
+  a.den = ctx->pden;
+  a.blk_max = ctx->pblk_max;
+  a.nblk_den = (MM + PROBE_NT - 1) / PROBE_NT;
+  a.reg = (float)ctx->p.reg;
+  a.K = K;
+  a.MM = MM;
+  a.nb = (K * MM + CG_NT - 1) / CG_NT;
+  a.part_rz = ctx->cg_part;
+  a.part_pq = ctx->cg_part + 2 * (size_t)a.nb;
+  if (int r = probe_normal_op(ctx, ctx->P, ctx->cg_q)) return r;
+  if (int r = launch(ctx, "probe_cg", 0.0, [&] { k_cg_start<<<a.nb, CG_NT, 0, ctx->st>>>(a); })) return r;
+  for (int it = 0; it < DM_PROBE_CG; ++it) {
+    a.it = it;
+    if (int r = probe_normal_op(ctx, ctx->cg_p, ctx->cg_q)) return r;
+    if (int r = launch(ctx, "probe_cg", 0.0, [&] {
+          k_cg_pq<<<a.nb, CG_NT, 0, ctx->st>>>(a);
+          k_cg_step<<<a.nb, CG_NT, 0, ctx->st>>>(a);
+          k_cg_dir<<<a.nb, CG_NT, 0, ctx->st>>>(a);
+        }))
+      return r;
+  }
+  return 0;
+}
+
 // probe: partial sums over position groups, fixed-order sum, apply.
 template <int K>
 int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, bool want_den, bool apply) {
@@ -611,7 +743,13 @@ int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, boo
   a.weights = w;
   a.J = ctx->p.J;
   a.M = ctx->p.M;
-  a.G = ctx->G;
+  a.G = ctx->S ? ctx->G_sub : ctx->G;
+  if (ctx->S) {  // groups in bin order, one numerator per bin
+    a.order = ctx->porder;
+    a.goff = ctx->goff;
+    a.bgrp = ctx->bgrp;
+    a.nbins = ctx->S * ctx->S;
+  }
   a.part_num = ctx->ppart;
   a.part_den = want_den ? ctx->ppart_den : nullptr;
   a.num = ctx->pnum;
@@ -626,12 +764,19 @@ int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, boo
   const double xb = 8.0 * ctx->p.J * K * (double)MM;
   if (X) {
     if (int r = launch(ctx, "probe_partial", xb, [&] {
-          k_probe_partial<K><<<dim3(nblk, ctx->G), PROBE_NT, 0, ctx->st>>>(a);
+          if (ctx->S) k_probe_partial<K, true><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+          else k_probe_partial<K, false><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
         }))
       return r;
-    if (int r = launch(ctx, "probe_sum", 0.0, [&] { k_probe_sum<K><<<nblk, PROBE_NT, 0, ctx->st>>>(a); })) return r;
+    ProbeArgs s = a;
+    if (ctx->S) s.num = ctx->pbins;
+    if (ctx->S && mode == PR_DM && want_den) s.bin_den = ctx->pbins_den;
+    if (int r = launch(ctx, "probe_sum", 0.0, [&] { k_probe_sum<K><<<nblk, PROBE_NT, 0, ctx->st>>>(s); })) return r;
+    if (ctx->S)  // adjoint shifts of the per-bin numerators, summed
+      if (int r = launch_shift(ctx, false, ctx->pbins, ctx->pnum)) return r;
   }
   if (!apply) return 0;
+  if (ctx->S && mode == PR_DM) return dm_probe_cg(ctx);
   switch (mode) {
     case PR_DM: return launch(ctx, "probe_apply", 0.0, [&] { k_probe_apply<K, PR_DM><<<nblk, PROBE_NT, 0, ctx->st>>>(a); });
     case PR_DIR: return launch(ctx, "probe_apply", 0.0, [&] { k_probe_apply<K, PR_DIR><<<nblk, PROBE_NT, 0, ctx->st>>>(a); });
@@ -648,12 +793,15 @@ int probe_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w, bool 
 }
 
 int steps_step(ptycho_ctx* ctx, bool upd) {
+  if (upd && ctx->S)  // the probe direction as each position sees it
+    if (int r = launch_shift(ctx, true, ctx->dP, ctx->dPt)) return r;
   StepArgs a{};
   a.O = ctx->O;
   a.dO = ctx->dO;
   a.nx = ctx->p.obj_nx;
-  a.P = ctx->P;
-  a.dP = upd ? ctx->dP : nullptr;
+  a.P = probe_view(ctx);
+  a.dP = upd ? (ctx->S ? ctx->dPt : ctx->dP) : nullptr;
+  a.pbin = bin_view(ctx);
   a.X = ctx->X;
   a.pos = ctx->pos;
   a.M = ctx->p.M;
@@ -661,10 +809,20 @@ int steps_step(ptycho_ctx* ctx, bool upd) {
   a.alpha_P = ctx->alphaP;
   const double xb = 8.0 * ctx->p.J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
   const int J = ctx->p.J;
+  const bool sub = ctx->S != 0;
   switch (ctx->p.K) {
-    case 1: return launch(ctx, "lsqml_steps", xb, [&] { k_lsqml_steps<1><<<J, STEP_NT, 0, ctx->st>>>(a); });
-    case 2: return launch(ctx, "lsqml_steps", xb, [&] { k_lsqml_steps<2><<<J, STEP_NT, 0, ctx->st>>>(a); });
-    default: return launch(ctx, "lsqml_steps", xb, [&] { k_lsqml_steps<3><<<J, STEP_NT, 0, ctx->st>>>(a); });
+    case 1: return launch(ctx, "lsqml_steps", xb, [&] {
+        if (sub) k_lsqml_steps<1, true><<<J, STEP_NT, 0, ctx->st>>>(a);
+        else k_lsqml_steps<1, false><<<J, STEP_NT, 0, ctx->st>>>(a);
+      });
+    case 2: return launch(ctx, "lsqml_steps", xb, [&] {
+        if (sub) k_lsqml_steps<2, true><<<J, STEP_NT, 0, ctx->st>>>(a);
+        else k_lsqml_steps<2, false><<<J, STEP_NT, 0, ctx->st>>>(a);
+      });
+    default: return launch(ctx, "lsqml_steps", xb, [&] {
+        if (sub) k_lsqml_steps<3, true><<<J, STEP_NT, 0, ctx->st>>>(a);
+        else k_lsqml_steps<3, false><<<J, STEP_NT, 0, ctx->st>>>(a);
+      });
   }
 }
 
@@ -674,8 +832,8 @@ int ensure_work_buffers(ptycho_ctx* ctx) {
   if (int r = dalloc(ctx, &ctx->X, (size_t)ctx->p.J * K * MM)) return r;
   if (int r = dalloc(ctx, &ctx->dO, (size_t)ctx->p.obj_ny * ctx->p.obj_nx)) return r;
   if (int r = dalloc(ctx, &ctx->dP, K * MM)) return r;
-  if (int r = dalloc(ctx, &ctx->ppart, (size_t)ctx->G * K * MM)) return r;
-  if (int r = dalloc(ctx, &ctx->ppart_den, (size_t)ctx->G * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->ppart, (size_t)ctx->G_cap * K * MM)) return r;
+  if (int r = dalloc(ctx, &ctx->ppart_den, (size_t)ctx->G_cap * MM)) return r;
   if (int r = dalloc(ctx, &ctx->pnum, K * MM)) return r;
   if (int r = dalloc(ctx, &ctx->pden, MM)) return r;
   if (int r = dalloc(ctx, &ctx->pblk_max, (MM + PROBE_NT - 1) / PROBE_NT)) return r;
@@ -695,8 +853,10 @@ int dm_prepare(ptycho_ctx* ctx) {
   const int J = ctx->p.J, K = ctx->p.K, M = ctx->p.M;
   if (!ctx->psi_valid) {
     const size_t n_el = (size_t)J * K * M * M;
+    if (int r = refresh_probe_table(ctx)) return r;
     if (int r = launch(ctx, "exit_waves", 8.0 * n_el, [&] {
-          k_exit_waves<<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->P, ctx->pos, J, K, M, ctx->X);
+          k_exit_waves<<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, probe_view(ctx), bin_view(ctx), ctx->pos, J,
+                                                   K, M, ctx->X);
         }))
       return r;
     ctx->psi_valid = true;
@@ -722,6 +882,7 @@ int ortho_step(ptycho_ctx* ctx, bool mix_psi) {
 }
 
 int dm_step(ptycho_ctx* ctx, bool upd) {
+  if (int r = refresh_probe_table(ctx)) return r;  // the probe may have changed since the last Fourier pass
   if (int r = obj_step(ctx, OBJ_STEP_DM, ctx->X, nullptr)) return r;
   if (upd)
     if (int r = probe_step(ctx, PR_DM, ctx->X, nullptr, true, true)) return r;
@@ -777,6 +938,8 @@ int run_lsqml(ptycho_ctx* ctx, int n) {
 }
 
 int run_epie(ptycho_ctx* ctx, int n) {
+  if (ctx->S)
+    return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE takes integer positions (create with subpixel = 0)");
   if (!ctx->epie_ok)
     return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE kernel for M=%d K=%d cluster=%d exceeds shared memory; use a larger cluster",
                 ctx->p.M, ctx->p.K, ctx->eks ? ctx->eks->C : ctx->C);
@@ -881,18 +1044,83 @@ int run_epie(ptycho_ctx* ctx, int n) {
   return 0;
 }
 
+// Sub-pixel positions: the probe-sum groups in bin order.  Bin b's n_b
+// positions (ascending index) are cut into max(1, ceil(n_b G / J)) groups, so
+// there are at most G + S^2 of them; empty bins get none.
+int build_subpixel_groups(ptycho_ctx* ctx, const std::vector<unsigned short>& bin) {
+  const int J = ctx->p.J, nb = ctx->S * ctx->S;
+  std::vector<int> start(nb + 1, 0);
+  for (int j = 0; j < J; ++j) start[bin[j] + 1]++;
+  for (int b = 0; b < nb; ++b) start[b + 1] += start[b];
+  std::vector<int> order(J), fill(start.begin(), start.end() - 1);
+  for (int j = 0; j < J; ++j) order[fill[bin[j]]++] = j;
+  std::vector<int> goff, bgrp(nb + 1);
+  for (int b = 0; b < nb; ++b) {
+    bgrp[b] = (int)goff.size();
+    const int n = start[b + 1] - start[b];
+    if (n == 0) continue;
+    int g = (int)(((long long)n * ctx->G + J - 1) / J);
+    g = std::max(1, std::min(g, n));
+    for (int i = 0; i < g; ++i) goff.push_back(start[b] + (int)((long long)n * i / g));
+  }
+  bgrp[nb] = (int)goff.size();
+  goff.push_back(J);
+  const int G = (int)goff.size() - 1;
+  if (G > ctx->G_cap) return fail(ctx, PTYCHO_ERR_ARG, "internal: %d probe-sum groups exceed %d", G, ctx->G_cap);
+  CK(cudaMemcpy(ctx->porder, order.data(), J * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->bgrp, bgrp.data(), bgrp.size() * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->G_sub = G;
+  return 0;
+}
+
 int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
   if (!positions) return fail(ctx, PTYCHO_ERR_ARG, "positions is NULL");
-  const int J = ctx->p.J, M = ctx->p.M, ny = ctx->p.obj_ny, nx = ctx->p.obj_nx;
+  const int J = ctx->p.J, M = ctx->p.M, ny = ctx->p.obj_ny, nx = ctx->p.obj_nx, S = ctx->S;
   std::vector<int2> pos(J);
+  std::vector<unsigned short> bin(S ? J : 0);
   for (int j = 0; j < J; ++j) {
     const float fy = positions[2 * j], fx = positions[2 * j + 1];
     if (!std::isfinite(fy) || !std::isfinite(fx))
       return fail(ctx, PTYCHO_ERR_NONFINITE, "position %d is not finite", j);
-    const double y = std::nearbyint((double)fy), x = std::nearbyint((double)fx);
+    double y, x;
+    if (S) {
+      // quantised to 1/S pixel (half to even), corner floor((q + S/2) / S),
+      // shift bin q - S corner + S/2 in [0, S)
+      const double qy = std::nearbyint((double)S * fy), qx = std::nearbyint((double)S * fx);
+      y = std::floor((qy + S / 2) / S);
+      x = std::floor((qx + S / 2) / S);
+      if (std::fabs(qy) > 1e9 || std::fabs(qx) > 1e9)
+        return fail(ctx, PTYCHO_ERR_BOUNDS, "position %d is far outside the object", j);
+      const int by = (int)(qy - S * y) + S / 2, bx = (int)(qx - S * x) + S / 2;
+      bin[j] = (unsigned short)(by * S + bx);
+    } else {
+      y = std::nearbyint((double)fy);
+      x = std::nearbyint((double)fx);
+    }
     if (y < 0 || x < 0 || y + M > ny || x + M > nx)
       return fail(ctx, PTYCHO_ERR_BOUNDS, "patch %d at (%g, %g) falls outside the %dx%d object", j, y, x, ny, nx);
     pos[j] = make_int2((int)y, (int)x);
+  }
+  if (S) {
+    const size_t tab = (size_t)S * S * ctx->p.K * M * M;
+    if (int r = dalloc(ctx, &ctx->pbin, (size_t)J)) return r;
+    if (int r = dalloc(ctx, &ctx->Pt, tab)) return r;
+    if (int r = dalloc(ctx, &ctx->dPt, tab)) return r;
+    if (int r = dalloc(ctx, &ctx->pbins, tab)) return r;
+    if (int r = dalloc(ctx, &ctx->stmp, (size_t)S * ctx->p.K * M * M)) return r;
+    if (int r = dalloc(ctx, &ctx->porder, (size_t)J)) return r;
+    if (int r = dalloc(ctx, &ctx->goff, (size_t)ctx->G_cap + 1)) return r;
+    if (int r = dalloc(ctx, &ctx->bgrp, (size_t)S * S + 1)) return r;
+    const size_t KMM = (size_t)ctx->p.K * M * M;
+    if (int r = dalloc(ctx, &ctx->pbins_den, (size_t)S * S * M * M)) return r;
+    if (int r = dalloc(ctx, &ctx->cg_r, KMM)) return r;
+    if (int r = dalloc(ctx, &ctx->cg_p, KMM)) return r;
+    if (int r = dalloc(ctx, &ctx->cg_q, KMM)) return r;
+    if (int r = dalloc(ctx, &ctx->cg_part, 3 * ((KMM + CG_NT - 1) / CG_NT))) return r;
+    if (int r = dalloc(ctx, &ctx->pos_corr, (size_t)J)) return r;
+    CK(cudaMemcpy(ctx->pbin, bin.data(), J * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    if (int r = build_subpixel_groups(ctx, bin)) return r;
   }
   // CSR lists of positions per object tile, ascending position index
   std::vector<int> cnt(ctx->n_tiles + 1, 0);
@@ -918,6 +1146,7 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
   CK(cudaMemcpy(ctx->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tile_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
   ctx->pos_host = pos;
+  ctx->pos_f.assign(positions, positions + 2 * (size_t)J);
   ctx->have_pos = true;
   ctx->psi_valid = false;
   return 0;
@@ -1085,6 +1314,7 @@ void ptycho_default_params(ptycho_params* p) {
   p->cluster = 0;
   p->likelihood = PTYCHO_LIK_AMPLITUDE;
   p->probe_ortho = 0;
+  p->subpixel = 0;
 }
 
 int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
@@ -1100,6 +1330,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     return fail(nullptr, PTYCHO_ERR_ARG, "likelihood=%d", p->likelihood);
   if (p->probe_ortho != 0 && p->probe_ortho != 1) return fail(nullptr, PTYCHO_ERR_ARG, "probe_ortho=%d", p->probe_ortho);
   if (p->K > MODE_KMAX) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "K=%d probe modes (at most %d)", p->K, MODE_KMAX);
+  if (p->subpixel != 0 && p->subpixel != 2 && p->subpixel != 4 && p->subpixel != 8 && p->subpixel != 16)
+    return fail(nullptr, PTYCHO_ERR_ARG, "subpixel=%d (0, 2, 4, 8 or 16)", p->subpixel);
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
@@ -1127,6 +1359,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     if (G > p->J) G = p->J;
     if (G < 1) G = 1;
     ctx->G = G;
+    ctx->S = p->subpixel;
+    ctx->G_cap = G + ctx->S * ctx->S;
   }
   int r = 0;
   const size_t obj = (size_t)p->obj_ny * p->obj_nx;
@@ -1490,6 +1724,59 @@ int ptycho_fourier_residual(ptycho_ctx* ctx, float* out, int on_device) {
   return r;
 }
 
+int ptycho_refine_positions(ptycho_ctx* ctx, double step, double max_shift) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!ctx->S) return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "position refinement needs sub-pixel positions (subpixel > 0)");
+  if (!ctx->have_data) return fail(ctx, PTYCHO_ERR_STATE, "refine_positions before set_data");
+  if (!std::isfinite(step) || !(max_shift >= 0.0) || !std::isfinite(max_shift))
+    return fail(ctx, PTYCHO_ERR_ARG, "step=%g max_shift=%g", step, max_shift);
+  if (int r = ensure_work_buffers(ctx)) return r;
+  ctx->psi_valid = false;  // the residual pass overwrites the exit-wave state
+  if (int r = launch_chi(ctx, ctx->X)) return r;
+  PosCorrArgs a{};
+  a.O = ctx->O;
+  a.ny = ctx->p.obj_ny;
+  a.nx = ctx->p.obj_nx;
+  a.P = ctx->Pt;
+  a.pbin = ctx->pbin;
+  a.X = ctx->X;
+  a.pos = ctx->pos;
+  a.M = ctx->p.M;
+  a.out = ctx->pos_corr;
+  const int J = ctx->p.J;
+  const double xb = 8.0 * J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
+  int r = launch(ctx, "pos_corr", xb, [&] {
+    switch (ctx->p.K) {
+      case 1: k_pos_corr<1><<<J, STEP_NT, 0, ctx->st>>>(a); break;
+      case 2: k_pos_corr<2><<<J, STEP_NT, 0, ctx->st>>>(a); break;
+      default: k_pos_corr<3><<<J, STEP_NT, 0, ctx->st>>>(a); break;
+    }
+  });
+  if (r) return r;
+  std::vector<float2> s(J);
+  CK(cudaMemcpyAsync(s.data(), ctx->pos_corr, J * sizeof(float2), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (int rc = check_device_flag(ctx)) return rc;
+  std::vector<float> next(ctx->pos_f);
+  for (int j = 0; j < J; ++j) {
+    const double sy = std::min(std::max((double)s[j].x, -max_shift), max_shift);
+    const double sx = std::min(std::max((double)s[j].y, -max_shift), max_shift);
+    if (!std::isfinite(sy) || !std::isfinite(sx))
+      return fail(ctx, PTYCHO_ERR_NONFINITE, "position correction of %d is not finite", j);
+    next[2 * j] = (float)((double)next[2 * j] + step * sy);
+    next[2 * j + 1] = (float)((double)next[2 * j + 1] + step * sx);
+  }
+  return set_positions_impl(ctx, next.data());  // checks bounds; unchanged on error
+}
+
+int ptycho_get_positions(ptycho_ctx* ctx, float* out) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (!out) return fail(ctx, PTYCHO_ERR_ARG, "out is NULL");
+  if (!ctx->have_pos) return fail(ctx, PTYCHO_ERR_STATE, "no positions set");
+  std::memcpy(out, ctx->pos_f.data(), ctx->pos_f.size() * sizeof(float));
+  return PTYCHO_OK;
+}
+
 long long ptycho_iteration(const ptycho_ctx* ctx) { return ctx ? ctx->t : -1; }
 
 int ptycho_set_iteration(ptycho_ctx* ctx, long long t) {
@@ -1559,7 +1846,10 @@ void ptycho_destroy(ptycho_ctx* ctx) {
                   ctx->pos,      ctx->amp,       ctx->amp_scale, ctx->denO,    ctx->tile_max,  ctx->denO_max,
                   ctx->tile_ptr, ctx->tile_list, ctx->ppart,    ctx->ppart_den, ctx->pnum,     ctx->pden,
                   ctx->pblk_max, ctx->alphaO,    ctx->alphaP,   ctx->err_part, ctx->err_out,   ctx->order,
-                  ctx->flag,     ctx->gram,      ctx->modeV};
+                  ctx->flag,     ctx->gram,      ctx->modeV,    ctx->pbin,     ctx->Pt,        ctx->dPt,
+                  ctx->pbins,    ctx->stmp,      ctx->porder,   ctx->goff,     ctx->bgrp,
+                  ctx->pbins_den, ctx->cg_r,     ctx->cg_p,     ctx->cg_q,     ctx->cg_part,
+                  ctx->pos_corr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (ctx->stage) cudaFree(ctx->stage);

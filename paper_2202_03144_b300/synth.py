@@ -17,7 +17,8 @@ Shapes follow the workloads the library is measured on:
 * object: a smoothed uniform amplitude in [0.8, 1.0] and a smoothed Gaussian
   phase field in [-pi/2, pi/2];
 * positions: a jittered raster or a Fermat spiral, as integer-valued floats
-  (y, x) of each patch's top-left corner.
+  (y, x) of each patch's top-left corner, optionally with uniform fractional
+  offsets (scan steps that are not whole pixels).
 """
 from __future__ import annotations
 
@@ -30,6 +31,7 @@ __all__ = [
     "make_probe",
     "make_object",
     "raster_positions",
+    "fractional_positions",
     "spiral_positions",
     "object_shape_for",
     "flat_object",
@@ -94,6 +96,14 @@ def raster_positions(ny: int, nx: int, step: float, jitter: int, offset: float,
     if jitter > 0:
         pos = pos + rng.integers(-jitter, jitter + 1, size=pos.shape)
     return pos.astype(np.float64)
+
+
+def fractional_positions(pos: np.ndarray, seed: int) -> np.ndarray:
+    """Whole-pixel positions plus a uniform [0, 1) offset per coordinate (a
+    scan whose steps are not whole pixels), as float32 values in float64."""
+    rng = np.random.default_rng(seed)
+    out = np.rint(pos) + rng.uniform(0.0, 1.0, pos.shape)
+    return out.astype(np.float32).astype(np.float64)
 
 
 def spiral_positions(n: int, spacing: float, center: tuple[float, float]) -> np.ndarray:

@@ -125,3 +125,27 @@ def test_batch_members_with_poisson_and_mode_orthogonalisation():
             r.set_init(c["O0"], c["P0"])
             r.iterate("lsqml", 3)
             assert np.array_equal(Og, r.get_object()) and np.array_equal(Pg, r.get_probe())
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+def test_batch_members_with_subpixel_positions(alg):
+    """Sub-pixel members (shifted-probe tables, the DM probe solve) inside the
+    captured graph: bit-identical to the members run alone, beside an
+    integer-position member."""
+    from gpu_cases import subpixel_scan
+    cases = [subpixel_scan(32, 2, 8, grid=3, photons=1e5, seed=31), subpixel_scan(64, 1, 4, grid=3, photons=1e5, seed=32),
+             scan(32, 1, grid=3, photons=1e5, seed=33)]
+    opts = [dict(subpixel=8), dict(subpixel=4), dict()]
+    members = [dict(M=c["M"], K=c["K"], J=len(c["pos"]), obj_shape=c["shape"], **o) for c, o in zip(cases, opts)]
+    with api.Batch(members) as b:
+        for m, c in zip(b.members, cases):
+            m.set_data(c["I"].astype(np.float32), c["pos"])
+            m.set_init(c["O0"], c["P0"])
+        b.iterate(alg, 3)
+        got = [(m.get_object(), m.get_probe()) for m in b.members]
+    for (Og, Pg), c, o in zip(got, cases, opts):
+        with api.Reconstruction(c["M"], c["K"], len(c["pos"]), c["shape"], **o) as r:
+            r.set_data(c["I"].astype(np.float32), c["pos"])
+            r.set_init(c["O0"], c["P0"])
+            r.iterate(alg, 3)
+            assert np.array_equal(Og, r.get_object()) and np.array_equal(Pg, r.get_probe())

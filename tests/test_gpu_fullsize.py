@@ -148,3 +148,57 @@ def test_beyond_2_to_31_elements():
         r.iterate("dm", 1)
         assert np.isfinite(r.fourier_error())
         assert np.all(np.isfinite(r.get_object())) and np.all(np.isfinite(r.get_probe()))
+
+
+def test_fullsize_subpixel(workload):
+    """The same workload at fractional positions (1/8-pixel shifts, 64
+    shifted probes): sampled residuals and forward model against the oracle,
+    noise-free data a fixed point of one LSQML iteration, whole == step mode."""
+    torch = pytest.importorskip("torch")
+    P, O, _, _, I = workload
+    S = 8
+    pos = synth.fractional_positions(synth.raster_positions(G, G, STEP, 2, 2, seed=2000), seed=2002)
+    corner, delta = orc.subpixel_positions(pos[SAMPLE], S)
+    J = len(pos)
+    O0 = synth.make_object(2640, 2640, seed=1001)
+    P0 = synth.noisy_probe(P, 0.1, seed=79)
+    Is = orc.far_field_intensity(O, P, corner, delta)
+    I = I.copy()
+    I[SAMPLE] = synth.poisson(Is * 1e5 / Is.sum(axis=(1, 2)).mean(), seed=81).astype(np.float32)
+    with api.Reconstruction(M, K, J, O.shape, subpixel=S) as r:
+        assert r.cluster == 16
+        r.set_data(I, pos)
+        r.set_init(O0, P0)
+        chi = torch.empty((J, K, M, M), dtype=torch.complex64, device="cuda")
+        r.fourier_residual(chi)
+        torch.cuda.synchronize()
+        got = chi[SAMPLE].cpu().numpy()
+        del chi
+        r.set_init(O, P)
+        Isim = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        r.simulate(Isim)
+        torch.cuda.synchronize()
+        Ig = Isim[SAMPLE].cpu().numpy()
+        r.set_data(Isim, pos)
+        del Isim
+        r.set_init(O, P)
+        r.iterate("lsqml", 1)
+        O1, P1 = r.get_object(), r.get_probe()
+    ref = orc.fourier_residual(O0, P0, corner, I[SAMPLE].astype(np.float64), delta=delta)
+    for s in range(len(SAMPLE)):
+        e = np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s])
+        assert e < 2e-5, (SAMPLE[s], e)
+    for s in range(len(SAMPLE)):
+        e = np.linalg.norm(Ig[s] - Is[s]) / np.linalg.norm(Is[s])
+        assert e < 2e-5, (SAMPLE[s], e)
+    assert np.linalg.norm(O1 - O) / np.linalg.norm(O) < 1e-5
+    assert np.linalg.norm(P1 - P) / np.linalg.norm(P) < 1e-5
+    outs = []
+    for steps in ([2], [1, 1]):
+        with api.Reconstruction(M, K, J, O.shape, subpixel=S) as r:
+            r.set_data(I, pos)
+            r.set_init(np.ones_like(O), P0)
+            for n in steps:
+                r.iterate("lsqml", n)
+            outs.append((r.get_object(), r.get_probe()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

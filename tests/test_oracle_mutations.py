@@ -80,6 +80,11 @@ MUTATIONS = {
     "subpixel_cg_step_sign": ("        X = X + a * p\n", "        X = X - a * p\n"),
     "subpixel_cg_no_conjugation": ("        p = z + b * p\n", "        p = z\n"),
     "subpixel_dm_diagonal_probe": ("    if update_probe and delta is not None:", "    if False:"),
+    "posref_forward_difference": ("return (Op[2:, 1:-1] - Op[:-2, 1:-1]) / 2.0,", "return (Op[2:, 1:-1] - Op[1:-1, 1:-1]),"),
+    "posref_sign": ("return np.asarray(positions, dtype=np.float64) + step * np.clip",
+                    "return np.asarray(positions, dtype=np.float64) - step * np.clip"),
+    "posref_xy_swapped": ("Gy, Gx = gather(gy, pos, M), gather(gx, pos, M)", "Gy, Gx = gather(gx, pos, M), gather(gy, pos, M)"),
+    "posref_unshifted_probe": ("Pk = Pj[0 if delta is None else j]", "Pk = P"),
     "poisson_residual_minus_phi": ("return ifft2(poisson_correction(fft2(phi), to_fft_order(I)))",
                                    "return ifft2(poisson_correction(fft2(phi), to_fft_order(I))) - phi"),
 }
