@@ -201,3 +201,72 @@ def test_subpixel_dm_converges():
     Oc, Pc, _ = orc.reconstruct("dm", c["O0"], c["P0"], c["pos"], c["I"], 14, subpixel=8)
     m = _illuminated(c)
     assert rel_l2(align_global(Og, Oc, m), Oc, m) < TOL_REC and rel_l2(Pg, Pc) < TOL_REC
+
+
+@pytest.mark.parametrize("M,K,C,S", [(32, 1, 1, 8), (32, 3, 4, 16), (64, 1, 2, 8), (256, 1, 16, 8)],
+                         ids=lambda v: str(v))
+def test_position_refinement_parity(M, K, C, S):
+    """One refinement call against the oracle's: the same fresh residual, the
+    per-position 2x2 fit, clipping and step, to 1e-4 pixel (float32
+    positions of a few hundred pixels carry ~3e-5)."""
+    c = subpixel_scan(M, K, S, grid=3, photons=1e6)
+    rng = np.random.default_rng(5)
+    start = (c["pos"] + rng.uniform(-0.4, 0.4, c["pos"].shape)).astype(np.float32).astype(np.float64)
+    start = np.clip(start, 0.0, np.array(c["shape"]) - c["M"] - 0.5)
+    with api.Reconstruction(M, K, len(start), c["shape"], cluster=C, subpixel=S) as r:
+        r.set_data(c["I"].astype(np.float32), start)
+        r.set_init(c["O"], c["P0"])
+        assert np.array_equal(r.get_positions(), start.astype(np.float32))
+        r.refine_positions(step=0.8, max_shift=0.3)
+        got = r.get_positions().astype(np.float64)
+        r.iterate("lsqml", 1)   # the context runs on at the new positions
+    ref = orc.refine_positions(c["O"], c["P0"], start, c["I"], S, step=0.8, max_shift=0.3)
+    assert np.abs(got - ref).max() < 1e-4, np.abs(got - ref).max()
+    assert np.abs(got - start).max() <= 0.8 * 0.3 + 1e-4
+
+
+def test_position_refinement_recovers_positions():
+    """From the true object and probe, repeated refinement walks positions
+    perturbed by up to 0.4 px back towards the truth, as the oracle does."""
+    c = subpixel_scan(64, 1, 16, grid=4, step=12)
+    rng = np.random.default_rng(6)
+    start = (c["pos"] + rng.uniform(-0.4, 0.4, c["pos"].shape)).astype(np.float32).astype(np.float64)
+    start = np.clip(start, 0.0, np.array(c["shape"]) - c["M"] - 0.5)
+    errs = []
+    with api.Reconstruction(64, 1, len(start), c["shape"], subpixel=16) as r:
+        r.set_data(c["I"].astype(np.float32), start)
+        r.set_init(c["O"], c["P"])
+        for _ in range(6):
+            errs.append(float(np.sqrt(np.mean((r.get_positions() - c["pos"]) ** 2))))
+            r.refine_positions()
+        errs.append(float(np.sqrt(np.mean((r.get_positions() - c["pos"]) ** 2))))
+    assert errs[-1] < 0.5 * errs[0], errs
+    assert all(b < a + 1e-3 for a, b in zip(errs, errs[1:])), errs
+
+
+def test_position_refinement_errors():
+    c = subpixel_scan(32, 1, 8, grid=2)
+    with api.Reconstruction(32, 1, len(c["pos"]), c["shape"]) as r:   # integer positions
+        r.set_data(c["I"].astype(np.float32), c["pos"])
+        with pytest.raises(api.PtychoError) as e:
+            r.refine_positions()
+        assert e.value.name == "UNSUPPORTED"
+    with api.Reconstruction(32, 1, len(c["pos"]), c["shape"], subpixel=8) as r:
+        with pytest.raises(api.PtychoError) as e:
+            r.refine_positions()
+        assert e.value.name == "STATE"
+        r.set_data(c["I"].astype(np.float32), c["pos"])
+        with pytest.raises(api.PtychoError) as e:
+            r.refine_positions(step=float("nan"))
+        assert e.value.name == "ARG"
+        with pytest.raises(api.PtychoError) as e:
+            r.refine_positions(max_shift=-1.0)
+        assert e.value.name == "ARG"
+        before = r.get_positions()
+        # a step so large that a patch leaves the object: nothing moves
+        r.set_init(c["O"], c["P0"])
+        with pytest.raises(api.PtychoError) as e:
+            r.refine_positions(step=1e6, max_shift=1e3)
+        assert e.value.name == "BOUNDS"
+        assert np.array_equal(r.get_positions(), before)
+        r.iterate("lsqml", 1)
