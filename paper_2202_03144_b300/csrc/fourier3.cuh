@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     const int colL = tid % W, n2 = (tid / W) % R2, k = tid / (W * R2);
     const int col = c * W + colL;
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = ldg_keep(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
     const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
 #pragma unroll
     for (int g0 = 0; g0 < R1; g0 += F3_OG) {
@@ -384,11 +384,11 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       const int row = n1 * R2 + n2;
       const size_t xi = (((size_t)j * K + k) * M + row) * M + col;
       if (mode == FM_CHI || mode == FM_CHIP) {
-        a.X[xi] = v[n1];
+        __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-        const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);
-        a.X[xi] = cadd(cmul(pr, o), v[n1]);
+        const float2 pr = ldg_keep(Pj + ((size_t)k * M + row) * M + col);
+        __stcs(a.X + xi, cadd(cmul(pr, o), v[n1]));
       }
     }
   }
