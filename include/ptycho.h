@@ -127,6 +127,17 @@ typedef struct {
                        simulation / residual calls); ePIE returns
                        PTYCHO_ERR_UNSUPPORTED.  Device memory: three tables
                        of S^2 K M^2 complex values and S^2 M^2 floats.       */
+  int block_positions; /* 0 (default): the residuals of all J positions stay
+                       in device memory (J K M^2 complex values).  B > 0 (and
+                       < J): LSQML keeps those of B positions at a time, for
+                       scans whose residuals exceed device memory (the paper's
+                       data larger than one GPU's memory, Sec. 3.3): each
+                       iteration computes every block's residual twice, once
+                       for the directions and once for the step sizes and the
+                       update (two Fourier passes instead of one); same
+                       results as B = 0 up to the grouping of the sums.  DM
+                       (whose state is every exit wave) and sub-pixel
+                       positions return PTYCHO_ERR_UNSUPPORTED.               */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */

@@ -41,6 +41,7 @@ class Params(C.Structure):
         ("epie_alpha", C.c_double), ("epie_beta", C.c_double), ("lsqml_beta", C.c_double),
         ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
         ("likelihood", C.c_int), ("probe_ortho", C.c_int), ("subpixel", C.c_int),
+        ("block_positions", C.c_int),
     ]
 
 

@@ -159,6 +159,7 @@ struct Fourier2Args {
   const float2* tw2;      // tw2[k1 * R2 + n2] = exp(-2 pi i n2 k1 / M)
   int* err_flag;          // set to 1 if a bounded wait gave up
   int j0;
+  int xoff;               // X holds positions from xoff on (position-blocked residuals)
   int mode;
 };
 
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
       asm volatile("" ::: "memory");
     }
     if (mode == FM_DM) {
-      const float2* xrow = a.X + (((size_t)j * K + k) * M + n2) * M + col;
+      const float2* xrow = a.X + (((size_t)(j - a.xoff) * K + k) * M + n2) * M + col;
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) v[n1] = csub(cscale(v[n1], 2.f), xrow[(size_t)n1 * R2 * M]);
     }
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       const int row = n1 * R2 + n2;
-      const size_t xi = (((size_t)j * K + k) * M + row) * M + col;
+      const size_t xi = (((size_t)(j - a.xoff) * K + k) * M + row) * M + col;
       if (mode == FM_CHI || mode == FM_CHIP) {
         __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
       } else {

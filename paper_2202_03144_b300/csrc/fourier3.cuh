@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       asm volatile("" ::: "memory");
     }
     if (mode == FM_DM) {
-      const float2* xrow = a.X + (((size_t)j * K + k) * M + n2) * M + col;
+      const float2* xrow = a.X + (((size_t)(j - a.xoff) * K + k) * M + n2) * M + col;
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) v[n1] = csub(cscale(v[n1], 2.f), xrow[(size_t)n1 * R2 * M]);
     }
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       const int row = n1 * R2 + n2;
-      const size_t xi = (((size_t)j * K + k) * M + row) * M + col;
+      const size_t xi = (((size_t)(j - a.xoff) * K + k) * M + row) * M + col;
       if (mode == FM_CHI || mode == FM_CHIP) {
         __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
       } else {

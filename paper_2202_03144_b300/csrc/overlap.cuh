@@ -64,11 +64,15 @@ struct ObjArgs {
   const int* tile_ptr;    // [n_tiles + 1]
   const int* tile_list;   // positions overlapping each tile, ascending
   const float* weights;   // per-position weight (alpha_O) or NULL
-  float* den;             // den_O [ny][nx] (written by OBJ_NUMDEN, read otherwise)
+  float* den;             // den_O [ny][nx] (written by OBJ_NUMDEN, read otherwise);
+                          // OBJ_NUMDEN with NULL: numerator only
   float* tile_max;        // OBJ_NUMDEN: max of den per tile
   const float* den_max;   // max over all tiles (one float)
   float reg, beta;
   int M;
+  // position blocks (residuals of positions [jlo, jhi) only, X holding
+  // them from position xoff on); accumulate: OBJ_NUMDEN adds to dO / den
+  int jlo, jhi, xoff, accumulate;
 };
 
 // SUB: sub-pixel positions (P is the shifted table, indexed by pbin).
@@ -90,14 +94,29 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
       num[i][e] = make_float2(0.f, 0.f);
       den[i][e] = 0.f;
     }
-  const int s0 = a.tile_ptr[tile], s1 = a.tile_ptr[tile + 1];
+  int s0 = a.tile_ptr[tile], s1 = a.tile_ptr[tile + 1];
+  if (a.jhi > a.jlo) {  // a block of positions: the tile's list is ascending, cut it by bisection
+    int lo = s0, hi = s1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.tile_list[mid] < a.jlo) lo = mid + 1; else hi = mid;
+    }
+    const int b0 = lo;
+    hi = s1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.tile_list[mid] < a.jhi) lo = mid + 1; else hi = mid;
+    }
+    s0 = b0;
+    s1 = lo;
+  }
   // the tile's positions (index, corner, weight) staged in shared memory in
   // chunks, so the inner loop has no chain of dependent global loads
   __shared__ int sj[OBJ_CHUNK];
   __shared__ int2 sp[OBJ_CHUNK];
   __shared__ float sw[OBJ_CHUNK];
   __shared__ int sb[SUB ? OBJ_CHUNK : 1];
-  const bool weighted = MODE == OBJ_UPD && a.weights != nullptr;
+  const bool weighted = a.weights != nullptr;
   for (int c0 = s0; c0 < s1; c0 += OBJ_CHUNK) {
     const int nc = min(OBJ_CHUNK, s1 - c0);
     __syncthreads();
@@ -126,7 +145,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
           const bool row_in = uy >= 0 && uy < M;
           const size_t u0 = (size_t)(row_in ? uy : 0) * M;
           const float2* prow = Pj + k * MM + u0;
-          const float2* xrow = a.X + ((size_t)j * K + k) * MM + u0;
+          const float2* xrow = a.X + ((size_t)(j - a.xoff) * K + k) * MM + u0;
           if (pairs) {
 #pragma unroll
             for (int e = 0; e < OBJ_COLS; e += 2) {
@@ -164,6 +183,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
   }
   if (MODE == OBJ_NUMDEN) {
     float m = 0.f;
+    const bool want_den = a.den != nullptr;
 #pragma unroll
     for (int i = 0; i < OBJ_ROWS; ++i)
 #pragma unroll
@@ -171,11 +191,18 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
         const int y = ty0 + ry + OBJ_RSTEP * i;
         if (y < a.ny && x + e < a.nx) {
           const size_t r = (size_t)y * a.nx + x + e;
-          a.den[r] = den[i][e];
-          a.dO[r] = num[i][e];
-          m = fmaxf(m, den[i][e]);
+          float d = den[i][e];
+          float2 nm = num[i][e];
+          if (a.accumulate) {
+            nm = cadd(a.dO[r], nm);
+            if (want_den) d += a.den[r];
+          }
+          if (want_den) a.den[r] = d;
+          a.dO[r] = nm;
+          m = fmaxf(m, d);
         }
       }
+    if (!want_den) return;
     m = block_max_f<OBJ_NT>(m, red);
     if (threadIdx.x == 0) a.tile_max[tile] = m;
     return;
@@ -217,6 +244,20 @@ __global__ void __launch_bounds__(256) k_obj_norm(float2* __restrict__ O, float2
   }
 }
 
+// LSQML update from an accumulated numerator (position blocks):
+//   O <- O + beta acc / (den + delta)
+__global__ void __launch_bounds__(256) k_obj_apply_acc(float2* __restrict__ O, const float2* __restrict__ acc,
+                                                       const float* __restrict__ den, const float* __restrict__ den_max,
+                                                       float reg, float beta, size_t n) {
+  const float delta = reg * den_max[0];
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < n; r += (size_t)gridDim.x * blockDim.x) {
+    const float d = den[r] + delta;
+    const float sc = beta * (d > 0.f ? 1.f / d : 0.f);
+    const float2 o = O[r], num = acc[r];
+    O[r] = make_float2(fmaf(sc, num.x, o.x), fmaf(sc, num.y, o.y));
+  }
+}
+
 // Max of n floats into out[0] (one CTA, fixed order).
 __global__ void __launch_bounds__(1024) k_reduce_max(const float* in, int n, float* out) {
   __shared__ float red[32];
@@ -237,6 +278,8 @@ struct ProbeArgs {
   const int* bgrp;         // [bins + 1] first group of each bin (sub-pixel), or NULL
   int nbins;
   int J, M, G;
+  int jlo, xoff;           // position blocks: positions [jlo, jlo + J), X from position xoff on
+  int accumulate;          // k_probe_sum adds to num / den
   float2* part_num;        // [G][K][M*M]
   float* part_den;         // [G][M*M] or NULL (skip den)
   float2* num;             // [K][M*M] (sub-pixel: [bins][K][M*M])
@@ -255,8 +298,8 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   const int u = blockIdx.x * PROBE_NT + threadIdx.x;
   const int uy = u / a.M, ux = u % a.M;
   const int g = blockIdx.y;
-  const int jb = SUB ? a.goff[g] : (int)(((long long)a.J * g) / a.G);
-  const int je = SUB ? a.goff[g + 1] : (int)(((long long)a.J * (g + 1)) / a.G);
+  const int jb = SUB ? a.goff[g] : a.jlo + (int)(((long long)a.J * g) / a.G);
+  const int je = SUB ? a.goff[g + 1] : a.jlo + (int)(((long long)a.J * (g + 1)) / a.G);
   float2 num[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) num[k] = make_float2(0.f, 0.f);
@@ -289,7 +332,8 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
           w[h] = in ? sw[i] : 0.f;
 #pragma unroll
           for (int k = 0; k < K; ++k)
-            xv[h][k] = in ? __ldcs(a.X + ((size_t)(SUB ? sj[i] : c0 + i) * K + k) * MM + u) : make_float2(0.f, 0.f);
+            xv[h][k] = in ? __ldcs(a.X + ((size_t)((SUB ? sj[i] : c0 + i) - a.xoff) * K + k) * MM + u)
+                          : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int h = 0; h < UJ; ++h) {
@@ -327,12 +371,14 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_sum(ProbeArgs a) {
       for (int k = 0; k < K; ++k) {
         float2 s = make_float2(0.f, 0.f);
         for (int g = g0; g < g1; ++g) s = cadd(s, a.part_num[((size_t)g * K + k) * MM + u]);
-        a.num[((size_t)b * K + k) * MM + u] = s;
+        const size_t o = ((size_t)b * K + k) * MM + u;
+        a.num[o] = a.accumulate ? cadd(a.num[o], s) : s;
       }
     }
     if (want_den) {
       float d = 0.f;
       for (int g = 0; g < a.G; ++g) d += a.part_den[(size_t)g * MM + u];
+      if (a.accumulate) d += a.den[u];
       a.den[u] = d;
       m = d;
       if (a.bgrp && a.bin_den)
@@ -400,6 +446,7 @@ struct StepArgs {
   int M;
   float* alpha_O;
   float* alpha_P;
+  int j0, xoff;       // first position of the launch; X holds positions from xoff on
 };
 
 constexpr int STEP_NT = 256;
@@ -409,7 +456,7 @@ constexpr int STEP_NT = 256;
 template <int K, bool SUB>
 __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k_lsqml_steps(StepArgs a) {
   __shared__ double red[32];
-  const int j = blockIdx.x;
+  const int j = a.j0 + blockIdx.x;
   const int2 p = a.pos[j];
   const int MM = a.M * a.M;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
@@ -441,7 +488,7 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       pr[k] = __ldg(reinterpret_cast<const float4*>(a.P + boff + (size_t)k * MM + u));
-      xv[k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)j * K + k) * MM + u));
+      xv[k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)(j - a.xoff) * K + k) * MM + u));
       dp[k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + boff + (size_t)k * MM + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll

@@ -343,6 +343,15 @@ struct ptycho_ctx {
   float2* cg_q = nullptr;
   double* cg_part = nullptr;   // [3][blocks] inner-product partials
   float2* pos_corr = nullptr;  // position refinement: per-position shift
+  // position blocks (params.block_positions = B > 0, LSQML): X holds the
+  // residuals of B positions; blk is the block the launches work on
+  int B = 0;
+  float2* objacc = nullptr;    // accumulated alpha-weighted object numerator
+  struct Block {
+    bool on = false;
+    int j0 = 0, n = 0;
+    bool accumulate = false;
+  } blk;
   std::vector<float> pos_f;    // positions as last set (or refined), [J][2]
   float2* ppart = nullptr;
   float* ppart_den = nullptr;
@@ -532,6 +541,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   a.tw2 = ctx->tw2;
   a.err_flag = ctx->err_flag;
   a.j0 = j0;
+  a.xoff = (ctx->blk.on && X == ctx->X) ? ctx->blk.j0 : 0;
   a.mode = mode;
   const double MM = (double)ctx->p.M * ctx->p.M;
   const double K = ctx->p.K;
@@ -624,6 +634,7 @@ const unsigned short* bin_view(const ptycho_ctx* ctx) { return ctx->S ? ctx->pbi
 // object-side modes of obj_step (OBJ_UPD is the LSQML update)
 constexpr int OBJ_STEP_DM = 100;   // DM overlap update of O
 constexpr int OBJ_STEP_DIR = 101;  // LSQML direction dO
+constexpr int OBJ_STEP_ACC = 102;  // position blocks: accumulate the weighted numerator in objacc
 
 template <int K>
 int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
@@ -646,10 +657,25 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
   a.reg = (float)ctx->p.reg;
   a.beta = (float)ctx->p.lsqml_beta;
   a.M = ctx->p.M;
+  const int nj = ctx->blk.on ? ctx->blk.n : ctx->p.J;
+  if (ctx->blk.on) {
+    a.jlo = ctx->blk.j0;
+    a.jhi = ctx->blk.j0 + ctx->blk.n;
+    a.xoff = ctx->blk.j0;
+    a.accumulate = ctx->blk.accumulate;
+  }
   const double obj = (double)ctx->p.obj_ny * ctx->p.obj_nx;
-  const double xb = 8.0 * ctx->p.J * K * (double)ctx->p.M * ctx->p.M;
+  const double xb = 8.0 * nj * K * (double)ctx->p.M * ctx->p.M;
   const dim3 g(ctx->n_tiles), b(OBJ_NT);
   const bool sub = ctx->S != 0;
+  if (mode == OBJ_STEP_ACC) {  // numerator only, into objacc
+    a.dO = ctx->objacc;
+    a.den = nullptr;
+    return launch(ctx, "obj_update", xb + obj * 16.0, [&] {
+      if (sub) k_obj<K, OBJ_NUMDEN, true><<<g, b, 0, ctx->st>>>(a);
+      else k_obj<K, OBJ_NUMDEN, false><<<g, b, 0, ctx->st>>>(a);
+    });
+  }
   if (mode == OBJ_UPD)
     return launch(ctx, "obj_update", xb + obj * 20.0, [&] {
       if (sub) k_obj<K, OBJ_UPD, true><<<g, b, 0, ctx->st>>>(a);
@@ -661,6 +687,7 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
         else k_obj<K, OBJ_NUMDEN, false><<<g, b, 0, ctx->st>>>(a);
       }))
     return r;
+  if (ctx->blk.on) return 0;  // the epilogue runs once, after the last block (obj_finish)
   if (int r = launch(ctx, "reduce_max", 0.0,
                      [&] { k_reduce_max<<<1, 1024, 0, ctx->st>>>(ctx->tile_max, ctx->n_tiles, ctx->denO_max); }))
     return r;
@@ -671,6 +698,22 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
     });
   return launch(ctx, "obj_norm", obj * 20.0, [&] {
     k_obj_norm<NORM_DIR><<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->dO, ctx->denO, ctx->denO_max, a.reg, n);
+  });
+}
+
+// After the last position block: max of den_O and the direction (or the DM update).
+int obj_finish(ptycho_ctx* ctx, int mode) {
+  if (int r = launch(ctx, "reduce_max", 0.0,
+                     [&] { k_reduce_max<<<1, 1024, 0, ctx->st>>>(ctx->tile_max, ctx->n_tiles, ctx->denO_max); }))
+    return r;
+  const size_t n = (size_t)ctx->p.obj_ny * ctx->p.obj_nx;
+  const float reg = (float)ctx->p.reg;
+  if (mode == OBJ_STEP_DM)
+    return launch(ctx, "obj_norm", n * 28.0, [&] {
+      k_obj_norm<NORM_DM><<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->dO, ctx->denO, ctx->denO_max, reg, n);
+    });
+  return launch(ctx, "obj_norm", n * 20.0, [&] {
+    k_obj_norm<NORM_DIR><<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->dO, ctx->denO, ctx->denO_max, reg, n);
   });
 }
 
@@ -744,6 +787,13 @@ int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, boo
   a.J = ctx->p.J;
   a.M = ctx->p.M;
   a.G = ctx->S ? ctx->G_sub : ctx->G;
+  if (ctx->blk.on) {  // this block's positions, added to the running sums
+    a.J = ctx->blk.n;
+    a.jlo = ctx->blk.j0;
+    a.xoff = ctx->blk.j0;
+    a.accumulate = ctx->blk.accumulate;
+    a.G = std::min(ctx->G, ctx->blk.n);
+  }
   if (ctx->S) {  // groups in bin order, one numerator per bin
     a.order = ctx->porder;
     a.goff = ctx->goff;
@@ -761,7 +811,7 @@ int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, boo
   a.beta = (float)ctx->p.lsqml_beta;
   const int MM = ctx->p.M * ctx->p.M;
   const int nblk = (MM + PROBE_NT - 1) / PROBE_NT;
-  const double xb = 8.0 * ctx->p.J * K * (double)MM;
+  const double xb = 8.0 * a.J * K * (double)MM;
   if (X) {
     if (int r = launch(ctx, "probe_partial", xb, [&] {
           if (ctx->S) k_probe_partial<K, true><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
@@ -807,8 +857,13 @@ int steps_step(ptycho_ctx* ctx, bool upd) {
   a.M = ctx->p.M;
   a.alpha_O = ctx->alphaO;
   a.alpha_P = ctx->alphaP;
-  const double xb = 8.0 * ctx->p.J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
-  const int J = ctx->p.J;
+  int J = ctx->p.J;
+  if (ctx->blk.on) {
+    a.j0 = ctx->blk.j0;
+    a.xoff = ctx->blk.j0;
+    J = ctx->blk.n;
+  }
+  const double xb = 8.0 * J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
   const bool sub = ctx->S != 0;
   switch (ctx->p.K) {
     case 1: return launch(ctx, "lsqml_steps", xb, [&] {
@@ -829,7 +884,10 @@ int steps_step(ptycho_ctx* ctx, bool upd) {
 int ensure_work_buffers(ptycho_ctx* ctx) {
   const size_t MM = (size_t)ctx->p.M * ctx->p.M;
   const size_t K = ctx->p.K;
-  if (int r = dalloc(ctx, &ctx->X, (size_t)ctx->p.J * K * MM)) return r;
+  const size_t xpos = ctx->B > 0 ? (size_t)std::min(ctx->B, ctx->p.J) : (size_t)ctx->p.J;
+  if (int r = dalloc(ctx, &ctx->X, xpos * K * MM)) return r;
+  if (ctx->B > 0)
+    if (int r = dalloc(ctx, &ctx->objacc, (size_t)ctx->p.obj_ny * ctx->p.obj_nx)) return r;
   if (int r = dalloc(ctx, &ctx->dO, (size_t)ctx->p.obj_ny * ctx->p.obj_nx)) return r;
   if (int r = dalloc(ctx, &ctx->dP, K * MM)) return r;
   if (int r = dalloc(ctx, &ctx->ppart, (size_t)ctx->G_cap * K * MM)) return r;
@@ -849,6 +907,8 @@ int ensure_work_buffers(ptycho_ctx* ctx) {
 // ------------------------------------------------------------- algorithms
 // DM: buffers and the initial exit waves psi = P_k O_j (outside any graph).
 int dm_prepare(ptycho_ctx* ctx) {
+  if (ctx->B > 0)
+    return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "DM keeps the exit waves of all positions (create with block_positions = 0)");
   if (int r = ensure_work_buffers(ctx)) return r;
   const int J = ctx->p.J, K = ctx->p.K, M = ctx->p.M;
   if (!ctx->psi_valid) {
@@ -904,7 +964,10 @@ int launch_chi(ptycho_ctx* ctx, float2* dst) {
   return launch_fourier(ctx, mode, dst, nullptr, 0, ctx->p.J, "fourier_chi");
 }
 
+int lsqml_step_blocked(ptycho_ctx* ctx, bool upd);
+
 int lsqml_step(ptycho_ctx* ctx, bool upd) {
+  if (ctx->B > 0 && ctx->B < ctx->p.J) return lsqml_step_blocked(ctx, upd);
   if (int r = launch_chi(ctx, ctx->X)) return r;
   if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
   if (upd)
@@ -915,6 +978,51 @@ int lsqml_step(ptycho_ctx* ctx, bool upd) {
   if (int r = obj_step(ctx, OBJ_UPD, ctx->X, ctx->alphaO)) return r;
   if (upd)
     if (int r = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return r;
+  if (upd && ctx->p.probe_ortho) return ortho_step(ctx, false);
+  return 0;
+}
+
+// LSQML with the residuals of B positions resident at a time: two Fourier
+// passes per iteration.  Pass 1 sums the directions' numerators and
+// denominators block by block; pass 2 recomputes each block's residual (the
+// same (O, P), so the same chi) for its step sizes and the alpha-weighted
+// update sums.  Same arithmetic as lsqml_step, sums grouped by block.
+int lsqml_step_blocked(ptycho_ctx* ctx, bool upd) {
+  const int J = ctx->p.J, B = ctx->B;
+  const int mode = ctx->p.likelihood == PTYCHO_LIK_POISSON ? FM_CHIP : FM_CHI;
+  int r = 0;
+  for (int pass = 0; pass < 2 && !r; ++pass) {
+    for (int j0 = 0; j0 < J && !r; j0 += B) {
+      ctx->blk.on = true;
+      ctx->blk.j0 = j0;
+      ctx->blk.n = std::min(B, J - j0);
+      ctx->blk.accumulate = j0 > 0;
+      r = launch_fourier(ctx, mode, ctx->X, nullptr, j0, ctx->blk.n, "fourier_chi");
+      if (!r && pass == 0) {
+        r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr);
+        if (!r && upd) r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, false);
+      } else if (!r) {
+        r = steps_step(ctx, upd);
+        if (!r && upd) r = probe_step(ctx, PR_UPD, ctx->X, ctx->alphaP, false, false);
+        if (!r) r = obj_step(ctx, OBJ_STEP_ACC, ctx->X, ctx->alphaO);
+      }
+      ctx->blk = ptycho_ctx::Block{};
+    }
+    if (r) break;
+    if (pass == 0) {
+      r = obj_finish(ctx, OBJ_STEP_DIR);
+      if (!r && upd) r = probe_step(ctx, PR_DIR, nullptr, nullptr, true, true);
+    }
+  }
+  if (r) return r;
+  const size_t n = (size_t)ctx->p.obj_ny * ctx->p.obj_nx;
+  if (int rr = launch(ctx, "obj_update", n * 28.0, [&] {
+        k_obj_apply_acc<<<1184, 256, 0, ctx->st>>>(ctx->O, ctx->objacc, ctx->denO, ctx->denO_max, (float)ctx->p.reg,
+                                                    (float)ctx->p.lsqml_beta, n);
+      }))
+    return rr;
+  if (upd)
+    if (int rr = probe_step(ctx, PR_UPD, nullptr, nullptr, false, true)) return rr;
   if (upd && ctx->p.probe_ortho) return ortho_step(ctx, false);
   return 0;
 }
@@ -1315,6 +1423,7 @@ void ptycho_default_params(ptycho_params* p) {
   p->likelihood = PTYCHO_LIK_AMPLITUDE;
   p->probe_ortho = 0;
   p->subpixel = 0;
+  p->block_positions = 0;
 }
 
 int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
@@ -1332,6 +1441,9 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (p->K > MODE_KMAX) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "K=%d probe modes (at most %d)", p->K, MODE_KMAX);
   if (p->subpixel != 0 && p->subpixel != 2 && p->subpixel != 4 && p->subpixel != 8 && p->subpixel != 16)
     return fail(nullptr, PTYCHO_ERR_ARG, "subpixel=%d (0, 2, 4, 8 or 16)", p->subpixel);
+  if (p->block_positions < 0) return fail(nullptr, PTYCHO_ERR_ARG, "block_positions=%d", p->block_positions);
+  if (p->block_positions > 0 && p->subpixel > 0)
+    return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "position blocks with sub-pixel positions are not supported");
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
@@ -1361,6 +1473,7 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     ctx->G = G;
     ctx->S = p->subpixel;
     ctx->G_cap = G + ctx->S * ctx->S;
+    ctx->B = p->block_positions < p->J ? p->block_positions : 0;
   }
   int r = 0;
   const size_t obj = (size_t)p->obj_ny * p->obj_nx;
@@ -1849,7 +1962,7 @@ void ptycho_destroy(ptycho_ctx* ctx) {
                   ctx->flag,     ctx->gram,      ctx->modeV,    ctx->pbin,     ctx->Pt,        ctx->dPt,
                   ctx->pbins,    ctx->stmp,      ctx->porder,   ctx->goff,     ctx->bgrp,
                   ctx->pbins_den, ctx->cg_r,     ctx->cg_p,     ctx->cg_q,     ctx->cg_part,
-                  ctx->pos_corr};
+                  ctx->pos_corr, ctx->objacc};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (ctx->stage) cudaFree(ctx->stage);

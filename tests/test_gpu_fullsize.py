@@ -202,3 +202,23 @@ def test_fullsize_subpixel(workload):
                 r.iterate("lsqml", n)
             outs.append((r.get_object(), r.get_probe()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_fullsize_position_blocks(workload):
+    """The bench scan with the residuals of 2,500 positions resident at a time
+    (4 blocks): two LSQML iterations agree with the resident run to the
+    parity tolerance (the probe sums over 10,000 positions, regrouped, differ
+    by ~2e-5 in FP32), and whole mode equals step mode."""
+    P, O, pos, P0, I = workload
+    outs = []
+    for B, steps in ((0, [2]), (2500, [2]), (2500, [1, 1])):
+        with api.Reconstruction(M, K, len(pos), O.shape, block_positions=B) as r:
+            r.set_data(I, pos)
+            r.set_init(np.ones_like(O), P0)
+            for n in steps:
+                r.iterate("lsqml", n)
+            outs.append((r.get_object(), r.get_probe()))
+    (Or, Pr), (Ob, Pb), (Os, Ps) = outs
+    assert np.linalg.norm(Ob - Or) / np.linalg.norm(Or) < 1e-4
+    assert np.linalg.norm(Pb - Pr) / np.linalg.norm(Pr) < 1e-4
+    assert np.array_equal(Ob, Os) and np.array_equal(Pb, Ps)
