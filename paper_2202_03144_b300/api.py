@@ -369,8 +369,10 @@ class Reconstruction:
 
     def checkpoint(self):
         """Everything a run needs to resume bit for bit: object, probe,
-        iteration index and (DM) the exit waves (host arrays)."""
-        state = {"object": self.get_object(), "probe": self.get_probe(), "iteration": self.iteration}
+        iteration index, the positions (as refined) and (DM) the exit waves
+        (host arrays)."""
+        state = {"object": self.get_object(), "probe": self.get_probe(), "iteration": self.iteration,
+                 "positions": self.get_positions()}
         try:
             state["exit_waves"] = self.get_exit_waves()
         except PtychoError as e:
@@ -380,6 +382,8 @@ class Reconstruction:
 
     def restore(self, state):
         """Resume from :meth:`checkpoint` (data must already be set)."""
+        if "positions" in state:
+            self.set_positions(state["positions"])
         self.set_init(state["object"], state["probe"])
         _check(self.ctx, lib().ptycho_set_iteration(self.ctx, int(state["iteration"])))
         if "exit_waves" in state:

@@ -270,3 +270,30 @@ def test_position_refinement_errors():
         assert e.value.name == "BOUNDS"
         assert np.array_equal(r.get_positions(), before)
         r.iterate("lsqml", 1)
+
+
+def test_subpixel_checkpoint_with_refined_positions():
+    """A run that refines positions, checkpointed and resumed in a new
+    context (data set with the original positions), ends bit for bit where
+    the uninterrupted run ends."""
+    c = subpixel_scan(32, 1, 8, grid=3, photons=1e6)
+
+    def fresh():
+        r = _recon(c, cluster=1)
+        return r
+
+    with fresh() as a:
+        a.iterate("lsqml", 2)
+        a.refine_positions(step=0.7)
+        a.iterate("lsqml", 2)
+        state = a.checkpoint()
+        a.refine_positions(step=0.7)
+        a.iterate("lsqml", 2)
+        Oa, Pa, pa = a.get_object(), a.get_probe(), a.get_positions()
+    with fresh() as b:
+        b.restore(state)
+        assert np.array_equal(b.get_positions(), state["positions"])
+        b.refine_positions(step=0.7)
+        b.iterate("lsqml", 2)
+        assert np.array_equal(b.get_object(), Oa) and np.array_equal(b.get_probe(), Pa)
+        assert np.array_equal(b.get_positions(), pa)
