@@ -42,6 +42,14 @@ constexpr int PROBE_NT = 256;
 #ifndef PT_STEP_MINB
 #define PT_STEP_MINB 4    // occupancy hint of the LSQML step-size kernel
 #endif
+#ifndef PT_PROBE_UJ
+#define PT_PROBE_UJ 8     // positions per step of the probe sums, K = 1 (8: 0.945 ms vs 1.03 at 4, 1.22 at 16)
+#endif
+#ifndef PT_STEP_UNROLL
+#define PT_STEP_UNROLL 1  // pixel-loop unrolling of the step-size kernel
+#endif
+#define PT_PRAGMA(x) _Pragma(#x)
+#define PT_UNROLL(n) PT_PRAGMA(unroll n)
 constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
 constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
 
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   for (int k = 0; k < K; ++k) num[k] = make_float2(0.f, 0.f);
   float den = 0.f;
   const bool want_den = a.part_den != nullptr;
-  constexpr int UJ = 4;  // positions per step: UJ*(K+1) independent loads in flight
+  constexpr int UJ = K == 1 ? PT_PROBE_UJ : 4;  // positions per step: UJ*(K+1) independent loads in flight
   __shared__ int2 sp[PROBE_CHUNK];
   __shared__ float sw[PROBE_CHUNK];
   __shared__ int sj[SUB ? PROBE_CHUNK : 1];
@@ -472,6 +480,7 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
   // the object pixel pair is 16-byte aligned when the patch's first object
   // column and the row length are even (uniform over the block)
   const bool pairs = ((p.y | a.nx) & 1) == 0;
+  PT_UNROLL(PT_STEP_UNROLL)
   for (; u < MM; u += STEP) {
     const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
     float2 o0, o1, d0, d1;
