@@ -78,7 +78,13 @@ class Clocks:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                                       "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # the timed region is short: let the sampler start before it begins
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.p.poll() is None:
+                if os.path.exists(self.path) and os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
 
     def stop(self):
         if self.p is None:
