@@ -149,3 +149,63 @@ def test_batch_members_with_subpixel_positions(alg):
             r.set_init(c["O0"], c["P0"])
             r.iterate(alg, 3)
             assert np.array_equal(Og, r.get_object()) and np.array_equal(Pg, r.get_probe())
+
+
+def test_batch_full_workload_sampled():
+    """The benchmark's 64-member batch (probe sizes 64-256, 100-4000
+    positions each, autotuned clusters, grouped graph): three sampled members
+    end bit for bit where they end alone, and the smallest member -- its
+    frames from the oracle's forward model -- matches the oracle to 1e-4.
+    Starts are random objects (a flat start makes the first projection
+    ill-conditioned; see test_gpu_configs)."""
+    torch = pytest.importorskip("torch")
+    from paper_2202_03144_b300 import synth
+    members = synth.batch_members(64, seed=7)
+    side = max(max(m["obj_shape"]) for m in members)
+    field = synth.make_object(side, side, seed=4242)
+    field0 = synth.make_object(side, side, seed=4343)
+    probes = {M: synth.make_probe(M, 1, R=0.3125 * M, sigma=M / 16.0, c=0.02 * (64.0 / M) ** 2)
+              for M in sorted(set(m["M"] for m in members))}
+    small = int(np.argmin([m["J"] * m["M"] ** 2 for m in members]))
+    big = next(i for i, m in enumerate(members) if m["M"] == 256)
+    mid = next(i for i, m in enumerate(members) if m["M"] == 96)
+    spec = [dict(M=m["M"], K=1, J=m["J"], obj_shape=m["obj_shape"], cluster=-1) for m in members]
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    data, starts, clusters = [], [], []
+    with api.Batch(spec) as b:
+        for i, (mem, m) in enumerate(zip(b.members, members)):
+            P = probes[m["M"]]
+            ny, nx = m["obj_shape"]
+            if i == small:  # the member checked against the oracle: oracle frames
+                I = orc.far_field_intensity(field[:ny, :nx], P, orc.round_positions(m["positions"]))
+                sc = m["photons"] / I.sum(axis=(1, 2)).mean()
+                I = synth.poisson(I * sc, seed=5).astype(np.float32)
+            else:
+                mem.set_positions(m["positions"])
+                mem.set_init(field[:ny, :nx], P)
+                It = torch.empty((m["J"], m["M"], m["M"]), dtype=torch.float32, device="cuda")
+                mem.simulate(It)
+                torch.cuda.synchronize()
+                sc = m["photons"] / float(It.sum(dim=(1, 2)).mean())
+                I = torch.poisson(It * sc, generator=gen).cpu().numpy()
+                del It
+            data.append(I)
+            starts.append((field0[:ny, :nx], synth.noisy_probe(P * np.sqrt(sc), 0.1, seed=i)))
+            clusters.append(mem.cluster)
+            mem.set_data(I, m["positions"])
+            mem.set_init(*starts[-1])
+        b.iterate("lsqml", 2)
+        got = {i: (b.members[i].get_object(), b.members[i].get_probe()) for i in (small, big, mid)}
+    for i in (small, big, mid):
+        m = members[i]
+        with api.Reconstruction(m["M"], 1, m["J"], m["obj_shape"], cluster=clusters[i]) as r:
+            r.set_data(data[i], m["positions"])
+            r.set_init(*starts[i])
+            r.iterate("lsqml", 2)
+            assert np.array_equal(got[i][0], r.get_object()) and np.array_equal(got[i][1], r.get_probe()), i
+    m = members[small]
+    Oc, Pc, _ = orc.reconstruct("lsqml", starts[small][0], starts[small][1], m["positions"],
+                                data[small].astype(np.float64), 2)
+    mask = illuminated(probes[m["M"]], m["positions"], m["obj_shape"])
+    Og, Pg = got[small]
+    assert rel_l2(align_global(Og, Oc, mask), Oc, mask) < 1e-4 and rel_l2(Pg, Pc) < 1e-4
