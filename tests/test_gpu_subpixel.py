@@ -297,3 +297,39 @@ def test_subpixel_checkpoint_with_refined_positions():
         b.iterate("lsqml", 2)
         assert np.array_equal(b.get_object(), Oa) and np.array_equal(b.get_probe(), Pa)
         assert np.array_equal(b.get_positions(), pa)
+
+
+@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+def test_subpixel_edge_cases(alg):
+    """One position; every position in the same bin (one probe-sum bin holds
+    them all, the other bins are empty); positions exactly on half pixels
+    (the corner rounds up, the shift is -1/2)."""
+    from paper_2202_03144_b300 import synth
+    M, S = 32, 8
+    P = synth_probe(M)
+    O = synth.make_object(72, 72, seed=3, smooth=2.0)
+    # a random start: from a flat one, with so few positions, the oracle
+    # itself moves its probe by ~3e-3 when the start is perturbed by 1e-7
+    O0 = synth.make_object(72, 72, seed=4, smooth=2.0)
+    P0 = synth.noisy_probe(P, 0.1, seed=5)
+    cases = [np.array([[5.3, 7.8]]),
+             np.array([[4.25, 6.25], [9.25, 14.25], [20.25, 3.25], [30.25, 30.25]]),
+             np.array([[4.5, 6.5], [9.5, 14.5], [20.5, 3.5]])]
+    for raw in cases:
+        raw = raw.astype(np.float32).astype(np.float64)
+        corner, delta = orc.subpixel_positions(raw, S)
+        I = orc.far_field_intensity(O, P, corner, delta)
+        with api.Reconstruction(M, 1, len(raw), O.shape, subpixel=S) as r:
+            r.set_data(I.astype(np.float32), raw)
+            r.set_init(O0, P0)
+            r.iterate(alg, 3)
+            Og, Pg = r.get_object(), r.get_probe()
+        Oc, Pc, _ = orc.reconstruct(alg, O0, P0, raw, I, 3, subpixel=S)
+        den = orc.object_denominator(P, corner, O.shape, delta)
+        m = den >= 0.1 * den.max()
+        assert rel_l2(align_global(Og, Oc, m), Oc, m) < TOL_REC and rel_l2(Pg, Pc) < TOL_REC, raw
+
+
+def synth_probe(M):
+    from paper_2202_03144_b300 import synth
+    return synth.make_probe(M, 1, R=M / 4.0, sigma=M / 16.0, c=0.6 / M)
