@@ -242,34 +242,45 @@ def epie_order(seed: int, t: int, J: int) -> np.ndarray:
     return np.asarray(order, dtype=np.int64)
 
 
-def epie_position_update(O, P, y, x, I_fft_j, alpha, beta, update_probe):
+def epie_position_update(O, P, y, x, I_fft_j, alpha, beta, update_probe, shift=None):
     """One ePIE step at the patch with top-left (y, x); updates O and P in place.
 
     psi_k = P_k O_j; Delta_k = F^-1 Pi(F psi)_k - psi_k;
     O_j += alpha sum_k conj(P_k) Delta_k / max_u sum_k |P_k(u)|^2;
     P_k += beta conj(O_j_old) Delta_k / max_u |O_j_old(u)|^2  (if update_probe),
     both from the values held before this step.
+
+    Sub-pixel position (shift = delta_j): the position sees P_j = T_delta P
+    (:func:`shift_probe`), which takes P's place in the exit wave, the object
+    step and its maximum; the probe step is taken in that frame and moved back
+    by the adjoint shift, P_k += beta T_-delta[conj(O_j_old) Delta_k] / max
+    |O_j_old|^2 (the steepest-descent step in P of the same objective).
     """
     M = P.shape[-1]
     Oj = O[y:y + M, x:x + M].copy()
-    psi = P * Oj[None]
+    Pj = P if shift is None else shift_probe(P, shift[0], shift[1])
+    psi = Pj * Oj[None]
     Delta = ifft2(project(fft2(psi)[None], I_fft_j[None])[0]) - psi
-    pmax = float(np.max(np.sum(np.abs(P) ** 2, axis=0)))
+    pmax = float(np.max(np.sum(np.abs(Pj) ** 2, axis=0)))
     omax = float(np.max(np.abs(Oj) ** 2))
     if pmax > 0:
-        O[y:y + M, x:x + M] = Oj + alpha * np.sum(np.conj(P) * Delta, axis=0) / pmax
+        O[y:y + M, x:x + M] = Oj + alpha * np.sum(np.conj(Pj) * Delta, axis=0) / pmax
     if update_probe and omax > 0:
-        P[...] = P + beta * np.conj(Oj)[None] * Delta / omax
+        step = np.conj(Oj)[None] * Delta
+        if shift is not None:
+            step = shift_probe(step, -shift[0], -shift[1])
+        P[...] = P + beta * step / omax
 
 
-def epie_iteration(O, P, pos, I, t, seed=0, alpha=1.0, beta=1.0, probe_start=0):
+def epie_iteration(O, P, pos, I, t, seed=0, alpha=1.0, beta=1.0, probe_start=0, delta=None):
     """One ePIE sweep (iteration index t) over all positions; returns new (O, P)."""
     O = O.astype(np.complex128).copy()
     P = P.astype(np.complex128).copy()
     I_fft = to_fft_order(I)
     for j in epie_order(seed, t, len(pos)):
         y, x = pos[j]
-        epie_position_update(O, P, y, x, I_fft[j], alpha, beta, t >= probe_start)
+        epie_position_update(O, P, y, x, I_fft[j], alpha, beta, t >= probe_start,
+                             None if delta is None else delta[j])
     return O, P
 
 
@@ -649,15 +660,11 @@ def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, re
     the same unitary so that psi_jk stays P_k O_j-shaped.
 
     subpixel: S > 0 quantises the positions to 1/S pixel and shifts the probe
-    by each position's sub-pixel part (:func:`subpixel_positions`); DM and
-    LSQML only (ePIE visits one position at a time and keeps integer
-    positions).
+    by each position's sub-pixel part (:func:`subpixel_positions`).
 
     Returns (O, P, psi) -- psi is the DM state (None for the others)."""
     delta = None
     if subpixel:
-        if alg == "epie":
-            raise ValueError("sub-pixel positions are not supported by ePIE")
         pos, delta = subpixel_positions(positions, subpixel)
     else:
         pos = round_positions(positions)
@@ -666,7 +673,7 @@ def reconstruct(alg: str, O, P, positions, I, n_iter, t0=0, psi=None, seed=0, re
     check_positions(pos, P.shape[-1], *O.shape)
     for t in range(t0, t0 + n_iter):
         if alg == "epie":
-            O, P = epie_iteration(O, P, pos, I, t, seed, epie_alpha, epie_beta, probe_start)
+            O, P = epie_iteration(O, P, pos, I, t, seed, epie_alpha, epie_beta, probe_start, delta)
         elif alg == "dm":
             if psi is None:
                 psi = dm_init(O, P, pos, delta)

@@ -749,6 +749,8 @@ def pin_subpixel_fixed_point_and_reduction(orc):
     O3, P3, psi3 = orc.reconstruct("dm", O, P, raw, I, 1, psi=psi, subpixel=8)
     assert np.allclose(O3, O, atol=1e-12) and np.allclose(P3, P, atol=1e-12) and np.allclose(psi3, psi, atol=1e-12), \
         "sub-pixel DM (probe updated) moved off the truth"
+    O4, P4, _ = orc.reconstruct("epie", O, P, raw, I, 1, seed=3, subpixel=8)
+    assert np.allclose(O4, O, atol=1e-12) and np.allclose(P4, P, atol=1e-12), "sub-pixel ePIE moved off the truth"
     ip = pos.astype(float)
     I2 = orc.far_field_intensity(O, P, pos)
     O0 = np.ones_like(O)
@@ -815,6 +817,62 @@ def pin_position_refinement(orc):
     assert all(b < a for a, b in zip(errs, errs[1:])) and errs[-1] < 0.5 * errs[0], errs
 
 
+def pin_subpixel_epie(orc):
+    """Sub-pixel ePIE: its object and probe corrections are steepest-descent
+    steps of f = 1/2 sum_k ||z_k - (T_delta P_k) O_j||^2 (z the projected
+    target, fixed), with steps alpha / max sum |T_delta P|^2 and
+    beta / max |O_j|^2 (central differences through the shift); with a
+    constant probe (T_delta 1 = 1) the patch moves to the error-reduction
+    step whatever the shift."""
+    rng = np.random.default_rng(28)
+    M, K = 6, 2
+    O = _crandn(8, 8, rng=rng)
+    P = _crandn(K, M, M, rng=rng)
+    raw = np.array([[1.25, 1.625]])
+    pos, delta = orc.subpixel_positions(raw, 8)
+    y, x = pos[0]
+    I = np.abs(_crandn(1, M, M, rng=rng)) ** 2
+    alpha, beta = 0.7, 0.3
+    O1, P1, _ = orc.reconstruct("epie", O, P, raw, I, 1, epie_alpha=alpha, epie_beta=beta, subpixel=8)
+    Oj = O[y:y + M, x:x + M]
+    Pj = orc.shift_probe(P, *delta[0])
+    F = np.fft.fft2(Pj * Oj)
+    A = np.sqrt(np.sum(np.abs(F) ** 2, axis=0))
+    z = np.fft.ifft2(F * np.fft.ifftshift(np.sqrt(I[0]))[None] / A[None])
+
+    def f(Ov, Pv):
+        return 0.5 * np.sum(np.abs(z - orc.shift_probe(Pv, *delta[0]) * Ov[None]) ** 2)
+
+    h = 1e-6
+    gO = np.zeros_like(Oj)
+    for u in range(M):
+        for v in range(M):
+            e = np.zeros_like(Oj)
+            e[u, v] = h
+            gO[u, v] = (f(Oj + e, P) - f(Oj - e, P)) / (2 * h) + 1j * (f(Oj + 1j * e, P) - f(Oj - 1j * e, P)) / (2 * h)
+    pmax = np.max(np.sum(np.abs(Pj) ** 2, axis=0))
+    assert np.allclose(O1[y:y + M, x:x + M] - Oj, -alpha / pmax * gO, atol=1e-6), "sub-pixel ePIE object step"
+    gP = np.zeros_like(P)
+    for k in range(K):
+        for u in range(M):
+            for v in range(M):
+                e = np.zeros_like(P)
+                e[k, u, v] = h
+                gP[k, u, v] = ((f(Oj, P + e) - f(Oj, P - e)) + 1j * (f(Oj, P + 1j * e) - f(Oj, P - 1j * e))) / (2 * h)
+    omax = np.max(np.abs(Oj) ** 2)
+    assert np.allclose(P1 - P, -beta / omax * gP, atol=1e-6), "sub-pixel ePIE probe step"
+    M = 8
+    O = _crandn(12, 12, rng=rng)
+    P1c = np.ones((1, M, M), dtype=complex)
+    raw = np.array([[2.375, 3.125]])
+    (yy, xx), = orc.subpixel_positions(raw, 8)[0]
+    I = np.abs(_crandn(1, M, M, rng=rng)) ** 2
+    O2, _, _ = orc.reconstruct("epie", O, P1c, raw, I, 1, probe_start=5, subpixel=8)
+    ref = O.copy()
+    ref[yy:yy + M, xx:xx + M] = _er_step(O[yy:yy + M, xx:xx + M], I[0])
+    assert np.allclose(O2, ref, atol=1e-12 * np.abs(ref).max()), "sub-pixel ePIE with P = 1 != error reduction"
+
+
 ALL_PINS = [
     pin_fft_bruteforce, pin_parseval, pin_forward_bruteforce, pin_mode_mixing_invariance,
     pin_gather_scatter_adjoint, pin_rounding, pin_projection, pin_fourier_error,
@@ -824,6 +882,6 @@ ALL_PINS = [
     pin_poisson_newton_step, pin_lsqml_poisson, pin_mode_orthogonalisation,
     pin_dm_mode_orthogonalisation_keeps_truth, pin_preprocess, pin_subpixel_positions,
     pin_fourier_shift, pin_subpixel_forward, pin_subpixel_gradients, pin_subpixel_dm_probe_solve,
-    pin_subpixel_step_sizes, pin_position_refinement,
+    pin_subpixel_step_sizes, pin_position_refinement, pin_subpixel_epie,
     pin_subpixel_fixed_point_and_reduction,
 ]

@@ -35,12 +35,14 @@ MUTATIONS = {
     "lsqml_swapped_weights": ("object_numerator(P, chi, pos, O.shape, weights=aO,",
                               "object_numerator(P, chi, pos, O.shape, weights=aP,"),
     "lsqml_lambda_too_big": ("lam = 1e-6 * tr / 2.0", "lam = 1e-3 * tr / 2.0"),
-    "epie_no_conj_probe": ("alpha * np.sum(np.conj(P) * Delta, axis=0) / pmax",
-                           "alpha * np.sum(P * Delta, axis=0) / pmax"),
-    "epie_sum_not_max": ("pmax = float(np.max(np.sum(np.abs(P) ** 2, axis=0)))",
-                         "pmax = float(np.sum(np.abs(P) ** 2))"),
-    "epie_probe_from_new_object": ("P[...] = P + beta * np.conj(Oj)[None] * Delta / omax",
-                                   "P[...] = P + beta * np.conj(O[y:y + M, x:x + M])[None] * Delta / omax"),
+    "epie_no_conj_probe": ("alpha * np.sum(np.conj(Pj) * Delta, axis=0) / pmax",
+                           "alpha * np.sum(Pj * Delta, axis=0) / pmax"),
+    "epie_sum_not_max": ("pmax = float(np.max(np.sum(np.abs(Pj) ** 2, axis=0)))",
+                         "pmax = float(np.sum(np.abs(Pj) ** 2))"),
+    "epie_probe_from_new_object": ("step = np.conj(Oj)[None] * Delta",
+                                   "step = np.conj(O[y:y + M, x:x + M])[None] * Delta"),
+    "epie_subpixel_probe_unshifted": ("Pj = P if shift is None else shift_probe(P, shift[0], shift[1])", "Pj = P"),
+    "epie_subpixel_no_adjoint": ("step = shift_probe(step, -shift[0], -shift[1])", "step = step"),
     "error_den_sqrt": ("den = float(np.sum(np.where(m, I_fft, 0.0)))",
                        "den = float(np.sum(np.where(m, sqrtI, 0.0)))"),
     "splitmix_constant": ("0xBF58476D1CE4E5B9", "0xBF58476D1CE4E5B8"),
