@@ -296,16 +296,20 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
                                      "measured against the FP32 data", "check_every": check, **out}
 
 
-def run_epie(api, torch, stream, iters=3, warm=1):
+def run_epie(api, torch, stream, iters=3, warm=1, subpixel=0):
     """ePIE (sequential by definition) on the 3-mode 128^2 spiral scan:
     positions*iterations/s of the persistent single-cluster sweep (on the
-    widest compiled cluster: its latency per position bounds the sweep)."""
+    widest compiled cluster: its latency per position bounds the sweep).
+    subpixel = S: the same scan at fractional positions, 1/S-pixel shifts
+    (one position at a time through the general kernels)."""
     from paper_2202_03144_b300 import synth
     d = synth.scan_config("modes128", seed=5)
     M, K, pos = d["M"], d["K"], d["positions"]
+    if subpixel:
+        pos = synth.fractional_positions(pos, seed=2005)
     shape = d["object"].shape
     with torch.cuda.stream(stream):
-        r = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream, seed=1)
+        r = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream, seed=1, subpixel=subpixel)
         r.set_positions(pos)
         r.set_init(d["object"], d["probe"])
         I = torch.empty((len(pos), M, M), dtype=torch.float32, device="cuda")
@@ -324,12 +328,15 @@ def run_epie(api, torch, stream, iters=3, warm=1):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        cl = r.epie_cluster
+        cl = r.epie_cluster if not subpixel else r.cluster
         E = r.fourier_error()
         r.close()
-    return {"value": len(pos) * iters / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms / iters,
-            "cluster": cl, "fourier_error": E,
-            "workload": "ePIE, 1600-position Fermat spiral, 3-mode 128^2 probe, 1088^2 object, Poisson 1e5"}
+    out = {"value": len(pos) * iters / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms / iters,
+           "cluster": cl, "fourier_error": E,
+           "workload": "ePIE, 1600-position Fermat spiral, 3-mode 128^2 probe, 1088^2 object, Poisson 1e5"}
+    if subpixel:
+        out["workload"] += f", fractional positions at 1/{subpixel} px"
+    return out
 
 
 def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, check=5):
@@ -616,6 +623,8 @@ def main():
     t2e = None if (args.no_eps or profiling_run) else time_to_eps(api, torch, stream, I, pos, P0s, w)
     del I
     epie = None if profiling_run else run_epie(api, torch, stream)
+    if epie is not None:
+        epie["subpixel"] = run_epie(api, torch, stream, subpixel=SUBPIXEL)
     warm = None if (args.no_warm or profiling_run) else run_warm_start(api, torch, stream, n_frames=args.warm_frames)
     if rank != 0:
         if dist:

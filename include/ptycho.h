@@ -123,10 +123,13 @@ typedef struct {
                        sum_j T_j^H |O_j|^2 T_j P + d P = rhs by 4
                        preconditioned conjugate-gradient iterations from the
                        current probe (the diagonal form makes the difference
-                       map diverge).  DM and LSQML (and the Fourier error /
-                       simulation / residual calls); ePIE returns
-                       PTYCHO_ERR_UNSUPPORTED.  Device memory: three tables
-                       of S^2 K M^2 complex values and S^2 M^2 floats.       */
+                       map diverge).  ePIE takes each position's probe step
+                       in its shifted frame and moves it back with the
+                       adjoint shift, one position at a time through the
+                       general kernels (slower than the whole-pixel sweep).
+                       All algorithms, the Fourier error, simulation and
+                       residual calls.  Device memory: three tables of
+                       S^2 K M^2 complex values and S^2 M^2 floats.          */
   int block_positions; /* 0 (default): the residuals of all J positions stay
                        in device memory (J K M^2 complex values).  B > 0 (and
                        < J): LSQML keeps those of B positions at a time, for

@@ -1,0 +1,59 @@
+// Sub-pixel ePIE: the per-position steps around the Fourier pass.  With the
+// probe seen at position j, P_j = T_delta_j P (a single-bin shift), and
+// Delta = F^-1 Pi(F(P_j O_j)) - P_j O_j from the residual pass:
+//   pmax = max_u sum_k |P_j,k(u)|^2,  omax = max_u |O_j(u)|^2      (k_epie_sub_max)
+//   O_j  += alpha sum_k conj(P_j,k) Delta_k / pmax                (k_epie_sub_update)
+//   step_k = beta conj(O_j_old) Delta_k / omax                    (k_epie_sub_update)
+//   P_k  += T_-delta_j[step_k]                                    (single-bin adjoint shift, accumulated)
+#pragma once
+#include "common.cuh"
+
+namespace ptycho {
+
+constexpr int EPS_NT = 1024;
+
+template <int K>
+__global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restrict__ Pj, const float2* __restrict__ O,
+                                                         int nx, const int2* __restrict__ pos, int j, int M,
+                                                         float2* __restrict__ out) {
+  __shared__ float red[32];
+  const int2 p = pos[j];
+  const int MM = M * M;
+  float pm = 0.f, om = 0.f;
+  for (int u = threadIdx.x; u < MM; u += EPS_NT) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) s += cabs2(Pj[(size_t)k * MM + u]);
+    pm = fmaxf(pm, s);
+    om = fmaxf(om, cabs2(O[(size_t)(p.x + u / M) * nx + p.y + u % M]));
+  }
+  pm = block_max_f<EPS_NT>(pm, red);
+  om = block_max_f<EPS_NT>(om, red);
+  if (threadIdx.x == 0) out[0] = make_float2(pm, om);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O, int nx, const int2* __restrict__ pos,
+                                                         int j, int M, const float2* __restrict__ Pj,
+                                                         const float2* __restrict__ D, const float2* __restrict__ mx,
+                                                         float alpha, float beta, int upd, float2* __restrict__ step) {
+  const int2 p = pos[j];
+  const int MM = M * M;
+  const float pmax = mx[0].x, omax = mx[0].y;
+  const float sa = pmax > 0.f ? alpha / pmax : 0.f;
+  const float sb = (upd && omax > 0.f) ? beta / omax : 0.f;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < MM; u += gridDim.x * blockDim.x) {
+    float2* op = O + (size_t)(p.x + u / M) * nx + p.y + u % M;
+    const float2 o = *op;
+    float2 num = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 d = D[(size_t)k * MM + u];
+      num = cadd(num, cconjmul(Pj[(size_t)k * MM + u], d));
+      if (upd) step[(size_t)k * MM + u] = cscale(cconjmul(o, d), sb);
+    }
+    *op = cadd(o, cscale(num, sa));
+  }
+}
+
+}  // namespace ptycho

@@ -30,6 +30,7 @@
 #include "overlap.cuh"
 #include "shift.cuh"
 #include "probe_cg.cuh"
+#include "epie_sub.cuh"
 
 using namespace ptycho;
 
@@ -352,6 +353,11 @@ struct ptycho_ctx {
     int j0 = 0, n = 0;
     bool accumulate = false;
   } blk;
+  // a Fourier pass with an explicit probe (no table) and residual offset:
+  // the sub-pixel ePIE sweep, one position at a time
+  const float2* f_P = nullptr;
+  int f_xoff = -1;
+  std::vector<unsigned short> bin_host;  // sub-pixel bin of each position
   std::vector<float> pos_f;    // positions as last set (or refined), [J][2]
   float2* ppart = nullptr;
   float* ppart_den = nullptr;
@@ -524,13 +530,14 @@ const unsigned short* bin_view(const ptycho_ctx* ctx);
 // Every Fourier pass reads the probe as it is now: with sub-pixel positions
 // the shifted table is rebuilt first.
 int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, int nj, const char* name) {
-  if (int r = refresh_probe_table(ctx)) return r;
+  if (!ctx->f_P)
+    if (int r = refresh_probe_table(ctx)) return r;
   const KernelSet* ks = ctx->ks;
   Fourier2Args a{};
   a.O = ctx->O;
   a.nx = ctx->p.obj_nx;
-  a.P = probe_view(ctx);
-  a.pbin = bin_view(ctx);
+  a.P = ctx->f_P ? ctx->f_P : probe_view(ctx);
+  a.pbin = ctx->f_P ? nullptr : bin_view(ctx);
   a.pos = ctx->pos;
   a.X = X;
   a.amp = ctx->amp;
@@ -541,7 +548,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   a.tw2 = ctx->tw2;
   a.err_flag = ctx->err_flag;
   a.j0 = j0;
-  a.xoff = (ctx->blk.on && X == ctx->X) ? ctx->blk.j0 : 0;
+  a.xoff = ctx->f_xoff >= 0 ? ctx->f_xoff : ((ctx->blk.on && X == ctx->X) ? ctx->blk.j0 : 0);
   a.mode = mode;
   const double MM = (double)ctx->p.M * ctx->p.M;
   const double K = ctx->p.K;
@@ -597,8 +604,9 @@ int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) 
   const double tab = 8.0 * S * S * K * (double)M * M;
   if (build) {
     if (int r = launch(ctx, "shift_build", tab, [&] {
-          k_shift_build_rows<M, LN><<<dim3(K * M / LN, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw);
-          k_shift_build_cols<M, LN><<<dim3(M / LN, K, S * S), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw);
+          k_shift_build_rows<M, LN><<<dim3(K * M / LN, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, -1, 1);
+          k_shift_build_cols<M, LN><<<dim3(M / LN, K, S * S), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, -1,
+                                                                                 1, 0);
         }))
       return r;
     return 0;
@@ -607,6 +615,31 @@ int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) 
     k_shift_sum_cols<M, LN><<<dim3(M / LN, K, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->bgrp, ctx->tw);
     k_shift_sum_rows<M, LN><<<dim3(K * M / LN), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw);
   });
+}
+
+// One bin: dst[k] = T_(sgn delta(bin)) src[k] (accumulate: dst[k] += ...).
+template <int M>
+int launch_shift_one_m(ptycho_ctx* ctx, int bin, int sgn, bool accumulate, const float2* src, float2* dst) {
+  constexpr int LN = 8;
+  const int K = ctx->p.K, S = ctx->S;
+  return launch(ctx, "shift_one", 16.0 * K * (double)M * M, [&] {
+    k_shift_build_rows<M, LN><<<dim3(K * M / LN, 1), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, bin, sgn);
+    k_shift_build_cols<M, LN><<<dim3(M / LN, K, 1), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, bin, sgn,
+                                                                         accumulate ? 1 : 0);
+  });
+}
+
+int launch_shift_one(ptycho_ctx* ctx, int bin, int sgn, bool accumulate, const float2* src, float2* dst) {
+  switch (ctx->p.M) {
+    case 16: return launch_shift_one_m<16>(ctx, bin, sgn, accumulate, src, dst);
+    case 32: return launch_shift_one_m<32>(ctx, bin, sgn, accumulate, src, dst);
+    case 64: return launch_shift_one_m<64>(ctx, bin, sgn, accumulate, src, dst);
+    case 96: return launch_shift_one_m<96>(ctx, bin, sgn, accumulate, src, dst);
+    case 128: return launch_shift_one_m<128>(ctx, bin, sgn, accumulate, src, dst);
+    case 192: return launch_shift_one_m<192>(ctx, bin, sgn, accumulate, src, dst);
+    case 256: return launch_shift_one_m<256>(ctx, bin, sgn, accumulate, src, dst);
+    default: return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "sub-pixel shifts are not compiled for M=%d", ctx->p.M);
+  }
 }
 
 // build: dst[bin][k] = T_delta(bin) src[k];  sum: dst[k] = sum_bin T_-delta(bin) src[bin][k]
@@ -1045,12 +1078,9 @@ int run_lsqml(ptycho_ctx* ctx, int n) {
   return 0;
 }
 
-int run_epie(ptycho_ctx* ctx, int n) {
-  if (ctx->S)
-    return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE takes integer positions (create with subpixel = 0)");
-  if (!ctx->epie_ok)
-    return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE kernel for M=%d K=%d cluster=%d exceeds shared memory; use a larger cluster",
-                ctx->p.M, ctx->p.K, ctx->eks ? ctx->eks->C : ctx->C);
+// Visiting order of iterations t .. t + n - 1: identity for seed 0, else a
+// Durstenfeld shuffle driven by SplitMix64(seed XOR t).
+std::vector<int> epie_orders(const ptycho_ctx* ctx, int n) {
   const int J = ctx->p.J;
   std::vector<int> ord((size_t)n * J);
   for (int it = 0; it < n; ++it) {
@@ -1064,6 +1094,65 @@ int run_epie(ptycho_ctx* ctx, int n) {
       }
     }
   }
+  return ord;
+}
+
+// Sub-pixel ePIE: one position at a time through the general kernels -- the
+// probe this position sees (a single-bin shift), the residual pass of one
+// position, the maxima, the object update and probe step, and the probe step
+// moved back by the adjoint shift and added to the probe.  Seven launches per
+// position, all on the context stream.
+template <int K>
+int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
+  const int J = ctx->p.J, M = ctx->p.M, MM = M * M;
+  const std::vector<int> ord = epie_orders(ctx, n);
+  float2* Pj = ctx->Pt;        // slot 0 of the table: the shifted probe
+  float2* D = ctx->cg_q;       // the position's residual
+  float2* step = ctx->cg_r;    // the probe step in the position's frame
+  float2* mx = ctx->pos_corr;  // (pmax, omax)
+  for (int it = 0; it < n; ++it) {
+    const bool upd = ctx->t + it >= ctx->p.probe_start;
+    for (int s = 0; s < J; ++s) {
+      const int j = ord[(size_t)it * J + s];
+      const int bin = ctx->bin_host[j];
+      if (int r = launch_shift_one(ctx, bin, 1, false, ctx->P, Pj)) return r;
+      ctx->f_P = Pj;
+      ctx->f_xoff = j;
+      int r = launch_fourier(ctx, FM_CHI, D, nullptr, j, 1, "fourier_epie");
+      ctx->f_P = nullptr;
+      ctx->f_xoff = -1;
+      if (r) return r;
+      if (int rr = launch(ctx, "epie_update", 8.0 * (3 * K + 2) * MM, [&] {
+            k_epie_sub_max<K><<<1, EPS_NT, 0, ctx->st>>>(Pj, ctx->O, ctx->p.obj_nx, ctx->pos, j, M, mx);
+            k_epie_sub_update<K><<<(MM + 255) / 256, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->pos, j, M, Pj, D,
+                                                                         mx, (float)ctx->p.epie_alpha,
+                                                                         (float)ctx->p.epie_beta, upd ? 1 : 0, step);
+          }))
+        return rr;
+      if (upd)
+        if (int rr = launch_shift_one(ctx, bin, -1, true, step, ctx->P)) return rr;
+    }
+    if (upd && ctx->p.probe_ortho && K > 1)
+      if (int r = ortho_step(ctx, false)) return r;
+  }
+  ctx->t += n;
+  ctx->psi_valid = false;
+  return 0;
+}
+
+int run_epie(ptycho_ctx* ctx, int n) {
+  if (ctx->S) {
+    switch (ctx->p.K) {
+      case 1: return run_epie_subpixel_k<1>(ctx, n);
+      case 2: return run_epie_subpixel_k<2>(ctx, n);
+      default: return run_epie_subpixel_k<3>(ctx, n);
+    }
+  }
+  if (!ctx->epie_ok)
+    return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "ePIE kernel for M=%d K=%d cluster=%d exceeds shared memory; use a larger cluster",
+                ctx->p.M, ctx->p.K, ctx->eks ? ctx->eks->C : ctx->C);
+  const int J = ctx->p.J;
+  const std::vector<int> ord = epie_orders(ctx, n);
   if ((size_t)ctx->order_cap < ord.size()) {
     if (ctx->order) cudaFree(ctx->order);
     ctx->order = nullptr;
@@ -1228,6 +1317,7 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
     if (int r = dalloc(ctx, &ctx->cg_part, 3 * ((KMM + CG_NT - 1) / CG_NT))) return r;
     if (int r = dalloc(ctx, &ctx->pos_corr, (size_t)J)) return r;
     CK(cudaMemcpy(ctx->pbin, bin.data(), J * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    ctx->bin_host = bin;
     if (int r = build_subpixel_groups(ctx, bin)) return r;
   }
   // CSR lists of positions per object tile, ascending position index

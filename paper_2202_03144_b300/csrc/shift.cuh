@@ -17,6 +17,11 @@
 //          rows: out[k]     = sum_bx T_x(-dx(bx)) tmp[bx][k]
 // The fan-in sums are taken in the frequency domain (one inverse FFT per line)
 // and skip bins that hold no position.
+//
+// Single-bin form (one_bin >= 0, the sub-pixel ePIE sweep): the build kernels
+// shift the K source arrays by the one bin's delta times sgn (+1: T_delta,
+// -1: its adjoint T_-delta) into slot 0, and the column pass may add its
+// result to the output instead of storing it.
 #pragma once
 #include "common.cuh"
 #include "fourier2.cuh"
@@ -58,15 +63,19 @@ __device__ __forceinline__ void sh_load_tw(float2* tw_s, const float2* tw) {
   for (int i = threadIdx.x; i < M; i += SH_NT) tw_s[i] = tw[i];
 }
 
-// build, rows: grid (K*M/LN, S).  tmp[bx][k][y][:] = T_x(dx(bx)) src[k][y][:]
+// build, rows: grid (K*M/LN, S) (single bin: (K*M/LN, 1)).
+// tmp[bx][k][y][:] = T_x(dx(bx)) src[k][y][:]
 template <int M, int LN>
 __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __restrict__ src, float2* __restrict__ tmp,
-                                                            int K, int S, const float2* __restrict__ tw) {
+                                                            int K, int S, const float2* __restrict__ tw,
+                                                            int one_bin, int sgn) {
   using C = ShCfg<M, LN>;
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
   sh_load_tw<M>(tw_s, tw);
-  const int row0 = blockIdx.x * LN, bx = blockIdx.y;
+  const int row0 = blockIdx.x * LN;
+  const int bx = one_bin >= 0 ? one_bin % S : (int)blockIdx.y;
+  const int slot = one_bin >= 0 ? 0 : bx;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
     s[l * C::PITCH + i] = src[(size_t)(row0 + l) * M + i];
@@ -75,28 +84,32 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __rest
   sh_fft<M, LN, false>(s, tw_s);
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
-    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, bx, S, 1));
+    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, bx, S, sgn));
   }
   __syncthreads();
   sh_fft<M, LN, true>(s, tw_s);
-  float2* dst = tmp + (size_t)bx * K * M * M;
+  float2* dst = tmp + (size_t)slot * K * M * M;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
     dst[(size_t)(row0 + l) * M + i] = s[l * C::PITCH + i];
   }
 }
 
-// build, columns: grid (M/LN, K, S*S).  tab[by S + bx][k][:][x] = T_y(dy(by)) tmp[bx][k][:][x]
+// build, columns: grid (M/LN, K, S*S) (single bin: (M/LN, K, 1)).
+// tab[by S + bx][k][:][x] = T_y(dy(by)) tmp[bx][k][:][x]  (accumulate: +=)
 template <int M, int LN>
 __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __restrict__ tmp, float2* __restrict__ tab,
-                                                            int K, int S, const float2* __restrict__ tw) {
+                                                            int K, int S, const float2* __restrict__ tw,
+                                                            int one_bin, int sgn, int accumulate) {
   using C = ShCfg<M, LN>;
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
   sh_load_tw<M>(tw_s, tw);
-  const int c0 = blockIdx.x * LN, k = blockIdx.y, b = blockIdx.z;
+  const int c0 = blockIdx.x * LN, k = blockIdx.y;
+  const int b = one_bin >= 0 ? one_bin : (int)blockIdx.z;
   const int by = b / S, bx = b % S;
-  const float2* in = tmp + ((size_t)bx * K + k) * M * M;
+  const int in_slot = one_bin >= 0 ? 0 : bx, out_slot = one_bin >= 0 ? 0 : b;
+  const float2* in = tmp + ((size_t)in_slot * K + k) * M * M;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int i = e / LN, l = e % LN;   // row i, column c0 + l
     s[l * C::PITCH + i] = in[(size_t)i * M + c0 + l];
@@ -105,14 +118,15 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __rest
   sh_fft<M, LN, false>(s, tw_s);
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
-    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, by, S, 1));
+    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, by, S, sgn));
   }
   __syncthreads();
   sh_fft<M, LN, true>(s, tw_s);
-  float2* out = tab + ((size_t)b * K + k) * M * M;
+  float2* out = tab + ((size_t)out_slot * K + k) * M * M;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int i = e / LN, l = e % LN;
-    out[(size_t)i * M + c0 + l] = s[l * C::PITCH + i];
+    const size_t o = (size_t)i * M + c0 + l;
+    out[o] = accumulate ? cadd(out[o], s[l * C::PITCH + i]) : s[l * C::PITCH + i];
   }
 }
 

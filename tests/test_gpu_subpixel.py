@@ -56,13 +56,13 @@ def test_subpixel_residual_and_error(M, K, C, S):
     assert abs(E - E_ref) <= 1e-5 * E_ref
 
 
-def _compare(c, alg, n, cluster=0, probe_start=0, **kw):
-    with _recon(c, cluster=cluster, probe_start=probe_start, **kw) as r:
+def _compare(c, alg, n, cluster=0, probe_start=0, seed=0, **kw):
+    with _recon(c, cluster=cluster, probe_start=probe_start, seed=seed, **kw) as r:
         r.iterate(alg, n)
         Og, Pg = r.get_object(), r.get_probe()
         E = r.fourier_error()
         psi = r.get_exit_waves() if alg == "dm" else None
-    Oc, Pc, psic = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, probe_start=probe_start,
+    Oc, Pc, psic = orc.reconstruct(alg, c["O0"], c["P0"], c["pos"], c["I"], n, probe_start=probe_start, seed=seed,
                                    subpixel=c["S"], **{k: v for k, v in kw.items() if k in ("likelihood", "probe_ortho")})
     m = _illuminated(c)
     out = dict(eo=rel_l2(align_global(Og, Oc, m), Oc, m), ep=rel_l2(Pg, Pc), E=E,
@@ -76,6 +76,8 @@ ALG_CASES = [
     ("dm", 32, 1, 1, 8), ("dm", 32, 3, 4, 4), ("dm", 16, 2, 1, 2), ("dm", 96, 1, 2, 16),
     ("lsqml", 32, 1, 1, 8), ("lsqml", 32, 3, 4, 16), ("lsqml", 64, 1, 2, 4), ("lsqml", 16, 3, 2, 2),
     ("lsqml", 192, 1, 4, 8), ("lsqml", 256, 1, 8, 8), ("dm", 128, 3, 8, 8),
+    ("epie", 32, 1, 1, 8), ("epie", 32, 3, 4, 4), ("epie", 64, 1, 2, 16), ("epie", 96, 1, 2, 8),
+    ("epie", 128, 3, 8, 8), ("epie", 16, 2, 1, 2),
 ]
 
 
@@ -85,7 +87,7 @@ def test_subpixel_algorithm_parity(alg, M, K, C, S, n):
     if M >= 128 and n > 1:
         n = 3
     c = subpixel_scan(M, K, S, grid=3, photons=1e6, mask_frac=0.02)
-    res = _compare(c, alg, n, cluster=C)
+    res = _compare(c, alg, n, cluster=C, seed=7 if alg == "epie" else 0)
     assert res["eo"] < TOL_REC, res
     assert res["ep"] < TOL_REC, res
     # E is evaluated at each side's own (O, P): besides the 1e-5 of one pass it
@@ -97,7 +99,7 @@ def test_subpixel_algorithm_parity(alg, M, K, C, S, n):
         assert res["epsi"] < TOL_REC, res
 
 
-@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+@pytest.mark.parametrize("alg", ["dm", "lsqml", "epie"])
 def test_subpixel_fixed_probe_then_update(alg):
     c = subpixel_scan(32, 2, 8, grid=3, photons=1e6)
     res = _compare(c, alg, 4, probe_start=2)
@@ -159,13 +161,20 @@ def test_subpixel_integral_positions_match_integer_path():
     assert rel_l2(out[1][0], out[0][0]) < 1e-5 and rel_l2(out[1][1], out[0][1]) < 1e-5
 
 
-def test_subpixel_epie_unsupported_and_bad_params():
-    c = subpixel_scan(32, 1, 8, grid=2)
-    with _recon(c) as r:
-        with pytest.raises(api.PtychoError) as e:
-            r.iterate("epie", 1)
-        assert e.value.name == "UNSUPPORTED"
-        r.iterate("lsqml", 1)   # the context stays usable
+def test_subpixel_epie_step_equals_whole_and_bad_params():
+    """Sub-pixel ePIE: n sweeps in one call equal n calls of one sweep, bit for
+    bit (the order depends on the iteration index), and the probe is
+    orthogonalised after each sweep when asked."""
+    c = subpixel_scan(32, 3, 8, grid=3, photons=1e5)
+    with _recon(c, cluster=4, seed=5) as a:
+        a.iterate("epie", 3)
+        Oa, Pa = a.get_object(), a.get_probe()
+    with _recon(c, cluster=4, seed=5) as b:
+        for _ in range(3):
+            b.iterate("epie", 1)
+        assert np.array_equal(Oa, b.get_object()) and np.array_equal(Pa, b.get_probe())
+    res = _compare(c, "epie", 2, cluster=4, seed=5, probe_ortho=True)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
     for S in (1, 3, 6, 32, -2):
         with pytest.raises(api.PtychoError) as e:
             api.Reconstruction(32, 1, 4, (64, 64), subpixel=S)
@@ -299,7 +308,7 @@ def test_subpixel_checkpoint_with_refined_positions():
         assert np.array_equal(b.get_positions(), pa)
 
 
-@pytest.mark.parametrize("alg", ["dm", "lsqml"])
+@pytest.mark.parametrize("alg", ["dm", "lsqml", "epie"])
 def test_subpixel_edge_cases(alg):
     """One position; every position in the same bin (one probe-sum bin holds
     them all, the other bins are empty); positions exactly on half pixels
