@@ -82,3 +82,28 @@ def test_modes128_workload(modes128, alg, n):
     # each side's E at its own (O, P): 1e-5 plus the first-order propagation
     # of their difference, 2 rel(A) / sqrt(E), rel(A) <= eo + ep
     assert abs(Eg - Ec) <= (1e-5 + 4.0 * max(eo, ep) / np.sqrt(Ec)) * Ec
+
+
+def test_modes128_workload_subpixel_epie(modes128):
+    """One ePIE sweep of the 3-mode spiral at fractional positions (1/8 px),
+    frames from the oracle's sub-pixel forward model, against the oracle."""
+    d, _, O0, P0 = modes128
+    pos = synth.fractional_positions(d["positions"], seed=2005)
+    corner, delta = orc.subpixel_positions(pos, 8)
+    I = orc.far_field_intensity(d["object"], d["probe"], corner, delta)
+    sc = d["photons"] / I.sum(axis=(1, 2)).mean()
+    I = synth.poisson(I * sc, seed=9)
+    P0 = synth.noisy_probe(d["probe"] * np.sqrt(sc), 0.1, seed=8)
+    with api.Reconstruction(d["M"], d["K"], len(pos), d["object"].shape, seed=7, subpixel=8) as r:
+        r.set_data(I.astype(np.float32), pos)
+        r.set_init(O0, P0)
+        r.iterate("epie", 1)
+        Og, Pg, Eg = r.get_object(), r.get_probe(), r.fourier_error()
+    Oc, Pc, _ = orc.reconstruct("epie", O0, P0, pos, I, 1, seed=7, subpixel=8)
+    den = orc.object_denominator(d["probe"], corner, d["object"].shape, delta)
+    m = den >= 0.1 * den.max()
+    eo = rel_l2(align_global(Og, Oc, m), Oc, m)
+    ep = rel_l2(Pg, Pc)
+    assert eo < 1e-4 and ep < 1e-4, (eo, ep)
+    Ec = orc.fourier_error(Oc, Pc, corner, I, delta=delta)
+    assert abs(Eg - Ec) <= (1e-5 + 4.0 * max(eo, ep) / np.sqrt(Ec)) * Ec
