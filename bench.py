@@ -469,12 +469,12 @@ def main():
     stream.synchronize()
 
     def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False, likelihood="amplitude",
-              subpixel=0, block_positions=0):
+              subpixel=0, block_positions=0, fractional_data=None):
         with torch.cuda.stream(stream):
             r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore,
                                    cluster=args.cluster, likelihood=likelihood, subpixel=subpixel,
                                    block_positions=block_positions)
-            if subpixel:
+            if subpixel or fractional_data:
                 r.set_data(I_sub, pos_sub)
             else:
                 r.set_data(I, pos)
@@ -514,6 +514,8 @@ def main():
     bf16_run = timed("lsqml", istore="bf16")
     poisson_run = timed("lsqml", likelihood="poisson")
     sub_run = timed("lsqml", subpixel=SUBPIXEL)
+    # the same fractional-position data under the whole-pixel model (positions rounded)
+    sub_rounded = timed("lsqml", fractional_data=True)
     sub_dm_run = timed("dm", subpixel=SUBPIXEL)
     blk_run = timed("lsqml", block_positions=J // 4)
     prof_run = timed("lsqml", steps=3, warm=1, profile=True)
@@ -650,6 +652,7 @@ def main():
             "lsqml_bf16": {"value": rate(bf16_run), "fourier_error": bf16_run["err"]},
             f"lsqml_subpixel{SUBPIXEL}_f32": {"value": rate(sub_run), "fourier_error": sub_run["err"],
                                               "positions": "whole-pixel raster + uniform [0, 1) offsets",
+                                              "fourier_error_rounded_positions": sub_rounded["err"],
                                               "refine_positions_ms": sub_run["refine_ms"]},
             f"dm_subpixel{SUBPIXEL}_f32": {"value": rate(sub_dm_run), "fourier_error": sub_dm_run["err"]},
             "lsqml_blocked_f32": {"value": rate(blk_run), "fourier_error": blk_run["err"],
