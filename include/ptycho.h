@@ -74,7 +74,8 @@ enum { PTYCHO_LIK_AMPLITUDE = 0, PTYCHO_LIK_POISSON = 1 };
 
 typedef struct {
   int M;            /* probe / detector side in pixels (16, 32, 64, 96, 128,
-                       192, 256; 96 and 192 without ePIE)                    */
+                       192, 256; for 96 and 192 ePIE runs only with
+                       subpixel > 0, through the general kernels)            */
   int K;            /* number of incoherent probe modes (1..3), Sec. 2.2       */
   int J;            /* number of scan positions (diffraction frames)          */
   int obj_ny;       /* object rows                                            */
