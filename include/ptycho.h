@@ -125,8 +125,9 @@ typedef struct {
                        preconditioned conjugate-gradient iterations from the
                        current probe (the diagonal form makes the difference
                        map diverge).  ePIE takes each position's probe step
-                       in its shifted frame and moves it back with the
-                       adjoint shift, one position at a time through the
+                       in its shifted frame (the probe is carried from one
+                       position's frame to the next by the difference of
+                       their shifts), one position at a time through the
                        general kernels (slower than the whole-pixel sweep).
                        All algorithms, the Fourier error, simulation and
                        residual calls.  Device memory: three tables of

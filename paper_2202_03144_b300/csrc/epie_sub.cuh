@@ -1,10 +1,11 @@
-// Sub-pixel ePIE: the per-position steps around the Fourier pass.  With the
-// probe seen at position j, P_j = T_delta_j P (a single-bin shift), and
-// Delta = F^-1 Pi(F(P_j O_j)) - P_j O_j from the residual pass:
+// Sub-pixel ePIE: the per-position steps around the Fourier pass.  The probe
+// is held in the frame of position j, P_j = T_delta_j P, and
+// Delta = F^-1 Pi(F(P_j O_j)) - P_j O_j comes from the residual pass:
 //   pmax = max_u sum_k |P_j,k(u)|^2,  omax = max_u |O_j(u)|^2      (k_epie_sub_max)
-//   O_j  += alpha sum_k conj(P_j,k) Delta_k / pmax                (k_epie_sub_update)
-//   step_k = beta conj(O_j_old) Delta_k / omax                    (k_epie_sub_update)
-//   P_k  += T_-delta_j[step_k]                                    (single-bin adjoint shift, accumulated)
+//   O_j   += alpha sum_k conj(P_j,k) Delta_k / pmax               (k_epie_sub_update)
+//   P_j,k += beta conj(O_j_old) Delta_k / omax                    (k_epie_sub_update)
+// -- the probe step in position j's frame; T_-delta_j of it is the step of
+// the unshifted probe, and the frame is changed by shifts between positions.
 #pragma once
 #include "common.cuh"
 
@@ -34,9 +35,9 @@ __global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restric
 
 template <int K>
 __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O, int nx, const int2* __restrict__ pos,
-                                                         int j, int M, const float2* __restrict__ Pj,
+                                                         int j, int M, float2* __restrict__ Pj,
                                                          const float2* __restrict__ D, const float2* __restrict__ mx,
-                                                         float alpha, float beta, int upd, float2* __restrict__ step) {
+                                                         float alpha, float beta, int upd) {
   const int2 p = pos[j];
   const int MM = M * M;
   const float pmax = mx[0].x, omax = mx[0].y;
@@ -49,8 +50,9 @@ __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const float2 d = D[(size_t)k * MM + u];
-      num = cadd(num, cconjmul(Pj[(size_t)k * MM + u], d));
-      if (upd) step[(size_t)k * MM + u] = cscale(cconjmul(o, d), sb);
+      const float2 pk = Pj[(size_t)k * MM + u];
+      num = cadd(num, cconjmul(pk, d));
+      if (upd) Pj[(size_t)k * MM + u] = cadd(pk, cscale(cconjmul(o, d), sb));
     }
     *op = cadd(o, cscale(num, sa));
   }

@@ -604,9 +604,9 @@ int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) 
   const double tab = 8.0 * S * S * K * (double)M * M;
   if (build) {
     if (int r = launch(ctx, "shift_build", tab, [&] {
-          k_shift_build_rows<M, LN><<<dim3(K * M / LN, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, -1, 1);
-          k_shift_build_cols<M, LN><<<dim3(M / LN, K, S * S), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, -1,
-                                                                                 1, 0);
+          k_shift_build_rows<M, LN><<<dim3(K * M / LN, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, 0, 0);
+          k_shift_build_cols<M, LN><<<dim3(M / LN, K, S * S), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, 0,
+                                                                                 0, 0);
         }))
       return r;
     return 0;
@@ -617,27 +617,27 @@ int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) 
   });
 }
 
-// One bin: dst[k] = T_(sgn delta(bin)) src[k] (accumulate: dst[k] += ...).
+// One shift: dst[k] = T_delta src[k], delta = (bye - S/2, bxe - S/2) / S
+// (src and dst may be the same array: the row pass goes through stmp).
 template <int M>
-int launch_shift_one_m(ptycho_ctx* ctx, int bin, int sgn, bool accumulate, const float2* src, float2* dst) {
+int launch_shift_one_m(ptycho_ctx* ctx, int bye, int bxe, const float2* src, float2* dst) {
   constexpr int LN = 8;
   const int K = ctx->p.K, S = ctx->S;
   return launch(ctx, "shift_one", 16.0 * K * (double)M * M, [&] {
-    k_shift_build_rows<M, LN><<<dim3(K * M / LN, 1), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, bin, sgn);
-    k_shift_build_cols<M, LN><<<dim3(M / LN, K, 1), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, bin, sgn,
-                                                                         accumulate ? 1 : 0);
+    k_shift_build_rows<M, LN><<<dim3(K * M / LN, 1), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, 1, bxe);
+    k_shift_build_cols<M, LN><<<dim3(M / LN, K, 1), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, 1, bye, 0);
   });
 }
 
-int launch_shift_one(ptycho_ctx* ctx, int bin, int sgn, bool accumulate, const float2* src, float2* dst) {
+int launch_shift_one(ptycho_ctx* ctx, int bye, int bxe, const float2* src, float2* dst) {
   switch (ctx->p.M) {
-    case 16: return launch_shift_one_m<16>(ctx, bin, sgn, accumulate, src, dst);
-    case 32: return launch_shift_one_m<32>(ctx, bin, sgn, accumulate, src, dst);
-    case 64: return launch_shift_one_m<64>(ctx, bin, sgn, accumulate, src, dst);
-    case 96: return launch_shift_one_m<96>(ctx, bin, sgn, accumulate, src, dst);
-    case 128: return launch_shift_one_m<128>(ctx, bin, sgn, accumulate, src, dst);
-    case 192: return launch_shift_one_m<192>(ctx, bin, sgn, accumulate, src, dst);
-    case 256: return launch_shift_one_m<256>(ctx, bin, sgn, accumulate, src, dst);
+    case 16: return launch_shift_one_m<16>(ctx, bye, bxe, src, dst);
+    case 32: return launch_shift_one_m<32>(ctx, bye, bxe, src, dst);
+    case 64: return launch_shift_one_m<64>(ctx, bye, bxe, src, dst);
+    case 96: return launch_shift_one_m<96>(ctx, bye, bxe, src, dst);
+    case 128: return launch_shift_one_m<128>(ctx, bye, bxe, src, dst);
+    case 192: return launch_shift_one_m<192>(ctx, bye, bxe, src, dst);
+    case 256: return launch_shift_one_m<256>(ctx, bye, bxe, src, dst);
     default: return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "sub-pixel shifts are not compiled for M=%d", ctx->p.M);
   }
 }
@@ -1097,40 +1097,48 @@ std::vector<int> epie_orders(const ptycho_ctx* ctx, int n) {
   return ord;
 }
 
-// Sub-pixel ePIE: one position at a time through the general kernels -- the
-// probe this position sees (a single-bin shift), the residual pass of one
-// position, the maxima, the object update and probe step, and the probe step
-// moved back by the adjoint shift and added to the probe.  Seven launches per
-// position, all on the context stream.
+// Sub-pixel ePIE: one position at a time through the general kernels.  The
+// probe is carried in the frame of the position being visited (T_j P, in
+// place in P): moving to the next position's frame is one shift by the
+// difference of the two shifts (exact composition of Fourier shifts), the
+// probe step is added in that frame, and the sweep ends with the shift back
+// to the unshifted frame.  Per position: the frame shift (when the bin
+// changes), the residual pass of the position, the maxima, the object and
+// probe update.
 template <int K>
 int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
-  const int J = ctx->p.J, M = ctx->p.M, MM = M * M;
+  const int J = ctx->p.J, M = ctx->p.M, MM = M * M, S = ctx->S, h = S / 2;
   const std::vector<int> ord = epie_orders(ctx, n);
-  float2* Pj = ctx->Pt;        // slot 0 of the table: the shifted probe
   float2* D = ctx->cg_q;       // the position's residual
-  float2* step = ctx->cg_r;    // the probe step in the position's frame
   float2* mx = ctx->pos_corr;  // (pmax, omax)
+  int cy = h, cx = h;          // bins of the frame P is held in (h, h: unshifted)
   for (int it = 0; it < n; ++it) {
     const bool upd = ctx->t + it >= ctx->p.probe_start;
     for (int s = 0; s < J; ++s) {
       const int j = ord[(size_t)it * J + s];
-      const int bin = ctx->bin_host[j];
-      if (int r = launch_shift_one(ctx, bin, 1, false, ctx->P, Pj)) return r;
-      ctx->f_P = Pj;
+      const int by = ctx->bin_host[j] / S, bx = ctx->bin_host[j] % S;
+      if (by != cy || bx != cx) {
+        if (int r = launch_shift_one(ctx, by - cy + h, bx - cx + h, ctx->P, ctx->P)) return r;
+        cy = by;
+        cx = bx;
+      }
+      ctx->f_P = ctx->P;
       ctx->f_xoff = j;
       int r = launch_fourier(ctx, FM_CHI, D, nullptr, j, 1, "fourier_epie");
       ctx->f_P = nullptr;
       ctx->f_xoff = -1;
       if (r) return r;
       if (int rr = launch(ctx, "epie_update", 8.0 * (3 * K + 2) * MM, [&] {
-            k_epie_sub_max<K><<<1, EPS_NT, 0, ctx->st>>>(Pj, ctx->O, ctx->p.obj_nx, ctx->pos, j, M, mx);
-            k_epie_sub_update<K><<<(MM + 255) / 256, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->pos, j, M, Pj, D,
-                                                                         mx, (float)ctx->p.epie_alpha,
-                                                                         (float)ctx->p.epie_beta, upd ? 1 : 0, step);
+            k_epie_sub_max<K><<<1, EPS_NT, 0, ctx->st>>>(ctx->P, ctx->O, ctx->p.obj_nx, ctx->pos, j, M, mx);
+            k_epie_sub_update<K><<<(MM + 255) / 256, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->pos, j, M, ctx->P,
+                                                                         D, mx, (float)ctx->p.epie_alpha,
+                                                                         (float)ctx->p.epie_beta, upd ? 1 : 0);
           }))
         return rr;
-      if (upd)
-        if (int rr = launch_shift_one(ctx, bin, -1, true, step, ctx->P)) return rr;
+    }
+    if (cy != h || cx != h) {  // back to the unshifted frame
+      if (int r = launch_shift_one(ctx, h - cy + h, h - cx + h, ctx->P, ctx->P)) return r;
+      cy = cx = h;
     }
     if (upd && ctx->p.probe_ortho && K > 1)
       if (int r = ortho_step(ctx, false)) return r;

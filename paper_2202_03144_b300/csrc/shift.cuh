@@ -18,10 +18,11 @@
 // The fan-in sums are taken in the frequency domain (one inverse FFT per line)
 // and skip bins that hold no position.
 //
-// Single-bin form (one_bin >= 0, the sub-pixel ePIE sweep): the build kernels
-// shift the K source arrays by the one bin's delta times sgn (+1: T_delta,
-// -1: its adjoint T_-delta) into slot 0, and the column pass may add its
-// result to the output instead of storing it.
+// Single-shift form (one != 0, the sub-pixel ePIE sweep): the build kernels
+// shift the K source arrays by one delta = (bye - S/2, bxe - S/2) / S into
+// slot 0, bye and bxe any integers (a bin, a reflected bin for the adjoint, or
+// the difference of two bins), and the column pass may add its result to the
+// output instead of storing it.
 #pragma once
 #include "common.cuh"
 #include "fourier2.cuh"
@@ -63,19 +64,19 @@ __device__ __forceinline__ void sh_load_tw(float2* tw_s, const float2* tw) {
   for (int i = threadIdx.x; i < M; i += SH_NT) tw_s[i] = tw[i];
 }
 
-// build, rows: grid (K*M/LN, S) (single bin: (K*M/LN, 1)).
+// build, rows: grid (K*M/LN, S) (single shift: (K*M/LN, 1)).
 // tmp[bx][k][y][:] = T_x(dx(bx)) src[k][y][:]
 template <int M, int LN>
 __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __restrict__ src, float2* __restrict__ tmp,
-                                                            int K, int S, const float2* __restrict__ tw,
-                                                            int one_bin, int sgn) {
+                                                            int K, int S, const float2* __restrict__ tw, int one,
+                                                            int bxe) {
   using C = ShCfg<M, LN>;
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
   sh_load_tw<M>(tw_s, tw);
   const int row0 = blockIdx.x * LN;
-  const int bx = one_bin >= 0 ? one_bin % S : (int)blockIdx.y;
-  const int slot = one_bin >= 0 ? 0 : bx;
+  const int bx = one ? bxe : (int)blockIdx.y;
+  const int slot = one ? 0 : bx;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
     s[l * C::PITCH + i] = src[(size_t)(row0 + l) * M + i];
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __rest
   sh_fft<M, LN, false>(s, tw_s);
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
-    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, bx, S, sgn));
+    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, bx, S, 1));
   }
   __syncthreads();
   sh_fft<M, LN, true>(s, tw_s);
@@ -95,20 +96,20 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __rest
   }
 }
 
-// build, columns: grid (M/LN, K, S*S) (single bin: (M/LN, K, 1)).
+// build, columns: grid (M/LN, K, S*S) (single shift: (M/LN, K, 1)).
 // tab[by S + bx][k][:][x] = T_y(dy(by)) tmp[bx][k][:][x]  (accumulate: +=)
 template <int M, int LN>
 __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __restrict__ tmp, float2* __restrict__ tab,
-                                                            int K, int S, const float2* __restrict__ tw,
-                                                            int one_bin, int sgn, int accumulate) {
+                                                            int K, int S, const float2* __restrict__ tw, int one,
+                                                            int bye, int accumulate) {
   using C = ShCfg<M, LN>;
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
   sh_load_tw<M>(tw_s, tw);
   const int c0 = blockIdx.x * LN, k = blockIdx.y;
-  const int b = one_bin >= 0 ? one_bin : (int)blockIdx.z;
-  const int by = b / S, bx = b % S;
-  const int in_slot = one_bin >= 0 ? 0 : bx, out_slot = one_bin >= 0 ? 0 : b;
+  const int b = one ? 0 : (int)blockIdx.z;
+  const int by = one ? bye : b / S, bx = b % S;
+  const int in_slot = one ? 0 : bx, out_slot = one ? 0 : b;
   const float2* in = tmp + ((size_t)in_slot * K + k) * M * M;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int i = e / LN, l = e % LN;   // row i, column c0 + l
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __rest
   sh_fft<M, LN, false>(s, tw_s);
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int l = e / M, i = e % M;
-    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, by, S, sgn));
+    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, by, S, 1));
   }
   __syncthreads();
   sh_fft<M, LN, true>(s, tw_s);
