@@ -11,8 +11,10 @@
 
 namespace ptycho {
 
-constexpr int EPS_NT = 1024;
+constexpr int EPS_NT = 256;
+constexpr int EPS_MX = 32;   // CTAs of the maxima kernel (partial maxima, reduced by the update)
 
+// grid EPS_MX: out[b] = (max sum_k |P_j,k|^2, max |O_j|^2) over CTA b's pixels
 template <int K>
 __global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restrict__ Pj, const float2* __restrict__ O,
                                                          int nx, const int2* __restrict__ pos, int j, int M,
@@ -21,7 +23,7 @@ __global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restric
   const int2 p = pos[j];
   const int MM = M * M;
   float pm = 0.f, om = 0.f;
-  for (int u = threadIdx.x; u < MM; u += EPS_NT) {
+  for (int u = blockIdx.x * EPS_NT + threadIdx.x; u < MM; u += EPS_MX * EPS_NT) {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) s += cabs2(Pj[(size_t)k * MM + u]);
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restric
   }
   pm = block_max_f<EPS_NT>(pm, red);
   om = block_max_f<EPS_NT>(om, red);
-  if (threadIdx.x == 0) out[0] = make_float2(pm, om);
+  if (threadIdx.x == 0) out[blockIdx.x] = make_float2(pm, om);
 }
 
 template <int K>
@@ -40,7 +42,12 @@ __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O,
                                                          float alpha, float beta, int upd) {
   const int2 p = pos[j];
   const int MM = M * M;
-  const float pmax = mx[0].x, omax = mx[0].y;
+  float pmax = 0.f, omax = 0.f;
+#pragma unroll 8
+  for (int b = 0; b < EPS_MX; ++b) {
+    pmax = fmaxf(pmax, mx[b].x);
+    omax = fmaxf(omax, mx[b].y);
+  }
   const float sa = pmax > 0.f ? alpha / pmax : 0.f;
   const float sb = (upd && omax > 0.f) ? beta / omax : 0.f;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < MM; u += gridDim.x * blockDim.x) {

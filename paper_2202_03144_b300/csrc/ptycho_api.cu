@@ -344,6 +344,7 @@ struct ptycho_ctx {
   float2* cg_q = nullptr;
   double* cg_part = nullptr;   // [3][blocks] inner-product partials
   float2* pos_corr = nullptr;  // position refinement: per-position shift
+  float2* ep_mx = nullptr;     // sub-pixel ePIE: partial maxima
   // position blocks (params.block_positions = B > 0, LSQML): X holds the
   // residuals of B positions; blk is the block the launches work on
   int B = 0;
@@ -1110,7 +1111,7 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
   const int J = ctx->p.J, M = ctx->p.M, MM = M * M, S = ctx->S, h = S / 2;
   const std::vector<int> ord = epie_orders(ctx, n);
   float2* D = ctx->cg_q;       // the position's residual
-  float2* mx = ctx->pos_corr;  // (pmax, omax)
+  float2* mx = ctx->ep_mx;     // partial (pmax, omax)
   int cy = h, cx = h;          // bins of the frame P is held in (h, h: unshifted)
   for (int it = 0; it < n; ++it) {
     const bool upd = ctx->t + it >= ctx->p.probe_start;
@@ -1129,7 +1130,7 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
       ctx->f_xoff = -1;
       if (r) return r;
       if (int rr = launch(ctx, "epie_update", 8.0 * (3 * K + 2) * MM, [&] {
-            k_epie_sub_max<K><<<1, EPS_NT, 0, ctx->st>>>(ctx->P, ctx->O, ctx->p.obj_nx, ctx->pos, j, M, mx);
+            k_epie_sub_max<K><<<EPS_MX, EPS_NT, 0, ctx->st>>>(ctx->P, ctx->O, ctx->p.obj_nx, ctx->pos, j, M, mx);
             k_epie_sub_update<K><<<(MM + 255) / 256, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->pos, j, M, ctx->P,
                                                                          D, mx, (float)ctx->p.epie_alpha,
                                                                          (float)ctx->p.epie_beta, upd ? 1 : 0);
@@ -1324,6 +1325,7 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
     if (int r = dalloc(ctx, &ctx->cg_q, KMM)) return r;
     if (int r = dalloc(ctx, &ctx->cg_part, 3 * ((KMM + CG_NT - 1) / CG_NT))) return r;
     if (int r = dalloc(ctx, &ctx->pos_corr, (size_t)J)) return r;
+    if (int r = dalloc(ctx, &ctx->ep_mx, (size_t)EPS_MX)) return r;
     CK(cudaMemcpy(ctx->pbin, bin.data(), J * sizeof(unsigned short), cudaMemcpyHostToDevice));
     ctx->bin_host = bin;
     if (int r = build_subpixel_groups(ctx, bin)) return r;
@@ -2060,7 +2062,7 @@ void ptycho_destroy(ptycho_ctx* ctx) {
                   ctx->flag,     ctx->gram,      ctx->modeV,    ctx->pbin,     ctx->Pt,        ctx->dPt,
                   ctx->pbins,    ctx->stmp,      ctx->porder,   ctx->goff,     ctx->bgrp,
                   ctx->pbins_den, ctx->cg_r,     ctx->cg_p,     ctx->cg_q,     ctx->cg_part,
-                  ctx->pos_corr, ctx->objacc};
+                  ctx->pos_corr, ctx->objacc, ctx->ep_mx};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (ctx->stage) cudaFree(ctx->stage);
