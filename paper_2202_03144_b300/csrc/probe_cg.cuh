@@ -4,8 +4,8 @@
 // with Dbar_b = sum_{j in bin b} |O_j|^2 (per-bin sums of the probe pass),
 // preconditioner W = den_P + d (den_P = sum_b Dbar_b), d = reg max den_P and
 // the real inner product Re<x, y> over all modes and pixels.  B X is a
-// shifted-table build of X, a per-bin scaling and an adjoint shift-sum
-// (shift.cuh); the vector steps below fuse everything else.
+// shifted-table build of X scaled per bin (fused into the build) and an
+// adjoint shift-sum (shift.cuh); the vector steps below fuse everything else.
 //
 // Every inner product is written as per-block FP64 partials; the next kernel
 // adds them in block order in every block (deterministic, no atomics), so the
@@ -140,16 +140,6 @@ __global__ void __launch_bounds__(CG_NT) k_cg_dir(CgArgs a) {
     const float2 z = w > 0.f ? cscale(r, 1.f / w) : make_float2(0.f, 0.f);
     const float2 p = a.p[i];
     a.p[i] = make_float2(fmaf(beta, p.x, z.x), fmaf(beta, p.y, z.y));
-  }
-}
-
-// tab[b][k][u] *= dbar[b][u]
-__global__ void __launch_bounds__(256) k_bin_scale(float2* __restrict__ tab, const float* __restrict__ dbar,
-                                                   int nbins, int K, int MM) {
-  const size_t n = (size_t)nbins * K * MM;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t u = i % MM, b = i / ((size_t)K * MM);
-    tab[i] = cscale(tab[i], dbar[b * MM + u]);
   }
 }
 

@@ -523,7 +523,7 @@ int collect_profile(ptycho_ctx* ctx) {
 size_t amp_bytes(const ptycho_ctx* ctx) { return ctx->p.istore == PTYCHO_I_F32 ? 4 : 2; }
 
 // ----------------------------------------------------------------- Fourier
-int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst);
+int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst, const float* bscale = nullptr);
 int refresh_probe_table(ptycho_ctx* ctx);
 const float2* probe_view(const ptycho_ctx* ctx);
 const unsigned short* bin_view(const ptycho_ctx* ctx);
@@ -599,7 +599,7 @@ int check_device_flag(ptycho_ctx* ctx) {
 
 // ------------------------------------------------------ sub-pixel shifts
 template <int M>
-int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) {
+int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst, const float* bscale) {
   constexpr int LN = 8;
   const int K = ctx->p.K, S = ctx->S;
   const double tab = 8.0 * S * S * K * (double)M * M;
@@ -607,7 +607,7 @@ int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) 
     if (int r = launch(ctx, "shift_build", tab, [&] {
           k_shift_build_rows<M, LN><<<dim3(K * M / LN, S), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, 0, 0);
           k_shift_build_cols<M, LN><<<dim3(M / LN, K, S * S), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, 0,
-                                                                                 0, 0);
+                                                                                 0, 0, bscale);
         }))
       return r;
     return 0;
@@ -626,7 +626,8 @@ int launch_shift_one_m(ptycho_ctx* ctx, int bye, int bxe, const float2* src, flo
   const int K = ctx->p.K, S = ctx->S;
   return launch(ctx, "shift_one", 16.0 * K * (double)M * M, [&] {
     k_shift_build_rows<M, LN><<<dim3(K * M / LN, 1), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, 1, bxe);
-    k_shift_build_cols<M, LN><<<dim3(M / LN, K, 1), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, 1, bye, 0);
+    k_shift_build_cols<M, LN><<<dim3(M / LN, K, 1), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, 1, bye, 0,
+                                                                         nullptr);
   });
 }
 
@@ -643,16 +644,17 @@ int launch_shift_one(ptycho_ctx* ctx, int bye, int bxe, const float2* src, float
   }
 }
 
-// build: dst[bin][k] = T_delta(bin) src[k];  sum: dst[k] = sum_bin T_-delta(bin) src[bin][k]
-int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst) {
+// build: dst[bin][k] = T_delta(bin) src[k] (times bscale[bin] if given);
+// sum: dst[k] = sum_bin T_-delta(bin) src[bin][k]
+int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst, const float* bscale) {
   switch (ctx->p.M) {
-    case 16: return launch_shift_m<16>(ctx, build, src, dst);
-    case 32: return launch_shift_m<32>(ctx, build, src, dst);
-    case 64: return launch_shift_m<64>(ctx, build, src, dst);
-    case 96: return launch_shift_m<96>(ctx, build, src, dst);
-    case 128: return launch_shift_m<128>(ctx, build, src, dst);
-    case 192: return launch_shift_m<192>(ctx, build, src, dst);
-    case 256: return launch_shift_m<256>(ctx, build, src, dst);
+    case 16: return launch_shift_m<16>(ctx, build, src, dst, bscale);
+    case 32: return launch_shift_m<32>(ctx, build, src, dst, bscale);
+    case 64: return launch_shift_m<64>(ctx, build, src, dst, bscale);
+    case 96: return launch_shift_m<96>(ctx, build, src, dst, bscale);
+    case 128: return launch_shift_m<128>(ctx, build, src, dst, bscale);
+    case 192: return launch_shift_m<192>(ctx, build, src, dst, bscale);
+    case 256: return launch_shift_m<256>(ctx, build, src, dst, bscale);
     default: return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "sub-pixel shifts are not compiled for M=%d", ctx->p.M);
   }
 }
@@ -766,14 +768,9 @@ int obj_step(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
 // sums of this iteration.
 constexpr int DM_PROBE_CG = 4;
 
-// q = B v = sum_b T_-delta(b)[Dbar_b T_delta(b) v]
+// q = B v = sum_b T_-delta(b)[Dbar_b T_delta(b) v] (the scaling fused into the build)
 int probe_normal_op(ptycho_ctx* ctx, const float2* v, float2* q) {
-  if (int r = launch_shift(ctx, true, v, ctx->dPt)) return r;
-  const int nb = ctx->S * ctx->S, K = ctx->p.K, MM = ctx->p.M * ctx->p.M;
-  if (int r = launch(ctx, "bin_scale", 0.0, [&] {
-        k_bin_scale<<<1184, 256, 0, ctx->st>>>(ctx->dPt, ctx->pbins_den, nb, K, MM);
-      }))
-    return r;
+  if (int r = launch_shift(ctx, true, v, ctx->dPt, ctx->pbins_den)) return r;
   return launch_shift(ctx, false, ctx->dPt, q);
 }
 

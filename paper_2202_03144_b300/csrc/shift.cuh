@@ -97,11 +97,14 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __rest
 }
 
 // build, columns: grid (M/LN, K, S*S) (single shift: (M/LN, K, 1)).
-// tab[by S + bx][k][:][x] = T_y(dy(by)) tmp[bx][k][:][x]  (accumulate: +=)
+// tab[by S + bx][k][:][x] = T_y(dy(by)) tmp[bx][k][:][x]  (accumulate: +=),
+// times bscale[b][pixel] when bscale is given (the DM probe solve's per-bin
+// |O|^2 sums)
 template <int M, int LN>
 __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __restrict__ tmp, float2* __restrict__ tab,
                                                             int K, int S, const float2* __restrict__ tw, int one,
-                                                            int bye, int accumulate) {
+                                                            int bye, int accumulate,
+                                                            const float* __restrict__ bscale) {
   using C = ShCfg<M, LN>;
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
@@ -124,10 +127,13 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __rest
   __syncthreads();
   sh_fft<M, LN, true>(s, tw_s);
   float2* out = tab + ((size_t)out_slot * K + k) * M * M;
+  const float* sc = bscale ? bscale + (size_t)b * M * M : nullptr;
   for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
     const int i = e / LN, l = e % LN;
     const size_t o = (size_t)i * M + c0 + l;
-    out[o] = accumulate ? cadd(out[o], s[l * C::PITCH + i]) : s[l * C::PITCH + i];
+    float2 v = s[l * C::PITCH + i];
+    if (sc) v = cscale(v, sc[o]);
+    out[o] = accumulate ? cadd(out[o], v) : v;
   }
 }
 
