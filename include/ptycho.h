@@ -25,8 +25,10 @@
  *    frequency at pixel (M/2, M/2)); a negative value marks a masked pixel
  *    (saturated or bad, Sec. 2.2), which the modulus projection leaves free.
  *  - positions: [J][2] float32 (y, x) of each patch's top-left corner on the
- *    object grid, in pixels; rounded half-to-even to integers.  Every patch
- *    must lie inside the object.
+ *    object grid, in pixels; rounded half-to-even to integers, or, with
+ *    ptycho_params.subpixel = S, quantised to 1/S pixel with the probe
+ *    Fourier-shifted by the fractional part.  Every patch must lie inside
+ *    the object.
  *  - on_device != 0: the pointer is CUDA device memory of the current device;
  *    otherwise it is host memory (pageable or pinned).
  *  - Ownership: the library COPIES every input; the caller keeps its
