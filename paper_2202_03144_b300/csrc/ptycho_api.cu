@@ -1110,7 +1110,7 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
   float2* D = ctx->cg_q;       // the position's residual
   float2* mx = ctx->ep_mx;     // partial (pmax, omax)
   int cy = h, cx = h;          // bins of the frame P is held in (h, h: unshifted)
-  for (int it = 0; it < n; ++it) {
+  auto sweep = [&](int it) -> int {
     const bool upd = ctx->t + it >= ctx->p.probe_start;
     for (int s = 0; s < J; ++s) {
       const int j = ord[(size_t)it * J + s];
@@ -1134,12 +1134,18 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
           }))
         return rr;
     }
-    if (cy != h || cx != h) {  // back to the unshifted frame
-      if (int r = launch_shift_one(ctx, h - cy + h, h - cx + h, ctx->P, ctx->P)) return r;
+    return 0;
+  };
+  for (int it = 0; it < n; ++it) {
+    const int r = sweep(it);
+    if (cy != h || cx != h) {  // back to the unshifted frame (also after an error)
+      const int rb = launch_shift_one(ctx, h - cy + h, h - cx + h, ctx->P, ctx->P);
       cy = cx = h;
+      if (!r && rb) return rb;
     }
-    if (upd && ctx->p.probe_ortho && K > 1)
-      if (int r = ortho_step(ctx, false)) return r;
+    if (r) return r;
+    if (ctx->t + it >= ctx->p.probe_start && ctx->p.probe_ortho && K > 1)
+      if (int rr = ortho_step(ctx, false)) return rr;
   }
   ctx->t += n;
   ctx->psi_valid = false;
