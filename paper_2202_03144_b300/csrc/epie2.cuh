@@ -334,10 +334,21 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
         }
         const float sa = pmax > 0.f ? a.alpha / pmax : 0.f;
         const float sb = (upd && omax > 0.f) ? a.beta / omax : 0.f;
-        for (int e = tid; e < M * W; e += NT) {
+        // all of this thread's object values in flight first (the loop
+        // otherwise waits for one L2 round trip per element)
+        constexpr int NU = (M * W + NT - 1) / NT;
+        float2 ov[NU];
+#pragma unroll
+        for (int q = 0; q < NU; ++q) {
+          const int e = tid + q * NT;
+          if (e < M * W) ov[q] = __ldcg(a.O + (size_t)(p.x + e / W) * a.nx + p.y + c * W + e % W);
+        }
+#pragma unroll
+        for (int q = 0; q < NU; ++q) {
+          const int e = tid + q * NT;
+          if (e >= M * W) continue;
           const int colL = e % W, row = e / W;
-          float2* op = a.O + (size_t)(p.x + row) * a.nx + p.y + c * W + colL;
-          const float2 o = __ldcg(op);
+          const float2 o = ov[q];
           float2 num = make_float2(0.f, 0.f);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
             num = cadd(num, cconjmul(pr, d));
             if (upd) pr = cadd(pr, cscale(cconjmul(o, d), sb));
           }
-          __stcg(op, cadd(o, cscale(num, sa)));
+          __stcg(a.O + (size_t)(p.x + row) * a.nx + p.y + c * W + colL, cadd(o, cscale(num, sa)));
         }
       }
       // object writes visible cluster-wide; buffers and barriers free for the
