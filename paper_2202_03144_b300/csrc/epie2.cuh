@@ -181,6 +181,23 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
         }
       }
       const float scale = a.istore != 0 ? __ldg(a.amp_scale + j) : 1.f;
+      // K > 1: this thread's amplitudes for the projection, loaded while the
+      // transpose completes
+      constexpr int NA = (H * M + NT - 1) / NT;
+      float amv[K > 1 ? NA : 1];
+      if constexpr (K > 1) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+          const int px = tid + q * NT;
+          if (px < H * M) {
+            const int rowL = px / M, pp = px % M;
+            const size_t ai = amp_row0 + (size_t)rowL * M + pp / R2 + R1 * (pp % R2);
+            if (a.istore == 0) amv[q] = __ldcg(reinterpret_cast<const float*>(a.amp) + ai);
+            else if (a.istore == 1) amv[q] = __half2float(reinterpret_cast<const __half*>(a.amp)[ai]) * scale;
+            else amv[q] = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.amp)[ai]) * scale;
+          }
+        }
+      }
       if (!mbar_wait_parity_or_abort(barY, phase, a.err_flag)) atomicExch(a.err_flag, 1);
       // ---- row stage 1
       {
@@ -230,9 +247,11 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
             for (int k2 = 0; k2 < R2; ++k2) Y[rb<F>(k, rowL, k1 * R2 + k2)] = w[q][k2];
           }
           __syncthreads();
-          for (int px = tid; px < H * M; px += NT) {
+#pragma unroll
+          for (int q = 0; q < NA; ++q) {
+            const int px = tid + q * NT;
+            if (px >= H * M) continue;
             const int rowL = px / M, pp = px % M;  // pp = k1 * R2 + k2 storage slot
-            const int kx = pp / R2 + R1 * (pp % R2);
             float2 z[K];
             float A2 = 0.f;
 #pragma unroll
@@ -240,12 +259,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
               z[k] = Y[rb<F>(k, rowL, pp)];
               A2 += cabs2(z[k]);
             }
-            const size_t ai = amp_row0 + (size_t)rowL * M + kx;
-            float am;
-            if (a.istore == 0) am = __ldcg(reinterpret_cast<const float*>(a.amp) + ai);
-            else if (a.istore == 1) am = __half2float(reinterpret_cast<const __half*>(a.amp)[ai]) * scale;
-            else am = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.amp)[ai]) * scale;
-            const float fct = proj_factor(FM_CHI, am, A2) * inv;
+            const float fct = proj_factor(FM_CHI, amv[q], A2) * inv;
 #pragma unroll
             for (int k = 0; k < K; ++k) Y[rb<F>(k, rowL, pp)] = cscale(z[k], fct);
           }
