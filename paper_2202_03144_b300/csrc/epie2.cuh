@@ -181,11 +181,27 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
         }
       }
       const float scale = a.istore != 0 ? __ldg(a.amp_scale + j) : 1.f;
-      // K > 1: this thread's amplitudes for the projection, loaded while the
-      // transpose completes
+      // this thread's amplitudes for the projection, loaded while the
+      // transpose completes (K = 1: in the register layout of row stage 2)
       constexpr int NA = (H * M + NT - 1) / NT;
       float amv[K > 1 ? NA : 1];
-      if constexpr (K > 1) {
+      float am1[K == 1 ? Q : 1][K == 1 ? R2 : 1];
+      if constexpr (K == 1) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int s2 = tid + q * NT;
+          const int k1 = s2 % R1, rowL = (s2 / R1) % H;
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const size_t ai = amp_row0 + (size_t)rowL * M + k1 + R1 * k2;
+            float am;
+            if (a.istore == 0) am = __ldcg(reinterpret_cast<const float*>(a.amp) + ai);
+            else if (a.istore == 1) am = __half2float(reinterpret_cast<const __half*>(a.amp)[ai]) * scale;
+            else am = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.amp)[ai]) * scale;
+            am1[q][k2] = am;
+          }
+        }
+      } else {
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
           const int px = tid + q * NT;
@@ -225,19 +241,10 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
         }
         if constexpr (K == 1) {
 #pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            const int s2 = tid + q * NT;
-            const int k1 = s2 % R1, rowL = (s2 / R1) % H;
+          for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) {
-              const size_t ai = amp_row0 + (size_t)rowL * M + k1 + R1 * k2;
-              float am;
-              if (a.istore == 0) am = __ldcg(reinterpret_cast<const float*>(a.amp) + ai);
-              else if (a.istore == 1) am = __half2float(reinterpret_cast<const __half*>(a.amp)[ai]) * scale;
-              else am = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.amp)[ai]) * scale;
-              w[q][k2] = cscale(w[q][k2], proj_factor(FM_CHI, am, cabs2(w[q][k2])) * inv);
-            }
-          }
+            for (int k2 = 0; k2 < R2; ++k2)
+              w[q][k2] = cscale(w[q][k2], proj_factor(FM_CHI, am1[q][k2], cabs2(w[q][k2])) * inv);
         } else {
 #pragma unroll
           for (int q = 0; q < Q; ++q) {
