@@ -132,18 +132,6 @@ __device__ __forceinline__ bool mbar_wait0(uint64_t* bar) {
   return done != 0;
 }
 
-// Read-only load with an L2 evict-last policy: the probe (or its shifted
-// table) is re-read by every position, while the exit waves and amplitudes
-// stream through L2 once.
-__device__ __forceinline__ float2 ldg_keep(const float2* ptr) {
-  float2 v;
-  asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
-      "ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], pol;\n\t}"
-      : "=f"(v.x), "=f"(v.y)
-      : "l"(ptr));
-  return v;
-}
-
 struct Fourier2Args {
   const float2* O;
   int nx;
@@ -238,7 +226,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
     // probe values first, then the object in groups of four: bounds the number
     // of loads in flight per thread (and so the registers they occupy)
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = ldg_keep(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
     const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
 #pragma unroll
     for (int g0 = 0; g0 < R1; g0 += 4) {
@@ -486,7 +474,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
         __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-        const float2 pr = ldg_keep(Pj + ((size_t)k * M + row) * M + col);
+        const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);
         __stcs(a.X + xi, cadd(cmul(pr, o), v[n1]));
       }
     }

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     const int colL = tid % W, n2 = (tid / W) % R2, k = tid / (W * R2);
     const int col = c * W + colL;
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = ldg_keep(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = __ldg(Pj + ((size_t)k * M + n1 * R2 + n2) * M + col);
     const float2* orow = a.O + (size_t)(p.x + n2) * a.nx + p.y + col;
 #pragma unroll
     for (int g0 = 0; g0 < R1; g0 += F3_OG) {
@@ -210,10 +210,31 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       }
     }
   };
+  // K > 1: the amplitudes of this thread's pixels in the mode-summing loop
+  // below, all loads in flight at once
+  constexpr int NA = (H * M + NT - 1) / NT;
+  float amv[K > 1 ? NA : 1];
+  auto load_amp_k = [&]() {
+    if constexpr (K > 1) {
+      if (need_amp) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+          const int px = tid + q * NT;
+          if (px < H * M) {
+            const int rowL = px / M, pp = px % M;
+            amv[q] = amp_global<IST_T>(a, amp_row0 + (size_t)rowL * M + pp / R2 + R1 * (pp % R2), scale);
+          }
+        }
+      }
+    }
+  };
   // LSQML residual pass: before the wait (256^2: 6.51 -> 6.24 ms); DM pass,
   // whose prologue holds more registers: after row stage 1 (2% faster there)
   constexpr bool amp_early = MODE_T != FM_DM;
-  if (amp_early) load_amp();
+  if (amp_early) {
+    load_amp();
+    load_amp_k();
+  }
   if (!mbar_wait0_or_abort(barY, a.err_flag)) atomicExch(a.err_flag, 1);
   // ---- row stage 1: task (k, rowL, n2'), columns n1'*R2 + n2'
   {
@@ -226,7 +247,10 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) Y[rb<F>(k, rowL, k1 * R2 + n2)] = v[k1];
   }
-  if (!amp_early) load_amp();
+  if (!amp_early) {
+    load_amp();
+    load_amp_k();
+  }
   __syncthreads();
   // ---- row stage 2 (+ projection + first inverse stage)
   constexpr float inv = 1.0f / (float)(M * M);
@@ -270,7 +294,10 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
         for (int k2 = 0; k2 < R2; ++k2) Y[rb<F>(k, rowL, k1 * R2 + k2)] = w[q][k2];
       }
       __syncthreads();
-      for (int px = tid; px < H * M; px += NT) {
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        const int px = tid + q * NT;
+        if (px >= H * M) continue;
         const int rowL = px / M, pp = px % M;
         const int kx = pp / R2 + R1 * (pp % R2);
         const int ky = c * H + rowL;
@@ -285,7 +312,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
           a.I_out[((size_t)j * M + ((ky + M / 2) % M)) * M + ((kx + M / 2) % M)] = A2;
           continue;
         }
-        const float am = amp_global<IST_T>(a, amp_row0 + (size_t)rowL * M + kx, scale);
+        const float am = amv[q];
         if (mode == FM_ERR) {
           if (am >= 0.f) {
             const double d = (double)sqrtf(A2) - (double)am;
@@ -387,7 +414,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
         __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-        const float2 pr = ldg_keep(Pj + ((size_t)k * M + row) * M + col);
+        const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);
         __stcs(a.X + xi, cadd(cmul(pr, o), v[n1]));
       }
     }
