@@ -138,8 +138,28 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
         for (int k = 0; k < K; ++k) ps += cabs2(Pb[k * M * W + e]);
         pm = fmaxf(pm, ps);
       }
-      pm = block_max_f<NT>(pm, redf);
-      om = block_max_f<NT>(om, redf + 32);
+      // both CTA maxima in one block reduction (valid in thread 0, which
+      // sends them to the peers)
+      {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          pm = fmaxf(pm, __shfl_down_sync(0xffffffffu, pm, o));
+          om = fmaxf(om, __shfl_down_sync(0xffffffffu, om, o));
+        }
+        constexpr int NW = (NT + 31) / 32;
+        const int lane = tid & 31, wid = tid >> 5;
+        __syncthreads();
+        if (lane == 0) {
+          redf[wid] = pm;
+          redf[32 + wid] = om;
+        }
+        __syncthreads();
+        if (tid == 0)
+          for (int i = 1; i < NW; ++i) {
+            pm = fmaxf(pm, redf[i]);
+            om = fmaxf(om, redf[32 + i]);
+          }
+      }
       // ---- column stage 1
       {
         const int colL = tid % W, n2 = (tid / W) % R2, k = tid / (W * R2);
