@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   constexpr float inv = 1.0f / (float)(M * M);
   uint32_t phase = 0;
+  // this thread's part of max_u sum_k |P_k(u)|^2 for the next position:
+  // computed by the probe update (or unchanged without one); < 0 = not yet
+  float pm_next = -1.f;
 
   for (int it = 0; it < a.n_iter; ++it) {
     const bool upd = (a.t0 + it) >= (long long)a.probe_start;
@@ -132,12 +135,17 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
           v[n1] = z;
         }
       }
-      for (int e = tid; e < M * W; e += NT) {
-        float ps = 0.f;
+      if (pm_next >= 0.f) {
+        pm = pm_next;
+      } else {
+        for (int e = tid; e < M * W; e += NT) {
+          float ps = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) ps += cabs2(Pb[k * M * W + e]);
-        pm = fmaxf(pm, ps);
+          for (int k = 0; k < K; ++k) ps += cabs2(Pb[k * M * W + e]);
+          pm = fmaxf(pm, ps);
+        }
       }
+      const float pm_own = pm;
       // both CTA maxima in one block reduction (valid in thread 0, which
       // sends them to the peers)
       {
@@ -384,6 +392,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
           const int e = tid + q * NT;
           if (e < M * W) ov[q] = __ldcg(a.O + (size_t)(p.x + e / W) * a.nx + p.y + c * W + e % W);
         }
+        float pmx = 0.f;
 #pragma unroll
         for (int q = 0; q < NU; ++q) {
           const int e = tid + q * NT;
@@ -391,15 +400,21 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, 1) k_epie2(Epie2Args a) {
           const int colL = e % W, row = e / W;
           const float2 o = ov[q];
           float2 num = make_float2(0.f, 0.f);
+          float ps = 0.f;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const float2 d = X[cb<F>(k, row, colL)];
             float2& pr = Pb[cb<F>(k, row, colL)];
             num = cadd(num, cconjmul(pr, d));
-            if (upd) pr = cadd(pr, cscale(cconjmul(o, d), sb));
+            if (upd) {
+              pr = cadd(pr, cscale(cconjmul(o, d), sb));
+              ps += cabs2(pr);
+            }
           }
+          pmx = fmaxf(pmx, ps);
           __stcg(a.O + (size_t)(p.x + row) * a.nx + p.y + c * W + colL, cadd(o, cscale(num, sa)));
         }
+        pm_next = upd ? pmx : pm_own;
       }
       // object writes visible cluster-wide; buffers and barriers free for the
       // next position
