@@ -418,6 +418,8 @@ def main():
     ap.add_argument("--no-eps", action="store_true", help="skip the time-to-epsilon runs")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
     ap.add_argument("--warm-frames", type=int, default=200_000)
+    ap.add_argument("--epie-only", action="store_true",
+                    help="run only the ePIE sweep of the 3-mode spiral scan and print its figures (profiling runs)")
     args = ap.parse_args()
     if args.small:
         WORKLOAD["grid"] = 20
@@ -439,6 +441,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    if args.epie_only:
+        stream = torch.cuda.Stream()
+        print(json.dumps(run_epie(api, torch, stream)), flush=True)
+        return
     w = WORKLOAD
     M, K, J = w["M"], w["K"], w["grid"] ** 2
     P, O, pos, P0 = make_scan(rank)
