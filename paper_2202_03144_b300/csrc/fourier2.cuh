@@ -304,7 +304,10 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
     if (!mbar_wait0(bar)) atomicExch(a.err_flag, 1);
   }
   constexpr float inv = 1.0f / (float)(M * M);
-  double en = 0.0, ed = 0.0;
+  // Fourier error: per-thread FP32 partials over the thread's few dozen pixels
+  // (A - a is exact in FP32 where A and a are within a factor 2), FP64 from the
+  // block sums on
+  float en = 0.f, ed = 0.f;
   {
     float2 w[Q][R2];
 #pragma unroll
@@ -326,9 +329,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
             const float am = amp_at<IST_T>(a, amp_s, rowL * M + kx, scale);
             if (mode == FM_ERR) {
               if (am >= 0.f) {
-                const double d = (double)sqrtf(A2) - (double)am;
-                en += d * d;
-                ed += (double)am * (double)am;
+                const float d = sqrtf(A2) - am;
+                en = fmaf(d, d, en);
+                ed = fmaf(am, am, ed);
               }
             } else {
               const float fct = proj_factor(mode, am, A2);
@@ -366,9 +369,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
         const float am = amp_at<IST_T>(a, amp_s, rowL * M + kx, scale);
         if (mode == FM_ERR) {
           if (am >= 0.f) {
-            const double d = (double)sqrtf(A2) - (double)am;
-            en += d * d;
-            ed += (double)am * (double)am;
+            const float d = sqrtf(A2) - am;
+            en = fmaf(d, d, en);
+            ed = fmaf(am, am, ed);
           }
           continue;
         }

@@ -254,7 +254,10 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
   __syncthreads();
   // ---- row stage 2 (+ projection + first inverse stage)
   constexpr float inv = 1.0f / (float)(M * M);
-  double en = 0.0, ed = 0.0;
+  // Fourier error: per-thread FP32 partials over the thread's few dozen pixels
+  // (A - a is exact in FP32 where A and a are within a factor 2), FP64 from the
+  // block sums on
+  float en = 0.f, ed = 0.f;
   {
     float2 w[Q][R2];
 #pragma unroll
@@ -274,9 +277,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
             a.I_out[((size_t)j * M + ((ky + M / 2) % M)) * M + ((kx + M / 2) % M)] = A2;
           } else if (mode == FM_ERR) {
             if (am[q][k2] >= 0.f) {
-              const double d = (double)sqrtf(A2) - (double)am[q][k2];
-              en += d * d;
-              ed += (double)am[q][k2] * (double)am[q][k2];
+              const float d = sqrtf(A2) - am[q][k2];
+              en = fmaf(d, d, en);
+              ed = fmaf(am[q][k2], am[q][k2], ed);
             }
           } else {
             const float fct = proj_factor(mode, am[q][k2], A2);
@@ -315,9 +318,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
         const float am = amv[q];
         if (mode == FM_ERR) {
           if (am >= 0.f) {
-            const double d = (double)sqrtf(A2) - (double)am;
-            en += d * d;
-            ed += (double)am * (double)am;
+            const float d = sqrtf(A2) - am;
+            en = fmaf(d, d, en);
+            ed = fmaf(am, am, ed);
           }
           continue;
         }
@@ -341,8 +344,12 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       const double sd = block_sum_d<NT>(ed, red);
       if (tid == 0) a.err_part[(size_t)j * C + c] = make_double2(sn, sd);
     }
-    // no peer writes into this CTA after its first transpose in these modes
-    if (mode == FM_ERR || mode == FM_SIM) return;
+    // no peer writes into this CTA after its first transpose in these modes;
+    // the cluster leaves together, after every CTA has received its rows
+    if (mode == FM_ERR || mode == FM_SIM) {
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int s = tid + q * NT;

@@ -34,7 +34,7 @@ struct KernelSet {
   size_t smem_fourier, smem_epie;
   FourierFn fourier;       // any mode, any amplitude format
   void (*epie)(EpieArgs);  // null: no ePIE kernel for this shape
-  FourierFn spec[3][3];    // [spec_row(mode)][f32, f16, bf16]
+  FourierFn spec[5][3];    // [spec_row(mode)][f32, f16, bf16]
   size_t smem_spec;        // dynamic shared memory of the spec kernels
   bool default_ok = true;  // a candidate for the default cluster size of DM/LSQML
   void (*epie2)(Epie2Args) = nullptr;  // register-resident ePIE sweep (C > 1), or null
@@ -42,9 +42,10 @@ struct KernelSet {
 };
 
 // Row of KernelSet::spec for a Fourier mode: DM, LSQML residual (amplitude),
-// LSQML residual (Poisson); -1 for the modes only the generic kernel runs.
+// LSQML residual (Poisson), Fourier error, forward model; -1 for modes only
+// the generic kernel runs.
 __host__ __device__ constexpr int spec_row(int mode) {
-  return mode == FM_DM ? 0 : mode == FM_CHI ? 1 : mode == FM_CHIP ? 2 : -1;
+  return mode == FM_DM ? 0 : mode == FM_CHI ? 1 : mode == FM_CHIP ? 2 : mode == FM_ERR ? 3 : mode == FM_SIM ? 4 : -1;
 }
 
 template <int M, int K, int C, int MODE>
@@ -68,6 +69,8 @@ void fill_spec(KernelSet& s) {
   fill_spec_row<M, K, C, FM_DM>(s);
   fill_spec_row<M, K, C, FM_CHI>(s);
   fill_spec_row<M, K, C, FM_CHIP>(s);
+  fill_spec_row<M, K, C, FM_ERR>(s);
+  fill_spec_row<M, K, C, FM_SIM>(s);
 }
 
 template <int M, int K, int C>
