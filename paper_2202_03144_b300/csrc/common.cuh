@@ -18,6 +18,16 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
 }
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may become resident while its predecessor in the stream still
+// runs; pdl_wait() returns once the predecessor has completed and its writes
+// are visible (at once for an ordinary launch: the stream already ordered it),
+// pdl_launch() lets the successor start its launch.  Kernels call pdl_wait()
+// before their first global access that a predecessor may have written or
+// may still read, so either launch form gives stream order.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 

@@ -20,6 +20,8 @@ __global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restric
                                                          int nx, const int2* __restrict__ pos, int j, int M,
                                                          float2* __restrict__ out) {
   __shared__ float red[32];
+  pdl_wait();
+  pdl_launch();
   const int2 p = pos[j];
   const int MM = M * M;
   float pm = 0.f, om = 0.f;
@@ -40,6 +42,8 @@ __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O,
                                                          int j, int M, float2* __restrict__ Pj,
                                                          const float2* __restrict__ D, const float2* __restrict__ mx,
                                                          float alpha, float beta, int upd) {
+  pdl_wait();
+  pdl_launch();
   const int2 p = pos[j];
   const int MM = M * M;
   float pmax = 0.f, omax = 0.f;

@@ -193,6 +193,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
   double* red = reinterpret_cast<double*>(amp_s + (size_t)H * M * 4);
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + F::NRED);
 
+  pdl_wait();
+  pdl_launch();
   const int tid = threadIdx.x;
   const int c = (C > 1) ? (int)(blockIdx.x % C) : 0;
   const int j = a.j0 + (int)(blockIdx.x / C);

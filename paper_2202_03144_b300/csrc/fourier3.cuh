@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
   uint64_t* barY = reinterpret_cast<uint64_t*>(red + F::NRED);
   uint64_t* barX = barY + 1;
 
+  pdl_wait();
+  pdl_launch();
   const int tid = threadIdx.x;
   const int c = (int)(blockIdx.x % C);
   const int j = a.j0 + (int)(blockIdx.x / C);

@@ -397,6 +397,7 @@ struct ptycho_ctx {
     double bytes;
   };
   bool prof = false;
+  bool pdl = false;   // launch with programmatic stream serialization (chains of small kernels)
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::string> fam_names;
@@ -503,6 +504,25 @@ int launch(ptycho_ctx* ctx, const char* name, double bytes, Fn&& fn) {
   return 0;
 }
 
+// A kernel launch on the context's stream, with programmatic stream
+// serialization when ctx->pdl is set (the kernel then calls pdl_wait() before
+// touching what its predecessor writes or reads).
+template <class... KArgs, class... Args>
+void launch_k(ptycho_ctx* ctx, void (*kern)(KArgs...), dim3 grid, dim3 block, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = ctx->st;
+  cudaLaunchAttribute attr[1];
+  if (ctx->pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 int collect_profile(ptycho_ctx* ctx) {
   if (ctx->pending.empty()) return 0;
   CK(cudaStreamSynchronize(ctx->st));
@@ -567,15 +587,22 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
     cfg.blockDim = dim3((unsigned)ks->NT2);
     cfg.dynamicSmemBytes = ks->smem_fourier;
     cfg.stream = ctx->st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    unsigned na = 0;
     if (ks->C > 1) {
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = ks->C;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
+      attr[na].id = cudaLaunchAttributeClusterDimension;
+      attr[na].val.clusterDim.x = ks->C;
+      attr[na].val.clusterDim.y = 1;
+      attr[na].val.clusterDim.z = 1;
+      ++na;
     }
+    if (ctx->pdl) {
+      attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[na].val.programmaticStreamSerializationAllowed = 1;
+      ++na;
+    }
+    cfg.attrs = na ? attr : nullptr;
+    cfg.numAttrs = na;
     FourierFn fn = ks->fourier;
     const int row = spec_row(mode);
     if (row >= 0 && a.istore >= 0 && a.istore < 3 && ks->spec[row][a.istore]) {
@@ -625,9 +652,10 @@ int launch_shift_one_m(ptycho_ctx* ctx, int bye, int bxe, const float2* src, flo
   constexpr int LN = 8;
   const int K = ctx->p.K, S = ctx->S;
   return launch(ctx, "shift_one", 16.0 * K * (double)M * M, [&] {
-    k_shift_build_rows<M, LN><<<dim3(K * M / LN, 1), SH_NT, 0, ctx->st>>>(src, ctx->stmp, K, S, ctx->tw, 1, bxe);
-    k_shift_build_cols<M, LN><<<dim3(M / LN, K, 1), SH_NT, 0, ctx->st>>>(ctx->stmp, dst, K, S, ctx->tw, 1, bye, 0,
-                                                                         nullptr);
+    launch_k(ctx, k_shift_build_rows<M, LN>, dim3(K * M / LN, 1), dim3(SH_NT), src, (float2*)ctx->stmp, K, S,
+             (const float2*)ctx->tw, 1, bxe);
+    launch_k(ctx, k_shift_build_cols<M, LN>, dim3(M / LN, K, 1), dim3(SH_NT), (const float2*)ctx->stmp, dst, K, S,
+             (const float2*)ctx->tw, 1, bye, 0, (const float*)nullptr);
   });
 }
 
@@ -1127,17 +1155,22 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
       ctx->f_xoff = -1;
       if (r) return r;
       if (int rr = launch(ctx, "epie_update", 8.0 * (3 * K + 2) * MM, [&] {
-            k_epie_sub_max<K><<<EPS_MX, EPS_NT, 0, ctx->st>>>(ctx->P, ctx->O, ctx->p.obj_nx, ctx->pos, j, M, mx);
-            k_epie_sub_update<K><<<(MM + 255) / 256, 256, 0, ctx->st>>>(ctx->O, ctx->p.obj_nx, ctx->pos, j, M, ctx->P,
-                                                                         D, mx, (float)ctx->p.epie_alpha,
-                                                                         (float)ctx->p.epie_beta, upd ? 1 : 0);
+            launch_k(ctx, k_epie_sub_max<K>, dim3(EPS_MX), dim3(EPS_NT), (const float2*)ctx->P,
+                     (const float2*)ctx->O, ctx->p.obj_nx, (const int2*)ctx->pos, j, M, mx);
+            launch_k(ctx, k_epie_sub_update<K>, dim3((MM + 255) / 256), dim3(256), ctx->O, ctx->p.obj_nx,
+                     (const int2*)ctx->pos, j, M, ctx->P, (const float2*)D, (const float2*)mx,
+                     (float)ctx->p.epie_alpha, (float)ctx->p.epie_beta, upd ? 1 : 0);
           }))
         return rr;
     }
     return 0;
   };
   for (int it = 0; it < n; ++it) {
+    // chains of small dependent kernels: overlap each launch with its
+    // predecessor's tail (not while profiling: events sit between launches)
+    ctx->pdl = !ctx->prof;
     const int r = sweep(it);
+    ctx->pdl = false;
     if (cy != h || cx != h) {  // back to the unshifted frame (also after an error)
       const int rb = launch_shift_one(ctx, h - cy + h, h - cx + h, ctx->P, ctx->P);
       cy = cx = h;

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_rows(const float2* __rest
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
   sh_load_tw<M>(tw_s, tw);
+  pdl_wait();
+  pdl_launch();
   const int row0 = blockIdx.x * LN;
   const int bx = one ? bxe : (int)blockIdx.y;
   const int slot = one ? 0 : bx;
@@ -109,6 +111,8 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __rest
   __shared__ float2 s[LN * C::PITCH];
   __shared__ float2 tw_s[M];
   sh_load_tw<M>(tw_s, tw);
+  pdl_wait();
+  pdl_launch();
   const int c0 = blockIdx.x * LN, k = blockIdx.y;
   const int b = one ? 0 : (int)blockIdx.z;
   const int by = one ? bye : b / S, bx = b % S;
