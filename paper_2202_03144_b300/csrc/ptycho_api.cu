@@ -304,6 +304,8 @@ struct ptycho_ctx {
   cudaStream_t st = nullptr;
   const KernelSet* ks = nullptr;
   const KernelSet* eks = nullptr;  // kernel set of the ePIE sweep
+  const KernelSet* fks_one = nullptr;  // Fourier kernels of one-position passes (sub-pixel ePIE)
+  const KernelSet* f_ks = nullptr;     // set by a pass that overrides ks
   int C = 1;
   // device state
   float2* O = nullptr;
@@ -553,7 +555,7 @@ const unsigned short* bin_view(const ptycho_ctx* ctx);
 int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, int nj, const char* name) {
   if (!ctx->f_P)
     if (int r = refresh_probe_table(ctx)) return r;
-  const KernelSet* ks = ctx->ks;
+  const KernelSet* ks = ctx->f_ks ? ctx->f_ks : ctx->ks;
   Fourier2Args a{};
   a.O = ctx->O;
   a.nx = ctx->p.obj_nx;
@@ -1150,9 +1152,11 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
       }
       ctx->f_P = ctx->P;
       ctx->f_xoff = j;
+      ctx->f_ks = ctx->fks_one;
       int r = launch_fourier(ctx, FM_CHI, D, nullptr, j, 1, "fourier_epie");
       ctx->f_P = nullptr;
       ctx->f_xoff = -1;
+      ctx->f_ks = nullptr;
       if (r) return r;
       if (int rr = launch(ctx, "epie_update", 8.0 * (3 * K + 2) * MM, [&] {
             launch_k(ctx, k_epie_sub_max<K>, dim3(EPS_MX), dim3(EPS_NT), (const float2*)ctx->P,
@@ -1648,6 +1652,13 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (e == cudaSuccess) e = set_fourier_attributes(ks);
   if (e == cudaSuccess) ctx->eks = epie_set(p, ks, optin);
   const KernelSet* eks = ctx->eks;
+  // one position at a time (sub-pixel ePIE) the largest cluster is the
+  // shortest chain: the ePIE set's Fourier kernels where they fit
+  ctx->fks_one = ks;
+  if (e == cudaSuccess && eks && eks != ks && eks->C > ks->C && eks->smem_fourier <= (size_t)optin &&
+      eks->smem_spec <= (size_t)optin && set_fourier_attributes(eks) == cudaSuccess)
+    ctx->fks_one = eks;
+  cudaGetLastError();
   // the register-resident sweep where it is compiled and fits, else the
   // shared-memory-pass one
   ctx->epie2 = e == cudaSuccess && eks->epie2 != nullptr && eks->smem_epie2 <= (size_t)optin;
