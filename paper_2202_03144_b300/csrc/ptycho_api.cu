@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -651,7 +652,9 @@ int launch_shift_m(ptycho_ctx* ctx, bool build, const float2* src, float2* dst, 
 // (src and dst may be the same array: the row pass goes through stmp).
 template <int M>
 int launch_shift_one_m(ptycho_ctx* ctx, int bye, int bxe, const float2* src, float2* dst) {
-  constexpr int LN = 8;
+  // one probe's shift is latency-bound: the fewest lines per CTA that still
+  // give every thread an element (LN M a multiple of the block size)
+  constexpr int LN = SH_NT / std::gcd(M, SH_NT);
   const int K = ctx->p.K, S = ctx->S;
   return launch(ctx, "shift_one", 16.0 * K * (double)M * M, [&] {
     launch_k(ctx, k_shift_build_rows<M, LN>, dim3(K * M / LN, 1), dim3(SH_NT), src, (float2*)ctx->stmp, K, S,
