@@ -1,7 +1,8 @@
 // Sub-pixel ePIE: the per-position steps around the Fourier pass.  The probe
 // is held in the frame of position j, P_j = T_delta_j P, and
 // Delta = F^-1 Pi(F(P_j O_j)) - P_j O_j comes from the residual pass:
-//   pmax = max_u sum_k |P_j,k(u)|^2,  omax = max_u |O_j(u)|^2      (k_epie_sub_max)
+//   pmax = max_u sum_k |P_j,k(u)|^2,  omax = max_u |O_j(u)|^2      (k_epie_sub_max, or
+//        the frame change's column pass when the frame changes: k_shift_one_cols)
 //   O_j   += alpha sum_k conj(P_j,k) Delta_k / pmax               (k_epie_sub_update)
 //   P_j,k += beta conj(O_j_old) Delta_k / omax                    (k_epie_sub_update)
 // -- the probe step in position j's frame; T_-delta_j of it is the step of
@@ -13,6 +14,7 @@ namespace ptycho {
 
 constexpr int EPS_NT = 256;
 constexpr int EPS_MX = 32;   // CTAs of the maxima kernel (partial maxima, reduced by the update)
+constexpr int EPS_MX_CAP = 256;  // partial maxima buffer: EPS_MX, or one per column block of the frame change
 
 // grid EPS_MX: out[b] = (max sum_k |P_j,k|^2, max |O_j|^2) over CTA b's pixels
 template <int K>
@@ -41,17 +43,24 @@ template <int K>
 __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O, int nx, const int2* __restrict__ pos,
                                                          int j, int M, float2* __restrict__ Pj,
                                                          const float2* __restrict__ D, const float2* __restrict__ mx,
-                                                         float alpha, float beta, int upd) {
+                                                         int nmx, float alpha, float beta, int upd) {
+  __shared__ float red[32];
+  __shared__ float2 tot;
   pdl_wait();
   pdl_launch();
   const int2 p = pos[j];
   const int MM = M * M;
   float pmax = 0.f, omax = 0.f;
-#pragma unroll 8
-  for (int b = 0; b < EPS_MX; ++b) {
+  for (int b = threadIdx.x; b < nmx; b += 256) {
     pmax = fmaxf(pmax, mx[b].x);
     omax = fmaxf(omax, mx[b].y);
   }
+  pmax = block_max_f<256>(pmax, red);
+  omax = block_max_f<256>(omax, red);
+  if (threadIdx.x == 0) tot = make_float2(pmax, omax);
+  __syncthreads();
+  pmax = tot.x;
+  omax = tot.y;
   const float sa = pmax > 0.f ? alpha / pmax : 0.f;
   const float sb = (upd && omax > 0.f) ? beta / omax : 0.f;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < MM; u += gridDim.x * blockDim.x) {

@@ -677,6 +677,38 @@ int launch_shift_one(ptycho_ctx* ctx, int bye, int bxe, const float2* src, float
   }
 }
 
+// The frame change of the sub-pixel ePIE sweep: P = T_delta P in place,
+// delta = (bye - S/2, bxe - S/2) / S, and the partial maxima of the step at
+// position j (sum_k |P_k|^2 of the shifted probe, |O_j|^2) into mx; *nmx is
+// their count.
+template <int M, int K>
+int launch_frame_change_m(ptycho_ctx* ctx, int bye, int bxe, int j, float2* mx, int* nmx) {
+  constexpr int LN = SH_NT / std::gcd(M, SH_NT);
+  static_assert(M / LN <= EPS_MX_CAP, "partial maxima buffer");
+  const int S = ctx->S;
+  *nmx = M / LN;
+  return launch(ctx, "shift_one", 16.0 * K * (double)M * M, [&] {
+    launch_k(ctx, k_shift_build_rows<M, LN>, dim3(K * M / LN, 1), dim3(SH_NT), (const float2*)ctx->P,
+             (float2*)ctx->stmp, K, S, (const float2*)ctx->tw, 1, bxe);
+    launch_k(ctx, k_shift_one_cols<M, LN, K>, dim3(M / LN), dim3(SH_NT), (const float2*)ctx->stmp, ctx->P, S,
+             (const float2*)ctx->tw, bye, (const float2*)ctx->O, ctx->p.obj_nx, (const int2*)ctx->pos, j, mx);
+  });
+}
+
+template <int K>
+int launch_frame_change(ptycho_ctx* ctx, int bye, int bxe, int j, float2* mx, int* nmx) {
+  switch (ctx->p.M) {
+    case 16: return launch_frame_change_m<16, K>(ctx, bye, bxe, j, mx, nmx);
+    case 32: return launch_frame_change_m<32, K>(ctx, bye, bxe, j, mx, nmx);
+    case 64: return launch_frame_change_m<64, K>(ctx, bye, bxe, j, mx, nmx);
+    case 96: return launch_frame_change_m<96, K>(ctx, bye, bxe, j, mx, nmx);
+    case 128: return launch_frame_change_m<128, K>(ctx, bye, bxe, j, mx, nmx);
+    case 192: return launch_frame_change_m<192, K>(ctx, bye, bxe, j, mx, nmx);
+    case 256: return launch_frame_change_m<256, K>(ctx, bye, bxe, j, mx, nmx);
+    default: return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "sub-pixel shifts are not compiled for M=%d", ctx->p.M);
+  }
+}
+
 // build: dst[bin][k] = T_delta(bin) src[k] (times bscale[bin] if given);
 // sum: dst[k] = sum_bin T_-delta(bin) src[bin][k]
 int launch_shift(ptycho_ctx* ctx, bool build, const float2* src, float2* dst, const float* bscale) {
@@ -1148,10 +1180,16 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
     for (int s = 0; s < J; ++s) {
       const int j = ord[(size_t)it * J + s];
       const int by = ctx->bin_host[j] / S, bx = ctx->bin_host[j] % S;
-      if (by != cy || bx != cx) {
-        if (int r = launch_shift_one(ctx, by - cy + h, bx - cx + h, ctx->P, ctx->P)) return r;
+      int nmx = EPS_MX;
+      if (by != cy || bx != cx) {  // the frame change also gives the maxima
+        if (int r = launch_frame_change<K>(ctx, by - cy + h, bx - cx + h, j, mx, &nmx)) return r;
         cy = by;
         cx = bx;
+      } else if (int r = launch(ctx, "epie_max", 8.0 * (K + 1) * MM, [&] {
+                   launch_k(ctx, k_epie_sub_max<K>, dim3(EPS_MX), dim3(EPS_NT), (const float2*)ctx->P,
+                            (const float2*)ctx->O, ctx->p.obj_nx, (const int2*)ctx->pos, j, M, mx);
+                 })) {
+        return r;
       }
       ctx->f_P = ctx->P;
       ctx->f_xoff = j;
@@ -1162,10 +1200,8 @@ int run_epie_subpixel_k(ptycho_ctx* ctx, int n) {
       ctx->f_ks = nullptr;
       if (r) return r;
       if (int rr = launch(ctx, "epie_update", 8.0 * (3 * K + 2) * MM, [&] {
-            launch_k(ctx, k_epie_sub_max<K>, dim3(EPS_MX), dim3(EPS_NT), (const float2*)ctx->P,
-                     (const float2*)ctx->O, ctx->p.obj_nx, (const int2*)ctx->pos, j, M, mx);
             launch_k(ctx, k_epie_sub_update<K>, dim3((MM + 255) / 256), dim3(256), ctx->O, ctx->p.obj_nx,
-                     (const int2*)ctx->pos, j, M, ctx->P, (const float2*)D, (const float2*)mx,
+                     (const int2*)ctx->pos, j, M, ctx->P, (const float2*)D, (const float2*)mx, nmx,
                      (float)ctx->p.epie_alpha, (float)ctx->p.epie_beta, upd ? 1 : 0);
           }))
         return rr;
@@ -1368,7 +1404,7 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
     if (int r = dalloc(ctx, &ctx->cg_q, KMM)) return r;
     if (int r = dalloc(ctx, &ctx->cg_part, 3 * ((KMM + CG_NT - 1) / CG_NT))) return r;
     if (int r = dalloc(ctx, &ctx->pos_corr, (size_t)J)) return r;
-    if (int r = dalloc(ctx, &ctx->ep_mx, (size_t)EPS_MX)) return r;
+    if (int r = dalloc(ctx, &ctx->ep_mx, (size_t)EPS_MX_CAP)) return r;
     CK(cudaMemcpy(ctx->pbin, bin.data(), J * sizeof(unsigned short), cudaMemcpyHostToDevice));
     ctx->bin_host = bin;
     if (int r = build_subpixel_groups(ctx, bin)) return r;

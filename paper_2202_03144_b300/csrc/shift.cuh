@@ -141,6 +141,59 @@ __global__ void __launch_bounds__(SH_NT) k_shift_build_cols(const float2* __rest
   }
 }
 
+// Single shift, columns, all K modes of LN columns per CTA (the sub-pixel
+// ePIE frame change): grid (M/LN).  dst[k][:][x] = T_y(dy(bye)) tmp[k][:][x]
+// for the CTA's columns x, and mx[blockIdx.x] = (max sum_k |dst_k|^2,
+// max |O_j|^2) over those columns: the partial probe and object maxima of the
+// ePIE step at position j (patch corner pos[j]).
+template <int M, int LN, int K>
+__global__ void __launch_bounds__(SH_NT) k_shift_one_cols(const float2* __restrict__ tmp, float2* __restrict__ dst,
+                                                          int S, const float2* __restrict__ tw, int bye,
+                                                          const float2* __restrict__ O, int nx,
+                                                          const int2* __restrict__ pos, int j,
+                                                          float2* __restrict__ mx) {
+  constexpr int L = K * LN;   // line l = k LN + (column - c0)
+  using C = ShCfg<M, L>;
+  __shared__ float2 s[L * C::PITCH];
+  __shared__ float2 tw_s[M];
+  __shared__ float red[32];
+  sh_load_tw<M>(tw_s, tw);
+  pdl_wait();
+  pdl_launch();
+  const int c0 = blockIdx.x * LN;
+  for (int e = threadIdx.x; e < L * M; e += SH_NT) {
+    const int i = e / L, l = e % L;
+    s[l * C::PITCH + i] = tmp[((size_t)(l / LN) * M + i) * M + c0 + l % LN];
+  }
+  const int2 p = pos[j];
+  float om = 0.f;
+  for (int e = threadIdx.x; e < LN * M; e += SH_NT)
+    om = fmaxf(om, cabs2(O[(size_t)(p.x + e / LN) * nx + p.y + c0 + e % LN]));
+  __syncthreads();
+  sh_fft<M, L, false>(s, tw_s);
+  for (int e = threadIdx.x; e < L * M; e += SH_NT) {
+    const int l = e / M, i = e % M;
+    s[l * C::PITCH + i] = cmul(s[l * C::PITCH + i], sh_phase(i, M, bye, S, 1));
+  }
+  __syncthreads();
+  sh_fft<M, L, true>(s, tw_s);
+  float pm = 0.f;
+  for (int e = threadIdx.x; e < LN * M; e += SH_NT) {
+    const int i = e / LN, lc = e % LN;
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 v = s[(k * LN + lc) * C::PITCH + i];
+      dst[((size_t)k * M + i) * M + c0 + lc] = v;
+      a += cabs2(v);
+    }
+    pm = fmaxf(pm, a);
+  }
+  pm = block_max_f<SH_NT>(pm, red);
+  om = block_max_f<SH_NT>(om, red);
+  if (threadIdx.x == 0) mx[blockIdx.x] = make_float2(pm, om);
+}
+
 // sum, columns: grid (M/LN, K, S).  tmp[bx][k][:][x] = sum_by T_y(-dy(by)) bins[by S + bx][k][:][x];
 // bgrp[b] == bgrp[b + 1] marks a bin without positions (its sum is zero).
 template <int M, int LN>
