@@ -548,7 +548,7 @@ def main():
     # shape that capture measured.
     traffic = None
     if top[0] == "fourier_chi" and (M, K) == (256, 1) and not args.cluster:
-        traffic = 771.0e3 * J
+        traffic = 769.8e3 * J
     if top[0].startswith("fourier"):
         # The fused Fourier kernel is bound by FP32 arithmetic issue, not by
         # DRAM (ncu: 16% DRAM, 50% issue-active): report it against the FP32
