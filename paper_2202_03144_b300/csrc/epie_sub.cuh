@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(EPS_NT) k_epie_sub_max(const float2* __restric
   if (threadIdx.x == 0) out[blockIdx.x] = make_float2(pm, om);
 }
 
+// grid MM / 256 (rounded up), one pixel per thread: the pixel's loads are
+// issued before the partial maxima are reduced
 template <int K>
 __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O, int nx, const int2* __restrict__ pos,
                                                          int j, int M, float2* __restrict__ Pj,
@@ -50,6 +52,19 @@ __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O,
   pdl_launch();
   const int2 p = pos[j];
   const int MM = M * M;
+  const int u = blockIdx.x * 256 + threadIdx.x;
+  const bool act = u < MM;
+  float2* op = nullptr;
+  float2 o = make_float2(0.f, 0.f), d[K], pk[K];
+  if (act) {
+    op = O + (size_t)(p.x + u / M) * nx + p.y + u % M;
+    o = *op;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      d[k] = D[(size_t)k * MM + u];
+      pk[k] = Pj[(size_t)k * MM + u];
+    }
+  }
   float pmax = 0.f, omax = 0.f;
   for (int b = threadIdx.x; b < nmx; b += 256) {
     pmax = fmaxf(pmax, mx[b].x);
@@ -61,21 +76,16 @@ __global__ void __launch_bounds__(256) k_epie_sub_update(float2* __restrict__ O,
   __syncthreads();
   pmax = tot.x;
   omax = tot.y;
+  if (!act) return;
   const float sa = pmax > 0.f ? alpha / pmax : 0.f;
   const float sb = (upd && omax > 0.f) ? beta / omax : 0.f;
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < MM; u += gridDim.x * blockDim.x) {
-    float2* op = O + (size_t)(p.x + u / M) * nx + p.y + u % M;
-    const float2 o = *op;
-    float2 num = make_float2(0.f, 0.f);
+  float2 num = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float2 d = D[(size_t)k * MM + u];
-      const float2 pk = Pj[(size_t)k * MM + u];
-      num = cadd(num, cconjmul(pk, d));
-      if (upd) Pj[(size_t)k * MM + u] = cadd(pk, cscale(cconjmul(o, d), sb));
-    }
-    *op = cadd(o, cscale(num, sa));
+  for (int k = 0; k < K; ++k) {
+    num = cadd(num, cconjmul(pk[k], d[k]));
+    if (upd) Pj[(size_t)k * MM + u] = cadd(pk[k], cscale(cconjmul(o, d[k]), sb));
   }
+  *op = cadd(o, cscale(num, sa));
 }
 
 }  // namespace ptycho

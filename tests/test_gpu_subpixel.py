@@ -9,7 +9,7 @@ import pytest
 
 from gpu_cases import subpixel_scan
 from oracle import ptycho_oracle as orc
-from paper_2202_03144_b300 import api
+from paper_2202_03144_b300 import api, synth
 from util import align_global, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -370,3 +370,39 @@ def test_refinement_improves_reconstruction():
             out[refine] = (r.fourier_error(), float(np.sqrt(np.mean(err ** 2))))
     (E0, d0), (E1, d1) = out[False], out[True]
     assert E1 < 0.8 * E0 and d1 < d0, out
+
+
+def _offset_scan(M, K, S, offsets, grid=3, seed=40):
+    """A raster whose positions carry the given fractional offsets (cycled
+    over the positions in scan order), with the oracle's sub-pixel forward
+    model."""
+    step = max(2, M // 4)
+    P = synth.make_probe(M, K, R=M / 4.0, sigma=M / 16.0, c=0.6 / M)
+    base = np.rint(synth.raster_positions(grid, grid, step, 1, 1, seed=seed + 1))
+    off = np.array([offsets[i % len(offsets)] for i in range(len(base))], dtype=np.float64)
+    pos = (base + off).astype(np.float32).astype(np.float64)
+    corner, delta = orc.subpixel_positions(pos, S)
+    ny, nx = int(corner[:, 0].max()) + M, int(corner[:, 1].max()) + M
+    O = synth.make_object(ny, nx, seed=seed + 2, smooth=max(1.0, M / 16))
+    I = orc.far_field_intensity(O, P, corner, delta)
+    I = synth.poisson(I * 1e6 / I.sum(axis=(1, 2)).mean(), seed=seed + 3)
+    return dict(M=M, K=K, S=S, P=P, O=O, pos=pos, corner=corner, delta=delta, I=I,
+                O0=synth.make_object(ny, nx, seed=seed + 4, smooth=max(1.0, M / 16)),
+                P0=synth.noisy_probe(P, 0.1, seed=seed + 5), shape=(ny, nx))
+
+
+@pytest.mark.parametrize("M,K,C", [(32, 3, 4), (128, 3, 8)], ids=lambda v: str(v))
+@pytest.mark.parametrize("frames", ["one_bin", "every_position"])
+def test_subpixel_epie_frame_paths(M, K, C, frames):
+    """The sub-pixel ePIE sweep takes the step's maxima from the frame
+    change when the probe's frame moves, else from a separate maxima
+    kernel.  One bin for every position (after the first, the frame never
+    moves) and alternating bins in visiting order (identity order: it moves
+    at every position) each against the oracle, two sweeps."""
+    S = 8
+    offsets = [(0.3, 0.6)] if frames == "one_bin" else [(0.3, 0.6), (0.8, 0.1)]
+    c = _offset_scan(M, K, S, offsets)
+    bins = {tuple(b) for b in np.round(c["delta"] * S).astype(int)}
+    assert len(bins) == len(offsets)
+    res = _compare(c, "epie", 2, cluster=C, seed=0)
+    assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
