@@ -48,10 +48,6 @@ __device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t ba
 __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // Bounded wait on phase 0 of a transpose barrier.  Gives up after ~2^20
 // polls, or as soon as another CTA has raised the error flag (checked every
 // 256 polls), so that a fault in one cluster cannot stall the whole grid.

@@ -39,6 +39,9 @@ constexpr int PROBE_NT = 256;
 // Step-size kernel: one pixel pair per thread per step at 4 CTAs per SM
 // measured fastest (3.9 TB/s against 3.6 for two pairs at the default
 // occupancy); it also reads ~40 B/pixel from L2 (O, dO, P, dP) per 8 B of chi.
+#ifndef PT_STEP_PF
+#define PT_STEP_PF 4      // residual L2 prefetch distance of the step-size kernel, in loop steps (0: none)
+#endif
 #ifndef PT_STEP_MINB
 #define PT_STEP_MINB 4    // occupancy hint of the LSQML step-size kernel
 #endif
@@ -480,8 +483,23 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
   // the object pixel pair is 16-byte aligned when the patch's first object
   // column and the row length are even (uniform over the block)
   const bool pairs = ((p.y | a.nx) & 1) == 0;
+  // this position's residuals, streamed from HBM: thread 0 keeps the next
+  // PT_STEP_PF loop steps' chunks (STEP values per mode) on their way to L2
+  const float2* xj = a.X + (size_t)(j - a.xoff) * K * MM;
+  if (PT_STEP_PF > 0 && threadIdx.x == 0)
+    for (int q = 0; q < PT_STEP_PF && q * STEP < MM; ++q)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        prefetch_l2(xj + (size_t)k * MM + q * STEP, (uint32_t)(min(STEP, MM - q * STEP) * sizeof(float2)));
   PT_UNROLL(PT_STEP_UNROLL)
   for (; u < MM; u += STEP) {
+    if (PT_STEP_PF > 0 && threadIdx.x == 0) {
+      const int ua = u + PT_STEP_PF * STEP;   // thread 0's u is the step's first value
+      if (ua < MM)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          prefetch_l2(xj + (size_t)k * MM + ua, (uint32_t)(min(STEP, MM - ua) * sizeof(float2)));
+    }
     const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
     float2 o0, o1, d0, d1;
     if (pairs) {
@@ -497,7 +515,7 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       pr[k] = __ldg(reinterpret_cast<const float4*>(a.P + boff + (size_t)k * MM + u));
-      xv[k] = __ldcs(reinterpret_cast<const float4*>(a.X + ((size_t)(j - a.xoff) * K + k) * MM + u));
+      xv[k] = __ldcs(reinterpret_cast<const float4*>(xj + (size_t)k * MM + u));
       dp[k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + boff + (size_t)k * MM + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
