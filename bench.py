@@ -328,7 +328,7 @@ def run_epie(api, torch, stream, iters=3, warm=1, subpixel=0):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        cl = r.epie_cluster if not subpixel else r.cluster
+        cl = r.epie_cluster
         E = r.fourier_error()
         r.close()
     out = {"value": len(pos) * iters / (ms / 1e3), "unit": UNIT, "ms_per_iteration": ms / iters,

@@ -298,7 +298,10 @@ int ptycho_get_profile(ptycho_ctx* ctx, ptycho_kernel_stat* out, int max, int* n
 int ptycho_cluster_size(const ptycho_ctx* ctx);
 
 /* CTAs of the persistent ePIE sweep (the widest compiled cluster for (M, K)
- * unless ptycho_params.cluster fixed it); 0 if no ePIE kernel fits. */
+ * unless ptycho_params.cluster fixed it); 0 if no ePIE kernel fits.  With
+ * sub-pixel positions (ptycho_params.subpixel > 0) the sweep visits one
+ * position at a time through the general kernels, and this is the cluster
+ * of that per-position Fourier pass (chosen the same way). */
 int ptycho_epie_cluster_size(const ptycho_ctx* ctx);
 
 /* ---- Many reconstructions per launch --------------------------------------

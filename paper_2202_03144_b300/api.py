@@ -431,7 +431,8 @@ class Reconstruction:
 
     @property
     def epie_cluster(self):
-        """CTAs of the ePIE sweep."""
+        """CTAs of the ePIE sweep (with sub-pixel positions: of its
+        per-position Fourier pass)."""
         return lib().ptycho_epie_cluster_size(self.ctx)
 
     @property

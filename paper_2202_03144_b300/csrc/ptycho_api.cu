@@ -2111,7 +2111,11 @@ int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* psi, int on_device) {
 }
 long long ptycho_launch_count(const ptycho_ctx* ctx) { return ctx ? ctx->launches : -1; }
 int ptycho_cluster_size(const ptycho_ctx* ctx) { return ctx ? ctx->C : 0; }
-int ptycho_epie_cluster_size(const ptycho_ctx* ctx) { return ctx && ctx->eks && ctx->epie_ok ? ctx->eks->C : 0; }
+int ptycho_epie_cluster_size(const ptycho_ctx* ctx) {
+  if (!ctx) return 0;
+  if (ctx->S) return ctx->fks_one ? ctx->fks_one->C : ctx->C;
+  return ctx->eks && ctx->epie_ok ? ctx->eks->C : 0;
+}
 
 int ptycho_set_profiling(ptycho_ctx* ctx, int enabled) {
   if (!ctx) return PTYCHO_ERR_ARG;

@@ -531,6 +531,11 @@ def test_epie_runs_on_the_widest_cluster_by_default():
         assert r.cluster == 8 and r.epie_cluster == 16
     with api.Reconstruction(128, 3, len(c["pos"]), c["shape"], cluster=4) as r:
         assert r.cluster == 4 and r.epie_cluster == 4
+    # sub-pixel positions: the per-position Fourier pass takes the same cluster
+    with api.Reconstruction(128, 3, len(c["pos"]), c["shape"], subpixel=8) as r:
+        assert r.cluster == 8 and r.epie_cluster == 16
+    with api.Reconstruction(128, 3, len(c["pos"]), c["shape"], cluster=4, subpixel=8) as r:
+        assert r.cluster == 4 and r.epie_cluster == 4
 
 
 def test_precision_report_256_detector():
