@@ -406,3 +406,19 @@ def test_subpixel_epie_frame_paths(M, K, C, frames):
     assert len(bins) == len(offsets)
     res = _compare(c, "epie", 2, cluster=C, seed=0)
     assert res["eo"] < TOL_REC and res["ep"] < TOL_REC, res
+
+
+@pytest.mark.parametrize("M,K,C", [(64, 1, 2), (128, 3, 8)], ids=lambda v: str(v))
+def test_subpixel_epie_dependent_launch_is_exact(M, K, C):
+    """The sweep's per-position kernels are issued with programmatic
+    dependent launch; with profiling on (events between launches) they are
+    ordinary launches.  Both must give the same bits: every kernel waits for
+    its predecessor before touching what it writes or reads."""
+    c = subpixel_scan(M, K, 8, grid=4, photons=1e6)
+    out = []
+    for prof in (False, True):
+        with _recon(c, cluster=C, seed=3) as r:
+            r.set_profiling(prof)
+            r.iterate("epie", 2)
+            out.append((r.get_object(), r.get_probe()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
