@@ -258,15 +258,15 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7, group_bytes=N
 def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
     """Wall time and iterations for 16-bit amplitude storage to reach the
     Fourier error that plain FP32 LSQML reaches after n_ref iterations.  Every
-    run is judged by the same FP32-stored context (its (O, P) copied over at
+    run is scored by the same FP32-stored context (its (O, P) copied over at
     each check), so the error is always measured against the FP32 data."""
     M, K, J = w["M"], w["K"], w["grid"] ** 2
     shape = (w["obj"], w["obj"])
     out = {}
     eps = None
     with torch.cuda.stream(stream):
-        judge = api.Reconstruction(M, K, J, shape, stream=stream.cuda_stream)
-        judge.set_data(I, pos)
+        scorer = api.Reconstruction(M, K, J, shape, stream=stream.cuda_stream)
+        scorer.set_data(I, pos)
         Ob = torch.empty(shape, dtype=torch.complex64, device="cuda")
         Pb = torch.empty((K, M, M), dtype=torch.complex64, device="cuda")
         for store in ("f32", "f16", "bf16"):
@@ -282,8 +282,8 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
                 it += check
                 r.get_object(Ob)
                 r.get_probe(Pb)
-                judge.set_init(Ob, Pb)
-                E = judge.fourier_error()
+                scorer.set_init(Ob, Pb)
+                E = scorer.fourier_error()
                 if eps is not None and E <= eps:
                     break
             dt = time.perf_counter() - t0
@@ -291,7 +291,7 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
             if store == "f32":
                 eps = E
             out[store] = {"iterations": it, "seconds": dt, "fourier_error": E, "reached": bool(E <= eps)}
-        judge.close()
+        scorer.close()
     return {"eps": eps, "reference": f"plain FP32 LSQML after {n_ref} iterations from a flat object; errors "
                                      "measured against the FP32 data", "check_every": check, **out}
 
@@ -368,10 +368,10 @@ def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, che
     P0 = d["probe0"] * np.sqrt(float(I.sum(dim=(1, 2)).mean()) / (M * M) / np.sum(np.abs(d["probe0"]) ** 2))
     scan = dict(M=M, K=K, positions=pos, object0=d["object0"], probe0=P0)
     res = warmstart.compare(net, scan, I, alg="lsqml", n_ref=n_ref, check=check, stream=stream.cuda_stream)
-    # warm start + 16-bit amplitude storage, judged on the FP32 data
+    # warm start + 16-bit amplitude storage, scored on the FP32 data
     with torch.cuda.stream(stream):
-        judge = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream)
-        judge.set_data(I, pos)
+        scorer = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream)
+        scorer.set_data(I, pos)
         r = api.Reconstruction(M, K, len(pos), shape, stream=stream.cuda_stream, istore="f16")
         r.set_data(I, pos)
         r.set_init(scan["object0"], scan["probe0"])
@@ -386,14 +386,14 @@ def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, che
             it += check
             r.get_object(Ob)
             r.get_probe(Pb)
-            judge.set_init(Ob, Pb)
-            E = judge.fourier_error()
+            scorer.set_init(Ob, Pb)
+            E = scorer.fourier_error()
             if E <= res["eps"]:
                 break
         res["warm_f16"] = {"iterations": it, "seconds": time.perf_counter() - t0, "final_error": E,
                            "reached": bool(E <= res["eps"])}
         r.close()
-        judge.close()
+        scorer.close()
     net.close()
     res["training"] = {"frames": n_frames, "epochs": epochs, "seconds": t_train, "data_seconds": t_data,
                        "frames_per_s": n_frames * epochs / t_train, "loss_first": losses[0][1],

@@ -196,7 +196,7 @@ int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preproces
 int ptycho_set_positions(ptycho_ctx* ctx, const float* positions);
 
 /* Upload the object [obj_ny][obj_nx][2] and probe [K][M][M][2] guesses
- * (Sec. 2.2: "the probe and/or object guess can also be specified").  Either
+ * (Sec. 2.2 lets the user supply either or both starting estimates).  Either
  * pointer may be NULL to keep the current value (initially object = 1 and
  * probe = 0).  Resets the DM exit-wave state. */
 int ptycho_set_init(ptycho_ctx* ctx, const float* object, const float* probe, int on_device);
@@ -362,9 +362,9 @@ int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position);
  * frame, x = log(1 + I) / 10 of a 128 x 128 detector-centred pattern, to the
  * amplitude and phase of the central 64 x 64 object patch under the probe.
  * Its predictions, stitched together, replace the flat initial object of a
- * DM or LSQML reconstruction, which stays the judge.  Not in the paper (whose
- * "probe and/or object guess can also be specified", Sec. 2.2, is the hook it
- * uses).  Training, inference and every gradient run in this library's CUDA
+ * DM or LSQML reconstruction, which has the last word.  Not in the paper; it
+ * uses the paper's option of a user-supplied initial probe or object
+ * (Sec. 2.2).  Training, inference and every gradient run in this library's CUDA
  * kernels.
  *
  * Parameter vector (FP32, host order used by get/set): for each of the 12

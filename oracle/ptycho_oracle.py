@@ -11,7 +11,7 @@ three reconstruction algorithms but prints no formulas:
 
 * the far-field forward model -- an exit wave (probe times object patch),
   whose Fourier transform's squared modulus is the measured diffraction
-  pattern -- and the "multiple FFTs over thousands of diffraction patterns"
+  pattern -- and the batched transforms of all the diffraction patterns
   are stated in Sec. 2.3 (Data reconstruction back end module);
 * ePIE (Maiden & Rodenburg 2009), DM (Thibault et al. 2009, 2008) and LSQML
   (Thibault & Menzel 2013; Odstrcil et al. 2018) are named in the Abstract,

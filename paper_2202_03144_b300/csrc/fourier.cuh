@@ -1,7 +1,7 @@
 // Fused Fourier step: exit wave -> 2-D FFT -> modulus projection ->
 // inverse 2-D FFT -> algorithm epilogue, one scan position per thread-block
-// cluster.  This is the "multiple FFTs over thousands of diffraction
-// patterns" of the ptychopy paper's back end (Sec. 2.3), fused so that the
+// cluster.  This is the batched transform of every diffraction pattern that
+// the paper's back end runs on the GPU (Sec. 2.3), fused so that the
 // per-position exit waves make exactly one trip through HBM.
 //
 // Work split.  The K x M x M complex exit waves of one position are shared by

@@ -2,7 +2,7 @@
 // diffraction frame, log(1 + I) of a 128 x 128 detector-centred pattern, to
 // the amplitude and phase of the central 64 x 64 object patch under the
 // probe.  Predicted patches are stitched into the initial object of a DM or
-// LSQML reconstruction (the iterations remain the judge).
+// LSQML reconstruction (the iterations have the last word).
 //
 // Layers (3 x 3 kernels, padding 1; "s2" = stride 2, "up" = nearest x2
 // upsampling of the input folded into the convolution's index map):
