@@ -48,6 +48,17 @@ def workload_desc(w=WORKLOAD):
             f"Poisson {w['photons']:.0e} photons/frame")
 
 
+def bench_config(world, w=WORKLOAD):
+    """The workload both arms report (the reference arm times bounded
+    samples of it, described in its cpu_baseline)."""
+    M, K, J = w["M"], w["K"], w["grid"] ** 2
+    return {"workload": workload_desc(w), "algorithm": "lsqml", "M": M, "K": K, "J": J,
+            "object": [w["obj"], w["obj"]], "intensity_store": "f32",
+            "l2": f"inputs larger than L2: {J * K * M * M * 8 / 1e9:.2g} GB of residuals and "
+                  f"{J * M * M * 4 / 1e9:.2g} GB of amplitudes per iteration",
+            "replicas": world}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -111,26 +122,78 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(P, O, pos, P0, I_sample_fn, w=WORKLOAD, sub=24):
-    """FP64 oracle, one LSQML iteration on a sub x sub block of the raster."""
-    from oracle import ptycho_oracle as orc
+def _block(P, O, pos, w, r0, c0, sub):
+    """The sub x sub block of the raster with its first position at raster
+    row r0, column c0, shifted to a cut of the object that holds it."""
     g = w["grid"]
-    idx = np.array([r * g + c for r in range(sub) for c in range(sub)])
+    idx = np.array([(r0 + r) * g + (c0 + c) for r in range(sub) for c in range(sub)])
     pos_s = pos[idx]
     y0 = int(np.rint(pos_s[:, 0]).min())
     x0 = int(np.rint(pos_s[:, 1]).min())
     pos_s = pos_s - [y0, x0]
     ny = int(np.rint(pos_s[:, 0]).max()) + w["M"]
     nx = int(np.rint(pos_s[:, 1]).max()) + w["M"]
-    O_s = O[y0:y0 + ny, x0:x0 + nx]
-    I_s = I_sample_fn(P, O_s, pos_s)
-    O0 = np.ones((ny, nx), complex)
-    t = time.perf_counter()
-    orc.reconstruct("lsqml", O0, P0, pos_s, I_s, 1)
-    dt = time.perf_counter() - t
-    return {"value": len(idx) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 LSQML iteration of the FP64 numpy oracle on a {sub}x{sub}-position block "
-                      f"({len(idx)} positions, same M, probe and step) in {dt:.1f} s, single-threaded FFT"}
+    return O[y0:y0 + ny, x0:x0 + nx].copy(), pos_s
+
+
+def _oracle_worker(P, O_s, pos_s, P0, photons, steps, barrier, q):
+    """One host core: the block's intensities from the oracle's forward
+    model (not timed), then `steps` timed LSQML iterations of the unchanged
+    FP64 oracle, each started together with the other workers."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    from oracle import ptycho_oracle as orc
+    I_s = oracle_intensities(P, O_s, pos_s, photons, 5)
+    O0 = np.ones(O_s.shape, complex)
+    out = []
+    for _ in range(steps):
+        barrier.wait()
+        t = time.perf_counter()
+        orc.reconstruct("lsqml", O0, P0, pos_s, I_s, 1)
+        out.append(time.perf_counter() - t)
+    q.put(out)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(P, O, pos, P0, w=WORKLOAD, sub=12, steps=1, max_workers=64):
+    """The FP64 oracle on the host's cores: one worker process per core
+    (started with spawn: the parent may already hold a CUDA context), each
+    on its own sub x sub block of the raster, the blocks' iterations started
+    together.  Returns per step (positions, wall seconds = the slowest
+    worker), the worker count and the host's core count."""
+    import multiprocessing as mp
+    cores = host_cores()
+    nb = w["grid"] // sub
+    n = max(1, min(cores, max_workers, nb * nb))
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(n), ctx.Queue()
+    procs = []
+    for i in range(n):
+        O_s, pos_s = _block(P, O, pos, w, (i // nb) * sub, (i % nb) * sub, sub)
+        p = ctx.Process(target=_oracle_worker, args=(P, O_s, pos_s, P0, w["photons"], steps, barrier, q))
+        p.start()
+        procs.append(p)
+    res = [q.get() for _ in procs]
+    for p in procs:
+        p.join()
+    per_step = [(n * sub * sub, max(r[s] for r in res)) for s in range(steps)]
+    return per_step, n, cores
+
+
+def cpu_baseline(P, O, pos, P0, w=WORKLOAD, sub=12):
+    """FP64 oracle, one LSQML iteration per host core, each on its own block."""
+    per_step, n, cores = oracle_parallel(P, O, pos, P0, w, sub=sub, steps=1)
+    units, dt = per_step[0]
+    return {"value": units / dt, "unit": UNIT, "cores": n, "kind": "oracle", "host_cores": cores,
+            "sample": f"1 LSQML iteration of the FP64 numpy oracle on each of {n} {sub}x{sub}-position blocks of "
+                      f"the raster ({units} positions, same M, probe and step), one process per core, all started "
+                      f"together; {dt:.1f} s for the slowest block"}
 
 
 def oracle_intensities(P, O, pos, photons, seed):
@@ -164,26 +227,27 @@ def aggregate_rate(units_per_rank, world, seconds):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle, as it stands, on bounded samples of the workload."""
+    """Reference arm: the FP64 oracle, as it stands, on bounded samples of the
+    workload, one process per host core."""
     _, rank, _ = rank_env()
     if rank != 0:
         return
     P, O, pos, P0 = make_scan(0)
     sub = 12
-    times = []
-    for s in range(args.warmup + args.steps):
-        cb = cpu_baseline(P, O, pos, P0, lambda P_, O_, p_: oracle_intensities(P_, O_, p_, WORKLOAD["photons"], 5),
-                          sub=sub)
-        if s >= args.warmup:
-            times.append(cb)
-    vals = [c["value"] for c in times]
+    per_step, n, cores = oracle_parallel(P, O, pos, P0, sub=sub, steps=args.warmup + args.steps)
+    timed = per_step[args.warmup:]
+    vals = [u / dt for u, dt in timed]
     v = statistics.median(vals)
-    ms = sub * sub / v * 1e3
+    units = timed[0][0]
+    ms = units / v * 1e3
+    sample = (f"per step, 1 LSQML iteration of the FP64 numpy oracle on each of {n} {sub}x{sub}-position blocks "
+              f"({units} positions), one process per host core, all started together")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_desc(), "sample": f"{sub}x{sub}-position block per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": times[-1]["sample"]},
+            "config": bench_config(args.gpus),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": n, "host_cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -549,27 +613,39 @@ def main():
     traffic = None
     if top[0] == "fourier_chi" and (M, K) == (256, 1) and not args.cluster:
         traffic = 769.8e3 * J
+    step_bytes = sum(v["bytes"] for v in prof.values())
     if top[0].startswith("fourier"):
         # The fused Fourier kernel is bound by FP32 arithmetic issue, not by
         # DRAM (ncu: 16% DRAM, 50% issue-active): report it against the FP32
-        # peak from the unit counts and clock (148 SMs x 128 FP32 lanes x 2
-        # FLOP x 2.032 GHz), counting the forward + inverse 2-D FFT of each
-        # (position, mode) at 5 N log2 N FLOP (N = M^2).
+        # rate measured on this device by the library's FMA microbenchmark
+        # (independent FMA chains on every SM; SM clock sampled meanwhile),
+        # counting the forward + inverse 2-D FFT of each (position, mode) at
+        # 5 N log2 N FLOP (N = M^2).
         fft_flop = J * K * 2 * 5.0 * M * M * np.log2(float(M * M))
-        peak_fp32 = 148 * 128 * 2 * 2.032e9 / 1e12
+        clk = Clocks(local)
+        runs = [api.fp32_fma_peak(stream.cuda_stream) for _ in range(20)]
+        pclk = clk.stop()
+        peak_fp32, _, sms = max(runs)
+        mhz = pclk["sm_mhz"] if pclk else None
         ach = fft_flop / (ms_launch / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": top[0], "achieved": ach, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": ach / peak_fp32, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                "frac": ach / peak_fp32,
+                "peak_kind": (f"measured: ptycho_fp32_fma_peak (independent FMA chains, 8 x 256 threads on each of "
+                              f"{sms} SMs, 2 flop per FMA), best of 20 runs"
+                              + (f" at a median SM clock of {mhz:.0f} MHz" if mhz else "")),
+                "peak_unit_count": {"sms": sms, "fp32_lanes_per_sm": 128,
+                                    "at_sampled_clock_tflops": (sms * 128 * 2 * mhz * 1e6 / 1e12) if mhz else None},
                 "flop_per_launch": fft_flop, "ms_per_launch": ms_launch, "traffic": traffic,
                 "traffic_source": "ncu capture of the 2500-position cut, scaled per position" if traffic else None,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
                         "peak_kind": peak_kind, "bytes_per_launch": bytes_launch},
-                "share_of_step": top[1]["ms"] / total_ms, "kernels": kernels}
+                "share_of_step": top[1]["ms"] / total_ms, "kernels": kernels,
+                "step_bytes_per_pattern": step_bytes / (prof[top[0]]["launches"] * J)}
     else:
         roof = {"bound": "hbm", "kernel": top[0], "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
                 "frac": hbm_achieved / hbm, "peak_kind": peak_kind, "bytes_per_launch": bytes_launch,
                 "ms_per_launch": ms_launch, "traffic": None, "share_of_step": top[1]["ms"] / total_ms,
-                "kernels": kernels}
+                "kernels": kernels, "step_bytes_per_pattern": step_bytes / (prof[top[0]]["launches"] * J)}
     # --- end to end through the ABI from pinned host buffers
     # inputs and outputs in pinned host memory, allocated once per job queue
     I_host = I.cpu().pin_memory()
@@ -640,16 +716,12 @@ def main():
         return
     cb = None
     if not args.no_cpu:
-        cb = cpu_baseline(P, O, pos, P0, lambda P_, O_, p_: oracle_intensities(P_, O_, p_, w["photons"], 5))
+        cb = cpu_baseline(P, O, pos, P0, w)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(), "algorithm": "lsqml", "M": M, "K": K, "J": J,
-                   "object": [w["obj"], w["obj"]], "intensity_store": "f32",
-                   "l2": f"inputs larger than L2: {J * K * M * M * 8 / 1e9:.2g} GB of residuals and "
-                         f"{J * M * M * 4 / 1e9:.2g} GB of amplitudes per iteration",
-                   "replicas": world},
+        "config": bench_config(world, w),
         "by_variant": {
             "lsqml_f32": {"value": value, "fourier_error": main_run["err"]},
             "dm_f32": {"value": rate(dm_run), "fourier_error": dm_run["err"]},

@@ -69,7 +69,7 @@ enum { PTYCHO_LIK_AMPLITUDE = 0, PTYCHO_LIK_POISSON = 1 };
 #define PTYCHO_ERR_NONFINITE (-3)   /* NaN/Inf in an input                      */
 #define PTYCHO_ERR_OOM (-4)         /* device allocation failed                 */
 #define PTYCHO_ERR_CUDA (-5)        /* a CUDA call failed                       */
-#define PTYCHO_ERR_TIMEOUT (-6)     /* reserved: a bounded device wait gave up  */
+#define PTYCHO_ERR_TIMEOUT (-6)     /* a bounded device wait gave up            */
 #define PTYCHO_ERR_DIVERGED (-7)    /* non-finite Fourier error                 */
 #define PTYCHO_ERR_STATE (-8)       /* call out of order (e.g. iterate first)   */
 #define PTYCHO_ERR_UNSUPPORTED (-9) /* (M, K) combination not compiled in       */
@@ -145,6 +145,13 @@ typedef struct {
                        results as B = 0 up to the grouping of the sums.  DM
                        (whose state is every exit wave) and sub-pixel
                        positions return PTYCHO_ERR_UNSUPPORTED.               */
+  unsigned long long mem_limit; /* 0 (default): no cap.  > 0: the context
+                       allocates at most this many bytes of device memory in
+                       total (a share of a GPU shared with other work); an
+                       allocation that would pass the cap fails with
+                       PTYCHO_ERR_OOM exactly as a failed cudaMalloc does:
+                       the call returns the code, nothing of it is applied
+                       and the context stays valid and destroyable.         */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */
@@ -219,6 +226,17 @@ int ptycho_set_likelihood(ptycho_ctx* ctx, int likelihood);
  * another algorithm ran.  Asynchronous on the context stream. */
 int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter);
 
+/* Bounded waits.  The Fourier kernels exchange data between the CTAs of a
+ * cluster and wait for it on shared-memory barriers; each such wait polls at
+ * most `polls` times (default 1 << 20, about a millisecond; 0 = give up at
+ * once).  A wait that gives up sets the context's device error flag, after
+ * which the kernel still waits (with a fixed bound) for the data already in
+ * flight into its shared memory and returns; the next call that reads the
+ * flag (get_object, get_probe, fourier_error) returns PTYCHO_ERR_TIMEOUT and
+ * clears it.  The results of the passes that gave up are meaningless.
+ * Errors: PTYCHO_ERR_ARG for polls < 0. */
+int ptycho_set_wait_limit(ptycho_ctx* ctx, long long polls);
+
 /* Copy the current object [obj_ny][obj_nx][2] / probe [K][M][M][2] out. */
 int ptycho_get_object(ptycho_ctx* ctx, float* out, int on_device);
 int ptycho_get_probe(ptycho_ctx* ctx, float* out, int on_device);
@@ -279,6 +297,10 @@ int ptycho_get_positions(ptycho_ctx* ctx, float* out);
 
 /* Number of this library's kernel launches issued so far on the context. */
 long long ptycho_launch_count(const ptycho_ctx* ctx);
+
+/* Bytes of device memory the context holds now (all its buffers; the figure
+ * ptycho_params.mem_limit caps); -1 for ctx = NULL. */
+long long ptycho_memory_used(const ptycho_ctx* ctx);
 
 /* Per-kernel timing.  When enabled, every launch is bracketed by CUDA events
  * on the context stream and its duration is accumulated per kernel family. */
@@ -430,22 +452,40 @@ int ptycho_warm_start(ptycho_ctx* ctx, ptycho_net* n);
  *               the call synchronises it before returning.
  * Limits: J <= 16384 and M <= 256, beyond which the call fails with
  * PTYCHO_ERR_ARG; (M, K) must be a compiled combination (else
- * PTYCHO_ERR_UNSUPPORTED).  Errors are reported by ptycho_last_error(NULL).
+ * PTYCHO_ERR_UNSUPPORTED).  Errors are reported by ptycho_last_error(NULL) on the calling thread.
+ * Pointer checks before any device work: object and probe must be 8-byte
+ * aligned and amplitudes 16-byte aligned, and all three must be device (or
+ * managed) memory of the current device; otherwise PTYCHO_ERR_ARG.
  *
  * Scratch: one fixed array of about 4.3 MB in device memory, defined at file
  * scope in the library, which every GPU that loads the library keeps until
- * the process exits.  The first call on each device looks up that array's
- * device address (once per device, with the device current); make that first
- * call before any stream capture.  All calls share the array: two calls whose
- * GPU work overlaps (different streams or threads) race on it and must be
- * serialised by the caller.  The call itself allocates nothing (no
- * cudaMalloc, no cudaFree, no allocating library routine). */
+ * the process exits.  Every call looks up that array's device address on
+ * the current device (a lookup, not an allocation).  All calls share the
+ * array: two calls whose GPU work overlaps (different streams or threads)
+ * race on it and must be serialised by the caller.  The call copies the
+ * positions from host memory and reads E back, synchronising its stream, so
+ * it cannot be recorded into a CUDA graph by stream capture.  The call itself
+ * allocates no device memory (no cudaMalloc, no cudaFree, no allocating
+ * library routine); it stages the positions in an ordinary host buffer. */
 int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int obj_nx, const float* probe, int M, int K,
                                  const float* positions, int J, const float* amplitudes, double* out,
                                  void* stream);
 
-/* Message of the last error on ctx (or of the last failed create if ctx is
- * NULL).  Valid until the next call on the same context. */
+/* FP32 fused multiply-add throughput of the current device, measured (a
+ * measurement utility with no counterpart in the paper: the denominator of
+ * the FP32 roofline of the instruction-bound Fourier passes).  A kernel of
+ * independent FMA chains filling every SM (8 CTAs of 256 threads per SM,
+ * 2 flops per FMA) is timed with CUDA events on `stream` (NULL = legacy
+ * default stream), best of three runs after one warm-up run.
+ * Out (host): *tflops (TFLOP/s), *ms (time of the best run, may be NULL),
+ * *sm_count (the device's multiprocessor count, may be NULL).  The rate
+ * follows the SM clock of the run: record the clock beside it.  Synchronises
+ * the stream; errors: PTYCHO_ERR_ARG (tflops NULL), PTYCHO_ERR_CUDA. */
+int ptycho_fp32_fma_peak(double* tflops, double* ms, int* sm_count, void* stream);
+
+/* Message of the last error on ctx (or, for ctx = NULL, of the last failed
+ * create or context-free call made on the calling thread: that message is
+ * kept per thread).  Valid until the next call on the same context (thread). */
 const char* ptycho_last_error(const ptycho_ctx* ctx);
 
 /* Free all device memory of ctx ("post", Sec. 3.2).  NULL is ignored. */

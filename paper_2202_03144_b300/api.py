@@ -41,7 +41,7 @@ class Params(C.Structure):
         ("epie_alpha", C.c_double), ("epie_beta", C.c_double), ("lsqml_beta", C.c_double),
         ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
         ("likelihood", C.c_int), ("probe_ortho", C.c_int), ("subpixel", C.c_int),
-        ("block_positions", C.c_int),
+        ("block_positions", C.c_int), ("mem_limit", C.c_ulonglong),
     ]
 
 
@@ -86,12 +86,15 @@ def lib() -> C.CDLL:
             "ptycho_fourier_residual": (i, [vp, f, i]),
             "ptycho_iteration": (C.c_longlong, [vp]),
             "ptycho_launch_count": (C.c_longlong, [vp]),
+            "ptycho_memory_used": (C.c_longlong, [vp]),
             "ptycho_set_profiling": (i, [vp, i]),
             "ptycho_get_profile": (i, [vp, C.POINTER(KernelStat), i, C.POINTER(i)]),
             "ptycho_cluster_size": (i, [vp]),
             "ptycho_last_error": (C.c_char_p, [vp]),
             "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
             "ptycho_set_likelihood": (i, [vp, i]),
+            "ptycho_set_wait_limit": (i, [vp, C.c_longlong]),
+            "ptycho_fp32_fma_peak": (i, [C.POINTER(d), C.POINTER(d), C.POINTER(i), vp]),
             "ptycho_orthogonalize_probe": (i, [vp]),
             "ptycho_set_iteration": (i, [vp, C.c_longlong]),
             "ptycho_epie_cluster_size": (i, [vp]),
@@ -399,6 +402,11 @@ class Reconstruction:
         v = LIKELIHOOD[likelihood] if isinstance(likelihood, str) else int(likelihood)
         _check(self.ctx, lib().ptycho_set_likelihood(self.ctx, v))
 
+    def set_wait_limit(self, polls):
+        """Polls of a cluster-transpose wait in the Fourier kernels before it
+        gives up (default 1 << 20; 0 gives up at once)."""
+        _check(self.ctx, lib().ptycho_set_wait_limit(self.ctx, int(polls)))
+
     def get_object(self, out=None):
         return get_object(self.ctx, self.obj_shape, out)
 
@@ -444,6 +452,11 @@ class Reconstruction:
         return launch_count(self.ctx)
 
     @property
+    def memory_used(self):
+        """Bytes of device memory the context holds."""
+        return lib().ptycho_memory_used(self.ctx)
+
+    @property
     def cluster(self):
         return cluster_size(self.ctx)
 
@@ -469,6 +482,14 @@ class Reconstruction:
             self.close()
         except Exception:
             pass
+
+
+def fp32_fma_peak(stream=None) -> tuple[float, float, int]:
+    """ptycho_fp32_fma_peak: (TFLOP/s, ms of the timed run, SM count) of the
+    FP32 fused multiply-add microbenchmark on the current device."""
+    tf, ms, sms = C.c_double(), C.c_double(), C.c_int()
+    _check(None, lib().ptycho_fp32_fma_peak(C.byref(tf), C.byref(ms), C.byref(sms), stream))
+    return tf.value, ms.value, sms.value
 
 
 def autotune(M: int, K: int) -> tuple[int, float]:

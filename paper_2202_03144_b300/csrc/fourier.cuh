@@ -1,8 +1,7 @@
-// Fused Fourier step: exit wave -> 2-D FFT -> modulus projection ->
-// inverse 2-D FFT -> algorithm epilogue, one scan position per thread-block
-// cluster.  This is the batched transform of every diffraction pattern that
-// the paper's back end runs on the GPU (Sec. 2.3), fused so that the
-// per-position exit waves make exactly one trip through HBM.
+// Shared-memory Fourier building blocks of the single-CTA ePIE kernel
+// (k_epie): the per-shape configuration FCfg, Stockham passes over lines held
+// in shared memory, the cluster transposes between the column-distributed and
+// the row-distributed layouts, and the modulus projection in place.
 //
 // Work split.  The K x M x M complex exit waves of one position are shared by
 // the C CTAs of a cluster (C = 1, 2, 4, 8).  Two shared-memory layouts:
@@ -16,12 +15,9 @@
 // modes of a Fourier pixel, which layout B holds locally.  The inverse runs
 // the same way backwards (rows in B, transpose B -> A, columns in A).
 //
-// Instead of keeping the exit wave z, the projection writes the Fourier
-// difference D = Pi(Z) - Z (scaled by 1/M^2), so that by linearity
-//   LSQML / ePIE:  chi = F^-1 Pi(F phi) - phi = F^-1 D           (z = phi)
-//   DM:            psi + F^-1 Pi(F(2 phi - psi)) - phi = phi + F^-1 D
-// and the DM epilogue needs only phi = P_k O_j (recomputed from L2-resident
-// O and P), not a second read of psi.
+// The projection writes the Fourier difference D = Pi(Z) - Z (scaled by
+// 1/M^2) instead of Pi(Z), so that by linearity
+//   chi = F^-1 Pi(F phi) - phi = F^-1 D.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
@@ -180,84 +176,6 @@ __device__ __forceinline__ void project_difference(float2* buf, const FourierArg
     for (int k = 0; k < F::K; ++k) buf[k * F::H * F::PB + rowL * F::PB + col] = cscale(z[k], f);
   }
   __syncthreads();
-}
-
-template <int M, int K, int C>
-__global__ void __launch_bounds__(FCfg<M, K, C>::NT) k_fourier(FourierArgs a) {
-  using F = FCfg<M, K, C>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = buf + F::SBUF;
-  double* red = reinterpret_cast<double*>(tw + M);
-  const int tid = threadIdx.x;
-  const int c = (C > 1) ? (int)(blockIdx.x % C) : 0;
-  const int j = a.j0 + (int)(blockIdx.x / C);
-  const int2 p = a.pos[j];  // (y, x)
-  const int mode = a.mode;
-
-  for (int i = tid; i < M; i += F::NT) tw[i] = a.tw[i];
-
-  // prologue: z = P_k O_j (or 2 phi - psi for DM) in layout A
-  for (int e = tid; e < K * M * F::W; e += F::NT) {
-    const int colL = e % F::W, row = (e / F::W) % M, k = e / (F::W * M);
-    const int col = c * F::W + colL;
-    const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-    const float2 pr = __ldg(a.P + ((size_t)k * M + row) * M + col);
-    float2 z = cmul(pr, o);
-    if (mode == FM_DM) {
-      const float2 psi = a.X[(((size_t)j * K + k) * M + row) * M + col];
-      z = csub(cscale(z, 2.f), psi);
-    }
-    buf[k * M * F::PA + row * F::PA + colL] = z;
-  }
-  __syncthreads();
-
-  fft2_forward<F>(buf, tw, c);
-
-  if (mode == FM_SIM || mode == FM_ERR) {
-    double en = 0.0, ed = 0.0;
-    for (int px = tid; px < F::H * M; px += F::NT) {
-      const int rowL = px / M, col = px % M;
-      const int ky = c * F::H + rowL;
-      float A2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) A2 += cabs2(buf[k * F::H * F::PB + rowL * F::PB + col]);
-      if (mode == FM_SIM) {
-        a.I_out[((size_t)j * M + ((ky + M / 2) % M)) * M + ((col + M / 2) % M)] = A2;
-      } else {
-        const float amp = load_amp(a, ((size_t)j * M + ky) * M + col, j);
-        if (amp >= 0.f) {
-          const double d = (double)sqrtf(A2) - (double)amp;
-          en += d * d;
-          ed += (double)amp * (double)amp;
-        }
-      }
-    }
-    if (mode == FM_ERR) {
-      const double sn = block_sum_d<F::NT>(en, red);
-      const double sd = block_sum_d<F::NT>(ed, red);
-      if (tid == 0) a.err_part[(size_t)j * C + c] = make_double2(sn, sd);
-    }
-    return;  // no DSMEM access after the forward transpose: safe to exit
-  }
-
-  project_difference<F>(buf, a, j, c);
-  fft2_inverse<F>(buf, tw, c);
-
-  // epilogue in layout A
-  for (int e = tid; e < K * M * F::W; e += F::NT) {
-    const int colL = e % F::W, row = (e / F::W) % M, k = e / (F::W * M);
-    const int col = c * F::W + colL;
-    const float2 d = buf[k * M * F::PA + row * F::PA + colL];
-    const size_t xi = (((size_t)j * K + k) * M + row) * M + col;
-    if (mode == FM_CHI) {
-      a.X[xi] = d;
-    } else {
-      const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
-      const float2 pr = __ldg(a.P + ((size_t)k * M + row) * M + col);
-      a.X[xi] = cadd(cmul(pr, o), d);
-    }
-  }
 }
 
 }  // namespace ptycho

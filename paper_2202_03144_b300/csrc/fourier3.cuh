@@ -48,12 +48,13 @@ __device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t ba
 __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait on phase 0 of a transpose barrier.  Gives up after ~2^20
-// polls, or as soon as another CTA has raised the error flag (checked every
-// 256 polls), so that a fault in one cluster cannot stall the whole grid.
-__device__ __forceinline__ bool mbar_wait0_or_abort(uint64_t* bar, const int* err_flag) {
+// Bounded wait on phase 0 of a transpose barrier.  Gives up after `limit`
+// polls (the context's wait limit; 0 gives up at once), or as soon as another
+// CTA has raised the error flag (checked every 256 polls), so that a fault in
+// one cluster cannot stall the whole grid.
+__device__ __forceinline__ bool mbar_wait0_or_abort(uint64_t* bar, const int* err_flag, int limit) {
   uint32_t done = 0;
-  for (int i = 0; i < (1 << 20) && !done; ++i) {
+  for (int i = 0; i < limit && !done; ++i) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
@@ -62,6 +63,21 @@ __device__ __forceinline__ bool mbar_wait0_or_abort(uint64_t* bar, const int* er
     if (!done && (i & 255) == 255 && *(volatile const int*)err_flag) break;
   }
   return done != 0;
+}
+
+// After a wait gave up: the peers' stores into this CTA's shared memory are
+// still on their way (every CTA sends its transpose data unconditionally),
+// and none may land after the CTA has exited.  Wait for all the bytes the
+// barrier expects, with a fixed bound, before leaving.
+__device__ __forceinline__ void mbar_drain0(uint64_t* bar, int* err_flag) {
+  uint32_t done = 0;
+  for (int i = 0; i < (1 << 22) && !done; ++i)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar))
+        : "memory");
+  if (!done) atomicExch(err_flag, 1);
 }
 
 template <int IST>
@@ -233,7 +249,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     load_amp();
     load_amp_k();
   }
-  if (!mbar_wait0_or_abort(barY, a.err_flag)) atomicExch(a.err_flag, 1);
+  const bool gotY = mbar_wait0_or_abort(barY, a.err_flag, a.wait_limit);
+  if (!gotY) atomicExch(a.err_flag, 1);
   // ---- row stage 1: task (k, rowL, n2'), columns n1'*R2 + n2'
   {
     const int n2 = tid % R2, rowL = (tid / R2) % H, k = tid / (R2 * H);
@@ -345,6 +362,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     // no peer writes into this CTA after its first transpose in these modes;
     // the cluster leaves together, after every CTA has received its rows
     if (mode == FM_ERR || mode == FM_SIM) {
+      if (!gotY) mbar_drain0(barY, a.err_flag);
       asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
       return;
     }
@@ -381,7 +399,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       st_async_f2(mapa_u32(smem_u32(X + cb<F>(k, f, x % W)), rank), v[n1], mapa_u32(barX_l, rank));
     }
   }
-  if (!mbar_wait0_or_abort(barX, a.err_flag)) atomicExch(a.err_flag, 1);
+  const bool gotX = mbar_wait0_or_abort(barX, a.err_flag, a.wait_limit);
+  if (!gotX) atomicExch(a.err_flag, 1);
   // ---- inverse column stage A: task (k, colL, k1), radix R2 over k2
   {
     float2 w[Q][R2];
@@ -424,6 +443,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       }
     }
   }
+  if (!gotY) mbar_drain0(barY, a.err_flag);
+  if (!gotX) mbar_drain0(barX, a.err_flag);
 }
 
 }  // namespace ptycho

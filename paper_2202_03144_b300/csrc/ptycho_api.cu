@@ -19,6 +19,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/ptycho.h"
@@ -317,6 +318,9 @@ struct ptycho_ctx {
   float2* tw = nullptr;
   float2* tw2 = nullptr;
   int* err_flag = nullptr;   // set by a device wait that gave up
+  int wait_limit = 1 << 20;  // polls of a cluster-transpose wait (ptycho_set_wait_limit)
+  size_t mem_used = 0;       // device bytes allocated by dalloc and not yet freed
+  std::unordered_map<void*, size_t> mem_blocks;
   int2* pos = nullptr;
   void* amp = nullptr;       // stored sqrt(I)
   float* amp_scale = nullptr;
@@ -432,13 +436,33 @@ int fail(ptycho_ctx* c, int code, const char* fmt, ...) {
 template <typename T>
 int dalloc(ptycho_ctx* ctx, T** p, size_t n) {
   if (*p) return 0;
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+  const size_t bytes = n * sizeof(T) + 16;
+  if (ctx->p.mem_limit && ctx->mem_used + bytes > ctx->p.mem_limit)
+    return fail(ctx, PTYCHO_ERR_OOM, "allocation of %zu bytes would pass the context's device memory limit (%zu of %llu bytes in use)",
+                bytes, ctx->mem_used, ctx->p.mem_limit);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
     return fail(ctx, PTYCHO_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
   }
+  ctx->mem_used += bytes;
+  ctx->mem_blocks[(void*)*p] = bytes;
   return 0;
+}
+
+// Free a buffer from dalloc (NULL is ignored) and return its bytes to the
+// context's budget.
+template <typename T>
+void dfree(ptycho_ctx* ctx, T*& p) {
+  if (!p) return;
+  auto it = ctx->mem_blocks.find((void*)p);
+  if (it != ctx->mem_blocks.end()) {
+    ctx->mem_used -= it->second;
+    ctx->mem_blocks.erase(it);
+  }
+  cudaFree((void*)p);
+  p = nullptr;
 }
 
 // Staging buffer of at least `bytes`, the copy stream and its events.
@@ -447,8 +471,7 @@ int ensure_stage(ptycho_ctx* ctx, size_t bytes) {
     if (ctx->stage) {
       CK(cudaStreamSynchronize(ctx->st));
       if (ctx->st_copy) CK(cudaStreamSynchronize(ctx->st_copy));
-      cudaFree(ctx->stage);
-      ctx->stage = nullptr;
+      dfree(ctx, ctx->stage);
       ctx->stage_bytes = 0;
     }
     if (int r = dalloc(ctx, &ctx->stage, bytes / 4 + 1)) return r;
@@ -571,6 +594,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   a.err_part = ctx->err_part;
   a.tw2 = ctx->tw2;
   a.err_flag = ctx->err_flag;
+  a.wait_limit = ctx->wait_limit;
   a.j0 = j0;
   a.xoff = ctx->f_xoff >= 0 ? ctx->f_xoff : ((ctx->blk.on && X == ctx->X) ? ctx->blk.j0 : 0);
   a.mode = mode;
@@ -1242,8 +1266,7 @@ int run_epie(ptycho_ctx* ctx, int n) {
   const int J = ctx->p.J;
   const std::vector<int> ord = epie_orders(ctx, n);
   if ((size_t)ctx->order_cap < ord.size()) {
-    if (ctx->order) cudaFree(ctx->order);
-    ctx->order = nullptr;
+    dfree(ctx, ctx->order);
     if (int r = dalloc(ctx, &ctx->order, ord.size())) return r;
     ctx->order_cap = (int)ord.size();
   }
@@ -1426,8 +1449,7 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
     for (int ty = t0y; ty <= t1y; ++ty)
       for (int tx = t0x; tx <= t1x; ++tx) list[fill[ty * ctx->ntx + tx]++] = j;
   }
-  if (ctx->tile_list) cudaFree(ctx->tile_list);
-  ctx->tile_list = nullptr;
+  dfree(ctx, ctx->tile_list);
   if (int r = dalloc(ctx, &ctx->tile_list, list.size() + 1)) return r;
   CK(cudaMemcpy(ctx->pos, pos.data(), J * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1468,25 +1490,33 @@ constexpr size_t NA_BYTES = NA_PART + (size_t)NOALLOC_MAX_J * NOALLOC_MAX_C * si
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-std::mutex g_noalloc_mu;
-unsigned char* g_noalloc_dev[128] = {};   // device address of the scratch, per device
+// With the caller's device current: the device address of the scratch
+// array (its host-side name is only a stand-in).  Looked up on every call --
+// a lookup allocates nothing -- so that no address outlives the module it
+// belongs to (a device reset reloads the module).
+int noalloc_scratch(unsigned char** out) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return fail(nullptr, PTYCHO_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+  *out = (unsigned char*)ptr;
+  return 0;
+}
 
-// Once per device, with that device current: resolve the device address of
-// the scratch array (the host-side name is only a stand-in).
-int noalloc_setup(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= 128) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "device index %d", dev);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_dev[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return fail(nullptr, PTYCHO_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
-    g_noalloc_dev[dev] = (unsigned char*)ptr;
+// A caller's input pointer must be device (or managed) memory of the current
+// device: a host pointer reaching the kernel would fault (or, where the GPU
+// can reach host memory, read the wrong memory).
+int noalloc_check_device_ptr(const void* p, int dev, const char* what) {
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, PTYCHO_ERR_ARG, "%s: not a CUDA pointer (%s)", what, cudaGetErrorString(e));
   }
-  *out = g_noalloc_dev[dev];
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(nullptr, PTYCHO_ERR_ARG, "%s is not device memory", what);
+  if (at.type == cudaMemoryTypeDevice && at.device != dev)
+    return fail(nullptr, PTYCHO_ERR_ARG, "%s lives on device %d, the current device is %d", what, at.device, dev);
   return 0;
 }
 
@@ -1503,35 +1533,39 @@ extern "C" int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int
     return fail(nullptr, PTYCHO_ERR_ARG,
                 "J=%d, M=%d exceed the fixed scratch of the allocation-free call (at most J=%d, M=%d)", J, M,
                 NOALLOC_MAX_J, NOALLOC_MAX_M);
+  // the kernel reads amplitudes with 16-byte bulk operations and the object
+  // and probe as 8-byte complex values
+  if ((uintptr_t)amplitudes % 16 != 0) return fail(nullptr, PTYCHO_ERR_ARG, "amplitudes are not 16-byte aligned");
+  if ((uintptr_t)object % 8 != 0 || (uintptr_t)probe % 8 != 0)
+    return fail(nullptr, PTYCHO_ERR_ARG, "object and probe must be 8-byte aligned");
   const int C = default_cluster(M, K);
   const KernelSet* ks = C ? find_set(M, K, C) : nullptr;
   if (!ks) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "no kernel compiled for M=%d K=%d", M, K);
   if (C > NOALLOC_MAX_C) return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "cluster size %d exceeds the scratch layout", C);
-  unsigned char* sc = nullptr;
-  if (int r = noalloc_setup(&sc)) return r;
-  cudaStream_t st = (cudaStream_t)stream;
-  int2* pos = (int2*)(sc + NA_POS);
-  // positions: round half-to-even, check bounds, copy through a small stack
-  // buffer (a pageable-source copy returns once the source has been staged)
-  int2 chunk[512];
-  for (int j0 = 0; j0 < J; j0 += 512) {
-    const int n = std::min(512, J - j0);
-    for (int i = 0; i < n; ++i) {
-      const float fy = positions[2 * (j0 + i)], fx = positions[2 * (j0 + i) + 1];
-      if (!std::isfinite(fy) || !std::isfinite(fx))
-        return fail(nullptr, PTYCHO_ERR_NONFINITE, "position %d is not finite", j0 + i);
-      const double y = std::nearbyint((double)fy), x = std::nearbyint((double)fx);
-      if (y < 0 || x < 0 || y + M > obj_ny || x + M > obj_nx)
-        return fail(nullptr, PTYCHO_ERR_BOUNDS, "patch %d at (%g, %g) falls outside the %dx%d object", j0 + i, y, x,
-                    obj_ny, obj_nx);
-      chunk[i] = make_int2((int)y, (int)x);
-    }
-    cudaError_t e = cudaMemcpyAsync(pos + j0, chunk, n * sizeof(int2), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "position upload: %s", cudaGetErrorString(e));
+  // positions: round half-to-even, check bounds, stage in one host buffer
+  std::vector<int2> hpos((size_t)J);
+  for (int j = 0; j < J; ++j) {
+    const float fy = positions[2 * j], fx = positions[2 * j + 1];
+    if (!std::isfinite(fy) || !std::isfinite(fx)) return fail(nullptr, PTYCHO_ERR_NONFINITE, "position %d is not finite", j);
+    const double y = std::nearbyint((double)fy), x = std::nearbyint((double)fx);
+    if (y < 0 || x < 0 || y + M > obj_ny || x + M > obj_nx)
+      return fail(nullptr, PTYCHO_ERR_BOUNDS, "patch %d at (%g, %g) falls outside the %dx%d object", j, y, x, obj_ny,
+                  obj_nx);
+    hpos[j] = make_int2((int)y, (int)x);
   }
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (int r = noalloc_check_device_ptr(object, dev, "object")) return r;
+  if (int r = noalloc_check_device_ptr(probe, dev, "probe")) return r;
+  if (int r = noalloc_check_device_ptr(amplitudes, dev, "amplitudes")) return r;
+  unsigned char* sc = nullptr;
+  if (int r = noalloc_scratch(&sc)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  int2* pos = (int2*)(sc + NA_POS);
+  e = cudaMemcpyAsync(pos, hpos.data(), (size_t)J * sizeof(int2), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(nullptr, PTYCHO_ERR_CUDA, "position upload: %s", cudaGetErrorString(e));
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e == cudaSuccess && ks->smem_fourier > (size_t)optin)
     return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "Fourier kernel needs more shared memory than the device offers");
   if (e == cudaSuccess) e = set_fourier_attributes(ks);
@@ -1548,6 +1582,7 @@ extern "C" int ptycho_fourier_error_noalloc(const float* object, int obj_ny, int
   a.err_part = (double2*)(sc + NA_PART);
   a.tw2 = (const float2*)(sc + NA_TW);
   a.err_flag = (int*)(sc + NA_FLAG);
+  a.wait_limit = 1 << 20;
   a.mode = FM_ERR;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(ks->C * J));
@@ -1864,8 +1899,7 @@ int ptycho_set_data_raw(ptycho_ctx* ctx, const void* raw, const ptycho_preproces
   if (ctx->pre_frames < chunk) {  // none yet, or one for a smaller chunk
     if (ctx->pre) {
       CK(cudaStreamSynchronize(ctx->st));
-      cudaFree(ctx->pre);
-      ctx->pre = nullptr;
+      dfree(ctx, ctx->pre);
     }
     if (int r = dalloc(ctx, &ctx->pre, (size_t)chunk * MM)) return r;
     ctx->pre_frames = chunk;
@@ -1938,6 +1972,13 @@ int ptycho_set_likelihood(ptycho_ctx* ctx, int likelihood) {
   return PTYCHO_OK;
 }
 
+int ptycho_set_wait_limit(ptycho_ctx* ctx, long long polls) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (polls < 0) return fail(ctx, PTYCHO_ERR_ARG, "wait limit %lld < 0", polls);
+  ctx->wait_limit = (int)std::min<long long>(polls, 1LL << 30);
+  return PTYCHO_OK;
+}
+
 int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter) {
   if (!ctx) return PTYCHO_ERR_ARG;
   if (n_iter < 0) return fail(ctx, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
@@ -2001,7 +2042,7 @@ int ptycho_simulate(ptycho_ctx* ctx, float* out, int on_device) {
     cudaError_t e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) r = fail(ctx, PTYCHO_ERR_CUDA, "simulate: %s", cudaGetErrorString(e));
   }
-  if (!on_device) cudaFree(dst);
+  if (!on_device) dfree(ctx, dst);
   return r;
 }
 
@@ -2019,7 +2060,7 @@ int ptycho_fourier_residual(ptycho_ctx* ctx, float* out, int on_device) {
     cudaError_t e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) r = fail(ctx, PTYCHO_ERR_CUDA, "residual: %s", cudaGetErrorString(e));
   }
-  if (!on_device) cudaFree(dst);
+  if (!on_device) dfree(ctx, dst);
   return r;
 }
 
@@ -2110,6 +2151,7 @@ int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* psi, int on_device) {
   return PTYCHO_OK;
 }
 long long ptycho_launch_count(const ptycho_ctx* ctx) { return ctx ? ctx->launches : -1; }
+long long ptycho_memory_used(const ptycho_ctx* ctx) { return ctx ? (long long)ctx->mem_used : -1; }
 int ptycho_cluster_size(const ptycho_ctx* ctx) { return ctx ? ctx->C : 0; }
 int ptycho_epie_cluster_size(const ptycho_ctx* ctx) {
   if (!ctx) return 0;

@@ -81,3 +81,58 @@ def test_to_pixels_listing1():
     assert dx == pytest.approx(2.8158e-9, rel=1e-4)
     assert step_px == pytest.approx(17.757, rel=1e-4)
     assert beam_px == pytest.approx(39.065, rel=1e-4)
+
+
+def _noalloc_args(shift_amp=0, shift_obj=0):
+    """Host buffers for the allocation-free call (a CPU test never reaches a
+    kernel: these calls must fail in the argument checks)."""
+    M, K, J, ny, nx = 32, 1, 2, 64, 64
+    obj = np.zeros(ny * nx * 2 + 8, np.float32)
+    prb = np.zeros(K * M * M * 2 + 8, np.float32)
+    amp = np.zeros(J * M * M + 8, np.float32)
+    pos = np.zeros((J, 2), np.float32)
+    out = ctypes.c_double()
+    o = obj.ctypes.data + (-obj.ctypes.data % 16) + shift_obj
+    p = prb.ctypes.data + (-prb.ctypes.data % 16)
+    a = amp.ctypes.data + (-amp.ctypes.data % 16) + shift_amp
+    keep = (obj, prb, amp, pos)
+    return keep, (o, ny, nx, p, M, K, pos.ctypes.data, J, a, ctypes.byref(out), None)
+
+
+@pytest.mark.parametrize("shift_amp,shift_obj,what", [(4, 0, b"16-byte"), (8, 0, b"16-byte"), (0, 4, b"8-byte")])
+def test_noalloc_rejects_misaligned_pointers(lib, shift_amp, shift_obj, what):
+    """Misaligned amplitude (16-byte bulk reads) or object (8-byte complex
+    loads) pointers are argument errors, caught before any device work."""
+    keep, args = _noalloc_args(shift_amp, shift_obj)
+    assert lib.ptycho_fourier_error_noalloc(*args) == -1
+    assert what in lib.ptycho_last_error(None)
+
+
+def test_error_message_is_per_thread(lib):
+    """The context-free error message is kept per thread: a failure on one
+    thread does not overwrite another thread's message."""
+    import threading
+
+    keep, args = _noalloc_args(4, 0)
+    assert lib.ptycho_fourier_error_noalloc(*args) == -1
+    seen = {}
+
+    def other():
+        k2, a2 = _noalloc_args(0, 4)
+        seen["rc"] = lib.ptycho_fourier_error_noalloc(*a2)
+        seen["msg"] = lib.ptycho_last_error(None)
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["rc"] == -1 and b"8-byte" in seen["msg"]
+    assert b"16-byte" in lib.ptycho_last_error(None)
+
+
+def test_new_controls_reject_null(lib):
+    assert lib.ptycho_set_wait_limit(None, 5) == -1
+    assert lib.ptycho_fp32_fma_peak(None, None, None, None) == -1
+    p = api.default_params(M=32, K=1, J=4, obj_ny=64, obj_nx=64)
+    assert p.mem_limit == 0
+    p2 = api.default_params(M=32, K=1, J=4, obj_ny=64, obj_nx=64, mem_limit=1 << 20)
+    assert p2.mem_limit == 1 << 20 and p2.block_positions == 0

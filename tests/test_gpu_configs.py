@@ -25,12 +25,24 @@ def _illuminated(P, pos, shape):
     return den >= 0.1 * den.max()
 
 
-def _gpu(d, I, P0, alg, n, seed=0):
+def _gpu(d, I, P0, alg, n, seed=0, first=None):
+    """Run n iterations; `first` (a dict) receives the GPU's E at the start."""
     with api.Reconstruction(d["M"], d["K"], len(d["positions"]), d["object"].shape, seed=seed) as r:
         r.set_data(I.astype(np.float32), d["positions"])
         r.set_init(d["object0"], P0)
+        if first is not None:
+            first["E"] = r.fourier_error()
         r.iterate(alg, n)
         return r.get_object(), r.get_probe(), r.fourier_error()
+
+
+def _error_pass_checks(first, E0_ref, Og, Pg, Eg, corner, I, delta=None):
+    """The fixed 1e-5 on E, where FP32 rounding of the iterations does not
+    enter: the first pass at the common start, and the GPU's E at its own
+    result against the oracle's E at that same (O, P)."""
+    assert abs(first["E"] - E0_ref) <= 1e-5 * E0_ref, (first["E"], E0_ref)
+    E_own = orc.fourier_error(Og.astype(np.complex128), Pg.astype(np.complex128), corner, I, delta=delta)
+    assert abs(Eg - E_own) <= 1e-5 * E_own, (Eg, E_own)
 
 
 def test_dm64_workload():
@@ -38,7 +50,8 @@ def test_dm64_workload():
     pos = orc.round_positions(d["positions"])
     I = orc.far_field_intensity(d["object"], d["probe"], pos)
     n = 20
-    Og, Pg, Eg = _gpu(d, I, d["probe0"], "dm", n)
+    first = {}
+    Og, Pg, Eg = _gpu(d, I, d["probe0"], "dm", n, first=first)
     Oc, Pc, _ = orc.reconstruct("dm", d["object0"], d["probe0"], d["positions"], I, n)
     m = _illuminated(d["probe"], d["positions"], d["object"].shape)
     eo, ep = rel_l2(align_global(Og, Oc, m), Oc, m), rel_l2(Pg, Pc)
@@ -47,6 +60,7 @@ def test_dm64_workload():
     E0 = orc.fourier_error(d["object0"], d["probe0"], pos, I)
     assert abs(Eg - Ec) <= (1e-5 + 4.0 * max(eo, ep) / np.sqrt(Ec)) * Ec
     assert Ec < 0.1 * E0   # the reconstruction converges (E falls by over 10x)
+    _error_pass_checks(first, E0, Og, Pg, Eg, pos, I)
 
 
 @pytest.fixture(scope="module")
@@ -72,7 +86,8 @@ def test_modes128_workload(modes128, alg, n):
     d, I, O0, P0 = modes128
     seed = 7 if alg == "epie" else 0
     d = dict(d, object0=O0)
-    Og, Pg, Eg = _gpu(d, I, P0, alg, n, seed=seed)
+    first = {}
+    Og, Pg, Eg = _gpu(d, I, P0, alg, n, seed=seed, first=first)
     Oc, Pc, _ = orc.reconstruct(alg, O0, P0, d["positions"], I, n, seed=seed)
     m = _illuminated(d["probe"], d["positions"], d["object"].shape)
     eo = rel_l2(align_global(Og, Oc, m), Oc, m)
@@ -82,6 +97,8 @@ def test_modes128_workload(modes128, alg, n):
     # each side's E at its own (O, P): 1e-5 plus the first-order propagation
     # of their difference, 2 rel(A) / sqrt(E), rel(A) <= eo + ep
     assert abs(Eg - Ec) <= (1e-5 + 4.0 * max(eo, ep) / np.sqrt(Ec)) * Ec
+    pos_i = orc.round_positions(d["positions"])
+    _error_pass_checks(first, orc.fourier_error(O0, P0, pos_i, I), Og, Pg, Eg, pos_i, I)
 
 
 def test_modes128_workload_subpixel_epie(modes128):
@@ -97,6 +114,7 @@ def test_modes128_workload_subpixel_epie(modes128):
     with api.Reconstruction(d["M"], d["K"], len(pos), d["object"].shape, seed=7, subpixel=8) as r:
         r.set_data(I.astype(np.float32), pos)
         r.set_init(O0, P0)
+        first = {"E": r.fourier_error()}
         r.iterate("epie", 1)
         Og, Pg, Eg = r.get_object(), r.get_probe(), r.fourier_error()
     Oc, Pc, _ = orc.reconstruct("epie", O0, P0, pos, I, 1, seed=7, subpixel=8)
@@ -107,6 +125,7 @@ def test_modes128_workload_subpixel_epie(modes128):
     assert eo < 1e-4 and ep < 1e-4, (eo, ep)
     Ec = orc.fourier_error(Oc, Pc, corner, I, delta=delta)
     assert abs(Eg - Ec) <= (1e-5 + 4.0 * max(eo, ep) / np.sqrt(Ec)) * Ec
+    _error_pass_checks(first, orc.fourier_error(O0, P0, corner, I, delta=delta), Og, Pg, Eg, corner, I, delta)
 
 
 def test_listing1_geometry_subpixel():
@@ -150,8 +169,10 @@ def test_listing1_geometry_subpixel():
         with api.Reconstruction(M, 1, len(pos), (side, side), seed=11, subpixel=S) as r:
             r.set_data(I.astype(np.float32), pos)
             r.set_init(O0, P0)
+            first = {"E": r.fourier_error()}
             r.iterate(alg, 1)
-            Og, Pg = r.get_object(), r.get_probe()
+            Og, Pg, Eg = r.get_object(), r.get_probe(), r.fourier_error()
+        _error_pass_checks(first, orc.fourier_error(O0, P0, corner, I, delta=delta), Og, Pg, Eg, corner, I, delta)
         Oc, Pc, _ = orc.reconstruct(alg, O0, P0, pos, I, 1, seed=11, subpixel=S)
         eo, ep = rel_l2(align_global(Og, Oc, m), Oc, m), rel_l2(Pg, Pc)
         if alg == "lsqml":

@@ -66,7 +66,9 @@ def _compare(c, alg, n, cluster=0, probe_start=0, seed=0, **kw):
                                    subpixel=c["S"], **{k: v for k, v in kw.items() if k in ("likelihood", "probe_ortho")})
     m = _illuminated(c)
     out = dict(eo=rel_l2(align_global(Og, Oc, m), Oc, m), ep=rel_l2(Pg, Pc), E=E,
-               E_ref=orc.fourier_error(Oc, Pc, c["corner"], c["I"], delta=c["delta"]))
+               E_ref=orc.fourier_error(Oc, Pc, c["corner"], c["I"], delta=c["delta"]),
+               E_own=orc.fourier_error(Og.astype(np.complex128), Pg.astype(np.complex128), c["corner"], c["I"],
+                                       delta=c["delta"]))
     if psi is not None:
         out["epsi"] = rel_l2(psi, psic)
     return out
@@ -95,6 +97,8 @@ def test_subpixel_algorithm_parity(alg, M, K, C, S, n):
     # with rel(A) <= eo + ep
     tol_E = 1e-5 + 4.0 * max(res["eo"], res["ep"]) / np.sqrt(res["E_ref"])
     assert abs(res["E"] - res["E_ref"]) <= tol_E * res["E_ref"] + 1e-12, res
+    # the error pass itself: the oracle's E at the GPU's own (O, P), fixed 1e-5
+    assert abs(res["E"] - res["E_own"]) <= 1e-5 * res["E_own"], res
     if "epsi" in res:
         assert res["epsi"] < TOL_REC, res
 
