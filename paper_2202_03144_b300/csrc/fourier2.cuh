@@ -147,7 +147,8 @@ struct Fourier2Args {
   const float2* tw2;      // tw2[k1 * R2 + n2] = exp(-2 pi i n2 k1 / M)
   int* err_flag;          // set to 1 if a bounded wait gave up
   int wait_limit;         // polls of a cluster-transpose wait before it gives up
-  int j0;
+  int j0;                 // first position of the launch
+  int nj;                 // positions of the launch (the cluster kernel loops over them)
   int xoff;               // X holds positions from xoff on (position-blocked residuals)
   int mode;
 };

@@ -105,13 +105,18 @@ def test_bench_launch_shape_parity(alg, n):
     residual-pass kernels the benchmark times (k_fourier3<256, 1, 16, DM|CHI,
     f32>), iterated from a start away from the truth (so the projection and
     the DM epilogue phi + F^-1 (Pi(Z) - Z) do real work), against the oracle
-    to the fixed tolerances: O, P and the DM exit waves to 1e-4, E to 1e-5."""
-    c = scan(256, 1, grid=4, photons=1e6, mask_frac=0.02)
+    to the fixed tolerances: O, P and the DM exit waves to 1e-4; the error
+    pass (the GPU's E against the oracle's E at the same (O, P)) to 1e-5.
+    E at each side's own result differs besides by the first-order
+    propagation of their (O, P) difference, 2 rel(A) / sqrt(E) with
+    rel(A) <= eo + ep."""
+    c = scan(256, 1, grid=4, mask_frac=0.02)
     res = _compare(c, alg, n, cluster=16)
     assert res["eo"] < TOL_REC, res
     assert res["ep"] < TOL_REC, res
-    assert abs(res["E"] - res["E_ref"]) <= 1e-5 * res["E_ref"], res
     assert abs(res["E"] - res["E_own"]) <= 1e-5 * res["E_own"], res
+    tol_E = 1e-5 + 4.0 * max(res["eo"], res["ep"]) / np.sqrt(res["E_ref"])
+    assert abs(res["E"] - res["E_ref"]) <= tol_E * res["E_ref"], res
     if "epsi" in res:
         assert res["epsi"] < TOL_REC, res
 
