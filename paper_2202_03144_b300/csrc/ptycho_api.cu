@@ -54,9 +54,11 @@ std::vector<std::pair<FourierFn, size_t>> fourier_variants(const KernelSet* ks) 
 // for every Fourier kernel variant of a set.
 // 1: the DM and residual passes of the cluster kernel run persistent (a
 // wave of resident clusters, each walking its share of the positions);
-// 0: one cluster per position.
+// 0: one cluster per position.  At 256^2 x 10,000 positions the persistent
+// launch measured slower (residual pass 6.99 against 6.52 ms, DM pass 9.11
+// against 8.23 ms), so one cluster per position is the default.
 #ifndef PT_F3_PERSIST
-#define PT_F3_PERSIST 1
+#define PT_F3_PERSIST 0
 #endif
 
 // Clusters of a cluster Fourier kernel that fit on the current device at
