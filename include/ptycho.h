@@ -60,6 +60,9 @@ enum { PTYCHO_EPIE = 0, PTYCHO_DM = 1, PTYCHO_LSQML = 2 };
  * all arithmetic stays float32. */
 enum { PTYCHO_I_F32 = 0, PTYCHO_I_F16 = 1, PTYCHO_I_BF16 = 2 };
 
+/* Transform engine of the Fourier passes (ptycho_params.fft_engine). */
+enum { PTYCHO_FFT_REGISTER = 0, PTYCHO_DFT_TENSOR_BF16X3 = 1 };
+
 /* LSQML likelihood (ptycho_params.likelihood). */
 enum { PTYCHO_LIK_AMPLITUDE = 0, PTYCHO_LIK_POISSON = 1 };
 
@@ -152,6 +155,18 @@ typedef struct {
                        PTYCHO_ERR_OOM exactly as a failed cudaMalloc does:
                        the call returns the code, nothing of it is applied
                        and the context stays valid and destroyable.         */
+  int fft_engine;   /* 2-D transforms of the DM, LSQML, Fourier-error and
+                       forward-model passes (the paper's batched transforms of
+                       every diffraction pattern, Sec. 2.3):
+                       PTYCHO_FFT_REGISTER (default): FP32 radix FFT in
+                       registers and shared memory;
+                       PTYCHO_DFT_TENSOR_BF16X3: each 1-D transform is one
+                       product with the DFT matrix on the tensor cores, in
+                       BF16 with a three-term split (hi*hi + lo*hi + hi*lo)
+                       and FP32 accumulation -- about 17 significant bits
+                       per transform stage instead of 24.  Compiled for M = 64,
+                       K = 1 (else PTYCHO_ERR_UNSUPPORTED).  ePIE's sweep
+                       keeps its own kernels.                                */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */

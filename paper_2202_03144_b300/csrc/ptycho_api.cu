@@ -33,6 +33,13 @@
 #include "shift.cuh"
 #include "probe_cg.cuh"
 #include "epie_sub.cuh"
+#include "dft_tc.cuh"
+
+namespace ptycho {
+using TcFourierFn = void (*)(Fourier2Args, const unsigned char*, int);
+TcFourierFn tc64_fourier(int mode, int istore);
+void tc64_build_matrix(unsigned char* out, cudaStream_t st);
+}  // namespace ptycho
 
 using namespace ptycho;
 
@@ -50,8 +57,6 @@ std::vector<std::pair<FourierFn, size_t>> fourier_variants(const KernelSet* ks) 
   return v;
 }
 
-// Dynamic shared memory (and, above 8 CTAs, the non-portable cluster size)
-// for every Fourier kernel variant of a set.
 // 1: the DM and residual passes of the cluster kernel run persistent (a
 // wave of resident clusters, each walking its share of the positions);
 // 0: one cluster per position.  At 256^2 x 10,000 positions the persistent
@@ -99,6 +104,8 @@ int f3_resident_clusters(FourierFn fn, bool query, int C = 0, int NT = 0, size_t
   return n;
 }
 
+// Dynamic shared memory (and, above 8 CTAs, the non-portable cluster size)
+// for every Fourier kernel variant of a set.
 cudaError_t set_fourier_attributes(const KernelSet* ks) {
   cudaError_t e = cudaSuccess;
   for (auto [f, smem] : fourier_variants(ks)) {
@@ -370,6 +377,8 @@ struct ptycho_ctx {
   float2* tw2 = nullptr;
   int* err_flag = nullptr;   // set by a device wait that gave up
   int wait_limit = 1 << 20;  // polls of a cluster-transpose wait (ptycho_set_wait_limit)
+  unsigned char* dftm = nullptr;  // split DFT matrix of the tensor-core engine
+  int n_sm = 0;
   size_t mem_used = 0;       // device bytes allocated by dalloc and not yet freed
   std::unordered_map<void*, size_t> mem_blocks;
   int2* pos = nullptr;
@@ -659,6 +668,15 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
     case FM_CHIP: bytes = nj * MM * (8.0 * K + amp_bytes(ctx)); break;
     case FM_ERR: bytes = nj * MM * amp_bytes(ctx); break;
     case FM_SIM: bytes = nj * MM * 4.0; break;
+  }
+  if (ctx->p.fft_engine == PTYCHO_DFT_TENSOR_BF16X3) {
+    // tensor-core DFT: persistent CTAs, two per SM
+    const TcFourierFn fn = tc64_fourier(mode, a.istore);
+    if (!fn) return fail(ctx, PTYCHO_ERR_UNSUPPORTED, "no tensor-core Fourier kernel for mode %d", mode);
+    const int grid = std::max(1, std::min(nj, 2 * ctx->n_sm));
+    return launch(ctx, name, bytes, [&] {
+      fn<<<grid, TC64_NT, TC64_SMEM, ctx->st>>>(a, ctx->dftm, ctx->C);
+    });
   }
   return launch(ctx, name, bytes, [&] {
     cudaLaunchConfig_t cfg{};
@@ -1720,6 +1738,11 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
+  if (p->fft_engine != PTYCHO_FFT_REGISTER && p->fft_engine != PTYCHO_DFT_TENSOR_BF16X3)
+    return fail(nullptr, PTYCHO_ERR_ARG, "fft_engine=%d", p->fft_engine);
+  if (p->fft_engine == PTYCHO_DFT_TENSOR_BF16X3 && (p->M != 64 || p->K != 1))
+    return fail(nullptr, PTYCHO_ERR_UNSUPPORTED, "the tensor-core DFT is compiled for M=64, K=1 (got M=%d K=%d)",
+                p->M, p->K);
   int C = p->cluster > 0 ? p->cluster : default_cluster(p->M, p->K);
   if (p->cluster < 0) {  // autotuned: the fastest compiled cluster size for (M, K)
     int best = 0;
@@ -1769,6 +1792,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     else r = dalloc(ctx, (__half**)&ctx->amp, (size_t)p->J * MM);
   }
   if (!r) r = dalloc(ctx, &ctx->amp_scale, (size_t)p->J);
+  if (!r && p->fft_engine == PTYCHO_DFT_TENSOR_BF16X3)
+    r = dalloc(ctx, &ctx->dftm, 2 * TC64_AMAT);
   if (r) {
     g_create_error = ctx->err;
     ptycho_destroy(ctx);
@@ -1806,6 +1831,13 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
     ctx->epie_ok = e == cudaSuccess && eks->epie != nullptr && eks->smem_epie <= (size_t)optin;
     if (ctx->epie_ok)
       e = cudaFuncSetAttribute(eks->epie, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eks->smem_epie);
+  }
+  if (e == cudaSuccess && p->fft_engine == PTYCHO_DFT_TENSOR_BF16X3) {
+    for (int mode : {FM_DM, FM_CHI, FM_CHIP, FM_ERR, FM_SIM})
+      for (int ist = 0; ist < 3 && e == cudaSuccess; ++ist)
+        e = cudaFuncSetAttribute(tc64_fourier(mode, ist), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC64_SMEM);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) tc64_build_matrix(ctx->dftm, ctx->st);
   }
   if (e == cudaSuccess) {
     k_twiddle<<<(p->M + 255) / 256, 256, 0, ctx->st>>>(ctx->tw, p->M);
@@ -2253,7 +2285,7 @@ void ptycho_destroy(ptycho_ctx* ctx) {
                   ctx->flag,     ctx->gram,      ctx->modeV,    ctx->pbin,     ctx->Pt,        ctx->dPt,
                   ctx->pbins,    ctx->stmp,      ctx->porder,   ctx->goff,     ctx->bgrp,
                   ctx->pbins_den, ctx->cg_r,     ctx->cg_p,     ctx->cg_q,     ctx->cg_part,
-                  ctx->pos_corr, ctx->objacc, ctx->ep_mx};
+                  ctx->pos_corr, ctx->objacc, ctx->ep_mx, ctx->dftm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (ctx->stage) cudaFree(ctx->stage);

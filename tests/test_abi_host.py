@@ -136,3 +136,17 @@ def test_new_controls_reject_null(lib):
     assert p.mem_limit == 0
     p2 = api.default_params(M=32, K=1, J=4, obj_ny=64, obj_nx=64, mem_limit=1 << 20)
     assert p2.mem_limit == 1 << 20 and p2.block_positions == 0
+
+
+def test_fft_engine_validated_before_device_work(lib):
+    """An unknown engine is an argument error and a shape the tensor-core DFT
+    is not compiled for is unsupported, both before any device call."""
+    with pytest.raises(api.PtychoError) as e:
+        api.create(api.default_params(M=64, K=1, J=4, obj_ny=96, obj_nx=96, fft_engine=7))
+    assert e.value.name == "ARG"
+    with pytest.raises(api.PtychoError) as e:
+        api.create(api.default_params(M=128, K=1, J=4, obj_ny=160, obj_nx=160, fft_engine="tensor_bf16x3"))
+    assert e.value.name == "UNSUPPORTED"
+    with pytest.raises(api.PtychoError) as e:
+        api.create(api.default_params(M=64, K=3, J=4, obj_ny=96, obj_nx=96, fft_engine="tensor_bf16x3"))
+    assert e.value.name == "UNSUPPORTED"
