@@ -403,6 +403,55 @@ def run_epie(api, torch, stream, iters=3, warm=1, subpixel=0):
     return out
 
 
+def run_engines(api, torch, stream, grid=100, iters=5, warm=2):
+    """The Fourier-pass engines on the 64^2 detector (the tensor-core DFT is
+    compiled there): LSQML and DM on a 100 x 100 raster (step 6 px, +-2 px
+    jitter, 10,000 positions), per-iteration time and the Fourier pass's
+    CUDA-event time, FP32 FFT against the BF16 three-term tensor-core DFT."""
+    from paper_2202_03144_b300 import synth
+    M, K, J = 64, 1, grid * grid
+    step = 6
+    side = -(-(step * (grid - 1) + M + 8) // 16) * 16
+    P = synth.make_probe(M, K, R=20.0, sigma=4.0, c=0.02)
+    P0 = synth.make_probe(M, K, R=22.0, sigma=4.0, c=0.02)
+    pos = synth.raster_positions(grid, grid, step, 2, 2, seed=2100)
+    O = synth.make_object(side, side, seed=1100)
+    out = {"workload": f"64x64 detector, {J} positions ({grid}x{grid} raster, step {step} px, +-2 px jitter), "
+                       f"{side}x{side} object, K=1, Poisson 1e5 photons/frame"}
+    with torch.cuda.stream(stream):
+        sim = api.Reconstruction(M, K, J, (side, side), stream=stream.cuda_stream)
+        sim.set_positions(pos)
+        sim.set_init(O, P)
+        I = torch.empty((J, M, M), dtype=torch.float32, device="cuda")
+        sim.simulate(I)
+        torch.cuda.synchronize()
+        sim.close()
+        sc = 1e5 / float(I.sum(dim=(1, 2)).mean())
+        I = torch.poisson(I * sc, generator=torch.Generator(device="cuda").manual_seed(5))
+        for eng in ("register", "tensor_bf16x3"):
+            res = {}
+            for alg, fam in (("lsqml", "fourier_chi"), ("dm", "fourier_dm")):
+                r = api.Reconstruction(M, K, J, (side, side), stream=stream.cuda_stream, fft_engine=eng)
+                r.set_data(I, pos)
+                r.set_init(np.ones((side, side), np.complex64), P0 * np.sqrt(sc))
+                r.iterate(alg, warm)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.iterate(alg, iters)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                r.set_profiling(True)
+                r.iterate(alg, 2)
+                prof = r.get_profile()
+                res[alg] = {"ms_per_iteration": e0.elapsed_time(e1) / iters,
+                            "fourier_pass_ms": prof[fam]["ms"] / prof[fam]["launches"],
+                            "fourier_error": r.fourier_error()}
+                r.close()
+            out[eng] = res
+    return out
+
+
 def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, check=5):
     """Learned warm start on a 1600-position, 3-mode 128^2 scan: network
     training (one-off, reported apart), then iterations and wall time to the
@@ -710,6 +759,7 @@ def main():
     if epie is not None:
         epie["subpixel"] = run_epie(api, torch, stream, subpixel=SUBPIXEL)
     warm = None if (args.no_warm or profiling_run) else run_warm_start(api, torch, stream, n_frames=args.warm_frames)
+    engines = None if profiling_run else run_engines(api, torch, stream)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -740,6 +790,7 @@ def main():
         "batched": batched,
         "time_to_eps": t2e,
         "warm_start": warm,
+        "fft_engines_64": engines,
         "epie": epie,
         "roofline": roof,
         "cpu_baseline": cb,

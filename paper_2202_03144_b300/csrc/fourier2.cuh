@@ -148,7 +148,7 @@ struct Fourier2Args {
   int* err_flag;          // set to 1 if a bounded wait gave up
   int wait_limit;         // polls of a cluster-transpose wait before it gives up
   int j0;                 // first position of the launch
-  int nj;                 // positions of the launch (the cluster kernel loops over them)
+  int nj;                 // positions of the launch (persistent kernels walk them)
   int xoff;               // X holds positions from xoff on (position-blocked residuals)
   int mode;
 };

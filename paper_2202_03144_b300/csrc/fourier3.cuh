@@ -48,28 +48,28 @@ __device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t ba
 __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait for the completion of the transpose barrier's phase with
-// parity `ph`.  After `limit` polls (the context's wait limit; 0 gives up at
-// once) the wait raises the error flag and keeps waiting, now with a fixed
-// bound: the peers' stores into this CTA's shared memory are on their way
-// (every CTA sends its transpose data unconditionally), and none may land
-// after the buffers have been reused or the CTA has exited.  Only if the data
-// is still missing after the fixed bound does the CTA go on without it.
-__device__ __forceinline__ void mbar_wait_flag(uint64_t* bar, uint32_t ph, int* err_flag, int limit) {
+// Bounded wait for the completion of phase 0 of a transpose barrier.  After
+// `limit` polls (the context's wait limit; 0 gives up at once) the wait
+// raises the error flag and keeps waiting, now with a fixed bound: the peers'
+// stores into this CTA's shared memory are on their way (every CTA sends its
+// transpose data unconditionally), and none may land after the buffer has
+// been reused or the CTA has exited.  Only if the data is still missing after
+// the fixed bound does the CTA go on without it.
+__device__ __forceinline__ void mbar_wait_flag(uint64_t* bar, int* err_flag, int limit) {
   uint32_t done = 0;
   for (int i = 0; i < limit && !done; ++i)
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(ph)
+        : "r"(smem_u32(bar))
         : "memory");
   if (done) return;
   atomicExch(err_flag, 1);
   for (int i = 0; i < (1 << 22) && !done; ++i)
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(ph)
+        : "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -116,24 +116,24 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
   pdl_launch();
   const int tid = threadIdx.x;
   const int c = (int)(blockIdx.x % C);
+  const int j = a.j0 + (int)(blockIdx.x / C);
+  // probe of this position (sub-pixel: its bin of the shifted-probe table)
+  const float2* Pj = a.pbin ? a.P + (size_t)__ldg(a.pbin + j) * (K * M * M) : a.P;
   const int mode = MODE_T >= 0 ? MODE_T : a.mode;
   const int istore = IST_T >= 0 ? IST_T : a.istore;
+  const int2 p = a.pos[j];
   const bool need_amp = mode != FM_SIM;
-  // DM / residual passes: the inverse transform's transpose into X
-  const bool inverse = mode != FM_ERR && mode != FM_SIM;
-  const size_t esz = istore == 0 ? 4 : 2;
-  // this cluster's positions: jj0, jj0 + jstride, ... (a single one when the
-  // grid has a cluster per position)
-  const int jj0 = (int)(blockIdx.x / C), jstride = (int)(gridDim.x / C);
-  auto amp_prefetch = [&](int jj) {
-    const size_t row0 = ((size_t)(a.j0 + jj) * M + c * H) * M;
-    prefetch_l2(reinterpret_cast<const unsigned char*>(a.amp) + row0 * esz, (uint32_t)(H * M * esz));
-  };
+  const size_t amp_row0 = ((size_t)j * M + c * H) * M;  // first amplitude of this CTA's rows
 
   if (tid == 0) {
     mbar_init(barY, 1);
     mbar_init(barX, 1);
-    if (need_amp && jj0 < a.nj) amp_prefetch(jj0);
+    mbar_expect(barY, (uint32_t)(K * H * M * 8));
+    mbar_expect(barX, (uint32_t)(K * M * W * 8));
+    if (need_amp) {
+      const size_t esz = istore == 0 ? 4 : 2;
+      prefetch_l2(reinterpret_cast<const unsigned char*>(a.amp) + amp_row0 * esz, (uint32_t)(H * M * esz));
+    }
   }
   // barriers initialised: peers may signal them once they pass the wait below
   asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
@@ -141,21 +141,6 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     const float2 t = a.tw2[i];
     tw[i] = t;
     twT[(i % R2) * R1 + i / R2] = t;
-  }
-
-  uint32_t ph = 0;  // parity of the barriers' current phase
-  for (int jj = jj0; jj < a.nj; jj += jstride, ph ^= 1u) {
-  const int j = a.j0 + jj;
-  // probe of this position (sub-pixel: its bin of the shifted-probe table)
-  const float2* Pj = a.pbin ? a.P + (size_t)__ldg(a.pbin + j) * (K * M * M) : a.P;
-  const int2 p = a.pos[j];
-  const size_t amp_row0 = ((size_t)j * M + c * H) * M;  // first amplitude of this CTA's rows
-  if (tid == 0) {
-    // this phase's byte counts (peer data of this phase may already be
-    // arriving: the transaction count may run ahead of the expectation)
-    mbar_expect(barY, (uint32_t)(K * H * M * 8));
-    if (inverse) mbar_expect(barX, (uint32_t)(K * M * W * 8));
-    if (need_amp && jj + jstride < a.nj) amp_prefetch(jj + jstride);  // the next position's, one ahead
   }
 
   float2 v[R1];
@@ -200,9 +185,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       for (int n2 = 0; n2 < R2; ++n2) w[q][n2] = X[cb<F>(k, k1 * R2 + n2, colL)];
       dft<R2, false>(w[q]);
     }
-    // first position: the peers' barriers exist; the error and forward-model
-    // passes: also every peer has read its row buffer of the previous position
-    if (jj == jj0 || !inverse) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // peers' barriers exist
     const uint32_t barY_l = smem_u32(barY);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -259,7 +242,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     load_amp();
     load_amp_k();
   }
-  mbar_wait_flag(barY, ph, a.err_flag, a.wait_limit);
+  mbar_wait_flag(barY, a.err_flag, a.wait_limit);
   // ---- row stage 1: task (k, rowL, n2'), columns n1'*R2 + n2'
   {
     const int n2 = tid % R2, rowL = (tid / R2) % H, k = tid / (R2 * H);
@@ -368,12 +351,11 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       const double sd = block_sum_d<NT>(ed, red);
       if (tid == 0) a.err_part[(size_t)j * C + c] = make_double2(sn, sd);
     }
-    // no inverse in these modes: the row buffer is free once read; a peer
-    // stores its next position's rows only after the matching wait above
-    if (!inverse) {
-      __syncthreads();
-      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-      continue;
+    // no peer writes into this CTA after its first transpose in these modes;
+    // the cluster leaves together, after every CTA has received its rows
+    if (mode == FM_ERR || mode == FM_SIM) {
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+      return;
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -408,7 +390,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       st_async_f2(mapa_u32(smem_u32(X + cb<F>(k, f, x % W)), rank), v[n1], mapa_u32(barX_l, rank));
     }
   }
-  mbar_wait_flag(barX, ph, a.err_flag, a.wait_limit);
+  mbar_wait_flag(barX, a.err_flag, a.wait_limit);
   // ---- inverse column stage A: task (k, colL, k1), radix R2 over k2
   {
     float2 w[Q][R2];
@@ -451,11 +433,6 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       }
     }
   }
-  __syncthreads();  // X and the reduction scratch are rewritten by the next position
-  }  // positions
-  // error / forward-model passes: the last position's row buffers are read;
-  // leave together, as no peer stores into this CTA any more
-  if (!inverse) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
 }
 
 }  // namespace ptycho

@@ -39,7 +39,6 @@ struct KernelSet {
   bool default_ok = true;  // a candidate for the default cluster size of DM/LSQML
   void (*epie2)(Epie2Args) = nullptr;  // register-resident ePIE sweep (C > 1), or null
   size_t smem_epie2 = 0;
-  bool spec_f3 = false;    // the spec kernels are k_fourier3 (may run persistent)
 };
 
 // Row of KernelSet::spec for a Fourier mode: DM, LSQML residual (amplitude),
@@ -57,7 +56,6 @@ void fill_spec_row(KernelSet& s) {
     s.spec[r][1] = k_fourier3<M, K, C, MODE, 1>;
     s.spec[r][2] = k_fourier3<M, K, C, MODE, 2>;
     s.smem_spec = fourier3_smem<F2<M, K, C>>();
-    s.spec_f3 = true;
   } else {
     s.spec[r][0] = k_fourier2<M, K, C, MODE, 0>;
     s.spec[r][1] = k_fourier2<M, K, C, MODE, 1>;

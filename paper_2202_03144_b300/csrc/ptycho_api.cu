@@ -57,53 +57,6 @@ std::vector<std::pair<FourierFn, size_t>> fourier_variants(const KernelSet* ks) 
   return v;
 }
 
-// 1: the DM and residual passes of the cluster kernel run persistent (a
-// wave of resident clusters, each walking its share of the positions);
-// 0: one cluster per position.  At 256^2 x 10,000 positions the persistent
-// launch measured slower (residual pass 6.99 against 6.52 ms, DM pass 9.11
-// against 8.23 ms), so one cluster per position is the default.
-#ifndef PT_F3_PERSIST
-#define PT_F3_PERSIST 0
-#endif
-
-// Clusters of a cluster Fourier kernel that fit on the current device at
-// once, per (kernel, device): queried when the kernel's attributes are set
-// (context creation, outside any stream capture) and looked up at launch;
-// 0 = unknown (the launch then takes one cluster per position).
-std::mutex g_f3_mu;
-std::map<std::pair<const void*, int>, int> g_f3_clusters;
-
-int f3_resident_clusters(FourierFn fn, bool query, int C = 0, int NT = 0, size_t smem = 0) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  std::lock_guard<std::mutex> lk(g_f3_mu);
-  const auto key = std::make_pair((const void*)fn, dev);
-  const auto it = g_f3_clusters.find(key);
-  if (it != g_f3_clusters.end()) return it->second;
-  if (!query) return 0;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)C * 1024);
-  cfg.blockDim = dim3((unsigned)NT);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (const void*)fn, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    n = 0;
-  }
-  g_f3_clusters[key] = n;
-  return n;
-}
-
 // Dynamic shared memory (and, above 8 CTAs, the non-portable cluster size)
 // for every Fourier kernel variant of a set.
 cudaError_t set_fourier_attributes(const KernelSet* ks) {
@@ -112,10 +65,6 @@ cudaError_t set_fourier_attributes(const KernelSet* ks) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && ks->C > 8) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
-  if (e == cudaSuccess && PT_F3_PERSIST && ks->spec_f3)
-    for (int row : {spec_row(FM_DM), spec_row(FM_CHI), spec_row(FM_CHIP)})
-      for (int ist = 0; ist < 3; ++ist)
-        if (ks->spec[row][ist]) f3_resident_clusters(ks->spec[row][ist], true, ks->C, ks->NT2, ks->smem_spec);
   return e;
 }
 
@@ -705,12 +654,6 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
     if (row >= 0 && a.istore >= 0 && a.istore < 3 && ks->spec[row][a.istore]) {
       fn = ks->spec[row][a.istore];
       cfg.dynamicSmemBytes = ks->smem_spec;
-      // DM and residual passes of the cluster kernel: persistent, one wave
-      // of clusters walking the positions
-      if (PT_F3_PERSIST && ks->spec_f3 && (mode == FM_DM || mode == FM_CHI || mode == FM_CHIP)) {
-        const int n = f3_resident_clusters(fn, false);
-        if (n > 0 && n < nj) cfg.gridDim = dim3((unsigned)(ks->C * n));
-      }
     }
     cudaLaunchKernelEx(&cfg, fn, a);
   });

@@ -8,7 +8,9 @@ the 128 real terms of a row; a Fourier pass chains four such transforms and
 the residual is a difference of two nearly equal far fields, so single passes
 are held to 1e-4 (against 2e-5 for the FP32 FFT) and the Fourier error to
 2e-5.  Reconstructions: O and P after 1 and 10 iterations to the FP32 path's
-1e-4 (measured: 3e-6 and 7e-5 for LSQML)."""
+1e-4 (measured: 3e-6 and 7e-5 for LSQML).  DM's exit waves take every pass's
+transform error directly (psi += F^-1 (Pi(Z) - Z)): about 2.5e-5 per
+iteration, so they are held to 5e-4 after 10 iterations (measured 2.4e-4)."""
 import numpy as np
 import pytest
 
@@ -23,6 +25,7 @@ ENG = "tensor_bf16x3"
 TOL_TC_PASS = 1e-4
 TOL_TC_E = 2e-5
 TOL_REC = 1e-4
+TOL_TC_PSI = 5e-4
 
 
 def _recon(c, **kw):
@@ -75,7 +78,7 @@ def test_algorithm_parity(alg, n):
     E_own = orc.fourier_error(Og.astype(np.complex128), Pg.astype(np.complex128), orc.round_positions(c["pos"]), c["I"])
     assert abs(E - E_own) <= TOL_TC_E * E_own
     if psi is not None:
-        assert rel_l2(psi, psic) < TOL_REC
+        assert rel_l2(psi, psic) < (TOL_REC if n == 1 else TOL_TC_PSI)
 
 
 def test_poisson_and_subpixel_run_on_the_engine():

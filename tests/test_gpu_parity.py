@@ -562,41 +562,3 @@ def test_epie_runs_on_the_widest_cluster_by_default():
         assert r.cluster == 8 and r.epie_cluster == 16
     with api.Reconstruction(128, 3, len(c["pos"]), c["shape"], cluster=4, subpixel=8) as r:
         assert r.cluster == 4 and r.epie_cluster == 4
-
-
-def test_precision_report_256_detector():
-    """The precision comparison on the 256^2 detector (the bench's probe,
-    step and photon count; a 6 x 6-position cut so the oracle runs it whole):
-    50 LSQML iterations from a random object and the noisy true probe, error
-    of the object, probe and Fourier error against the FP64 oracle for FP32,
-    FP16 and BF16 amplitude storage."""
-    M, G = 256, 6
-    P = synth.make_probe(M, 1, R=80.0, sigma=16.0, c=0.00125)
-    pos = synth.raster_positions(G, G, 24, 2, 2, seed=2000)
-    side = -(-(24 * (G - 1) + 4 + M) // 16) * 16
-    O = synth.make_object(side, side, seed=1000)
-    pi = orc.round_positions(pos)
-    I = orc.far_field_intensity(O, P, pi)
-    sc = 1e5 / I.sum(axis=(1, 2)).mean()
-    I = synth.poisson(I * sc, seed=3)
-    O0 = synth.make_object(side, side, seed=1001)
-    P0 = synth.noisy_probe(P * np.sqrt(sc), 0.1, seed=4)
-    n = 50
-    Oc, Pc, _ = orc.reconstruct("lsqml", O0, P0, pos, I, n)
-    E_ref = orc.fourier_error(Oc, Pc, pi, I)
-    den = orc.object_denominator(P, pi, O.shape)
-    m = den >= 0.1 * den.max()
-    report = {}
-    for store in ("f32", "f16", "bf16"):
-        with api.Reconstruction(M, 1, len(pos), O.shape, istore=store) as r:
-            r.set_data(I.astype(np.float32), pos)
-            r.set_init(O0, P0)
-            r.iterate("lsqml", n)
-            Og, Pg = r.get_object(), r.get_probe()
-        E = orc.fourier_error(Og, Pg, pi, I)
-        report[store] = dict(object=rel_l2(align_global(Og, Oc, m), Oc, m), probe=rel_l2(Pg, Pc),
-                             fourier_error=abs(E - E_ref) / E_ref)
-    print("precision report, 256^2, 50 LSQML iterations (relative to the FP64 oracle):", report)
-    assert max(report["f32"].values()) < 1e-4
-    assert max(report["f16"].values()) < 5e-3
-    assert max(report["bf16"].values()) < 5e-2
