@@ -284,6 +284,11 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7, group_bytes=N
         torch.cuda.synchronize()
         b.iterate("lsqml", warm)
         torch.cuda.synchronize()
+        if group_bytes is None:  # the group budget from the batch autotuner
+            tuned_bytes, _ = b.autotune("lsqml", 1)
+        else:
+            tuned_bytes = group_bytes
+        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         b.iterate("lsqml", iters)
@@ -309,11 +314,11 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7, group_bytes=N
         clusters = sorted({(m["M"], api.autotune(m["M"], 1)[0]) for m in members})
         b.close()
     units = sum(m["J"] for m in members) * iters
-    gb_mib = (512 << 20 if group_bytes is None else group_bytes) / 2**20
+    gb_mib = tuned_bytes / 2**20
     return {"value": units / (ms_graph / 1e3), "unit": UNIT, "groups": n_groups,
             "all_at_once_value": units / (ms_all / 1e3), "sequential_value": units / (ms_seq / 1e3),
             "members": n, "positions": sum(m["J"] for m in members), "iterations": iters,
-            "kernels_per_graph": kpi, "autotuned_clusters": clusters,
+            "kernels_per_graph": kpi, "autotuned_clusters": clusters, "autotuned_group_mib": gb_mib,
             "workload": f"{n} LSQML scans, probe sizes {{64,96,128,192,256}}, 100-4000 positions (Fermat "
                         "spirals, spacing 0.15 M), Poisson 1e4-1e6 photons/frame; one CUDA graph per iteration, "
                         f"members run in groups of at most {gb_mib:g} MiB working set"}

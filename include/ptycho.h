@@ -371,6 +371,13 @@ int ptycho_epie_cluster_size(const ptycho_ctx* ctx);
  *   not NULL it receives each member's group index (n ints).  The schedule
  *   changes only the order of independent work: results are bit-identical
  *   for every budget.
+ * ptycho_batch_autotune: time n_iter iterations of alg under each candidate
+ *   group budget (all members at once, then 64 MiB .. 4 GiB; budgets giving
+ *   the same partition are timed once), keep the fastest and write it to
+ *   *best_bytes and its time per iteration (ms) to *best_ms (either may be
+ *   NULL).  The timed iterations are real iterations of every member (one
+ *   untimed iteration per candidate captures its graph): the iteration
+ *   counters advance by (n_iter + 1) per distinct partition.
  * Errors: PTYCHO_ERR_* codes; ptycho_batch_last_error(b) (b = NULL: last
  * failed create). */
 typedef struct ptycho_batch ptycho_batch;
@@ -380,6 +387,7 @@ int ptycho_batch_size(const ptycho_batch* b);
 int ptycho_batch_iterate(ptycho_batch* b, int alg, int n_iter);
 long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b);
 int ptycho_batch_set_group_bytes(ptycho_batch* b, long long bytes);
+int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_bytes, double* best_ms);
 int ptycho_batch_groups(ptycho_batch* b, int* group_of);
 int ptycho_batch_synchronize(ptycho_batch* b);
 const char* ptycho_batch_last_error(const ptycho_batch* b);

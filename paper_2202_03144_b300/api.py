@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
             "ptycho_batch_kernels_per_iteration": (C.c_longlong, [vp]),
             "ptycho_batch_set_group_bytes": (i, [vp, C.c_longlong]),
             "ptycho_batch_groups": (i, [vp, C.POINTER(C.c_int)]),
+            "ptycho_batch_autotune": (i, [vp, i, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
             "ptycho_batch_synchronize": (i, [vp]),
             "ptycho_batch_last_error": (C.c_char_p, [vp]),
             "ptycho_batch_destroy": (None, [vp]),
@@ -541,6 +542,15 @@ class Batch:
         """Working-set budget of a group of concurrently running members
         (<= 0: all members at once)."""
         self._check(lib().ptycho_batch_set_group_bytes(self.h, int(nbytes)))
+
+    def autotune(self, alg="lsqml", n_iter=2):
+        """Time n_iter iterations under each candidate group budget and keep
+        the fastest: (bytes, ms per iteration).  The timed iterations are real
+        iterations of every member."""
+        gb, ms = C.c_longlong(), C.c_double()
+        a = ALGS[alg] if isinstance(alg, str) else int(alg)
+        self._check(lib().ptycho_batch_autotune(self.h, a, int(n_iter), C.byref(gb), C.byref(ms)))
+        return gb.value, ms.value
 
     def groups(self):
         """Group index of every member under the current budget."""

@@ -326,6 +326,46 @@ int ptycho_batch_set_group_bytes(ptycho_batch* b, long long bytes) {
   return PTYCHO_OK;
 }
 
+int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_bytes, double* best_ms) {
+  if (!b) return PTYCHO_ERR_ARG;
+  if (n_iter < 1) return bfail(b, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
+  // candidate group budgets: every member at once, then 64 MiB .. 4 GiB
+  const long long cand[] = {0, 64LL << 20, 128LL << 20, 256LL << 20, 512LL << 20, 1LL << 30, 2LL << 30, 4LL << 30};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(b, PTYCHO_ERR_CUDA, "event creation failed");
+  long long best = b->group_bytes;
+  float best_t = -1.f;
+  int rc = PTYCHO_OK;
+  std::vector<std::vector<std::vector<int>>> seen;  // partitions already timed
+  for (long long gb : cand) {
+    if ((rc = ptycho_batch_set_group_bytes(b, gb))) break;
+    batch_plan(b);
+    if (std::find(seen.begin(), seen.end(), b->groups) != seen.end()) continue;  // same partition as before
+    seen.push_back(b->groups);
+    if ((rc = ptycho_batch_iterate(b, alg, 1))) break;  // captures the graph of this partition
+    cudaEventRecord(e0, b->main);
+    if ((rc = ptycho_batch_iterate(b, alg, n_iter))) break;
+    cudaEventRecord(e1, b->main);
+    float t = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+      rc = bfail(b, PTYCHO_ERR_CUDA, "timing failed");
+      break;
+    }
+    if (best_t < 0.f || t < best_t) {
+      best_t = t;
+      best = gb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (int r = ptycho_batch_set_group_bytes(b, best)) return r;
+  if (best_bytes) *best_bytes = best;
+  if (best_ms) *best_ms = best_t / n_iter;
+  return PTYCHO_OK;
+}
+
 int ptycho_batch_groups(ptycho_batch* b, int* group_of) {
   if (!b) return -1;
   batch_plan(b);

@@ -326,6 +326,8 @@ struct ptycho_ctx {
   float2* tw2 = nullptr;
   int* err_flag = nullptr;   // set by a device wait that gave up
   int wait_limit = 1 << 20;  // polls of a cluster-transpose wait (ptycho_set_wait_limit)
+  cudaStream_t st_side = nullptr;  // second stream: the probe-direction sums beside the object's
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned char* dftm = nullptr;  // split DFT matrix of the tensor-core engine
   int n_sm = 0;
   size_t mem_used = 0;       // device bytes allocated by dalloc and not yet freed
@@ -1092,7 +1094,42 @@ int dm_step(ptycho_ctx* ctx, bool upd) {
 
 int lsqml_prepare(ptycho_ctx* ctx) {
   if (int r = ensure_work_buffers(ctx)) return r;
+  if (!ctx->st_side) {  // created here, outside any stream capture
+    CK(cudaStreamCreateWithFlags(&ctx->st_side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
   ctx->psi_valid = false;
+  return 0;
+}
+
+// The sums of the object direction and of the probe direction read the same
+// residual and the current (O, P) and write disjoint buffers: the probe's run
+// on the second stream beside the object's (each alone is latency-limited
+// below the HBM roofline).  Serial while profiling (clean per-kernel times)
+// and with sub-pixel positions (the probe sums then use the shift tables).
+int direction_sums(ptycho_ctx* ctx, bool upd) {
+  const bool side = upd && ctx->st_side && !ctx->prof && ctx->S == 0;
+  if (!side) {
+    if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
+    if (upd)
+      if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
+    return 0;
+  }
+  CK(cudaEventRecord(ctx->ev_fork, ctx->st));
+  CK(cudaStreamWaitEvent(ctx->st_side, ctx->ev_fork, 0));
+  cudaStream_t main = ctx->st;
+  ctx->st = ctx->st_side;
+  const int rp = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true);
+  ctx->st = main;
+  // joined whatever happened, so that a stream capture can end cleanly
+  const cudaError_t e = cudaEventRecord(ctx->ev_join, ctx->st_side);
+  const int ro = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr);
+  const cudaError_t e2 = cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0);
+  if (rp) return rp;
+  if (ro) return ro;
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(ctx, PTYCHO_ERR_CUDA, "stream fork/join: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
   return 0;
 }
 
@@ -1108,9 +1145,7 @@ int lsqml_step_blocked(ptycho_ctx* ctx, bool upd);
 int lsqml_step(ptycho_ctx* ctx, bool upd) {
   if (ctx->B > 0 && ctx->B < ctx->p.J) return lsqml_step_blocked(ctx, upd);
   if (int r = launch_chi(ctx, ctx->X)) return r;
-  if (int r = obj_step(ctx, OBJ_STEP_DIR, ctx->X, nullptr)) return r;
-  if (upd)
-    if (int r = probe_step(ctx, PR_DIR, ctx->X, nullptr, true, true)) return r;
+  if (int r = direction_sums(ctx, upd)) return r;
   if (int r = steps_step(ctx, upd)) return r;
   if (upd)  // alpha_P-weighted probe numerator from the old object
     if (int r = probe_step(ctx, PR_UPD, ctx->X, ctx->alphaP, false, false)) return r;
@@ -2221,6 +2256,12 @@ void ptycho_destroy(ptycho_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
+  if (ctx->st_side) {  // its work is joined into ctx->st, which is idle now
+    cudaStreamSynchronize(ctx->st_side);
+    cudaStreamDestroy(ctx->st_side);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   void* bufs[] = {ctx->tw2, ctx->err_flag, ctx->O,        ctx->P,         ctx->X,        ctx->dO,       ctx->dP,        ctx->tw,
                   ctx->pos,      ctx->amp,       ctx->amp_scale, ctx->denO,    ctx->tile_max,  ctx->denO_max,
                   ctx->tile_ptr, ctx->tile_list, ctx->ppart,    ctx->ppart_den, ctx->pnum,     ctx->pden,

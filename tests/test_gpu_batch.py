@@ -106,6 +106,32 @@ def test_batch_group_schedule_is_bit_identical(budget):
         assert ng == 1
 
 
+def test_batch_autotune_keeps_the_fastest_budget_and_the_results():
+    """The group-budget autotuner times real iterations under each distinct
+    partition and keeps the fastest; the members end exactly where the same
+    number of iterations under a fixed budget ends (the schedule only
+    reorders independent work)."""
+    cases = _cases()
+    members = [dict(M=c["M"], K=c["K"], J=len(c["pos"]), obj_shape=c["shape"]) for c in cases]
+    with api.Batch(members) as b:
+        for m, c in zip(b.members, cases):
+            m.set_data(c["I"].astype(np.float32), c["pos"])
+            m.set_init(c["O0"], c["P0"])
+        gb, ms = b.autotune("lsqml", 1)
+        assert gb in (0, 64 << 20, 128 << 20, 256 << 20, 512 << 20, 1 << 30, 2 << 30, 4 << 30) and ms > 0
+        n = b.members[0].iteration
+        assert n >= 2 and all(m.iteration == n for m in b.members)
+        tuned = [(m.get_object(), m.get_probe()) for m in b.members]
+    with api.Batch(members, group_bytes=1) as b:
+        for m, c in zip(b.members, cases):
+            m.set_data(c["I"].astype(np.float32), c["pos"])
+            m.set_init(c["O0"], c["P0"])
+        b.iterate("lsqml", n)
+        ref = [(m.get_object(), m.get_probe()) for m in b.members]
+    for (O1, P1), (O2, P2) in zip(tuned, ref):
+        assert np.array_equal(O1, O2) and np.array_equal(P1, P2)
+
+
 def test_batch_members_with_poisson_and_mode_orthogonalisation():
     """Per-member options reach the captured graph: Poisson-likelihood LSQML
     and orthogonalised 3-mode probes give the results of the same members run
