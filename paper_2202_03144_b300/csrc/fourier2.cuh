@@ -27,9 +27,8 @@
 //
 // Six shared-memory round trips per transform pair (two of them across the
 // cluster), against twelve for a pass-per-stage shared-memory FFT.  The row
-// buffer is XOR-swizzled inside 16-element groups so that both the stride-R2
-// reads of row stage 2 and the unit-stride reads of row stage 1 are free of
-// bank conflicts.
+// buffer is laid out (rb()) so that both the stride-R2 reads of row stage 2
+// and the unit-stride reads of row stage 1 are free of bank conflicts.
 //
 // The inverse FFT is unnormalised; 1/M^2 is folded into the projection.  By
 // linearity the epilogue needs no second read of psi:
@@ -73,6 +72,8 @@ __host__ __device__ constexpr size_t fourier2_smem() {
   return (size_t)F::SBUF * 8 + (size_t)F::M * 16 + (size_t)F::H * F::M * 4 + F::NRED * 8 + 16;
 }
 
+// Row-buffer index of column x: XOR swizzle inside groups of 16 (an explicit
+// pad element after every 16 columns measured 6% slower at M = 256).
 template <class F>
 __device__ __forceinline__ int rb(int k, int rowL, int x) {
   const int sx = x ^ ((x >> 4) & (F::R2 - 1));

@@ -613,18 +613,30 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int nchunk, size_t 
   }
 }
 
-// Bias gradient: one CTA per output channel, fixed-order block sum.
-__global__ void __launch_bounds__(CV_NT) k_bias_grad(const float* __restrict__ dout, int B, int co, int hw,
-                                                      float* __restrict__ db) {
+// Bias gradient, stage 1: CTA (channel, slice) sums its slice of the
+// channel's B x hw deltas (FP32 per thread, FP64 block sum) into
+// part[slice][channel]; stage 2 adds the slices in order.
+__global__ void __launch_bounds__(CV_NT) k_bias_grad_part(const float* __restrict__ dout, int B, int co, int hw,
+                                                           int nslice, double* __restrict__ part) {
   __shared__ double red[32];
-  const int c = blockIdx.x;
+  const int c = blockIdx.x, sl = blockIdx.y;
+  const int tot = B * hw;
+  const int i0 = (int)((long long)tot * sl / nslice), i1 = (int)((long long)tot * (sl + 1) / nslice);
   float s = 0.f;
-  for (long long i = threadIdx.x; i < (long long)B * hw; i += CV_NT) {
-    const int n = (int)(i / hw), r = (int)(i % hw);
+  for (int i = i0 + threadIdx.x; i < i1; i += CV_NT) {
+    const int n = i / hw, r = i - n * hw;
     s += dout[((size_t)n * co + c) * hw + r];
   }
   const double t = block_sum_d<CV_NT>((double)s, red);
-  if (threadIdx.x == 0) db[c] = (float)t;
+  if (threadIdx.x == 0) part[(size_t)sl * co + c] = t;
+}
+
+__global__ void k_bias_grad_sum(const double* __restrict__ part, int nslice, int co, float* __restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= co) return;
+  double s = 0.0;
+  for (int sl = 0; sl < nslice; ++sl) s += part[(size_t)sl * co + c];
+  db[c] = (float)s;
 }
 
 // Loss L = sum (out - target)^2 / (B * 2 * 64 * 64) and its gradient.

@@ -22,6 +22,10 @@ struct ptycho_net {
   int* err_flag = nullptr;      // set by a bounded device wait that gave up
   float* tc_part = nullptr;     // split-K partial tiles of the tensor-core forward
   size_t tc_part_n = 0;
+  double* bpart = nullptr;      // bias-gradient slice sums [slice][channel]
+  float* bd_part = nullptr;     // split-K partial tiles of the tensor-core data gradient
+  size_t bd_part_n = 0;
+  size_t wpart_n = 0;           // capacity of wpart (floats)
   void* x = nullptr;            // input [B][1][128][128]
   void* act[NET_LAYERS] = {};   // layers 0..10 (BF16, or FP32 in verification mode)
   float* out = nullptr;         // layer 11 output [B][2][64][64] (FP32)
@@ -31,6 +35,8 @@ struct ptycho_net {
   long long adam_t = 0;
   std::string err;
 };
+
+constexpr int NET_BPART = 4096;  // capacity of the bias-gradient slice sums (doubles)
 
 namespace {
 
@@ -143,6 +149,50 @@ void launch_conv_tc(ptycho_net* n, const ConvArgs& a, const NetLayer& L, bool ou
   }
 }
 
+// Backward on the tensor cores (net_bwd_tc.cuh).  Pixel splits of the
+// weight gradient: about two CTAs per SM, within the partial buffer.
+int bw_tc_splits(const NetLayer& L, int B, size_t wpart_n) {
+  const int tiles = ((L.co + 127) / 128) * ((L.ci * 9 + BW_NT - 1) / BW_NT);
+  const long long nchunk = ((long long)B * L.hout * L.wout + BW_KC - 1) / BW_KC;
+  long long s = (2 * 148 + tiles - 1) / tiles;
+  s = std::min<long long>(s, nchunk);
+  s = std::min<long long>(s, (long long)(wpart_n / ((size_t)L.co * L.ci * 9)));
+  return (int)std::max<long long>(s, 1);
+}
+
+// K splits of the data gradient over co * 9 (deep layers have few pixels)
+int bd_tc_splits(const NetLayer& L, int B) {
+  const long long tiles = ((long long)B * L.hin * L.win + 127) / 128;
+  const int nchunk = (L.co * 9 + BD_KC - 1) / BD_KC;
+  long long ks = (2 * 148 + tiles - 1) / tiles;
+  if (ks > nchunk) ks = nchunk;
+  if (ks < 1) ks = 1;
+  return (int)ks;
+}
+
+size_t bd_part_size(int max_batch) {
+  size_t m = 0;
+  for (int B = 1; B <= max_batch; ++B)
+    for (int l = 1; l < NET_LAYERS; ++l) {
+      const NetLayer L = net_layer(l);
+      const int ks = bd_tc_splits(L, B);
+      if (ks > 1) m = std::max(m, (size_t)ks * L.ci * B * L.hin * L.win);
+    }
+  return m;
+}
+
+template <int NP>
+void launch_bwd_data_tc(ptycho_net* n, const ConvArgs& a, const NetLayer& L) {
+  const long long npix = (long long)a.B * a.hin * a.win;
+  const int ks = bd_tc_splits(L, a.B);
+  const dim3 g((unsigned)((npix + 127) / 128), (unsigned)ks);
+  k_conv_bwd_data_tc<__nv_bfloat16, NP><<<g, 128, bd_tc_smem<NP>(), n->st>>>(a, ks, n->bd_part, n->err_flag);
+  if (ks > 1) {
+    const unsigned rb = (unsigned)std::min<long long>((npix * a.ci + 255) / 256, 4 * 1184);
+    k_bwd_data_reduce<__nv_bfloat16><<<rb, 256, 0, n->st>>>(a, ks, n->bd_part);
+  }
+}
+
 // Inference forward (predict, warm start): the tensor-core convolutions on
 // channel-last activations with tap-major weights (see k_conv_fwd_tc).  The
 // sums run in another order than the training forward, so the two agree to
@@ -223,20 +273,44 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
     a.dout = n->delta[cur];
     a.wpart = n->wpart;
     const long long npo = (long long)B * L.hout * L.wout;
-    const int nchunk = (int)((npo + BW_CHUNK - 1) / BW_CHUNK);
-    const int nciq = (L.ci + BW_CI - 1) / BW_CI;
-    if (n->f32) k_conv_bwd_w<float><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
-    else k_conv_bwd_w<__nv_bfloat16><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
+    int nchunk = (int)((npo + BW_CHUNK - 1) / BW_CHUNK);
+    if (n->tc) {  // tensor cores: pixel splits of (co tile x k tile) GEMMs
+      nchunk = bw_tc_splits(L, B, n->wpart_n);
+      const int tiles = ((L.co + 127) / 128) * ((L.ci * 9 + BW_NT - 1) / BW_NT);
+      k_conv_bwd_w_tc<__nv_bfloat16><<<dim3((unsigned)tiles, (unsigned)nchunk), 128, bw_tc_smem_launch(), n->st>>>(
+          a, nchunk, n->err_flag);
+    } else {
+      const int nciq = (L.ci + BW_CI - 1) / BW_CI;
+      if (n->f32) k_conv_bwd_w<float><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
+      else k_conv_bwd_w<__nv_bfloat16><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
+    }
     const size_t nw = (size_t)L.co * L.ci * 9;
     k_sum_chunks<<<(unsigned)std::min<size_t>((nw + 255) / 256, 1184), 256, 0, n->st>>>(n->wpart, nchunk, nw,
                                                                                           n->grads + n->w_off[l]);
-    k_bias_grad<<<L.co, CV_NT, 0, n->st>>>(n->delta[cur], B, L.co, L.hout * L.wout, n->grads + n->b_off[l]);
+    {  // bias gradient: about four CTAs per SM, slices of >= 4096 deltas
+      const int tot = B * L.hout * L.wout;
+      const int nsl = std::max(1, std::min({(4 * 148 + L.co - 1) / L.co, (tot + 4095) / 4096, NET_BPART / L.co}));
+      k_bias_grad_part<<<dim3((unsigned)L.co, (unsigned)nsl), CV_NT, 0, n->st>>>(n->delta[cur], B, L.co,
+                                                                               L.hout * L.wout, nsl, n->bpart);
+      k_bias_grad_sum<<<(L.co + 255) / 256, 256, 0, n->st>>>(n->bpart, nsl, L.co, n->grads + n->b_off[l]);
+    }
     if (l > 0) {
       a.din = n->delta[cur ^ 1];
       a.mask = net_layer(l - 1).relu ? n->act[l - 1] : nullptr;
-      const dim3 g((unsigned)(((long long)B * L.hin * L.win + CV_NT - 1) / CV_NT), (unsigned)((L.ci + CV_CI - 1) / CV_CI));
-      if (n->f32) k_conv_bwd_data<float><<<g, CV_NT, 0, n->st>>>(a);
-      else k_conv_bwd_data<__nv_bfloat16><<<g, CV_NT, 0, n->st>>>(a);
+      if (n->tc) {
+        switch (L.ci <= 16 ? 16 : L.ci) {
+          case 16: launch_bwd_data_tc<16>(n, a, L); break;
+          case 32: launch_bwd_data_tc<32>(n, a, L); break;
+          case 64: launch_bwd_data_tc<64>(n, a, L); break;
+          case 128: launch_bwd_data_tc<128>(n, a, L); break;
+          default: launch_bwd_data_tc<256>(n, a, L); break;
+        }
+      } else {
+        const dim3 g((unsigned)(((long long)B * L.hin * L.win + CV_NT - 1) / CV_NT),
+                     (unsigned)((L.ci + CV_CI - 1) / CV_CI));
+        if (n->f32) k_conv_bwd_data<float><<<g, CV_NT, 0, n->st>>>(a);
+        else k_conv_bwd_data<__nv_bfloat16><<<g, CV_NT, 0, n->st>>>(a);
+      }
       cur ^= 1;
     }
   }
@@ -343,13 +417,17 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
   if (!r) r = nalloc(n, &n->out, act_size(NET_LAYERS - 1, max_batch));
   if (!r) r = nalloc(n, &n->delta[0], maxd);
   if (!r) r = nalloc(n, &n->delta[1], maxd);
+  n->wpart_n = maxpart;
   if (!r) r = nalloc(n, &n->wpart, maxpart);
   if (!r) r = nalloc(n, &n->lpart, 256);
+  if (!r) r = nalloc(n, &n->bpart, NET_BPART);
   if (!r) r = nalloc(n, &n->err_flag, 1);
   if (!r && cudaMemset(n->err_flag, 0, sizeof(int)) != cudaSuccess) r = nfail(n, PTYCHO_ERR_CUDA, "memset");
   if (!r && n->tc) {
     n->tc_part_n = tc_part_size(max_batch);
     if (n->tc_part_n) r = nalloc(n, &n->tc_part, n->tc_part_n);
+    n->bd_part_n = bd_part_size(max_batch);
+    if (!r && n->bd_part_n) r = nalloc(n, &n->bd_part, n->bd_part_n);
     cudaError_t e2 = cudaSuccess;
     auto setsm = [&](const void* f, size_t b) {
       if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
@@ -374,6 +452,12 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     setsm((const void*)k_conv_fwd_tc<true, 128, true>, conv_tc_smem<128>());
     setsm((const void*)k_conv_fwd_tc<false, 256, true>, conv_tc_smem<256>());
     setsm((const void*)k_conv_fwd_tc<true, 256, true>, conv_tc_smem<256>());
+    setsm((const void*)k_conv_bwd_w_tc<__nv_bfloat16>, bw_tc_smem_launch());
+    setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 16>, bd_tc_smem<16>());
+    setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 32>, bd_tc_smem<32>());
+    setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 64>, bd_tc_smem<64>());
+    setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 128>, bd_tc_smem<128>());
+    setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 256>, bd_tc_smem<256>());
     if (!r && e2 != cudaSuccess) r = nfail(n, PTYCHO_ERR_CUDA, "tensor-core kernel setup: %s", cudaGetErrorString(e2));
   }
   if (r) {
@@ -493,7 +577,7 @@ void ptycho_net_destroy(ptycho_net* n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
   else cudaDeviceSynchronize();
-  void* bufs[] = {n->tc_part, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->wt,       n->is_w,     n->wb_index,
+  void* bufs[] = {n->tc_part, n->bd_part, n->bpart, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->wt,       n->is_w,     n->wb_index,
                   n->x,      n->out,   n->wpart, n->lpart, n->delta[0], n->delta[1]};
   for (void* b : bufs)
     if (b) cudaFree(b);

@@ -1,0 +1,382 @@
+// Backward passes of the warm-start network on the tensor cores (BF16
+// operands, FP32 accumulation in tensor memory), the transposes of the
+// forward implicit GEMM (k_conv_fwd_tc):
+//
+//   weight gradient  dW[co][k] = sum_p dY[p][co] X[p][k],   k = ci * 9 + tap,
+//                    p over the output pixels of the batch: M = output
+//                    channels, N = a tile of 144 (16 input channels x 9
+//                    taps), K = pixels in chunks of 64; the pixel range is
+//                    split over CTAs and the FP32 partial tiles are summed in
+//                    order afterwards (k_sum_chunks: deterministic);
+//   data gradient    dX[q][ci] = sum_k G[q][k] Wt[ci][k],     k = co * 9 + tap,
+//                    q over the input pixels: G gathers the output deltas
+//                    that read pixel q through tap (zero-dilated for stride
+//                    2; the two virtual rows / columns of the nearest x2
+//                    upsampling summed), Wt[ci][k] = W[co][ci][tap]; the
+//                    previous layer's ReLU derivative is applied in the
+//                    epilogue (or in the in-order split-K reduction).
+//
+// Both stage their operands through two shared-memory stages in the K-major
+// no-swizzle layout of tc.cuh (core matrices of 8 rows x 16 bytes), with the
+// tensor cores working on one stage while the 128 threads fill the other.
+// The deltas are FP32 in memory and rounded to BF16 as operands.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "net.cuh"
+#include "tc.cuh"
+
+namespace ptycho {
+
+constexpr int BW_NT = 144;   // weight-gradient N tile: 16 input channels x 9 taps
+constexpr int BW_KC = 64;    // pixels per K chunk
+constexpr size_t bw_tc_smem() {
+  // two (A: 128 x 64, B: 144 x 64) BF16 stages, mbarriers, tensor-memory slot
+  return 2 * ((size_t)128 * BW_KC * 2 + (size_t)BW_NT * BW_KC * 2) + 64;
+}
+// The launch asks for more: a CTA holds 256 tensor-memory columns, so at most
+// two may share an SM's 512 (a third would wait in its allocation).
+constexpr size_t bw_tc_smem_launch() { return 80 * 1024; }
+static_assert(bw_tc_smem() <= bw_tc_smem_launch() && 3 * bw_tc_smem_launch() > 228 * 1024, "two CTAs per SM");
+
+// 8 floats -> 8 BF16 in one 16-byte word
+__device__ __forceinline__ uint4 pack8_bf16(const float* v) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Weight gradient.  grid = (co tiles of 128 x k tiles of 144, pixel splits).
+// Writes the FP32 partial dW of its pixel range: part[split][co][ci * 9].
+template <typename TA>
+__global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, int* err_flag) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr size_t ABYTES = (size_t)128 * BW_KC * 2, BBYTES = (size_t)BW_NT * BW_KC * 2;
+  unsigned char* stage[2] = {smem_raw, smem_raw + ABYTES + BBYTES};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (ABYTES + BBYTES));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  constexpr uint32_t LBO = 128, SBO = (BW_KC / 8) * 128;
+  constexpr uint32_t NCOLS = 256;
+  const TA* in = reinterpret_cast<const TA*>(a.in);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int KW = a.ci * 9;
+  const int nkt = (KW + BW_NT - 1) / BW_NT;
+  const int co0 = (blockIdx.x / nkt) * 128, k0 = (blockIdx.x % nkt) * BW_NT;
+  const int hw = a.hout * a.wout;
+  const long long npix = (long long)a.B * hw;
+  const long long nchunk = (npix + BW_KC - 1) / BW_KC;
+  const long long c_begin = nchunk * blockIdx.y / nsplit, c_end = nchunk * (blockIdx.y + 1) / nsplit;
+  // rows past the output channels / past ci * 9 stay zero: written once
+  const int rows_a = min(128, a.co - co0), rows_b = min(BW_NT, KW - k0);
+  for (int i = tid; i < (int)(2 * (ABYTES + BBYTES) / 16); i += 128)
+    reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    tc::mbar_init1(&bar[0]);
+    tc::mbar_init1(&bar[1]);
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, NCOLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BW_NT);
+  uint32_t ph[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  for (long long c = c_begin; c < c_end; ++c) {
+    const int s = (int)((c - c_begin) & 1);
+    if (pending[s]) {
+      if (!tc::mbar_wait(&bar[s], ph[s])) ok = false;
+      ph[s] ^= 1u;
+      pending[s] = false;
+      tc::fence_after();
+    }
+    unsigned char* As = stage[s];
+    unsigned char* Bs = stage[s] + ABYTES;
+    const long long p0 = c * BW_KC;
+    // this thread's 8 pixels of the chunk: p0 + 8 g .. + 7 (g = tid % 8, the
+    // same for every unit the thread stages; hw is a multiple of 8, so the
+    // group lies in one image)
+    const long long pg = p0 + 8 * (tid & 7);
+    const bool pin = pg < npix;
+    const int n = pin ? (int)(pg / hw) : 0;
+    const int yx0 = pin ? (int)(pg - (long long)n * hw) : 0;
+    // A: dY rows (output channels) x 64 pixels: two 16-byte loads per unit
+    for (int u = tid; u < rows_a * (BW_KC / 8); u += 128) {
+      const int r = u >> 3, g = u & 7;
+      const int co = co0 + r;
+      float v[8];
+      if (pin) {
+        const float4* src = reinterpret_cast<const float4*>(a.dout + ((size_t)n * a.co + co) * hw + yx0);
+        const float4 q0 = __ldg(src), q1 = __ldg(src + 1);
+        v[0] = q0.x, v[1] = q0.y, v[2] = q0.z, v[3] = q0.w, v[4] = q1.x, v[5] = q1.y, v[6] = q1.z, v[7] = q1.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
+      }
+      *reinterpret_cast<uint4*>(As + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
+    }
+    // B: im2col rows (ci, tap) x 64 pixels, the forward's gather; this
+    // thread's 8 pixel coordinates once per chunk (wout >= 4: at most one
+    // row change inside the group)
+    const TA* img = in + (size_t)n * a.ci * a.hin * a.win;
+    int py[8], px[8];
+    {
+      int y = yx0 / a.wout, x = yx0 - y * a.wout;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        py[e] = y;
+        px[e] = x;
+        if (++x == a.wout) {
+          x = 0;
+          ++y;
+        }
+      }
+    }
+    for (int u = tid; u < rows_b * (BW_KC / 8); u += 128) {
+      const int r = u >> 3, g = u & 7;
+      const int k = k0 + r;
+      const int ci = k / 9, t = k - 9 * (k / 9), ty = t / 3, tx = t - 3 * (t / 3);
+      const TA* plane = img + (size_t)ci * a.hin * a.win;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float x = 0.f;
+        if (pin) {
+          const int sy = net_src(py[e], ty, a.stride, a.up, a.hin), sx = net_src(px[e], tx, a.stride, a.up, a.win);
+          if (sy >= 0 && sx >= 0) x = ldact(plane, (size_t)sy * a.win + sx);
+        }
+        v[e] = x;
+      }
+      *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < BW_KC / 16; ++kk) {
+        const uint64_t ad = tc::smem_desc(As + kk * 2 * LBO, LBO, SBO);
+        const uint64_t bd = tc::smem_desc(Bs + kk * 2 * LBO, LBO, SBO);
+        tc::mma_bf16(tbase, ad, bd, idesc, (c > c_begin || kk > 0) ? 1u : 0u);
+      }
+      tc::commit(&bar[s]);
+    }
+    pending[s] = true;
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    if (pending[s] && !tc::mbar_wait(&bar[s], ph[s])) ok = false;
+  tc::fence_after();
+  if (!ok && tid == 0) atomicExch(err_flag, 1);
+  // epilogue: lane = output channel co0 + 32 warp + lane, columns = k tile
+  const int co = co0 + warp * 32 + (tid & 31);
+  const bool any = c_end > c_begin;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BW_NT; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (co < a.co) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int k = k0 + c0 + j;
+        if (k < KW) a.wpart[((size_t)blockIdx.y * a.co + co) * KW + k] = any ? v[j] : 0.f;
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tbase, NCOLS);
+}
+
+// Data gradient.  grid = (input-pixel tiles of 128, K splits).  NP = input
+// channels rounded up to 16.  ksplit == 1: dX (masked) straight to a.din;
+// else FP32 partials part[split][ci][pixel], reduced by k_bwd_data_reduce.
+constexpr int BD_KC = 64;
+template <int NP>
+__host__ __device__ constexpr size_t bd_tc_smem() {
+  // two (A, B) stages, mbarriers and slot, the per-thread delta offsets
+  // [9 taps][4 (row, column) choices][128]
+  return 2 * ((size_t)128 * BD_KC * 2 + (size_t)NP * BD_KC * 2) + 64 + 36 * 128 * 4;
+}
+
+template <typename TA, int NP>
+__global__ void __launch_bounds__(128) k_conv_bwd_data_tc(ConvArgs a, int ksplit, float* part, int* err_flag) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr size_t ABYTES = (size_t)128 * BD_KC * 2, BBYTES = (size_t)NP * BD_KC * 2;
+  unsigned char* stage[2] = {smem_raw, smem_raw + ABYTES + BBYTES};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (ABYTES + BBYTES));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  int* offs = reinterpret_cast<int*>(smem_raw + 2 * (ABYTES + BBYTES) + 64);  // [36][128]
+  constexpr uint32_t LBO = 128, SBO = (BD_KC / 8) * 128;
+  constexpr uint32_t NCOLS = NP < 32 ? 32 : NP;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int hwi = a.hin * a.win, hwo = a.hout * a.wout;
+  const long long npix = (long long)a.B * hwi;
+  const long long q = (long long)blockIdx.x * 128 + tid;  // this thread's input pixel
+  const bool valid = q < npix;
+  const int n = valid ? (int)(q / hwi) : 0;
+  const int iyx = valid ? (int)(q - (long long)n * hwi) : 0;
+  const int iy = iyx / a.win, ix = iyx - iy * a.win;
+  // output rows / columns that read this input row / column through tap d
+  // (two each with upsampling: the virtual rows 2 iy and 2 iy + 1)
+  {
+    int oy[3][2], ox[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        oy[d][h] = -1;
+        ox[d][h] = -1;
+        if (h == 1 && !a.up) continue;
+        const int vy = a.up ? 2 * iy + h : iy, vx = a.up ? 2 * ix + h : ix;
+        const int ty = vy + 1 - d, tx = vx + 1 - d;
+        if (valid && ty >= 0 && ty % a.stride == 0 && ty / a.stride < a.hout) oy[d][h] = ty / a.stride;
+        if (valid && tx >= 0 && tx % a.stride == 0 && tx / a.stride < a.wout) ox[d][h] = tx / a.stride;
+      }
+    // offset of each (tap, row choice, column choice) delta in its plane, -1: none
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int yy = oy[t / 3][h >> 1], xx = ox[t % 3][h & 1];
+        offs[(t * 4 + h) * 128 + tid] = (yy >= 0 && xx >= 0) ? yy * a.wout + xx : -1;
+      }
+  }
+  if (tid == 0) {
+    tc::mbar_init1(&bar[0]);
+    tc::mbar_init1(&bar[1]);
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, NCOLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  const int K = a.co * 9;
+  const int nchunk = (K + BD_KC - 1) / BD_KC;
+  const int c_begin = (int)(((long long)nchunk * blockIdx.y) / ksplit);
+  const int c_end = (int)(((long long)nchunk * (blockIdx.y + 1)) / ksplit);
+  const float* dy = a.dout + (size_t)n * a.co * hwo;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+  uint32_t ph[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  for (int c = c_begin; c < c_end; ++c) {
+    const int s = (c - c_begin) & 1;
+    if (pending[s]) {
+      if (!tc::mbar_wait(&bar[s], ph[s])) ok = false;
+      ph[s] ^= 1u;
+      pending[s] = false;
+      tc::fence_after();
+    }
+    unsigned char* As = stage[s];
+    unsigned char* Bs = stage[s] + ABYTES;
+    const int kb = c * BD_KC;
+    // A: this thread's pixel (row tid), 64 values of k = co * 9 + tap
+#pragma unroll 1
+    for (int g = 0; g < BD_KC / 8; ++g) {
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = kb + 8 * g + e;
+        float x = 0.f;
+        if (k < K) {
+          const int co = k / 9, t = k - 9 * (k / 9);
+          const float* pl = dy + (size_t)co * hwo;
+          const int o0 = offs[(t * 4) * 128 + tid];
+          if (o0 >= 0) x = pl[o0];
+          if (a.up) {  // the other virtual rows / columns of the upsampling
+#pragma unroll
+            for (int h = 1; h < 4; ++h) {
+              const int o = offs[(t * 4 + h) * 128 + tid];
+              if (o >= 0) x += pl[o];
+            }
+          }
+        }
+        v[e] = x;
+      }
+      *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = pack8_bf16(v);
+    }
+    // B: Wt rows (input channels) x 64 values of k: W[co][ci][tap]
+    for (int u = tid; u < NP * (BD_KC / 8); u += 128) {
+      const int r = u / (BD_KC / 8), g = u % (BD_KC / 8);
+      __align__(16) __nv_bfloat16 w8[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = kb + 8 * g + e;
+        w8[e] = (r < a.ci && k < K) ? a.w[((size_t)(k / 9) * a.ci + r) * 9 + (k - 9 * (k / 9))]
+                                    : __float2bfloat16_rn(0.f);
+      }
+      *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = *reinterpret_cast<const uint4*>(w8);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < BD_KC / 16; ++kk) {
+        const uint64_t ad = tc::smem_desc(As + kk * 2 * LBO, LBO, SBO);
+        const uint64_t bd = tc::smem_desc(Bs + kk * 2 * LBO, LBO, SBO);
+        tc::mma_bf16(tbase, ad, bd, idesc, (c > c_begin || kk > 0) ? 1u : 0u);
+      }
+      tc::commit(&bar[s]);
+    }
+    pending[s] = true;
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    if (pending[s] && !tc::mbar_wait(&bar[s], ph[s])) ok = false;
+  tc::fence_after();
+  if (!ok && tid == 0) atomicExch(err_flag, 1);
+  const bool any = c_end > c_begin;
+  // epilogue: lane = input pixel blockIdx.x * 128 + tid, columns = ci
+#pragma unroll 1
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (!valid) continue;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int ci = c0 + j;
+      if (ci >= a.ci) continue;
+      const float r = any ? v[j] : 0.f;
+      if (ksplit > 1) {
+        part[((size_t)blockIdx.y * a.ci + ci) * npix + q] = r;
+        continue;
+      }
+      const size_t o = ((size_t)n * a.ci + ci) * hwi + iyx;
+      float rr = r;
+      if (a.mask && !(ldact(reinterpret_cast<const TA*>(a.mask), o) > 0.f)) rr = 0.f;
+      a.din[o] = rr;
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tbase, NCOLS);
+}
+
+// Split-K epilogue of the data gradient: the partials summed in order, the
+// previous layer's ReLU derivative applied, into a.din [B][ci][h][w].
+template <typename TA>
+__global__ void k_bwd_data_reduce(ConvArgs a, int ksplit, const float* __restrict__ part) {
+  const long long hwi = (long long)a.hin * a.win, npix = a.B * hwi;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix * a.ci;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ci = (int)(i / npix);
+    const long long q = i % npix;
+    float r = 0.f;
+    for (int s = 0; s < ksplit; ++s) r += part[((size_t)s * a.ci + ci) * npix + q];
+    const int n = (int)(q / hwi);
+    const size_t o = ((size_t)n * a.ci + ci) * hwi + (q % hwi);
+    if (a.mask && !(ldact(reinterpret_cast<const TA*>(a.mask), o) > 0.f)) r = 0.f;
+    a.din[o] = r;
+  }
+}
+
+}  // namespace ptycho

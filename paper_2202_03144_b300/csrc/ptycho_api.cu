@@ -29,6 +29,7 @@
 #include "kernel_sets.cuh"
 #include "modes.cuh"
 #include "net.cuh"
+#include "net_bwd_tc.cuh"
 #include "overlap.cuh"
 #include "shift.cuh"
 #include "probe_cg.cuh"

@@ -61,3 +61,51 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(api.PtychoError) as e:
         api.fourier_error_noalloc(O, P, pos, A)
     assert e.value.name == "ARG" and "16384" in str(e.value)
+
+
+def test_noalloc_at_its_position_limit_on_16_cta_clusters():
+    """16,384 positions (the limit) on the 256^2 detector, whose Fourier
+    kernel runs on 16-CTA clusters: the per-CTA error partials fill the whole
+    fixed scratch.  Two calls in a row against the regular call on the same
+    data (random object, probe and intensities with masked pixels)."""
+    torch = pytest.importorskip("torch")
+    M, G = 256, 128
+    J = G * G
+    iy, ix = np.meshgrid(np.arange(G), np.arange(G), indexing="ij")
+    pos = (np.stack([iy.ravel(), ix.ravel()], axis=1) * 8.0).astype(np.float32)
+    side = 8 * (G - 1) + M
+    gen = torch.Generator(device="cuda").manual_seed(16384)
+    O = torch.complex(torch.rand((side, side), device="cuda", generator=gen) + 0.5,
+                      torch.rand((side, side), device="cuda", generator=gen) - 0.5)
+    P = torch.complex(torch.rand((1, M, M), device="cuda", generator=gen),
+                      torch.rand((1, M, M), device="cuda", generator=gen) - 0.5) * 0.1
+    I = torch.rand((J, M, M), device="cuda", generator=gen) * 100.0
+    I[torch.rand((J, M, M), device="cuda", generator=gen) < 0.01] = -1.0   # masked pixels
+    with api.Reconstruction(M, 1, J, (side, side)) as r:
+        r.set_data(I, pos)
+        r.set_init(O, P)
+        E_ref = r.fourier_error()
+    # the same data as stored amplitudes: sqrt(I) with the zero frequency at (0, 0)
+    Ifft = torch.roll(I, shifts=(-(M // 2), -(M // 2)), dims=(1, 2))
+    amp = torch.where(Ifft < 0, torch.full_like(Ifft, -1.0), torch.sqrt(torch.clamp(Ifft, min=0.0)))
+    del I, Ifft
+    torch.cuda.synchronize()
+    for _ in range(2):
+        E = api.fourier_error_noalloc(O, P, pos, amp)
+        assert abs(E - E_ref) <= TOL_E * E_ref, (E, E_ref)
+
+
+def test_noalloc_rejects_host_pointers_before_any_launch():
+    """A host buffer where device memory is expected is an argument error:
+    the pointer's memory type is checked before any device work."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    M, J = 32, 2
+    O_host = np.ones((64, 64, 2), np.float32)
+    P = torch.ones((1, M, M), dtype=torch.complex64, device="cuda")
+    A = torch.ones((J, M, M), dtype=torch.float32, device="cuda")
+    pos = np.zeros((J, 2), np.float32)
+    out = ctypes.c_double()
+    rc = api.lib().ptycho_fourier_error_noalloc(O_host.ctypes.data, 64, 64, torch.view_as_real(P).data_ptr(), M, 1,
+                                                pos.ctypes.data, J, A.data_ptr(), ctypes.byref(out), None)
+    assert rc == -1 and b"device memory" in api.lib().ptycho_last_error(None)
