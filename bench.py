@@ -338,8 +338,11 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
         scorer.set_data(I, pos)
         Ob = torch.empty(shape, dtype=torch.complex64, device="cuda")
         Pb = torch.empty((K, M, M), dtype=torch.complex64, device="cuda")
-        for store in ("f32", "f16", "bf16"):
-            r = api.Reconstruction(M, K, J, shape, stream=stream.cuda_stream, istore=store)
+        runs = [("f32", {}), ("f16", dict(istore="f16")), ("bf16", dict(istore="bf16")),
+                ("f32_residual16", dict(residual_store="f16")),
+                ("f16_residual16", dict(istore="f16", residual_store="f16"))]
+        for store, kw in runs:
+            r = api.Reconstruction(M, K, J, shape, stream=stream.cuda_stream, **kw)
             r.set_data(I, pos)
             r.set_init(np.ones(shape, np.complex64), P0s)
             torch.cuda.synchronize()
@@ -362,7 +365,9 @@ def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
             out[store] = {"iterations": it, "seconds": dt, "fourier_error": E, "reached": bool(E <= eps)}
         scorer.close()
     return {"eps": eps, "reference": f"plain FP32 LSQML after {n_ref} iterations from a flat object; errors "
-                                     "measured against the FP32 data", "check_every": check, **out}
+                                     "measured against the FP32 data", "check_every": check,
+            "variants": "amplitude storage f32 / f16 / bf16; *_residual16: LSQML residuals stored as FP16",
+            **out}
 
 
 def run_epie(api, torch, stream, iters=3, warm=1, subpixel=0):
@@ -457,6 +462,21 @@ def run_engines(api, torch, stream, grid=100, iters=5, warm=2):
     return out
 
 
+def run_training(api, torch, n_frames, batch=64):
+    """Warm-start network training speed alone: n_frames simulated frames,
+    one epoch at the given batch after a four-batch warm-up."""
+    from paper_2202_03144_b300 import warmstart
+    frames, targets, _ = warmstart.make_training_set(n_frames, seed=3, per_object=min(25000, n_frames))
+    net = api.Net(seed=11, max_batch=256)
+    warmstart.train(net, frames[:batch * 4], targets[:batch * 4], epochs=1, batch=batch)
+    torch.cuda.synchronize()
+    # the loss is read back (a host sync) only at the first and the last step
+    losses, t = warmstart.train(net, frames, targets, epochs=1, batch=batch, lr=1e-3, log_every=1 << 30)
+    net.close()
+    return {"frames": n_frames, "batch": batch, "seconds": t, "frames_per_s": n_frames / t,
+            "loss_first": losses[0][1], "loss_last": losses[-1][1]}
+
+
 def run_warm_start(api, torch, stream, n_frames=200_000, epochs=1, n_ref=50, check=5):
     """Learned warm start on a 1600-position, 3-mode 128^2 scan: network
     training (one-off, reported apart), then iterations and wall time to the
@@ -538,6 +558,10 @@ def main():
     ap.add_argument("--warm-frames", type=int, default=200_000)
     ap.add_argument("--epie-only", action="store_true",
                     help="run only the ePIE sweep of the 3-mode spiral scan and print its figures (profiling runs)")
+    ap.add_argument("--engines-only", action="store_true",
+                    help="run only the 64^2 Fourier-engine comparison on a --grid (default 100) raster (profiling runs)")
+    ap.add_argument("--train-only", type=int, default=0, metavar="FRAMES",
+                    help="only train the warm-start network on FRAMES frames at batch 64 (profiling runs)")
     args = ap.parse_args()
     if args.small:
         WORKLOAD["grid"] = 20
@@ -562,6 +586,13 @@ def main():
     if args.epie_only:
         stream = torch.cuda.Stream()
         print(json.dumps(run_epie(api, torch, stream)), flush=True)
+        return
+    if args.engines_only:
+        stream = torch.cuda.Stream()
+        print(json.dumps(run_engines(api, torch, stream, grid=args.grid or 100)), flush=True)
+        return
+    if args.train_only:
+        print(json.dumps(run_training(api, torch, args.train_only)), flush=True)
         return
     w = WORKLOAD
     M, K, J = w["M"], w["K"], w["grid"] ** 2
@@ -593,11 +624,11 @@ def main():
     stream.synchronize()
 
     def timed(alg, istore="f32", steps=args.steps, warm=args.warmup, profile=False, likelihood="amplitude",
-              subpixel=0, block_positions=0, fractional_data=None):
+              subpixel=0, block_positions=0, fractional_data=None, residual_store="f32"):
         with torch.cuda.stream(stream):
             r = api.Reconstruction(M, K, J, (w["obj"], w["obj"]), stream=stream.cuda_stream, istore=istore,
                                    cluster=args.cluster, likelihood=likelihood, subpixel=subpixel,
-                                   block_positions=block_positions)
+                                   block_positions=block_positions, residual_store=residual_store)
             if subpixel or fractional_data:
                 r.set_data(I_sub, pos_sub)
             else:
@@ -637,6 +668,8 @@ def main():
     f16_run = timed("lsqml", istore="f16")
     bf16_run = timed("lsqml", istore="bf16")
     poisson_run = timed("lsqml", likelihood="poisson")
+    r16_run = timed("lsqml", residual_store="f16")
+    r16a16_run = timed("lsqml", istore="f16", residual_store="f16")
     sub_run = timed("lsqml", subpixel=SUBPIXEL)
     # the same fractional-position data under the whole-pixel model (positions rounded)
     sub_rounded = timed("lsqml", fractional_data=True)
@@ -783,6 +816,10 @@ def main():
             "lsqml_f16": {"value": rate(f16_run), "fourier_error": f16_run["err"]},
             "lsqml_poisson_f32": {"value": rate(poisson_run), "fourier_error": poisson_run["err"]},
             "lsqml_bf16": {"value": rate(bf16_run), "fourier_error": bf16_run["err"]},
+            "lsqml_f32_residual16": {"value": rate(r16_run), "fourier_error": r16_run["err"],
+                                     "note": "LSQML residuals stored as FP16 between the passes"},
+            "lsqml_f16_residual16": {"value": rate(r16a16_run), "fourier_error": r16a16_run["err"],
+                                     "note": "FP16 amplitudes and FP16 residuals"},
             f"lsqml_subpixel{SUBPIXEL}_f32": {"value": rate(sub_run), "fourier_error": sub_run["err"],
                                               "positions": "whole-pixel raster + uniform [0, 1) offsets",
                                               "fourier_error_rounded_positions": sub_rounded["err"],

@@ -60,6 +60,10 @@ enum { PTYCHO_EPIE = 0, PTYCHO_DM = 1, PTYCHO_LSQML = 2 };
  * all arithmetic stays float32. */
 enum { PTYCHO_I_F32 = 0, PTYCHO_I_F16 = 1, PTYCHO_I_BF16 = 2 };
 
+/* Storage of LSQML's residuals between the passes of an iteration
+ * (ptycho_params.residual_store). */
+enum { PTYCHO_R_F32 = 0, PTYCHO_R_F16 = 1 };
+
 /* Transform engine of the Fourier passes (ptycho_params.fft_engine). */
 enum { PTYCHO_FFT_REGISTER = 0, PTYCHO_DFT_TENSOR_BF16X3 = 1 };
 
@@ -167,6 +171,16 @@ typedef struct {
                        per transform stage instead of 24.  Compiled for M = 64,
                        K = 1 (else PTYCHO_ERR_UNSUPPORTED).  ePIE's sweep
                        keeps its own kernels.                                */
+  int residual_store; /* LSQML's residuals chi between the Fourier pass that
+                       writes them and the five passes that read them (object
+                       and probe directions, step sizes, object and probe
+                       updates): PTYCHO_R_F32 (default) or PTYCHO_R_F16
+                       (half the bytes of the iteration's dominant traffic;
+                       chi rounded to 11 significant bits, every sum and
+                       update still FP32 / FP64).  The reduced-precision
+                       storage pattern applied to the residual; DM's exit
+                       waves, ptycho_fourier_residual's output and the
+                       position refinement stay FP32.                      */
 } ptycho_params;
 
 /* Fill *p with the defaults above (M, K, J and the object size are zero). */

@@ -21,6 +21,7 @@ I_F32, I_F16, I_BF16 = 0, 1, 2
 ISTORE = {"f32": I_F32, "f16": I_F16, "bf16": I_BF16}
 LIKELIHOOD = {"amplitude": 0, "poisson": 1}  # PTYCHO_LIK_AMPLITUDE, PTYCHO_LIK_POISSON
 FFT_ENGINE = {"register": 0, "tensor_bf16x3": 1}  # PTYCHO_FFT_REGISTER, PTYCHO_DFT_TENSOR_BF16X3
+RESIDUAL_STORE = {"f32": 0, "f16": 1}  # PTYCHO_R_F32, PTYCHO_R_F16
 
 ERRORS = {
     -1: "ARG", -2: "BOUNDS", -3: "NONFINITE", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
@@ -43,6 +44,7 @@ class Params(C.Structure):
         ("reg", C.c_double), ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("cluster", C.c_int),
         ("likelihood", C.c_int), ("probe_ortho", C.c_int), ("subpixel", C.c_int),
         ("block_positions", C.c_int), ("mem_limit", C.c_ulonglong), ("fft_engine", C.c_int),
+        ("residual_store", C.c_int),
     ]
 
 
@@ -180,6 +182,8 @@ def default_params(**kw) -> Params:
             v = LIKELIHOOD[v]
         if k == "fft_engine" and isinstance(v, str):
             v = FFT_ENGINE[v]
+        if k == "residual_store" and isinstance(v, str):
+            v = RESIDUAL_STORE[v]
         if k == "probe_ortho":
             v = int(bool(v))
         setattr(p, k, v)

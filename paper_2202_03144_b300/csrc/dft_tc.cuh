@@ -252,7 +252,9 @@ __global__ void __launch_bounds__(TC64_NT, 2) k_fourier_tc64(Fourier2Args a, con
     for (int r = 0; r < 64; ++r) {
       const size_t xi = ((size_t)r * M + idx) * 2 + ri;
       if (mode == FM_CHI || mode == FM_CHIP) {
-        __stcs(xo + xi, d[r]);
+        if (a.x16) __stcs(reinterpret_cast<unsigned short*>(a.X) + (size_t)(j - a.xoff) * M * M * 2 + xi,
+                          __half_as_ushort(__float2half_rn(d[r])));
+        else __stcs(xo + xi, d[r]);
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + r) * a.nx + p.y + idx);
         const float2 pr = __ldg(Pj + (size_t)r * M + idx);

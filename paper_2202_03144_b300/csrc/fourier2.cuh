@@ -148,11 +148,18 @@ struct Fourier2Args {
   const float2* tw2;      // tw2[k1 * R2 + n2] = exp(-2 pi i n2 k1 / M)
   int* err_flag;          // set to 1 if a bounded wait gave up
   int wait_limit;         // polls of a cluster-transpose wait before it gives up
+  int x16;                // residual passes: X holds chi as FP16 complex (__half2)
   int j0;                 // first position of the launch
   int nj;                 // positions of the launch (persistent kernels walk them)
   int xoff;               // X holds positions from xoff on (position-blocked residuals)
   int mode;
 };
+
+// A complex value rounded to FP16, as the 32-bit pattern of a __half2.
+__device__ __forceinline__ unsigned half2_bits(float2 v) {
+  const __half2 h = __float22half2_rn(v);
+  return *reinterpret_cast<const unsigned*>(&h);
+}
 
 // Detector-plane factor f with D = f Psi (before the 1/M^2 of the inverse
 // transform), from the stored amplitude am = sqrt(I) (< 0: masked) and
@@ -479,7 +486,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, (F2<M, K, C>::R1 > 16 ? 1 : (
       const int row = n1 * R2 + n2;
       const size_t xi = (((size_t)(j - a.xoff) * K + k) * M + row) * M + col;
       if (mode == FM_CHI || mode == FM_CHIP) {
-        __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
+        // streamed out (evict first: keep L2 for O and P), FP32 or FP16
+        if (a.x16) __stcs(reinterpret_cast<unsigned*>(a.X) + xi, half2_bits(v[n1]));
+        else __stcs(a.X + xi, v[n1]);
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
         const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);

@@ -425,7 +425,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       const int row = n1 * R2 + n2;
       const size_t xi = (((size_t)(j - a.xoff) * K + k) * M + row) * M + col;
       if (mode == FM_CHI || mode == FM_CHIP) {
-        __stcs(a.X + xi, v[n1]);  // streamed out: evict first, keep L2 for O and P
+        // streamed out (evict first: keep L2 for O and P), FP32 or FP16
+        if (a.x16) __stcs(reinterpret_cast<unsigned*>(a.X) + xi, half2_bits(v[n1]));
+        else __stcs(a.X + xi, v[n1]);
       } else {
         const float2 o = __ldg(a.O + (size_t)(p.x + row) * a.nx + p.y + col);
         const float2 pr = __ldg(Pj + ((size_t)k * M + row) * M + col);

@@ -401,6 +401,10 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     maxd = std::max(maxd, (size_t)max_batch * L.ci * L.hin * L.win);
     const long long npo = (long long)max_batch * L.hout * L.wout;
     maxpart = std::max(maxpart, (size_t)((npo + BW_CHUNK - 1) / BW_CHUNK) * L.co * L.ci * 9);
+    // the tensor-core weight gradient: about two CTAs per SM of pixel splits
+    const long long tiles = ((L.co + 127) / 128) * ((L.ci * 9 + BW_NT - 1) / BW_NT);
+    const long long want = std::min<long long>((2 * 148 + tiles - 1) / tiles, (npo + BW_KC - 1) / BW_KC);
+    maxpart = std::max(maxpart, (size_t)want * L.co * L.ci * 9);
   }
   int r = 0;
   if (!r) r = nalloc(n, &n->params, n->n_params);

@@ -19,6 +19,8 @@
 // bin order and the groups never straddle a bin, so the fixed-order sum
 // yields one numerator per bin (the caller then applies the adjoint shifts).
 #pragma once
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace ptycho {
@@ -53,6 +55,26 @@ constexpr int PROBE_NT = 256;
 #endif
 #define PT_PRAGMA(x) _Pragma(#x)
 #define PT_UNROLL(n) PT_PRAGMA(unroll n)
+// Residual loads: X holds FP32 complex values (float2) or, with FP16
+// residual storage, __half2; either way the kernels compute in FP32.
+// ld_x: element i; ld_x2: elements i and i + 1 (i even) as one float4.
+template <typename XT>
+__device__ __forceinline__ float2 ld_x(const float2* X, size_t i) {
+  if constexpr (sizeof(XT) == 8) return __ldcs(X + i);
+  else return __half22float2(__ldcs(reinterpret_cast<const __half2*>(X) + i));
+}
+template <typename XT>
+__device__ __forceinline__ float4 ld_x2(const float2* X, size_t i) {
+  if constexpr (sizeof(XT) == 8) {
+    return __ldcs(reinterpret_cast<const float4*>(X + i));
+  } else {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __half2*>(X) + i));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 constexpr int OBJ_CHUNK = 256;   // positions staged per chunk (k_obj)
 constexpr int PROBE_CHUNK = 512; // positions staged per chunk (k_probe_partial)
 
@@ -87,7 +109,7 @@ struct ObjArgs {
 };
 
 // SUB: sub-pixel positions (P is the shifted table, indexed by pbin).
-template <int K, int MODE, bool SUB>
+template <int K, int MODE, bool SUB, typename XT = float2>
 __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArgs a) {  // K > 1: 3 (no spills)
   __shared__ float red[32];
   const int tile = blockIdx.x;
@@ -156,7 +178,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
           const bool row_in = uy >= 0 && uy < M;
           const size_t u0 = (size_t)(row_in ? uy : 0) * M;
           const float2* prow = Pj + k * MM + u0;
-          const float2* xrow = a.X + ((size_t)(j - a.xoff) * K + k) * MM + u0;
+          const size_t xrow = ((size_t)(j - a.xoff) * K + k) * MM + u0;  // element index in X
           if (pairs) {
 #pragma unroll
             for (int e = 0; e < OBJ_COLS; e += 2) {
@@ -164,7 +186,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
               float4 pq = make_float4(0.f, 0.f, 0.f, 0.f), xq = pq;
               if (in) {
                 pq = __ldg(reinterpret_cast<const float4*>(prow + ux + e));
-                xq = __ldcs(reinterpret_cast<const float4*>(xrow + ux + e));
+                xq = ld_x2<XT>(a.X, xrow + ux + e);
               }
               pv[i][e] = make_float2(pq.x, pq.y);
               pv[i][e + 1] = make_float2(pq.z, pq.w);
@@ -176,7 +198,7 @@ __global__ void __launch_bounds__(OBJ_NT, K == 1 ? PT_OBJ_MINB : 3) k_obj(ObjArg
             for (int e = 0; e < OBJ_COLS; ++e) {
               const bool in = row_in && ux + e >= 0 && ux + e < M;
               pv[i][e] = in ? __ldg(prow + ux + e) : make_float2(0.f, 0.f);
-              xv[i][e] = in ? __ldcs(xrow + ux + e) : make_float2(0.f, 0.f);
+              xv[i][e] = in ? ld_x<XT>(a.X, xrow + ux + e) : make_float2(0.f, 0.f);
             }
           }
         }
@@ -303,7 +325,7 @@ struct ProbeArgs {
 };
 
 // SUB: positions taken through the bin order and its group offsets.
-template <int K, bool SUB>
+template <int K, bool SUB, typename XT = float2>
 __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
   const int MM = a.M * a.M;
   const int u = blockIdx.x * PROBE_NT + threadIdx.x;
@@ -343,7 +365,7 @@ __global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
           w[h] = in ? sw[i] : 0.f;
 #pragma unroll
           for (int k = 0; k < K; ++k)
-            xv[h][k] = in ? __ldcs(a.X + ((size_t)((SUB ? sj[i] : c0 + i) - a.xoff) * K + k) * MM + u)
+            xv[h][k] = in ? ld_x<XT>(a.X, ((size_t)((SUB ? sj[i] : c0 + i) - a.xoff) * K + k) * MM + u)
                           : make_float2(0.f, 0.f);
         }
 #pragma unroll
@@ -458,13 +480,14 @@ struct StepArgs {
   float* alpha_O;
   float* alpha_P;
   int j0, xoff;       // first position of the launch; X holds positions from xoff on
+  int nj;             // positions of the launch
 };
 
 constexpr int STEP_NT = 256;
 
 // SUB: sub-pixel positions (P and dP are shifted tables indexed by pbin); the
 // extra offset costs registers, so K = 3 then runs at three CTAs per SM.
-template <int K, bool SUB>
+template <int K, bool SUB, typename XT = float2>
 __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k_lsqml_steps(StepArgs a) {
   __shared__ double red[32];
   const int j = a.j0 + blockIdx.x;
@@ -485,12 +508,13 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
   const bool pairs = ((p.y | a.nx) & 1) == 0;
   // this position's residuals, streamed from HBM: thread 0 keeps the next
   // PT_STEP_PF loop steps' chunks (STEP values per mode) on their way to L2
-  const float2* xj = a.X + (size_t)(j - a.xoff) * K * MM;
+  const size_t xj = (size_t)(j - a.xoff) * K * MM;  // element index of this position's residuals
+  const unsigned char* xb = reinterpret_cast<const unsigned char*>(a.X);
   if (PT_STEP_PF > 0 && threadIdx.x == 0)
     for (int q = 0; q < PT_STEP_PF && q * STEP < MM; ++q)
 #pragma unroll
       for (int k = 0; k < K; ++k)
-        prefetch_l2(xj + (size_t)k * MM + q * STEP, (uint32_t)(min(STEP, MM - q * STEP) * sizeof(float2)));
+        prefetch_l2(xb + (xj + (size_t)k * MM + q * STEP) * sizeof(XT), (uint32_t)(min(STEP, MM - q * STEP) * sizeof(XT)));
   PT_UNROLL(PT_STEP_UNROLL)
   for (; u < MM; u += STEP) {
     if (PT_STEP_PF > 0 && threadIdx.x == 0) {
@@ -498,7 +522,7 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
       if (ua < MM)
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          prefetch_l2(xj + (size_t)k * MM + ua, (uint32_t)(min(STEP, MM - ua) * sizeof(float2)));
+          prefetch_l2(xb + (xj + (size_t)k * MM + ua) * sizeof(XT), (uint32_t)(min(STEP, MM - ua) * sizeof(XT)));
     }
     const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
     float2 o0, o1, d0, d1;
@@ -515,7 +539,7 @@ __global__ void __launch_bounds__(STEP_NT, (SUB && K == 3) ? 3 : PT_STEP_MINB) k
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       pr[k] = __ldg(reinterpret_cast<const float4*>(a.P + boff + (size_t)k * MM + u));
-      xv[k] = __ldcs(reinterpret_cast<const float4*>(xj + (size_t)k * MM + u));
+      xv[k] = ld_x2<XT>(a.X, xj + (size_t)k * MM + u);
       dp[k] = upd ? __ldg(reinterpret_cast<const float4*>(a.dP + boff + (size_t)k * MM + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll

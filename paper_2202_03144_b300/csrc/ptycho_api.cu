@@ -327,6 +327,7 @@ struct ptycho_ctx {
   float2* tw2 = nullptr;
   int* err_flag = nullptr;   // set by a device wait that gave up
   int wait_limit = 1 << 20;  // polls of a cluster-transpose wait (ptycho_set_wait_limit)
+  bool x16 = false;          // inside an LSQML iteration with FP16 residual storage
   cudaStream_t st_side = nullptr;  // second stream: the probe-direction sums beside the object's
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned char* dftm = nullptr;  // split DFT matrix of the tensor-core engine
@@ -607,6 +608,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   a.tw2 = ctx->tw2;
   a.err_flag = ctx->err_flag;
   a.wait_limit = ctx->wait_limit;
+  a.x16 = ctx->x16 && X == ctx->X && (mode == FM_CHI || mode == FM_CHIP);
   a.j0 = j0;
   a.nj = nj;
   a.xoff = ctx->f_xoff >= 0 ? ctx->f_xoff : ((ctx->blk.on && X == ctx->X) ? ctx->blk.j0 : 0);
@@ -617,7 +619,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
   switch (mode) {
     case FM_DM: bytes = nj * MM * (16.0 * K + amp_bytes(ctx)); break;
     case FM_CHI:
-    case FM_CHIP: bytes = nj * MM * (8.0 * K + amp_bytes(ctx)); break;
+    case FM_CHIP: bytes = nj * MM * ((a.x16 ? 4.0 : 8.0) * K + amp_bytes(ctx)); break;
     case FM_ERR: bytes = nj * MM * amp_bytes(ctx); break;
     case FM_SIM: bytes = nj * MM * 4.0; break;
   }
@@ -812,26 +814,28 @@ int launch_obj(ptycho_ctx* ctx, int mode, const float2* X, const float* w) {
     a.accumulate = ctx->blk.accumulate;
   }
   const double obj = (double)ctx->p.obj_ny * ctx->p.obj_nx;
-  const double xb = 8.0 * nj * K * (double)ctx->p.M * ctx->p.M;
+  const double xb = (ctx->x16 && X == ctx->X ? 4.0 : 8.0) * nj * K * (double)ctx->p.M * ctx->p.M;
   const dim3 g(ctx->n_tiles), b(OBJ_NT);
   const bool sub = ctx->S != 0;
+  const bool h = ctx->x16 && X == ctx->X;  // FP16 residuals
+  auto go = [&](auto kern) { kern<<<g, b, 0, ctx->st>>>(a); };
   if (mode == OBJ_STEP_ACC) {  // numerator only, into objacc
     a.dO = ctx->objacc;
     a.den = nullptr;
     return launch(ctx, "obj_update", xb + obj * 16.0, [&] {
-      if (sub) k_obj<K, OBJ_NUMDEN, true><<<g, b, 0, ctx->st>>>(a);
-      else k_obj<K, OBJ_NUMDEN, false><<<g, b, 0, ctx->st>>>(a);
+      if (sub) go(h ? k_obj<K, OBJ_NUMDEN, true, __half2> : k_obj<K, OBJ_NUMDEN, true>);
+      else go(h ? k_obj<K, OBJ_NUMDEN, false, __half2> : k_obj<K, OBJ_NUMDEN, false>);
     });
   }
   if (mode == OBJ_UPD)
     return launch(ctx, "obj_update", xb + obj * 20.0, [&] {
-      if (sub) k_obj<K, OBJ_UPD, true><<<g, b, 0, ctx->st>>>(a);
-      else k_obj<K, OBJ_UPD, false><<<g, b, 0, ctx->st>>>(a);
+      if (sub) go(h ? k_obj<K, OBJ_UPD, true, __half2> : k_obj<K, OBJ_UPD, true>);
+      else go(h ? k_obj<K, OBJ_UPD, false, __half2> : k_obj<K, OBJ_UPD, false>);
     });
   // numerator + den_O in one pass, then the max of den_O, then the epilogue
   if (int r = launch(ctx, "obj_sums", xb + obj * 12.0, [&] {
-        if (sub) k_obj<K, OBJ_NUMDEN, true><<<g, b, 0, ctx->st>>>(a);
-        else k_obj<K, OBJ_NUMDEN, false><<<g, b, 0, ctx->st>>>(a);
+        if (sub) go(h ? k_obj<K, OBJ_NUMDEN, true, __half2> : k_obj<K, OBJ_NUMDEN, true>);
+        else go(h ? k_obj<K, OBJ_NUMDEN, false, __half2> : k_obj<K, OBJ_NUMDEN, false>);
       }))
     return r;
   if (ctx->blk.on) return 0;  // the epilogue runs once, after the last block (obj_finish)
@@ -953,11 +957,17 @@ int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, boo
   a.beta = (float)ctx->p.lsqml_beta;
   const int MM = ctx->p.M * ctx->p.M;
   const int nblk = (MM + PROBE_NT - 1) / PROBE_NT;
-  const double xb = 8.0 * a.J * K * (double)MM;
+  const double xb = (ctx->x16 && X == ctx->X ? 4.0 : 8.0) * a.J * K * (double)MM;
   if (X) {
     if (int r = launch(ctx, "probe_partial", xb, [&] {
-          if (ctx->S) k_probe_partial<K, true><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
-          else k_probe_partial<K, false><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+          const bool h = ctx->x16 && X == ctx->X;  // FP16 residuals
+          if (ctx->S) {
+            if (h) k_probe_partial<K, true, __half2><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+            else k_probe_partial<K, true><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+          } else {
+            if (h) k_probe_partial<K, false, __half2><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+            else k_probe_partial<K, false><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+          }
         }))
       return r;
     ProbeArgs s = a;
@@ -1005,20 +1015,23 @@ int steps_step(ptycho_ctx* ctx, bool upd) {
     a.xoff = ctx->blk.j0;
     J = ctx->blk.n;
   }
-  const double xb = 8.0 * J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
+  a.nj = J;
+  const bool h = ctx->x16;  // FP16 residuals (a.X is ctx->X)
+  const double xb = (h ? 4.0 : 8.0) * J * ctx->p.K * (double)ctx->p.M * ctx->p.M;
   const bool sub = ctx->S != 0;
+  auto go = [&](auto kern, unsigned grid) { kern<<<grid, STEP_NT, 0, ctx->st>>>(a); };
   switch (ctx->p.K) {
     case 1: return launch(ctx, "lsqml_steps", xb, [&] {
-        if (sub) k_lsqml_steps<1, true><<<J, STEP_NT, 0, ctx->st>>>(a);
-        else k_lsqml_steps<1, false><<<J, STEP_NT, 0, ctx->st>>>(a);
+        if (sub) go(h ? k_lsqml_steps<1, true, __half2> : k_lsqml_steps<1, true>, J);
+        else go(h ? k_lsqml_steps<1, false, __half2> : k_lsqml_steps<1, false>, J);
       });
     case 2: return launch(ctx, "lsqml_steps", xb, [&] {
-        if (sub) k_lsqml_steps<2, true><<<J, STEP_NT, 0, ctx->st>>>(a);
-        else k_lsqml_steps<2, false><<<J, STEP_NT, 0, ctx->st>>>(a);
+        if (sub) go(h ? k_lsqml_steps<2, true, __half2> : k_lsqml_steps<2, true>, J);
+        else go(h ? k_lsqml_steps<2, false, __half2> : k_lsqml_steps<2, false>, J);
       });
     default: return launch(ctx, "lsqml_steps", xb, [&] {
-        if (sub) k_lsqml_steps<3, true><<<J, STEP_NT, 0, ctx->st>>>(a);
-        else k_lsqml_steps<3, false><<<J, STEP_NT, 0, ctx->st>>>(a);
+        if (sub) go(h ? k_lsqml_steps<3, true, __half2> : k_lsqml_steps<3, true>, J);
+        else go(h ? k_lsqml_steps<3, false, __half2> : k_lsqml_steps<3, false>, J);
       });
   }
 }
@@ -1143,8 +1156,18 @@ int launch_chi(ptycho_ctx* ctx, float2* dst) {
 
 int lsqml_step_blocked(ptycho_ctx* ctx, bool upd);
 
+int lsqml_step_impl(ptycho_ctx* ctx, bool upd);
+
+// One LSQML iteration; with FP16 residual storage the residual passes of this
+// iteration read and write ctx->X as __half2.
 int lsqml_step(ptycho_ctx* ctx, bool upd) {
-  if (ctx->B > 0 && ctx->B < ctx->p.J) return lsqml_step_blocked(ctx, upd);
+  ctx->x16 = ctx->p.residual_store == PTYCHO_R_F16;
+  const int r = (ctx->B > 0 && ctx->B < ctx->p.J) ? lsqml_step_blocked(ctx, upd) : lsqml_step_impl(ctx, upd);
+  ctx->x16 = false;
+  return r;
+}
+
+int lsqml_step_impl(ptycho_ctx* ctx, bool upd) {
   if (int r = launch_chi(ctx, ctx->X)) return r;
   if (int r = direction_sums(ctx, upd)) return r;
   if (int r = steps_step(ctx, upd)) return r;
@@ -1717,6 +1740,8 @@ int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
   if (!(p->reg >= 0.0) || !std::isfinite(p->epie_alpha) || !std::isfinite(p->epie_beta) ||
       !std::isfinite(p->lsqml_beta))
     return fail(nullptr, PTYCHO_ERR_ARG, "non-finite or negative step parameter");
+  if (p->residual_store != PTYCHO_R_F32 && p->residual_store != PTYCHO_R_F16)
+    return fail(nullptr, PTYCHO_ERR_ARG, "residual_store=%d", p->residual_store);
   if (p->fft_engine != PTYCHO_FFT_REGISTER && p->fft_engine != PTYCHO_DFT_TENSOR_BF16X3)
     return fail(nullptr, PTYCHO_ERR_ARG, "fft_engine=%d", p->fft_engine);
   if (p->fft_engine == PTYCHO_DFT_TENSOR_BF16X3 && (p->M != 64 || p->K != 1))

@@ -150,3 +150,10 @@ def test_fft_engine_validated_before_device_work(lib):
     with pytest.raises(api.PtychoError) as e:
         api.create(api.default_params(M=64, K=3, J=4, obj_ny=96, obj_nx=96, fft_engine="tensor_bf16x3"))
     assert e.value.name == "UNSUPPORTED"
+
+
+def test_residual_store_validated(lib):
+    with pytest.raises(api.PtychoError) as e:
+        api.create(api.default_params(M=64, K=1, J=4, obj_ny=96, obj_nx=96, residual_store=3))
+    assert e.value.name == "ARG"
+    assert api.default_params().residual_store == 0
