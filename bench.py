@@ -560,6 +560,8 @@ def main():
                     help="run only the ePIE sweep of the 3-mode spiral scan and print its figures (profiling runs)")
     ap.add_argument("--engines-only", action="store_true",
                     help="run only the 64^2 Fourier-engine comparison on a --grid (default 100) raster (profiling runs)")
+    ap.add_argument("--residual-store", default="f32", choices=["f32", "f16"],
+                    help="LSQML residual storage of the headline and profile runs (profiling runs; --grid or --small)")
     ap.add_argument("--train-only", type=int, default=0, metavar="FRAMES",
                     help="only train the warm-start network on FRAMES frames at batch 64 (profiling runs)")
     args = ap.parse_args()
@@ -572,6 +574,8 @@ def main():
         WORKLOAD["obj"] = -(-(24 * args.grid + 236) // 16) * 16
     if args.impl == "reference":
         return run_reference(args)
+    if args.residual_store != "f32" and not (args.small or args.grid):
+        ap.error("--residual-store is for profiling runs (--grid or --small): the headline stores FP32 residuals")
 
     import torch
     from paper_2202_03144_b300 import api, synth
@@ -663,7 +667,7 @@ def main():
         ms = max_over_ranks(dist, ms)
         return dict(ms=ms, launches=launches, clocks=clocks, prof=prof, err=err, refine_ms=refine_ms)
 
-    main_run = timed("lsqml")
+    main_run = timed("lsqml", residual_store=args.residual_store)
     dm_run = timed("dm")
     f16_run = timed("lsqml", istore="f16")
     bf16_run = timed("lsqml", istore="bf16")
@@ -675,7 +679,7 @@ def main():
     sub_rounded = timed("lsqml", fractional_data=True)
     sub_dm_run = timed("dm", subpixel=SUBPIXEL)
     blk_run = timed("lsqml", block_positions=J // 4)
-    prof_run = timed("lsqml", steps=3, warm=1, profile=True)
+    prof_run = timed("lsqml", steps=3, warm=1, profile=True, residual_store=args.residual_store)
 
     def rate(run):
         return aggregate_rate(J * args.steps, world, run["ms"] / 1e3)
@@ -809,7 +813,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": bench_config(world, w),
+        "config": dict(bench_config(world, w), **({"residual_store": args.residual_store}
+                                                   if args.residual_store != "f32" else {})),
         "by_variant": {
             "lsqml_f32": {"value": value, "fourier_error": main_run["err"]},
             "dm_f32": {"value": rate(dm_run), "fourier_error": dm_run["err"]},

@@ -244,6 +244,27 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(ConvArgs a, int ksplit, flo
 #pragma unroll
       for (int g = 0; g < TC_KC / 8; ++g)
         *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = q[g];
+    } else if (a.ci >= 8) {
+      // NCHW with tap-major weights: k = tap * ci + c, so a group of eight k
+      // is one tap (one offset) and eight channel planes
+      const int lg = 31 - __clz(a.ci);
+      const unsigned short* src16 = reinterpret_cast<const unsigned short*>(src);
+      uint32_t w[TC_KC / 2];
+#pragma unroll
+      for (int g = 0; g < TC_KC / 8; ++g) {
+        const int k = k0 + 8 * g;
+        const int o = k < K ? offs[(k >> lg) * 128 + tid] : -1;
+        const unsigned short* pc = src16 + (size_t)(k & (a.ci - 1)) * plane + (o >= 0 ? o : 0);
+        unsigned short raw[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) raw[e] = o >= 0 ? __ldg(pc + (size_t)e * plane) : (unsigned short)0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[4 * g + e] = (uint32_t)raw[2 * e] | ((uint32_t)raw[2 * e + 1] << 16);
+      }
+#pragma unroll
+      for (int g = 0; g < TC_KC / 8; ++g)
+        *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) =
+            make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
     } else {
     // A: this thread's pixel (row tid), 64 values of k = ci * 9 + tap, in
     // two halves of 32 independent loads (one memory latency per half, not
@@ -613,6 +634,22 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int nchunk, size_t 
   }
 }
 
+// The same sums for few weights and many chunks: a warp per weight, lane l
+// adding chunks l, l + 32, ... in order, then a fixed butterfly across the
+// lanes (deterministic; the serial per-thread loop is a long latency chain
+// there).
+__global__ void __launch_bounds__(256) k_sum_chunks_warp(const float* __restrict__ part, int nchunk, size_t n,
+                                                         float* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int c = lane; c < nchunk; c += 32) s += part[(size_t)c * n + i];
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if (lane == 0) out[i] = s;
+}
+
 // Bias gradient, stage 1: CTA (channel, slice) sums its slice of the
 // channel's B x hw deltas (FP32 per thread, FP64 block sum) into
 // part[slice][channel]; stage 2 adds the slices in order.
@@ -661,8 +698,10 @@ struct AdamArgs {
   float* m;
   float* v;
   __nv_bfloat16* wb;     // BF16 copy (weights only; NULL entries skipped via is_w)
+  __nv_bfloat16* wt;     // tap-major BF16 copy, or NULL
   const unsigned char* is_w;
   const int* wb_index;   // position of the parameter in the BF16 copy
+  const int* wt_index;   // ... and in the tap-major copy
   size_t n;
   float lr, b1, b2, eps, wd, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
 };
@@ -677,7 +716,11 @@ __global__ void k_adam(AdamArgs a) {
     float p = a.p[i];
     p -= a.lr * ((m / a.c1) / (sqrtf(v / a.c2) + a.eps) + (a.is_w[i] ? a.wd * p : 0.f));
     a.p[i] = p;
-    if (a.is_w[i]) a.wb[a.wb_index[i]] = __float2bfloat16_rn(p);
+    if (a.is_w[i]) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(p);
+      a.wb[a.wb_index[i]] = h;
+      if (a.wt) a.wt[a.wt_index[i]] = h;
+    }
   }
 }
 

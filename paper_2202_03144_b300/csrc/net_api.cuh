@@ -17,6 +17,7 @@ struct ptycho_net {
   bool wt_valid = false;        // wt matches wb
   unsigned char* is_w = nullptr;
   int* wb_index = nullptr;
+  int* wt_index = nullptr;      // position of each weight in wt
   bool f32 = false;             // FP32 activations (verification mode)
   bool tc = true;               // forward convolutions on the tensor cores (BF16 mode)
   int* err_flag = nullptr;      // set by a bounded device wait that gave up
@@ -160,10 +161,32 @@ int bw_tc_splits(const NetLayer& L, int B, size_t wpart_n) {
   return (int)std::max<long long>(s, 1);
 }
 
-// K splits of the data gradient over co * 9 (deep layers have few pixels)
+// The parity-class data gradient of the stride-2 layers takes even input
+// sizes, outputs of half the size and co a multiple of 8.
+constexpr bool s2_layers_ok(int l = 0) {
+  return l == NET_LAYERS ? true
+                         : ((net_layer(l).stride != 2 ||
+                             (net_layer(l).hin % 2 == 0 && net_layer(l).win % 2 == 0 &&
+                              net_layer(l).hout == net_layer(l).hin / 2 && net_layer(l).wout == net_layer(l).win / 2 &&
+                              net_layer(l).co % 8 == 0 && !net_layer(l).up)) &&
+                            s2_layers_ok(l + 1));
+}
+static_assert(s2_layers_ok(), "stride-2 layer shapes");
+// The tap-major gathers take a channel as k & (ci - 1) from 8 channels on.
+constexpr bool ci_pow2(int l = 0) {
+  return l == NET_LAYERS ? true
+                         : ((net_layer(l).ci < 8 || (net_layer(l).ci & (net_layer(l).ci - 1)) == 0) && ci_pow2(l + 1));
+}
+static_assert(ci_pow2(), "input channels a power of two");
+
+// K splits of the data gradient over co * 9 (deep layers have few pixels).
+// Stride 2: four parity classes of B hin win / 4 pixels each, at most four
+// taps per class.
 int bd_tc_splits(const NetLayer& L, int B) {
-  const long long tiles = ((long long)B * L.hin * L.win + 127) / 128;
-  const int nchunk = (L.co * 9 + BD_KC - 1) / BD_KC;
+  const bool s2 = L.stride == 2;
+  const long long tiles = s2 ? 4 * (((long long)B * (L.hin / 2) * (L.win / 2) + 127) / 128)
+                             : ((long long)B * L.hin * L.win + 127) / 128;
+  const int nchunk = (L.co * (s2 ? 4 : 9) + BD_KC - 1) / BD_KC;
   long long ks = (2 * 148 + tiles - 1) / tiles;
   if (ks > nchunk) ks = nchunk;
   if (ks < 1) ks = 1;
@@ -185,8 +208,15 @@ template <int NP>
 void launch_bwd_data_tc(ptycho_net* n, const ConvArgs& a, const NetLayer& L) {
   const long long npix = (long long)a.B * a.hin * a.win;
   const int ks = bd_tc_splits(L, a.B);
-  const dim3 g((unsigned)((npix + 127) / 128), (unsigned)ks);
-  k_conv_bwd_data_tc<__nv_bfloat16, NP><<<g, 128, bd_tc_smem<NP>(), n->st>>>(a, ks, n->bd_part, n->err_flag);
+  if (L.stride == 2) {  // by parity class (even sizes, co a multiple of 8: the layer table)
+    const long long tiles = ((long long)a.B * (L.hin / 2) * (L.win / 2) + 127) / 128;
+    const dim3 g((unsigned)(4 * tiles), (unsigned)ks);
+    k_conv_bwd_data_s2_tc<__nv_bfloat16, NP><<<g, 128, bd_s2_tc_smem<__nv_bfloat16, NP>(), n->st>>>(
+        a, ks, n->bd_part, n->err_flag);
+  } else {
+    const dim3 g((unsigned)((npix + 127) / 128), (unsigned)ks);
+    k_conv_bwd_data_tc<__nv_bfloat16, NP><<<g, 128, bd_tc_smem<NP>(), n->st>>>(a, ks, n->bd_part, n->err_flag);
+  }
   if (ks > 1) {
     const unsigned rb = (unsigned)std::min<long long>((npix * a.ci + 255) / 256, 4 * 1184);
     k_bwd_data_reduce<__nv_bfloat16><<<rb, 256, 0, n->st>>>(a, ks, n->bd_part);
@@ -202,14 +232,19 @@ static_assert(net_layer(NET_LAYERS - 1).ci == 16 && net_layer(NET_LAYERS - 1).co
                   !net_layer(NET_LAYERS - 1).relu && !net_layer(NET_LAYERS - 1).up,
               "last-layer kernel shape");
 
-int net_infer(ptycho_net* n, int B) {
-  if (!n->wt_valid) {
-    for (int l = 0; l < NET_LAYERS; ++l) {
-      const NetLayer L = net_layer(l);
-      k_perm_weights<<<256, 256, 0, n->st>>>(n->wb + n->wb_off[l], n->wt + n->wb_off[l], L.co, L.ci);
-    }
-    n->wt_valid = true;
+// The tap-major weight copy, rebuilt from wb after the weights were set from
+// the host (AdamW keeps it current afterwards).
+void net_refresh_wt(ptycho_net* n) {
+  if (n->wt_valid) return;
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const NetLayer L = net_layer(l);
+    k_perm_weights<<<256, 256, 0, n->st>>>(n->wb + n->wb_off[l], n->wt + n->wb_off[l], L.co, L.ci);
   }
+  n->wt_valid = true;
+}
+
+int net_infer(ptycho_net* n, int B) {
+  net_refresh_wt(n);
   for (int l = 0; l < NET_LAYERS; ++l) {
     const NetLayer L = net_layer(l);
     ConvArgs a = conv_args(n, l, B);
@@ -236,9 +271,11 @@ int net_infer(ptycho_net* n, int B) {
 }
 
 int net_forward_tc(ptycho_net* n, int B) {
+  net_refresh_wt(n);
   for (int l = 0; l < NET_LAYERS; ++l) {
     const NetLayer L = net_layer(l);
     ConvArgs a = conv_args(n, l, B);
+    if (L.ci >= 8) a.w = n->wt + n->wb_off[l];  // the NCHW gather takes tap-major k from 8 channels on
     const bool last = l == NET_LAYERS - 1;
     a.out = last ? (void*)n->out : n->act[l];
     const int np = L.co <= 16 ? 16 : L.co;
@@ -285,8 +322,11 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
       else k_conv_bwd_w<__nv_bfloat16><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
     }
     const size_t nw = (size_t)L.co * L.ci * 9;
-    k_sum_chunks<<<(unsigned)std::min<size_t>((nw + 255) / 256, 1184), 256, 0, n->st>>>(n->wpart, nchunk, nw,
-                                                                                          n->grads + n->w_off[l]);
+    if (nchunk >= 32 && nw <= 65536)  // few weights, many chunks: a warp per weight
+      k_sum_chunks_warp<<<(unsigned)((nw + 7) / 8), 256, 0, n->st>>>(n->wpart, nchunk, nw, n->grads + n->w_off[l]);
+    else
+      k_sum_chunks<<<(unsigned)std::min<size_t>((nw + 255) / 256, 1184), 256, 0, n->st>>>(n->wpart, nchunk, nw,
+                                                                                            n->grads + n->w_off[l]);
     {  // bias gradient: about four CTAs per SM, slices of >= 4096 deltas
       const int tot = B * L.hout * L.wout;
       const int nsl = std::max(1, std::min({(4 * 148 + L.co - 1) / L.co, (tot + 4095) / 4096, NET_BPART / L.co}));
@@ -415,6 +455,7 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
   if (!r && n->tc) r = nalloc(n, &n->wt, n->n_w);
   if (!r) r = nalloc(n, &n->is_w, n->n_params);
   if (!r) r = nalloc(n, &n->wb_index, n->n_params);
+  if (!r) r = nalloc(n, &n->wt_index, n->n_params);
   const size_t asz = n->f32 ? 4 : 2;
   if (!r) r = nalloc(n, (unsigned char**)&n->x, (size_t)max_batch * NET_IN * NET_IN * asz);
   for (int l = 0; l + 1 < NET_LAYERS && !r; ++l) r = nalloc(n, (unsigned char**)&n->act[l], act_size(l, max_batch) * asz);
@@ -462,6 +503,11 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 64>, bd_tc_smem<64>());
     setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 128>, bd_tc_smem<128>());
     setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 256>, bd_tc_smem<256>());
+    setsm((const void*)k_conv_bwd_data_s2_tc<__nv_bfloat16, 16>, bd_s2_tc_smem<__nv_bfloat16, 16>());
+    setsm((const void*)k_conv_bwd_data_s2_tc<__nv_bfloat16, 32>, bd_s2_tc_smem<__nv_bfloat16, 32>());
+    setsm((const void*)k_conv_bwd_data_s2_tc<__nv_bfloat16, 64>, bd_s2_tc_smem<__nv_bfloat16, 64>());
+    setsm((const void*)k_conv_bwd_data_s2_tc<__nv_bfloat16, 128>, bd_s2_tc_smem<__nv_bfloat16, 128>());
+    setsm((const void*)k_conv_bwd_data_s2_tc<__nv_bfloat16, 256>, bd_s2_tc_smem<__nv_bfloat16, 256>());
     if (!r && e2 != cudaSuccess) r = nfail(n, PTYCHO_ERR_CUDA, "tensor-core kernel setup: %s", cudaGetErrorString(e2));
   }
   if (r) {
@@ -472,7 +518,7 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
   // He-normal weights (std = sqrt(2 / (9 ci))), zero biases, from SplitMix64(seed)
   std::vector<float> p(n->n_params, 0.f);
   std::vector<unsigned char> isw(n->n_params, 0);
-  std::vector<int> idx(n->n_params, 0);
+  std::vector<int> idx(n->n_params, 0), tidx(n->n_params, 0);
   uint64_t s = seed;
   for (int l = 0; l < NET_LAYERS; ++l) {
     const NetLayer L = net_layer(l);
@@ -482,10 +528,14 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
       p[n->w_off[l] + i] = (float)(sd * net_normal(s));
       isw[n->w_off[l] + i] = 1;
       idx[n->w_off[l] + i] = (int)(n->wb_off[l] + i);
+      // i = (o ci + c) 9 + t  ->  tap-major o 9 ci + t ci + c
+      const long long o = i / (9LL * L.ci), c = (i / 9) % L.ci, t = i % 9;
+      tidx[n->w_off[l] + i] = (int)(n->wb_off[l] + (o * 9 + t) * L.ci + c);
     }
   }
   cudaError_t e = cudaMemcpy(n->is_w, isw.data(), isw.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(n->wb_index, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(n->wt_index, tidx.data(), tidx.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, n->n_params * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, n->n_params * sizeof(float));
   int rc = e == cudaSuccess ? net_upload_params(n, p.data()) : PTYCHO_ERR_CUDA;
@@ -562,6 +612,10 @@ int ptycho_net_train_step(ptycho_net* n, const float* intensities, const float* 
   a.wb = n->wb;
   a.is_w = n->is_w;
   a.wb_index = n->wb_index;
+  // the tap-major copy follows each step once it is valid (every weight is
+  // updated), so the training forward needs no separate permutation
+  a.wt = n->wt_valid ? n->wt : nullptr;
+  a.wt_index = n->wt_index;
   a.n = (size_t)n->n_params;
   a.lr = lr;
   a.b1 = 0.9f;
@@ -571,7 +625,6 @@ int ptycho_net_train_step(ptycho_net* n, const float* intensities, const float* 
   a.c1 = (float)(1.0 - std::pow(0.9, (double)n->adam_t));
   a.c2 = (float)(1.0 - std::pow(0.999, (double)n->adam_t));
   k_adam<<<1184, 256, 0, n->st>>>(a);
-  n->wt_valid = false;
   return net_check(n, "adam");
 }
 
@@ -581,7 +634,7 @@ void ptycho_net_destroy(ptycho_net* n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
   else cudaDeviceSynchronize();
-  void* bufs[] = {n->tc_part, n->bd_part, n->bpart, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->wt,       n->is_w,     n->wb_index,
+  void* bufs[] = {n->tc_part, n->bd_part, n->bpart, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->wt,       n->is_w,     n->wb_index, n->wt_index,
                   n->x,      n->out,   n->wpart, n->lpart, n->delta[0], n->delta[1]};
   for (void* b : bufs)
     if (b) cudaFree(b);

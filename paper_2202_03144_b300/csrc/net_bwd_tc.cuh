@@ -2,19 +2,26 @@
 // operands, FP32 accumulation in tensor memory), the transposes of the
 // forward implicit GEMM (k_conv_fwd_tc):
 //
-//   weight gradient  dW[co][k] = sum_p dY[p][co] X[p][k],   k = ci * 9 + tap,
+//   weight gradient  dW[co][ci, tap] = sum_p dY[p][co] X[p][ci, tap],
 //                    p over the output pixels of the batch: M = output
-//                    channels, N = a tile of 144 (16 input channels x 9
-//                    taps), K = pixels in chunks of 64; the pixel range is
-//                    split over CTAs and the FP32 partial tiles are summed in
-//                    order afterwards (k_sum_chunks: deterministic);
-//   data gradient    dX[q][ci] = sum_k G[q][k] Wt[ci][k],     k = co * 9 + tap,
+//                    channels, N = a tile of 144 = 9 taps x 16 input channels
+//                    (column n = tap * 16 + channel), K = pixels in chunks of
+//                    64; the pixel range is split over CTAs and the FP32
+//                    partial tiles are summed in order afterwards
+//                    (k_sum_chunks: deterministic);
+//   data gradient    dX[q][ci] = sum_k G[q][k] Wt[ci][k],  k = tap * co + c,
 //                    q over the input pixels: G gathers the output deltas
 //                    that read pixel q through tap (zero-dilated for stride
 //                    2; the two virtual rows / columns of the nearest x2
-//                    upsampling summed), Wt[ci][k] = W[co][ci][tap]; the
+//                    upsampling summed), Wt[ci][k] = W[c][ci][tap]; the
 //                    previous layer's ReLU derivative is applied in the
 //                    epilogue (or in the in-order split-K reduction).
+//
+// Tap-major order (the tap outside the channel) lets a thread stage eight
+// operand values of one tap and eight channels with one set of pixel
+// offsets, held in registers (weight gradient) or loaded once per group of
+// eight (data gradient), instead of recomputing the source coordinates for
+// every value.
 //
 // Both stage their operands through two shared-memory stages in the K-major
 // no-swizzle layout of tc.cuh (core matrices of 8 rows x 16 bytes), with the
@@ -70,8 +77,13 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
   const long long npix = (long long)a.B * hw;
   const long long nchunk = (npix + BW_KC - 1) / BW_KC;
   const long long c_begin = nchunk * blockIdx.y / nsplit, c_end = nchunk * (blockIdx.y + 1) / nsplit;
-  // rows past the output channels / past ci * 9 stay zero: written once
-  const int rows_a = min(128, a.co - co0), rows_b = min(BW_NT, KW - k0);
+  // rows past the output channels / past the input channels stay zero:
+  // written once
+  const int rows_a = min(128, a.co - co0);
+  // B rows n = tap * 16 + cl: this thread stages channel ci0 + cl (the same
+  // for every chunk) for all nine taps, pixel group tid % 8
+  const int ci0 = k0 / 9, cl = tid >> 3;
+  const int ncl = min(16, a.ci - ci0);  // input channels of this tile
   for (int i = tid; i < (int)(2 * (ABYTES + BBYTES) / 16); i += 128)
     reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
@@ -120,39 +132,74 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
       }
       *reinterpret_cast<uint4*>(As + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
     }
-    // B: im2col rows (ci, tap) x 64 pixels, the forward's gather; this
-    // thread's 8 pixel coordinates once per chunk (wout >= 4: at most one
-    // row change inside the group)
-    const TA* img = in + (size_t)n * a.ci * a.hin * a.win;
-    int py[8], px[8];
-    {
-      int y = yx0 / a.wout, x = yx0 - y * a.wout;
+    // B: im2col rows (tap, channel) x 64 pixels, the forward's gather.  This
+    // thread's 8 pixels' source rows (as plane offsets) and columns for the
+    // three vertical and three horizontal taps, once per chunk (wout >= 4:
+    // at most one row change inside the group); -1 outside the input.
+    if (ncl == 16) {
+      const TA* plane = in + ((size_t)n * a.ci + ci0 + cl) * a.hin * a.win;
+      int roff[3][8], sx[3][8];
+      {
+        int y = yx0 / a.wout, x = yx0 - y * a.wout;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        py[e] = y;
-        px[e] = x;
-        if (++x == a.wout) {
-          x = 0;
-          ++y;
+        for (int e = 0; e < 8; ++e) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const int sy = pin ? net_src(y, d, a.stride, a.up, a.hin) : -1;
+            roff[d][e] = sy >= 0 ? sy * a.win : -1;
+            sx[d][e] = pin ? net_src(x, d, a.stride, a.up, a.win) : -1;
+          }
+          if (++x == a.wout) {
+            x = 0;
+            ++y;
+          }
         }
       }
-    }
-    for (int u = tid; u < rows_b * (BW_KC / 8); u += 128) {
-      const int r = u >> 3, g = u & 7;
-      const int k = k0 + r;
-      const int ci = k / 9, t = k - 9 * (k / 9), ty = t / 3, tx = t - 3 * (t / 3);
-      const TA* plane = img + (size_t)ci * a.hin * a.win;
-      float v[8];
+      const int g = tid & 7;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float x = 0.f;
-        if (pin) {
-          const int sy = net_src(py[e], ty, a.stride, a.up, a.hin), sx = net_src(px[e], tx, a.stride, a.up, a.win);
-          if (sy >= 0 && sx >= 0) x = ldact(plane, (size_t)sy * a.win + sx);
+      for (int t = 0; t < 9; ++t) {
+        const int r = t * 16 + cl;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int ro = roff[t / 3][e], cx = sx[t % 3][e];
+          v[e] = (ro >= 0 && cx >= 0) ? ldact(plane, (size_t)(ro + cx)) : 0.f;
         }
-        v[e] = x;
+        *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
       }
-      *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
+    } else {
+      // fewer channels (the one-channel first layer): the (tap, channel,
+      // pixel group) units spread over all threads, source coordinates per
+      // value; the pixel group is tid % 8 for every unit of the thread
+      int py[8], px[8];
+      {
+        int y = yx0 / a.wout, x = yx0 - y * a.wout;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          py[e] = y;
+          px[e] = x;
+          if (++x == a.wout) {
+            x = 0;
+            ++y;
+          }
+        }
+      }
+      for (int u = tid; u < 9 * ncl * 8; u += 128) {
+        const int g = u & 7, c2 = (u >> 3) % ncl, t = (u >> 3) / ncl, ty = t / 3, tx = t - 3 * ty;
+        const TA* plane = in + ((size_t)n * a.ci + ci0 + c2) * a.hin * a.win;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          float x = 0.f;
+          if (pin) {
+            const int sy = net_src(py[e], ty, a.stride, a.up, a.hin), sx = net_src(px[e], tx, a.stride, a.up, a.win);
+            if (sy >= 0 && sx >= 0) x = ldact(plane, (size_t)sy * a.win + sx);
+          }
+          v[e] = x;
+        }
+        const int r = t * 16 + c2;
+        *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc::fence_before();
@@ -182,10 +229,12 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
     float v[16];
     tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
     if (co < a.co) {
+      // column c0 + j = tap * 16 + channel: a 16-column slice is one tap
+      const int t = c0 >> 4;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int k = k0 + c0 + j;
-        if (k < KW) a.wpart[((size_t)blockIdx.y * a.co + co) * KW + k] = any ? v[j] : 0.f;
+        const int ci = ci0 + j;
+        if (ci < a.ci) a.wpart[((size_t)blockIdx.y * a.co + co) * KW + ci * 9 + t] = any ? v[j] : 0.f;
       }
     }
   }
@@ -258,6 +307,7 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data_tc(ConvArgs a, int ksplit
   tc::fence_after();
   const uint32_t tbase = *tslot;
   const int K = a.co * 9;
+  const bool co8 = (a.co & 7) == 0;
   const int nchunk = (K + BD_KC - 1) / BD_KC;
   const int c_begin = (int)(((long long)nchunk * blockIdx.y) / ksplit);
   const int c_end = (int)(((long long)nchunk * (blockIdx.y + 1)) / ksplit);
@@ -277,40 +327,66 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data_tc(ConvArgs a, int ksplit
     unsigned char* As = stage[s];
     unsigned char* Bs = stage[s] + ABYTES;
     const int kb = c * BD_KC;
-    // A: this thread's pixel (row tid), 64 values of k = co * 9 + tap
+    // A: this thread's pixel (row tid), 64 values of k = tap * co + c.
+    // With co a multiple of 8 a group of eight k is one tap and eight
+    // channels: its delta offsets are read once and the eight loads differ
+    // by whole planes.
 #pragma unroll 1
     for (int g = 0; g < BD_KC / 8; ++g) {
       float v[8];
+      const int kg = kb + 8 * g;
+      if (co8) {
+        const int t = kg / a.co, c = kg - t * a.co;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = kb + 8 * g + e;
-        float x = 0.f;
-        if (k < K) {
-          const int co = k / 9, t = k - 9 * (k / 9);
-          const float* pl = dy + (size_t)co * hwo;
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        if (kg < K) {
+          const float* pl = dy + (size_t)c * hwo;
           const int o0 = offs[(t * 4) * 128 + tid];
-          if (o0 >= 0) x = pl[o0];
+          if (o0 >= 0)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = pl[(size_t)e * hwo + o0];
           if (a.up) {  // the other virtual rows / columns of the upsampling
 #pragma unroll
             for (int h = 1; h < 4; ++h) {
               const int o = offs[(t * 4 + h) * 128 + tid];
-              if (o >= 0) x += pl[o];
+              if (o >= 0)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] += pl[(size_t)e * hwo + o];
             }
           }
         }
-        v[e] = x;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = kg + e;
+          float x = 0.f;
+          if (k < K) {
+            const int t = k / a.co, c = k - t * a.co;
+            const float* pl = dy + (size_t)c * hwo;
+            const int o0 = offs[(t * 4) * 128 + tid];
+            if (o0 >= 0) x = pl[o0];
+            if (a.up) {
+#pragma unroll
+              for (int h = 1; h < 4; ++h) {
+                const int o = offs[(t * 4 + h) * 128 + tid];
+                if (o >= 0) x += pl[o];
+              }
+            }
+          }
+          v[e] = x;
+        }
       }
       *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = pack8_bf16(v);
     }
-    // B: Wt rows (input channels) x 64 values of k: W[co][ci][tap]
+    // B: Wt rows (input channels) x 64 values of k: W[c][ci][tap]
     for (int u = tid; u < NP * (BD_KC / 8); u += 128) {
       const int r = u / (BD_KC / 8), g = u % (BD_KC / 8);
       __align__(16) __nv_bfloat16 w8[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int k = kb + 8 * g + e;
-        w8[e] = (r < a.ci && k < K) ? a.w[((size_t)(k / 9) * a.ci + r) * 9 + (k - 9 * (k / 9))]
-                                    : __float2bfloat16_rn(0.f);
+        const int t = k / a.co, c = k - t * a.co;
+        w8[e] = (r < a.ci && k < K) ? a.w[((size_t)c * a.ci + r) * 9 + t] : __float2bfloat16_rn(0.f);
       }
       *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = *reinterpret_cast<const uint4*>(w8);
     }
@@ -352,6 +428,162 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data_tc(ConvArgs a, int ksplit
       }
       const size_t o = ((size_t)n * a.ci + ci) * hwi + iyx;
       float rr = r;
+      if (a.mask && !(ldact(reinterpret_cast<const TA*>(a.mask), o) > 0.f)) rr = 0.f;
+      a.din[o] = rr;
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tbase, NCOLS);
+}
+
+// Data gradient of a stride-2 layer, by input-pixel parity class.  An input
+// pixel (iy, ix) is read by tap (dy, dx) of output (oy, ox) only where
+// iy + 1 - dy = 2 oy and ix + 1 - dx = 2 ox: the even rows through dy = 1,
+// the odd rows through dy = 0 and 2 (likewise for columns).  So the pixels
+// of one parity class (iy % 2, ix % 2) take 1, 2, 2 or 4 taps, and a tile of
+// 128 pixels of one class runs a GEMM over K = co x its taps with no zero
+// rows: k = t * co + c, t the index of the tap in the class's list.
+// grid = (4 classes x tiles of 128 class pixels, K splits).  The class's
+// pixels are (iy, ix) = (2 my + py, 2 mx + px), my < hin / 2, mx < win / 2.
+template <typename TA, int NP>
+__host__ __device__ constexpr size_t bd_s2_tc_smem() {
+  return 2 * ((size_t)128 * BD_KC * 2 + (size_t)NP * BD_KC * 2) + 64 + 4 * 128 * 4;
+}
+
+template <typename TA, int NP>
+__global__ void __launch_bounds__(128) k_conv_bwd_data_s2_tc(ConvArgs a, int ksplit, float* part, int* err_flag) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr size_t ABYTES = (size_t)128 * BD_KC * 2, BBYTES = (size_t)NP * BD_KC * 2;
+  unsigned char* stage[2] = {smem_raw, smem_raw + ABYTES + BBYTES};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (ABYTES + BBYTES));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  int* offs = reinterpret_cast<int*>(smem_raw + 2 * (ABYTES + BBYTES) + 64);  // [4][128]
+  constexpr uint32_t LBO = 128, SBO = (BD_KC / 8) * 128;
+  constexpr uint32_t NCOLS = NP < 32 ? 32 : NP;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int hwi = a.hin * a.win, hwo = a.hout * a.wout;
+  const int hh = a.hin >> 1, wh = a.win >> 1, pc = hh * wh;
+  const long long ncls = (long long)a.B * pc;             // pixels per class
+  const long long tiles = (ncls + 127) / 128;
+  const int cls = (int)(blockIdx.x / tiles);
+  const int py = cls >> 1, px = cls & 1;
+  const long long qc = (long long)(blockIdx.x % tiles) * 128 + tid;
+  const bool valid = qc < ncls;
+  const int n = valid ? (int)(qc / pc) : 0;
+  const int r = valid ? (int)(qc - (long long)n * pc) : 0;
+  const int iy = 2 * (r / wh) + py, ix = 2 * (r % wh) + px;
+  const long long q = (long long)n * hwi + (long long)iy * a.win + ix;  // pixel index in the batch
+  // the class's taps: rows dy = 1 (even iy) or 0, 2 (odd); columns likewise
+  const int nty = py ? 2 : 1, ntx = px ? 2 : 1, ntap = nty * ntx;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    int o = -1;
+    if (t < ntap && valid) {
+      const int dy = py ? 2 * (t / ntx) : 1, dx = px ? 2 * (t % ntx) : 1;
+      const int oy = (iy + 1 - dy) >> 1, ox = (ix + 1 - dx) >> 1;  // exact: the parity matches
+      if (iy + 1 - dy >= 0 && oy < a.hout && ix + 1 - dx >= 0 && ox < a.wout) o = oy * a.wout + ox;
+    }
+    offs[t * 128 + tid] = o;
+  }
+  if (tid == 0) {
+    tc::mbar_init1(&bar[0]);
+    tc::mbar_init1(&bar[1]);
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, NCOLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  const int K = a.co * ntap;  // co is a multiple of 8: a group of eight k is one tap
+  const int nchunk = (K + BD_KC - 1) / BD_KC;
+  const int c_begin = (int)(((long long)nchunk * blockIdx.y) / ksplit);
+  const int c_end = (int)(((long long)nchunk * (blockIdx.y + 1)) / ksplit);
+  const float* dy_n = a.dout + (size_t)n * a.co * hwo;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+  uint32_t ph[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  for (int c = c_begin; c < c_end; ++c) {
+    const int s = (c - c_begin) & 1;
+    if (pending[s]) {
+      if (!tc::mbar_wait(&bar[s], ph[s])) ok = false;
+      ph[s] ^= 1u;
+      pending[s] = false;
+      tc::fence_after();
+    }
+    unsigned char* As = stage[s];
+    unsigned char* Bs = stage[s] + ABYTES;
+    const int kb = c * BD_KC;
+    // A: this thread's pixel, 64 values of k: eight groups of one tap and
+    // eight channels, all loads of the chunk in flight together
+#pragma unroll
+    for (int g = 0; g < BD_KC / 8; ++g) {
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = 0.f;
+      const int kg = kb + 8 * g;
+      if (kg < K) {
+        const int t = kg / a.co, ch = kg - t * a.co;
+        const int o = offs[t * 128 + tid];
+        if (o >= 0) {
+          const float* pl = dy_n + (size_t)ch * hwo + o;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = pl[(size_t)e * hwo];
+        }
+      }
+      *reinterpret_cast<uint4*>(As + (tid >> 3) * SBO + g * LBO + (tid & 7) * 16) = pack8_bf16(v);
+    }
+    // B: Wt rows (input channels) x 64 values of k: W[c][ci][tap of t]
+    for (int u = tid; u < NP * (BD_KC / 8); u += 128) {
+      const int rr = u / (BD_KC / 8), g = u % (BD_KC / 8);
+      __align__(16) __nv_bfloat16 w8[8];
+      const int kg = kb + 8 * g;
+      const int t = kg / a.co, ch = kg - t * a.co;
+      const int tap = (py ? 2 * (t / ntx) : 1) * 3 + (px ? 2 * (t % ntx) : 1);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        w8[e] = (rr < a.ci && kg < K) ? a.w[((size_t)(ch + e) * a.ci + rr) * 9 + tap] : __float2bfloat16_rn(0.f);
+      *reinterpret_cast<uint4*>(Bs + (rr >> 3) * SBO + g * LBO + (rr & 7) * 16) = *reinterpret_cast<const uint4*>(w8);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < BD_KC / 16; ++kk) {
+        const uint64_t ad = tc::smem_desc(As + kk * 2 * LBO, LBO, SBO);
+        const uint64_t bd = tc::smem_desc(Bs + kk * 2 * LBO, LBO, SBO);
+        tc::mma_bf16(tbase, ad, bd, idesc, (c > c_begin || kk > 0) ? 1u : 0u);
+      }
+      tc::commit(&bar[s]);
+    }
+    pending[s] = true;
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    if (pending[s] && !tc::mbar_wait(&bar[s], ph[s])) ok = false;
+  tc::fence_after();
+  if (!ok && tid == 0) atomicExch(err_flag, 1);
+  const bool any = c_end > c_begin;
+  const long long npix = (long long)a.B * hwi;
+#pragma unroll 1
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (!valid) continue;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int ci = c0 + j;
+      if (ci >= a.ci) continue;
+      const float rv = any ? v[j] : 0.f;
+      if (ksplit > 1) {
+        part[((size_t)blockIdx.y * a.ci + ci) * npix + q] = rv;
+        continue;
+      }
+      const size_t o = ((size_t)n * a.ci + ci) * hwi + (size_t)iy * a.win + ix;
+      float rr = rv;
       if (a.mask && !(ldact(reinterpret_cast<const TA*>(a.mask), o) > 0.f)) rr = 0.f;
       a.din[o] = rr;
     }
