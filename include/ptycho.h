@@ -65,7 +65,7 @@ enum { PTYCHO_I_F32 = 0, PTYCHO_I_F16 = 1, PTYCHO_I_BF16 = 2 };
 enum { PTYCHO_R_F32 = 0, PTYCHO_R_F16 = 1 };
 
 /* Transform engine of the Fourier passes (ptycho_params.fft_engine). */
-enum { PTYCHO_FFT_REGISTER = 0, PTYCHO_DFT_TENSOR_BF16X3 = 1 };
+enum { PTYCHO_FFT_AUTO = -1, PTYCHO_FFT_REGISTER = 0, PTYCHO_DFT_TENSOR_BF16X3 = 1 };
 
 /* LSQML likelihood (ptycho_params.likelihood). */
 enum { PTYCHO_LIK_AMPLITUDE = 0, PTYCHO_LIK_POISSON = 1 };
@@ -170,7 +170,10 @@ typedef struct {
                        and FP32 accumulation -- about 17 significant bits
                        per transform stage instead of 24.  Compiled for M = 64,
                        K = 1 (else PTYCHO_ERR_UNSUPPORTED).  ePIE's sweep
-                       keeps its own kernels.                                */
+                       keeps its own kernels.
+                       PTYCHO_FFT_AUTO: the faster engine for (M, K) as
+                       ptycho_autotune_engine measures it (with cluster = -1
+                       also its cluster size).                               */
   int residual_store; /* LSQML's residuals chi between the Fourier pass that
                        writes them and the five passes that read them (object
                        and probe directions, step sizes, object and probe
@@ -331,6 +334,23 @@ long long ptycho_launch_count(const ptycho_ctx* ctx);
  * ptycho_params.mem_limit caps); -1 for ctx = NULL. */
 long long ptycho_memory_used(const ptycho_ctx* ctx);
 
+/* Logging and feedback (Sec. 3.4: progress and error reports while a
+ * reconstruction runs).  The sink is called synchronously, on the calling
+ * thread, from inside the library call that produces the message:
+ *   PTYCHO_LOG_ERROR  a call on this context failed; msg is the text that
+ *                     ptycho_last_error() returns for it;
+ *   PTYCHO_LOG_INFO   a progress report of ptycho_iterate:
+ *                     "<alg> iteration <t>: E = <Fourier error>", t counting
+ *                     completed iterations of the context.
+ * error_every > 0: ptycho_iterate reports after every error_every-th
+ * iteration (and after its last one), each report one extra Fourier-error
+ * pass and a host synchronisation -- the iterates are unchanged, bit for bit;
+ * 0: errors only.  fn = NULL removes the sink.  The message is valid during
+ * the call only.  Errors: PTYCHO_ERR_ARG (ctx NULL, error_every < 0). */
+typedef void (*ptycho_log_fn)(void* user, int level, const char* msg);
+enum { PTYCHO_LOG_ERROR = 0, PTYCHO_LOG_INFO = 1 };
+int ptycho_set_log(ptycho_ctx* ctx, ptycho_log_fn fn, void* user, int error_every);
+
 /* Per-kernel timing.  When enabled, every launch is bracketed by CUDA events
  * on the context stream and its duration is accumulated per kernel family. */
 typedef struct {
@@ -414,6 +434,16 @@ void ptycho_batch_destroy(ptycho_batch* b);
  * *ms_per_position (either may be NULL).  Allocates and frees temporary
  * contexts; synchronises the device work it issues. */
 int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position);
+
+/* FFT-variant autotuner: ptycho_autotune over the transform engines too --
+ * the register FFT at its best cluster size and, where it is compiled
+ * (M = 64, K = 1), the tensor-core DFT, timed the same way -- writing the
+ * faster engine (PTYCHO_FFT_REGISTER or PTYCHO_DFT_TENSOR_BF16X3), the
+ * register FFT's best cluster size and the winner's time per scan position
+ * (any output may be NULL).  Cached per (M, K) like ptycho_autotune.
+ * Errors: PTYCHO_ERR_ARG (M < 2, K < 1), PTYCHO_ERR_UNSUPPORTED (nothing
+ * compiled for (M, K)). */
+int ptycho_autotune_engine(int M, int K, int* best_engine, int* best_cluster, double* ms_per_position);
 
 /* ---- Learned warm start ----------------------------------------------------
  * A convolutional encoder-decoder (6 levels, 128^2 -> 4^2 -> 64^2, ~1.96M

@@ -20,7 +20,7 @@ ALGS = {"epie": EPIE, "dm": DM, "lsqml": LSQML}
 I_F32, I_F16, I_BF16 = 0, 1, 2
 ISTORE = {"f32": I_F32, "f16": I_F16, "bf16": I_BF16}
 LIKELIHOOD = {"amplitude": 0, "poisson": 1}  # PTYCHO_LIK_AMPLITUDE, PTYCHO_LIK_POISSON
-FFT_ENGINE = {"register": 0, "tensor_bf16x3": 1}  # PTYCHO_FFT_REGISTER, PTYCHO_DFT_TENSOR_BF16X3
+FFT_ENGINE = {"auto": -1, "register": 0, "tensor_bf16x3": 1}  # PTYCHO_FFT_AUTO, _REGISTER, PTYCHO_DFT_TENSOR_BF16X3
 RESIDUAL_STORE = {"f32": 0, "f16": 1}  # PTYCHO_R_F32, PTYCHO_R_F16
 
 ERRORS = {
@@ -62,6 +62,9 @@ class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
+LOG_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_char_p)  # ptycho_log_fn
+
+
 _lib = None
 
 
@@ -97,6 +100,7 @@ def lib() -> C.CDLL:
             "ptycho_fourier_error_noalloc": (i, [f, i, i, f, i, i, f, i, f, C.POINTER(d), vp]),
             "ptycho_set_likelihood": (i, [vp, i]),
             "ptycho_set_wait_limit": (i, [vp, C.c_longlong]),
+            "ptycho_set_log": (i, [vp, LOG_FN, vp, i]),
             "ptycho_fp32_fma_peak": (i, [C.POINTER(d), C.POINTER(d), C.POINTER(i), vp]),
             "ptycho_orthogonalize_probe": (i, [vp]),
             "ptycho_set_iteration": (i, [vp, C.c_longlong]),
@@ -117,6 +121,7 @@ def lib() -> C.CDLL:
             "ptycho_batch_last_error": (C.c_char_p, [vp]),
             "ptycho_batch_destroy": (None, [vp]),
             "ptycho_autotune": (i, [i, i, C.POINTER(i), C.POINTER(d)]),
+            "ptycho_autotune_engine": (i, [i, i, C.POINTER(i), C.POINTER(i), C.POINTER(d)]),
             "ptycho_net_create": (i, [C.POINTER(vp), C.c_ulonglong, i, i, vp]),
             "ptycho_net_num_params": (C.c_longlong, [vp]),
             "ptycho_net_get_params": (i, [vp, f]),
@@ -410,6 +415,17 @@ class Reconstruction:
         v = LIKELIHOOD[likelihood] if isinstance(likelihood, str) else int(likelihood)
         _check(self.ctx, lib().ptycho_set_likelihood(self.ctx, v))
 
+    def set_log(self, fn=None, error_every=0):
+        """Log sink fn(level, message) (level 0 error, 1 progress), called
+        from inside the library calls; error_every > 0 adds a progress report
+        with the Fourier error every error_every iterations.  fn=None removes it."""
+        if fn is None:
+            self._log_cb = None
+            _check(self.ctx, lib().ptycho_set_log(self.ctx, LOG_FN(), None, int(error_every)))
+            return
+        self._log_cb = LOG_FN(lambda user, level, msg: fn(int(level), msg.decode()))  # kept alive with the context
+        _check(self.ctx, lib().ptycho_set_log(self.ctx, self._log_cb, None, int(error_every)))
+
     def set_wait_limit(self, polls):
         """Polls of a cluster-transpose wait in the Fourier kernels before it
         gives up (default 1 << 20; 0 gives up at once)."""
@@ -506,6 +522,15 @@ def autotune(M: int, K: int) -> tuple[int, float]:
     ms = C.c_double()
     _check(None, lib().ptycho_autotune(M, K, C.byref(best), C.byref(ms)))
     return best.value, ms.value
+
+
+def autotune_engine(M: int, K: int) -> tuple[str, int, float]:
+    """ptycho_autotune_engine: (faster transform engine, the register FFT's
+    best cluster size, ms per scan position of the winner) for (M, K)."""
+    eng, best, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(None, lib().ptycho_autotune_engine(M, K, C.byref(eng), C.byref(best), C.byref(ms)))
+    name = {v: k for k, v in FFT_ENGINE.items()}[eng.value]
+    return name, best.value, ms.value
 
 
 class _Member(Reconstruction):

@@ -149,6 +149,7 @@ int batch_capture(ptycho_batch* b, int alg, const std::vector<char>& upd) {
 
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, std::pair<int, double>> g_tune_cache;
+std::map<std::pair<int, int>, std::pair<int, double>> g_engine_cache;  // (engine, ms per position)
 
 // k_fill_amp: a deterministic pseudo-random amplitude pattern (tuning data)
 __global__ void k_fill_amp(float* a, size_t n) {
@@ -232,6 +233,81 @@ int ptycho_autotune(int M, int K, int* best_cluster, double* ms_per_position) {
   }
   if (best_cluster) *best_cluster = best;
   if (ms_per_position) *ms_per_position = best_ms / (double)J;
+  return PTYCHO_OK;
+}
+
+int ptycho_autotune_engine(int M, int K, int* best_engine, int* best_cluster, double* ms_per_position) {
+  if (M < 2 || K < 1) return fail(nullptr, PTYCHO_ERR_ARG, "bad sizes M=%d K=%d", M, K);
+  int C = 0;
+  double ms_reg = 0.0;
+  if (int r = ptycho_autotune(M, K, &C, &ms_reg)) return r;
+  int eng = PTYCHO_FFT_REGISTER;
+  double ms = ms_reg;
+  if (M == 64 && K == 1) {
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_engine_cache.find({M, K});
+      if (it != g_engine_cache.end()) {
+        eng = it->second.first;
+        ms = it->second.second;
+        cached = true;
+      }
+    }
+    if (!cached) {
+      // the tensor-core DFT on the same synthetic residual pass
+      const long long J = 4096;
+      std::vector<float> pos(2 * J);
+      for (long long j = 0; j < J; ++j) {
+        pos[2 * j] = (float)((j * 37) % 65);
+        pos[2 * j + 1] = (float)((j * 53) % 65);
+      }
+      ptycho_params p;
+      ptycho_default_params(&p);
+      p.M = M;
+      p.K = K;
+      p.J = (int)J;
+      p.obj_ny = M + 64;
+      p.obj_nx = M + 64;
+      p.cluster = C;
+      p.fft_engine = PTYCHO_DFT_TENSOR_BF16X3;
+      ptycho_ctx* ctx = nullptr;
+      double ms_tc = 1e30;
+      if (ptycho_create(&ctx, &p) == PTYCHO_OK) {
+        int rc = set_positions_impl(ctx, pos.data());
+        if (!rc) {
+          k_fill_amp<<<1184, 256, 0, ctx->st>>>((float*)ctx->amp, (size_t)J * M * M);
+          ctx->have_data = true;
+          rc = ensure_work_buffers(ctx);
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int rep = 0; rep < 4 && !rc; ++rep) {
+          cudaEventRecord(e0, ctx->st);
+          rc = launch_fourier(ctx, FM_CHI, ctx->X, nullptr, 0, (int)J, "fourier_chi");
+          cudaEventRecord(e1, ctx->st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) rc = PTYCHO_ERR_CUDA;
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep > 0 && t / (double)J < ms_tc) ms_tc = t / (double)J;  // first launch is the warm-up
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ptycho_destroy(ctx);
+        if (rc) ms_tc = 1e30;
+      }
+      if (ms_tc < ms_reg) {
+        eng = PTYCHO_DFT_TENSOR_BF16X3;
+        ms = ms_tc;
+      }
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_engine_cache[{M, K}] = {eng, ms};
+    }
+  }
+  if (best_engine) *best_engine = eng;
+  if (best_cluster) *best_cluster = C;
+  if (ms_per_position) *ms_per_position = ms;
   return PTYCHO_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -410,6 +411,10 @@ struct ptycho_ctx {
   long long t = 0;
   long long launches = 0;
   std::string err;
+  // logging (ptycho_set_log)
+  ptycho_log_fn log_fn = nullptr;
+  void* log_user = nullptr;
+  int log_every = 0;
   // profiling
   struct Pending {
     int fam;
@@ -433,10 +438,20 @@ int fail(ptycho_ctx* c, int code, const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(b, sizeof b, fmt, ap);
   va_end(ap);
-  if (c) c->err = b;
-  else g_create_error = b;
+  if (c) {
+    c->err = b;
+    if (c->log_fn) c->log_fn(c->log_user, PTYCHO_LOG_ERROR, b);
+  } else {
+    g_create_error = b;
+  }
   return code;
 }
+
+// NVTX range (host timeline of a profiler; no-op without one attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define CK(call)                                                                              \
   do {                                                                                        \
@@ -524,6 +539,7 @@ int family(ptycho_ctx* ctx, const char* name) {
 // checks the launch error.
 template <class Fn>
 int launch(ptycho_ctx* ctx, const char* name, double bytes, Fn&& fn) {
+  NvtxRange range(name);
   ptycho_ctx::Pending rec{};
   if (ctx->prof) {
     rec.fam = family(ctx, name);
@@ -1719,7 +1735,24 @@ void ptycho_default_params(ptycho_params* p) {
   p->block_positions = 0;
 }
 
+static int create_impl(ptycho_ctx** out, const ptycho_params* p);
+
 int ptycho_create(ptycho_ctx** out, const ptycho_params* p) {
+  if (p && p->fft_engine == PTYCHO_FFT_AUTO) {  // the measured faster engine for (M, K)
+    ptycho_params q = *p;
+    int eng = PTYCHO_FFT_REGISTER, C = 0;
+    if (q.M >= 2 && q.K >= 1 && ptycho_autotune_engine(q.M, q.K, &eng, &C, nullptr) == PTYCHO_OK) {
+      q.fft_engine = eng;
+      if (q.cluster < 0) q.cluster = C;
+    } else {
+      q.fft_engine = PTYCHO_FFT_REGISTER;
+    }
+    return create_impl(out, &q);
+  }
+  return create_impl(out, p);
+}
+
+static int create_impl(ptycho_ctx** out, const ptycho_params* p) {
   ptycho_ctx* ctx = nullptr;
   if (!out || !p) return fail(nullptr, PTYCHO_ERR_ARG, "NULL argument");
   *out = nullptr;
@@ -2078,13 +2111,41 @@ int ptycho_iterate(ptycho_ctx* ctx, int alg, int n_iter) {
   if (!ctx) return PTYCHO_ERR_ARG;
   if (n_iter < 0) return fail(ctx, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
   if (!ctx->have_data) return fail(ctx, PTYCHO_ERR_STATE, "iterate before set_data");
+  if (alg != PTYCHO_EPIE && alg != PTYCHO_DM && alg != PTYCHO_LSQML)
+    return fail(ctx, PTYCHO_ERR_ARG, "unknown algorithm %d", alg);
   if (n_iter == 0) return PTYCHO_OK;
-  switch (alg) {
-    case PTYCHO_EPIE: return run_epie(ctx, n_iter);
-    case PTYCHO_DM: return run_dm(ctx, n_iter);
-    case PTYCHO_LSQML: return run_lsqml(ctx, n_iter);
-    default: return fail(ctx, PTYCHO_ERR_ARG, "unknown algorithm %d", alg);
+  static const char* names[] = {"epie", "dm", "lsqml"};
+  const char* name = names[alg];
+  auto run = [&](int n) {
+    NvtxRange range(name);
+    return alg == PTYCHO_EPIE ? run_epie(ctx, n) : alg == PTYCHO_DM ? run_dm(ctx, n) : run_lsqml(ctx, n);
+  };
+  const int every = ctx->log_fn ? ctx->log_every : 0;
+  if (every <= 0) return run(n_iter);
+  // progress reports: n calls of iterate(1) equal one call of n, so the
+  // iterations run in pieces that end where a report is due
+  for (int done = 0; done < n_iter;) {
+    const int n = (int)std::min<long long>(n_iter - done, every - ctx->t % every);
+    if (int r = run(n)) return r;
+    done += n;
+    if (ctx->t % every == 0 || done == n_iter) {
+      double E = 0.0;
+      if (int r = ptycho_fourier_error(ctx, &E)) return r;
+      char b[128];
+      snprintf(b, sizeof b, "%s iteration %lld: E = %.9e", name, ctx->t, E);
+      ctx->log_fn(ctx->log_user, PTYCHO_LOG_INFO, b);
+    }
   }
+  return PTYCHO_OK;
+}
+
+int ptycho_set_log(ptycho_ctx* ctx, ptycho_log_fn fn, void* user, int error_every) {
+  if (!ctx) return PTYCHO_ERR_ARG;
+  if (error_every < 0) return fail(ctx, PTYCHO_ERR_ARG, "error_every=%d", error_every);
+  ctx->log_fn = fn;
+  ctx->log_user = user;
+  ctx->log_every = error_every;
+  return PTYCHO_OK;
 }
 
 int ptycho_get_object(ptycho_ctx* ctx, float* out, int on_device) {

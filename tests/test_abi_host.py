@@ -132,6 +132,9 @@ def test_error_message_is_per_thread(lib):
 def test_new_controls_reject_null(lib):
     assert lib.ptycho_set_wait_limit(None, 5) == -1
     assert lib.ptycho_fp32_fma_peak(None, None, None, None) == -1
+    assert lib.ptycho_set_log(None, api.LOG_FN(), None, 0) == -1
+    assert lib.ptycho_autotune_engine(1, 1, None, None, None) == -1
+    assert api.FFT_ENGINE["auto"] == -1 and api.default_params(fft_engine="auto").fft_engine == -1
     p = api.default_params(M=32, K=1, J=4, obj_ny=64, obj_nx=64)
     assert p.mem_limit == 0
     p2 = api.default_params(M=32, K=1, J=4, obj_ny=64, obj_nx=64, mem_limit=1 << 20)

@@ -116,3 +116,25 @@ def test_unsupported_shape_is_rejected():
     with pytest.raises(api.PtychoError) as e:
         api.Reconstruction(128, 1, 4, (200, 200), fft_engine=ENG)
     assert e.value.name == "UNSUPPORTED"
+
+
+def test_engine_autotuner_and_auto_engine():
+    """ptycho_autotune_engine times both engines where both are compiled and
+    keeps the faster; fft_engine = "auto" then builds a context with that
+    engine, whose results equal an explicit context of the same engine bit
+    for bit.  Elsewhere only the register FFT is compiled and is chosen."""
+    eng, C, ms = api.autotune_engine(64, 1)
+    assert eng in ("register", "tensor_bf16x3") and C >= 1 and ms > 0
+    assert api.autotune_engine(64, 1) == (eng, C, ms)     # cached
+    eng128, C128, _ = api.autotune_engine(128, 1)
+    assert eng128 == "register" and C128 == api.autotune(128, 1)[0]
+    c = scan(64, 1, grid=3, photons=1e5, seed=31)
+    outs = []
+    for kw in (dict(fft_engine="auto", cluster=-1), dict(fft_engine=eng, cluster=C)):
+        with api.Reconstruction(64, 1, len(c["pos"]), c["shape"], **kw) as r:
+            r.set_data(c["I"].astype(np.float32), c["pos"])
+            r.set_init(c["O0"], c["P0"])
+            r.iterate("lsqml", 2)
+            outs.append((r.get_object(), r.get_probe(), r.fourier_error()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]

@@ -144,3 +144,33 @@ def test_inference_forward_follows_parameter_updates():
         ref.predict(It, r)
         torch.cuda.synchronize()
         assert rel(o, r) < 1e-2
+
+
+@pytest.mark.parametrize("B", [64, 37], ids=["batch64", "batch37"])
+def test_tensor_core_gradients_match_cuda_cores_at_training_batches(B):
+    """The tensor-core backward (tap-major gathers, parity-class stride-2 data
+    gradients, pixel-split weight gradients summed in order) at the training
+    batch and at a ragged one, against the CUDA-core backward on identical
+    BF16 weights and frames.  The two forwards sum in different orders before
+    each BF16 rounding, so ReLU masks flip between them as between the method
+    and the oracle: the same 8e-2 per gradient tensor, 2e-2 on the loss.
+    Repeated calls agree bit for bit."""
+    torch = pytest.importorskip("torch")
+    I, t = _batch(B, 40 + B)
+    It, tt = torch.from_numpy(I).cuda(), torch.from_numpy(t).cuda()
+    res = []
+    for cc in (False, True):
+        with api.Net(seed=13, max_batch=B, cuda_cores=cc) as net:
+            L, g = net.gradients(It, tt)
+            if not cc:
+                L2, g2 = net.gradients(It, tt)
+                assert L == L2 and np.array_equal(g, g2), "tensor-core gradients not deterministic"
+            res.append((L, g))
+    (Lt, gt), (Lc, gc) = res
+    assert abs(Lt - Lc) / Lc < 2e-2
+    errs = []
+    for l, ((wo, bo), (ci, co, *_)) in enumerate(zip(orc_net.layout()[0], orc_net.LAYERS)):
+        for kind, (a, b) in (("w", (wo, wo + co * ci * 9)), ("b", (bo, bo + co))):
+            errs.append((l, kind, float(np.linalg.norm(gt[a:b] - gc[a:b]) / max(np.linalg.norm(gc[a:b]), 1e-30))))
+    print(f"batch {B}: tensor-core vs CUDA-core gradients, worst", max(errs, key=lambda e: e[2]))
+    assert all(e < 8e-2 for _, _, e in errs), errs
