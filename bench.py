@@ -285,10 +285,10 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7, group_bytes=N
         torch.cuda.synchronize()
         b.iterate("lsqml", warm)
         torch.cuda.synchronize()
-        if group_bytes is None:  # the group budget from the batch autotuner
-            tuned_bytes, _ = b.autotune("lsqml", 1)
+        if group_bytes is None:  # the schedule (group budget or lanes) from the batch autotuner
+            tuned_bytes, tuned_lanes, _ = b.autotune("lsqml", 1)
         else:
-            tuned_bytes = group_bytes
+            tuned_bytes, tuned_lanes = group_bytes, 0
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -321,10 +321,11 @@ def run_batched(api, torch, stream, n=64, iters=4, warm=2, seed=7, group_bytes=N
             "all_at_once_value": units / (ms_all / 1e3), "sequential_value": units / (ms_seq / 1e3),
             "members": n, "positions": sum(m["J"] for m in members), "iterations": iters,
             "kernels_per_graph": kpi, "autotuned_clusters": clusters, "autotuned_engines": engines,
-            "autotuned_group_mib": gb_mib,
+            "autotuned_group_mib": gb_mib, "autotuned_lanes": tuned_lanes,
             "workload": f"{n} LSQML scans, probe sizes {{64,96,128,192,256}}, 100-4000 positions (Fermat "
                         "spirals, spacing 0.15 M), Poisson 1e4-1e6 photons/frame; one CUDA graph per iteration, "
-                        f"members run in groups of at most {gb_mib:g} MiB working set"}
+                        + (f"members in {tuned_lanes} chains run side by side" if tuned_lanes else
+                           f"members run in groups of at most {gb_mib:g} MiB working set")}
 
 
 def time_to_eps(api, torch, stream, I, pos, P0s, w, n_ref=30, check=5):
@@ -570,6 +571,8 @@ def main():
     ap.add_argument("--warm-frames", type=int, default=200_000)
     ap.add_argument("--epie-only", action="store_true",
                     help="run only the ePIE sweep of the 3-mode spiral scan and print its figures (profiling runs)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the 64-scan batched workload and print its figures (profiling runs)")
     ap.add_argument("--engines-only", action="store_true",
                     help="run only the 64^2 Fourier-engine comparison on a --grid (default 100) raster (profiling runs)")
     ap.add_argument("--residual-store", default="f32", choices=["f32", "f16"],
@@ -602,6 +605,10 @@ def main():
     if args.epie_only:
         stream = torch.cuda.Stream()
         print(json.dumps(run_epie(api, torch, stream)), flush=True)
+        return
+    if args.batch_only:
+        stream = torch.cuda.Stream()
+        print(json.dumps(run_batched(api, torch, stream)), flush=True)
         return
     if args.engines_only:
         stream = torch.cuda.Stream()

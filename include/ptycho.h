@@ -401,17 +401,29 @@ int ptycho_epie_cluster_size(const ptycho_ctx* ctx);
  * ptycho_batch_kernels_per_iteration: kernel nodes in the captured graph.
  * ptycho_batch_set_group_bytes: the group budget in bytes (<= 0: all members
  *   in one group); the graph is captured again at the next iterate.
- * ptycho_batch_groups: number of groups of the current plan; if group_of is
- *   not NULL it receives each member's group index (n ints).  The schedule
+ * ptycho_batch_groups: number of groups (lanes in lanes mode) of the current
+ *   plan; if group_of is not NULL it receives each member's group (lane)
+ *   index (n ints).  The schedule
  *   changes only the order of independent work: results are bit-identical
  *   for every budget.
+ * ptycho_batch_set_lanes: lanes > 0 replaces the groups by that many
+ *   chains: members sorted by work (J K M^2 (log2 M + 6)), largest first,
+ *   each to the chain with the least work so far; a chain runs its members
+ *   one after another and the chains run side by side, with no barrier
+ *   between chains until the end of the iteration.  0 returns to groups
+ *   (as does ptycho_batch_set_group_bytes).  Errors: PTYCHO_ERR_ARG
+ *   (lanes < 0).
+ * ptycho_batch_lanes: the current number of lanes (0: groups mode; -1 for
+ *   b = NULL).
  * ptycho_batch_autotune: time n_iter iterations of alg under each candidate
- *   group budget (all members at once, then 64 MiB .. 4 GiB; budgets giving
- *   the same partition are timed once), keep the fastest and write it to
- *   *best_bytes and its time per iteration (ms) to *best_ms (either may be
+ *   schedule -- group budgets (all members at once, then 64 MiB .. 4 GiB)
+ *   and lanes (2 .. 32 chains, fewer than the members); candidates giving
+ *   the same schedule are timed once -- keep the fastest and write its group
+ *   budget to *best_bytes, its lanes (0 for a group schedule) to
+ *   *best_lanes and its time per iteration (ms) to *best_ms (any may be
  *   NULL).  The timed iterations are real iterations of every member (one
  *   untimed iteration per candidate captures its graph): the iteration
- *   counters advance by (n_iter + 1) per distinct partition.
+ *   counters advance by (n_iter + 1) per distinct schedule.
  * Errors: PTYCHO_ERR_* codes; ptycho_batch_last_error(b) (b = NULL: last
  * failed create). */
 typedef struct ptycho_batch ptycho_batch;
@@ -421,7 +433,10 @@ int ptycho_batch_size(const ptycho_batch* b);
 int ptycho_batch_iterate(ptycho_batch* b, int alg, int n_iter);
 long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b);
 int ptycho_batch_set_group_bytes(ptycho_batch* b, long long bytes);
-int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_bytes, double* best_ms);
+int ptycho_batch_set_lanes(ptycho_batch* b, int lanes);
+int ptycho_batch_lanes(const ptycho_batch* b);
+int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_bytes, int* best_lanes,
+                          double* best_ms);
 int ptycho_batch_groups(ptycho_batch* b, int* group_of);
 int ptycho_batch_synchronize(ptycho_batch* b);
 const char* ptycho_batch_last_error(const ptycho_batch* b);

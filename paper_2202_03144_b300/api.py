@@ -116,7 +116,9 @@ def lib() -> C.CDLL:
             "ptycho_batch_kernels_per_iteration": (C.c_longlong, [vp]),
             "ptycho_batch_set_group_bytes": (i, [vp, C.c_longlong]),
             "ptycho_batch_groups": (i, [vp, C.POINTER(C.c_int)]),
-            "ptycho_batch_autotune": (i, [vp, i, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
+            "ptycho_batch_autotune": (i, [vp, i, i, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(d)]),
+            "ptycho_batch_set_lanes": (i, [vp, i]),
+            "ptycho_batch_lanes": (i, [vp]),
             "ptycho_batch_synchronize": (i, [vp]),
             "ptycho_batch_last_error": (C.c_char_p, [vp]),
             "ptycho_batch_destroy": (None, [vp]),
@@ -572,14 +574,23 @@ class Batch:
         (<= 0: all members at once)."""
         self._check(lib().ptycho_batch_set_group_bytes(self.h, int(nbytes)))
 
+    def set_lanes(self, lanes):
+        """lanes > 0: members in that many chains run side by side (largest
+        work first, each to the least-loaded chain); 0: groups."""
+        self._check(lib().ptycho_batch_set_lanes(self.h, int(lanes)))
+
+    @property
+    def lanes(self):
+        return lib().ptycho_batch_lanes(self.h)
+
     def autotune(self, alg="lsqml", n_iter=2):
-        """Time n_iter iterations under each candidate group budget and keep
-        the fastest: (bytes, ms per iteration).  The timed iterations are real
-        iterations of every member."""
-        gb, ms = C.c_longlong(), C.c_double()
+        """Time n_iter iterations under each candidate schedule (group budgets
+        and lanes) and keep the fastest: (group bytes, lanes or 0, ms per
+        iteration).  The timed iterations are real iterations of every member."""
+        gb, ln, ms = C.c_longlong(), C.c_int(), C.c_double()
         a = ALGS[alg] if isinstance(alg, str) else int(alg)
-        self._check(lib().ptycho_batch_autotune(self.h, a, int(n_iter), C.byref(gb), C.byref(ms)))
-        return gb.value, ms.value
+        self._check(lib().ptycho_batch_autotune(self.h, a, int(n_iter), C.byref(gb), C.byref(ln), C.byref(ms)))
+        return gb.value, ln.value, ms.value
 
     def groups(self):
         """Group index of every member under the current budget."""

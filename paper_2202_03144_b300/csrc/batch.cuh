@@ -33,7 +33,8 @@ struct ptycho_batch {
   std::vector<cudaEvent_t> join;
   std::vector<cudaEvent_t> gfork;     // one fork event per group
   long long group_bytes = 512LL << 20;
-  std::vector<std::vector<int>> groups;
+  int lanes = 0;                      // > 0: lanes mode (see batch_plan)
+  std::vector<std::vector<int>> groups;  // groups, or in lanes mode the members of each lane in order
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_alg = -1;
@@ -74,11 +75,36 @@ long long member_bytes(const ptycho_ctx* c) {
          (long long)c->p.obj_ny * c->p.obj_nx * 24;
 }
 
-// Partition the members into groups (see the top of this file).
+// Work of one iteration of a member, for the lane assignment: the Fourier
+// pass grows as M^2 log2 M per frame, the overlap passes as M^2.
+double member_work(const ptycho_ctx* c) {
+  const double MM = (double)c->p.M * c->p.M;
+  return (double)c->p.J * c->p.K * MM * (std::log2((double)c->p.M) + 6.0);
+}
+
+// Partition the members into groups (see the top of this file), or, in lanes
+// mode, into `lanes` chains: members sorted by work, largest first, each to
+// the chain with the least work so far (longest-processing-time order).  A
+// chain runs its members one after another and the chains run side by side,
+// so a member starts as soon as its chain's previous member ends, with no
+// barrier across chains until the iteration's end.
 void batch_plan(ptycho_batch* b) {
   const int n = (int)b->m.size();
   b->groups.clear();
-  if (b->group_bytes <= 0) {
+  if (b->lanes > 0) {
+    const int L = std::min(b->lanes, n);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return member_work(b->m[x]) > member_work(b->m[y]); });
+    b->groups.assign(L, {});
+    std::vector<double> load(L, 0.0);
+    for (int i : order) {
+      const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());  // first least-loaded
+      b->groups[l].push_back(i);
+      load[l] += member_work(b->m[i]);
+    }
+  } else if (b->group_bytes <= 0) {
     b->groups.emplace_back();
     for (int i = 0; i < n; ++i) b->groups.back().push_back(i);
   } else {
@@ -113,7 +139,26 @@ int batch_capture(ptycho_batch* b, int alg, const std::vector<char>& upd) {
   if (e != cudaSuccess) return bfail(b, PTYCHO_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
   long long before = 0, after = 0;
   int rc = 0;
-  for (size_t g = 0; g < b->groups.size() && !rc; ++g) {
+  if (b->lanes > 0) {
+    // lanes: each member after its chain's previous one, chains side by side
+    cudaEventRecord(b->gfork[0], b->main);
+    for (size_t l = 0; l < b->groups.size() && !rc; ++l) {
+      cudaEvent_t prev = b->gfork[0];
+      for (int i : b->groups[l]) {
+        ptycho_ctx* c = b->m[i];
+        cudaStreamWaitEvent(c->st, prev, 0);
+        before += c->launches;
+        rc = alg == PTYCHO_DM ? dm_step(c, upd[i] != 0) : lsqml_step(c, upd[i] != 0);
+        after += c->launches;
+        if (rc) b->err = "member " + std::to_string(i) + ": " + c->err;
+        cudaEventRecord(b->join[i], c->st);
+        prev = b->join[i];
+        if (rc) break;
+      }
+      cudaStreamWaitEvent(b->main, prev, 0);  // joined even on failure: the capture ends cleanly
+    }
+  }
+  for (size_t g = 0; g < b->groups.size() && !rc && b->lanes <= 0; ++g) {
     cudaEventRecord(b->gfork[g], b->main);  // after the previous group's joins
     for (int i : b->groups[g]) {
       ptycho_ctx* c = b->m[i];
@@ -395,31 +440,59 @@ long long ptycho_batch_kernels_per_iteration(const ptycho_batch* b) { return b ?
 
 int ptycho_batch_set_group_bytes(ptycho_batch* b, long long bytes) {
   if (!b) return PTYCHO_ERR_ARG;
-  if (bytes != b->group_bytes) {
+  if (bytes != b->group_bytes || b->lanes != 0) {
     b->group_bytes = bytes;
+    b->lanes = 0;         // groups mode
     batch_drop_graph(b);  // captured again at the next iterate
   }
   return PTYCHO_OK;
 }
 
-int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_bytes, double* best_ms) {
+int ptycho_batch_set_lanes(ptycho_batch* b, int lanes) {
+  if (!b) return PTYCHO_ERR_ARG;
+  if (lanes < 0) return bfail(b, PTYCHO_ERR_ARG, "lanes=%d", lanes);
+  if (lanes != b->lanes) {
+    b->lanes = lanes;
+    batch_drop_graph(b);
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_batch_lanes(const ptycho_batch* b) { return b ? b->lanes : -1; }
+
+int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_bytes, int* best_lanes,
+                          double* best_ms) {
   if (!b) return PTYCHO_ERR_ARG;
   if (n_iter < 1) return bfail(b, PTYCHO_ERR_ARG, "n_iter=%d", n_iter);
-  // candidate group budgets: every member at once, then 64 MiB .. 4 GiB
-  const long long cand[] = {0, 64LL << 20, 128LL << 20, 256LL << 20, 512LL << 20, 1LL << 30, 2LL << 30, 4LL << 30};
+  // candidates: group budgets (every member at once, then 64 MiB .. 4 GiB),
+  // then lanes of 2 .. 32 chains
+  struct Cand {
+    long long bytes;
+    int lanes;
+  };
+  std::vector<Cand> cand;
+  for (long long gb : {0LL, 64LL << 20, 128LL << 20, 256LL << 20, 512LL << 20, 1LL << 30, 2LL << 30, 4LL << 30})
+    cand.push_back({gb, 0});
+  for (int l : {2, 4, 8, 16, 32})
+    if (l < (int)b->m.size()) cand.push_back({b->group_bytes, l});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return bfail(b, PTYCHO_ERR_CUDA, "event creation failed");
-  long long best = b->group_bytes;
+  Cand best{b->group_bytes, b->lanes};
   float best_t = -1.f;
   int rc = PTYCHO_OK;
-  std::vector<std::vector<std::vector<int>>> seen;  // partitions already timed
-  for (long long gb : cand) {
-    if ((rc = ptycho_batch_set_group_bytes(b, gb))) break;
+  std::vector<std::pair<int, std::vector<std::vector<int>>>> seen;  // schedules already timed
+  for (const Cand& cd : cand) {
+    if (cd.lanes > 0) {
+      if ((rc = ptycho_batch_set_lanes(b, cd.lanes))) break;
+    } else if ((rc = ptycho_batch_set_group_bytes(b, cd.bytes))) {
+      break;
+    }
     batch_plan(b);
-    if (std::find(seen.begin(), seen.end(), b->groups) != seen.end()) continue;  // same partition as before
-    seen.push_back(b->groups);
-    if ((rc = ptycho_batch_iterate(b, alg, 1))) break;  // captures the graph of this partition
+    const std::pair<int, std::vector<std::vector<int>>> key{cd.lanes > 0, b->groups};
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;  // same schedule as before
+    seen.push_back(key);
+    if ((rc = ptycho_batch_iterate(b, alg, 1))) break;  // captures the graph of this schedule
     cudaEventRecord(e0, b->main);
     if ((rc = ptycho_batch_iterate(b, alg, n_iter))) break;
     cudaEventRecord(e1, b->main);
@@ -430,14 +503,17 @@ int ptycho_batch_autotune(ptycho_batch* b, int alg, int n_iter, long long* best_
     }
     if (best_t < 0.f || t < best_t) {
       best_t = t;
-      best = gb;
+      best = cd;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if (int r = ptycho_batch_set_group_bytes(b, best)) return r;
-  if (best_bytes) *best_bytes = best;
+  if (int r = ptycho_batch_set_group_bytes(b, best.bytes)) return r;
+  if (best.lanes > 0)
+    if (int r = ptycho_batch_set_lanes(b, best.lanes)) return r;
+  if (best_bytes) *best_bytes = best.bytes;
+  if (best_lanes) *best_lanes = best.lanes;
   if (best_ms) *best_ms = best_t / n_iter;
   return PTYCHO_OK;
 }

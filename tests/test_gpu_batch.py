@@ -106,6 +106,35 @@ def test_batch_group_schedule_is_bit_identical(budget):
         assert ng == 1
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 3])
+def test_batch_lane_schedule_is_bit_identical(lanes):
+    """Lanes (chains of members run side by side, no barrier between chains)
+    reorder independent work only: DM and LSQML give the group schedule's
+    results bit for bit, DM's exit waves included.  Members go largest work
+    first to the least-loaded chain, so the chains' work differs by at most
+    one member's."""
+    cases = _cases()
+    members = [dict(M=c["M"], K=c["K"], J=len(c["pos"]), obj_shape=c["shape"]) for c in cases]
+    for alg in ("lsqml", "dm"):
+        outs = []
+        for ln in (0, lanes):
+            with api.Batch(members) as b:
+                b.set_lanes(ln)
+                assert b.lanes == ln
+                for m, c in zip(b.members, cases):
+                    m.set_data(c["I"].astype(np.float32), c["pos"])
+                    m.set_init(c["O0"], c["P0"])
+                b.iterate(alg, 2)
+                outs.append([(m.get_object(), m.get_probe(), m.fourier_error()) for m in b.members])
+                chain = b.groups()
+        for (O1, P1, E1), (O2, P2, E2) in zip(*outs):
+            assert np.array_equal(O1, O2) and np.array_equal(P1, P2) and E1 == E2
+        assert max(chain) + 1 == min(lanes, len(cases))
+        work = [len(c["pos"]) * c["K"] * c["M"] ** 2 * (np.log2(c["M"]) + 6) for c in cases]
+        load = [sum(w for w, l in zip(work, chain) if l == k) for k in range(max(chain) + 1)]
+        assert max(load) - min(load) <= max(work) * (1 + 1e-12)
+
+
 def test_batch_autotune_keeps_the_fastest_budget_and_the_results():
     """The group-budget autotuner times real iterations under each distinct
     partition and keeps the fastest; the members end exactly where the same
@@ -117,8 +146,9 @@ def test_batch_autotune_keeps_the_fastest_budget_and_the_results():
         for m, c in zip(b.members, cases):
             m.set_data(c["I"].astype(np.float32), c["pos"])
             m.set_init(c["O0"], c["P0"])
-        gb, ms = b.autotune("lsqml", 1)
+        gb, lanes, ms = b.autotune("lsqml", 1)
         assert gb in (0, 64 << 20, 128 << 20, 256 << 20, 512 << 20, 1 << 30, 2 << 30, 4 << 30) and ms > 0
+        assert lanes in (0, 2, 4, 8, 16, 32) and b.lanes == lanes
         n = b.members[0].iteration
         assert n >= 2 and all(m.iteration == n for m in b.members)
         tuned = [(m.get_object(), m.get_probe()) for m in b.members]
