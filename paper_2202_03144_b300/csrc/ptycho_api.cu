@@ -343,6 +343,7 @@ struct ptycho_ctx {
   float* denO_max = nullptr;
   int* tile_ptr = nullptr;
   int* tile_list = nullptr;
+  size_t tile_list_cap = 0;   // ints allocated for tile_list
   int n_tiles = 0, ntx = 0, nty = 0;
   int G = 1;                 // position groups of the probe sums
   int G_cap = 1;             // capacity of the group partials
@@ -1469,9 +1470,10 @@ int build_subpixel_groups(ptycho_ctx* ctx, const std::vector<unsigned short>& bi
   goff.push_back(J);
   const int G = (int)goff.size() - 1;
   if (G > ctx->G_cap) return fail(ctx, PTYCHO_ERR_ARG, "internal: %d probe-sum groups exceed %d", G, ctx->G_cap);
-  CK(cudaMemcpy(ctx->porder, order.data(), J * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->bgrp, bgrp.data(), bgrp.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(ctx->porder, order.data(), J * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->bgrp, bgrp.data(), bgrp.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // the host vectors end with this call
   ctx->G_sub = G;
   return 0;
 }
@@ -1522,7 +1524,7 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
     if (int r = dalloc(ctx, &ctx->cg_part, 3 * ((KMM + CG_NT - 1) / CG_NT))) return r;
     if (int r = dalloc(ctx, &ctx->pos_corr, (size_t)J)) return r;
     if (int r = dalloc(ctx, &ctx->ep_mx, (size_t)EPS_MX_CAP)) return r;
-    CK(cudaMemcpy(ctx->pbin, bin.data(), J * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(ctx->pbin, bin.data(), J * sizeof(unsigned short), cudaMemcpyHostToDevice, ctx->st));
     ctx->bin_host = bin;
     if (int r = build_subpixel_groups(ctx, bin)) return r;
   }
@@ -1543,11 +1545,22 @@ int set_positions_impl(ptycho_ctx* ctx, const float* positions) {
     for (int ty = t0y; ty <= t1y; ++ty)
       for (int tx = t0x; tx <= t1x; ++tx) list[fill[ty * ctx->ntx + tx]++] = j;
   }
-  dfree(ctx, ctx->tile_list);
-  if (int r = dalloc(ctx, &ctx->tile_list, list.size() + 1)) return r;
-  CK(cudaMemcpy(ctx->pos, pos.data(), J * sizeof(int2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->tile_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // the tile lists keep their allocation while they fit (a free would wait
+  // for the whole device, other contexts' work included); the uploads are
+  // ordered on the context's stream after its own earlier kernels, which
+  // read the lists they replace
+  if (list.size() + 1 > ctx->tile_list_cap) {
+    dfree(ctx, ctx->tile_list);
+    ctx->tile_list_cap = 0;
+    if (int r = dalloc(ctx, &ctx->tile_list, list.size() + 1)) return r;
+    ctx->tile_list_cap = list.size() + 1;
+  }
+  CK(cudaMemcpyAsync(ctx->pos, pos.data(), J * sizeof(int2), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->tile_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  // the sources are host vectors of this call: wait until the copies have
+  // consumed them (a pageable copy may return before it has)
+  CK(cudaStreamSynchronize(ctx->st));
   ctx->pos_host = pos;
   ctx->pos_f.assign(positions, positions + 2 * (size_t)J);
   ctx->have_pos = true;
