@@ -33,11 +33,28 @@
 
 namespace ptycho {
 
-// bytes of dynamic shared memory: X, Y, twiddle tables, reduction scratch,
-// two mbarriers
-template <class F>
+// Merged column and row buffer (the DM pass of the one-mode 256^2 shapes):
+// one 32 KB exchange buffer instead of two, so four CTAs share an SM (at 64
+// registers); the two write-after-read hazards that separate buffers avoid
+// -- a peer still reading its buffer when this CTA's transpose data arrives
+// in it -- are closed by a split cluster barrier before each transpose
+// (arrive with release once a thread's reads of the buffer are issued, wait
+// with acquire just before its first remote store).  Measured at 256^2 x 10k
+// positions: DM pass 7.39 against 7.92 ms (it also streams psi, and the
+// fourth CTA hides that latency); the LSQML residual pass lost (6.69 against
+// 6.06 ms: its barriers and register spills cost more than the occupancy
+// gains), so it keeps two buffers.
+template <class F, int MODE_T>
+__host__ __device__ constexpr bool f3_merged() {
+  return MODE_T == FM_DM && F::K == 1 && F::M == 256 && F::L == F::K * F::H * F::PB;
+}
+
+// bytes of dynamic shared memory: X, Y (one buffer when merged), twiddle
+// tables, reduction scratch, two mbarriers
+template <class F, int MODE_T = -1>
 __host__ __device__ constexpr size_t fourier3_smem() {
-  return (size_t)F::L * 8 + (size_t)F::K * F::H * F::PB * 8 + (size_t)F::M * 16 + F::NRED * 8 + 16;
+  return (size_t)F::L * 8 + (f3_merged<F, MODE_T>() ? 0 : (size_t)F::K * F::H * F::PB * 8) + (size_t)F::M * 16 +
+         F::NRED * 8 + 16;
 }
 
 __device__ __forceinline__ void st_async_f2(uint32_t addr, float2 v, uint32_t bar) {
@@ -90,23 +107,24 @@ constexpr int F3_OG = PT_F3_OG;
 
 // CTAs per SM for the launch bounds: by threads (and the radix-24 register
 // demand) and by shared memory
-template <class F>
+template <class F, int MODE_T>
 constexpr int f3_min_blocks() {
-  const int by_threads = F::R1 > 16 ? 1 : (F::NT <= 256 ? 3 : (F::NT <= 512 ? 2 : 1));
-  const int by_smem = (int)((228 * 1024) / (fourier3_smem<F>() + 1024));
+  const int by_threads = F::R1 > 16 ? 1 : (F::NT <= 256 ? (f3_merged<F, MODE_T>() ? 4 : 3) : (F::NT <= 512 ? 2 : 1));
+  const int by_smem = (int)((228 * 1024) / (fourier3_smem<F, MODE_T>() + 1024));
   const int b = by_threads < by_smem ? by_threads : by_smem;
   return b < 1 ? 1 : b;
 }
 
 template <int M, int K, int C, int MODE_T = -1, int IST_T = -1>
-__global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>()) k_fourier3(Fourier2Args a) {
+__global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>, MODE_T>()) k_fourier3(Fourier2Args a) {
   using F = F2<M, K, C>;
   static_assert(C > 1, "cluster kernel");
   constexpr int R1 = F::R1, R2 = F::R2, W = F::W, H = F::H, NT = F::NT, Q = F::Q;
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr bool MERGED = f3_merged<F, MODE_T>();
   float2* X = reinterpret_cast<float2*>(smem_raw);  // column layout, cb<F>()
-  float2* Y = X + F::L;                               // row layout, rb<F>()
-  float2* tw = Y + K * H * F::PB;                     // tw[k1 * R2 + n2] = W_M^(n2 k1)
+  float2* Y = MERGED ? X : X + F::L;                  // row layout, rb<F>()
+  float2* tw = X + F::L + (MERGED ? 0 : K * H * F::PB);  // tw[k1 * R2 + n2] = W_M^(n2 k1)
   float2* twT = tw + M;                               // twT[n2 * R1 + k1]
   double* red = reinterpret_cast<double*>(twT + M);
   uint64_t* barY = reinterpret_cast<uint64_t*>(red + F::NRED);
@@ -136,7 +154,8 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     }
   }
   // barriers initialised: peers may signal them once they pass the wait below
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  // (merged buffer: the arrive after column stage 2's reads does this too)
+  if (!MERGED) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   for (int i = tid; i < M; i += NT) {
     const float2 t = a.tw2[i];
     tw[i] = t;
@@ -183,9 +202,14 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
       const int colL = s % W, k1 = (s / W) % R1, k = s / (W * R1);
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) w[q][n2] = X[cb<F>(k, k1 * R2 + n2, colL)];
+      // merged: this thread's reads of the buffer are issued; peers may
+      // overwrite it (with their row data) once every thread has arrived
+      if (MERGED && q == Q - 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
       dft<R2, false>(w[q]);
     }
-    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // peers' barriers exist
+    // peers' barriers exist (and, merged, every peer has read its buffer)
+    if (MERGED) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     const uint32_t barY_l = smem_u32(barY);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -380,7 +404,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>>())
     const int n2 = tid % R2, rowL = (tid / R2) % H, k = tid / (R2 * H);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) v[k1] = Y[rb<F>(k, rowL, k1 * R2 + n2)];
+    if (MERGED) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");  // row data read
     dft<R1, true>(v);
+    if (MERGED) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");  // peers' too
     const int f = c * H + rowL;
     const uint32_t barX_l = smem_u32(barX);
 #pragma unroll

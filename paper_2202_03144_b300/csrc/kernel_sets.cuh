@@ -35,10 +35,11 @@ struct KernelSet {
   FourierFn fourier;       // any mode, any amplitude format
   void (*epie)(EpieArgs);  // null: no ePIE kernel for this shape
   FourierFn spec[5][3];    // [spec_row(mode)][f32, f16, bf16]
-  size_t smem_spec;        // dynamic shared memory of the spec kernels
+  size_t smem_spec;        // dynamic shared memory of the spec kernels: the largest row
   bool default_ok = true;  // a candidate for the default cluster size of DM/LSQML
   void (*epie2)(Epie2Args) = nullptr;  // register-resident ePIE sweep (C > 1), or null
   size_t smem_epie2 = 0;
+  size_t smem_row[5] = {};  // dynamic shared memory of each row of spec
 };
 
 // Row of KernelSet::spec for a Fourier mode: DM, LSQML residual (amplitude),
@@ -51,17 +52,18 @@ __host__ __device__ constexpr int spec_row(int mode) {
 template <int M, int K, int C, int MODE>
 void fill_spec_row(KernelSet& s) {
   constexpr int r = spec_row(MODE);
-  if constexpr (C > 1 && PT_F3 && fourier3_smem<F2<M, K, C>>() <= 227 * 1024) {
+  if constexpr (C > 1 && PT_F3 && fourier3_smem<F2<M, K, C>, MODE>() <= 227 * 1024) {
     s.spec[r][0] = k_fourier3<M, K, C, MODE, 0>;
     s.spec[r][1] = k_fourier3<M, K, C, MODE, 1>;
     s.spec[r][2] = k_fourier3<M, K, C, MODE, 2>;
-    s.smem_spec = fourier3_smem<F2<M, K, C>>();
+    s.smem_row[r] = fourier3_smem<F2<M, K, C>, MODE>();
   } else {
     s.spec[r][0] = k_fourier2<M, K, C, MODE, 0>;
     s.spec[r][1] = k_fourier2<M, K, C, MODE, 1>;
     s.spec[r][2] = k_fourier2<M, K, C, MODE, 2>;
-    s.smem_spec = fourier2_smem<F2<M, K, C>>();
+    s.smem_row[r] = fourier2_smem<F2<M, K, C>>();
   }
+  if (s.smem_row[r] > s.smem_spec) s.smem_spec = s.smem_row[r];
 }
 
 template <int M, int K, int C>

@@ -53,9 +53,9 @@ namespace {
 // The Fourier kernel variants of a set with their dynamic shared memory.
 std::vector<std::pair<FourierFn, size_t>> fourier_variants(const KernelSet* ks) {
   std::vector<std::pair<FourierFn, size_t>> v{{ks->fourier, ks->smem_fourier}};
-  for (const auto& row : ks->spec)
-    for (FourierFn f : row)
-      if (f) v.push_back({f, ks->smem_spec});
+  for (int r = 0; r < 5; ++r)
+    for (FourierFn f : ks->spec[r])
+      if (f) v.push_back({f, ks->smem_row[r]});
   return v;
 }
 
@@ -675,7 +675,7 @@ int launch_fourier(ptycho_ctx* ctx, int mode, float2* X, float* I_out, int j0, i
     const int row = spec_row(mode);
     if (row >= 0 && a.istore >= 0 && a.istore < 3 && ks->spec[row][a.istore]) {
       fn = ks->spec[row][a.istore];
-      cfg.dynamicSmemBytes = ks->smem_spec;
+      cfg.dynamicSmemBytes = ks->smem_row[row];
     }
     cudaLaunchKernelEx(&cfg, fn, a);
   });
