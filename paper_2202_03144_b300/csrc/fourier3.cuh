@@ -42,11 +42,15 @@ namespace ptycho {
 // with acquire just before its first remote store).  Measured at 256^2 x 10k
 // positions: DM pass 7.39 against 7.92 ms (it also streams psi, and the
 // fourth CTA hides that latency); the LSQML residual pass lost (6.69 against
-// 6.06 ms: its barriers and register spills cost more than the occupancy
-// gains), so it keeps two buffers.
+// 6.06 ms, 6.50 with its amplitude loads after the first transpose), so it
+// keeps two buffers unless PT_F3_MERGED_CHI is set.
+#ifndef PT_F3_MERGED_CHI
+#define PT_F3_MERGED_CHI 0
+#endif
 template <class F, int MODE_T>
 __host__ __device__ constexpr bool f3_merged() {
-  return MODE_T == FM_DM && F::K == 1 && F::M == 256 && F::L == F::K * F::H * F::PB;
+  return (MODE_T == FM_DM || (PT_F3_MERGED_CHI && MODE_T == FM_CHI)) && F::K == 1 && F::M == 256 &&
+         F::L == F::K * F::H * F::PB;
 }
 
 // bytes of dynamic shared memory: X, Y (one buffer when merged), twiddle
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>, MO
   };
   // LSQML residual pass: before the wait (256^2: 6.51 -> 6.24 ms); DM pass,
   // whose prologue holds more registers: after row stage 1 (2% faster there)
-  constexpr bool amp_early = MODE_T != FM_DM;
+  constexpr bool amp_early = MODE_T != FM_DM && !MERGED;
   if (amp_early) {
     load_amp();
     load_amp_k();
