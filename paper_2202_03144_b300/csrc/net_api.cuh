@@ -151,11 +151,19 @@ void launch_conv_tc(ptycho_net* n, const ConvArgs& a, const NetLayer& L, bool ou
 }
 
 // Backward on the tensor cores (net_bwd_tc.cuh).  Pixel splits of the
-// weight gradient: about two CTAs per SM, within the partial buffer.
+// weight gradient: about as many CTAs as fit on the SMs at once (two per SM
+// for the 144-wide tile, six for the one-channel one), within the partial
+// buffer.
+int bw_tc_nt(const NetLayer& L) { return L.ci == 1 ? BW_NT1 : BW_NT; }
+int bw_tc_tiles(const NetLayer& L) {
+  const int nt = bw_tc_nt(L);
+  return ((L.co + 127) / 128) * ((L.ci * 9 + nt - 1) / nt);
+}
+long long bw_tc_want(const NetLayer& L) { return (bw_tc_nt(L) == BW_NT ? 2 : 6) * 148LL; }
 int bw_tc_splits(const NetLayer& L, int B, size_t wpart_n) {
-  const int tiles = ((L.co + 127) / 128) * ((L.ci * 9 + BW_NT - 1) / BW_NT);
+  const int tiles = bw_tc_tiles(L);
   const long long nchunk = ((long long)B * L.hout * L.wout + BW_KC - 1) / BW_KC;
-  long long s = (2 * 148 + tiles - 1) / tiles;
+  long long s = (bw_tc_want(L) + tiles - 1) / tiles;
   s = std::min<long long>(s, nchunk);
   s = std::min<long long>(s, (long long)(wpart_n / ((size_t)L.co * L.ci * 9)));
   return (int)std::max<long long>(s, 1);
@@ -313,9 +321,11 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
     int nchunk = (int)((npo + BW_CHUNK - 1) / BW_CHUNK);
     if (n->tc) {  // tensor cores: pixel splits of (co tile x k tile) GEMMs
       nchunk = bw_tc_splits(L, B, n->wpart_n);
-      const int tiles = ((L.co + 127) / 128) * ((L.ci * 9 + BW_NT - 1) / BW_NT);
-      k_conv_bwd_w_tc<__nv_bfloat16><<<dim3((unsigned)tiles, (unsigned)nchunk), 128, bw_tc_smem_launch(), n->st>>>(
-          a, nchunk, n->err_flag);
+      const dim3 g((unsigned)bw_tc_tiles(L), (unsigned)nchunk);
+      if (bw_tc_nt(L) == BW_NT1)
+        k_conv_bwd_w_tc<__nv_bfloat16, BW_NT1><<<g, 128, bw_tc_smem_launch<BW_NT1>(), n->st>>>(a, nchunk, n->err_flag);
+      else
+        k_conv_bwd_w_tc<__nv_bfloat16, BW_NT><<<g, 128, bw_tc_smem_launch<BW_NT>(), n->st>>>(a, nchunk, n->err_flag);
     } else {
       const int nciq = (L.ci + BW_CI - 1) / BW_CI;
       if (n->f32) k_conv_bwd_w<float><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
@@ -442,8 +452,8 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     const long long npo = (long long)max_batch * L.hout * L.wout;
     maxpart = std::max(maxpart, (size_t)((npo + BW_CHUNK - 1) / BW_CHUNK) * L.co * L.ci * 9);
     // the tensor-core weight gradient: about two CTAs per SM of pixel splits
-    const long long tiles = ((L.co + 127) / 128) * ((L.ci * 9 + BW_NT - 1) / BW_NT);
-    const long long want = std::min<long long>((2 * 148 + tiles - 1) / tiles, (npo + BW_KC - 1) / BW_KC);
+    const long long tiles = bw_tc_tiles(L);
+    const long long want = std::min<long long>((bw_tc_want(L) + tiles - 1) / tiles, (npo + BW_KC - 1) / BW_KC);
     maxpart = std::max(maxpart, (size_t)want * L.co * L.ci * 9);
   }
   int r = 0;
@@ -497,7 +507,8 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     setsm((const void*)k_conv_fwd_tc<true, 128, true>, conv_tc_smem<128>());
     setsm((const void*)k_conv_fwd_tc<false, 256, true>, conv_tc_smem<256>());
     setsm((const void*)k_conv_fwd_tc<true, 256, true>, conv_tc_smem<256>());
-    setsm((const void*)k_conv_bwd_w_tc<__nv_bfloat16>, bw_tc_smem_launch());
+    setsm((const void*)k_conv_bwd_w_tc<__nv_bfloat16, BW_NT>, bw_tc_smem_launch<BW_NT>());
+    setsm((const void*)k_conv_bwd_w_tc<__nv_bfloat16, BW_NT1>, bw_tc_smem_launch<BW_NT1>());
     setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 16>, bd_tc_smem<16>());
     setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 32>, bd_tc_smem<32>());
     setsm((const void*)k_conv_bwd_data_tc<__nv_bfloat16, 64>, bd_tc_smem<64>());

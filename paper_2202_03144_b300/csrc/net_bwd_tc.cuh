@@ -36,15 +36,21 @@
 namespace ptycho {
 
 constexpr int BW_NT = 144;   // weight-gradient N tile: 16 input channels x 9 taps
+constexpr int BW_NT1 = 16;   // ... for a one-channel input: the 9 taps, padded
 constexpr int BW_KC = 64;    // pixels per K chunk
+template <int NT>
 constexpr size_t bw_tc_smem() {
-  // two (A: 128 x 64, B: 144 x 64) BF16 stages, mbarriers, tensor-memory slot
-  return 2 * ((size_t)128 * BW_KC * 2 + (size_t)BW_NT * BW_KC * 2) + 64;
+  // two (A: 128 x 64, B: NT x 64) BF16 stages, mbarriers, tensor-memory slot
+  return 2 * ((size_t)128 * BW_KC * 2 + (size_t)NT * BW_KC * 2) + 64;
 }
-// The launch asks for more: a CTA holds 256 tensor-memory columns, so at most
-// two may share an SM's 512 (a third would wait in its allocation).
-constexpr size_t bw_tc_smem_launch() { return 80 * 1024; }
-static_assert(bw_tc_smem() <= bw_tc_smem_launch() && 3 * bw_tc_smem_launch() > 228 * 1024, "two CTAs per SM");
+// The launch asks for more at N = 144: a CTA holds 256 tensor-memory
+// columns, so at most two may share an SM's 512 (a third would wait in its
+// allocation).  The one-channel tile holds 32 columns: six CTAs per SM, by
+// shared memory.
+template <int NT>
+constexpr size_t bw_tc_smem_launch() { return NT == BW_NT ? 80 * 1024 : bw_tc_smem<NT>(); }
+static_assert(bw_tc_smem<BW_NT>() <= bw_tc_smem_launch<BW_NT>() && 3 * bw_tc_smem_launch<BW_NT>() > 228 * 1024,
+              "two CTAs per SM");
 
 // 8 floats -> 8 BF16 in one 16-byte word
 __device__ __forceinline__ uint4 pack8_bf16(const float* v) {
@@ -57,22 +63,24 @@ __device__ __forceinline__ uint4 pack8_bf16(const float* v) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Weight gradient.  grid = (co tiles of 128 x k tiles of 144, pixel splits).
+// Weight gradient.  grid = (co tiles of 128 x k tiles of NT, pixel splits).
 // Writes the FP32 partial dW of its pixel range: part[split][co][ci * 9].
-template <typename TA>
+// NT = BW_NT: tap-major tiles of 16 input channels; NT = BW_NT1: the
+// one-channel first layer, column = tap.
+template <typename TA, int NT>
 __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, int* err_flag) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  constexpr size_t ABYTES = (size_t)128 * BW_KC * 2, BBYTES = (size_t)BW_NT * BW_KC * 2;
+  constexpr size_t ABYTES = (size_t)128 * BW_KC * 2, BBYTES = (size_t)NT * BW_KC * 2;
   unsigned char* stage[2] = {smem_raw, smem_raw + ABYTES + BBYTES};
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (ABYTES + BBYTES));
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   constexpr uint32_t LBO = 128, SBO = (BW_KC / 8) * 128;
-  constexpr uint32_t NCOLS = 256;
+  constexpr uint32_t NCOLS = NT <= 32 ? 32 : 256;
   const TA* in = reinterpret_cast<const TA*>(a.in);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KW = a.ci * 9;
-  const int nkt = (KW + BW_NT - 1) / BW_NT;
-  const int co0 = (blockIdx.x / nkt) * 128, k0 = (blockIdx.x % nkt) * BW_NT;
+  const int nkt = (KW + NT - 1) / NT;
+  const int co0 = (blockIdx.x / nkt) * 128, k0 = (blockIdx.x % nkt) * NT;
   const int hw = a.hout * a.wout;
   const long long npix = (long long)a.B * hw;
   const long long nchunk = (npix + BW_KC - 1) / BW_KC;
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *tslot;
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BW_NT);
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NT);
   uint32_t ph[2] = {0u, 0u};
   bool pending[2] = {false, false};
   bool ok = true;
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
     // thread's 8 pixels' source rows (as plane offsets) and columns for the
     // three vertical and three horizontal taps, once per chunk (wout >= 4:
     // at most one row change inside the group); -1 outside the input.
-    if (ncl == 16) {
+    if (NT == BW_NT && ncl == 16) {
       const TA* plane = in + ((size_t)n * a.ci + ci0 + cl) * a.hin * a.win;
       int roff[3][8], sx[3][8];
       {
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
           }
           v[e] = x;
         }
-        const int r = t * 16 + c2;
+        const int r = t * (NT == BW_NT ? 16 : 1) + c2;  // one-channel tile: column = tap
         *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) = pack8_bf16(v);
       }
     }
@@ -225,16 +233,22 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
   const int co = co0 + warp * 32 + (tid & 31);
   const bool any = c_end > c_begin;
 #pragma unroll 1
-  for (int c0 = 0; c0 < BW_NT; c0 += 16) {
+  for (int c0 = 0; c0 < NT; c0 += 16) {
     float v[16];
     tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
     if (co < a.co) {
-      // column c0 + j = tap * 16 + channel: a 16-column slice is one tap
-      const int t = c0 >> 4;
+      if constexpr (NT == BW_NT) {
+        // column c0 + j = tap * 16 + channel: a 16-column slice is one tap
+        const int t = c0 >> 4;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int ci = ci0 + j;
-        if (ci < a.ci) a.wpart[((size_t)blockIdx.y * a.co + co) * KW + ci * 9 + t] = any ? v[j] : 0.f;
+        for (int j = 0; j < 16; ++j) {
+          const int ci = ci0 + j;
+          if (ci < a.ci) a.wpart[((size_t)blockIdx.y * a.co + co) * KW + ci * 9 + t] = any ? v[j] : 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)  // column = tap of the one channel
+          if (j < KW) a.wpart[((size_t)blockIdx.y * a.co + co) * KW + j] = any ? v[j] : 0.f;
       }
     }
   }
