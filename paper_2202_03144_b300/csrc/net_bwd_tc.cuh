@@ -63,6 +63,77 @@ __device__ __forceinline__ uint4 pack8_bf16(const float* v) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// The BF16 im2col values of 8 output pixels (x0 .. x0 + 7 of output row y,
+// x0 a multiple of 8) for vertical tap ty and the three horizontal taps, as
+// w[tx][4] (value e in half e % 2 of word e / 2, as pack8_bf16 lays them
+// out), read from one source plane with the coordinates of net_src:
+//   stride 1:   source columns x0 - 1 .. x0 + 8: the 8 aligned values and the
+//               two neighbours, each tap a shift by one value;
+//   stride 2:   source columns 2 x0 - 1 .. 2 x0 + 15: 16 aligned values and
+//               the left neighbour, taps 0 / 2 the odd values, tap 1 the even;
+//   upsampling: source columns x0 / 2 - 1 .. x0 / 2 + 4: 4 aligned values and
+//               the two neighbours, each repeated twice.
+// Values outside the source are zero, as is everything when !pin.
+__device__ __forceinline__ void bw_row_taps(const ConvArgs& a, const unsigned short* plane, bool pin, int y, int x0,
+                                            int ty, uint32_t (&w)[3][4]) {
+  int sy;
+  bool ok;
+  if (a.up) {
+    const int vy = y + ty - 1;
+    ok = pin && vy >= 0 && vy < 2 * a.hin;
+    sy = vy >> 1;
+  } else {
+    sy = a.stride * y + ty - 1;
+    ok = pin && sy >= 0 && sy < a.hin;
+  }
+  const unsigned short* row = plane + (size_t)(ok ? sy : 0) * a.win;
+  if (a.up) {
+    const int c = x0 >> 1;
+    const uint2 q = ok ? __ldg(reinterpret_cast<const uint2*>(row + c)) : make_uint2(0u, 0u);
+    const uint32_t L = (ok && x0 > 0) ? (uint32_t)__ldg(row + c - 1) : 0u;
+    const uint32_t R = (ok && x0 + 8 < a.wout) ? (uint32_t)__ldg(row + c + 4) : 0u;
+    w[1][0] = __byte_perm(q.x, q.x, 0x1010);
+    w[1][1] = __byte_perm(q.x, q.x, 0x3232);
+    w[1][2] = __byte_perm(q.y, q.y, 0x1010);
+    w[1][3] = __byte_perm(q.y, q.y, 0x3232);
+    w[0][0] = __byte_perm(L, q.x, 0x5410);
+    w[0][1] = q.x;
+    w[0][2] = __byte_perm(q.x, q.y, 0x5432);
+    w[0][3] = q.y;
+    w[2][0] = q.x;
+    w[2][1] = __byte_perm(q.x, q.y, 0x5432);
+    w[2][2] = q.y;
+    w[2][3] = __byte_perm(q.y, R, 0x5432);
+  } else if (a.stride == 1) {
+    const uint4 b = ok ? __ldg(reinterpret_cast<const uint4*>(row + x0)) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t L = (ok && x0 > 0) ? (uint32_t)__ldg(row + x0 - 1) << 16 : 0u;
+    const uint32_t R = (ok && x0 + 8 < a.win) ? (uint32_t)__ldg(row + x0 + 8) : 0u;
+    w[1][0] = b.x;
+    w[1][1] = b.y;
+    w[1][2] = b.z;
+    w[1][3] = b.w;
+    w[0][0] = __byte_perm(L, b.x, 0x5432);
+    w[0][1] = __byte_perm(b.x, b.y, 0x5432);
+    w[0][2] = __byte_perm(b.y, b.z, 0x5432);
+    w[0][3] = __byte_perm(b.z, b.w, 0x5432);
+    w[2][0] = w[0][1];
+    w[2][1] = w[0][2];
+    w[2][2] = w[0][3];
+    w[2][3] = __byte_perm(b.w, R, 0x5432);
+  } else {
+    const uint4 b0 = ok ? __ldg(reinterpret_cast<const uint4*>(row + 2 * x0)) : make_uint4(0u, 0u, 0u, 0u);
+    const uint4 b1 = ok ? __ldg(reinterpret_cast<const uint4*>(row + 2 * x0 + 8)) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t L = (ok && x0 > 0) ? (uint32_t)__ldg(row + 2 * x0 - 1) << 16 : 0u;
+    const uint32_t W[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w[1][i] = __byte_perm(W[2 * i], W[2 * i + 1], 0x5410);
+      w[2][i] = __byte_perm(W[2 * i], W[2 * i + 1], 0x7632);
+      w[0][i] = __byte_perm(i ? W[2 * i - 1] : L, W[2 * i], 0x7632);
+    }
+  }
+}
+
 // Weight gradient.  grid = (co tiles of 128 x k tiles of NT, pixel splits).
 // Writes the FP32 partial dW of its pixel range: part[split][co][ci * 9].
 // NT = BW_NT: tap-major tiles of 16 input channels; NT = BW_NT1: the
@@ -144,7 +215,28 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w_tc(ConvArgs a, int nsplit, i
     // thread's 8 pixels' source rows (as plane offsets) and columns for the
     // three vertical and three horizontal taps, once per chunk (wout >= 4:
     // at most one row change inside the group); -1 outside the input.
-    if (NT == BW_NT && ncl == 16) {
+    if (NT == BW_NT && ncl == 16 && a.wout % 8 == 0 && sizeof(TA) == 2) {
+      // output rows of at least 8 pixels: the 8 pixels of a group share one
+      // output row, and for each vertical tap one aligned load of the source
+      // row segment (16 bytes, stride 2: 32, upsampling: 8) plus the edge
+      // values yields all three horizontal taps by byte permutes
+      // (bw_row_taps); the source coordinates are those of net_src
+      const unsigned short* plane16 =
+          reinterpret_cast<const unsigned short*>(in) + ((size_t)n * a.ci + ci0 + cl) * a.hin * a.win;
+      const int y = yx0 / a.wout, x0 = yx0 - y * a.wout;
+      const int g = tid & 7;
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty) {
+        uint32_t w[3][4];
+        bw_row_taps(a, plane16, pin, y, x0, ty, w);
+#pragma unroll
+        for (int tx = 0; tx < 3; ++tx) {
+          const int r = (ty * 3 + tx) * 16 + cl;
+          *reinterpret_cast<uint4*>(Bs + (r >> 3) * SBO + g * LBO + (r & 7) * 16) =
+              make_uint4(w[tx][0], w[tx][1], w[tx][2], w[tx][3]);
+        }
+      }
+    } else if (NT == BW_NT && ncl == 16) {
       const TA* plane = in + ((size_t)n * a.ci + ci0 + cl) * a.hin * a.win;
       int roff[3][8], sx[3][8];
       {
