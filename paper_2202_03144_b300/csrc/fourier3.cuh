@@ -38,14 +38,21 @@ namespace ptycho {
 // registers); the two write-after-read hazards that separate buffers avoid
 // -- a peer still reading its buffer when this CTA's transpose data arrives
 // in it -- are closed by a split cluster barrier before each transpose
-// (arrive with release once a thread's reads of the buffer are issued, wait
+// (arrive once a thread has consumed what it read from the buffer, wait
 // with acquire just before its first remote store).  Measured at 256^2 x 10k
-// positions: DM pass 7.39 against 7.92 ms (it also streams psi, and the
-// fourth CTA hides that latency); the LSQML residual pass lost (6.69 against
-// 6.06 ms, 6.50 with its amplitude loads after the first transpose), so it
-// keeps two buffers unless PT_F3_MERGED_CHI is set.
+// positions: DM pass 7.10 against 7.92 ms with two buffers (it also streams
+// psi, and the fourth CTA hides that latency); the LSQML residual pass
+// loses (6.25 against 6.07 ms), so it keeps two buffers unless
+// PT_F3_MERGED_CHI is set.
 #ifndef PT_F3_MERGED_CHI
 #define PT_F3_MERGED_CHI 0
+#endif
+// 1 (default): the merged form arrives (relaxed) after the radix stage has
+// consumed the values it read -- the reads are then complete, so no release
+// fence is needed; 0: it arrives (release) right after issuing the reads.
+// DM pass at 256^2 x 10k: 7.10 against 7.40 ms.
+#ifndef PT_F3_ARRIVE_LATE
+#define PT_F3_ARRIVE_LATE 1
 #endif
 template <class F, int MODE_T>
 __host__ __device__ constexpr bool f3_merged() {
@@ -208,9 +215,12 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>, MO
       for (int n2 = 0; n2 < R2; ++n2) w[q][n2] = X[cb<F>(k, k1 * R2 + n2, colL)];
       // merged: this thread's reads of the buffer are issued; peers may
       // overwrite it (with their row data) once every thread has arrived
-      if (MERGED && q == Q - 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      if (MERGED && !PT_F3_ARRIVE_LATE && q == Q - 1)
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
       dft<R2, false>(w[q]);
     }
+    // (late form: the values are consumed, so the reads are complete)
+    if (MERGED && PT_F3_ARRIVE_LATE) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     // peers' barriers exist (and, merged, every peer has read its buffer)
     if (MERGED) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     else asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
@@ -408,8 +418,9 @@ __global__ void __launch_bounds__(F2<M, K, C>::NT, f3_min_blocks<F2<M, K, C>, MO
     const int n2 = tid % R2, rowL = (tid / R2) % H, k = tid / (R2 * H);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) v[k1] = Y[rb<F>(k, rowL, k1 * R2 + n2)];
-    if (MERGED) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");  // row data read
+    if (MERGED && !PT_F3_ARRIVE_LATE) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");  // row data read
     dft<R1, true>(v);
+    if (MERGED && PT_F3_ARRIVE_LATE) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     if (MERGED) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");  // peers' too
     const int f = c * H + rowL;
     const uint32_t barX_l = smem_u32(barX);
