@@ -325,8 +325,11 @@ struct ProbeArgs {
 };
 
 // SUB: positions taken through the bin order and its group offsets.
+#ifndef PT_PROBE_MINB
+#define PT_PROBE_MINB 1   // occupancy hint of the probe partial sums (1: none)
+#endif
 template <int K, bool SUB, typename XT = float2>
-__global__ void __launch_bounds__(PROBE_NT) k_probe_partial(ProbeArgs a) {
+__global__ void __launch_bounds__(PROBE_NT, PT_PROBE_MINB) k_probe_partial(ProbeArgs a) {
   const int MM = a.M * a.M;
   const int u = blockIdx.x * PROBE_NT + threadIdx.x;
   const int uy = u / a.M, ux = u % a.M;
