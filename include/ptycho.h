@@ -346,7 +346,9 @@ long long ptycho_memory_used(const ptycho_ctx* ctx);
  * iteration (and after its last one), each report one extra Fourier-error
  * pass and a host synchronisation -- the iterates are unchanged, bit for bit;
  * 0: errors only.  fn = NULL removes the sink.  The message is valid during
- * the call only.  Errors: PTYCHO_ERR_ARG (ctx NULL, error_every < 0). */
+ * the call only.  The sink runs inside a library call on this context: it
+ * may call ptycho_last_error(ctx) but no other function on the same
+ * context.  Errors: PTYCHO_ERR_ARG (ctx NULL, error_every < 0). */
 typedef void (*ptycho_log_fn)(void* user, int level, const char* msg);
 enum { PTYCHO_LOG_ERROR = 0, PTYCHO_LOG_INFO = 1 };
 int ptycho_set_log(ptycho_ctx* ctx, ptycho_log_fn fn, void* user, int error_every);
