@@ -5,6 +5,8 @@
 
 struct ptycho_net {
   cudaStream_t st = nullptr;
+  cudaStream_t st_side = nullptr;  // bias gradients and weight split sums beside the main chain
+  cudaEvent_t ev_fork1 = nullptr, ev_fork2 = nullptr, ev_join = nullptr;
   int max_batch = 0;
   long long n_params = 0, n_w = 0;
   long long w_off[NET_LAYERS], b_off[NET_LAYERS], wb_off[NET_LAYERS];
@@ -312,6 +314,11 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
   const int lb = 256;
   k_net_loss<<<lb, CV_NT, 0, n->st>>>(n->out, targets, nout, 1.f / (float)nout, n->delta[0], n->lpart);
   int cur = 0;
+  // Per layer the bias gradient (it reads only this layer's delta) runs on
+  // the side stream beside the weight gradient, and the weight gradient's
+  // split sums beside the data gradient; the next layer's weight gradient
+  // (which reuses the split buffer) and data gradient (which overwrites this
+  // delta) wait for both.
   for (int l = NET_LAYERS - 1; l >= 0; --l) {
     const NetLayer L = net_layer(l);
     ConvArgs a = conv_args(n, l, B);
@@ -319,6 +326,16 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
     a.wpart = n->wpart;
     const long long npo = (long long)B * L.hout * L.wout;
     int nchunk = (int)((npo + BW_CHUNK - 1) / BW_CHUNK);
+    if (l < NET_LAYERS - 1) cudaStreamWaitEvent(n->st, n->ev_join, 0);
+    cudaEventRecord(n->ev_fork1, n->st);
+    cudaStreamWaitEvent(n->st_side, n->ev_fork1, 0);
+    {  // bias gradient: about four CTAs per SM, slices of >= 4096 deltas
+      const int tot = B * L.hout * L.wout;
+      const int nsl = std::max(1, std::min({(4 * 148 + L.co - 1) / L.co, (tot + 4095) / 4096, NET_BPART / L.co}));
+      k_bias_grad_part<<<dim3((unsigned)L.co, (unsigned)nsl), CV_NT, 0, n->st_side>>>(n->delta[cur], B, L.co,
+                                                                                    L.hout * L.wout, nsl, n->bpart);
+      k_bias_grad_sum<<<(L.co + 255) / 256, 256, 0, n->st_side>>>(n->bpart, nsl, L.co, n->grads + n->b_off[l]);
+    }
     if (n->tc) {  // tensor cores: pixel splits of (co tile x k tile) GEMMs
       nchunk = bw_tc_splits(L, B, n->wpart_n);
       const dim3 g((unsigned)bw_tc_tiles(L), (unsigned)nchunk);
@@ -332,18 +349,15 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
       else k_conv_bwd_w<__nv_bfloat16><<<dim3((unsigned)(L.co * nciq), (unsigned)nchunk), CV_NT, 0, n->st>>>(a);
     }
     const size_t nw = (size_t)L.co * L.ci * 9;
+    cudaEventRecord(n->ev_fork2, n->st);
+    cudaStreamWaitEvent(n->st_side, n->ev_fork2, 0);
     if (nchunk >= 32 && nw <= 65536)  // few weights, many chunks: a warp per weight
-      k_sum_chunks_warp<<<(unsigned)((nw + 7) / 8), 256, 0, n->st>>>(n->wpart, nchunk, nw, n->grads + n->w_off[l]);
+      k_sum_chunks_warp<<<(unsigned)((nw + 7) / 8), 256, 0, n->st_side>>>(n->wpart, nchunk, nw,
+                                                                          n->grads + n->w_off[l]);
     else
-      k_sum_chunks<<<(unsigned)std::min<size_t>((nw + 255) / 256, 1184), 256, 0, n->st>>>(n->wpart, nchunk, nw,
-                                                                                            n->grads + n->w_off[l]);
-    {  // bias gradient: about four CTAs per SM, slices of >= 4096 deltas
-      const int tot = B * L.hout * L.wout;
-      const int nsl = std::max(1, std::min({(4 * 148 + L.co - 1) / L.co, (tot + 4095) / 4096, NET_BPART / L.co}));
-      k_bias_grad_part<<<dim3((unsigned)L.co, (unsigned)nsl), CV_NT, 0, n->st>>>(n->delta[cur], B, L.co,
-                                                                               L.hout * L.wout, nsl, n->bpart);
-      k_bias_grad_sum<<<(L.co + 255) / 256, 256, 0, n->st>>>(n->bpart, nsl, L.co, n->grads + n->b_off[l]);
-    }
+      k_sum_chunks<<<(unsigned)std::min<size_t>((nw + 255) / 256, 1184), 256, 0, n->st_side>>>(
+          n->wpart, nchunk, nw, n->grads + n->w_off[l]);
+    cudaEventRecord(n->ev_join, n->st_side);
     if (l > 0) {
       a.din = n->delta[cur ^ 1];
       a.mask = net_layer(l - 1).relu ? n->act[l - 1] : nullptr;
@@ -364,6 +378,7 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
       cur ^= 1;
     }
   }
+  cudaStreamWaitEvent(n->st, n->ev_join, 0);  // every gradient is in place
   if (int r = net_check(n, "backward")) return r;
   if (loss) {
     double part[lb];
@@ -457,6 +472,11 @@ int ptycho_net_create(ptycho_net** out, unsigned long long seed, int max_batch, 
     maxpart = std::max(maxpart, (size_t)want * L.co * L.ci * 9);
   }
   int r = 0;
+  if (cudaStreamCreateWithFlags(&n->st_side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_fork1, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    r = nfail(n, PTYCHO_ERR_CUDA, "side stream: %s", cudaGetErrorString(cudaGetLastError()));
   if (!r) r = nalloc(n, &n->params, n->n_params);
   if (!r) r = nalloc(n, &n->grads, n->n_params);
   if (!r) r = nalloc(n, &n->m, n->n_params);
@@ -645,6 +665,12 @@ void ptycho_net_destroy(ptycho_net* n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
   else cudaDeviceSynchronize();
+  if (n->st_side) {
+    cudaStreamSynchronize(n->st_side);
+    cudaStreamDestroy(n->st_side);
+  }
+  for (cudaEvent_t e : {n->ev_fork1, n->ev_fork2, n->ev_join})
+    if (e) cudaEventDestroy(e);
   void* bufs[] = {n->tc_part, n->bd_part, n->bpart, n->err_flag, n->params, n->grads, n->m,   n->v,        n->wb,       n->wt,       n->is_w,     n->wb_index, n->wt_index,
                   n->x,      n->out,   n->wpart, n->lpart, n->delta[0], n->delta[1]};
   for (void* b : bufs)
