@@ -570,7 +570,7 @@ def main():
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
     ap.add_argument("--warm-frames", type=int, default=200_000)
     ap.add_argument("--epie-only", action="store_true",
-                    help="run only the ePIE sweep of the 3-mode spiral scan and print its figures (profiling runs)")
+                    help="run only the ePIE sweeps of the 3-mode spiral scan, whole-pixel and sub-pixel (profiling runs)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the 64-scan batched workload and print its figures (profiling runs)")
     ap.add_argument("--engines-only", action="store_true",
@@ -604,7 +604,9 @@ def main():
 
     if args.epie_only:
         stream = torch.cuda.Stream()
-        print(json.dumps(run_epie(api, torch, stream)), flush=True)
+        ep = run_epie(api, torch, stream)
+        ep["subpixel"] = run_epie(api, torch, stream, subpixel=SUBPIXEL)
+        print(json.dumps(ep), flush=True)
         return
     if args.batch_only:
         stream = torch.cuda.Stream()
