@@ -72,6 +72,48 @@ def test_fullsize_residual_and_forward_sampled(workload):
         assert e < 2e-5, (SAMPLE[s], e)
 
 
+def test_fullsize_dm_pass_sampled(workload):
+    """The DM pass at the bench's launch shape (one exchange buffer, four CTAs
+    per SM), on sampled exit waves.  From psi = P O_j the first iteration's
+    overlap updates return O and P unchanged in exact arithmetic (num = den O)
+    and within FP32 rounding on the GPU (checked); the pass then forms
+    psi + F^-1 Pi(F(2 phi - psi)) - phi with phi = P O_j of the updated O, P.
+    The oracle takes that step from the GPU's own updated O and P (so the
+    check isolates the pass from the rounding of the sums, which the
+    projection amplifies where the far field is weak: from the start O, P
+    position 0 differs by 3.3e-5) and the start psi.  Bound 4e-5, twice the
+    single pass's: the pass's input 2 phi - psi has up to three times the
+    exit wave's magnitude and its output adds phi to the inverse transform,
+    two more FP32 roundings of exit-wave size ahead of and behind the
+    projection (measured at most 2.04e-5 over the sampled positions)."""
+    torch = pytest.importorskip("torch")
+    P, O, pos, P0, I = workload
+    J = len(pos)
+    O0 = synth.make_object(2640, 2640, seed=1002)
+    P0 = synth.noisy_probe(P, 0.1, seed=80)
+    with api.Reconstruction(M, K, J, O.shape) as r:
+        assert r.cluster == 16
+        r.set_data(I, pos)
+        r.set_init(O0, P0)
+        r.iterate("dm", 1)
+        psi = torch.empty((J, K, M, M), dtype=torch.complex64, device="cuda")
+        r.get_exit_waves(psi)
+        torch.cuda.synchronize()
+        got = psi[SAMPLE].cpu().numpy()
+        O1, P1 = r.get_object(), r.get_probe()
+        del psi
+    # the start comes back unchanged up to FP32 rounding
+    assert np.linalg.norm(O1 - O0) / np.linalg.norm(O0) < 1e-5
+    assert np.linalg.norm(P1 - P0) / np.linalg.norm(P0) < 1e-5
+    pi = orc.round_positions(pos[SAMPLE])
+    psi0 = orc.exit_waves(O0.astype(np.complex128), P0.astype(np.complex128), pi)
+    phi = orc.exit_waves(O1.astype(np.complex128), P1.astype(np.complex128), pi)
+    ref = psi0 + orc.ifft2(orc.project(orc.fft2(2.0 * phi - psi0), orc.to_fft_order(I[SAMPLE].astype(np.float64)))) - phi
+    errs = [float(np.linalg.norm(got[s_] - ref[s_]) / np.linalg.norm(ref[s_])) for s_ in range(len(SAMPLE))]
+    print("full-size DM pass, sampled exit waves against the oracle:", max(errs))
+    assert max(errs) < 4e-5, list(zip(SAMPLE, errs))
+
+
 def test_fullsize_step_mode_equals_whole_mode(workload):
     P, O, pos, P0, I = workload
     outs = []
