@@ -285,9 +285,18 @@ int net_forward_tc(ptycho_net* n, int B) {
   for (int l = 0; l < NET_LAYERS; ++l) {
     const NetLayer L = net_layer(l);
     ConvArgs a = conv_args(n, l, B);
-    if (L.ci >= 8) a.w = n->wt + n->wb_off[l];  // the NCHW gather takes tap-major k from 8 channels on
     const bool last = l == NET_LAYERS - 1;
     a.out = last ? (void*)n->out : n->act[l];
+    if (l == 0) {
+      // the 1 -> 16 layer (144 FMAs per pixel) on CUDA cores, as in
+      // inference: its tensor-core K chunk is 9 / 64 full (47 against 85 us
+      // per step; the 16 -> 2 layer measured the other way, 71 against 52 us)
+      const dim3 g((unsigned)(((long long)B * L.hout * L.wout + CV_NT - 1) / CV_NT),
+                   (unsigned)((L.co + CV_CO - 1) / CV_CO));
+      k_conv_fwd<__nv_bfloat16, false><<<g, CV_NT, 0, n->st>>>(a);
+      continue;
+    }
+    if (L.ci >= 8) a.w = n->wt + n->wb_off[l];  // the NCHW gather takes tap-major k from 8 channels on
     const int np = L.co <= 16 ? 16 : L.co;
     switch (np) {
       case 16: launch_conv_tc<16>(n, a, L, last); break;
