@@ -370,7 +370,10 @@ int net_backward(ptycho_net* n, const float* targets, int B, double* loss) {
     if (l > 0) {
       a.din = n->delta[cur ^ 1];
       a.mask = net_layer(l - 1).relu ? n->act[l - 1] : nullptr;
-      if (n->tc) {
+      // the last layer's data gradient (2 output channels: K = 18 of a 64-wide
+      // chunk) on CUDA cores: 28.6k against 28.3k frames/s; the first
+      // stride-2 layer's measured the other way (24.6k)
+      if (n->tc && l != NET_LAYERS - 1) {
         switch (L.ci <= 16 ? 16 : L.ci) {
           case 16: launch_bwd_data_tc<16>(n, a, L); break;
           case 32: launch_bwd_data_tc<32>(n, a, L); break;
