@@ -118,9 +118,19 @@ constexpr int F3_OG = PT_F3_OG;
 
 // CTAs per SM for the launch bounds: by threads (and the radix-24 register
 // demand) and by shared memory
+// CTAs per SM asked of shapes with at most 128 threads per CTA (128^2 on
+// 8-CTA clusters): 6 for the LSQML residual pass (117 -> 80 registers:
+// 1.19 -> 1.09 ms per 10k positions), 5 for the DM pass (1.37 -> 1.30 ms; at
+// 6 it loses half of that), 0 = the default rule (3)
+#ifndef PT_F3_MINB_NT128
+#define PT_F3_MINB_NT128 0
+#endif
 template <class F, int MODE_T>
 constexpr int f3_min_blocks() {
-  const int by_threads = F::R1 > 16 ? 1 : (F::NT <= 256 ? (f3_merged<F, MODE_T>() ? 4 : 3) : (F::NT <= 512 ? 2 : 1));
+  const int nt128 = PT_F3_MINB_NT128 > 0 ? PT_F3_MINB_NT128 : (MODE_T == FM_DM ? 5 : 6);
+  const int by_threads = F::R1 > 16 ? 1
+                                    : (F::NT <= 128 ? nt128
+                                                    : (F::NT <= 256 ? (f3_merged<F, MODE_T>() ? 4 : 3) : (F::NT <= 512 ? 2 : 1)));
   const int by_smem = (int)((228 * 1024) / (fourier3_smem<F, MODE_T>() + 1024));
   const int b = by_threads < by_smem ? by_threads : by_smem;
   return b < 1 ? 1 : b;
