@@ -50,6 +50,9 @@ constexpr int PROBE_NT = 256;
 #ifndef PT_PROBE_UJ
 #define PT_PROBE_UJ 8     // positions per step of the probe sums, K = 1 (8: 0.945 ms vs 1.03 at 4, 1.22 at 16)
 #endif
+#ifndef PT_PROBE_UJ16
+#define PT_PROBE_UJ16 4   // the same for FP16 residuals (two pixels per thread)
+#endif
 #ifndef PT_STEP_UNROLL
 #define PT_STEP_UNROLL 1  // pixel-loop unrolling of the step-size kernel
 #endif
@@ -325,23 +328,38 @@ struct ProbeArgs {
 };
 
 // SUB: positions taken through the bin order and its group offsets.
+// Pixels per thread: one for FP32 residuals, two adjacent ones (in one row, M
+// being even) for FP16 residuals of one mode, whose 4-byte values would
+// otherwise halve the bytes each load request moves (with three modes the
+// two-pixel form needs over 100 registers).  Each pixel sums its positions
+// in the same order either way.
 #ifndef PT_PROBE_MINB
 #define PT_PROBE_MINB 1   // occupancy hint of the probe partial sums (1: none)
 #endif
+template <typename XT, int K>
+__host__ __device__ constexpr int probe_px() {
+  return sizeof(XT) == 4 && K == 1 ? 2 : 1;
+}
 template <int K, bool SUB, typename XT = float2>
 __global__ void __launch_bounds__(PROBE_NT, PT_PROBE_MINB) k_probe_partial(ProbeArgs a) {
+  constexpr int PX = probe_px<XT, K>();
   const int MM = a.M * a.M;
-  const int u = blockIdx.x * PROBE_NT + threadIdx.x;
+  const int u = (blockIdx.x * PROBE_NT + threadIdx.x) * PX;  // first pixel of this thread
   const int uy = u / a.M, ux = u % a.M;
   const int g = blockIdx.y;
   const int jb = SUB ? a.goff[g] : a.jlo + (int)(((long long)a.J * g) / a.G);
   const int je = SUB ? a.goff[g + 1] : a.jlo + (int)(((long long)a.J * (g + 1)) / a.G);
-  float2 num[K];
+  float2 num[PX][K];
+  float den[PX];
 #pragma unroll
-  for (int k = 0; k < K; ++k) num[k] = make_float2(0.f, 0.f);
-  float den = 0.f;
+  for (int e = 0; e < PX; ++e) {
+    den[e] = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) num[e][k] = make_float2(0.f, 0.f);
+  }
   const bool want_den = a.part_den != nullptr;
-  constexpr int UJ = K == 1 ? PT_PROBE_UJ : 4;  // positions per step: UJ*(K+1) independent loads in flight
+  // positions per step: UJ*(K+1) independent loads in flight
+  constexpr int UJ = PX == 2 ? PT_PROBE_UJ16 : (K == 1 ? PT_PROBE_UJ : 4);
   __shared__ int2 sp[PROBE_CHUNK];
   __shared__ float sw[PROBE_CHUNK];
   __shared__ int sj[SUB ? PROBE_CHUNK : 1];
@@ -357,37 +375,70 @@ __global__ void __launch_bounds__(PROBE_NT, PT_PROBE_MINB) k_probe_partial(Probe
     __syncthreads();
     if (u < MM) {
       for (int s = 0; s < nc; s += UJ) {
-        float2 o[UJ], xv[UJ][K];
+        float2 o[UJ][PX], xv[UJ][K][PX];
         float w[UJ];
 #pragma unroll
         for (int h = 0; h < UJ; ++h) {
           const bool in = s + h < nc;
           const int i = in ? s + h : 0;
           const int2 p = sp[i];
-          o[h] = in ? __ldg(a.O + (size_t)(p.x + uy) * a.nx + p.y + ux) : make_float2(0.f, 0.f);
+          if constexpr (PX == 1) {
+            o[h][0] = in ? __ldg(a.O + (size_t)(p.x + uy) * a.nx + p.y + ux) : make_float2(0.f, 0.f);
+          } else {
+            const size_t r = (size_t)(p.x + uy) * a.nx + p.y + ux;
+            // the object pixel pair is 16-byte aligned when the patch's first
+            // column and the row length are even (uniform over the block)
+            float4 oq = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in && ((p.y | a.nx) & 1) == 0) {
+              oq = __ldg(reinterpret_cast<const float4*>(a.O + r));
+            } else if (in) {
+              const float2 o0 = __ldg(a.O + r), o1 = __ldg(a.O + r + 1);
+              oq = make_float4(o0.x, o0.y, o1.x, o1.y);
+            }
+            o[h][0] = make_float2(oq.x, oq.y);
+            o[h][1] = make_float2(oq.z, oq.w);
+          }
           w[h] = in ? sw[i] : 0.f;
 #pragma unroll
-          for (int k = 0; k < K; ++k)
-            xv[h][k] = in ? ld_x<XT>(a.X, ((size_t)((SUB ? sj[i] : c0 + i) - a.xoff) * K + k) * MM + u)
-                          : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int h = 0; h < UJ; ++h) {
-          if (want_den) den += cabs2(o[h]);
-#pragma unroll
           for (int k = 0; k < K; ++k) {
-            const float2 t = cconjmul(o[h], xv[h][k]);
-            num[k].x = fmaf(w[h], t.x, num[k].x);
-            num[k].y = fmaf(w[h], t.y, num[k].y);
+            if constexpr (PX == 1) {
+              xv[h][k][0] = in ? ld_x<XT>(a.X, ((size_t)((SUB ? sj[i] : c0 + i) - a.xoff) * K + k) * MM + u)
+                               : make_float2(0.f, 0.f);
+            } else {
+              const size_t xi = ((size_t)((SUB ? sj[i] : c0 + i) - a.xoff) * K + k) * MM + u;
+              const float4 xq = in ? ld_x2<XT>(a.X, xi) : make_float4(0.f, 0.f, 0.f, 0.f);
+              xv[h][k][0] = make_float2(xq.x, xq.y);
+              xv[h][k][1] = make_float2(xq.z, xq.w);
+            }
           }
         }
+#pragma unroll
+        for (int h = 0; h < UJ; ++h)
+#pragma unroll
+          for (int e = 0; e < PX; ++e) {
+            if (want_den) den[e] += cabs2(o[h][e]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const float2 t = cconjmul(o[h][e], xv[h][k][e]);
+              num[e][k].x = fmaf(w[h], t.x, num[e][k].x);
+              num[e][k].y = fmaf(w[h], t.y, num[e][k].y);
+            }
+          }
       }
     }
   }
   if (u >= MM) return;
 #pragma unroll
-  for (int k = 0; k < K; ++k) a.part_num[((size_t)g * K + k) * MM + u] = num[k];
-  if (want_den) a.part_den[(size_t)g * MM + u] = den;
+  for (int k = 0; k < K; ++k) {
+    float2* dst = a.part_num + ((size_t)g * K + k) * MM + u;
+    if constexpr (PX == 1) *dst = num[0][k];
+    else *reinterpret_cast<float4*>(dst) = make_float4(num[0][k].x, num[0][k].y, num[1][k].x, num[1][k].y);
+  }
+  if (want_den) {
+    float* dst = a.part_den + (size_t)g * MM + u;
+    if constexpr (PX == 1) *dst = den[0];
+    else *reinterpret_cast<float2*>(dst) = make_float2(den[0], den[1]);
+  }
 }
 
 // Sum the G partials in group order (sub-pixel: per bin, into num[bin]);

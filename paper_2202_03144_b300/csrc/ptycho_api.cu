@@ -977,12 +977,13 @@ int launch_probe(ptycho_ctx* ctx, int mode, const float2* X, const float* w, boo
   const double xb = (ctx->x16 && X == ctx->X ? 4.0 : 8.0) * a.J * K * (double)MM;
   if (X) {
     if (int r = launch(ctx, "probe_partial", xb, [&] {
-          const bool h = ctx->x16 && X == ctx->X;  // FP16 residuals
+          const bool h = ctx->x16 && X == ctx->X;  // FP16 residuals: two pixels per thread
+          const int nbh = (MM / probe_px<__half2, K>() + PROBE_NT - 1) / PROBE_NT;
           if (ctx->S) {
-            if (h) k_probe_partial<K, true, __half2><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+            if (h) k_probe_partial<K, true, __half2><<<dim3(nbh, a.G), PROBE_NT, 0, ctx->st>>>(a);
             else k_probe_partial<K, true><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
           } else {
-            if (h) k_probe_partial<K, false, __half2><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
+            if (h) k_probe_partial<K, false, __half2><<<dim3(nbh, a.G), PROBE_NT, 0, ctx->st>>>(a);
             else k_probe_partial<K, false><<<dim3(nblk, a.G), PROBE_NT, 0, ctx->st>>>(a);
           }
         }))

@@ -88,3 +88,31 @@ def test_fp16_residuals_leave_dm_and_the_residual_call_fp32():
             outs.append((chi, r.get_object(), r.get_exit_waves()))
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("width", ["even", "odd"])
+def test_fp16_residual_probe_sums_any_alignment(width):
+    """The probe sums take two adjacent pixels per thread from FP16
+    residuals; the object pair is one 16-byte load only where the patch's
+    first column and the object's row length are both even, two 8-byte loads
+    otherwise.  Positions of both column parities, on objects of even and odd
+    width, match the oracle as the other cases do, and the FP32-residual run
+    to within the FP16 rounding."""
+    c = scan(64, 1, grid=4, photons=1e6)
+    ny, nx = c["shape"]
+    nx2 = nx + (nx & 1) + (1 if width == "odd" else 0)
+    O0 = np.ones((ny, nx2), np.complex128)
+    O0[:, :nx] = c["O0"]
+    c = dict(c, O0=O0, shape=(ny, nx2))
+    cols = orc.round_positions(c["pos"])[:, 1].astype(int)
+    assert (cols % 2 == 0).any() and (cols % 2 == 1).any()
+    n = 3
+    Og, Pg, E = _run(c, n, residual_store="f16")
+    O32, P32, E32 = _run(c, n)
+    Oc, Pc, _ = orc.reconstruct("lsqml", c["O0"], c["P0"], c["pos"], c["I"], n)
+    m = illuminated(c["P"], c["pos"], c["shape"])
+    eo, ep = rel_l2(align_global(Og, Oc, m), Oc, m), rel_l2(Pg, Pc)
+    d32 = rel_l2(Pg, P32)
+    print(f"FP16 residuals, {width} width: object {eo:.2e} probe {ep:.2e} (probe {d32:.2e} from FP32 residuals)")
+    assert eo < TOL_R16 and ep < TOL_R16, (eo, ep)
+    assert d32 < TOL_R16 and abs(E - E32) <= 1e-3 * E32

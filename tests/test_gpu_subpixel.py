@@ -133,6 +133,28 @@ def test_subpixel_16bit_storage(istore):
     assert rel_l2(align_global(Og, Oc, m), Oc, m) < tol and rel_l2(Pg, Pc) < tol
 
 
+def test_subpixel_fp16_residuals():
+    """FP16 residual storage with sub-pixel positions (the probe sums then
+    walk the positions in bin order, two pixels per thread): within the
+    FP16-residual bound of the integer path (1e-3) of the oracle, and
+    n x iterate(1) == iterate(n) bit for bit."""
+    c = subpixel_scan(64, 1, 8, grid=3, photons=1e6)
+    n = 3
+    Oc, Pc, _ = orc.reconstruct("lsqml", c["O0"], c["P0"], c["pos"], c["I"], n, subpixel=8)
+    with _recon(c, cluster=2, residual_store="f16") as r:
+        r.iterate("lsqml", n)
+        Og, Pg = r.get_object(), r.get_probe()
+    with _recon(c, cluster=2, residual_store="f16") as r:
+        for _ in range(n):
+            r.iterate("lsqml", 1)
+        Os, Ps = r.get_object(), r.get_probe()
+    assert np.array_equal(Og, Os) and np.array_equal(Pg, Ps)
+    m = _illuminated(c)
+    eo, ep = rel_l2(align_global(Og, Oc, m), Oc, m), rel_l2(Pg, Pc)
+    print(f"sub-pixel, FP16 residuals: object {eo:.2e} probe {ep:.2e}")
+    assert eo < 1e-3 and ep < 1e-3, (eo, ep)
+
+
 @pytest.mark.parametrize("alg", ["dm", "lsqml"])
 def test_subpixel_step_mode_equals_whole_mode(alg):
     c = subpixel_scan(32, 3, 8, grid=3, photons=1e5)
