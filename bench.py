@@ -721,10 +721,10 @@ def main():
     # on a 2500-position cut (profiles/fourier_chi_det256_2500pos.md): bytes
     # per position, scaled to this launch's positions (amplitudes in,
     # residuals out: traffic grows in proportion).  Only for the kernel and
-    # shape that capture measured.
+    # shape that capture measured (FP32 residuals).
     traffic = None
-    if top[0] == "fourier_chi" and (M, K) == (256, 1) and not args.cluster:
-        traffic = 769.8e3 * J
+    if top[0] == "fourier_chi" and (M, K) == (256, 1) and not args.cluster and args.residual_store == "f32":
+        traffic = 768.5e3 * J
     step_bytes = sum(v["bytes"] for v in prof.values())
     if top[0].startswith("fourier"):
         # The fused Fourier kernel is bound by FP32 arithmetic issue, not by
